@@ -1,0 +1,205 @@
+"""FP64 oracle of the per-Gaussian spatiotemporal motion-probability update.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Follows Sec. IV-A and Eq. (17) step by step, one view:
+
+  per pixel p (the "features" of the hot path are the image pixels)
+    e(p)        residual between observed and rendered RGB-D: the hot path has
+                no feature matches, so the reprojection error of Eq. (3) is
+                read as |D_obs - D_rend| + kappa_c * ||C_obs - C_rend||_1 (m);
+                the depth term only where D_obs > 0
+    region k    the instance label of p (0 = background, its own region)
+    mu_e, sigma_e, e_ub   Eq. (4) over the region's pixels (population std);
+                e_ub is floored at e_floor (a reading: without it a static
+                instance normalises its own noise to MP_geo ~ 1)
+    MP_geo      Eq. (5); inside an instance whose sigma_e < sigma_min the
+                instance mean replaces e(p) ("use the instance-mean error")
+    MP_ins, Gamma_ins     Eq. (2) from the instance table (row 0 = background)
+    Gamma_geo   exp(-sigma_e,k / sigma_g) of the pixel's region
+    K_p, M_p    Eqs. (6), (7)  (fusion_mode 1 forces K = 0, 2 forces K = 1)
+  per Gaussian G
+    N(G)        pixels within r_s of the projected mean, Eq. (1), one scale;
+                w(p, G) = exp(-|p - pi(G)|^2 / (2 sigma_w^2))
+    observed    z > z_near, N(G) non-empty, and not behind the rendered
+                surface: z <= max_{N(G)} D_rend + vis_tol
+    M_hat       Eq. (8)
+    U           Eq. (10): binary entropy of M^{t-1} (natural log, eps) +
+                lambda_u * Var{M_p} (population variance over N(G))
+    U_tilde     min-max normalisation over the observed Gaussians (0 if all equal)
+    C           exp(-sigma_e,G / sigma_c), sigma_e,G = population std of e over N(G)
+    alpha       Eq. (11); alpha' = rho * alpha when the prior was not
+                refreshed, Eq. (17)
+    M^t         Eq. (9)
+  per frame
+    tau         Eq. (12) with the lower median of M^t over observed Gaussians
+    labels      dynamic iff M^t > tau; unobserved Gaussians keep M and label
+    U_bar       Eq. (13): lower median of U_tilde over observed Gaussians
+
+Pins: the K = 0 / K = 1 special cases, fixed and instant rates, the rho
+scaling, M in [0, 1], tau >= 0.5, unobserved unchanged, and closed-form cases
+in tests/test_oracle_mp.py.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, asdict
+
+import numpy as np
+
+
+@dataclass
+class MPConfig:
+    kappa_c: float = 0.05      # m per unit of L1 colour residual
+    lam: float = 2.0           # lambda in e_ub = mu_e + lambda sigma_e, Eq. (4)
+    sigma_min: float = 0.005   # "sigma_e is small" threshold (m)
+    e_floor: float = 0.05      # floor on e_ub (m)
+    sigma_g: float = 0.05      # Gamma_geo scale (m), Eq. (7)
+    sigma_c: float = 0.05      # C scale (m), Eq. (11)
+    lam_u: float = 1.0         # lambda_u, Eq. (10)
+    eps: float = 1e-6          # epsilon, Eq. (10)
+    alpha_min: float = 0.05
+    alpha_max: float = 0.6
+    rho: float = 0.5           # Eq. (17)
+    r_s: float = 2.0           # association radius (px), Eq. (1)
+    sigma_w: float = 1.0       # association kernel width (px)
+    vis_tol: float = 0.1       # occlusion tolerance (m); <= 0 disables
+    z_near: float = 0.2
+    tau_floor: float = 0.5     # Eq. (12)
+    fusion_mode: int = 0       # 0 fused, 1 K = 0 (MP_ins only), 2 K = 1 (MP_geo only)
+
+    def as_dict(self):
+        return asdict(self)
+
+
+def lower_median(x: np.ndarray) -> float:
+    """Element at index floor((n-1)/2) of the ascending sort."""
+    s = np.sort(np.asarray(x, dtype=np.float64))
+    return float(s[(len(s) - 1) // 2])
+
+
+def pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg: MPConfig):
+    """Per-pixel fused MP observation. Returns dict(e, e_used, M_p, K,
+    region stats (count, mean, std, e_ub) per label)."""
+    inst = np.asarray(inst).astype(np.int64).ravel()
+    d_obs = np.asarray(d_obs, np.float64).ravel()
+    d_rend = np.asarray(d_rend, np.float64).ravel()
+    c_obs = np.asarray(c_obs, np.float64).reshape(-1, 3)
+    c_rend = np.asarray(c_rend, np.float64).reshape(-1, 3)
+    table = np.asarray(table, np.float64).reshape(-1, 2)
+    nreg = table.shape[0]
+    e = np.where(d_obs > 0, np.abs(d_obs - d_rend), 0.0) + cfg.kappa_c * np.abs(c_obs - c_rend).sum(1)
+    cnt = np.zeros(nreg)
+    mean = np.zeros(nreg)
+    std = np.zeros(nreg)
+    for k in range(nreg):
+        sel = e[inst == k]
+        cnt[k] = sel.size
+        if sel.size:
+            mean[k] = sel.mean()
+            std[k] = np.sqrt(np.mean((sel - mean[k]) ** 2))
+    e_ub = np.maximum(mean + cfg.lam * std, cfg.e_floor)
+    small = (np.arange(nreg) >= 1) & (std < cfg.sigma_min)
+    e_used = np.where(small[inst], mean[inst], e)
+    mp_geo = np.clip(e_used / e_ub[inst], 0.0, 1.0)
+    mp_ins = table[inst, 0]
+    g_ins = table[inst, 1]
+    g_geo = np.exp(-std[inst] / cfg.sigma_g)
+    K = g_geo / (g_ins + g_geo)
+    if cfg.fusion_mode == 1:
+        K = np.zeros_like(K)
+    elif cfg.fusion_mode == 2:
+        K = np.ones_like(K)
+    M_p = (1.0 - K) * mp_ins + K * mp_geo
+    return dict(e=e, e_used=e_used, mp_geo=mp_geo, mp_ins=mp_ins, K=K, M_p=M_p, count=cnt, mean=mean,
+                std=std, e_ub=e_ub)
+
+
+def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend, c_rend, table,
+              cfg: MPConfig = None, seg_refreshed: bool = True):
+    """One MP update. cam = (fx, fy, cx, cy, W, H); pose 3x4 world->camera.
+
+    Returns dict with mp (n), labels (n, uint8), observed (n bool), m_hat,
+    U, U_tilde, alpha (after Eq. (17)), tau, U_bar, median_M, the pixel dict,
+    and decision-margin flags: label_flag (|M^t - tau| small), disk_flag (a
+    pixel within 1e-5 of the association radius), vis_flag (occlusion test
+    within 1e-5).
+    """
+    cfg = MPConfig() if cfg is None else cfg
+    fx, fy, cx, cy, W, H = cam
+    W, H = int(W), int(H)
+    px = pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg)
+    M_p, e = px["M_p"], px["e"]
+    d_rend = np.asarray(d_rend, np.float64).ravel()
+    means = np.asarray(means, np.float64).reshape(-1, 3)
+    n = means.shape[0]
+    pose = np.asarray(pose, np.float64).reshape(3, 4)
+    pc = means @ pose[:, :3].T + pose[:, 3]
+    mp_prev = np.asarray(mp_prev, np.float64)
+    out_mp = mp_prev.copy()
+    labels = np.asarray(labels_prev).astype(np.uint8).copy()
+    observed = np.zeros(n, bool)
+    m_hat = np.zeros(n)
+    var = np.zeros(n)
+    sig_e = np.zeros(n)
+    disk_flag = np.zeros(n, bool)
+    vis_flag = np.zeros(n, bool)
+    R = int(np.ceil(cfg.r_s)) + 1
+    for g in range(n):
+        x, y, z = pc[g]
+        if not z > cfg.z_near:
+            continue
+        u = fx * x / z + cx
+        v = fy * y / z + cy
+        i0, j0 = int(np.floor(u)), int(np.floor(v))
+        ii, jj = np.meshgrid(np.arange(i0 - R, i0 + R + 2), np.arange(j0 - R, j0 + R + 2), indexing="xy")
+        ii, jj = ii.ravel(), jj.ravel()
+        inside = (ii >= 0) & (ii < W) & (jj >= 0) & (jj < H)
+        d2 = (ii - u) ** 2 + (jj - v) ** 2
+        if np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= 1e-5 * cfg.r_s ** 2)):
+            disk_flag[g] = True
+        sel = inside & (d2 <= cfg.r_s ** 2)
+        if not np.any(sel):
+            continue
+        pidx = jj[sel] * W + ii[sel]
+        dmax = d_rend[pidx].max()
+        if cfg.vis_tol > 0 and dmax > 0:
+            if abs(z - (dmax + cfg.vis_tol)) <= 1e-5 * (dmax + cfg.vis_tol):
+                vis_flag[g] = True
+            if z > dmax + cfg.vis_tol:
+                continue
+        w = np.exp(-d2[sel] / (2.0 * cfg.sigma_w ** 2))
+        mp_set = M_p[pidx]
+        m_hat[g] = np.sum(w * mp_set) / np.sum(w)
+        var[g] = np.mean((mp_set - mp_set.mean()) ** 2)
+        es = e[pidx]
+        sig_e[g] = np.sqrt(np.mean((es - es.mean()) ** 2))
+        observed[g] = True
+    M0 = mp_prev
+    ent = -M0 * np.log(M0 + cfg.eps) - (1.0 - M0) * np.log(1.0 - M0 + cfg.eps)
+    U = ent + cfg.lam_u * var
+    U_t = np.zeros(n)
+    alpha = np.zeros(n)
+    tau = cfg.tau_floor
+    U_bar = 0.0
+    med = float("nan")
+    label_flag = np.zeros(n, bool)
+    if observed.any():
+        uo = U[observed]
+        umin, umax = uo.min(), uo.max()
+        if umax > umin:
+            U_t[observed] = (uo - umin) / (umax - umin)
+        C = np.exp(-sig_e / cfg.sigma_c)
+        a = cfg.alpha_min + (cfg.alpha_max - cfg.alpha_min) * (1.0 - U_t) * C
+        a = np.clip(a, cfg.alpha_min, cfg.alpha_max)
+        if not seg_refreshed:
+            a = cfg.rho * a
+        alpha = np.where(observed, a, 0.0)
+        out_mp = np.where(observed, (1.0 - alpha) * M0 + alpha * m_hat, M0)
+        med = lower_median(out_mp[observed])
+        tau = max(med, cfg.tau_floor)
+        U_bar = lower_median(U_t[observed])
+        labels = np.where(observed, (out_mp > tau).astype(np.uint8), labels).astype(np.uint8)
+        label_flag = observed & (np.abs(out_mp - tau) <= 1e-5)
+    return dict(mp=out_mp, labels=labels, observed=observed, m_hat=m_hat, var=var, sigma_e=sig_e, U=U,
+                U_tilde=U_t, alpha=alpha, tau=tau, U_bar=U_bar, median_M=med, pixel=px,
+                label_flag=label_flag, disk_flag=disk_flag, vis_flag=vis_flag)

@@ -1,0 +1,677 @@
+/*
+ * FP64 CPU oracle of the MP-aware differentiable Gaussian splatting path.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may link or call this
+ * file; only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it. It shares no code with the CUDA kernels.
+ *
+ * What it computes, in plain double precision, one view at a time:
+ *
+ *   project   the 3D Gaussian of each record to a 2D conic (EWA splatting,
+ *             the rasterisation the paper inherits from 3DGS, Sec. IV-D
+ *             "during rasterization");
+ *   render    for every pixel, front-to-back alpha compositing of colour,
+ *             depth, opacity and motion probability over ALL Gaussians in
+ *             (depth, id) order; the per-pixel static weight w(u) of Eq. (20)
+ *             and the MP-weighted L1 photometric and depth losses of
+ *             Eqs. (21), (22) with the lambda_1, lambda_2 of Sec. V-A(c);
+ *   backward  the hand-derived adjoint of all of the above with respect to
+ *             every Gaussian parameter and to the left-perturbation twist of
+ *             the world-to-camera pose (joint optimisation of Gaussians and
+ *             poses, Eq. (27));
+ *   binning   the (tile, Gaussian) pair list sorted by (tile, depth, id).
+ *
+ * The paper does not print the rasteriser's equations or constants; the
+ * readings used here (alpha clamp 0.99, skip below 1/255, stop before
+ * transmittance falls under 1e-4, 0.3 px^2 dilation, near plane 0.2 m,
+ * 1.3x frustum guard on the Jacobian, opacity-aware bounding radius) are
+ * stated in the design notes and mirrored in the C ABI's config struct.
+ *
+ * Decisions that floating point takes (skip, clamp, stop, tile bounds,
+ * depth ties, residual signs) are flagged when the FP64 quantity lies within
+ * a relative 1e-5 of its threshold, so a test can tell an FP32-vs-FP64
+ * rounding disagreement from a bug.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- layouts shared with the Python wrapper (oracle/__init__.py) ---- */
+
+/* Gaussian parameters, FP64, one row of G_STRIDE per Gaussian. */
+enum { G_MX = 0, G_MY, G_MZ, G_LOGIT, G_QW, G_QX, G_QY, G_QZ, G_S0, G_S1, G_S2,
+       G_MP, G_CR, G_CG, G_CB, G_STRIDE };
+
+/* Camera: fx, fy, cx, cy, width, height. Pose: 3x4 row-major [R | t], world->camera. */
+enum { CAM_FX = 0, CAM_FY, CAM_CX, CAM_CY, CAM_W, CAM_H };
+
+/* Raster constants. */
+enum { RC_TILE = 0, RC_ALPHA_MIN, RC_ALPHA_MAX, RC_T_MIN, RC_DILATION, RC_Z_NEAR,
+       RC_GUARD, RC_N };
+
+/* Loss constants: lambda_pho, lambda_depth, weight_mode (0: normalised w =
+ * (O - R_MP)/O, 1: unnormalised w = O - R_MP), weight_grad (0: w is a
+ * constant in the adjoint), o_eps (normalised w is 0 where O <= o_eps). */
+enum { LC_LPHO = 0, LC_LDEPTH, LC_WMODE, LC_WGRAD, LC_OEPS, LC_N };
+
+/* Projection record per Gaussian. */
+enum { PJ_VIS = 0, PJ_U, PJ_V, PJ_Z, PJ_A, PJ_B, PJ_C, PJ_O, PJ_SA, PJ_SB, PJ_SC,
+       PJ_LMAX, PJ_R, PJ_X0, PJ_Y0, PJ_X1, PJ_Y1, PJ_FLAG, PJ_PX, PJ_PY, PJ_STRIDE };
+
+/* Per-pixel output: colour (3), depth, opacity, rendered MP, final
+ * transmittance, number of contributors, id of the last contributor (-1),
+ * static weight w(u) of Eq. (20) (0 without targets). */
+enum { PX_CR = 0, PX_CG, PX_CB, PX_D, PX_O, PX_RMP, PX_T, PX_N, PX_LAST, PX_W, PX_STRIDE };
+
+/* Gradient per Gaussian, same layout as G_*. */
+
+/* Flag bits. */
+#define FL_ZNEAR    1   /* depth within margin of the near plane           */
+#define FL_CLAMP    2   /* x/z or y/z within margin of the frustum guard    */
+#define FL_RADIUS   4   /* bounding radius within margin of an integer      */
+#define FL_RECT     8   /* (u +- r)/tile within margin of an integer        */
+#define FL_OPAC    16   /* opacity within margin of alpha_min               */
+#define FL_ALPHA   32   /* pixel: some o*G within margin of alpha_min        */
+#define FL_AMAX    64   /* pixel: some o*G within margin of alpha_max        */
+#define FL_TSTOP  128   /* pixel: transmittance test within margin of t_min  */
+#define FL_ZTIE   256   /* pixel/bin: two consecutive depths within 1e-6 z   */
+#define FL_OEPS   512   /* pixel: opacity within margin of o_eps             */
+#define FL_SIGN  1024   /* pixel: a loss residual within margin of zero      */
+
+#define MARGIN 1e-5
+
+static int near_rel(double x, double thr) { return fabs(x - thr) <= MARGIN * fabs(thr); }
+
+static int near_int(double x) {
+  double f = x - floor(x + 0.5);
+  return fabs(f) <= MARGIN * fmax(1.0, fabs(x));
+}
+
+/* Rotation matrix of the unit quaternion n = q/|q| (Hamilton convention,
+ * scalar first), row-major. */
+static void quat_rot(const double *q, double *R, double *nq, double *qn) {
+  double len = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  double w = q[0] / len, x = q[1] / len, y = q[2] / len, z = q[3] / len;
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+  if (nq) { nq[0] = w; nq[1] = x; nq[2] = y; nq[3] = z; }
+  if (qn) *qn = len;
+}
+
+/* C = A * B for 3x3 row-major. */
+static void mm3(const double *A, const double *B, double *C) {
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) {
+      double s = 0;
+      for (int k = 0; k < 3; k++) s += A[3 * i + k] * B[3 * k + j];
+      C[3 * i + j] = s;
+    }
+}
+static void tr3(const double *A, double *T) {
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) T[3 * j + i] = A[3 * i + j];
+}
+
+/* Everything projection computes for one Gaussian, kept for the adjoint. */
+typedef struct {
+  int vis, flags;
+  double p[3];          /* camera-space mean                        */
+  double tx, ty;        /* clamped x/z, y/z                          */
+  int clx, cly;         /* 1 if the guard clamp was active           */
+  double J[6];          /* 2x3 projection Jacobian                   */
+  double Rq[9];         /* rotation of the Gaussian                  */
+  double nq[4], qlen;   /* unit quaternion and |q|                   */
+  double S[3];          /* exp(log-scale)                            */
+  double Sig[9];        /* world covariance                          */
+  double Sc[9];         /* camera covariance                         */
+  double A, B, C;       /* 2D covariance after dilation              */
+  double a, b, c;       /* conic = inverse 2D covariance             */
+  double o, u, v, lmax, rext;
+  int r, x0, y0, x1, y1;
+} proj_t;
+
+static void project_one(const double *g, const double *cam, const double *pose,
+                        const double *rc, proj_t *P) {
+  memset(P, 0, sizeof(*P));
+  const double *Rw = pose; /* rows at 0,4,8; t at 3,7,11 */
+  double R[9] = {pose[0], pose[1], pose[2], pose[4], pose[5], pose[6], pose[8], pose[9], pose[10]};
+  double t[3] = {pose[3], pose[7], pose[11]};
+  (void)Rw;
+  for (int i = 0; i < 3; i++)
+    P->p[i] = R[3 * i] * g[G_MX] + R[3 * i + 1] * g[G_MY] + R[3 * i + 2] * g[G_MZ] + t[i];
+  double x = P->p[0], y = P->p[1], z = P->p[2];
+  if (near_rel(z, rc[RC_Z_NEAR])) P->flags |= FL_ZNEAR;
+  if (!(z > rc[RC_Z_NEAR])) return;
+
+  double fx = cam[CAM_FX], fy = cam[CAM_FY];
+  double limx = rc[RC_GUARD] * 0.5 * cam[CAM_W] / fx;
+  double limy = rc[RC_GUARD] * 0.5 * cam[CAM_H] / fy;
+  double txz = x / z, tyz = y / z;
+  if (near_rel(fabs(txz), limx) || near_rel(fabs(tyz), limy)) P->flags |= FL_CLAMP;
+  P->clx = (txz > limx || txz < -limx);
+  P->cly = (tyz > limy || tyz < -limy);
+  P->tx = txz > limx ? limx : (txz < -limx ? -limx : txz);
+  P->ty = tyz > limy ? limy : (tyz < -limy ? -limy : tyz);
+  double *J = P->J;
+  J[0] = fx / z; J[1] = 0; J[2] = -fx * P->tx / z;
+  J[3] = 0; J[4] = fy / z; J[5] = -fy * P->ty / z;
+
+  quat_rot(g + G_QW, P->Rq, P->nq, &P->qlen);
+  for (int i = 0; i < 3; i++) P->S[i] = exp(g[G_S0 + i]);
+  double M[9], Mt[9];
+  for (int i = 0; i < 3; i++)
+    for (int j = 0; j < 3; j++) M[3 * i + j] = P->Rq[3 * i + j] * P->S[j];
+  tr3(M, Mt);
+  mm3(M, Mt, P->Sig);
+  double Rt[9], tmp[9];
+  tr3(R, Rt);
+  mm3(R, P->Sig, tmp);
+  mm3(tmp, Rt, P->Sc);
+  /* Sigma' = J Sc J^T (2x2) */
+  double JS[6];
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 3; j++) {
+      double s = 0;
+      for (int k = 0; k < 3; k++) s += J[3 * i + k] * P->Sc[3 * k + j];
+      JS[3 * i + j] = s;
+    }
+  double S2[4];
+  for (int i = 0; i < 2; i++)
+    for (int j = 0; j < 2; j++) {
+      double s = 0;
+      for (int k = 0; k < 3; k++) s += JS[3 * i + k] * J[3 * j + k];
+      S2[2 * i + j] = s;
+    }
+  P->A = S2[0] + rc[RC_DILATION];
+  P->B = S2[1];
+  P->C = S2[3] + rc[RC_DILATION];
+  double det = P->A * P->C - P->B * P->B;
+  if (!(det > 0)) return;
+  P->a = P->C / det;
+  P->b = -P->B / det;
+  P->c = P->A / det;
+
+  P->o = 1.0 / (1.0 + exp(-g[G_LOGIT]));
+  if (near_rel(P->o, rc[RC_ALPHA_MIN])) P->flags |= FL_OPAC;
+  if (!(P->o > rc[RC_ALPHA_MIN])) return;
+
+  P->u = fx * x / z + cam[CAM_CX];
+  P->v = fy * y / z + cam[CAM_CY];
+  double mid = 0.5 * (P->A + P->C);
+  double disc = mid * mid - det;
+  P->lmax = mid + sqrt(disc > 0.1 ? disc : 0.1);
+  /* Outside |d| <= sqrt(2 lmax ln(o/alpha_min)) the Gaussian's alpha is below
+   * alpha_min, so it cannot contribute there. */
+  P->rext = sqrt(2.0 * P->lmax * log(P->o / rc[RC_ALPHA_MIN]));
+  if (near_int(P->rext)) P->flags |= FL_RADIUS;
+  P->r = (int)ceil(P->rext);
+  double tile = rc[RC_TILE];
+  int tx = (int)ceil(cam[CAM_W] / tile), ty = (int)ceil(cam[CAM_H] / tile);
+  double ex[4] = {(P->u - P->r) / tile, (P->v - P->r) / tile, (P->u + P->r) / tile,
+                  (P->v + P->r) / tile};
+  for (int i = 0; i < 4; i++)
+    if (near_int(ex[i])) P->flags |= FL_RECT;
+  int x0 = (int)floor(ex[0]), y0 = (int)floor(ex[1]);
+  int x1 = (int)floor(ex[2]) + 1, y1 = (int)floor(ex[3]) + 1;
+  P->x0 = x0 < 0 ? 0 : (x0 > tx ? tx : x0);
+  P->y0 = y0 < 0 ? 0 : (y0 > ty ? ty : y0);
+  P->x1 = x1 < 0 ? 0 : (x1 > tx ? tx : x1);
+  P->y1 = y1 < 0 ? 0 : (y1 > ty ? ty : y1);
+  if ((P->x1 - P->x0) * (P->y1 - P->y0) <= 0) return;
+  P->vis = 1;
+}
+
+/* Projection of all Gaussians into out[n * PJ_STRIDE]. */
+void oracle_project(int64_t n, const double *G, const double *cam, const double *pose,
+                    const double *rc, double *out) {
+  for (int64_t i = 0; i < n; i++) {
+    proj_t P;
+    project_one(G + i * G_STRIDE, cam, pose, rc, &P);
+    double *o = out + i * PJ_STRIDE;
+    o[PJ_VIS] = P.vis; o[PJ_U] = P.u; o[PJ_V] = P.v; o[PJ_Z] = P.p[2];
+    o[PJ_A] = P.a; o[PJ_B] = P.b; o[PJ_C] = P.c; o[PJ_O] = P.o;
+    o[PJ_SA] = P.A; o[PJ_SB] = P.B; o[PJ_SC] = P.C; o[PJ_LMAX] = P.lmax;
+    o[PJ_R] = P.r; o[PJ_X0] = P.x0; o[PJ_Y0] = P.y0; o[PJ_X1] = P.x1; o[PJ_Y1] = P.y1;
+    o[PJ_FLAG] = P.flags; o[PJ_PX] = P.p[0]; o[PJ_PY] = P.p[1];
+  }
+}
+
+/* ---- depth order ---- */
+
+typedef struct { double z; int64_t id; } zkey_t;
+
+static int cmp_zkey(const void *pa, const void *pb) {
+  const zkey_t *a = (const zkey_t *)pa, *b = (const zkey_t *)pb;
+  if (a->z < b->z) return -1;
+  if (a->z > b->z) return 1;
+  return (a->id > b->id) - (a->id < b->id);
+}
+
+/* ---- binning ---- */
+
+/* Pairs (tile, id) of every visible Gaussian and every tile of its rect,
+ * sorted by (tile, depth, id). Writes up to cap pairs, returns the total.
+ * tie_flag[k] = 1 where pair k and pair k-1 share a tile and their depths
+ * are within 1e-6 z (their order is not decided by FP64 vs FP32 alike). */
+typedef struct { int64_t tile; double z; int64_t id; } bkey_t;
+
+static int cmp_bkey(const void *pa, const void *pb) {
+  const bkey_t *a = (const bkey_t *)pa, *b = (const bkey_t *)pb;
+  if (a->tile != b->tile) return (a->tile > b->tile) - (a->tile < b->tile);
+  if (a->z < b->z) return -1;
+  if (a->z > b->z) return 1;
+  return (a->id > b->id) - (a->id < b->id);
+}
+
+int64_t oracle_binning(int64_t n, const double *G, const double *cam, const double *pose,
+                       const double *rc, int64_t cap, int64_t *tiles, int64_t *ids,
+                       int32_t *tie_flag) {
+  int tx = (int)ceil(cam[CAM_W] / rc[RC_TILE]);
+  proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; i++) {
+    project_one(G + i * G_STRIDE, cam, pose, rc, &P[i]);
+    if (P[i].vis) total += (int64_t)(P[i].x1 - P[i].x0) * (P[i].y1 - P[i].y0);
+  }
+  bkey_t *keys = (bkey_t *)malloc(sizeof(bkey_t) * (size_t)(total > 0 ? total : 1));
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; i++) {
+    if (!P[i].vis) continue;
+    for (int y = P[i].y0; y < P[i].y1; y++)
+      for (int x = P[i].x0; x < P[i].x1; x++) {
+        keys[k].tile = (int64_t)y * tx + x;
+        keys[k].z = P[i].p[2];
+        keys[k].id = i;
+        k++;
+      }
+  }
+  qsort(keys, (size_t)total, sizeof(bkey_t), cmp_bkey);
+  for (int64_t j = 0; j < total && j < cap; j++) {
+    tiles[j] = keys[j].tile;
+    ids[j] = keys[j].id;
+    tie_flag[j] = (j > 0 && keys[j].tile == keys[j - 1].tile &&
+                   fabs(keys[j].z - keys[j - 1].z) <= 1e-6 * keys[j].z);
+  }
+  free(keys);
+  free(P);
+  return total;
+}
+
+/* ---- render, loss and adjoint ---- */
+
+typedef struct { int64_t id; double alpha, T, G, dx, dy; int clamped; } contrib_t;
+
+/* Candidate lists: a pixel's candidates are the visible Gaussians whose
+ * bounding square |dx|, |dy| <= r holds the pixel, in (depth, id) order.
+ * Outside that square alpha < alpha_min exactly, so restricting to it does
+ * not change any value; with accel = 0 every visible Gaussian is tested. */
+typedef struct { int64_t *start; int64_t *ids; int cw, ch, cell; } cells_t;
+
+static void build_cells(int64_t n, const proj_t *P, const int64_t *order, int W, int H,
+                        int cell, int accel, cells_t *cs) {
+  cs->cell = accel ? cell : (W > H ? W : H);
+  cs->cw = (W + cs->cell - 1) / cs->cell;
+  cs->ch = (H + cs->cell - 1) / cs->cell;
+  int nc = cs->cw * cs->ch;
+  cs->start = (int64_t *)calloc((size_t)nc + 1, sizeof(int64_t));
+  for (int pass = 0; pass < 2; pass++) {
+    int64_t *fill = NULL;
+    if (pass == 1) {
+      for (int c = 0; c < nc; c++) cs->start[c + 1] += cs->start[c];
+      cs->ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)(cs->start[nc] > 0 ? cs->start[nc] : 1));
+      fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nc);
+      for (int c = 0; c < nc; c++) fill[c] = cs->start[c];
+    }
+    for (int64_t oi = 0; oi < n; oi++) {
+      int64_t i = order[oi];
+      const proj_t *p = &P[i];
+      if (!p->vis) continue;
+      int px0 = 0, py0 = 0, px1 = W - 1, py1 = H - 1;
+      if (accel) {
+        px0 = (int)ceil(p->u - p->r); px1 = (int)floor(p->u + p->r);
+        py0 = (int)ceil(p->v - p->r); py1 = (int)floor(p->v + p->r);
+        if (px0 < 0) px0 = 0;
+        if (py0 < 0) py0 = 0;
+        if (px1 > W - 1) px1 = W - 1;
+        if (py1 > H - 1) py1 = H - 1;
+        if (px0 > px1 || py0 > py1) continue;
+      }
+      for (int cy = py0 / cs->cell; cy <= py1 / cs->cell; cy++)
+        for (int cx = px0 / cs->cell; cx <= px1 / cs->cell; cx++) {
+          int c = cy * cs->cw + cx;
+          if (pass == 0) cs->start[c + 1]++;
+          else cs->ids[fill[c]++] = i;
+        }
+    }
+    free(fill);
+  }
+}
+
+/* Render one view: out_px[P * PX_STRIDE], out_flags[P]; if targets
+ * (P x 4: r, g, b, depth) is given, the loss goes to *loss and, if grads /
+ * pose_grad are non-NULL, the adjoint is ADDED to grads[n * G_STRIDE] and
+ * written to pose_grad[6] = (rho, phi) of the left-perturbation twist.
+ * wfix (P, or NULL) replaces the static weight w(u) by given constants, so
+ * that finite differences can check the stop-gradient adjoint.
+ * Returns 0, or -1 on allocation failure. */
+int oracle_render(int64_t n, const double *G, const double *cam, const double *pose,
+                  const double *rc, const double *lc, const double *targets, const double *wfix,
+                  int accel, double *out_px, int32_t *out_flags, double *loss, double *grads,
+                  double *pose_grad) {
+  int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
+  proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
+  zkey_t *zk = (zkey_t *)malloc(sizeof(zkey_t) * (size_t)(n > 0 ? n : 1));
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!P || !zk || !order) return -1;
+  int64_t nv = 0;
+  for (int64_t i = 0; i < n; i++) {
+    project_one(G + i * G_STRIDE, cam, pose, rc, &P[i]);
+    if (P[i].vis) { zk[nv].z = P[i].p[2]; zk[nv].id = i; nv++; }
+  }
+  qsort(zk, (size_t)nv, sizeof(zkey_t), cmp_zkey);
+  for (int64_t k = 0; k < nv; k++) order[k] = zk[k].id;
+  cells_t cs;
+  build_cells(nv, P, order, W, H, 8, accel, &cs);
+
+  const int want_grad = (targets != NULL) && (grads != NULL || pose_grad != NULL);
+  /* per-Gaussian accumulated 2D gradients: u, v, a, b, c, o, z, cr, cg, cb */
+  double *g2 = want_grad ? (double *)calloc((size_t)(n > 0 ? n : 1) * 10, sizeof(double)) : NULL;
+  int64_t cap = 256;
+  contrib_t *list = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)cap);
+  double L = 0.0;
+  const double amin = rc[RC_ALPHA_MIN], amax = rc[RC_ALPHA_MAX], tmin = rc[RC_T_MIN];
+
+  for (int j = 0; j < H; j++)
+    for (int i = 0; i < W; i++) {
+      int c = (j / cs.cell) * cs.cw + (i / cs.cell);
+      double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0};
+      int flags = 0;
+      int64_t nl = 0, last = -1;
+      double prev_z = -1.0;
+      for (int64_t q = cs.start[c]; q < cs.start[c + 1]; q++) {
+        int64_t id = cs.ids[q];
+        const proj_t *p = &P[id];
+        double dx = p->u - i, dy = p->v - j;
+        double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
+        double Gv = exp(power);
+        double ag = p->o * Gv;
+        if (near_rel(ag, amin)) flags |= FL_ALPHA;
+        if (near_rel(ag, amax)) flags |= FL_AMAX;
+        if (ag < amin) continue;
+        int clamped = ag > amax;
+        double alpha = clamped ? amax : ag;
+        if (prev_z >= 0 && fabs(p->p[2] - prev_z) <= 1e-6 * p->p[2]) flags |= FL_ZTIE;
+        prev_z = p->p[2];
+        double testT = T * (1.0 - alpha);
+        if (near_rel(testT, tmin)) flags |= FL_TSTOP;
+        if (testT < tmin) break;
+        const double *g = G + id * G_STRIDE;
+        double wgt = alpha * T;
+        acc[0] += g[G_CR] * wgt;
+        acc[1] += g[G_CG] * wgt;
+        acc[2] += g[G_CB] * wgt;
+        acc[3] += p->p[2] * wgt;
+        acc[4] += wgt;
+        acc[5] += g[G_MP] * wgt;
+        if (nl == cap) {
+          cap *= 2;
+          list = (contrib_t *)realloc(list, sizeof(contrib_t) * (size_t)cap);
+        }
+        list[nl].id = id; list[nl].alpha = alpha; list[nl].T = T; list[nl].G = Gv;
+        list[nl].dx = dx; list[nl].dy = dy; list[nl].clamped = clamped;
+        nl++;
+        last = id;
+        T = testT;
+      }
+      int64_t pix = (int64_t)j * W + i;
+      double *o = out_px + pix * PX_STRIDE;
+      for (int k = 0; k < 6; k++) o[k] = acc[k];
+      o[PX_T] = T; o[PX_N] = (double)nl; o[PX_LAST] = (double)last; o[PX_W] = 0.0;
+
+      if (targets) {
+        const double *tg = targets + pix * 4;
+        double O = acc[4], Rm = acc[5];
+        double w = 0.0;
+        if (lc[LC_WMODE] == 0) {
+          if (near_rel(O, lc[LC_OEPS])) flags |= FL_OEPS;
+          if (O > lc[LC_OEPS]) w = (O - Rm) / O;
+        } else {
+          w = O - Rm;
+        }
+        if (wfix) w = wfix[pix];
+        o[PX_W] = w;
+        double rcol[3], sc[3], rd = acc[3] - tg[3], sd;
+        double l1 = 0;
+        for (int k = 0; k < 3; k++) {
+          rcol[k] = acc[k] - tg[k];
+          if (fabs(rcol[k]) <= MARGIN * fmax(fabs(acc[k]), fabs(tg[k]))) flags |= FL_SIGN;
+          sc[k] = (rcol[k] > 0) - (rcol[k] < 0);
+          l1 += fabs(rcol[k]);
+        }
+        int dvalid = tg[3] > 0;
+        if (dvalid && fabs(rd) <= MARGIN * fmax(fabs(acc[3]), fabs(tg[3]))) flags |= FL_SIGN;
+        sd = dvalid ? (double)((rd > 0) - (rd < 0)) : 0.0;
+        double lw = lc[LC_LPHO] * l1 + (dvalid ? lc[LC_LDEPTH] * fabs(rd) : 0.0);
+        L += w * lw;
+
+        if (want_grad && nl > 0) {
+          /* upstream gradients of the six composited channels */
+          double gF[6];
+          for (int k = 0; k < 3; k++) gF[k] = lc[LC_LPHO] * w * sc[k];
+          gF[3] = lc[LC_LDEPTH] * w * sd;
+          gF[4] = 0.0;
+          gF[5] = 0.0;
+          if (lc[LC_WGRAD] != 0 && !wfix) {
+            if (lc[LC_WMODE] == 0) {
+              if (O > lc[LC_OEPS]) { gF[4] += lw * Rm / (O * O); gF[5] += -lw / O; }
+            } else {
+              gF[4] += lw; gF[5] += -lw;
+            }
+          }
+          double S[6] = {0, 0, 0, 0, 0, 0}; /* sum over later contributors */
+          for (int64_t k = nl - 1; k >= 0; k--) {
+            const contrib_t *e = &list[k];
+            const proj_t *p = &P[e->id];
+            const double *g = G + e->id * G_STRIDE;
+            double f[6] = {g[G_CR], g[G_CG], g[G_CB], p->p[2], 1.0, g[G_MP]};
+            double wk = e->alpha * e->T;
+            double dal = 0;
+            for (int ch = 0; ch < 6; ch++)
+              dal += gF[ch] * (f[ch] * e->T - S[ch] / (1.0 - e->alpha));
+            double *gg = g2 + e->id * 10;
+            gg[7] += gF[0] * wk;
+            gg[8] += gF[1] * wk;
+            gg[9] += gF[2] * wk;
+            gg[6] += gF[3] * wk;
+            if (!e->clamped) {
+              gg[5] += dal * e->G;
+              double dpw = dal * e->alpha;
+              gg[0] += dpw * (-(p->a * e->dx + p->b * e->dy));
+              gg[1] += dpw * (-(p->b * e->dx + p->c * e->dy));
+              gg[2] += dpw * (-0.5 * e->dx * e->dx);
+              gg[3] += dpw * (-e->dx * e->dy);
+              gg[4] += dpw * (-0.5 * e->dy * e->dy);
+            }
+            for (int ch = 0; ch < 6; ch++) S[ch] += f[ch] * wk;
+          }
+        }
+      }
+      out_flags[pix] = flags;
+    }
+  if (loss) *loss = L;
+
+  if (want_grad) {
+    double R[9] = {pose[0], pose[1], pose[2], pose[4], pose[5], pose[6], pose[8], pose[9], pose[10]};
+    double pg[6] = {0, 0, 0, 0, 0, 0};
+    double fx = cam[CAM_FX], fy = cam[CAM_FY];
+    for (int64_t id = 0; id < n; id++) {
+      const proj_t *p = &P[id];
+      if (!p->vis) continue;
+      const double *gg = g2 + id * 10;
+      double x = p->p[0], y = p->p[1], z = p->p[2];
+      /* conic -> 2D covariance: dL/dSigma' = -Q Gq Q (symmetric matrix form) */
+      double Q[4] = {p->a, p->b, p->b, p->c};
+      double Gq[4] = {gg[2], 0.5 * gg[3], 0.5 * gg[3], gg[4]};
+      double QG[4], dS2[4];
+      for (int r = 0; r < 2; r++)
+        for (int s = 0; s < 2; s++)
+          QG[2 * r + s] = Q[2 * r] * Gq[s] + Q[2 * r + 1] * Gq[2 + s];
+      for (int r = 0; r < 2; r++)
+        for (int s = 0; s < 2; s++)
+          dS2[2 * r + s] = -(QG[2 * r] * Q[s] + QG[2 * r + 1] * Q[2 + s]);
+      const double *J = p->J;
+      /* dL/dSc = J^T dS2 J */
+      double dSc[9];
+      for (int r = 0; r < 3; r++)
+        for (int s = 0; s < 3; s++) {
+          double acc2 = 0;
+          for (int k = 0; k < 2; k++)
+            for (int l = 0; l < 2; l++) acc2 += J[3 * k + r] * dS2[2 * k + l] * J[3 * l + s];
+          dSc[3 * r + s] = acc2;
+        }
+      /* dL/dJ = 2 dS2 J Sc */
+      double JSc[6], dJ[6];
+      for (int r = 0; r < 2; r++)
+        for (int s = 0; s < 3; s++) {
+          double acc2 = 0;
+          for (int k = 0; k < 3; k++) acc2 += J[3 * r + k] * p->Sc[3 * k + s];
+          JSc[3 * r + s] = acc2;
+        }
+      for (int r = 0; r < 2; r++)
+        for (int s = 0; s < 3; s++) dJ[3 * r + s] = 2.0 * (dS2[2 * r] * JSc[s] + dS2[2 * r + 1] * JSc[3 + s]);
+      /* dL/dp (camera-space mean) */
+      double dp[3] = {0, 0, 0};
+      dp[0] += gg[0] * fx / z;
+      dp[2] += gg[0] * (-fx * x / (z * z));
+      dp[1] += gg[1] * fy / z;
+      dp[2] += gg[1] * (-fy * y / (z * z));
+      dp[2] += gg[6];
+      dp[2] += dJ[0] * (-fx / (z * z));
+      dp[2] += dJ[4] * (-fy / (z * z));
+      if (!p->clx) {
+        dp[0] += dJ[2] * (-fx / (z * z));
+        dp[2] += dJ[2] * (2.0 * fx * x / (z * z * z));
+      } else {
+        dp[2] += dJ[2] * (fx * p->tx / (z * z));
+      }
+      if (!p->cly) {
+        dp[1] += dJ[5] * (-fy / (z * z));
+        dp[2] += dJ[5] * (2.0 * fy * y / (z * z * z));
+      } else {
+        dp[2] += dJ[5] * (fy * p->ty / (z * z));
+      }
+      /* pose: rho += dp; phi += p x dp + covariance term */
+      pg[0] += dp[0]; pg[1] += dp[1]; pg[2] += dp[2];
+      pg[3] += y * dp[2] - z * dp[1];
+      pg[4] += z * dp[0] - x * dp[2];
+      pg[5] += x * dp[1] - y * dp[0];
+      double Am[9];
+      mm3(p->Sc, dSc, Am);
+      pg[3] += 2.0 * (Am[5] - Am[7]);
+      pg[4] += 2.0 * (Am[6] - Am[2]);
+      pg[5] += 2.0 * (Am[1] - Am[3]);
+
+      if (grads) {
+        double *out = grads + id * G_STRIDE;
+        /* mean: p = R mu + t */
+        for (int k = 0; k < 3; k++)
+          out[G_MX + k] += R[k] * dp[0] + R[3 + k] * dp[1] + R[6 + k] * dp[2];
+        /* world covariance: dSig = R^T dSc R */
+        double Rt[9], tmp[9], dSig[9];
+        tr3(R, Rt);
+        mm3(Rt, dSc, tmp);
+        mm3(tmp, R, dSig);
+        /* Sig = M M^T, M = Rq diag(S): dM = 2 dSig M */
+        double M[9], dM[9];
+        for (int r = 0; r < 3; r++)
+          for (int s = 0; s < 3; s++) M[3 * r + s] = p->Rq[3 * r + s] * p->S[s];
+        mm3(dSig, M, dM);
+        for (int k = 0; k < 9; k++) dM[k] *= 2.0;
+        double dRq[9];
+        for (int s = 0; s < 3; s++) {
+          double dSs = 0;
+          for (int r = 0; r < 3; r++) {
+            dSs += p->Rq[3 * r + s] * dM[3 * r + s];
+            dRq[3 * r + s] = dM[3 * r + s] * p->S[s];
+          }
+          out[G_S0 + s] += dSs * p->S[s];
+        }
+        double w = p->nq[0], qx = p->nq[1], qy = p->nq[2], qz = p->nq[3];
+        double dn[4];
+        dn[0] = dRq[1] * (-2 * qz) + dRq[2] * (2 * qy) + dRq[3] * (2 * qz) + dRq[5] * (-2 * qx) +
+                dRq[6] * (-2 * qy) + dRq[7] * (2 * qx);
+        dn[1] = dRq[1] * (2 * qy) + dRq[2] * (2 * qz) + dRq[3] * (2 * qy) + dRq[4] * (-4 * qx) +
+                dRq[5] * (-2 * w) + dRq[6] * (2 * qz) + dRq[7] * (2 * w) + dRq[8] * (-4 * qx);
+        dn[2] = dRq[0] * (-4 * qy) + dRq[1] * (2 * qx) + dRq[2] * (2 * w) + dRq[3] * (2 * qx) +
+                dRq[5] * (2 * qz) + dRq[6] * (-2 * w) + dRq[7] * (2 * qz) + dRq[8] * (-4 * qy);
+        dn[3] = dRq[0] * (-4 * qz) + dRq[1] * (-2 * w) + dRq[2] * (2 * qx) + dRq[3] * (2 * w) +
+                dRq[4] * (-4 * qz) + dRq[5] * (2 * qy) + dRq[6] * (2 * qx) + dRq[7] * (2 * qy);
+        double ndn = w * dn[0] + qx * dn[1] + qy * dn[2] + qz * dn[3];
+        out[G_QW] += (dn[0] - w * ndn) / p->qlen;
+        out[G_QX] += (dn[1] - qx * ndn) / p->qlen;
+        out[G_QY] += (dn[2] - qy * ndn) / p->qlen;
+        out[G_QZ] += (dn[3] - qz * ndn) / p->qlen;
+        out[G_LOGIT] += gg[5] * p->o * (1.0 - p->o);
+        out[G_CR] += gg[7];
+        out[G_CG] += gg[8];
+        out[G_CB] += gg[9];
+      }
+    }
+    if (pose_grad)
+      for (int k = 0; k < 6; k++) pose_grad[k] = pg[k];
+  }
+  free(list);
+  free(g2);
+  free(cs.start);
+  free(cs.ids);
+  free(order);
+  free(zk);
+  free(P);
+  return 0;
+}
+
+/* Render one pixel (i, j) by testing every Gaussian: the per-pixel form of
+ * oracle_render for spot checks at sizes where a whole image is too slow.
+ * out[PX_STRIDE]; returns the flags. */
+int oracle_render_pixel(int64_t n, const double *G, const double *cam, const double *pose,
+                        const double *rc, int i, int j, double *out) {
+  zkey_t *zk = (zkey_t *)malloc(sizeof(zkey_t) * (size_t)(n > 0 ? n : 1));
+  proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
+  int64_t nv = 0;
+  for (int64_t k = 0; k < n; k++) {
+    project_one(G + k * G_STRIDE, cam, pose, rc, &P[k]);
+    if (P[k].vis) { zk[nv].z = P[k].p[2]; zk[nv].id = k; nv++; }
+  }
+  qsort(zk, (size_t)nv, sizeof(zkey_t), cmp_zkey);
+  double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0}, prev_z = -1;
+  int flags = 0, nl = 0;
+  int64_t last = -1;
+  for (int64_t q = 0; q < nv; q++) {
+    const proj_t *p = &P[zk[q].id];
+    const double *g = G + zk[q].id * G_STRIDE;
+    double dx = p->u - i, dy = p->v - j;
+    double ag = p->o * exp(-0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy);
+    if (near_rel(ag, rc[RC_ALPHA_MIN])) flags |= FL_ALPHA;
+    if (near_rel(ag, rc[RC_ALPHA_MAX])) flags |= FL_AMAX;
+    if (ag < rc[RC_ALPHA_MIN]) continue;
+    double alpha = ag > rc[RC_ALPHA_MAX] ? rc[RC_ALPHA_MAX] : ag;
+    if (prev_z >= 0 && fabs(p->p[2] - prev_z) <= 1e-6 * p->p[2]) flags |= FL_ZTIE;
+    prev_z = p->p[2];
+    double testT = T * (1.0 - alpha);
+    if (near_rel(testT, rc[RC_T_MIN])) flags |= FL_TSTOP;
+    if (testT < rc[RC_T_MIN]) break;
+    double wgt = alpha * T;
+    acc[0] += g[G_CR] * wgt; acc[1] += g[G_CG] * wgt; acc[2] += g[G_CB] * wgt;
+    acc[3] += p->p[2] * wgt; acc[4] += wgt; acc[5] += g[G_MP] * wgt;
+    T = testT;
+    nl++;
+    last = zk[q].id;
+  }
+  for (int k = 0; k < 6; k++) out[k] = acc[k];
+  out[PX_T] = T; out[PX_N] = nl; out[PX_LAST] = (double)last; out[PX_W] = 0.0;
+  free(zk);
+  free(P);
+  return flags;
+}

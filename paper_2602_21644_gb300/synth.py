@@ -1,0 +1,365 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests and benchmark and by
+the oracle's tests.
+
+This module holds none of the method's arithmetic: it samples Gaussians,
+packs them into the 64-byte record format, builds camera poses, and makes
+ground-truth RGB-D frames by ray-casting the analytic scene (planes and
+ellipsoids) that the Gaussians were sampled from. It never splats.
+
+The paper evaluates on the TUM RGB-D and BONN sequences (Sec. V-A(a));
+neither is available here, so these scenes stand in for them: 640x480
+RGB-D frames with fx = fy = 525 of an indoor room with moving objects.
+
+Record layout (16 x 32-bit words, 64 bytes, little endian):
+  0-2 mean (m, world), 3 opacity logit, 4-7 rotation quaternion (w, x, y, z;
+  any norm), 8-10 natural-log scale per axis, 11 motion probability,
+  12 = bf16(r) | bf16(g) << 16, 13 = bf16(b), 14-15 zero.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+RECORD_WORDS = 16
+
+
+# ------------------------------------------------------------------ packing
+
+def f32_to_bf16_bits(x: np.ndarray) -> np.ndarray:
+    """Round float32 to bfloat16 (round to nearest, ties to even); uint16 bits."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    rounded = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return rounded.astype(np.uint16)
+
+
+def bf16_bits_to_f32(b: np.ndarray) -> np.ndarray:
+    return (np.asarray(b).astype(np.uint32) << 16).view(np.float32)
+
+
+def pack_records(means, logits, quats, logscales, mp, rgb) -> np.ndarray:
+    """Pack per-Gaussian arrays into n x 16 float32 records (colours to BF16)."""
+    n = means.shape[0]
+    rec = np.zeros((n, RECORD_WORDS), dtype=np.float32)
+    rec[:, 0:3] = means
+    rec[:, 3] = logits
+    rec[:, 4:8] = quats
+    rec[:, 8:11] = logscales
+    rec[:, 11] = mp
+    bits = f32_to_bf16_bits(np.asarray(rgb, dtype=np.float32)).astype(np.uint32)
+    words = rec.view(np.uint32)
+    words[:, 12] = bits[:, 0] | (bits[:, 1] << 16)
+    words[:, 13] = bits[:, 2]
+    return rec
+
+
+def record_rgb(rec: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(rec).view(np.uint32)
+    r = bf16_bits_to_f32((w[:, 12] & 0xFFFF).astype(np.uint16))
+    g = bf16_bits_to_f32((w[:, 12] >> 16).astype(np.uint16))
+    b = bf16_bits_to_f32((w[:, 13] & 0xFFFF).astype(np.uint16))
+    return np.stack([r, g, b], axis=1)
+
+
+# ------------------------------------------------------------------ cameras
+
+@dataclass
+class Camera:
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+
+    def as_tuple(self):
+        return (self.fx, self.fy, self.cx, self.cy, self.width, self.height)
+
+
+def identity_pose() -> np.ndarray:
+    p = np.zeros((3, 4))
+    p[:, :3] = np.eye(3)
+    return p
+
+
+def look_at_pose(eye, target, up=(0.0, -1.0, 0.0)) -> np.ndarray:
+    """World-to-camera 3x4 pose of a camera at eye looking at target
+    (camera x right, y down, z forward)."""
+    eye = np.asarray(eye, dtype=np.float64)
+    f = np.asarray(target, dtype=np.float64) - eye
+    f /= np.linalg.norm(f)
+    r = np.cross(np.asarray(up, dtype=np.float64), f)
+    r /= np.linalg.norm(r)
+    d = np.cross(f, r)
+    R = np.stack([r, d, f], axis=0)          # rows: camera axes in world
+    pose = np.zeros((3, 4))
+    pose[:, :3] = R
+    pose[:, 3] = -R @ eye
+    return pose
+
+
+def rotmat_to_quat(R: np.ndarray) -> np.ndarray:
+    """Unit quaternions (w, x, y, z) of rotation matrices (..., 3, 3)."""
+    R = np.asarray(R, dtype=np.float64)
+    m00, m11, m22 = R[..., 0, 0], R[..., 1, 1], R[..., 2, 2]
+    tr = m00 + m11 + m22
+    q = np.zeros(R.shape[:-2] + (4,))
+    c0 = tr > 0
+    s = np.sqrt(np.maximum(tr + 1.0, 1e-12)) * 2
+    q0 = np.stack([0.25 * s, (R[..., 2, 1] - R[..., 1, 2]) / s, (R[..., 0, 2] - R[..., 2, 0]) / s,
+                   (R[..., 1, 0] - R[..., 0, 1]) / s], -1)
+    c1 = (~c0) & (m00 > m11) & (m00 > m22)
+    s1 = np.sqrt(np.maximum(1.0 + m00 - m11 - m22, 1e-12)) * 2
+    q1 = np.stack([(R[..., 2, 1] - R[..., 1, 2]) / s1, 0.25 * s1, (R[..., 0, 1] + R[..., 1, 0]) / s1,
+                   (R[..., 0, 2] + R[..., 2, 0]) / s1], -1)
+    c2 = (~c0) & (~c1) & (m11 > m22)
+    s2 = np.sqrt(np.maximum(1.0 + m11 - m00 - m22, 1e-12)) * 2
+    q2 = np.stack([(R[..., 0, 2] - R[..., 2, 0]) / s2, (R[..., 0, 1] + R[..., 1, 0]) / s2, 0.25 * s2,
+                   (R[..., 1, 2] + R[..., 2, 1]) / s2], -1)
+    s3 = np.sqrt(np.maximum(1.0 + m22 - m00 - m11, 1e-12)) * 2
+    q3 = np.stack([(R[..., 1, 0] - R[..., 0, 1]) / s3, (R[..., 0, 2] + R[..., 2, 0]) / s3,
+                   (R[..., 1, 2] + R[..., 2, 1]) / s3, 0.25 * s3], -1)
+    q = np.where(c0[..., None], q0, np.where(c1[..., None], q1, np.where(c2[..., None], q2, q3)))
+    return q / np.linalg.norm(q, axis=-1, keepdims=True)
+
+
+# ------------------------------------------------------------------ tiny
+
+@dataclass
+class Scene:
+    records: np.ndarray                 # n x 16 float32
+    camera: Camera
+    poses: np.ndarray                   # V x 3 x 4 float64 (world -> camera)
+    targets: np.ndarray                 # V x H*W x 4 float32 (r, g, b, depth; depth 0 = invalid)
+    dynamic: np.ndarray = None          # n bool: Gaussian belongs to a moving object
+    extra: dict = field(default_factory=dict)
+
+
+def tiny_scene(seed: int = 0, n: int = 2000, width: int = 160, height: int = 120, f: float = 120.0,
+               dyn_frac: float = 0.2) -> Scene:
+    """2,000 anisotropic Gaussians: means U([-1,1]x[-1,1]x[1,4]) m, log-scales
+    N(-3, 0.5), random unit quaternions, RGB U[0,1], opacity logit N(0,1); the
+    first 20% re-drawn inside a 'dynamic' box with MP 0.9, the rest MP 0.1;
+    one pinhole camera fx = fy = 120 at 160x120, identity pose; target RGB
+    U[0,1] and depth U[1,4] per pixel."""
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.uniform(-1, 1, n), rng.uniform(-1, 1, n), rng.uniform(1, 4, n)], 1)
+    logscales = rng.normal(-3.0, 0.5, (n, 3))
+    q = rng.normal(0, 1, (n, 4))
+    quats = q / np.linalg.norm(q, axis=1, keepdims=True)
+    rgb = rng.uniform(0, 1, (n, 3))
+    logits = rng.normal(0, 1, n)
+    nd = int(round(dyn_frac * n))
+    means[:nd] = np.stack([rng.uniform(0.2, 0.8, nd), rng.uniform(-0.3, 0.3, nd), rng.uniform(1.5, 2.5, nd)], 1)
+    mp = np.full(n, 0.1)
+    mp[:nd] = 0.9
+    dyn = np.zeros(n, bool)
+    dyn[:nd] = True
+    rec = pack_records(means, logits, quats, logscales, mp, rgb)
+    cam = Camera(f, f, width / 2.0, height / 2.0, width, height)
+    tg = np.zeros((1, width * height, 4), np.float32)
+    tg[0, :, 0:3] = rng.uniform(0, 1, (width * height, 3))
+    tg[0, :, 3] = rng.uniform(1, 4, width * height)
+    return Scene(rec, cam, identity_pose()[None], tg, dyn)
+
+
+# ------------------------------------------------------------------ room
+
+ROOM_HALF = np.array([3.0, 1.5, 3.0])   # x, y (down), z half-extents: 6 x 3 x 6 m
+
+
+@dataclass
+class Ellipsoid:
+    center: np.ndarray
+    axes: np.ndarray
+    velocity: np.ndarray      # m/s; zero for static objects
+
+    def center_at(self, t: float) -> np.ndarray:
+        return self.center + self.velocity * t
+
+
+def default_objects(n_moving: int = 2, n_static: int = 1):
+    objs = []
+    cs = [np.array([-1.2, 0.6, 0.8]), np.array([1.0, 0.5, -0.6]), np.array([0.2, 0.9, 1.6])]
+    ax = [np.array([0.35, 0.5, 0.3]), np.array([0.4, 0.3, 0.45]), np.array([0.5, 0.25, 0.2])]
+    vs = [np.array([0.3, 0.0, 0.0]), np.array([0.0, 0.0, 0.3])]
+    for k in range(n_moving + n_static):
+        v = vs[k] if k < n_moving else np.zeros(3)
+        objs.append(Ellipsoid(cs[k % 3].copy(), ax[k % 3].copy(), v.copy()))
+    return objs
+
+
+def texture(p: np.ndarray) -> np.ndarray:
+    """Smooth colour field of the room surfaces (RGB in [0.1, 0.9])."""
+    r = 0.5 + 0.3 * np.sin(2.1 * p[..., 0] + 0.7 * p[..., 2]) * np.cos(1.3 * p[..., 1])
+    g = 0.5 + 0.3 * np.sin(1.7 * p[..., 2] - 1.1 * p[..., 1] + 0.4)
+    b = 0.5 + 0.3 * np.cos(2.5 * p[..., 0] - 1.9 * p[..., 2] + 1.3 * p[..., 1])
+    return np.stack([r, g, b], -1)
+
+
+def _frames_from_normals(nrm: np.ndarray) -> np.ndarray:
+    """Rotation matrices whose third column is the given unit normal."""
+    helper = np.where(np.abs(nrm[:, 1:2]) < 0.9, np.array([[0.0, 1.0, 0.0]]), np.array([[1.0, 0.0, 0.0]]))
+    t1 = np.cross(helper, nrm)
+    t1 /= np.linalg.norm(t1, axis=1, keepdims=True)
+    t2 = np.cross(nrm, t1)
+    return np.stack([t1, t2, nrm], axis=2)
+
+
+def room_scene(n: int, seed: int = 0, objects=None, opacity_logit=(2.5, 0.5), mp_static=0.1,
+               mp_dynamic=0.9):
+    """n Gaussians sampled on the 6 x 6 x 3 m room's walls, floor and ceiling
+    and on the objects' ellipsoidal surfaces, area-proportionally. Disc-like
+    Gaussians: tangent sigma = 0.7 x mean spacing, normal sigma = 2 mm.
+    Returns (records, object_id per Gaussian (-1 = room), objects)."""
+    rng = np.random.default_rng(seed)
+    objects = default_objects() if objects is None else objects
+    hx, hy, hz = ROOM_HALF
+    planes = [  # (axis, sign): wall at coordinate sign * half on that axis
+        (0, -1), (0, 1), (2, -1), (2, 1), (1, -1), (1, 1)]
+    areas = []
+    for axis, _ in planes:
+        o = [a for a in range(3) if a != axis]
+        areas.append(4 * ROOM_HALF[o[0]] * ROOM_HALF[o[1]])
+    for ob in objects:
+        a, b, c = ob.axes
+        p = 1.6075
+        areas.append(4 * np.pi * (((a * b) ** p + (a * c) ** p + (b * c) ** p) / 3) ** (1 / p))
+    areas = np.array(areas)
+    counts = np.floor(n * areas / areas.sum()).astype(int)
+    counts[0] += n - counts.sum()
+    spacing = np.sqrt(areas.sum() / n)
+    pts, nrms, oid = [], [], []
+    for k, (axis, sgn) in enumerate(planes):
+        m = counts[k]
+        p = rng.uniform(-1, 1, (m, 3)) * ROOM_HALF
+        p[:, axis] = sgn * ROOM_HALF[axis]
+        nv = np.zeros((m, 3))
+        nv[:, axis] = -sgn
+        pts.append(p); nrms.append(nv); oid.append(np.full(m, -1))
+    for j, ob in enumerate(objects):
+        m = counts[len(planes) + j]
+        d = rng.normal(0, 1, (m, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        p = ob.center + d * ob.axes
+        nv = d / ob.axes
+        nv /= np.linalg.norm(nv, axis=1, keepdims=True)
+        pts.append(p); nrms.append(nv); oid.append(np.full(m, j))
+    pts = np.concatenate(pts); nrms = np.concatenate(nrms); oid = np.concatenate(oid)
+    quats = rotmat_to_quat(_frames_from_normals(nrms))
+    sig_t = 0.7 * spacing
+    logscales = np.stack([np.log(sig_t) + rng.normal(0, 0.1, n), np.log(sig_t) + rng.normal(0, 0.1, n),
+                          np.full(n, np.log(0.002))], 1)
+    rgb = np.clip(texture(pts) + rng.uniform(-0.05, 0.05, (n, 3)), 0, 1)
+    logits = rng.normal(opacity_logit[0], opacity_logit[1], n)
+    moving = np.array([np.any(ob.velocity != 0) for ob in objects] + [False])
+    mp = np.where((oid >= 0) & moving[np.where(oid >= 0, oid, len(objects))], mp_dynamic, mp_static)
+    rec = pack_records(pts, logits, quats, logscales, mp, rgb)
+    return rec, oid, objects
+
+
+def raycast(cam: Camera, pose: np.ndarray, objects, t: float = 0.0, depth_noise: float = 0.0,
+            rng=None):
+    """Ground-truth RGB-D of the analytic room at time t: per pixel (r, g, b,
+    depth) with depth = camera z of the first hit, and the index of the hit
+    object (-1 = room). Depth noise is multiplicative N(0, depth_noise)."""
+    W, H = cam.width, cam.height
+    jj, ii = np.meshgrid(np.arange(H, dtype=np.float64), np.arange(W, dtype=np.float64), indexing="ij")
+    dc = np.stack([(ii - cam.cx) / cam.fx, (jj - cam.cy) / cam.fy, np.ones_like(ii)], -1).reshape(-1, 3)
+    R, tr = pose[:, :3], pose[:, 3]
+    dw = dc @ R                                # rows: R^T d
+    ow = -R.T @ tr
+    best = np.full(dw.shape[0], np.inf)
+    hit = np.full(dw.shape[0], -1)
+    for axis in range(3):
+        for sgn in (-1.0, 1.0):
+            with np.errstate(divide="ignore", invalid="ignore"):
+                s = (sgn * ROOM_HALF[axis] - ow[axis]) / dw[:, axis]
+            ok = (s > 1e-6) & (s < best)
+            best = np.where(ok, s, best)
+            hit = np.where(ok, -1, hit)
+    for j, ob in enumerate(objects):
+        c = ob.center_at(t)
+        oc = (ow - c) / ob.axes
+        dd = dw / ob.axes
+        a = np.sum(dd * dd, 1)
+        b = 2 * dd @ oc
+        cc = oc @ oc - 1
+        disc = b * b - 4 * a * cc
+        sq = np.sqrt(np.maximum(disc, 0))
+        s = (-b - sq) / (2 * a)
+        ok = (disc > 0) & (s > 1e-6) & (s < best)
+        best = np.where(ok, s, best)
+        hit = np.where(ok, j, hit)
+    p = ow + best[:, None] * dw
+    rgb = texture(p)
+    depth = best.copy()                          # camera z, since d_c has unit z
+    if depth_noise > 0:
+        rng = np.random.default_rng(0) if rng is None else rng
+        depth = depth * (1 + rng.normal(0, depth_noise, depth.shape))
+    out = np.zeros((W * H, 4), np.float32)
+    out[:, 0:3] = rgb
+    out[:, 3] = depth
+    return out, hit
+
+
+def camera_path(n_frames: int, fps: float = 30.0):
+    """Smooth camera trajectory inside the room looking roughly at its centre."""
+    poses = []
+    for k in range(n_frames):
+        s = k / fps
+        eye = np.array([0.6 * np.sin(0.5 * s), -0.2 + 0.05 * np.sin(0.9 * s), -1.8 + 0.3 * np.cos(0.4 * s)])
+        target = np.array([0.4 * np.sin(0.3 * s), 0.3, 1.5])
+        poses.append(look_at_pose(eye, target))
+    return poses
+
+
+def room_camera(width: int = 640, height: int = 480, f: float = 525.0) -> Camera:
+    return Camera(f, f, width / 2.0, height / 2.0, width, height)
+
+
+def mapping_scene(n: int = 200_000, views: int = 8, seed: int = 0, width: int = 640, height: int = 480) -> Scene:
+    """Mapping step: n room Gaussians, `views` keyframes on a ring inside the
+    room looking inward, targets ray-cast with 1% depth noise (depth outside
+    0.5-5 m marked invalid)."""
+    rec, oid, objs = room_scene(n, seed)
+    cam = room_camera(width, height)
+    rng = np.random.default_rng(seed + 1)
+    poses, tgs = [], []
+    for v in range(views):
+        a = 2 * np.pi * v / views
+        eye = np.array([1.6 * np.cos(a), -0.3, 1.6 * np.sin(a)])
+        target = np.array([-0.5 * np.cos(a), 0.4, -0.5 * np.sin(a)])
+        pose = look_at_pose(eye, target)
+        tg, _ = raycast(cam, pose, objs, 0.0, 0.01, rng)
+        tg[(tg[:, 3] < 0.5) | (tg[:, 3] > 5.0), 3] = 0.0
+        poses.append(pose); tgs.append(tg)
+    return Scene(rec, cam, np.stack(poses), np.stack(tgs), oid >= 0, dict(objects=objs, object_id=oid))
+
+
+def tracking_scene(n: int = 300_000, frame: int = 10, seed: int = 0, width: int = 640, height: int = 480,
+                   fps: float = 30.0, flip: float = 0.05) -> Scene:
+    """Tracking + MP update: the map holds the objects at their frame-0
+    positions; the target of `frame` is ray-cast with the two moving objects
+    translated at 0.3 m/s; the pose is the previous frame's (the tracking
+    starting point) and extra['gt_pose'] the frame's own. Also returns the
+    instance label map of the moving objects with `flip` pixel flip noise."""
+    rec, oid, objs = room_scene(n, seed)
+    cam = room_camera(width, height)
+    path = camera_path(frame + 1, fps)
+    rng = np.random.default_rng(seed + 7 + frame)
+    tg, hit = raycast(cam, path[frame], objs, frame / fps, 0.01, rng)
+    tg[(tg[:, 3] < 0.5) | (tg[:, 3] > 5.0), 3] = 0.0
+    moving = [k for k, ob in enumerate(objs) if np.any(ob.velocity != 0)]
+    inst = np.zeros(hit.shape, np.uint8)
+    for lab, k in enumerate(moving, start=1):
+        inst[hit == k] = lab
+    if flip > 0:
+        fl = rng.random(inst.shape) < flip
+        repl = rng.integers(0, len(moving) + 1, inst.shape).astype(np.uint8)
+        same = repl == inst
+        repl[same] = (repl[same] + 1) % (len(moving) + 1)
+        inst = np.where(fl, repl, inst).astype(np.uint8)
+    prev = path[frame - 1] if frame > 0 else path[0]
+    return Scene(rec, cam, prev[None], tg[None], np.isin(oid, moving),
+                 dict(objects=objs, object_id=oid, gt_pose=path[frame], instance=inst, n_instances=len(moving)))

@@ -1,0 +1,172 @@
+"""Pins of the FP64 MP-update oracle: special cases that reduce each step of
+Sec. IV-A to a closed form (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import mp as M
+from paper_2602_21644_gb300 import synth
+
+W, H = 24, 20
+CAM = (30.0, 30.0, 12.0, 10.0, W, H)
+
+
+def flat_obs(inst=None, e_depth=0.0, d_rend=2.0):
+    """Maps where the residual is |D_obs - D_rend| = e_depth everywhere."""
+    inst = np.zeros(W * H, np.uint8) if inst is None else inst
+    d_obs = np.full(W * H, d_rend + e_depth)
+    c = np.full((W * H, 3), 0.5)
+    return inst, d_obs, c, np.full(W * H, d_rend), c.copy()
+
+
+def points_on_grid(n, z=2.0, seed=0):
+    rng = np.random.default_rng(seed)
+    u = rng.uniform(3, W - 4, n)
+    v = rng.uniform(3, H - 4, n)
+    return np.stack([(u - 12.0) * z / 30.0, (v - 10.0) * z / 30.0, np.full(n, z)], 1)
+
+
+TABLE = np.array([[0.1, 0.05], [0.9, 0.8]])
+
+
+def test_lower_median():
+    assert M.lower_median([3, 1, 2]) == 2
+    assert M.lower_median([4, 1, 3, 2]) == 2
+    assert M.lower_median([5.0]) == 5.0
+
+
+def test_fusion_special_cases():
+    rng = np.random.default_rng(0)
+    inst = (rng.random(W * H) < 0.3).astype(np.uint8)
+    d_obs = rng.uniform(1, 3, W * H)
+    d_rend = d_obs + rng.normal(0, 0.1, W * H)
+    c_obs = rng.uniform(0, 1, (W * H, 3))
+    c_rend = rng.uniform(0, 1, (W * H, 3))
+    k0 = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(fusion_mode=1))
+    np.testing.assert_array_equal(k0["M_p"], TABLE[inst, 0])          # K = 0: MP_ins, Eq. (2)
+    k1 = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(fusion_mode=2))
+    np.testing.assert_array_equal(k1["M_p"], k1["mp_geo"])             # K = 1: MP_geo
+    fz = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig())
+    lo = np.minimum(fz["mp_ins"], fz["mp_geo"]) - 1e-15
+    hi = np.maximum(fz["mp_ins"], fz["mp_geo"]) + 1e-15
+    assert np.all((fz["M_p"] >= lo) & (fz["M_p"] <= hi))                # convex combination
+    assert np.all((fz["K"] >= 0) & (fz["K"] <= 1))
+
+
+def test_geometric_mp_closed_form():
+    # Region statistics by hand: background residuals 0.01 / 0.03 alternating
+    # (mean 0.02, std 0.01) -> e_ub = max(0.02 + 2 * 0.01, 0.05) = 0.05;
+    # instance residual 0.3 everywhere (std 0 < sigma_min -> instance mean).
+    inst = np.zeros(W * H, np.uint8)
+    inst[: W * 4] = 1
+    e = np.where(np.arange(W * H) % 2 == 0, 0.01, 0.03)
+    e[inst == 1] = 0.3
+    d_rend = np.full(W * H, 2.0)
+    c = np.full((W * H, 3), 0.5)
+    cfg = M.MPConfig()
+    px = M.pixel_mp(inst, d_rend + e, c, d_rend, c, TABLE, cfg)
+    np.testing.assert_allclose(px["mean"], [0.02, 0.3], rtol=1e-12)
+    np.testing.assert_allclose(px["std"], [0.01, 0.0], atol=1e-12)
+    np.testing.assert_allclose(px["e_ub"], [0.05, 0.3], rtol=1e-12)
+    bg = inst == 0
+    np.testing.assert_allclose(px["mp_geo"][bg], e[bg] / 0.05, rtol=1e-12)
+    np.testing.assert_allclose(px["mp_geo"][~bg], 1.0, rtol=1e-12)
+    g_geo_bg = np.exp(-0.01 / 0.05)
+    K_bg = g_geo_bg / (0.05 + g_geo_bg)
+    np.testing.assert_allclose(px["K"][bg], K_bg, rtol=1e-12)
+    np.testing.assert_allclose(px["M_p"][bg], (1 - K_bg) * 0.1 + K_bg * e[bg] / 0.05, rtol=1e-12)
+    K_in = 1.0 / (0.8 + 1.0)
+    np.testing.assert_allclose(px["M_p"][~bg], (1 - K_in) * 0.9 + K_in * 1.0, rtol=1e-12)
+
+
+def test_instant_update_equals_observation():
+    # alpha_min = alpha_max = 1 -> M^t = M_hat (Instant MP, Sec. V-E Ablation I)
+    # and with uniform M_p the observation is that value exactly.
+    n = 40
+    means = points_on_grid(n)
+    inst, d_obs, c, d_rend, c2 = flat_obs()
+    cfg = M.MPConfig(alpha_min=1.0, alpha_max=1.0, fusion_mode=1)
+    r = M.mp_update(means, np.full(n, 0.7), np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c,
+                    d_rend, c2, TABLE, cfg)
+    assert r["observed"].all()
+    np.testing.assert_allclose(r["mp"], 0.1, rtol=1e-12)
+    assert r["tau"] == 0.5 and not r["labels"].any()
+
+
+def test_fixed_rate_and_rho():
+    n = 30
+    means = points_on_grid(n, seed=1)
+    inst, d_obs, c, d_rend, c2 = flat_obs()
+    prev = np.linspace(0.05, 0.95, n)
+    cfg = M.MPConfig(alpha_min=0.3, alpha_max=0.3, fusion_mode=1)
+    r = M.mp_update(means, prev, np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c, d_rend, c2,
+                    TABLE, cfg)
+    np.testing.assert_allclose(r["mp"], 0.7 * prev + 0.3 * 0.1, rtol=1e-12)    # Eq. (9), fixed rate
+    r2 = M.mp_update(means, prev, np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c, d_rend, c2,
+                     TABLE, cfg, seg_refreshed=False)
+    np.testing.assert_allclose(r2["mp"], (1 - 0.15) * prev + 0.15 * 0.1, rtol=1e-12)  # Eq. (17), rho = 0.5
+
+
+def test_adaptive_rate_closed_form():
+    # Two observed Gaussians with known uncertainty: Var{M_p} = 0 (uniform map)
+    # so U is the entropy of M^{t-1}; min-max normalisation gives U~ = 0 for the
+    # more certain and 1 for the less certain one. With sigma_e,G = 0, C = 1:
+    # alpha = alpha_max for the first and alpha_min for the second (Eq. (11)).
+    means = points_on_grid(2, seed=2)
+    inst, d_obs, c, d_rend, c2 = flat_obs()
+    prev = np.array([0.05, 0.45])
+    cfg = M.MPConfig(fusion_mode=1)
+    r = M.mp_update(means, prev, np.zeros(2, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c, d_rend, c2,
+                    TABLE, cfg)
+    ent = -prev * np.log(prev + 1e-6) - (1 - prev) * np.log(1 - prev + 1e-6)
+    np.testing.assert_allclose(r["U"], ent, rtol=1e-12)
+    np.testing.assert_allclose(r["U_tilde"], [0.0, 1.0], atol=1e-15)
+    np.testing.assert_allclose(r["alpha"], [0.6, 0.05], rtol=1e-12)
+    np.testing.assert_allclose(r["mp"], (1 - r["alpha"]) * prev + r["alpha"] * 0.1, rtol=1e-12)
+    assert r["U_bar"] == 0.0                                      # lower median of {0, 1}
+
+
+def test_weighted_observation_and_variance():
+    # One Gaussian projected exactly on a pixel centre p0 of a map where
+    # M_p = 1 at p0 and 0 elsewhere (K = 0, table values): its disk of radius 2
+    # holds 13 pixels; M_hat = 1 / sum_{13} exp(-d^2/2) and Var = (1/13)(12/13).
+    n = 1
+    z = 2.0
+    means = np.array([[(15 - 12.0) * z / 30.0, (9 - 10.0) * z / 30.0, z]])
+    inst = np.zeros(W * H, np.uint8)
+    inst[9 * W + 15] = 1
+    table = np.array([[0.0, 0.05], [1.0, 0.8]])
+    d_rend = np.full(W * H, 2.0)
+    c = np.full((W * H, 3), 0.5)
+    cfg = M.MPConfig(fusion_mode=1, alpha_min=1.0, alpha_max=1.0)
+    r = M.mp_update(means, np.array([0.5]), np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_rend, c,
+                    d_rend, c, table, cfg)
+    d2 = np.array([0, 1, 1, 1, 1, 2, 2, 2, 2, 4, 4, 4, 4], float)
+    np.testing.assert_allclose(r["m_hat"], 1.0 / np.exp(-d2 / 2).sum(), rtol=1e-12)
+    np.testing.assert_allclose(r["var"], (1 / 13) * (12 / 13), rtol=1e-12)
+
+
+def test_unobserved_unchanged_and_bounds():
+    rng = np.random.default_rng(4)
+    n = 200
+    means = np.concatenate([points_on_grid(150, seed=3), [[0, 0, -1.0]] * 10,        # behind the camera
+                            [[50.0, 0, 2.0]] * 10,                                   # outside the image
+                            points_on_grid(30, z=3.0, seed=5)])                       # occluded (behind 2 m)
+    inst = (rng.random(W * H) < 0.3).astype(np.uint8)
+    d_obs = rng.uniform(1.5, 2.5, W * H)
+    d_rend = np.full(W * H, 2.0)
+    c_obs = rng.uniform(0, 1, (W * H, 3))
+    c_rend = rng.uniform(0, 1, (W * H, 3))
+    prev = rng.uniform(0, 1, n)
+    lab = (rng.random(n) < 0.5).astype(np.uint8)
+    for refreshed in (True, False):
+        r = M.mp_update(means, prev, lab, CAM, synth.identity_pose(), inst, d_obs, c_obs, d_rend, c_rend, TABLE,
+                        M.MPConfig(), refreshed)
+        obs = r["observed"]
+        assert obs[:150].all() and not obs[150:].any()
+        np.testing.assert_array_equal(r["mp"][~obs], prev[~obs])
+        np.testing.assert_array_equal(r["labels"][~obs], lab[~obs])
+        assert np.all((r["mp"] >= 0) & (r["mp"] <= 1))
+        assert r["tau"] >= 0.5
+        assert np.all((r["alpha"][obs] >= (0.5 if not refreshed else 1) * 0.05 - 1e-15))
+        assert np.all(r["alpha"][obs] <= 0.6 + 1e-15)
+        np.testing.assert_array_equal(r["labels"][obs], (r["mp"][obs] > r["tau"]).astype(np.uint8))
