@@ -33,15 +33,15 @@ _lib = None
 
 # Layout constants mirrored from splat_oracle.c.
 G_STRIDE = 15
-PJ_STRIDE = 20
+PJ_STRIDE = 21
 PX_STRIDE = 10
 PJ = dict(VIS=0, U=1, V=2, Z=3, A=4, B=5, C=6, O=7, SA=8, SB=9, SC=10, LMAX=11, R=12,
-          X0=13, Y0=14, X1=15, Y1=16, FLAG=17, PX=18, PY=19)
+          X0=13, Y0=14, X1=15, Y1=16, FLAG=17, PX=18, PY=19, ZKEY=20)
 PX = dict(CR=0, CG=1, CB=2, D=3, O=4, RMP=5, T=6, N=7, LAST=8, W=9)
 FLAGS = dict(ZNEAR=1, CLAMP=2, RADIUS=4, RECT=8, OPAC=16, ALPHA=32, AMAX=64, TSTOP=128,
              ZTIE=256, OEPS=512, SIGN=1024)
 # Pixel flags that make a pixel's values not decided identically in FP32 and FP64.
-PIXEL_DECISION_FLAGS = FLAGS["ALPHA"] | FLAGS["AMAX"] | FLAGS["TSTOP"] | FLAGS["ZTIE"] | FLAGS["OEPS"]
+PIXEL_DECISION_FLAGS = FLAGS["ALPHA"] | FLAGS["AMAX"] | FLAGS["TSTOP"] | FLAGS["OEPS"]
 
 
 def build(force: bool = False) -> str:
@@ -141,7 +141,7 @@ def project(G, cam, pose, rc=None):
 
 def binning(G, cam, pose, rc=None):
     """(tiles, ids, tie_flags) of all (tile, Gaussian) pairs sorted by
-    (tile, depth, id); tile = ty * tiles_x + tx."""
+    (tile, FP32 depth key, id); tile = ty * tiles_x + tx."""
     lib = _load()
     G = _f64(G, (-1, G_STRIDE))
     rc = raster_vec() if rc is None else _f64(rc)

@@ -27,10 +27,12 @@
  * 1.3x frustum guard on the Jacobian, opacity-aware bounding radius) are
  * stated in the design notes and mirrored in the C ABI's config struct.
  *
- * Decisions that floating point takes (skip, clamp, stop, tile bounds,
- * depth ties, residual signs) are flagged when the FP64 quantity lies within
- * a relative 1e-5 of its threshold, so a test can tell an FP32-vs-FP64
- * rounding disagreement from a bug.
+ * The depth order is decided on an FP32 depth key that both this oracle and
+ * the CUDA path evaluate bit-identically (see depth_key). Other decisions
+ * that floating point takes (skip, clamp, stop, tile bounds, residual signs)
+ * are flagged when the FP64 quantity lies within a relative 1e-5 of its
+ * threshold, so a test can tell an FP32-vs-FP64 rounding disagreement from
+ * a bug.
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,7 +59,7 @@ enum { LC_LPHO = 0, LC_LDEPTH, LC_WMODE, LC_WGRAD, LC_OEPS, LC_N };
 
 /* Projection record per Gaussian. */
 enum { PJ_VIS = 0, PJ_U, PJ_V, PJ_Z, PJ_A, PJ_B, PJ_C, PJ_O, PJ_SA, PJ_SB, PJ_SC,
-       PJ_LMAX, PJ_R, PJ_X0, PJ_Y0, PJ_X1, PJ_Y1, PJ_FLAG, PJ_PX, PJ_PY, PJ_STRIDE };
+       PJ_LMAX, PJ_R, PJ_X0, PJ_Y0, PJ_X1, PJ_Y1, PJ_FLAG, PJ_PX, PJ_PY, PJ_ZKEY, PJ_STRIDE };
 
 /* Per-pixel output: colour (3), depth, opacity, rendered MP, final
  * transmittance, number of contributors, id of the last contributor (-1),
@@ -75,7 +77,7 @@ enum { PX_CR = 0, PX_CG, PX_CB, PX_D, PX_O, PX_RMP, PX_T, PX_N, PX_LAST, PX_W, P
 #define FL_ALPHA   32   /* pixel: some o*G within margin of alpha_min        */
 #define FL_AMAX    64   /* pixel: some o*G within margin of alpha_max        */
 #define FL_TSTOP  128   /* pixel: transmittance test within margin of t_min  */
-#define FL_ZTIE   256   /* pixel/bin: two consecutive depths within 1e-6 z   */
+#define FL_ZTIE   256   /* unused (depth order is decided on the FP32 key)   */
 #define FL_OEPS   512   /* pixel: opacity within margin of o_eps             */
 #define FL_SIGN  1024   /* pixel: a loss residual within margin of zero      */
 
@@ -129,8 +131,27 @@ typedef struct {
   double A, B, C;       /* 2D covariance after dilation              */
   double a, b, c;       /* conic = inverse 2D covariance             */
   double o, u, v, lmax, rext;
+  float zkey;           /* FP32 depth key that decides the depth order      */
   int r, x0, y0, x1, y1;
 } proj_t;
+
+/* Depth order key. The order of two Gaussians whose depths differ by less
+ * than the rounding of a 32-bit float is not decided by the depth itself,
+ * so the order is defined on this FP32 key (ties by id): the camera z of the
+ * record's FP32 mean under the pose rounded to FP32, evaluated in FP32 in
+ * exactly this order, without fused multiply-adds. The CUDA path evaluates
+ * the same expression, so both sides take the decision identically. */
+static float depth_key(const double *g, const double *pose) {
+  float r20 = (float)pose[8], r21 = (float)pose[9], r22 = (float)pose[10], tz = (float)pose[11];
+  float mx = (float)g[G_MX], my = (float)g[G_MY], mz = (float)g[G_MZ];
+  volatile float a = r20 * mx;
+  volatile float b = r21 * my;
+  volatile float c = r22 * mz;
+  volatile float ab = a + b;
+  volatile float abc = ab + c;
+  volatile float z = abc + tz;
+  return z;
+}
 
 static void project_one(const double *g, const double *cam, const double *pose,
                         const double *rc, proj_t *P) {
@@ -141,6 +162,7 @@ static void project_one(const double *g, const double *cam, const double *pose,
   (void)Rw;
   for (int i = 0; i < 3; i++)
     P->p[i] = R[3 * i] * g[G_MX] + R[3 * i + 1] * g[G_MY] + R[3 * i + 2] * g[G_MZ] + t[i];
+  P->zkey = depth_key(g, pose);
   double x = P->p[0], y = P->p[1], z = P->p[2];
   if (near_rel(z, rc[RC_Z_NEAR])) P->flags |= FL_ZNEAR;
   if (!(z > rc[RC_Z_NEAR])) return;
@@ -234,13 +256,13 @@ void oracle_project(int64_t n, const double *G, const double *cam, const double 
     o[PJ_A] = P.a; o[PJ_B] = P.b; o[PJ_C] = P.c; o[PJ_O] = P.o;
     o[PJ_SA] = P.A; o[PJ_SB] = P.B; o[PJ_SC] = P.C; o[PJ_LMAX] = P.lmax;
     o[PJ_R] = P.r; o[PJ_X0] = P.x0; o[PJ_Y0] = P.y0; o[PJ_X1] = P.x1; o[PJ_Y1] = P.y1;
-    o[PJ_FLAG] = P.flags; o[PJ_PX] = P.p[0]; o[PJ_PY] = P.p[1];
+    o[PJ_FLAG] = P.flags; o[PJ_PX] = P.p[0]; o[PJ_PY] = P.p[1]; o[PJ_ZKEY] = (double)P.zkey;
   }
 }
 
-/* ---- depth order ---- */
+/* ---- depth order: (FP32 depth key, id) ---- */
 
-typedef struct { double z; int64_t id; } zkey_t;
+typedef struct { float z; int64_t id; } zkey_t;
 
 static int cmp_zkey(const void *pa, const void *pb) {
   const zkey_t *a = (const zkey_t *)pa, *b = (const zkey_t *)pb;
@@ -252,10 +274,10 @@ static int cmp_zkey(const void *pa, const void *pb) {
 /* ---- binning ---- */
 
 /* Pairs (tile, id) of every visible Gaussian and every tile of its rect,
- * sorted by (tile, depth, id). Writes up to cap pairs, returns the total.
- * tie_flag[k] = 1 where pair k and pair k-1 share a tile and their depths
- * are within 1e-6 z (their order is not decided by FP64 vs FP32 alike). */
-typedef struct { int64_t tile; double z; int64_t id; } bkey_t;
+ * sorted by (tile, depth key, id). Writes up to cap pairs, returns the total.
+ * tie_flag[k] = 1 where pair k and pair k-1 share a tile and an equal depth
+ * key (their order is then decided by the id). */
+typedef struct { int64_t tile; float z; int64_t id; } bkey_t;
 
 static int cmp_bkey(const void *pa, const void *pb) {
   const bkey_t *a = (const bkey_t *)pa, *b = (const bkey_t *)pb;
@@ -282,7 +304,7 @@ int64_t oracle_binning(int64_t n, const double *G, const double *cam, const doub
     for (int y = P[i].y0; y < P[i].y1; y++)
       for (int x = P[i].x0; x < P[i].x1; x++) {
         keys[k].tile = (int64_t)y * tx + x;
-        keys[k].z = P[i].p[2];
+        keys[k].z = P[i].zkey;
         keys[k].id = i;
         k++;
       }
@@ -291,8 +313,7 @@ int64_t oracle_binning(int64_t n, const double *G, const double *cam, const doub
   for (int64_t j = 0; j < total && j < cap; j++) {
     tiles[j] = keys[j].tile;
     ids[j] = keys[j].id;
-    tie_flag[j] = (j > 0 && keys[j].tile == keys[j - 1].tile &&
-                   fabs(keys[j].z - keys[j - 1].z) <= 1e-6 * keys[j].z);
+    tie_flag[j] = (j > 0 && keys[j].tile == keys[j - 1].tile && keys[j].z == keys[j - 1].z);
   }
   free(keys);
   free(P);
@@ -368,7 +389,7 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
   int64_t nv = 0;
   for (int64_t i = 0; i < n; i++) {
     project_one(G + i * G_STRIDE, cam, pose, rc, &P[i]);
-    if (P[i].vis) { zk[nv].z = P[i].p[2]; zk[nv].id = i; nv++; }
+    if (P[i].vis) { zk[nv].z = P[i].zkey; zk[nv].id = i; nv++; }
   }
   qsort(zk, (size_t)nv, sizeof(zkey_t), cmp_zkey);
   for (int64_t k = 0; k < nv; k++) order[k] = zk[k].id;
@@ -389,7 +410,6 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
       double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0};
       int flags = 0;
       int64_t nl = 0, last = -1;
-      double prev_z = -1.0;
       for (int64_t q = cs.start[c]; q < cs.start[c + 1]; q++) {
         int64_t id = cs.ids[q];
         const proj_t *p = &P[id];
@@ -402,8 +422,6 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
         if (ag < amin) continue;
         int clamped = ag > amax;
         double alpha = clamped ? amax : ag;
-        if (prev_z >= 0 && fabs(p->p[2] - prev_z) <= 1e-6 * p->p[2]) flags |= FL_ZTIE;
-        prev_z = p->p[2];
         double testT = T * (1.0 - alpha);
         if (near_rel(testT, tmin)) flags |= FL_TSTOP;
         if (testT < tmin) break;
@@ -642,10 +660,10 @@ int oracle_render_pixel(int64_t n, const double *G, const double *cam, const dou
   int64_t nv = 0;
   for (int64_t k = 0; k < n; k++) {
     project_one(G + k * G_STRIDE, cam, pose, rc, &P[k]);
-    if (P[k].vis) { zk[nv].z = P[k].p[2]; zk[nv].id = k; nv++; }
+    if (P[k].vis) { zk[nv].z = P[k].zkey; zk[nv].id = k; nv++; }
   }
   qsort(zk, (size_t)nv, sizeof(zkey_t), cmp_zkey);
-  double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0}, prev_z = -1;
+  double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0};
   int flags = 0, nl = 0;
   int64_t last = -1;
   for (int64_t q = 0; q < nv; q++) {
@@ -657,8 +675,6 @@ int oracle_render_pixel(int64_t n, const double *G, const double *cam, const dou
     if (near_rel(ag, rc[RC_ALPHA_MAX])) flags |= FL_AMAX;
     if (ag < rc[RC_ALPHA_MIN]) continue;
     double alpha = ag > rc[RC_ALPHA_MAX] ? rc[RC_ALPHA_MAX] : ag;
-    if (prev_z >= 0 && fabs(p->p[2] - prev_z) <= 1e-6 * p->p[2]) flags |= FL_ZTIE;
-    prev_z = p->p[2];
     double testT = T * (1.0 - alpha);
     if (near_rel(testT, rc[RC_T_MIN])) flags |= FL_TSTOP;
     if (testT < rc[RC_T_MIN]) break;

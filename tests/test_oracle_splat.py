@@ -223,7 +223,7 @@ def test_transmittance_monotone_in_depth_order():
     pj = oracle.project(G, cam, sc.poses[0])
     r = oracle.render(G, cam, sc.poses[0])
     vis = np.nonzero(pj[:, 0] > 0)[0]
-    order = vis[np.lexsort((vis, pj[vis, 3]))]
+    order = vis[np.lexsort((vis, pj[vis, oracle.PJ["ZKEY"]]))]
     for pix in [0, 77, 500, 1000, 1919]:
         i, j = pix % 48, pix // 48
         T, Ts = 1.0, [1.0]
@@ -287,8 +287,8 @@ def test_binning_order_and_content():
             for tx in range(int(pj[g, 13]), int(pj[g, 15])):
                 exp.append((ty * 10 + tx, g))
     assert sorted(exp) == sorted(zip(tiles.tolist(), ids.tolist()))
-    # order: (tile, depth, id)
-    order = np.lexsort((ids, pj[ids, 3], tiles))
+    # order: (tile, FP32 depth key, id)
+    order = np.lexsort((ids, pj[ids, oracle.PJ["ZKEY"]], tiles))
     np.testing.assert_array_equal(order, np.arange(len(ids)))
 
 
@@ -363,3 +363,23 @@ def test_paper_constants_fixture():
         c = json.load(f)
     lc = oracle.loss_vec()
     assert lc[0] == c["lambda_1"]["value"] and lc[1] == c["lambda_2"]["value"]
+
+
+def test_depth_key_is_fp32_camera_depth():
+    # The key is the FP32 evaluation of r20 mx + r21 my + r22 mz + tz (no FMA),
+    # written here with numpy float32 scalars; it equals the FP64 depth to
+    # FP32 precision.
+    sc = synth.tiny_scene(3, n=200)
+    G = oracle.params_from_records(sc.records)
+    pose = synth.look_at_pose([0.3, -0.2, -0.5], [0.1, 0.0, 2.0])
+    cam = oracle.camera_vec(*sc.camera.as_tuple())
+    pj = oracle.project(G, cam, pose)
+    f = np.float32
+    r = pose.astype(np.float32)
+    m = sc.records[:, 0:3]
+    key = ((r[2, 0] * m[:, 0] + r[2, 1] * m[:, 1]) + r[2, 2] * m[:, 2]) + r[2, 3]
+    assert key.dtype == np.float32
+    np.testing.assert_array_equal(pj[:, oracle.PJ["ZKEY"]].astype(np.float32), key)
+    vis = pj[:, 0] > 0
+    np.testing.assert_allclose(pj[vis, oracle.PJ["ZKEY"]], pj[vis, oracle.PJ["Z"]], rtol=3e-7)
+    del f
