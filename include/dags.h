@@ -1,0 +1,194 @@
+/*
+ * dags.h -- C ABI of the GB300 (sm_103a) MP-aware differentiable Gaussian
+ * splatting library (libdags.so): the data-parallel hot path of DAGS-SLAM
+ * (arXiv 2602.21644).
+ *
+ * Conventions for every entry point
+ *   - extern "C", plain pointers and sizes; no C++ or framework types.
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary CPU memory, read before the call returns.
+ *   - Work is enqueued asynchronously on the given cudaStream_t (passed as
+ *     void*; NULL = legacy default stream). No call synchronises the device
+ *     except dags_sync_status and the e2e helpers that say so.
+ *   - The caller owns every input and output buffer; a dags_ctx owns only
+ *     its workspace. A ctx must not be used from two streams at once.
+ *   - Return value: DAGS_OK (0) or a negative DAGS_E_* code. Argument errors
+ *     are found on the host before anything is launched. Errors that only the
+ *     device can see (pair-capacity overflow, a bounded wait that gave up)
+ *     are recorded in the ctx's device status word, which dags_sync_status
+ *     reads (and clears); the outputs of the call that raised them are
+ *     undefined. Enqueuing never waits for the device.
+ *   - Nothing traps, asserts or spins without a bound on the device.
+ *
+ * Data layouts
+ *   Gaussian record: 16 x 32-bit words (64 bytes), n records contiguous:
+ *     0-2 mean (world, m) | 3 opacity logit | 4-7 rotation quaternion
+ *     (w, x, y, z; any non-zero norm) | 8-10 natural-log scale per axis |
+ *     11 motion probability M in [0, 1] | 12 = bf16(r) | bf16(g) << 16 |
+ *     13 = bf16(b) | 14-15 ignored.  (Sec. IV-A: a Gaussian is a mean,
+ *     opacity, scale and rotation, augmented with its MP state; colour is
+ *     view-independent RGB stored in BF16.)
+ *   Pose: 12 doubles, row-major 3x4 [R | t], world -> camera (T_CW).
+ *   Targets: per view H*W float4 (r, g, b, depth) in row-major pixel order;
+ *     depth <= 0 marks a pixel without valid depth.
+ *   Image (forward output): per view DAGS_IMG_CHANNELS planes of H*W float:
+ *     0-2 colour C, 3 depth D, 4 opacity O = 1 - T_final, 5 rendered MP
+ *     R_MP = sum_k omega_k M_k, 6 final transmittance, 7 static weight w(u)
+ *     of Eq. (20) (0 when no targets are given).
+ *   Gaussian gradient: 16 floats per Gaussian, same slots as the record
+ *     (mean, opacity logit, quaternion, log-scale, 0, colour r g b, 0, 0).
+ *   Pose gradient / twist: 6 doubles (rho_x, rho_y, rho_z, phi_x, phi_y,
+ *     phi_z) of the left perturbation T <- exp(xi^) T.
+ *   Pixel (i, j) is the point (u, v) = (i, j); u = fx x / z + cx.
+ */
+#ifndef DAGS_H
+#define DAGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DAGS_ABI_VERSION 1
+#define DAGS_IMG_CHANNELS 8
+#define DAGS_GRAD_WORDS 16
+#define DAGS_RECORD_WORDS 16
+
+enum {
+  DAGS_OK = 0,
+  DAGS_E_INVAL = -1,     /* bad argument (host check)                         */
+  DAGS_E_CUDA = -2,      /* a CUDA runtime call failed                        */
+  DAGS_E_CAPACITY = -3,  /* tile/Gaussian pairs exceeded the ctx's max_pairs  */
+  DAGS_E_TIMEOUT = -4,   /* a bounded device wait gave up                     */
+  DAGS_E_NOMEM = -5,     /* workspace allocation failed                       */
+  DAGS_E_ORDER = -6      /* splat_backward without its matching splat_forward */
+};
+
+typedef struct dags_ctx dags_ctx;
+
+/* Pinhole camera shared by all views of a call. */
+typedef struct {
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} dags_camera;
+
+/* Rasteriser constants. The paper inherits the 3DGS rasteriser without
+ * printing it (Sec. IV-D, "during rasterization"); these are the readings
+ * the oracle uses. tile must be 16. */
+typedef struct {
+  int32_t tile;       /* 16 */
+  float alpha_min;    /* skip a Gaussian whose alpha is below this (1/255)    */
+  float alpha_max;    /* clamp alpha to this (0.99)                           */
+  float t_min;        /* stop before transmittance would fall below (1e-4)    */
+  float dilation;     /* added to the 2D covariance diagonal, px^2 (0.3)      */
+  float z_near;       /* cull means with camera z <= z_near, m (0.2)          */
+  float guard;        /* Jacobian evaluated with |x/z| clamped to guard * W/(2 fx) (1.3) */
+} dags_raster_cfg;
+
+/* MP-weighted loss of Eqs. (20)-(22): L = sum_u w(u) (lambda_pho ||C - C_gt||_1
+ * + lambda_depth [D_gt > 0] |D - D_gt|). weight_mode 0: w = (O - R_MP) / O
+ * (compositing weights normalised to sum to 1, as Eq. (20) states; w = 0
+ * where O <= o_eps); 1: w = O - R_MP. weight_grad 0: w is a constant of the
+ * adjoint (stop-gradient); 1: it is differentiated. lambda_pho = 0.9,
+ * lambda_depth = 0.1 are the paper's (Sec. V-A(c)). */
+typedef struct {
+  float lambda_pho, lambda_depth;
+  int32_t weight_mode, weight_grad;
+  float o_eps;
+} dags_loss_cfg;
+
+/* Adam on the pose twist (Eq. (27)'s pose part; first-order reading of the
+ * paper's pose refinement). lr per twist component. */
+typedef struct {
+  double lr[6];
+  double beta1, beta2, eps;
+} dags_pose_cfg;
+
+void dags_default_raster_cfg(dags_raster_cfg *cfg);
+void dags_default_loss_cfg(dags_loss_cfg *cfg);
+void dags_default_pose_cfg(dags_pose_cfg *cfg);
+
+/* Create a context on the current CUDA device with workspace for up to
+ * max_gaussians Gaussians, images up to max_width x max_height, max_views
+ * views per call and max_pairs (tile, Gaussian) pairs per call (0 picks
+ * 16 * max_gaussians * max_views). Allocates device memory (cudaMalloc).
+ * Returns DAGS_E_INVAL / DAGS_E_NOMEM / DAGS_E_CUDA on failure (*out = NULL). */
+int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_t max_height,
+                int32_t max_views, int64_t max_pairs);
+void dags_destroy(dags_ctx *ctx);
+const char *dags_status_string(int code);
+int dags_abi_version(void);
+
+/* Synchronise the ctx's last stream, read and clear the device status word.
+ * Returns the pending status (DAGS_OK if none); *required_pairs (may be
+ * NULL) receives the pair count the last forward needed. */
+int dags_sync_status(dags_ctx *ctx, int64_t *required_pairs);
+
+/* Introspection (tests): after a splat_forward on this ctx, copy its tile
+ * offsets (n_start = n_views * tiles + 1 uint32, tiles = ceil(W/16) *
+ * ceil(H/16), view-major then row-major tiles) and the depth-ordered Gaussian
+ * ids of all tiles (up to cap uint32) to host memory. Synchronises the ctx's
+ * last stream. *n_pairs (may be NULL) receives the pair count. Returns
+ * DAGS_E_CAPACITY if that forward overflowed, DAGS_E_INVAL if n_start does
+ * not match it. The sort key is (tile, FP32 camera depth of the mean
+ * computed as ((r20 mx + r21 my) + r22 mz) + tz without FMA, Gaussian id). */
+int dags_copy_bins(dags_ctx *ctx, uint32_t *tile_start, int64_t n_start, uint32_t *ids, int64_t cap,
+                   int64_t *n_pairs);
+
+/* Forward: project, bin, depth-sort and alpha-composite n Gaussians into
+ * n_views views (one camera, per-view poses), and with targets the loss.
+ *
+ * gauss     device, n records (see layout). n may be 0.
+ * cam       host, one camera; width/height <= the ctx maxima.
+ * poses     device, n_views x 12 doubles.
+ * targets   device, n_views x H*W float4, or NULL (no loss, w = 0).
+ * image     device out, n_views x DAGS_IMG_CHANNELS x H*W floats.
+ * last      device out, n_views x H*W int32: per pixel, how many entries of
+ *           its tile's depth-sorted list the compositing walked up to and
+ *           including its last contributor (forward state for the backward).
+ * loss      device out (1 double) or NULL; the sum over views of Eq. (21),
+ *           (22) weighted by lambda_pho, lambda_depth; needs targets.
+ * The ctx keeps the depth-sorted tile lists and the projected Gaussians of
+ * this call for splat_backward.
+ * Sec. IV-D (MP-guided rendering), Eqs. (20)-(22). */
+int splat_forward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam,
+                  const double *poses, int32_t n_views, const float *targets,
+                  const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg, float *image,
+                  int32_t *last, double *loss, void *stream);
+
+#define DAGS_GRAD_GAUSS 1u
+#define DAGS_GRAD_POSE 2u
+
+/* Backward of the loss of the preceding splat_forward on this ctx (same
+ * gauss, n, cam, poses, n_views, targets, configs, image and last; the ctx
+ * checks that image and last are the buffers of its latest forward and
+ * returns DAGS_E_ORDER otherwise). targets must be non-NULL.
+ * grad_flags   DAGS_GRAD_GAUSS and/or DAGS_GRAD_POSE.
+ * grad_gauss   device out n x 16 floats (overwritten), needed with
+ *              DAGS_GRAD_GAUSS, else may be NULL.
+ * grad_pose    device out n_views x 6 doubles (overwritten), needed with
+ *              DAGS_GRAD_POSE, else may be NULL.
+ * The adjoint re-derives each pixel's transmittance backwards from its
+ * final value and walks only its recorded contributors; per-Gaussian 2D
+ * gradients are summed over each warp before one atomic add per Gaussian;
+ * the pose gradient is reduced in a fixed order in FP64.
+ * Eq. (27): joint optimisation of Gaussian parameters and camera poses. */
+int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam,
+                   const double *poses, int32_t n_views, const float *targets,
+                   const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg, const float *image,
+                   const int32_t *last, uint32_t grad_flags, float *grad_gauss,
+                   double *grad_pose, void *stream);
+
+/* FP64 pose step for n_views poses: Adam on the twist (state per view: 13
+ * doubles m[6], v[6], step, device, in/out), then pose <- exp(xi^) pose.
+ * poses device in/out n_views x 12; grad device n_views x 6; cfg host.
+ * Sec. V-A(c) (pose refinement) and Eq. (27). */
+int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state,
+              int32_t n_views, const dags_pose_cfg *cfg, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAGS_H */

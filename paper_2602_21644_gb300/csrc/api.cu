@@ -1,0 +1,316 @@
+// C ABI of libdags.so (declared in include/dags.h): context and workspace,
+// host-side argument checks, and the launch sequence of each entry point.
+#include <math.h>
+#include <new>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+
+using namespace dags;
+
+struct dags_ctx {
+  int device = 0;
+  Workspace ws;
+  cudaStream_t last_stream = nullptr;
+  // the buffers of the latest forward (backward must follow its forward)
+  const void *fwd_image = nullptr;
+  const void *fwd_last = nullptr;
+  const void *fwd_gauss = nullptr;
+  int64_t fwd_n = -1;
+  int fwd_views = 0, fwd_w = 0, fwd_h = 0, fwd_tiles = 0;
+};
+
+namespace {
+
+template <class T>
+cudaError_t alloc(T **p, size_t count) {
+  return cudaMalloc((void **)p, (count > 0 ? count : 1) * sizeof(T));
+}
+
+void free_ws(Workspace &w) {
+  void *ptrs[] = {w.rec2d, w.rect, w.grad2d, w.tile_count, w.tile_start, w.tile_cursor, w.keys,
+                  w.keys_tmp, w.sorted_ids, w.big_tiles, w.loss_partial, w.pose_partial, w.pose32,
+                  w.counters};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  w = Workspace();
+}
+
+bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
+
+int check_camera(const dags_ctx *ctx, const dags_camera *cam) {
+  if (!cam) return DAGS_E_INVAL;
+  if (cam->width <= 0 || cam->height <= 0 || cam->width > ctx->ws.max_w || cam->height > ctx->ws.max_h)
+    return DAGS_E_INVAL;
+  if (!finite_pos(cam->fx) || !finite_pos(cam->fy) || !isfinite(cam->cx) || !isfinite(cam->cy))
+    return DAGS_E_INVAL;
+  return DAGS_OK;
+}
+
+int make_raster(const dags_camera *cam, const dags_raster_cfg *rc_in, Raster *r) {
+  dags_raster_cfg rc;
+  if (rc_in) rc = *rc_in;
+  else dags_default_raster_cfg(&rc);
+  if (rc.tile != kTile) return DAGS_E_INVAL;
+  if (!(rc.alpha_min > 0.f) || !(rc.alpha_max <= 1.f) || !(rc.alpha_min < rc.alpha_max)) return DAGS_E_INVAL;
+  if (!(rc.t_min > 0.f && rc.t_min < 1.f) || !(rc.dilation >= 0.f) || !(rc.z_near > 0.f) || !(rc.guard > 0.f))
+    return DAGS_E_INVAL;
+  r->fx = cam->fx; r->fy = cam->fy; r->cx = cam->cx; r->cy = cam->cy;
+  r->W = cam->width; r->H = cam->height;
+  r->tiles_x = (cam->width + kTile - 1) / kTile;
+  r->tiles_y = (cam->height + kTile - 1) / kTile;
+  r->T = r->tiles_x * r->tiles_y;
+  r->alpha_min = rc.alpha_min; r->alpha_max = rc.alpha_max; r->t_min = rc.t_min;
+  r->dilation = rc.dilation; r->z_near = rc.z_near;
+  r->limx = rc.guard * 0.5f * (float)cam->width / cam->fx;
+  r->limy = rc.guard * 0.5f * (float)cam->height / cam->fy;
+  return DAGS_OK;
+}
+
+int make_loss(const dags_loss_cfg *lc_in, Loss *l) {
+  dags_loss_cfg lc;
+  if (lc_in) lc = *lc_in;
+  else dags_default_loss_cfg(&lc);
+  if (!isfinite(lc.lambda_pho) || !isfinite(lc.lambda_depth) || !(lc.o_eps >= 0.f)) return DAGS_E_INVAL;
+  if (lc.weight_mode != 0 && lc.weight_mode != 1) return DAGS_E_INVAL;
+  l->lambda_pho = lc.lambda_pho; l->lambda_depth = lc.lambda_depth; l->o_eps = lc.o_eps;
+  l->weight_mode = lc.weight_mode; l->weight_grad = lc.weight_grad ? 1 : 0;
+  return DAGS_OK;
+}
+
+int cuda_status(cudaError_t e) { return e == cudaSuccess ? DAGS_OK : DAGS_E_CUDA; }
+
+int common_args(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *poses,
+                int32_t n_views) {
+  if (!ctx) return DAGS_E_INVAL;
+  if (n < 0 || n > ctx->ws.max_n || (n > 0 && !gauss)) return DAGS_E_INVAL;
+  if (n_views < 1 || n_views > ctx->ws.max_v || !poses) return DAGS_E_INVAL;
+  if (((uintptr_t)gauss & 15u) != 0) return DAGS_E_INVAL;
+  return check_camera(ctx, cam);
+}
+
+}  // namespace
+
+extern "C" {
+
+void dags_default_raster_cfg(dags_raster_cfg *c) {
+  if (!c) return;
+  c->tile = 16;
+  c->alpha_min = 1.0f / 255.0f;
+  c->alpha_max = 0.99f;
+  c->t_min = 1e-4f;
+  c->dilation = 0.3f;
+  c->z_near = 0.2f;
+  c->guard = 1.3f;
+}
+
+void dags_default_loss_cfg(dags_loss_cfg *c) {
+  if (!c) return;
+  c->lambda_pho = 0.9f;
+  c->lambda_depth = 0.1f;
+  c->weight_mode = 0;
+  c->weight_grad = 0;
+  c->o_eps = 1e-6f;
+}
+
+void dags_default_pose_cfg(dags_pose_cfg *c) {
+  if (!c) return;
+  for (int k = 0; k < 6; ++k) c->lr[k] = 1e-3;
+  c->beta1 = 0.9;
+  c->beta2 = 0.999;
+  c->eps = 1e-8;
+}
+
+int dags_abi_version(void) { return DAGS_ABI_VERSION; }
+
+const char *dags_status_string(int code) {
+  switch (code) {
+    case DAGS_OK: return "ok";
+    case DAGS_E_INVAL: return "invalid argument";
+    case DAGS_E_CUDA: return "CUDA runtime error";
+    case DAGS_E_CAPACITY: return "tile/Gaussian pair capacity exceeded (see dags_sync_status)";
+    case DAGS_E_TIMEOUT: return "a bounded device wait gave up";
+    case DAGS_E_NOMEM: return "workspace allocation failed";
+    case DAGS_E_ORDER: return "splat_backward does not follow its splat_forward on this context";
+    default: return "unknown status";
+  }
+}
+
+int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_t max_height,
+                int32_t max_views, int64_t max_pairs) {
+  if (!out) return DAGS_E_INVAL;
+  *out = nullptr;
+  if (max_gaussians < 0 || max_gaussians > (int64_t)0x7FFFFFFF || max_width <= 0 || max_height <= 0 ||
+      max_width > 32768 || max_height > 32768 || max_views < 1 || max_views > 64 || max_pairs < 0)
+    return DAGS_E_INVAL;
+  if (max_pairs == 0) max_pairs = 16 * max_gaussians * (int64_t)max_views;
+  if (max_pairs < 1024) max_pairs = 1024;
+  if (max_pairs > (int64_t)0xFFFFFFFE) return DAGS_E_INVAL;
+  dags_ctx *c = new (std::nothrow) dags_ctx();
+  if (!c) return DAGS_E_NOMEM;
+  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return DAGS_E_CUDA; }
+  Workspace &w = c->ws;
+  w.max_n = max_gaussians > 0 ? max_gaussians : 1;
+  w.max_w = max_width;
+  w.max_h = max_height;
+  w.max_v = max_views;
+  w.max_tiles = ((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
+  w.max_pairs = max_pairs;
+  w.bwd_prep_blocks = (int)((w.max_n + kBwdPrepBlock - 1) / kBwdPrepBlock);
+  const size_t vn = (size_t)w.max_v * (size_t)w.max_n;
+  const size_t vt = (size_t)w.max_v * (size_t)w.max_tiles;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(alloc(&w.rec2d, vn * 3));
+  A(alloc(&w.rect, vn));
+  A(alloc(&w.grad2d, vn * kGradWords));
+  A(alloc(&w.tile_count, vt));
+  A(alloc(&w.tile_start, vt + 1));
+  A(alloc(&w.tile_cursor, vt));
+  A(alloc(&w.keys, (size_t)max_pairs));
+  A(alloc(&w.keys_tmp, (size_t)max_pairs));
+  A(alloc(&w.sorted_ids, (size_t)max_pairs));
+  A(alloc(&w.big_tiles, vt));
+  A(alloc(&w.loss_partial, vt));
+  A(alloc(&w.pose_partial, (size_t)w.bwd_prep_blocks * w.max_v * 6));
+  A(alloc(&w.pose32, (size_t)w.max_v * 12));
+  A(alloc(&w.counters, (size_t)CNT_N));
+  if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(w.counters, 0, CNT_N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = configure_fwd_kernels();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? DAGS_E_NOMEM : DAGS_E_CUDA;
+    cudaGetLastError();
+    free_ws(w);
+    delete c;
+    return code;
+  }
+  *out = c;
+  return DAGS_OK;
+}
+
+void dags_destroy(dags_ctx *ctx) {
+  if (!ctx) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  free_ws(ctx->ws);
+  cudaSetDevice(cur);
+  delete ctx;
+}
+
+int dags_sync_status(dags_ctx *ctx, int64_t *required_pairs) {
+  if (!ctx) return DAGS_E_INVAL;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return DAGS_E_CUDA;
+  uint32_t cnt[CNT_N];
+  if (cudaMemcpy(cnt, ctx->ws.counters, sizeof(cnt), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DAGS_E_CUDA;
+  if (required_pairs) *required_pairs = (int64_t)((uint64_t)cnt[CNT_REQ_LO] | ((uint64_t)cnt[CNT_REQ_HI] << 32));
+  const uint32_t st = cnt[CNT_STATUS];
+  if (st) {
+    uint32_t zero = 0;
+    if (cudaMemcpy(ctx->ws.counters + CNT_STATUS, &zero, sizeof(zero), cudaMemcpyHostToDevice) != cudaSuccess)
+      return DAGS_E_CUDA;
+  }
+  if (st & kStatusCapacity) return DAGS_E_CAPACITY;
+  if (st & kStatusTimeout) return DAGS_E_TIMEOUT;
+  return DAGS_OK;
+}
+
+int splat_forward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *poses,
+                  int32_t n_views, const float *targets, const dags_raster_cfg *rcfg,
+                  const dags_loss_cfg *lcfg, float *image, int32_t *last, double *loss, void *stream) {
+  int rc = common_args(ctx, gauss, n, cam, poses, n_views);
+  if (rc) return rc;
+  if (!image || !last || (loss && !targets)) return DAGS_E_INVAL;
+  if (((uintptr_t)targets & 15u) != 0) return DAGS_E_INVAL;
+  Raster r;
+  Loss l;
+  if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  ctx->fwd_image = nullptr;
+  const Workspace &w = ctx->ws;
+  const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
+  cudaError_t e = launch_preprocess(w, g4, n, poses, n_views, r, kGradWords, s);
+  if (e == cudaSuccess) e = launch_emit(w, n, n_views, r, s);
+  if (e == cudaSuccess) e = launch_tile_sort(w, n_views, r, s);
+  if (e == cudaSuccess)
+    e = launch_render_fwd(w, n_views, n, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
+  if (e != cudaSuccess) return DAGS_E_CUDA;
+  ctx->fwd_image = image;
+  ctx->fwd_last = last;
+  ctx->fwd_gauss = gauss;
+  ctx->fwd_n = n;
+  ctx->fwd_views = n_views;
+  ctx->fwd_w = cam->width;
+  ctx->fwd_h = cam->height;
+  ctx->fwd_tiles = r.T;
+  return DAGS_OK;
+}
+
+int dags_copy_bins(dags_ctx *ctx, uint32_t *tile_start, int64_t n_start, uint32_t *ids, int64_t cap,
+                   int64_t *n_pairs) {
+  if (!ctx || !tile_start || !ctx->fwd_image || cap < 0 || (cap > 0 && !ids)) return DAGS_E_INVAL;
+  if (n_start != (int64_t)ctx->fwd_views * ctx->fwd_tiles + 1) return DAGS_E_INVAL;
+  int64_t req = 0;
+  int st = dags_sync_status(ctx, &req);
+  if (n_pairs) *n_pairs = req;
+  if (st != DAGS_OK) return st;
+  if (cudaMemcpy(tile_start, ctx->ws.tile_start, (size_t)n_start * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return DAGS_E_CUDA;
+  const int64_t m = req < cap ? req : cap;
+  if (m > 0 && cudaMemcpy(ids, ctx->ws.sorted_ids, (size_t)m * sizeof(uint32_t), cudaMemcpyDeviceToHost) !=
+                   cudaSuccess)
+    return DAGS_E_CUDA;
+  return DAGS_OK;
+}
+
+int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *poses,
+                   int32_t n_views, const float *targets, const dags_raster_cfg *rcfg,
+                   const dags_loss_cfg *lcfg, const float *image, const int32_t *last, uint32_t grad_flags,
+                   float *grad_gauss, double *grad_pose, void *stream) {
+  int rc = common_args(ctx, gauss, n, cam, poses, n_views);
+  if (rc) return rc;
+  if (!targets || !image || !last) return DAGS_E_INVAL;
+  if ((grad_flags & ~(DAGS_GRAD_GAUSS | DAGS_GRAD_POSE)) || !grad_flags) return DAGS_E_INVAL;
+  if ((grad_flags & DAGS_GRAD_GAUSS) && !grad_gauss) return DAGS_E_INVAL;
+  if ((grad_flags & DAGS_GRAD_POSE) && !grad_pose) return DAGS_E_INVAL;
+  if (((uintptr_t)targets & 15u) != 0 || ((uintptr_t)grad_gauss & 15u) != 0) return DAGS_E_INVAL;
+  if (ctx->fwd_image != image || ctx->fwd_last != last || ctx->fwd_gauss != gauss || ctx->fwd_n != n ||
+      ctx->fwd_views != n_views || ctx->fwd_w != cam->width || ctx->fwd_h != cam->height)
+    return DAGS_E_ORDER;
+  Raster r;
+  Loss l;
+  if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const bool full = (grad_flags & DAGS_GRAD_GAUSS) != 0;
+  cudaError_t e = launch_render_bwd(ctx->ws, n_views, n, r, l, reinterpret_cast<const float4 *>(targets),
+                                    image, last, full, s);
+  if (e == cudaSuccess)
+    e = launch_preprocess_bwd(ctx->ws, reinterpret_cast<const float4 *>(gauss), n, n_views, r,
+                              full ? grad_gauss : nullptr, (grad_flags & DAGS_GRAD_POSE) ? grad_pose : nullptr, s);
+  return cuda_status(e);
+}
+
+int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state, int32_t n_views,
+              const dags_pose_cfg *cfg, void *stream) {
+  if (!ctx || !poses || !grad || !adam_state || n_views < 1 || n_views > ctx->ws.max_v) return DAGS_E_INVAL;
+  dags_pose_cfg c;
+  if (cfg) c = *cfg;
+  else dags_default_pose_cfg(&c);
+  for (int k = 0; k < 6; ++k)
+    if (!isfinite(c.lr[k]) || c.lr[k] < 0) return DAGS_E_INVAL;
+  if (!(c.beta1 >= 0 && c.beta1 < 1) || !(c.beta2 >= 0 && c.beta2 < 1) || !(c.eps > 0)) return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return cuda_status(launch_pose_step(poses, grad, adam_state, n_views, c, s));
+}
+
+}  // extern "C"

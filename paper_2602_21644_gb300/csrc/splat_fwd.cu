@@ -1,0 +1,425 @@
+// Forward half of the MP-aware splatting path (sm_103a).
+//
+//   preprocess_kernel   per (view, Gaussian): camera transform, EWA 2D
+//                       covariance, conic, opacity, opacity-aware bounding
+//                       radius, tile rect; counts pairs per tile; the last
+//                       CTA scans the counts into tile offsets.
+//   emit_kernel         writes (depth bits << 32 | id) keys into per-tile
+//                       buckets (order inside a bucket is arbitrary).
+//   tile_sort_kernel    sorts each bucket in shared memory (bitonic) and
+//                       writes the depth-ordered Gaussian ids; oversized
+//                       buckets are queued for tile_sort_big_kernel, which
+//                       sorts 16k-key chunks in shared memory and merges them.
+//   render_fwd_kernel   one CTA per 16x16 tile: front-to-back alpha
+//                       compositing of colour, depth, opacity and MP with the
+//                       tile's sorted list staged through shared memory, warp
+//                       and CTA early exit on transmittance, and the static
+//                       weight and MP-weighted L1 loss of Eqs. (20)-(22) in
+//                       the epilogue; the last CTA sums the loss in FP64.
+#include "common.cuh"
+
+namespace dags {
+
+namespace {
+
+constexpr int kMaxViewsSmem = 64;  // poses staged in shared memory per CTA
+
+__device__ __forceinline__ int clampi(float x, int lo, int hi) {
+  // x may be huge or non-finite; clamp in float before converting
+  float c = fminf(fmaxf(x, (float)lo), (float)hi);
+  return c != c ? lo : (int)c;
+}
+
+// Exclusive scan of `total` uint32 counts by one CTA, in rounds of blockDim.
+// Also clears the counts and cursors for the next call. Returns the sum.
+__device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint64_t s_carry;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  if (tid == 0) s_carry = 0;
+  __syncthreads();
+  for (int base = 0; base < total; base += blockDim.x) {
+    int idx = base + tid;
+    uint32_t val = idx < total ? __ldcg(count + idx) : 0u;
+    uint32_t inc = val;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      uint32_t t = lane < nw ? warp_tot[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
+    }
+    __syncthreads();
+    uint32_t before = (wid > 0 ? warp_tot[wid - 1] : 0u) + inc - val;
+    uint64_t carry = s_carry;
+    if (idx < total) {
+      uint64_t st = carry + before;
+      start[idx] = (uint32_t)(st > 0xFFFFFFFFull ? 0xFFFFFFFFull : st);
+      count[idx] = 0u;
+      cursor[idx] = 0u;
+    }
+    __syncthreads();
+    if (tid == 0) s_carry = carry + warp_tot[nw - 1];
+    __syncthreads();
+  }
+  return s_carry;
+}
+
+__global__ void __launch_bounds__(kPrepBlock)
+preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
+                  const double *__restrict__ poses, int views, Raster r, int zero_words) {
+  __shared__ float sp[kMaxViewsSmem * 12];
+  __shared__ int s_last;
+  for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = (float)poses[k];
+  __syncthreads();
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
+
+  const int v = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float *P = sp + v * 12;
+    const size_t slot = (size_t)v * ws.max_n + i;
+    float4 g0 = __ldg(gauss + 4 * i + 0);
+    float4 g1 = __ldg(gauss + 4 * i + 1);
+    float4 g2 = __ldg(gauss + 4 * i + 2);
+    float4 g3 = __ldg(gauss + 4 * i + 3);
+    float4 *gz = reinterpret_cast<float4 *>(ws.grad2d + slot * kGradWords);
+    for (int w = 0; w < zero_words / 4; ++w) gz[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
+    uint2 rect = make_uint2(0u, 0u);
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    Proj q;
+    if (project_gaussian(g0, g1, g2, P, r, q)) {
+      // Outside |d| <= sqrt(2 lambda_max ln(o / alpha_min)) the Gaussian's
+      // alpha is below alpha_min: that radius bounds its footprint.
+      const float mid = 0.5f * (q.A + q.C);
+      const float disc = 0.25f * (q.A - q.C) * (q.A - q.C) + q.B * q.B;
+      const float lmax = mid + sqrtf(fmaxf(disc, 0.1f));
+      const float rext = sqrtf(2.f * lmax * logf(q.o / r.alpha_min));
+      const float rad = ceilf(rext);
+      const float inv_tile = 1.f / (float)kTile;
+      x0 = clampi(floorf((q.u - rad) * inv_tile), 0, r.tiles_x);
+      y0 = clampi(floorf((q.v - rad) * inv_tile), 0, r.tiles_y);
+      x1 = clampi(floorf((q.u + rad) * inv_tile) + 1.f, 0, r.tiles_x);
+      y1 = clampi(floorf((q.v + rad) * inv_tile) + 1.f, 0, r.tiles_y);
+      if (x1 > x0 && y1 > y0 && isfinite(q.u) && isfinite(q.v)) {
+        o0 = make_float4(q.u, q.v, q.z, q.o);
+        o1 = make_float4(q.ca, q.cb, q.cc, g2.w);
+        const uint32_t cw0 = __float_as_uint(g3.x), cw1 = __float_as_uint(g3.y);
+        o2 = make_float4(bf16_lo(cw0), bf16_hi(cw0), bf16_lo(cw1), 0.f);
+        rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+      } else {
+        x0 = y0 = x1 = y1 = 0;
+      }
+    }
+    ws.rec2d[slot * 3 + 0] = o0;
+    ws.rec2d[slot * 3 + 1] = o1;
+    ws.rec2d[slot * 3 + 2] = o2;
+    ws.rect[slot] = rect;
+    uint32_t *cnt = ws.tile_count + (size_t)v * r.T;
+    for (int ty = y0; ty < y1; ++ty)
+      for (int tx = x0; tx < x1; ++tx) atomicAdd(cnt + ty * r.tiles_x + tx, 1u);
+  }
+
+  // The last CTA to finish turns the per-tile counts into offsets.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
+    s_last = (t == gridDim.x * gridDim.y - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T);
+  if (threadIdx.x == 0) {
+    ws.tile_start[views * r.T] = (uint32_t)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
+    ws.counters[CNT_REQ_LO] = (uint32_t)total;
+    ws.counters[CNT_REQ_HI] = (uint32_t)(total >> 32);
+    if (total > (uint64_t)ws.max_pairs) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
+    ws.counters[CNT_BIG_TILES] = 0u;
+    ws.counters[CNT_DONE_PREP] = 0u;
+  }
+}
+
+__device__ __forceinline__ bool pairs_overflow(const Workspace &ws, int entries) {
+  uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
+  (void)entries;
+  return tot > (uint64_t)ws.max_pairs;
+}
+
+__global__ void __launch_bounds__(kPrepBlock)
+emit_kernel(Workspace ws, int64_t n, Raster r) {
+  const int v = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (pairs_overflow(ws, 0)) return;
+  const size_t slot = (size_t)v * ws.max_n + i;
+  const uint2 rc = ws.rect[slot];
+  const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
+  if (x1 <= x0 || y1 <= y0) return;
+  const float z = ws.rec2d[slot * 3].z;
+  const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)i;
+  const int base = v * r.T;
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx) {
+      const int t = base + ty * r.tiles_x + tx;
+      const uint32_t pos = atomicAdd(ws.tile_cursor + t, 1u);
+      ws.keys[ws.tile_start[t] + pos] = key;
+    }
+}
+
+// Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
+__device__ __forceinline__ void bitonic_smem(uint64_t *s, int len2) {
+  for (int k = 2; k <= len2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (len2 >> 1); t += blockDim.x) {
+        const int i = 2 * t - (t & (j - 1));
+        const int p = i + j;
+        const uint64_t a = s[i], b = s[p];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) { s[i] = b; s[p] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+__global__ void __launch_bounds__(256)
+tile_sort_kernel(Workspace ws, int entries) {
+  __shared__ uint64_t sk[kSortSmallCap];
+  const int tile = blockIdx.x;
+  if (pairs_overflow(ws, entries)) return;
+  const uint32_t s = ws.tile_start[tile], e = ws.tile_start[tile + 1];
+  const int len = (int)(e - s);
+  if (len == 0) return;
+  if (len > kSortSmallCap) {
+    if (threadIdx.x == 0) ws.big_tiles[atomicAdd(ws.counters + CNT_BIG_TILES, 1u)] = (uint32_t)tile;
+    return;
+  }
+  const int len2 = next_pow2(len);
+  for (int k = threadIdx.x; k < len2; k += blockDim.x) sk[k] = k < len ? ws.keys[s + k] : ~0ull;
+  __syncthreads();
+  bitonic_smem(sk, len2);
+  for (int k = threadIdx.x; k < len; k += blockDim.x) ws.sorted_ids[s + k] = (uint32_t)sk[k];
+}
+
+// Merge sorted runs a[0, la) and b[0, lb) into out[0, la + lb) with the CTA
+// (merge path: each thread finds its split by binary search, then merges its
+// slice sequentially). Keys are unique within a tile.
+__device__ void merge_runs(const uint64_t *a, int la, const uint64_t *b, int lb, uint64_t *out) {
+  const int m = la + lb;
+  const int per = (m + blockDim.x - 1) / blockDim.x;
+  const int k0 = min(m, (int)threadIdx.x * per);
+  const int k1 = min(m, k0 + per);
+  if (k0 < k1) {
+    int lo = max(0, k0 - lb), hi = min(k0, la);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a[mid] < b[k0 - mid - 1]) lo = mid + 1;
+      else hi = mid;
+    }
+    int ia = lo, ib = k0 - lo;
+    for (int k = k0; k < k1; ++k) {
+      const bool take_a = ib >= lb || (ia < la && a[ia] < b[ib]);
+      out[k] = take_a ? a[ia++] : b[ib++];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024)
+tile_sort_big_kernel(Workspace ws, int entries) {
+  extern __shared__ uint64_t sbig[];
+  if (pairs_overflow(ws, entries)) return;
+  const uint32_t nbig = ws.counters[CNT_BIG_TILES];
+  for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const uint32_t tile = ws.big_tiles[b];
+    const uint32_t s = ws.tile_start[tile], e = ws.tile_start[tile + 1];
+    const int len = (int)(e - s);
+    uint64_t *src = ws.keys + s, *dst = ws.keys_tmp + s;
+    for (int c0 = 0; c0 < len; c0 += kSortBigChunk) {
+      const int cl = min(kSortBigChunk, len - c0);
+      const int cl2 = next_pow2(cl);
+      for (int k = threadIdx.x; k < cl2; k += blockDim.x) sbig[k] = k < cl ? src[c0 + k] : ~0ull;
+      __syncthreads();
+      bitonic_smem(sbig, cl2);
+      for (int k = threadIdx.x; k < cl; k += blockDim.x) src[c0 + k] = sbig[k];
+      __syncthreads();
+    }
+    for (int width = kSortBigChunk; width < len; width <<= 1) {
+      for (int lo = 0; lo < len; lo += 2 * width) {
+        const int la = min(width, len - lo);
+        const int lb = max(0, min(width, len - lo - width));
+        merge_runs(src + lo, la, src + lo + la, lb, dst + lo);
+      }
+      __syncthreads();
+      uint64_t *t = src; src = dst; dst = t;
+    }
+    for (int k = threadIdx.x; k < len; k += blockDim.x) ws.sorted_ids[s + k] = (uint32_t)src[k];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kTilePix)
+render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
+                  float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
+  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
+  __shared__ float s_red[kTilePix / 32];
+  __shared__ int s_last;
+  const int tid = threadIdx.x;
+  const int v = blockIdx.z;
+  const int tile = v * r.T + blockIdx.y * r.tiles_x + blockIdx.x;
+  const int px = blockIdx.x * kTile + (tid % kTile);
+  const int py = blockIdx.y * kTile + (tid / kTile);
+  const bool inside = px < r.W && py < r.H;
+  const bool ovf = pairs_overflow(ws, views * r.T);
+  const uint32_t s = ovf ? 0u : ws.tile_start[tile];
+  const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
+  const size_t vbase = (size_t)v * ws.max_n;
+
+  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, oo = 0.f, rm = 0.f;
+  int lastk = 0;
+  bool done = !inside;
+  const float fpx = (float)px, fpy = (float)py;
+  for (uint32_t base = s; base < e; base += kTilePix) {
+    if (__syncthreads_count(!done) == 0) break;
+    const uint32_t k = base + tid;
+    if (k < e) {
+      const size_t slot = vbase + ws.sorted_ids[k];
+      s_a[tid] = ws.rec2d[slot * 3 + 0];
+      s_b[tid] = ws.rec2d[slot * 3 + 1];
+      s_c[tid] = ws.rec2d[slot * 3 + 2];
+    }
+    __syncthreads();
+    const int cnt = (int)min((uint32_t)kTilePix, e - base);
+    if (!done) {
+      for (int j = 0; j < cnt; ++j) {
+        const float4 a = s_a[j], b = s_b[j];
+        const float dx = a.x - fpx, dy = a.y - fpy;
+        const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
+        const float ag = a.w * __expf(power);
+        if (ag < r.alpha_min) continue;
+        const float alpha = fminf(r.alpha_max, ag);
+        const float tt = T * (1.f - alpha);
+        if (tt < r.t_min) { done = true; break; }
+        const float w = alpha * T;
+        const float4 c = s_c[j];
+        cr += c.x * w; cg += c.y * w; cb += c.z * w;
+        dd += a.z * w; oo += w; rm += b.w * w;
+        T = tt;
+        lastk = (int)(base - s) + j + 1;
+      }
+    }
+  }
+
+  float lpx = 0.f;
+  if (inside) {
+    const size_t P = (size_t)r.W * r.H;
+    const size_t pix = (size_t)py * r.W + px;
+    float wgt = 0.f;
+    if (targets) {
+      if (l.weight_mode == 0) wgt = oo > l.o_eps ? (oo - rm) / oo : 0.f;
+      else wgt = oo - rm;
+      const float4 tg = targets[(size_t)v * P + pix];
+      const float l1 = fabsf(cr - tg.x) + fabsf(cg - tg.y) + fabsf(cb - tg.z);
+      const float ld = tg.w > 0.f ? fabsf(dd - tg.w) : 0.f;
+      lpx = wgt * (l.lambda_pho * l1 + l.lambda_depth * ld);
+    }
+    float *img = image + (size_t)v * DAGS_IMG_CHANNELS * P + pix;
+    img[0 * P] = cr; img[1 * P] = cg; img[2 * P] = cb; img[3 * P] = dd;
+    img[4 * P] = oo; img[5 * P] = rm; img[6 * P] = T; img[7 * P] = wgt;
+    last[(size_t)v * P + pix] = lastk;
+  }
+  if (!loss) return;
+  lpx = warp_sum(lpx);
+  if ((tid & 31) == 0) s_red[tid >> 5] = lpx;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kTilePix / 32; ++w) t += s_red[w];
+    ws.loss_partial[tile] = t;
+    __threadfence();
+    unsigned int done_ctas = atomicAdd(ws.counters + CNT_DONE_RENDER, 1u);
+    s_last = (done_ctas == gridDim.x * gridDim.y * gridDim.z - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // Deterministic FP64 sum of the per-tile partials: fixed strided
+  // assignment, then a fixed tree.
+  __shared__ double s_d[kTilePix];
+  const int np = views * r.T;
+  double acc = 0.0;
+  for (int k = tid; k < np; k += kTilePix) acc += (double)__ldcg(ws.loss_partial + k);
+  s_d[tid] = acc;
+  __syncthreads();
+  for (int o = kTilePix / 2; o > 0; o >>= 1) {
+    if (tid < o) s_d[tid] += s_d[tid + o];
+    __syncthreads();
+  }
+  if (tid == 0) {
+    *loss = ovf ? 0.0 : s_d[0];
+    ws.counters[CNT_DONE_RENDER] = 0u;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t n, const double *poses,
+                              int views, const Raster &r, int zero_grad_words, cudaStream_t s) {
+  if (views > kMaxViewsSmem) return cudaErrorInvalidValue;
+  const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
+  dim3 grid(gx > 0 ? gx : 1u, (unsigned)views);
+  preprocess_kernel<<<grid, kPrepBlock, 0, s>>>(ws, gauss, n, poses, views, r, zero_grad_words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  dim3 grid((unsigned)((n + kPrepBlock - 1) / kPrepBlock), (unsigned)views);
+  emit_kernel<<<grid, kPrepBlock, 0, s>>>(ws, n, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_sort(const Workspace &ws, int views, const Raster &r, cudaStream_t s) {
+  const int entries = views * r.T;
+  tile_sort_kernel<<<entries, 256, 0, s>>>(ws, entries);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int smem = kSortBigChunk * (int)sizeof(uint64_t);
+  tile_sort_big_kernel<<<32, 1024, smem, s>>>(ws, entries);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_fwd_kernels() {
+  return cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              kSortBigChunk * (int)sizeof(uint64_t));
+}
+
+cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
+                              const float4 *targets, float *image, int32_t *last, double *loss,
+                              cudaStream_t s) {
+  (void)n;
+  dim3 grid((unsigned)r.tiles_x, (unsigned)r.tiles_y, (unsigned)views);
+  render_fwd_kernel<<<grid, kTilePix, 0, s>>>(ws, views, r, l, targets, image, last, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace dags

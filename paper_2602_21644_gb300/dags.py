@@ -1,0 +1,258 @@
+"""Thin ctypes binding of libdags.so (C ABI in include/dags.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. Tensors are torch CUDA tensors; their data pointers and torch's
+current CUDA stream are handed to the C entry points. If the library is
+missing this module raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdags.so")
+
+IMG_CHANNELS = 8
+GRAD_WORDS = 16
+RECORD_WORDS = 16
+GRAD_GAUSS = 1
+GRAD_POSE = 2
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "pair capacity exceeded",
+          -4: "device wait timed out", -5: "workspace allocation failed",
+          -6: "backward does not follow its forward"}
+
+
+class DagsError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({code})")
+        self.code = code
+
+
+class CCamera(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class CRasterCfg(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("alpha_min", ctypes.c_float), ("alpha_max", ctypes.c_float),
+                ("t_min", ctypes.c_float), ("dilation", ctypes.c_float), ("z_near", ctypes.c_float),
+                ("guard", ctypes.c_float)]
+
+
+class CLossCfg(ctypes.Structure):
+    _fields_ = [("lambda_pho", ctypes.c_float), ("lambda_depth", ctypes.c_float), ("weight_mode", ctypes.c_int32),
+                ("weight_grad", ctypes.c_int32), ("o_eps", ctypes.c_float)]
+
+
+class CPoseCfg(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double * 6), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
+           "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
+           "splat_backward", "pose_step", "dags_copy_bins"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdags.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdags.so not found at {path}; build it with "
+                           "`python -m paper_2602_21644_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, U32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    lib.dags_create.argtypes = [ctypes.POINTER(P), I64, I32, I32, I32, I64]
+    lib.dags_create.restype = ctypes.c_int
+    lib.dags_destroy.argtypes = [P]
+    lib.dags_destroy.restype = None
+    lib.dags_status_string.argtypes = [ctypes.c_int]
+    lib.dags_status_string.restype = ctypes.c_char_p
+    lib.dags_abi_version.argtypes = []
+    lib.dags_abi_version.restype = ctypes.c_int
+    lib.dags_sync_status.argtypes = [P, ctypes.POINTER(I64)]
+    lib.dags_sync_status.restype = ctypes.c_int
+    lib.dags_default_raster_cfg.argtypes = [ctypes.POINTER(CRasterCfg)]
+    lib.dags_default_loss_cfg.argtypes = [ctypes.POINTER(CLossCfg)]
+    lib.dags_default_pose_cfg.argtypes = [ctypes.POINTER(CPoseCfg)]
+    lib.splat_forward.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, I32, P, ctypes.POINTER(CRasterCfg),
+                                  ctypes.POINTER(CLossCfg), P, P, P, P]
+    lib.splat_forward.restype = ctypes.c_int
+    lib.splat_backward.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, I32, P, ctypes.POINTER(CRasterCfg),
+                                   ctypes.POINTER(CLossCfg), P, P, U32, P, P, P]
+    lib.splat_backward.restype = ctypes.c_int
+    lib.pose_step.argtypes = [P, P, P, P, I32, ctypes.POINTER(CPoseCfg), P]
+    lib.pose_step.restype = ctypes.c_int
+    lib.dags_copy_bins.argtypes = [P, P, I64, P, I64, ctypes.POINTER(I64)]
+    lib.dags_copy_bins.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise DagsError(code, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass
+class Camera:
+    fx: float
+    fy: float
+    cx: float
+    cy: float
+    width: int
+    height: int
+
+    def c(self) -> CCamera:
+        return CCamera(self.fx, self.fy, self.cx, self.cy, self.width, self.height)
+
+
+def default_raster_cfg() -> CRasterCfg:
+    c = CRasterCfg()
+    load().dags_default_raster_cfg(ctypes.byref(c))
+    return c
+
+
+def default_loss_cfg(**kw) -> CLossCfg:
+    c = CLossCfg()
+    load().dags_default_loss_cfg(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_pose_cfg(lr=None, **kw) -> CPoseCfg:
+    c = CPoseCfg()
+    load().dags_default_pose_cfg(ctypes.byref(c))
+    if lr is not None:
+        for k in range(6):
+            c.lr[k] = float(lr[k] if hasattr(lr, "__len__") else lr)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def _need(t: torch.Tensor, dtype, name):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+class Context:
+    """Owns a dags_ctx (device workspace) on the current CUDA device."""
+
+    def __init__(self, max_gaussians: int, max_width: int, max_height: int, max_views: int = 1,
+                 max_pairs: int = 0):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.dags_create(ctypes.byref(h), int(max_gaussians), int(max_width), int(max_height),
+                                    int(max_views), int(max_pairs)), "dags_create")
+        self.h = h
+        self.max = (max_gaussians, max_width, max_height, max_views)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.dags_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync_status(self):
+        """(status_code, required_pairs); synchronises the last stream."""
+        req = ctypes.c_int64(0)
+        code = self.lib.dags_sync_status(self.h, ctypes.byref(req))
+        return code, req.value
+
+    def check(self):
+        code, req = self.sync_status()
+        if code != 0:
+            raise DagsError(code, f"device status (required pairs {req})")
+
+    def copy_bins(self, views: int, cam: Camera):
+        """(tile_start [views*T+1] uint32, ids [pairs] uint32) of the last forward."""
+        import numpy as np
+        T = ((cam.width + 15) // 16) * ((cam.height + 15) // 16)
+        start = np.zeros(views * T + 1, np.uint32)
+        npairs = ctypes.c_int64(0)
+        _check(self.lib.dags_copy_bins(self.h, start.ctypes.data_as(ctypes.c_void_p), start.size, None, 0,
+                                       ctypes.byref(npairs)), "dags_copy_bins")
+        ids = np.zeros(max(1, npairs.value), np.uint32)
+        _check(self.lib.dags_copy_bins(self.h, start.ctypes.data_as(ctypes.c_void_p), start.size,
+                                       ids.ctypes.data_as(ctypes.c_void_p), ids.size, ctypes.byref(npairs)),
+               "dags_copy_bins")
+        return start, ids[:npairs.value]
+
+    # ------------------------------------------------------------ splatting
+
+    def forward(self, gauss, cam: Camera, poses, targets=None, rcfg=None, lcfg=None, image=None, last=None,
+                loss=None, want_loss=True):
+        """Returns (image [V,8,H,W] f32, last [V,H,W] i32, loss [1] f64 or None)."""
+        _need(gauss, torch.float32, "gauss")
+        _need(poses, torch.float64, "poses")
+        n = gauss.shape[0]
+        V = poses.shape[0]
+        H, W = cam.height, cam.width
+        dev = gauss.device
+        if targets is not None:
+            _need(targets, torch.float32, "targets")
+        if image is None:
+            image = torch.empty((V, IMG_CHANNELS, H, W), dtype=torch.float32, device=dev)
+        if last is None:
+            last = torch.empty((V, H, W), dtype=torch.int32, device=dev)
+        if loss is None and targets is not None and want_loss:
+            loss = torch.empty(1, dtype=torch.float64, device=dev)
+        c = cam.c()
+        rc = rcfg if rcfg is not None else default_raster_cfg()
+        lc = lcfg if lcfg is not None else default_loss_cfg()
+        _check(self.lib.splat_forward(self.h, _ptr(gauss), n, ctypes.byref(c), _ptr(poses), V, _ptr(targets),
+                                      ctypes.byref(rc), ctypes.byref(lc), _ptr(image), _ptr(last),
+                                      _ptr(loss if targets is not None else None), _stream()), "splat_forward")
+        return image, last, loss
+
+    def backward(self, gauss, cam: Camera, poses, targets, image, last, flags=GRAD_POSE, rcfg=None, lcfg=None,
+                 grad_gauss=None, grad_pose=None):
+        """Returns (grad_gauss [n,16] f32 or None, grad_pose [V,6] f64 or None)."""
+        n = gauss.shape[0]
+        V = poses.shape[0]
+        dev = gauss.device
+        if flags & GRAD_GAUSS and grad_gauss is None:
+            grad_gauss = torch.empty((n, GRAD_WORDS), dtype=torch.float32, device=dev)
+        if flags & GRAD_POSE and grad_pose is None:
+            grad_pose = torch.empty((V, 6), dtype=torch.float64, device=dev)
+        c = cam.c()
+        rc = rcfg if rcfg is not None else default_raster_cfg()
+        lc = lcfg if lcfg is not None else default_loss_cfg()
+        _check(self.lib.splat_backward(self.h, _ptr(gauss), n, ctypes.byref(c), _ptr(poses), V, _ptr(targets),
+                                       ctypes.byref(rc), ctypes.byref(lc), _ptr(image), _ptr(last), int(flags),
+                                       _ptr(grad_gauss if flags & GRAD_GAUSS else None),
+                                       _ptr(grad_pose if flags & GRAD_POSE else None), _stream()), "splat_backward")
+        return (grad_gauss if flags & GRAD_GAUSS else None), (grad_pose if flags & GRAD_POSE else None)
+
+    def pose_step(self, poses, grad_pose, adam_state, cfg=None):
+        _need(poses, torch.float64, "poses")
+        _need(grad_pose, torch.float64, "grad_pose")
+        _need(adam_state, torch.float64, "adam_state")
+        c = cfg if cfg is not None else default_pose_cfg()
+        _check(self.lib.pose_step(self.h, _ptr(poses), _ptr(grad_pose), _ptr(adam_state), poses.shape[0],
+                                  ctypes.byref(c), _stream()), "pose_step")
