@@ -29,10 +29,11 @@
  *
  * The depth order is decided on an FP32 depth key that both this oracle and
  * the CUDA path evaluate bit-identically (see depth_key). Other decisions
- * that floating point takes (skip, clamp, stop, tile bounds, residual signs)
- * are flagged when the FP64 quantity lies within a relative 1e-5 of its
- * threshold, so a test can tell an FP32-vs-FP64 rounding disagreement from
- * a bug.
+ * that floating point takes are flagged when the FP64 quantity lies within
+ * the error an FP32 evaluation can have of its threshold: alpha skip, clamp
+ * and the transmittance stop by a propagated bound (exponent_margin), tile
+ * bounds, radius, residual signs and the near plane by a relative 1e-5. A
+ * test can then tell an FP32-vs-FP64 rounding disagreement from a bug.
  */
 #include <math.h>
 #include <stdint.h>
@@ -131,6 +132,7 @@ typedef struct {
   double A, B, C;       /* 2D covariance after dilation              */
   double a, b, c;       /* conic = inverse 2D covariance             */
   double o, u, v, lmax, rext;
+  double cond;          /* condition number of the dilated 2D covariance   */
   float zkey;           /* FP32 depth key that decides the depth order      */
   int r, x0, y0, x1, y1;
 } proj_t;
@@ -214,6 +216,10 @@ static void project_one(const double *g, const double *cam, const double *pose,
   P->a = P->C / det;
   P->b = -P->B / det;
   P->c = P->A / det;
+  {
+    double m2 = 0.5 * (P->A + P->C), hd = sqrt(0.25 * (P->A - P->C) * (P->A - P->C) + P->B * P->B);
+    P->cond = (m2 + hd) / fmax(m2 - hd, 1e-300);
+  }
 
   P->o = 1.0 / (1.0 + exp(-g[G_LOGIT]));
   if (near_rel(P->o, rc[RC_ALPHA_MIN])) P->flags |= FL_OPAC;
@@ -258,6 +264,17 @@ void oracle_project(int64_t n, const double *G, const double *cam, const double 
     o[PJ_R] = P.r; o[PJ_X0] = P.x0; o[PJ_Y0] = P.y0; o[PJ_X1] = P.x1; o[PJ_Y1] = P.y1;
     o[PJ_FLAG] = P.flags; o[PJ_PX] = P.p[0]; o[PJ_PY] = P.p[1]; o[PJ_ZKEY] = (double)P.zkey;
   }
+}
+
+/* Bound on the error of an FP32 evaluation of the exponent ln(o G) at pixel
+ * offset (dx, dy): the projected centre carries a few ulps of its own
+ * magnitude (2^-22 |u|), the conic a relative error growing with the 2D
+ * covariance's condition number. Decisions of alpha against a threshold
+ * closer than this are flagged. */
+static double exponent_margin(const proj_t *p, double dx, double dy, double power) {
+  double gx = fabs(p->a * dx + p->b * dy), gy = fabs(p->b * dx + p->c * dy);
+  double ecoord = ldexp(1.0, -22) * fmax(fmax(fabs(p->u), fabs(p->v)), 1.0);
+  return (gx + gy) * ecoord + fabs(power) * (1e-6 + 4e-7 * p->cond) + 2e-6;
 }
 
 /* ---- depth order: (FP32 depth key, id) ---- */
@@ -408,6 +425,7 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
     for (int i = 0; i < W; i++) {
       int c = (j / cs.cell) * cs.cw + (i / cs.cell);
       double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0};
+      double eT = 0.0; /* bound on the relative FP32 error of T */
       int flags = 0;
       int64_t nl = 0, last = -1;
       for (int64_t q = cs.start[c]; q < cs.start[c + 1]; q++) {
@@ -417,14 +435,18 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
         double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
         double Gv = exp(power);
         double ag = p->o * Gv;
-        if (near_rel(ag, amin)) flags |= FL_ALPHA;
-        if (near_rel(ag, amax)) flags |= FL_AMAX;
+        double em = exponent_margin(p, dx, dy, power);
+        double lag = power + log(p->o);
+        if (fabs(lag - log(amin)) <= em) flags |= FL_ALPHA;
+        if (fabs(lag - log(amax)) <= em) flags |= FL_AMAX;
         if (ag < amin) continue;
         int clamped = ag > amax;
         double alpha = clamped ? amax : ag;
         double testT = T * (1.0 - alpha);
-        if (near_rel(testT, tmin)) flags |= FL_TSTOP;
+        double eTk = eT + (clamped ? 0.0 : alpha / (1.0 - alpha) * em) + 1e-6;
+        if (fabs(log(testT) - log(tmin)) <= eTk) flags |= FL_TSTOP;
         if (testT < tmin) break;
+        eT = eTk;
         const double *g = G + id * G_STRIDE;
         double wgt = alpha * T;
         acc[0] += g[G_CR] * wgt;
@@ -663,21 +685,27 @@ int oracle_render_pixel(int64_t n, const double *G, const double *cam, const dou
     if (P[k].vis) { zk[nv].z = P[k].zkey; zk[nv].id = k; nv++; }
   }
   qsort(zk, (size_t)nv, sizeof(zkey_t), cmp_zkey);
-  double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0};
+  double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0}, eT = 0.0;
   int flags = 0, nl = 0;
   int64_t last = -1;
   for (int64_t q = 0; q < nv; q++) {
     const proj_t *p = &P[zk[q].id];
     const double *g = G + zk[q].id * G_STRIDE;
     double dx = p->u - i, dy = p->v - j;
-    double ag = p->o * exp(-0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy);
-    if (near_rel(ag, rc[RC_ALPHA_MIN])) flags |= FL_ALPHA;
-    if (near_rel(ag, rc[RC_ALPHA_MAX])) flags |= FL_AMAX;
+    double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
+    double ag = p->o * exp(power);
+    double em = exponent_margin(p, dx, dy, power);
+    double lag = power + log(p->o);
+    if (fabs(lag - log(rc[RC_ALPHA_MIN])) <= em) flags |= FL_ALPHA;
+    if (fabs(lag - log(rc[RC_ALPHA_MAX])) <= em) flags |= FL_AMAX;
     if (ag < rc[RC_ALPHA_MIN]) continue;
-    double alpha = ag > rc[RC_ALPHA_MAX] ? rc[RC_ALPHA_MAX] : ag;
+    int clamped = ag > rc[RC_ALPHA_MAX];
+    double alpha = clamped ? rc[RC_ALPHA_MAX] : ag;
     double testT = T * (1.0 - alpha);
-    if (near_rel(testT, rc[RC_T_MIN])) flags |= FL_TSTOP;
+    double eTk = eT + (clamped ? 0.0 : alpha / (1.0 - alpha) * em) + 1e-6;
+    if (fabs(log(testT) - log(rc[RC_T_MIN])) <= eTk) flags |= FL_TSTOP;
     if (testT < rc[RC_T_MIN]) break;
+    eT = eTk;
     double wgt = alpha * T;
     acc[0] += g[G_CR] * wgt; acc[1] += g[G_CG] * wgt; acc[2] += g[G_CB] * wgt;
     acc[3] += p->p[2] * wgt; acc[4] += wgt; acc[5] += g[G_MP] * wgt;

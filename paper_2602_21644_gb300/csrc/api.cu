@@ -279,7 +279,7 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   if (rc) return rc;
   if (!targets || !image || !last) return DAGS_E_INVAL;
   if ((grad_flags & ~(DAGS_GRAD_GAUSS | DAGS_GRAD_POSE)) || !grad_flags) return DAGS_E_INVAL;
-  if ((grad_flags & DAGS_GRAD_GAUSS) && !grad_gauss) return DAGS_E_INVAL;
+  if ((grad_flags & DAGS_GRAD_GAUSS) && !grad_gauss && n > 0) return DAGS_E_INVAL;
   if ((grad_flags & DAGS_GRAD_POSE) && !grad_pose) return DAGS_E_INVAL;
   if (((uintptr_t)targets & 15u) != 0 || ((uintptr_t)grad_gauss & 15u) != 0) return DAGS_E_INVAL;
   if (ctx->fwd_image != image || ctx->fwd_last != last || ctx->fwd_gauss != gauss || ctx->fwd_n != n ||

@@ -42,7 +42,7 @@ struct Workspace {
   int64_t max_pairs = 0;
   int bwd_prep_blocks = 0;
   float4 *rec2d = nullptr;        // [V][N][3]: {u, v, z, o}, {a, b, c, M}, {r, g, b, -}
-  uint2 *rect = nullptr;          // [V][N]: x0 | y0 << 16, x1 | y1 << 16 (tiles)
+  uint2 *rect = nullptr;          // [V][N]: {x0 | x1 << 16, y0 | y1 << 16}, tiles [x0, x1) x [y0, y1)
   float *grad2d = nullptr;        // [V][N][kGradWords]
   uint32_t *tile_count = nullptr; // [V * T]
   uint32_t *tile_start = nullptr; // [V * T + 1]

@@ -118,7 +118,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
         o1 = make_float4(q.ca, q.cb, q.cc, g2.w);
         const uint32_t cw0 = __float_as_uint(g3.x), cw1 = __float_as_uint(g3.y);
         o2 = make_float4(bf16_lo(cw0), bf16_hi(cw0), bf16_lo(cw1), 0.f);
-        rect = make_uint2((uint32_t)x0 | ((uint32_t)y0 << 16), (uint32_t)x1 | ((uint32_t)y1 << 16));
+        rect = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
       } else {
         x0 = y0 = x1 = y1 = 0;
       }
@@ -176,7 +176,8 @@ emit_kernel(Workspace ws, int64_t n, Raster r) {
     for (int tx = x0; tx < x1; ++tx) {
       const int t = base + ty * r.tiles_x + tx;
       const uint32_t pos = atomicAdd(ws.tile_cursor + t, 1u);
-      ws.keys[ws.tile_start[t] + pos] = key;
+      const uint32_t dst = ws.tile_start[t] + pos;
+      if (dst < ws.tile_start[t + 1]) ws.keys[dst] = key;
     }
 }
 

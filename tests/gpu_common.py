@@ -37,9 +37,24 @@ def oracle_views(sc, grads=True, lc=None):
     return G, cam, outs
 
 
+# A pixel whose decision is within FP32 error of a threshold may include or
+# drop one near-threshold contribution (alpha ~ 1/255, or the tail after
+# T ~ 1e-4): its values must still lie within that much of the oracle's.
+FLAGGED_ABS = 0.01
+
+
 def compare_image(img, ref_pix, flags, report=None, label=""):
     """img: (P, 8) GPU rows; ref_pix: (P, 10) oracle rows."""
     ok = (flags & oracle.PIXEL_DECISION_FLAGS) == 0
+    if (~ok).any():
+        fl = ~ok
+        for c, rc in zip([0, 1, 2, 4, 5, 6], [0, 1, 2, 4, 5, 6]):
+            d = np.abs(img[fl, c] - ref_pix[fl, rc]).max()
+            assert d <= FLAGGED_ABS, f"{label}: flagged pixel channel {c} off by {d:.3e}"
+        dz = np.abs(img[fl, 3] - ref_pix[fl, 3]) / np.maximum(1.0, np.abs(ref_pix[fl, 3]))
+        assert dz.max() <= FLAGGED_ABS, f"{label}: flagged pixel depth off by {dz.max():.3e}"
+        if report is not None:
+            report.append(f"{label}: {int(fl.sum())} flagged pixels within the validity envelope")
     cols = [0, 1, 2, 3, 4, 5, 6, 7]
     refc = [0, 1, 2, 3, 4, 5, 6, 9]
     worst = {}
