@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of the MP-aware splatting hot path on GB300.
+
+Metric: splat fwd+bwd iterations/s at 300k Gaussians, 640x480 (the tracking
+workload: one step = one tracking frame = `--iters` (100) pose-only
+forward + backward + FP64 pose-step iterations through the C ABI, plus the
+per-frame MP update when the library has it), and the fraction of the HBM
+roofline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0). With N > 1 (torchrun) every rank runs an
+independent replica of the workload (the path does not shard across GPUs);
+value = iterations of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "splat fwd+bwd iters/s (300k Gaussians, 640×480) and % of GB300 HBM roofline"
+UNIT = "iters/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--iters", type=int, default=100, help="fwd+bwd iterations per tracking frame")
+    ap.add_argument("--gaussians", type=int, default=300_000)
+    ap.add_argument("--width", type=int, default=640)
+    ap.add_argument("--height", type=int, default=480)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle arm
+
+def oracle_baseline(args, budget_s):
+    """The FP64 oracle, as it stands, on the host cores: full-image fwd+bwd
+    (pose gradient) iterations of the same frame, as many as fit the budget."""
+    import oracle
+    from paper_2602_21644_gb300 import synth
+    sc = synth.tracking_scene(args.gaussians, frame=10, width=args.width, height=args.height)
+    G = oracle.params_from_records(sc.records)
+    cam = oracle.camera_vec(*sc.camera.as_tuple())
+    oracle.render(G, cam, sc.poses[0], targets=sc.targets[0], grads=True)     # build + page in
+    t0 = time.perf_counter()
+    it = 0
+    while True:
+        oracle.render(G, cam, sc.poses[0], targets=sc.targets[0], grads=True)
+        it += 1
+        if time.perf_counter() - t0 >= budget_s and it >= 2:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{it} full-image fwd+bwd iterations (pose gradient) of the 300k-Gaussian 640x480 frame, "
+                      f"single-threaded FP64 C, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = oracle_baseline(args, max(5.0, args.cpu_seconds))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args), "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args):
+    return {"workload": f"tracking frame of the synthetic room: {args.gaussians} Gaussians, "
+                        f"{args.width}x{args.height} RGB-D, {args.iters} pose-only fwd+bwd iterations "
+                        f"with FP64 pose steps per step",
+            "gaussians": args.gaussians, "width": args.width, "height": args.height,
+            "iters_per_step": args.iters,
+            "l2": "flushed between steps by a 256 MiB write; inside a step the iterations re-read the "
+                  "L2-resident map as the tracking loop does",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------ our arm
+
+def algorithmic_bytes(n, nv, K, P):
+    """Compulsory bytes per kernel launch (pose-only mode): each stage reads
+    its inputs and writes its outputs once."""
+    return {"preprocess": 64 * n + 48 * nv,
+            "emit": 12 * K,
+            "tile_sort": 24 * K,
+            "render_fwd": 52 * K + 16 * P + 32 * P,
+            "render_bwd": 52 * K + 48 * P + 24 * nv,
+            "preprocess_bwd": 64 * nv + 24 * nv,
+            "pose_step": 6 * 8 + 13 * 8 * 2 + 12 * 8 * 2}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2602_21644_gb300 import dags, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    sc = synth.tracking_scene(args.gaussians, frame=10, width=args.width, height=args.height)
+    cam = dags.Camera(*sc.camera.as_tuple())
+    n = sc.records.shape[0]
+    P = cam.width * cam.height
+    gauss = torch.from_numpy(sc.records).to(dev)
+    pose0 = torch.from_numpy(np.ascontiguousarray(sc.poses)).to(dev)
+    targets = torch.from_numpy(np.ascontiguousarray(sc.targets)).to(dev)
+    poses = pose0.clone()
+    state = torch.zeros((1, 13), dtype=torch.float64, device=dev)
+    image = torch.empty((1, dags.IMG_CHANNELS, cam.height, cam.width), dtype=torch.float32, device=dev)
+    last = torch.empty((1, cam.height, cam.width), dtype=torch.int32, device=dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    gpose = torch.empty((1, 6), dtype=torch.float64, device=dev)
+    ctx = dags.Context(n, cam.width, cam.height, 1)
+    pcfg = dags.default_pose_cfg(lr=[1e-3, 1e-3, 1e-3, 5e-4, 5e-4, 5e-4])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def iteration():
+        ctx.forward(gauss, cam, poses, targets, image=image, last=last, loss=loss)
+        ctx.backward(gauss, cam, poses, targets, image, last, dags.GRAD_POSE, grad_pose=gpose)
+        ctx.pose_step(poses, gpose, state, pcfg)
+
+    def frame():
+        poses.copy_(pose0)
+        state.zero_()
+        for _ in range(args.iters):
+            iteration()
+
+    # warm-up (also checks the device status once)
+    for _ in range(max(1, args.warmup)):
+        frame()
+    torch.cuda.synchronize()
+    ctx.check()
+    start_bins, ids = ctx.copy_bins(1, cam)
+    K = int(len(ids))
+    nv = int(len(np.unique(ids)))
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+
+    def timed(steps, fn, timing=False):
+        ctx.timing(timing)
+        tot = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        ctx.timing(False)
+        return tot
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ctx.timing_read()
+    t_ms = timed(args.steps, frame, timing=True)
+    kt = ctx.timing_read()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        dist.barrier()
+    total_iters = args.iters * args.steps * world
+    value = total_iters / (t_ms / 1e3)
+
+    # same steps without the per-kernel events, for the instrumentation overhead
+    t_plain = timed(args.steps, frame, timing=False)
+
+    # e2e: public API with host buffers; every step copies the frame (RGB-D
+    # target) and the starting pose from pinned host memory and reads back the
+    # refined pose and the loss
+    tg_host = torch.from_numpy(np.ascontiguousarray(sc.targets)).pin_memory()
+    pose_host = torch.from_numpy(np.ascontiguousarray(sc.poses)).pin_memory()
+    pose_out = torch.empty_like(pose_host).pin_memory()
+    loss_out = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def frame_e2e():
+        targets.copy_(tg_host, non_blocking=True)
+        poses.copy_(pose_host, non_blocking=True)
+        state.zero_()
+        for _ in range(args.iters):
+            iteration()
+        pose_out.copy_(poses, non_blocking=True)
+        loss_out.copy_(loss, non_blocking=True)
+
+    t_e2e = timed(args.steps, frame_e2e)
+    if world > 1:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    h2d = tg_host.numel() * 4 + pose_host.numel() * 8
+    d2h = pose_out.numel() * 8 + 8
+
+    peaks, src = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    ab = algorithmic_bytes(n, nv, K, P)
+    kernels = {}
+    for name, (ms, cnt) in kt.items():
+        if cnt:
+            avg_us = 1e3 * ms / cnt
+            kernels[name] = {"launches": cnt, "avg_us": round(avg_us, 3), "share": round(ms / max(t_ms, 1e-9), 4)}
+            if name in ab:
+                kernels[name]["alg_bytes"] = ab[name]
+                kernels[name]["hbm_frac"] = round(ab[name] / (avg_us * 1e-6) / 1e9 / hbm, 4)
+    dom = max(kernels, key=lambda k: kt[k][0]) if kernels else None
+    roof = None
+    if dom:
+        avg_s = kernels[dom]["avg_us"] * 1e-6
+        ach = ab[dom] / avg_s / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs (copy)",
+                "alg_bytes_per_launch": ab[dom]}
+    iter_bytes = sum(ab.values())
+    iter_us = 1e3 * t_ms / (args.iters * args.steps)
+    gpu_launches = sum(c for _, (_, c) in kt.items()) + kt["tile_sort"][1]   # tile sort = 2 kernels
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args),
+            "iteration_hbm_roofline": {"alg_bytes": iter_bytes, "us_per_iter": round(iter_us, 3),
+                                       "frac": round(iter_bytes / (iter_us * 1e-6) / 1e9 / hbm, 4),
+                                       "peak_gbs": hbm, "pairs_K": K, "visible_Nv": nv, "pixels_P": P},
+            "roofline": roof, "kernels": kernels, "gpu_launches": gpu_launches,
+            "timing_overhead": {"ms_per_step_without_kernel_events": round(t_plain / args.steps, 4)},
+            "e2e": {"value": round(args.iters * args.steps * world / (t_e2e / 1e3), 2), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(args, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

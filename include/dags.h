@@ -30,7 +30,8 @@
  *     view-independent RGB stored in BF16.)
  *   Pose: 12 doubles, row-major 3x4 [R | t], world -> camera (T_CW).
  *   Targets: per view H*W float4 (r, g, b, depth) in row-major pixel order;
- *     depth <= 0 marks a pixel without valid depth.
+ *     depth <= 0 marks a pixel without valid depth (no depth term), r < 0 a
+ *     pixel without valid colour (left out of the loss altogether).
  *   Image (forward output): per view DAGS_IMG_CHANNELS planes of H*W float:
  *     0-2 colour C, 3 depth D, 4 opacity O = 1 - T_final, 5 rendered MP
  *     R_MP = sum_k omega_k M_k, 6 final transmittance, 7 static weight w(u)
@@ -186,6 +187,29 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
  * Sec. V-A(c) (pose refinement) and Eq. (27). */
 int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state,
               int32_t n_views, const dags_pose_cfg *cfg, void *stream);
+
+/* Per-kernel device timing (tracing). When enabled, every kernel the
+ * library launches on a stream that is not being captured into a CUDA graph
+ * is bracketed by a pair of CUDA events on that stream. dags_timing_read
+ * waits for them, writes the accumulated milliseconds and launch counts per
+ * kernel id (DAGS_K_*) into ms[count] and launches[count], and resets them.
+ * Disabling collects and keeps the pending totals. Not for use from two
+ * host threads at once. */
+enum {
+  DAGS_K_PREPROCESS = 0,   /* projection + tile counts + offsets           */
+  DAGS_K_EMIT,             /* (depth, id) keys into per-tile buckets       */
+  DAGS_K_TILE_SORT,        /* per-tile depth sort (both sort kernels)      */
+  DAGS_K_RENDER_FWD,       /* forward compositing + loss                   */
+  DAGS_K_RENDER_BWD,       /* adjoint compositing                          */
+  DAGS_K_PREPROCESS_BWD,   /* adjoint projection + pose reduction          */
+  DAGS_K_POSE_STEP,        /* FP64 pose step                               */
+  DAGS_K_MP_PIXEL,         /* MP update: per-pixel observation             */
+  DAGS_K_MP_GAUSS,         /* MP update: per-Gaussian update and medians   */
+  DAGS_K_MPNET,            /* learned MP network                           */
+  DAGS_KERNEL_COUNT
+};
+int dags_timing_enable(dags_ctx *ctx, int enable);
+int dags_timing_read(dags_ctx *ctx, double *ms, int64_t *launches, int32_t count);
 
 #ifdef __cplusplus
 }

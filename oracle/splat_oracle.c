@@ -494,9 +494,14 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
         if (dvalid && fabs(rd) <= MARGIN * fmax(fabs(acc[3]), fabs(tg[3]))) flags |= FL_SIGN;
         sd = dvalid ? (double)((rd > 0) - (rd < 0)) : 0.0;
         double lw = lc[LC_LPHO] * l1 + (dvalid ? lc[LC_LDEPTH] * fabs(rd) : 0.0);
+        /* a target with negative red marks a pixel without valid colour: it is
+         * left out of both loss terms, as a pixel without valid depth is left
+         * out of the depth term */
+        const int pvalid = tg[0] >= 0;
+        if (!pvalid) lw = 0.0;
         L += w * lw;
 
-        if (want_grad && nl > 0) {
+        if (want_grad && nl > 0 && pvalid) {
           /* upstream gradients of the six composited channels */
           double gF[6];
           for (int k = 0; k < 3; k++) gF[k] = lc[LC_LPHO] * w * sc[k];

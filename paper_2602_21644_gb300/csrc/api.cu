@@ -5,13 +5,69 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 using namespace dags;
 
+// Opt-in per-kernel device timing: a pair of CUDA events around every
+// kernel launch of the library, on the launch stream; read and reset by
+// dags_timing_read. Skipped while the stream is being captured into a graph.
+struct KernelTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kid;      // kernel id per used pair
+  size_t used = 0;           // pairs in use
+  double ms[DAGS_KERNEL_COUNT] = {};
+  int64_t launches[DAGS_KERNEL_COUNT] = {};
+
+  bool active(cudaStream_t s) {
+    if (!on) return false;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return false;
+    return true;
+  }
+  // returns the index of the begin event, or -1
+  int begin(int k, cudaStream_t s) {
+    if (!active(s)) return -1;
+    if (2 * (used + 1) > pool.size()) {
+      for (int i = 0; i < 512; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return -1;
+        pool.push_back(e);
+      }
+    }
+    const int i = (int)used++;
+    kid.resize(used);
+    kid[i] = k;
+    cudaEventRecord(pool[2 * i], s);
+    return i;
+  }
+  void end(int i, cudaStream_t s) {
+    if (i >= 0) cudaEventRecord(pool[2 * i + 1], s);
+  }
+  int collect() {
+    for (size_t i = 0; i < used; ++i) {
+      float t = 0.f;
+      if (cudaEventSynchronize(pool[2 * i + 1]) != cudaSuccess) return DAGS_E_CUDA;
+      if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) != cudaSuccess) return DAGS_E_CUDA;
+      ms[kid[i]] += t;
+      launches[kid[i]] += 1;
+    }
+    used = 0;
+    return DAGS_OK;
+  }
+  void release() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+    pool.clear();
+  }
+};
+
 struct dags_ctx {
   int device = 0;
   Workspace ws;
+  KernelTimer timer;
   cudaStream_t last_stream = nullptr;
   // the buffers of the latest forward (backward must follow its forward)
   const void *fwd_image = nullptr;
@@ -198,6 +254,7 @@ void dags_destroy(dags_ctx *ctx) {
   cudaGetDevice(&cur);
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
+  ctx->timer.release();
   free_ws(ctx->ws);
   cudaSetDevice(cur);
   delete ctx;
@@ -236,11 +293,25 @@ int splat_forward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camer
   ctx->fwd_image = nullptr;
   const Workspace &w = ctx->ws;
   const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
+  KernelTimer &tm = ctx->timer;
+  int ev = tm.begin(DAGS_K_PREPROCESS, s);
   cudaError_t e = launch_preprocess(w, g4, n, poses, n_views, r, kGradWords, s);
-  if (e == cudaSuccess) e = launch_emit(w, n, n_views, r, s);
-  if (e == cudaSuccess) e = launch_tile_sort(w, n_views, r, s);
-  if (e == cudaSuccess)
+  tm.end(ev, s);
+  if (e == cudaSuccess && n > 0) {
+    ev = tm.begin(DAGS_K_EMIT, s);
+    e = launch_emit(w, n, n_views, r, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_TILE_SORT, s);
+    e = launch_tile_sort(w, n_views, r, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_RENDER_FWD, s);
     e = launch_render_fwd(w, n_views, n, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
+    tm.end(ev, s);
+  }
   if (e != cudaSuccess) return DAGS_E_CUDA;
   ctx->fwd_image = image;
   ctx->fwd_last = last;
@@ -291,11 +362,17 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
   const bool full = (grad_flags & DAGS_GRAD_GAUSS) != 0;
+  KernelTimer &tm = ctx->timer;
+  int ev = tm.begin(DAGS_K_RENDER_BWD, s);
   cudaError_t e = launch_render_bwd(ctx->ws, n_views, n, r, l, reinterpret_cast<const float4 *>(targets),
                                     image, last, full, s);
-  if (e == cudaSuccess)
+  tm.end(ev, s);
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_PREPROCESS_BWD, s);
     e = launch_preprocess_bwd(ctx->ws, reinterpret_cast<const float4 *>(gauss), n, n_views, r,
                               full ? grad_gauss : nullptr, (grad_flags & DAGS_GRAD_POSE) ? grad_pose : nullptr, s);
+    tm.end(ev, s);
+  }
   return cuda_status(e);
 }
 
@@ -310,7 +387,32 @@ int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_sta
   if (!(c.beta1 >= 0 && c.beta1 < 1) || !(c.beta2 >= 0 && c.beta2 < 1) || !(c.eps > 0)) return DAGS_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
-  return cuda_status(launch_pose_step(poses, grad, adam_state, n_views, c, s));
+  const int ev = ctx->timer.begin(DAGS_K_POSE_STEP, s);
+  const cudaError_t e = launch_pose_step(poses, grad, adam_state, n_views, c, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+int dags_timing_enable(dags_ctx *ctx, int enable) {
+  if (!ctx) return DAGS_E_INVAL;
+  int rc = DAGS_OK;
+  if (!enable && ctx->timer.used) rc = ctx->timer.collect();
+  ctx->timer.on = enable != 0;
+  return rc;
+}
+
+int dags_timing_read(dags_ctx *ctx, double *ms, int64_t *launches, int32_t count) {
+  if (!ctx || count < 0 || (count > 0 && (!ms || !launches))) return DAGS_E_INVAL;
+  const int rc = ctx->timer.collect();
+  if (rc != DAGS_OK) return rc;
+  for (int k = 0; k < count && k < DAGS_KERNEL_COUNT; ++k) {
+    ms[k] = ctx->timer.ms[k];
+    launches[k] = ctx->timer.launches[k];
+    ctx->timer.ms[k] = 0.0;
+    ctx->timer.launches[k] = 0;
+  }
+  for (int k = DAGS_KERNEL_COUNT; k < count; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  return DAGS_OK;
 }
 
 }  // extern "C"

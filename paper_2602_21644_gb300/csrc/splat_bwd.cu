@@ -47,14 +47,15 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;  // upstream per channel
   int lastp = 0;
   if (inside) {
+    // a pixel whose target has negative red is outside the loss (no gradient)
     const size_t pix = (size_t)py * r.W + px;
     const float *img = image + (size_t)v * DAGS_IMG_CHANNELS * P + pix;
     const float cr = img[0], cg = img[P], cb = img[2 * P], dd = img[3 * P];
     const float oo = img[4 * P], rm = img[5 * P];
     T = img[6 * P];
     const float w = img[7 * P];
-    lastp = last[(size_t)v * P + pix];
     const float4 tg = targets[(size_t)v * P + pix];
+    lastp = tg.x >= 0.f ? last[(size_t)v * P + pix] : 0;
     const float rc0 = cr - tg.x, rc1 = cg - tg.y, rc2 = cb - tg.z, rd = dd - tg.w;
     const bool dvalid = tg.w > 0.f;
     auto sgn = [](float x) { return (float)((x > 0.f) - (x < 0.f)); };

@@ -341,7 +341,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
       const float4 tg = targets[(size_t)v * P + pix];
       const float l1 = fabsf(cr - tg.x) + fabsf(cg - tg.y) + fabsf(cb - tg.z);
       const float ld = tg.w > 0.f ? fabsf(dd - tg.w) : 0.f;
-      lpx = wgt * (l.lambda_pho * l1 + l.lambda_depth * ld);
+      lpx = tg.x >= 0.f ? wgt * (l.lambda_pho * l1 + l.lambda_depth * ld) : 0.f;
     }
     float *img = image + (size_t)v * DAGS_IMG_CHANNELS * P + pix;
     img[0 * P] = cr; img[1 * P] = cg; img[2 * P] = cb; img[3 * P] = dd;

@@ -56,7 +56,10 @@ class CPoseCfg(ctypes.Structure):
 
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
-           "splat_backward", "pose_step", "dags_copy_bins"]
+           "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read"]
+
+KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
+           "mp_pixel", "mp_gauss", "mpnet"]
 
 _lib = None
 
@@ -94,6 +97,10 @@ def load(path: str = LIB_PATH):
     lib.pose_step.restype = ctypes.c_int
     lib.dags_copy_bins.argtypes = [P, P, I64, P, I64, ctypes.POINTER(I64)]
     lib.dags_copy_bins.restype = ctypes.c_int
+    lib.dags_timing_enable.argtypes = [P, ctypes.c_int]
+    lib.dags_timing_enable.restype = ctypes.c_int
+    lib.dags_timing_read.argtypes = [P, P, P, I32]
+    lib.dags_timing_read.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -188,6 +195,19 @@ class Context:
         code, req = self.sync_status()
         if code != 0:
             raise DagsError(code, f"device status (required pairs {req})")
+
+    def timing(self, enable: bool):
+        _check(self.lib.dags_timing_enable(self.h, int(bool(enable))), "dags_timing_enable")
+
+    def timing_read(self):
+        """{kernel: (total_ms, launches)} accumulated since the last read."""
+        import numpy as np
+        k = len(KERNELS)
+        ms = np.zeros(k, np.float64)
+        n = np.zeros(k, np.int64)
+        _check(self.lib.dags_timing_read(self.h, ms.ctypes.data_as(ctypes.c_void_p),
+                                         n.ctypes.data_as(ctypes.c_void_p), k), "dags_timing_read")
+        return {KERNELS[i]: (float(ms[i]), int(n[i])) for i in range(k)}
 
     def copy_bins(self, views: int, cam: Camera):
         """(tile_start [views*T+1] uint32, ids [pairs] uint32) of the last forward."""

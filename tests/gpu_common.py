@@ -29,6 +29,26 @@ def image_rows(image_v):
     return image_v.permute(1, 2, 0).reshape(-1, image_v.shape[0]).double().cpu().numpy()
 
 
+GRAD_MASK_FLAGS = oracle.PIXEL_DECISION_FLAGS | oracle.FLAGS["SIGN"]
+
+
+def mask_flagged_targets(sc, lc=None):
+    """Copy of the scene whose flagged pixels (a decision or a residual sign
+    within FP32 error of its threshold) are left out of the loss (r < 0), so
+    that gradients compare only what both sides decide identically."""
+    G = oracle.params_from_records(sc.records)
+    cam = oracle.camera_vec(*sc.camera.as_tuple())
+    tg = sc.targets.copy()
+    masked = 0
+    for v in range(sc.poses.shape[0]):
+        r = oracle.render(G, cam, sc.poses[v], lc=lc, targets=sc.targets[v])
+        bad = (r["flags"] & GRAD_MASK_FLAGS) != 0
+        tg[v, bad, 0] = -1.0
+        masked += int(bad.sum())
+    from paper_2602_21644_gb300 import synth
+    return synth.Scene(sc.records, sc.camera, sc.poses, tg, sc.dynamic, sc.extra), masked
+
+
 def oracle_views(sc, grads=True, lc=None):
     G = oracle.params_from_records(sc.records)
     cam = oracle.camera_vec(*sc.camera.as_tuple())

@@ -7,7 +7,7 @@ from oracle import pose as opose
 from paper_2602_21644_gb300 import synth
 
 from gpu_common import (GRAD_NORM, IMG_NORM, LOSS_REL, POSE_REL, compare_grads, compare_image, image_rows,
-                        oracle_views, to_dev)
+                        mask_flagged_targets, oracle_views, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -78,7 +78,7 @@ def assert_bins_match(res, sc, dags, views_outs=None):
 
 
 def test_forward_backward_tiny(dags):
-    sc = synth.tiny_scene(0)
+    sc, _ = mask_flagged_targets(synth.tiny_scene(0))
     res = run(dags, sc, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
     G, cam, outs = oracle_views(sc)
     report = []
@@ -102,7 +102,8 @@ def test_binning_bit_exact_tiny(dags):
 
 @pytest.mark.parametrize("wmode,wgrad", [(0, 1), (1, 0), (1, 1)])
 def test_loss_weight_modes(dags, wmode, wgrad):
-    sc = synth.tiny_scene(2, n=800, width=96, height=72, f=80.0)
+    sc, _ = mask_flagged_targets(synth.tiny_scene(2, n=800, width=96, height=72, f=80.0),
+                                 oracle.loss_vec(weight_mode=wmode, weight_grad=wgrad))
     lc = dags.default_loss_cfg(weight_mode=wmode, weight_grad=wgrad)
     res = run(dags, sc, flags=dags.GRAD_GAUSS | dags.GRAD_POSE, lcfg=lc)
     G, cam, outs = oracle_views(sc, lc=oracle.loss_vec(weight_mode=wmode, weight_grad=wgrad))
@@ -120,6 +121,7 @@ def test_ragged_image_and_pose(dags):
     # image size not a multiple of the tile, non-identity pose, partly outside
     sc = synth.tiny_scene(4, n=1500, width=150, height=101, f=110.0)
     sc.poses[0] = synth.look_at_pose([0.4, -0.3, -0.6], [0.1, 0.1, 2.5])
+    sc, _ = mask_flagged_targets(sc)
     res = run(dags, sc, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
     G, cam, outs = oracle_views(sc)
     report = []
@@ -136,7 +138,7 @@ def test_multiview_equals_single_views(dags):
     poses = [synth.identity_pose(), synth.look_at_pose([0.2, 0.0, -0.3], [0.0, 0.0, 2.5]),
              synth.look_at_pose([-0.3, 0.2, 0.0], [0.1, -0.1, 2.0])]
     tg = np.repeat(sc.targets, 3, axis=0)
-    scm = synth.Scene(sc.records, sc.camera, np.stack(poses), tg)
+    scm, _ = mask_flagged_targets(synth.Scene(sc.records, sc.camera, np.stack(poses), tg))
     res = run(dags, scm, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
     G, cam, outs = oracle_views(scm)
     report = []
@@ -260,7 +262,8 @@ def test_pose_step_matches_oracle(dags):
 def test_full_size_tracking_frame(dags):
     # 300k Gaussians, 640x480: the whole image and the pose gradient against
     # the oracle (which takes about a second here).
-    sc = synth.tracking_scene(300_000, frame=10)
+    sc, masked = mask_flagged_targets(synth.tracking_scene(300_000, frame=10))
+    assert masked < 0.01 * sc.targets.shape[1]
     res = run(dags, sc, flags=dags.GRAD_POSE)
     G, cam, outs = oracle_views(sc)
     report = []
@@ -275,12 +278,28 @@ def test_full_size_tracking_frame(dags):
 
 def test_full_size_mapping_window(dags):
     # 200k Gaussians, 8 keyframes of 640x480, full parameter gradients.
-    sc = synth.mapping_scene(200_000, views=8)
+    sc, masked = mask_flagged_targets(synth.mapping_scene(200_000, views=8))
+    assert masked < 0.01 * sc.targets.shape[1] * 8
     res = run(dags, sc, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
     G, cam, outs = oracle_views(sc)
     report = []
     assert_image_parity(res, outs, "map", report)
     g = compare_grads(res["gg"], sum(o["grad"] for o in outs), report)
     print("\n".join(report))
+    for k, v in g.items():
+        assert v <= GRAD_NORM, k
+
+
+def test_invalid_colour_pixels_leave_the_loss(dags):
+    # r < 0 removes a pixel from the loss and the gradient on both sides
+    sc = synth.tiny_scene(7, n=600, width=64, height=48, f=60.0)
+    tg = sc.targets.copy()
+    tg[0, ::3, 0] = -1.0
+    sc2 = synth.Scene(sc.records, sc.camera, sc.poses, tg)
+    sc2, _ = mask_flagged_targets(sc2)
+    res = run(dags, sc2, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
+    G, cam, outs = oracle_views(sc2)
+    assert abs(res["loss"] - outs[0]["loss"]) <= LOSS_REL * abs(outs[0]["loss"])
+    g = compare_grads(res["gg"], outs[0]["grad"])
     for k, v in g.items():
         assert v <= GRAD_NORM, k
