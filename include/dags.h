@@ -188,6 +188,22 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
 int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state,
               int32_t n_views, const dags_pose_cfg *cfg, void *stream);
 
+/* Tracking loop: iters x { splat_forward with loss, splat_backward
+ * (DAGS_GRAD_POSE), pose_step } on one view, enqueued by the library -- the
+ * pose refinement of the tracking thread (Sec. III) with the pose part of
+ * Eq. (27). pose (device, 12 doubles) and adam_state (device, 13 doubles)
+ * are updated in place; image, last, loss and grad_pose hold the last
+ * iteration's values. With use_graph != 0 (and timing off) one iteration
+ * is captured once into a CUDA graph on a private stream, cached in the ctx
+ * for exactly these arguments (pointers, sizes, camera, configs), and
+ * replayed iters times on `stream`; (re)capturing synchronises `stream`
+ * first. Capacity overflow is reported by dags_sync_status as for
+ * splat_forward. */
+int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
+                const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                const dags_pose_cfg *pcfg, int32_t iters, double *adam_state, float *image, int32_t *last,
+                double *loss, double *grad_pose, int32_t use_graph, void *stream);
+
 /* Per-kernel device timing (tracing). When enabled, every kernel the
  * library launches on a stream that is not being captured into a CUDA graph
  * is bracketed by a pair of CUDA events on that stream. dags_timing_read

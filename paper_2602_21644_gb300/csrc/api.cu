@@ -64,10 +64,19 @@ struct KernelTimer {
   }
 };
 
+// A captured tracking iteration and the arguments it was captured with.
+struct TrackGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;       // private stream used for capture
+  unsigned char key[512];
+  size_t key_len = 0;
+};
+
 struct dags_ctx {
   int device = 0;
   Workspace ws;
   KernelTimer timer;
+  TrackGraph graph;
   cudaStream_t last_stream = nullptr;
   // the buffers of the latest forward (backward must follow its forward)
   const void *fwd_image = nullptr;
@@ -255,6 +264,8 @@ void dags_destroy(dags_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   ctx->timer.release();
+  if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+  if (ctx->graph.cap) cudaStreamDestroy(ctx->graph.cap);
   free_ws(ctx->ws);
   cudaSetDevice(cur);
   delete ctx;
@@ -391,6 +402,93 @@ int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_sta
   const cudaError_t e = launch_pose_step(poses, grad, adam_state, n_views, c, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Enqueues one tracking iteration: forward with loss, pose-only backward, pose step.
+int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
+                    const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                    const dags_pose_cfg *pcfg, double *adam_state, float *image, int32_t *last, double *loss,
+                    double *grad_pose, cudaStream_t s) {
+  int rc = splat_forward(ctx, gauss, n, cam, pose, 1, targets, rcfg, lcfg, image, last, loss, s);
+  if (rc) return rc;
+  rc = splat_backward(ctx, gauss, n, cam, pose, 1, targets, rcfg, lcfg, image, last, DAGS_GRAD_POSE, nullptr,
+                      grad_pose, s);
+  if (rc) return rc;
+  return pose_step(ctx, pose, grad_pose, adam_state, 1, pcfg, s);
+}
+
+template <class T>
+void key_put(unsigned char *key, size_t &len, const T &v) {
+  if (len + sizeof(T) <= 512) { memcpy(key + len, &v, sizeof(T)); }
+  len += sizeof(T);
+}
+
+}  // namespace
+
+extern "C" {
+
+int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
+                const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                const dags_pose_cfg *pcfg, int32_t iters, double *adam_state, float *image, int32_t *last,
+                double *loss, double *grad_pose, int32_t use_graph, void *stream) {
+  if (!ctx || iters < 0 || !pose || !targets || !adam_state || !image || !last || !loss || !grad_pose)
+    return DAGS_E_INVAL;
+  int rc = common_args(ctx, gauss, n, cam, pose, 1);
+  if (rc) return rc;
+  dags_raster_cfg rc_v;
+  dags_loss_cfg lc_v;
+  dags_pose_cfg pc_v;
+  if (rcfg) rc_v = *rcfg; else dags_default_raster_cfg(&rc_v);
+  if (lcfg) lc_v = *lcfg; else dags_default_loss_cfg(&lc_v);
+  if (pcfg) pc_v = *pcfg; else dags_default_pose_cfg(&pc_v);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!use_graph || ctx->timer.on) {
+    for (int k = 0; k < iters; ++k) {
+      rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
+                           grad_pose, s);
+      if (rc) return rc;
+    }
+    return DAGS_OK;
+  }
+  // Graph path: capture one iteration on a private stream (the caller's may be
+  // the legacy default stream, which cannot be captured), keyed by every
+  // argument, and replay it on the caller's stream.
+  unsigned char key[512];
+  size_t kl = 0;
+  key_put(key, kl, gauss); key_put(key, kl, n); key_put(key, kl, *cam); key_put(key, kl, pose);
+  key_put(key, kl, targets); key_put(key, kl, rc_v); key_put(key, kl, lc_v); key_put(key, kl, pc_v);
+  key_put(key, kl, adam_state); key_put(key, kl, image); key_put(key, kl, last); key_put(key, kl, loss);
+  key_put(key, kl, grad_pose);
+  TrackGraph &g = ctx->graph;
+  if (!g.exec || g.key_len != kl || memcmp(g.key, key, kl) != 0) {
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return DAGS_E_CUDA;
+    // order the capture after the caller's pending work on the workspace
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DAGS_E_CUDA;
+    if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
+    rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
+                         grad_pose, g.cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
+    if (rc != DAGS_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != DAGS_OK ? rc : DAGS_E_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { g.exec = nullptr; return DAGS_E_CUDA; }
+    memcpy(g.key, key, kl < 512 ? kl : 512);
+    g.key_len = kl;
+  }
+  ctx->last_stream = s;
+  for (int k = 0; k < iters; ++k)
+    if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return DAGS_E_CUDA;
+  return DAGS_OK;
 }
 
 int dags_timing_enable(dags_ctx *ctx, int enable) {

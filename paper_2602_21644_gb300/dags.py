@@ -56,7 +56,8 @@ class CPoseCfg(ctypes.Structure):
 
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
-           "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read"]
+           "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
+           "splat_track"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet"]
@@ -101,6 +102,9 @@ def load(path: str = LIB_PATH):
     lib.dags_timing_enable.restype = ctypes.c_int
     lib.dags_timing_read.argtypes = [P, P, P, I32]
     lib.dags_timing_read.restype = ctypes.c_int
+    lib.splat_track.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
+                                ctypes.POINTER(CLossCfg), ctypes.POINTER(CPoseCfg), I32, P, P, P, P, P, I32, P]
+    lib.splat_track.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -268,6 +272,19 @@ class Context:
                                        _ptr(grad_gauss if flags & GRAD_GAUSS else None),
                                        _ptr(grad_pose if flags & GRAD_POSE else None), _stream()), "splat_backward")
         return (grad_gauss if flags & GRAD_GAUSS else None), (grad_pose if flags & GRAD_POSE else None)
+
+    def track(self, gauss, cam: Camera, pose, targets, iters, adam_state, image, last, loss, grad_pose,
+              rcfg=None, lcfg=None, pcfg=None, use_graph=True):
+        """iters tracking iterations (forward, pose backward, pose step) enqueued
+        by the library; pose and adam_state are updated in place."""
+        c = cam.c()
+        rc = rcfg if rcfg is not None else default_raster_cfg()
+        lc = lcfg if lcfg is not None else default_loss_cfg()
+        pc = pcfg if pcfg is not None else default_pose_cfg()
+        _check(self.lib.splat_track(self.h, _ptr(gauss), gauss.shape[0], ctypes.byref(c), _ptr(pose), _ptr(targets),
+                                    ctypes.byref(rc), ctypes.byref(lc), ctypes.byref(pc), int(iters),
+                                    _ptr(adam_state), _ptr(image), _ptr(last), _ptr(loss), _ptr(grad_pose),
+                                    int(bool(use_graph)), _stream()), "splat_track")
 
     def pose_step(self, poses, grad_pose, adam_state, cfg=None):
         _need(poses, torch.float64, "poses")

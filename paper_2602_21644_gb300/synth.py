@@ -206,11 +206,36 @@ def _frames_from_normals(nrm: np.ndarray) -> np.ndarray:
     return np.stack([t1, t2, nrm], axis=2)
 
 
-def room_scene(n: int, seed: int = 0, objects=None, opacity_logit=(2.5, 0.5), mp_static=0.1,
+def _jittered_grid(m: int, ex: float, ey: float, rng) -> np.ndarray:
+    """m points covering [-ex, ex] x [-ey, ey] on a jittered grid (one
+    point per cell, no holes), extra points uniform."""
+    nx = max(1, int(np.floor(np.sqrt(m * ex / ey))))
+    ny = max(1, m // nx)
+    gx, gy = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    px = (gx.ravel() + rng.uniform(0.1, 0.9, nx * ny)) / nx * 2 * ex - ex
+    py = (gy.ravel() + rng.uniform(0.1, 0.9, nx * ny)) / ny * 2 * ey - ey
+    extra = m - nx * ny
+    if extra > 0:
+        px = np.concatenate([px, rng.uniform(-ex, ex, extra)])
+        py = np.concatenate([py, rng.uniform(-ey, ey, extra)])
+    return np.stack([px[:m], py[:m]], 1)
+
+
+def _fibonacci_sphere(m: int, rng) -> np.ndarray:
+    k = np.arange(m) + 0.5
+    z = 1 - 2 * k / m
+    phi = np.pi * (1 + 5 ** 0.5) * k + rng.uniform(0, 2 * np.pi)
+    r = np.sqrt(np.maximum(0.0, 1 - z * z))
+    return np.stack([r * np.cos(phi), r * np.sin(phi), z], 1)
+
+
+def room_scene(n: int, seed: int = 0, objects=None, opacity_logit=(4.0, 0.5), mp_static=0.1,
                mp_dynamic=0.9):
-    """n Gaussians sampled on the 6 x 6 x 3 m room's walls, floor and ceiling
-    and on the objects' ellipsoidal surfaces, area-proportionally. Disc-like
-    Gaussians: tangent sigma = 0.7 x mean spacing, normal sigma = 2 mm.
+    """n Gaussians covering the 6 x 6 x 3 m room's walls, floor and ceiling
+    and the objects' ellipsoidal surfaces, area-proportionally, on jittered
+    grids (Fibonacci lattices on the ellipsoids) so that the surfaces have no
+    holes, as in a converged map. Disc-like Gaussians: tangent sigma = 0.7 x
+    mean spacing, normal sigma = 2 mm; opacity logit N(4, 0.5).
     Returns (records, object_id per Gaussian (-1 = room), objects)."""
     rng = np.random.default_rng(seed)
     objects = default_objects() if objects is None else objects
@@ -232,15 +257,16 @@ def room_scene(n: int, seed: int = 0, objects=None, opacity_logit=(2.5, 0.5), mp
     pts, nrms, oid = [], [], []
     for k, (axis, sgn) in enumerate(planes):
         m = counts[k]
-        p = rng.uniform(-1, 1, (m, 3)) * ROOM_HALF
+        o = [a for a in range(3) if a != axis]
+        p = np.zeros((m, 3))
+        p[:, o] = _jittered_grid(m, ROOM_HALF[o[0]], ROOM_HALF[o[1]], rng)
         p[:, axis] = sgn * ROOM_HALF[axis]
         nv = np.zeros((m, 3))
         nv[:, axis] = -sgn
         pts.append(p); nrms.append(nv); oid.append(np.full(m, -1))
     for j, ob in enumerate(objects):
         m = counts[len(planes) + j]
-        d = rng.normal(0, 1, (m, 3))
-        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        d = _fibonacci_sphere(m, rng)
         p = ob.center + d * ob.axes
         nv = d / ob.axes
         nv /= np.linalg.norm(nv, axis=1, keepdims=True)
