@@ -33,10 +33,11 @@ _lib = None
 
 # Layout constants mirrored from splat_oracle.c.
 G_STRIDE = 15
-PJ_STRIDE = 21
+PJ_STRIDE = 24
 PX_STRIDE = 10
 PJ = dict(VIS=0, U=1, V=2, Z=3, A=4, B=5, C=6, O=7, SA=8, SB=9, SC=10, LMAX=11, R=12,
-          X0=13, Y0=14, X1=15, Y1=16, FLAG=17, PX=18, PY=19, ZKEY=20)
+          X0=13, Y0=14, X1=15, Y1=16, FLAG=17, PX=18, PY=19, ZKEY=20,
+          EX=21, EY=22, CTHR=23)
 PX = dict(CR=0, CG=1, CB=2, D=3, O=4, RMP=5, T=6, N=7, LAST=8, W=9)
 FLAGS = dict(ZNEAR=1, CLAMP=2, RADIUS=4, RECT=8, OPAC=16, ALPHA=32, AMAX=64, TSTOP=128,
              ZTIE=256, OEPS=512, SIGN=1024)

@@ -60,7 +60,8 @@ enum { LC_LPHO = 0, LC_LDEPTH, LC_WMODE, LC_WGRAD, LC_OEPS, LC_N };
 
 /* Projection record per Gaussian. */
 enum { PJ_VIS = 0, PJ_U, PJ_V, PJ_Z, PJ_A, PJ_B, PJ_C, PJ_O, PJ_SA, PJ_SB, PJ_SC,
-       PJ_LMAX, PJ_R, PJ_X0, PJ_Y0, PJ_X1, PJ_Y1, PJ_FLAG, PJ_PX, PJ_PY, PJ_ZKEY, PJ_STRIDE };
+       PJ_LMAX, PJ_R, PJ_X0, PJ_Y0, PJ_X1, PJ_Y1, PJ_FLAG, PJ_PX, PJ_PY, PJ_ZKEY, PJ_EX, PJ_EY,
+       PJ_CTHR, PJ_STRIDE };
 
 /* Per-pixel output: colour (3), depth, opacity, rendered MP, final
  * transmittance, number of contributors, id of the last contributor (-1),
@@ -118,7 +119,8 @@ static void tr3(const double *A, double *T) {
 }
 
 /* Everything projection computes for one Gaussian, kept for the adjoint. */
-typedef struct {
+struct proj_s;
+typedef struct proj_s {
   int vis, flags;
   double p[3];          /* camera-space mean                        */
   double tx, ty;        /* clamped x/z, y/z                          */
@@ -132,6 +134,8 @@ typedef struct {
   double A, B, C;       /* 2D covariance after dilation              */
   double a, b, c;       /* conic = inverse 2D covariance             */
   double o, u, v, lmax, rext;
+  double cthr;          /* 2 ln(o / alpha_min): alpha >= alpha_min iff q(d) <= cthr */
+  double ex, ey;        /* half extents of the bounding box of that ellipse */
   double cond;          /* condition number of the dilated 2D covariance   */
   float zkey;           /* FP32 depth key that decides the depth order      */
   int r, x0, y0, x1, y1;
@@ -154,6 +158,8 @@ static float depth_key(const double *g, const double *pose) {
   volatile float z = abc + tz;
   return z;
 }
+
+static int tile_reached(const proj_t *p, int tx, int ty, double tile, int W, int H, double *margin);
 
 static void project_one(const double *g, const double *cam, const double *pose,
                         const double *rc, proj_t *P) {
@@ -232,13 +238,19 @@ static void project_one(const double *g, const double *cam, const double *pose,
   P->lmax = mid + sqrt(disc > 0.1 ? disc : 0.1);
   /* Outside |d| <= sqrt(2 lmax ln(o/alpha_min)) the Gaussian's alpha is below
    * alpha_min, so it cannot contribute there. */
-  P->rext = sqrt(2.0 * P->lmax * log(P->o / rc[RC_ALPHA_MIN]));
-  if (near_int(P->rext)) P->flags |= FL_RADIUS;
+  P->cthr = 2.0 * log(P->o / rc[RC_ALPHA_MIN]);
+  P->rext = sqrt(P->lmax * P->cthr);
   P->r = (int)ceil(P->rext);
+  /* Bounding box of the ellipse q(d) = d^T Q d <= cthr outside of which the
+   * Gaussian's alpha is below alpha_min: half extents sqrt(cthr Sigma'_xx),
+   * sqrt(cthr Sigma'_yy). Its tile range is the candidate range; binning
+   * keeps the candidate tiles the ellipse actually reaches (tile_reached). */
+  P->ex = sqrt(P->cthr * P->A);
+  P->ey = sqrt(P->cthr * P->C);
   double tile = rc[RC_TILE];
   int tx = (int)ceil(cam[CAM_W] / tile), ty = (int)ceil(cam[CAM_H] / tile);
-  double ex[4] = {(P->u - P->r) / tile, (P->v - P->r) / tile, (P->u + P->r) / tile,
-                  (P->v + P->r) / tile};
+  double ex[4] = {(P->u - P->ex) / tile, (P->v - P->ey) / tile, (P->u + P->ex) / tile,
+                  (P->v + P->ey) / tile};
   for (int i = 0; i < 4; i++)
     if (near_int(ex[i])) P->flags |= FL_RECT;
   int x0 = (int)floor(ex[0]), y0 = (int)floor(ex[1]);
@@ -251,18 +263,32 @@ static void project_one(const double *g, const double *cam, const double *pose,
   P->vis = 1;
 }
 
+/* Flags FL_RECT on a visible Gaussian if any of its candidate-tile decisions
+ * lies within FP32 rounding of the threshold. */
+static void flag_tile_decisions(proj_t *P, const double *cam, const double *rc) {
+  if (!P->vis) return;
+  for (int y = P->y0; y < P->y1; y++)
+    for (int x = P->x0; x < P->x1; x++) {
+      double m;
+      tile_reached(P, x, y, rc[RC_TILE], (int)cam[CAM_W], (int)cam[CAM_H], &m);
+      if (m < 1.0) P->flags |= FL_RECT;
+    }
+}
+
 /* Projection of all Gaussians into out[n * PJ_STRIDE]. */
 void oracle_project(int64_t n, const double *G, const double *cam, const double *pose,
                     const double *rc, double *out) {
   for (int64_t i = 0; i < n; i++) {
     proj_t P;
     project_one(G + i * G_STRIDE, cam, pose, rc, &P);
+    flag_tile_decisions(&P, cam, rc);
     double *o = out + i * PJ_STRIDE;
     o[PJ_VIS] = P.vis; o[PJ_U] = P.u; o[PJ_V] = P.v; o[PJ_Z] = P.p[2];
     o[PJ_A] = P.a; o[PJ_B] = P.b; o[PJ_C] = P.c; o[PJ_O] = P.o;
     o[PJ_SA] = P.A; o[PJ_SB] = P.B; o[PJ_SC] = P.C; o[PJ_LMAX] = P.lmax;
     o[PJ_R] = P.r; o[PJ_X0] = P.x0; o[PJ_Y0] = P.y0; o[PJ_X1] = P.x1; o[PJ_Y1] = P.y1;
     o[PJ_FLAG] = P.flags; o[PJ_PX] = P.p[0]; o[PJ_PY] = P.p[1]; o[PJ_ZKEY] = (double)P.zkey;
+    o[PJ_EX] = P.ex; o[PJ_EY] = P.ey; o[PJ_CTHR] = P.cthr;
   }
 }
 
@@ -290,6 +316,43 @@ static int cmp_zkey(const void *pa, const void *pb) {
 
 /* ---- binning ---- */
 
+/* Does the ellipse q(d) <= cthr reach the pixel-centre rectangle of tile
+ * (tx, ty) (pixels 16 tx .. 16 tx + 15 clipped to the image)? The minimum of
+ * the positive-definite q over the rectangle is 0 if the centre is inside,
+ * else it lies on one of the four edges, where q is a 1-D quadratic whose
+ * minimiser is clamped to the edge. *margin receives the distance of that
+ * minimum to cthr relative to the FP32 error bound of its evaluation (< 1:
+ * the decision is within FP32 rounding). */
+static int tile_reached(const proj_t *p, int tx, int ty, double tile, int W, int H, double *margin) {
+  double xl = tx * tile - p->u, xh = fmin(tx * tile + tile - 1, W - 1) - p->u;
+  double yl = ty * tile - p->v, yh = fmin(ty * tile + tile - 1, H - 1) - p->v;
+  double qmin;
+  if (xl <= 0 && xh >= 0 && yl <= 0 && yh >= 0) {
+    qmin = 0.0;
+  } else {
+    double a = p->a, b = p->b, c = p->c;
+    double best = INFINITY;
+    double X[2] = {xl, xh}, Y[2] = {yl, yh};
+    for (int k = 0; k < 2; k++) {
+      double x = X[k];
+      double y = -b * x / c;
+      y = y < yl ? yl : (y > yh ? yh : y);
+      double q = a * x * x + 2 * b * x * y + c * y * y;
+      if (q < best) best = q;
+      double yy = Y[k];
+      double xx = -b * yy / a;
+      xx = xx < xl ? xl : (xx > xh ? xh : xx);
+      q = a * xx * xx + 2 * b * xx * yy + c * yy * yy;
+      if (q < best) best = q;
+    }
+    qmin = best;
+  }
+  double ecoord = ldexp(1.0, -22) * fmax(fmax(fabs(p->u), fabs(p->v)), 1.0);
+  double err = 2.0 * sqrt(fmax(qmin, 0.0) * fmax(p->a, p->c)) * ecoord * 2.0 + 1e-5 * p->cthr * (1.0 + p->cond * 0.1) + 1e-6;
+  if (margin) *margin = fabs(qmin - p->cthr) / err;
+  return qmin <= p->cthr;
+}
+
 /* Pairs (tile, id) of every visible Gaussian and every tile of its rect,
  * sorted by (tile, depth key, id). Writes up to cap pairs, returns the total.
  * tie_flag[k] = 1 where pair k and pair k-1 share a tile and an equal depth
@@ -310,6 +373,7 @@ int64_t oracle_binning(int64_t n, const double *G, const double *cam, const doub
   int tx = (int)ceil(cam[CAM_W] / rc[RC_TILE]);
   proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
   int64_t total = 0;
+  const int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
   for (int64_t i = 0; i < n; i++) {
     project_one(G + i * G_STRIDE, cam, pose, rc, &P[i]);
     if (P[i].vis) total += (int64_t)(P[i].x1 - P[i].x0) * (P[i].y1 - P[i].y0);
@@ -320,12 +384,15 @@ int64_t oracle_binning(int64_t n, const double *G, const double *cam, const doub
     if (!P[i].vis) continue;
     for (int y = P[i].y0; y < P[i].y1; y++)
       for (int x = P[i].x0; x < P[i].x1; x++) {
+        double m;
+        if (!tile_reached(&P[i], x, y, rc[RC_TILE], W, H, &m)) continue;
         keys[k].tile = (int64_t)y * tx + x;
         keys[k].z = P[i].zkey;
         keys[k].id = i;
         k++;
       }
   }
+  total = k;
   qsort(keys, (size_t)total, sizeof(bkey_t), cmp_bkey);
   for (int64_t j = 0; j < total && j < cap; j++) {
     tiles[j] = keys[j].tile;
@@ -342,9 +409,10 @@ int64_t oracle_binning(int64_t n, const double *G, const double *cam, const doub
 typedef struct { int64_t id; double alpha, T, G, dx, dy; int clamped; } contrib_t;
 
 /* Candidate lists: a pixel's candidates are the visible Gaussians whose
- * bounding square |dx|, |dy| <= r holds the pixel, in (depth, id) order.
- * Outside that square alpha < alpha_min exactly, so restricting to it does
- * not change any value; with accel = 0 every visible Gaussian is tested. */
+ * bounding square |dx|, |dy| <= r (r >= sqrt(lambda_max cthr)) holds the
+ * pixel, in (depth, id) order. Outside that square alpha < alpha_min
+ * exactly, so restricting to it does not change any value; with accel = 0
+ * every visible Gaussian is tested. */
 typedef struct { int64_t *start; int64_t *ids; int cw, ch, cell; } cells_t;
 
 static void build_cells(int64_t n, const proj_t *P, const int64_t *order, int W, int H,

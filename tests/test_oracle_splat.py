@@ -251,27 +251,62 @@ def test_render_pixel_matches_full_render():
         np.testing.assert_allclose(v, r["pix"][pix], rtol=1e-14, atol=1e-15)
 
 
-def test_rect_bounds_every_contributing_pixel():
-    # Brute force over all pixels: every pixel where a Gaussian's alpha reaches
-    # 1/255 lies in a tile of its rect, and the rect is the tightest tile range
-    # holding the square |dx|, |dy| <= r.
+def _quad(p, dx, dy):
+    return p[4] * dx * dx + 2 * p[5] * dx * dy + p[6] * dy * dy
+
+
+def test_binned_tiles_are_the_tiles_the_alpha_ellipse_reaches():
+    # Brute force over pixels and over a fine sub-pixel grid of every
+    # candidate tile: a tile is binned iff the ellipse q(d) <= 2 ln(255 o),
+    # outside of which alpha < 1/255, reaches its pixel-centre rectangle; every
+    # contributing pixel's tile is binned; the candidate range is the tile range
+    # of the ellipse's bounding box.
     sc = synth.tiny_scene(2, n=400)
     G = oracle.params_from_records(sc.records)
     cam = oracle.camera_vec(*sc.camera.as_tuple())
     pj = oracle.project(G, cam, sc.poses[0])
+    tiles, ids, _ = oracle.binning(G, cam, sc.poses[0])
+    binned = {}
+    for t, g in zip(tiles.tolist(), ids.tolist()):
+        binned.setdefault(g, set()).add(t)
     ii, jj = pixel_grid(160, 120)
+    fine = np.arange(0, 15.001, 0.125)
+    fx, fy = np.meshgrid(fine, fine, indexing="xy")
+    checked = 0
     for g in np.nonzero(pj[:, 0] > 0)[0]:
         p = pj[g]
-        dx, dy = p[1] - ii, p[2] - jj
-        ag = p[7] * np.exp(-0.5 * (p[4] * dx * dx + p[6] * dy * dy) - p[5] * dx * dy)
-        hit = ag >= 1 / 255
-        tx, ty = (ii[hit] // 16).astype(int), (jj[hit] // 16).astype(int)
-        assert np.all((tx >= p[13]) & (tx < p[15]) & (ty >= p[14]) & (ty < p[16]))
-        assert np.all(np.abs(dx[hit]) <= p[12]) and np.all(np.abs(dy[hit]) <= p[12])
-        r = p[12]
-        x0 = max(0, int(np.floor((p[1] - r) / 16)))
-        x1 = min(10, int(np.floor((p[1] + r) / 16)) + 1)
-        assert (p[13], p[15]) == (x0, x1)
+        cth = p[oracle.PJ["CTHR"]]
+        np.testing.assert_allclose(cth, 2 * np.log(255 * p[7]), rtol=1e-12)
+        ex, ey = p[oracle.PJ["EX"]], p[oracle.PJ["EY"]]
+        assert (p[13], p[15]) == (max(0, np.floor((p[1] - ex) / 16)), min(10, np.floor((p[1] + ex) / 16) + 1))
+        assert (p[14], p[16]) == (max(0, np.floor((p[2] - ey) / 16)), min(8, np.floor((p[2] + ey) / 16) + 1))
+        q = _quad(p, p[1] - ii, p[2] - jj)
+        hit = q <= cth
+        # alpha >= 1/255 exactly where q <= cthr
+        ag = p[7] * np.exp(-0.5 * q)
+        assert np.array_equal(hit, ag >= 1 / 255) or (np.abs(ag - 1 / 255) < 1e-12).any()
+        pix_tiles = set(((jj[hit] // 16) * 10 + ii[hit] // 16).astype(int).tolist())
+        got = binned.get(g, set())
+        assert pix_tiles <= got
+        for t in got:
+            tx, ty = t % 10, t // 10
+            assert p[13] <= tx < p[15] and p[14] <= ty < p[16]
+            if t in pix_tiles:
+                continue
+            # a binned tile without a contributing pixel: the ellipse still
+            # reaches its (continuous) rectangle
+            xs = np.minimum(16 * tx + fx, 159) - p[1]
+            ys = np.minimum(16 * ty + fy, 119) - p[2]
+            assert _quad(p, xs, ys).min() <= cth * (1 + 1e-3)
+        for ty in range(int(p[14]), int(p[16])):
+            for tx in range(int(p[13]), int(p[15])):
+                if ty * 10 + tx in got:
+                    continue
+                xs = np.minimum(16 * tx + fx, 159) - p[1]
+                ys = np.minimum(16 * ty + fy, 119) - p[2]
+                assert _quad(p, xs, ys).min() > cth * (1 - 1e-9)
+                checked += 1
+    assert checked > 50      # the exact test drops tiles the bounding box holds
 
 
 def test_binning_order_and_content():
@@ -279,14 +314,11 @@ def test_binning_order_and_content():
     G = oracle.params_from_records(sc.records)
     cam = oracle.camera_vec(*sc.camera.as_tuple())
     pj = oracle.project(G, cam, sc.poses[0])
-    tiles, ids, ties = oracle.binning(G, cam, sc.poses[0])
-    # content: exactly the rect tiles of each visible Gaussian
-    exp = []
-    for g in np.nonzero(pj[:, 0] > 0)[0]:
-        for ty in range(int(pj[g, 14]), int(pj[g, 16])):
-            for tx in range(int(pj[g, 13]), int(pj[g, 15])):
-                exp.append((ty * 10 + tx, g))
-    assert sorted(exp) == sorted(zip(tiles.tolist(), ids.tolist()))
+    tiles, ids, _ = oracle.binning(G, cam, sc.poses[0])
+    # every pair lies in its Gaussian's candidate range, no pair twice
+    assert len(set(zip(tiles.tolist(), ids.tolist()))) == len(tiles)
+    tx, ty = tiles % 10, tiles // 10
+    assert np.all((tx >= pj[ids, 13]) & (tx < pj[ids, 15]) & (ty >= pj[ids, 14]) & (ty < pj[ids, 16]))
     # order: (tile, FP32 depth key, id)
     order = np.lexsort((ids, pj[ids, oracle.PJ["ZKEY"]], tiles))
     np.testing.assert_array_equal(order, np.arange(len(ids)))
