@@ -77,6 +77,7 @@ struct dags_ctx {
   Workspace ws;
   KernelTimer timer;
   TrackGraph graph;
+  PoseStep fused_step;            // set only inside the tracking loop
   cudaStream_t last_stream = nullptr;
   // the buffers of the latest forward (backward must follow its forward)
   const void *fwd_image = nullptr;
@@ -130,6 +131,7 @@ int make_raster(const dags_camera *cam, const dags_raster_cfg *rc_in, Raster *r)
   r->dilation = rc.dilation; r->z_near = rc.z_near;
   r->limx = rc.guard * 0.5f * (float)cam->width / cam->fx;
   r->limy = rc.guard * 0.5f * (float)cam->height / cam->fy;
+  r->log2_alpha_min = log2f(rc.alpha_min);
   return DAGS_OK;
 }
 
@@ -381,7 +383,8 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   if (e == cudaSuccess) {
     ev = tm.begin(DAGS_K_PREPROCESS_BWD, s);
     e = launch_preprocess_bwd(ctx->ws, reinterpret_cast<const float4 *>(gauss), n, n_views, r,
-                              full ? grad_gauss : nullptr, (grad_flags & DAGS_GRAD_POSE) ? grad_pose : nullptr, s);
+                              full ? grad_gauss : nullptr, (grad_flags & DAGS_GRAD_POSE) ? grad_pose : nullptr,
+                              ctx->fused_step, s);
     tm.end(ev, s);
   }
   return cuda_status(e);
@@ -415,10 +418,14 @@ int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_cam
                     double *grad_pose, cudaStream_t s) {
   int rc = splat_forward(ctx, gauss, n, cam, pose, 1, targets, rcfg, lcfg, image, last, loss, s);
   if (rc) return rc;
+  // the pose step runs in the last CTA of the preprocess backward
+  ctx->fused_step.poses = pose;
+  ctx->fused_step.state = adam_state;
+  ctx->fused_step.cfg = *pcfg;
   rc = splat_backward(ctx, gauss, n, cam, pose, 1, targets, rcfg, lcfg, image, last, DAGS_GRAD_POSE, nullptr,
                       grad_pose, s);
-  if (rc) return rc;
-  return pose_step(ctx, pose, grad_pose, adam_state, 1, pcfg, s);
+  ctx->fused_step = PoseStep();
+  return rc;
 }
 
 template <class T>
@@ -445,6 +452,10 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   if (rcfg) rc_v = *rcfg; else dags_default_raster_cfg(&rc_v);
   if (lcfg) lc_v = *lcfg; else dags_default_loss_cfg(&lc_v);
   if (pcfg) pc_v = *pcfg; else dags_default_pose_cfg(&pc_v);
+  for (int k = 0; k < 6; ++k)
+    if (!isfinite(pc_v.lr[k]) || pc_v.lr[k] < 0) return DAGS_E_INVAL;
+  if (!(pc_v.beta1 >= 0 && pc_v.beta1 < 1) || !(pc_v.beta2 >= 0 && pc_v.beta2 < 1) || !(pc_v.eps > 0))
+    return DAGS_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (!use_graph || ctx->timer.on) {
     for (int k = 0; k < iters; ++k) {

@@ -16,6 +16,7 @@ constexpr int kSortSmallCap = 4096;     // per-tile list length sorted in one pa
 constexpr int kSortBigChunk = 16384;    // chunk of the out-of-core merge sort
 constexpr int kPrepBlock = 256;         // threads per preprocess CTA
 constexpr int kBwdPrepBlock = 128;      // threads per preprocess-backward CTA
+constexpr int kBwdPoseBlocks = 608;     // CTAs of the pose-only preprocess backward (4 per SM)
 
 // Status word bits (device).
 constexpr uint32_t kStatusCapacity = 1u;
@@ -36,13 +37,26 @@ enum {
   CNT_N
 };
 
+// Projected Gaussian, 3 float4 per (view, Gaussian):
+//   r0 = {u, v, ex, ey}      centre (px) and half extents of the bounding box
+//                            of the alpha >= alpha_min ellipse
+//   r1 = {a', b', c', lo}    exponent p(d) = a' dx^2 + b' dx dy + c' dy^2 + lo
+//                            in log2 units: alpha = min(alpha_max, 2^p),
+//                            a' = -a log2(e) / 2, b' = -b log2(e),
+//                            c' = -c log2(e) / 2 for the conic (a, b, c), and
+//                            lo = log2(opacity)
+//   r2 = {z, M, rg, bl}      depth, motion probability, colour as the
+//                            record's BF16 bit patterns
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
 struct Workspace {
   int64_t max_n = 0;
   int max_w = 0, max_h = 0, max_v = 0, max_tiles = 0;
   int64_t max_pairs = 0;
   int bwd_prep_blocks = 0;
-  float4 *rec2d = nullptr;        // [V][N][3]: {u, v, z, o}, {a, b, c, M}, {r, g, b, -}
-  uint2 *rect = nullptr;          // [V][N]: {x0 | x1 << 16, y0 | y1 << 16}, tiles [x0, x1) x [y0, y1)
+  float4 *rec2d = nullptr;        // [V][N][3], see above
+  uint2 *rect = nullptr;          // [V][N]: {x0 | x1 << 16, y0 | y1 << 16}, candidate tiles [x0, x1) x [y0, y1)
   float *grad2d = nullptr;        // [V][N][kGradWords]
   uint32_t *tile_count = nullptr; // [V * T]
   uint32_t *tile_start = nullptr; // [V * T + 1]
@@ -62,11 +76,19 @@ struct Raster {
   float fx, fy, cx, cy;
   int W, H, tiles_x, tiles_y, T;   // T = tiles per view
   float alpha_min, alpha_max, t_min, dilation, z_near, limx, limy;
+  float log2_alpha_min;
 };
 
 struct Loss {
   float lambda_pho, lambda_depth, o_eps;
   int weight_mode, weight_grad;
+};
+
+// Optional pose step fused into the end of the preprocess backward.
+struct PoseStep {
+  double *poses = nullptr;     // [V][12], in/out; nullptr: no step
+  double *state = nullptr;     // [V][13]
+  dags_pose_cfg cfg;
 };
 
 // ---- launchers (defined in the .cu files) ----
@@ -82,7 +104,8 @@ cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const R
                               const float4 *targets, const float *image, const int32_t *last, bool full,
                               cudaStream_t s);
 cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int64_t n, int views,
-                                  const Raster &r, float *grad_gauss, double *grad_pose, cudaStream_t s);
+                                  const Raster &r, float *grad_gauss, double *grad_pose, const PoseStep &ps,
+                                  cudaStream_t s);
 cudaError_t launch_pose_step(double *poses, const double *grad, double *state, int views,
                              const dags_pose_cfg &cfg, cudaStream_t s);
 
@@ -194,6 +217,104 @@ __device__ __forceinline__ bool project_gaussian(const float4 &g0, const float4 
   q.u = r.fx * q.x / q.z + r.cx;
   q.v = r.fy * q.y / q.z + r.cy;
   return true;
+}
+
+// Does the ellipse Q(d) = A2 dx^2 + B2 dx dy + C2 dy^2 <= thr (centre (u, v);
+// A2 = -a', B2 = -b', C2 = -c', thr = lo - log2(alpha_min)) reach the
+// pixel-centre rectangle [x0, x1] x [y0, y1]? The minimum of the positive
+// definite Q over the rectangle is 0 if the centre is inside, else it is on
+// an edge, where Q is a 1-D quadratic whose minimiser is clamped to the edge.
+// Every operation is explicitly rounded (no contraction), so that the kernel
+// that counts pairs and the kernel that emits them decide identically.
+__device__ __forceinline__ bool ellipse_reaches_rect(float u, float v, float A2, float B2, float C2, float thr,
+                                                     float x0, float x1, float y0, float y1) {
+  const float xl = __fsub_rn(x0, u), xh = __fsub_rn(x1, u);
+  const float yl = __fsub_rn(y0, v), yh = __fsub_rn(y1, v);
+  if (xl <= 0.f && xh >= 0.f && yl <= 0.f && yh >= 0.f) return true;
+  float best = INFINITY;
+  const float xs[2] = {xl, xh}, ys[2] = {yl, yh};
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float x = xs[k];
+    float y = __fdiv_rn(__fmul_rn(-B2, x), __fmul_rn(2.f, C2));
+    y = fminf(fmaxf(y, yl), yh);
+    float q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A2, x), x), __fmul_rn(__fmul_rn(B2, x), y)),
+                        __fmul_rn(__fmul_rn(C2, y), y));
+    best = fminf(best, q);
+    const float yy = ys[k];
+    float xx = __fdiv_rn(__fmul_rn(-B2, yy), __fmul_rn(2.f, A2));
+    xx = fminf(fmaxf(xx, xl), xh);
+    q = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(A2, xx), xx), __fmul_rn(__fmul_rn(B2, xx), yy)),
+                  __fmul_rn(__fmul_rn(C2, yy), yy));
+    best = fminf(best, q);
+  }
+  return best <= thr;
+}
+
+// FP64 Adam step on the twist of one pose followed by T <- exp(xi^) T, with
+// no transcendental on the common path (GB300's FP64 units are few): the
+// bias corrections beta^k by binary powering, and sin/cos of |phi| < 0.25 by
+// their Taylor series to |phi|^12 (omitted terms below 1e-17).
+__device__ inline double pow_int(double b, double kd) {
+  unsigned long long k = (unsigned long long)kd;
+  double r = 1.0;
+  while (k) {
+    if (k & 1ull) r *= b;
+    b *= b;
+    k >>= 1;
+  }
+  return r;
+}
+
+__device__ inline void pose_adam_exp(double *T, const double *grad, double *st, const dags_pose_cfg &cfg) {
+  const double k = st[12] + 1.0;
+  const double bc1 = 1.0 - pow_int(cfg.beta1, k), bc2 = 1.0 - pow_int(cfg.beta2, k);
+  double xi[6];
+  for (int c = 0; c < 6; ++c) {
+    const double g = grad[c];
+    const double m = cfg.beta1 * st[c] + (1.0 - cfg.beta1) * g;
+    const double s2 = cfg.beta2 * st[6 + c] + (1.0 - cfg.beta2) * g * g;
+    st[c] = m;
+    st[6 + c] = s2;
+    xi[c] = -cfg.lr[c] * (m / bc1) / (sqrt(s2 / bc2) + cfg.eps);
+  }
+  st[12] = k;
+  const double px = xi[3], py = xi[4], pz = xi[5];
+  const double t2 = px * px + py * py + pz * pz;
+  double a, b, c;
+  if (t2 < 0.0625) {
+    // sin(t)/t, (1-cos t)/t^2, (t-sin t)/t^3 as series in t^2
+    a = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880 + t2 * (-1.0 / 39916800 +
+        t2 * (1.0 / 6227020800.0))))));
+    b = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800 + t2 * (-1.0 / 479001600 +
+        t2 * (1.0 / 87178291200.0))))));
+    c = 1.0 / 6 + t2 * (-1.0 / 120 + t2 * (1.0 / 5040 + t2 * (-1.0 / 362880 + t2 * (1.0 / 39916800 +
+        t2 * (-1.0 / 6227020800.0 + t2 * (1.0 / 1307674368000.0))))));
+  } else {
+    const double t = sqrt(t2);
+    a = sin(t) / t;
+    b = (1.0 - cos(t)) / t2;
+    c = (t - sin(t)) / (t2 * t);
+  }
+  const double Kh[9] = {0.0, -pz, py, pz, 0.0, -px, -py, px, 0.0};
+  double K2[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      K2[3 * i + j] = Kh[3 * i] * Kh[j] + Kh[3 * i + 1] * Kh[3 + j] + Kh[3 * i + 2] * Kh[6 + j];
+  double Re[9], V[9];
+  for (int e = 0; e < 9; ++e) {
+    const double I = (e % 4 == 0) ? 1.0 : 0.0;
+    Re[e] = I + a * Kh[e] + b * K2[e];
+    V[e] = I + b * Kh[e] + c * K2[e];
+  }
+  double te[3];
+  for (int i = 0; i < 3; ++i) te[i] = V[3 * i] * xi[0] + V[3 * i + 1] * xi[1] + V[3 * i + 2] * xi[2];
+  double out[12];
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) out[4 * i + j] = Re[3 * i] * T[j] + Re[3 * i + 1] * T[4 + j] + Re[3 * i + 2] * T[8 + j];
+    out[4 * i + 3] = Re[3 * i] * T[3] + Re[3 * i + 1] * T[7] + Re[3 * i + 2] * T[11] + te[i];
+  }
+  for (int e = 0; e < 12; ++e) T[e] = out[e];
 }
 
 }  // namespace dags

@@ -31,17 +31,19 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
   __shared__ uint32_t s_id[kTilePix];
   __shared__ int s_max;
+  const unsigned FULLM = 0xffffffffu;
   const uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
   if (tot > (uint64_t)ws.max_pairs) return;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int v = blockIdx.z;
   const int tile = v * r.T + blockIdx.y * r.tiles_x + blockIdx.x;
-  const int px = blockIdx.x * kTile + (tid % kTile);
-  const int py = blockIdx.y * kTile + (tid / kTile);
+  const int bx0 = blockIdx.x * kTile + (warp & 1) * 8, by0 = blockIdx.y * kTile + (warp >> 1) * 4;
+  const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
   const uint32_t s = ws.tile_start[tile];
   const size_t vbase = (size_t)v * ws.max_n;
   const size_t P = (size_t)r.W * r.H;
+  const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
 
   float T = 1.f;
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;  // upstream per channel
@@ -76,7 +78,7 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   }
   if (tid == 0) s_max = 0;
   __syncthreads();
-  const int wmax = __reduce_max_sync(0xffffffffu, (unsigned)lastp);
+  const int wmax = (int)__reduce_max_sync(FULLM, (unsigned)lastp);
   if (lane == 0) atomicMax(&s_max, wmax);
   __syncthreads();
   const int kmax = s_max;
@@ -95,54 +97,72 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
       s_c[tid] = ws.rec2d[slot * 3 + 2];
     }
     __syncthreads();
-    for (int j = end - beg - 1; j >= 0; --j) {
-      const int k = beg + j;
-      bool contrib = false;
-      float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gz = 0.f;
-      float go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
-      if (k < lastp) {
-        const float4 a = s_a[j], b = s_b[j];
-        const float dx = a.x - fpx, dy = a.y - fpy;
-        const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
-        const float G = __expf(power);
-        const float ag = a.w * G;
-        if (ag >= r.alpha_min) {
-          contrib = true;
-          const float alpha = fminf(r.alpha_max, ag);
-          const float inv = 1.f / (1.f - alpha);
-          T *= inv;                       // transmittance in front of this Gaussian
-          const float wk = alpha * T;
-          const float4 c = s_c[j];
-          const float dal = g0 * (c.x * T - S0 * inv) + g1 * (c.y * T - S1 * inv) +
-                            g2 * (c.z * T - S2 * inv) + g3 * (a.z * T - S3 * inv) +
-                            g4 * (T - S4 * inv) + g5 * (b.w * T - S5 * inv);
-          gz = g3 * wk;
-          if (FULL) { gr = g0 * wk; gg = g1 * wk; gbl = g2 * wk; }
-          if (ag <= r.alpha_max) {
-            const float dpw = dal * alpha;
-            gu = -dpw * (b.x * dx + b.y * dy);
-            gv = -dpw * (b.y * dx + b.z * dy);
-            ga = -0.5f * dpw * dx * dx;
-            gb = -dpw * dx * dy;
-            gc = -0.5f * dpw * dy * dy;
-            if (FULL) go = dal * G;
-          }
-          S0 += c.x * wk; S1 += c.y * wk; S2 += c.z * wk;
-          S3 += a.z * wk; S4 += wk; S5 += b.w * wk;
-        }
+    const int cnt = end - beg;
+    if (wmax <= beg) continue;               // no pixel of this warp reaches this batch
+    for (int g = (cnt - 1) >> 5; g >= 0; --g) {
+      const int jj = g * 32 + lane;
+      bool hit = false;
+      if (jj < cnt) {
+        const float4 a = s_a[jj];
+        hit = fabsf(a.x - bcx) <= a.z + 3.5f && fabsf(a.y - bcy) <= a.w + 1.5f;
       }
-      if (__any_sync(0xffffffffu, contrib)) {
-        gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga);
-        gb = warp_sum(gb); gc = warp_sum(gc); gz = warp_sum(gz);
-        if (FULL) { go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl); }
-        if (lane == 0) {
-          float *dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
-          atomicAdd(dst + G2_U, gu); atomicAdd(dst + G2_V, gv);
-          atomicAdd(dst + G2_A, ga); atomicAdd(dst + G2_B, gb);
-          atomicAdd(dst + G2_C, gc); atomicAdd(dst + G2_Z, gz);
-          if (FULL) {
-            atomicAdd(dst + G2_O, go); atomicAdd(dst + G2_R, gr);
-            atomicAdd(dst + G2_G, gg); atomicAdd(dst + G2_BL, gbl);
+      unsigned mask = __ballot_sync(FULLM, hit);
+      while (mask) {
+        const int bit = 31 - __clz(mask);
+        mask &= ~(1u << bit);
+        const int j = g * 32 + bit;
+        const int k = beg + j;
+        bool contrib = false;
+        float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gz = 0.f;
+        float go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
+        if (k < lastp) {
+          const float4 a = s_a[j], b = s_b[j];
+          const float dx = a.x - fpx, dy = a.y - fpy;
+          const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+          if (p >= r.log2_alpha_min) {
+            contrib = true;
+            const float ag = exp2f(p);
+            const float alpha = fminf(r.alpha_max, ag);
+            const float inv = 1.f / (1.f - alpha);
+            T *= inv;                       // transmittance in front of this Gaussian
+            const float wk = alpha * T;
+            const float4 c = s_c[j];
+            const uint32_t rgb = __float_as_uint(c.z), blb = __float_as_uint(c.w);
+            const float fr = bf16_lo(rgb), fg = bf16_hi(rgb), fb = bf16_lo(blb);
+            const float dal = g0 * (fr * T - S0 * inv) + g1 * (fg * T - S1 * inv) +
+                              g2 * (fb * T - S2 * inv) + g3 * (c.x * T - S3 * inv) +
+                              g4 * (T - S4 * inv) + g5 * (c.y * T - S5 * inv);
+            gz = g3 * wk;
+            if (FULL) { gr = g0 * wk; gg = g1 * wk; gbl = g2 * wk; }
+            if (ag <= r.alpha_max) {
+              // d alpha / d(natural exponent) = alpha; the exponent in log2
+              // units is p, so d/dx of the natural exponent is ln2 * dp/dx
+              const float dpw = dal * alpha;
+              const float hl = dpw * kLn2;
+              gu = hl * (2.f * b.x * dx + b.y * dy);
+              gv = hl * (b.y * dx + 2.f * b.z * dy);
+              ga = -0.5f * dpw * dx * dx;
+              gb = -dpw * dx * dy;
+              gc = -0.5f * dpw * dy * dy;
+              if (FULL) go = dal * exp2f(p - b.w);
+            }
+            S0 += fr * wk; S1 += fg * wk; S2 += fb * wk;
+            S3 += c.x * wk; S4 += wk; S5 += c.y * wk;
+          }
+        }
+        if (__any_sync(FULLM, contrib)) {
+          gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga);
+          gb = warp_sum(gb); gc = warp_sum(gc); gz = warp_sum(gz);
+          if (FULL) { go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl); }
+          if (lane == 0) {
+            float *dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
+            atomicAdd(dst + G2_U, gu); atomicAdd(dst + G2_V, gv);
+            atomicAdd(dst + G2_A, ga); atomicAdd(dst + G2_B, gb);
+            atomicAdd(dst + G2_C, gc); atomicAdd(dst + G2_Z, gz);
+            if (FULL) {
+              atomicAdd(dst + G2_O, go); atomicAdd(dst + G2_R, gr);
+              atomicAdd(dst + G2_G, gg); atomicAdd(dst + G2_BL, gbl);
+            }
           }
         }
       }
@@ -150,157 +170,178 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   }
 }
 
+// Chains the 2D gradients of Gaussian i in view v (pose Pm) to the pose
+// twist (pg, added) and, FULL, to the record's parameters (acc, added).
+template <bool FULL>
+__device__ __forceinline__ void chain_one(const Workspace &ws, const Raster &r, const float4 &g0, const float4 &g1,
+                                          const float4 &g2, const float *Pm, size_t slot, float *pg, float *acc) {
+  const uint2 rc = ws.rect[slot];
+  Proj q;
+  if (!((rc.x >> 16) > (rc.x & 0xFFFF)) || !project_gaussian(g0, g1, g2, Pm, r, q)) return;
+  const float *gd = ws.grad2d + slot * kGradWords;
+  const float4 ga4 = *reinterpret_cast<const float4 *>(gd);
+  const float4 gb4 = *reinterpret_cast<const float4 *>(gd + 4);
+  const float gu = ga4.x, gv = ga4.y, gA = ga4.z, gB = ga4.w, gC = gb4.x, gzz = gb4.y;
+  // conic -> 2D covariance: dS = -Q Gq Q with Gq the symmetric-matrix form of
+  // the conic gradient (the off-diagonal appears twice in the quadratic form)
+  const float qa = q.ca, qb = q.cb, qc = q.cc;
+  const float h = 0.5f * gB;
+  const float t00 = qa * gA + qb * h, t01 = qa * h + qb * gC;
+  const float t10 = qb * gA + qc * h, t11 = qb * h + qc * gC;
+  const float d00 = -(t00 * qa + t01 * qb);
+  const float d01 = -(t00 * qb + t01 * qc);
+  const float d11 = -(t10 * qb + t11 * qc);
+  // Sigma' = M2 M2^T + d I with M2 = J K: dM2 = 2 dS M2
+  float dm0[3], dm1[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    dm0[s] = 2.f * (d00 * q.m0[s] + d01 * q.m1[s]);
+    dm1[s] = 2.f * (d01 * q.m0[s] + d11 * q.m1[s]);
+  }
+  const float dj00 = dm0[0] * q.K[0] + dm0[1] * q.K[1] + dm0[2] * q.K[2];
+  const float dj02 = dm0[0] * q.K[6] + dm0[1] * q.K[7] + dm0[2] * q.K[8];
+  const float dj11 = dm1[0] * q.K[3] + dm1[1] * q.K[4] + dm1[2] * q.K[5];
+  const float dj12 = dm1[0] * q.K[6] + dm1[1] * q.K[7] + dm1[2] * q.K[8];
+  float dK[9];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    dK[s] = q.j00 * dm0[s];
+    dK[3 + s] = q.j11 * dm1[s];
+    dK[6 + s] = q.j02 * dm0[s] + q.j12 * dm1[s];
+  }
+  // camera-space mean
+  const float z = q.z, iz = 1.f / z, iz2 = iz * iz;
+  float dpx = gu * r.fx * iz;
+  float dpy = gv * r.fy * iz;
+  float dpz = -gu * r.fx * q.x * iz2 - gv * r.fy * q.y * iz2 + gzz;
+  dpz += -dj00 * r.fx * iz2 - dj11 * r.fy * iz2;
+  const bool clx = q.txz > r.limx || q.txz < -r.limx;
+  const bool cly = q.tyz > r.limy || q.tyz < -r.limy;
+  if (!clx) { dpx += -dj02 * r.fx * iz2; dpz += dj02 * 2.f * r.fx * q.x * iz2 * iz; }
+  else { dpz += dj02 * r.fx * q.tx * iz2; }
+  if (!cly) { dpy += -dj12 * r.fy * iz2; dpz += dj12 * 2.f * r.fy * q.y * iz2 * iz; }
+  else { dpz += dj12 * r.fy * q.ty * iz2; }
+  // pose twist (left perturbation): rho += dp, phi += p x dp + the covariance
+  // term from K' = (I + [phi]x) K: B = K dK^T
+  pg[0] += dpx; pg[1] += dpy; pg[2] += dpz;
+  pg[3] += q.y * dpz - z * dpy;
+  pg[4] += z * dpx - q.x * dpz;
+  pg[5] += q.x * dpy - q.y * dpx;
+  float Bm[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      Bm[3 * a + b] = q.K[3 * a] * dK[3 * b] + q.K[3 * a + 1] * dK[3 * b + 1] + q.K[3 * a + 2] * dK[3 * b + 2];
+  pg[3] += Bm[5] - Bm[7];
+  pg[4] += Bm[6] - Bm[2];
+  pg[5] += Bm[1] - Bm[3];
+  if (FULL) {
+    const float4 gc4 = *reinterpret_cast<const float4 *>(gd + 8);
+    const float go = gb4.z;
+    acc[0] += Pm[0] * dpx + Pm[4] * dpy + Pm[8] * dpz;
+    acc[1] += Pm[1] * dpx + Pm[5] * dpy + Pm[9] * dpz;
+    acc[2] += Pm[2] * dpx + Pm[6] * dpy + Pm[10] * dpz;
+    acc[3] += go * q.o * (1.f - q.o);
+    // K = R M, M = Rq diag(S): dM = R^T dK
+    float dRq[9];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      float dS = 0.f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float dM = Pm[a] * dK[s] + Pm[4 + a] * dK[3 + s] + Pm[8 + a] * dK[6 + s];
+        dS += q.Rq[3 * a + s] * dM;
+        dRq[3 * a + s] = dM * q.S[s];
+      }
+      acc[8 + s] += dS * q.S[s];
+    }
+    const float w = q.nq[0], x = q.nq[1], y = q.nq[2], zq = q.nq[3];
+    const float dn0 = -2.f * zq * dRq[1] + 2.f * y * dRq[2] + 2.f * zq * dRq[3] - 2.f * x * dRq[5] -
+                      2.f * y * dRq[6] + 2.f * x * dRq[7];
+    const float dn1 = 2.f * y * dRq[1] + 2.f * zq * dRq[2] + 2.f * y * dRq[3] - 4.f * x * dRq[4] -
+                      2.f * w * dRq[5] + 2.f * zq * dRq[6] + 2.f * w * dRq[7] - 4.f * x * dRq[8];
+    const float dn2 = -4.f * y * dRq[0] + 2.f * x * dRq[1] + 2.f * w * dRq[2] + 2.f * x * dRq[3] +
+                      2.f * zq * dRq[5] - 2.f * w * dRq[6] + 2.f * zq * dRq[7] - 4.f * y * dRq[8];
+    const float dn3 = -4.f * zq * dRq[0] - 2.f * w * dRq[1] + 2.f * x * dRq[2] + 2.f * w * dRq[3] -
+                      4.f * zq * dRq[4] + 2.f * y * dRq[5] + 2.f * x * dRq[6] + 2.f * y * dRq[7];
+    const float ndn = w * dn0 + x * dn1 + y * dn2 + zq * dn3;
+    const float iq = 1.f / q.qlen;
+    acc[4] += (dn0 - w * ndn) * iq;
+    acc[5] += (dn1 - x * ndn) * iq;
+    acc[6] += (dn2 - y * ndn) * iq;
+    acc[7] += (dn3 - zq * ndn) * iq;
+    acc[12] += gb4.w;   // colour: slots G2_R, G2_G, G2_BL
+    acc[13] += gc4.x;
+    acc[14] += gc4.y;
+  }
+}
+
+// Sums pg[6] over the CTA and stores the FP64 partial of (view v, CTA b).
+__device__ __forceinline__ void store_pose_partial(const Workspace &ws, float *pg, int v, int b, int nb,
+                                                   float (*s_red)[6]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const float t = warp_sum(pg[c]);
+    if (lane == 0) s_red[wid][c] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    float t = 0.f;
+    for (int w = 0; w < kBwdPrepBlock / 32; ++w) t += s_red[w][threadIdx.x];
+    ws.pose_partial[((size_t)v * nb + b) * 6 + threadIdx.x] = (double)t;
+  }
+  __syncthreads();
+}
+
+// FULL: one thread per Gaussian, all views, parameter gradients written.
+// !FULL (pose only): a fixed grid strides over the Gaussians of each view.
+// The last CTA sums the pose partials in a fixed order in FP64 (one warp per
+// twist component) and, if ps.poses is set, applies the pose step.
 template <bool FULL>
 __global__ void __launch_bounds__(kBwdPrepBlock)
 preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, int views, Raster r,
-                      float *__restrict__ grad_gauss, double *__restrict__ grad_pose) {
+                      float *__restrict__ grad_gauss, double *__restrict__ grad_pose, PoseStep ps) {
   __shared__ float sp[kMaxViewsSmem * 12];
   __shared__ float s_red[kBwdPrepBlock / 32][6];
   __shared__ int s_last;
   for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = ws.pose32[k];
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
-  if (i < n) {
-    g0 = __ldg(gauss + 4 * i + 0);
-    g1 = __ldg(gauss + 4 * i + 1);
-    g2 = __ldg(gauss + 4 * i + 2);
-    g3 = __ldg(gauss + 4 * i + 3);
-  }
-  float acc[16];
-#pragma unroll
-  for (int k = 0; k < 16; ++k) acc[k] = 0.f;
-
-  for (int v = 0; v < views; ++v) {
-    float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    const float *Pm = sp + v * 12;
+  const int nb = gridDim.x;
+  if (FULL) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
     if (i < n) {
-      const size_t slot = (size_t)v * ws.max_n + i;
-      const uint2 rc = ws.rect[slot];
-      Proj q;
-      if ((rc.x >> 16) > (rc.x & 0xFFFF) && project_gaussian(g0, g1, g2, Pm, r, q)) {
-        const float *gd = ws.grad2d + slot * kGradWords;
-        const float4 ga4 = *reinterpret_cast<const float4 *>(gd);
-        const float4 gb4 = *reinterpret_cast<const float4 *>(gd + 4);
-        const float gu = ga4.x, gv = ga4.y, gA = ga4.z, gB = ga4.w, gC = gb4.x, gzz = gb4.y;
-        // conic -> 2D covariance: dS = -Q Gq Q with Gq the symmetric-matrix
-        // form of the conic gradient (off-diagonal counted twice in the form)
-        const float qa = q.ca, qb = q.cb, qc = q.cc;
-        const float h = 0.5f * gB;
-        const float t00 = qa * gA + qb * h, t01 = qa * h + qb * gC;
-        const float t10 = qb * gA + qc * h, t11 = qb * h + qc * gC;
-        const float d00 = -(t00 * qa + t01 * qb);
-        const float d01 = -(t00 * qb + t01 * qc);
-        const float d11 = -(t10 * qb + t11 * qc);
-        // Sigma' = M2 M2^T + d I, M2 = J K: dM2 = 2 dS M2
-        float dm0[3], dm1[3];
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          dm0[s] = 2.f * (d00 * q.m0[s] + d01 * q.m1[s]);
-          dm1[s] = 2.f * (d01 * q.m0[s] + d11 * q.m1[s]);
-        }
-        const float dj00 = dm0[0] * q.K[0] + dm0[1] * q.K[1] + dm0[2] * q.K[2];
-        const float dj02 = dm0[0] * q.K[6] + dm0[1] * q.K[7] + dm0[2] * q.K[8];
-        const float dj11 = dm1[0] * q.K[3] + dm1[1] * q.K[4] + dm1[2] * q.K[5];
-        const float dj12 = dm1[0] * q.K[6] + dm1[1] * q.K[7] + dm1[2] * q.K[8];
-        float dK[9];
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-          dK[s] = q.j00 * dm0[s];
-          dK[3 + s] = q.j11 * dm1[s];
-          dK[6 + s] = q.j02 * dm0[s] + q.j12 * dm1[s];
-        }
-        // camera-space mean
-        const float z = q.z, iz = 1.f / z, iz2 = iz * iz;
-        float dpx = gu * r.fx * iz;
-        float dpy = gv * r.fy * iz;
-        float dpz = -gu * r.fx * q.x * iz2 - gv * r.fy * q.y * iz2 + gzz;
-        dpz += -dj00 * r.fx * iz2 - dj11 * r.fy * iz2;
-        const bool clx = q.txz > r.limx || q.txz < -r.limx;
-        const bool cly = q.tyz > r.limy || q.tyz < -r.limy;
-        if (!clx) { dpx += -dj02 * r.fx * iz2; dpz += dj02 * 2.f * r.fx * q.x * iz2 * iz; }
-        else { dpz += dj02 * r.fx * q.tx * iz2; }
-        if (!cly) { dpy += -dj12 * r.fy * iz2; dpz += dj12 * 2.f * r.fy * q.y * iz2 * iz; }
-        else { dpz += dj12 * r.fy * q.ty * iz2; }
-        // pose twist (left perturbation): rho += dp, phi += p x dp + covariance
-        // term from K' = (I + [phi]x) K: B = K dK^T
-        pg[0] = dpx; pg[1] = dpy; pg[2] = dpz;
-        pg[3] = q.y * dpz - z * dpy;
-        pg[4] = z * dpx - q.x * dpz;
-        pg[5] = q.x * dpy - q.y * dpx;
-        float Bm[9];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b)
-            Bm[3 * a + b] = q.K[3 * a] * dK[3 * b] + q.K[3 * a + 1] * dK[3 * b + 1] + q.K[3 * a + 2] * dK[3 * b + 2];
-        pg[3] += Bm[5] - Bm[7];
-        pg[4] += Bm[6] - Bm[2];
-        pg[5] += Bm[1] - Bm[3];
-        if (FULL) {
-          const float4 gc4 = *reinterpret_cast<const float4 *>(gd + 8);
-          const float go = gb4.z;
-          // mean: p = R mu + t
-          acc[0] += Pm[0] * dpx + Pm[4] * dpy + Pm[8] * dpz;
-          acc[1] += Pm[1] * dpx + Pm[5] * dpy + Pm[9] * dpz;
-          acc[2] += Pm[2] * dpx + Pm[6] * dpy + Pm[10] * dpz;
-          acc[3] += go * q.o * (1.f - q.o);
-          // K = R M, M = Rq diag(S): dM = R^T dK
-          float dRq[9];
-#pragma unroll
-          for (int s = 0; s < 3; ++s) {
-            float dS = 0.f;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float dM = Pm[a] * dK[s] + Pm[4 + a] * dK[3 + s] + Pm[8 + a] * dK[6 + s];
-              dS += q.Rq[3 * a + s] * dM;
-              dRq[3 * a + s] = dM * q.S[s];
-            }
-            acc[8 + s] += dS * q.S[s];
-          }
-          const float w = q.nq[0], x = q.nq[1], y = q.nq[2], zq = q.nq[3];
-          const float dn0 = -2.f * zq * dRq[1] + 2.f * y * dRq[2] + 2.f * zq * dRq[3] - 2.f * x * dRq[5] -
-                            2.f * y * dRq[6] + 2.f * x * dRq[7];
-          const float dn1 = 2.f * y * dRq[1] + 2.f * zq * dRq[2] + 2.f * y * dRq[3] - 4.f * x * dRq[4] -
-                            2.f * w * dRq[5] + 2.f * zq * dRq[6] + 2.f * w * dRq[7] - 4.f * x * dRq[8];
-          const float dn2 = -4.f * y * dRq[0] + 2.f * x * dRq[1] + 2.f * w * dRq[2] + 2.f * x * dRq[3] +
-                            2.f * zq * dRq[5] - 2.f * w * dRq[6] + 2.f * zq * dRq[7] - 4.f * y * dRq[8];
-          const float dn3 = -4.f * zq * dRq[0] - 2.f * w * dRq[1] + 2.f * x * dRq[2] + 2.f * w * dRq[3] -
-                            4.f * zq * dRq[4] + 2.f * y * dRq[5] + 2.f * x * dRq[6] + 2.f * y * dRq[7];
-          const float ndn = w * dn0 + x * dn1 + y * dn2 + zq * dn3;
-          const float iq = 1.f / q.qlen;
-          acc[4] += (dn0 - w * ndn) * iq;
-          acc[5] += (dn1 - x * ndn) * iq;
-          acc[6] += (dn2 - y * ndn) * iq;
-          acc[7] += (dn3 - zq * ndn) * iq;
-          acc[12] += gb4.w;   // colour: slots G2_R, G2_G, G2_BL
-          acc[13] += gc4.x;
-          acc[14] += gc4.y;
-        }
-      }
+      g0 = __ldg(gauss + 4 * i + 0);
+      g1 = __ldg(gauss + 4 * i + 1);
+      g2 = __ldg(gauss + 4 * i + 2);
     }
-    if (grad_pose) {
+    float acc[16];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const float t = warp_sum(pg[c]);
-        if (lane == 0) s_red[wid][c] = t;
-      }
-      __syncthreads();
-      if (tid < 6) {
-        float t = 0.f;
-        for (int w = 0; w < kBwdPrepBlock / 32; ++w) t += s_red[w][tid];
-        ws.pose_partial[((size_t)v * gridDim.x + blockIdx.x) * 6 + tid] = (double)t;
-      }
-      __syncthreads();
+    for (int k = 0; k < 16; ++k) acc[k] = 0.f;
+    for (int v = 0; v < views; ++v) {
+      float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (i < n) chain_one<true>(ws, r, g0, g1, g2, sp + v * 12, (size_t)v * ws.max_n + i, pg, acc);
+      if (grad_pose) store_pose_partial(ws, pg, v, blockIdx.x, nb, s_red);
     }
-  }
-  if (FULL && i < n) {
-    float4 *out = reinterpret_cast<float4 *>(grad_gauss + 16 * i);
-    out[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    out[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-    out[2] = make_float4(acc[8], acc[9], acc[10], 0.f);
-    out[3] = make_float4(acc[12], acc[13], acc[14], 0.f);
+    if (i < n) {
+      float4 *out = reinterpret_cast<float4 *>(grad_gauss + 16 * i);
+      out[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+      out[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+      out[2] = make_float4(acc[8], acc[9], acc[10], 0.f);
+      out[3] = make_float4(acc[12], acc[13], acc[14], 0.f);
+    }
+  } else {
+    for (int v = 0; v < views; ++v) {
+      float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n; i += (int64_t)nb * blockDim.x) {
+        const float4 g0 = __ldg(gauss + 4 * i + 0), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
+        chain_one<false>(ws, r, g0, g1, g2, sp + v * 12, (size_t)v * ws.max_n + i, pg, nullptr);
+      }
+      store_pose_partial(ws, pg, v, blockIdx.x, nb, s_red);
+    }
   }
   if (!grad_pose) return;
   __threadfence();
@@ -312,23 +353,21 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // Fixed-order FP64 sum of the per-CTA partials of each view.
-  __shared__ double s_d[kBwdPrepBlock];
-  const int nb = gridDim.x;
-  for (int v = 0; v < views; ++v)
-    for (int c = 0; c < 6; ++c) {
-      double a = 0.0;
-      for (int b = tid; b < nb; b += kBwdPrepBlock) a += __ldcg(ws.pose_partial + ((size_t)v * nb + b) * 6 + c);
-      s_d[tid] = a;
-      __syncthreads();
-      for (int o = kBwdPrepBlock / 2; o > 0; o >>= 1) {
-        if (tid < o) s_d[tid] += s_d[tid + o];
-        __syncthreads();
-      }
-      if (tid == 0) grad_pose[v * 6 + c] = s_d[0];
-      __syncthreads();
-    }
+  // one warp per (view, component): lane-strided partial sums in a fixed
+  // order, then a fixed shuffle tree
+  for (int vc = wid; vc < views * 6; vc += kBwdPrepBlock / 32) {
+    const int v = vc / 6, c = vc % 6;
+    double a = 0.0;
+    for (int b = lane; b < nb; b += 32) a += __ldcg(ws.pose_partial + ((size_t)v * nb + b) * 6 + c);
+    a = warp_sum_d(a);
+    if (lane == 0) grad_pose[v * 6 + c] = a;
+  }
+  __syncthreads();
   if (tid == 0) ws.counters[CNT_DONE_BWDPREP] = 0u;
+  if (ps.poses) {
+    __threadfence_block();
+    if (tid < views) pose_adam_exp(ps.poses + 12 * tid, grad_pose + 6 * tid, ps.state + 13 * tid, ps.cfg);
+  }
 }
 
 }  // namespace
@@ -344,14 +383,18 @@ cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const R
 }
 
 cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int64_t n, int views,
-                                  const Raster &r, float *grad_gauss, double *grad_pose, cudaStream_t s) {
+                                  const Raster &r, float *grad_gauss, double *grad_pose, const PoseStep &ps,
+                                  cudaStream_t s) {
   if (views > kMaxViewsSmem) return cudaErrorInvalidValue;
   const unsigned gx = (unsigned)((n + kBwdPrepBlock - 1) / kBwdPrepBlock);
-  const unsigned grid = gx > 0 ? gx : 1u;
-  if (grad_gauss)
-    preprocess_bwd_kernel<true><<<grid, kBwdPrepBlock, 0, s>>>(ws, gauss, n, views, r, grad_gauss, grad_pose);
-  else
-    preprocess_bwd_kernel<false><<<grid, kBwdPrepBlock, 0, s>>>(ws, gauss, n, views, r, grad_gauss, grad_pose);
+  unsigned grid = gx > 0 ? gx : 1u;
+  if (grad_gauss) {
+    preprocess_bwd_kernel<true><<<grid, kBwdPrepBlock, 0, s>>>(ws, gauss, n, views, r, grad_gauss, grad_pose, ps);
+  } else {
+    // pose only: a fixed grid of kBwdPoseBlocks CTAs strides over the Gaussians
+    if (grid > (unsigned)kBwdPoseBlocks) grid = kBwdPoseBlocks;
+    preprocess_bwd_kernel<false><<<grid, kBwdPrepBlock, 0, s>>>(ws, gauss, n, views, r, grad_gauss, grad_pose, ps);
+  }
   return cudaGetLastError();
 }
 

@@ -1,21 +1,29 @@
 // Forward half of the MP-aware splatting path (sm_103a).
 //
 //   preprocess_kernel   per (view, Gaussian): camera transform, EWA 2D
-//                       covariance, conic, opacity, opacity-aware bounding
-//                       radius, tile rect; counts pairs per tile; the last
+//                       covariance, conic, opacity, the bounding box of the
+//                       alpha >= alpha_min ellipse; each warp then walks the
+//                       candidate tiles of its 32 Gaussians together, keeps
+//                       the tiles the ellipse reaches and counts them per tile
+//                       with one atomic per distinct tile per warp; the last
 //                       CTA scans the counts into tile offsets.
-//   emit_kernel         writes (depth bits << 32 | id) keys into per-tile
-//                       buckets (order inside a bucket is arbitrary).
+//   emit_kernel         the same warp-cooperative walk, writing (depth bits
+//                       << 32 | id) keys into per-tile buckets (order inside a
+//                       bucket is arbitrary).
 //   tile_sort_kernel    sorts each bucket in shared memory (bitonic) and
 //                       writes the depth-ordered Gaussian ids; oversized
 //                       buckets are queued for tile_sort_big_kernel, which
 //                       sorts 16k-key chunks in shared memory and merges them.
-//   render_fwd_kernel   one CTA per 16x16 tile: front-to-back alpha
-//                       compositing of colour, depth, opacity and MP with the
-//                       tile's sorted list staged through shared memory, warp
-//                       and CTA early exit on transmittance, and the static
-//                       weight and MP-weighted L1 loss of Eqs. (20)-(22) in
-//                       the epilogue; the last CTA sums the loss in FP64.
+//   render_fwd_kernel   one CTA per 16x16 tile, one warp per 8x4 pixel block:
+//                       the tile's sorted list is staged through shared memory
+//                       in batches of 256; each warp keeps (by ballot) only the
+//                       entries whose ellipse box meets its block, tests alpha
+//                       in the exponent before exponentiating, and leaves when
+//                       all its pixels are saturated (the CTA when all warps
+//                       are); front-to-back compositing of colour, depth,
+//                       opacity and MP, and the static weight and MP-weighted
+//                       L1 loss of Eqs. (20)-(22) in the epilogue; the last
+//                       CTA sums the loss in FP64.
 #include "common.cuh"
 
 namespace dags {
@@ -74,6 +82,76 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
   return s_carry;
 }
 
+// The 32 lanes of a warp walk the candidate tiles of their 32 Gaussians
+// together: lane l takes candidate c = base + l of the warp's concatenated
+// candidate lists, finds its owner by binary search over the warp's
+// inclusive prefix of candidate counts, and tests whether the owner's
+// ellipse reaches that tile. EMIT = false: the kept pairs are counted per
+// tile (one atomic per distinct tile per warp); EMIT = true: each kept pair
+// gets a slot in its tile's bucket the same way and its key is written.
+template <bool EMIT>
+__device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r, int v, uint32_t id, uint2 rect,
+                                           float4 r0, float4 r1, float zkey) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int x0 = rect.x & 0xFFFF, x1 = rect.x >> 16, y0 = rect.y & 0xFFFF, y1 = rect.y >> 16;
+  const int cw = x1 - x0;
+  const int m = (x1 > x0 && y1 > y0) ? cw * (y1 - y0) : 0;
+  int incl = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(FULL, incl, 31);
+  const float thr = r1.w - r.log2_alpha_min;
+  const int vbase = v * r.T;
+  for (int base = 0; base < total; base += 32) {
+    const int c = base + lane;
+    int owner = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const int cand = owner + step;
+      if (__shfl_sync(FULL, incl, cand - 1) <= c) owner = cand;
+    }
+    owner = min(owner, 31);
+    const int o_incl = __shfl_sync(FULL, incl, owner);
+    const int o_m = __shfl_sync(FULL, m, owner);
+    const int o_x0 = __shfl_sync(FULL, x0, owner), o_y0 = __shfl_sync(FULL, y0, owner);
+    const int o_cw = __shfl_sync(FULL, cw, owner);
+    const float u = __shfl_sync(FULL, r0.x, owner), vv = __shfl_sync(FULL, r0.y, owner);
+    const float A2 = -__shfl_sync(FULL, r1.x, owner), B2 = -__shfl_sync(FULL, r1.y, owner);
+    const float C2 = -__shfl_sync(FULL, r1.z, owner), th = __shfl_sync(FULL, thr, owner);
+    const uint32_t o_id = __shfl_sync(FULL, id, owner);
+    const float o_z = __shfl_sync(FULL, zkey, owner);
+    bool keep = false;
+    uint32_t key = 0xFFFFFFFFu;
+    if (c < total) {
+      const int k = c - (o_incl - o_m);
+      const int tx = o_x0 + k % o_cw, ty = o_y0 + k / o_cw;
+      const float px0 = (float)(tx * kTile), py0 = (float)(ty * kTile);
+      const float px1 = (float)min(tx * kTile + kTile - 1, r.W - 1);
+      const float py1 = (float)min(ty * kTile + kTile - 1, r.H - 1);
+      keep = ellipse_reaches_rect(u, vv, A2, B2, C2, th, px0, px1, py0, py1);
+      if (keep) key = (uint32_t)(vbase + ty * r.tiles_x + tx);
+    }
+    const unsigned grp = __match_any_sync(FULL, key);
+    const int leader = __ffs(grp) - 1;
+    if (!EMIT) {
+      if (keep && lane == leader) atomicAdd(ws.tile_count + key, (uint32_t)__popc(grp));
+    } else {
+      uint32_t basepos = 0;
+      if (keep && lane == leader) basepos = atomicAdd(ws.tile_cursor + key, (uint32_t)__popc(grp));
+      basepos = __shfl_sync(FULL, basepos, leader);
+      if (keep) {
+        const uint32_t dst = ws.tile_start[key] + basepos + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+        if (dst < ws.tile_start[key + 1])
+          ws.keys[dst] = ((uint64_t)__float_as_uint(o_z) << 32) | (uint64_t)o_id;
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kPrepBlock)
 preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
@@ -86,6 +164,8 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
 
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint2 my_rect = make_uint2(0u, 0u);
+  float4 my_r0 = make_float4(0.f, 0.f, 0.f, 0.f), my_r1 = my_r0;
   if (i < n) {
     const float *P = sp + v * 12;
     const size_t slot = (size_t)v * ws.max_n + i;
@@ -98,39 +178,34 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
 
     float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
     uint2 rect = make_uint2(0u, 0u);
-    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     Proj q;
     if (project_gaussian(g0, g1, g2, P, r, q)) {
-      // Outside |d| <= sqrt(2 lambda_max ln(o / alpha_min)) the Gaussian's
-      // alpha is below alpha_min: that radius bounds its footprint.
-      const float mid = 0.5f * (q.A + q.C);
-      const float disc = 0.25f * (q.A - q.C) * (q.A - q.C) + q.B * q.B;
-      const float lmax = mid + sqrtf(fmaxf(disc, 0.1f));
-      const float rext = sqrtf(2.f * lmax * logf(q.o / r.alpha_min));
-      const float rad = ceilf(rext);
+      const float lo = log2f(q.o);
+      const float thr = lo - r.log2_alpha_min;             // ellipse: Q(d) <= thr
+      const float cnat = 2.f * kLn2 * thr;                 // 2 ln(o / alpha_min)
+      const float ex = sqrtf(cnat * q.A), ey = sqrtf(cnat * q.C);
       const float inv_tile = 1.f / (float)kTile;
-      x0 = clampi(floorf((q.u - rad) * inv_tile), 0, r.tiles_x);
-      y0 = clampi(floorf((q.v - rad) * inv_tile), 0, r.tiles_y);
-      x1 = clampi(floorf((q.u + rad) * inv_tile) + 1.f, 0, r.tiles_x);
-      y1 = clampi(floorf((q.v + rad) * inv_tile) + 1.f, 0, r.tiles_y);
-      if (x1 > x0 && y1 > y0 && isfinite(q.u) && isfinite(q.v)) {
-        o0 = make_float4(q.u, q.v, q.z, q.o);
-        o1 = make_float4(q.ca, q.cb, q.cc, g2.w);
-        const uint32_t cw0 = __float_as_uint(g3.x), cw1 = __float_as_uint(g3.y);
-        o2 = make_float4(bf16_lo(cw0), bf16_hi(cw0), bf16_lo(cw1), 0.f);
+      const int x0 = clampi(floorf((q.u - ex) * inv_tile), 0, r.tiles_x);
+      const int y0 = clampi(floorf((q.v - ey) * inv_tile), 0, r.tiles_y);
+      const int x1 = clampi(floorf((q.u + ex) * inv_tile) + 1.f, 0, r.tiles_x);
+      const int y1 = clampi(floorf((q.v + ey) * inv_tile) + 1.f, 0, r.tiles_y);
+      if (thr > 0.f && x1 > x0 && y1 > y0 && isfinite(q.u) && isfinite(q.v)) {
+        o0 = make_float4(q.u, q.v, ex, ey);
+        o1 = make_float4(-0.5f * kLog2e * q.ca, -kLog2e * q.cb, -0.5f * kLog2e * q.cc, lo);
+        o2 = make_float4(q.z, g2.w, g3.x, g3.y);
         rect = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
-      } else {
-        x0 = y0 = x1 = y1 = 0;
       }
     }
     ws.rec2d[slot * 3 + 0] = o0;
     ws.rec2d[slot * 3 + 1] = o1;
     ws.rec2d[slot * 3 + 2] = o2;
     ws.rect[slot] = rect;
-    uint32_t *cnt = ws.tile_count + (size_t)v * r.T;
-    for (int ty = y0; ty < y1; ++ty)
-      for (int tx = x0; tx < x1; ++tx) atomicAdd(cnt + ty * r.tiles_x + tx, 1u);
+    my_rect = rect;
+    my_r0 = o0;
+    my_r1 = o1;
   }
+  // Warp-cooperative walk over the candidate tiles of the warp's Gaussians.
+  walk_tiles<false>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, 0.f);
 
   // The last CTA to finish turns the per-tile counts into offsets.
   __threadfence();
@@ -163,22 +238,18 @@ __global__ void __launch_bounds__(kPrepBlock)
 emit_kernel(Workspace ws, int64_t n, Raster r) {
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   if (pairs_overflow(ws, 0)) return;
-  const size_t slot = (size_t)v * ws.max_n + i;
-  const uint2 rc = ws.rect[slot];
-  const int x0 = rc.x & 0xFFFF, x1 = rc.x >> 16, y0 = rc.y & 0xFFFF, y1 = rc.y >> 16;
-  if (x1 <= x0 || y1 <= y0) return;
-  const float z = ws.rec2d[slot * 3].z;
-  const uint64_t key = ((uint64_t)__float_as_uint(z) << 32) | (uint64_t)(uint32_t)i;
-  const int base = v * r.T;
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx) {
-      const int t = base + ty * r.tiles_x + tx;
-      const uint32_t pos = atomicAdd(ws.tile_cursor + t, 1u);
-      const uint32_t dst = ws.tile_start[t] + pos;
-      if (dst < ws.tile_start[t + 1]) ws.keys[dst] = key;
-    }
+  uint2 rect = make_uint2(0u, 0u);
+  float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+  float z = 0.f;
+  if (i < n) {
+    const size_t slot = (size_t)v * ws.max_n + i;
+    rect = ws.rect[slot];
+    r0 = ws.rec2d[slot * 3 + 0];
+    r1 = ws.rec2d[slot * 3 + 1];
+    z = ws.rec2d[slot * 3 + 2].x;
+  }
+  walk_tiles<true>(ws, r, v, (uint32_t)(i < n ? i : 0), rect, r0, r1, z);
 }
 
 // Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
@@ -284,16 +355,19 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
   __shared__ float s_red[kTilePix / 32];
   __shared__ int s_last;
-  const int tid = threadIdx.x;
+  const unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int v = blockIdx.z;
   const int tile = v * r.T + blockIdx.y * r.tiles_x + blockIdx.x;
-  const int px = blockIdx.x * kTile + (tid % kTile);
-  const int py = blockIdx.y * kTile + (tid / kTile);
+  // warp w covers the 8x4 pixel block (w % 2, w / 2) of the tile
+  const int bx0 = blockIdx.x * kTile + (warp & 1) * 8, by0 = blockIdx.y * kTile + (warp >> 1) * 4;
+  const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
   const bool ovf = pairs_overflow(ws, views * r.T);
   const uint32_t s = ovf ? 0u : ws.tile_start[tile];
   const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
   const size_t vbase = (size_t)v * ws.max_n;
+  const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, oo = 0.f, rm = 0.f;
   int lastk = 0;
@@ -310,23 +384,36 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kTilePix, e - base);
-    if (!done) {
-      for (int j = 0; j < cnt; ++j) {
+    if (__all_sync(FULL, done)) continue;
+    for (int g = 0; g < 8 && g * 32 < cnt; ++g) {
+      // entries whose ellipse box meets this warp's pixel block
+      const int jj = g * 32 + lane;
+      bool hit = false;
+      if (jj < cnt) {
+        const float4 a = s_a[jj];
+        hit = fabsf(a.x - bcx) <= a.z + 3.5f && fabsf(a.y - bcy) <= a.w + 1.5f;
+      }
+      unsigned mask = __ballot_sync(FULL, hit);
+      while (mask) {
+        const int j = g * 32 + __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (done) continue;
         const float4 a = s_a[j], b = s_b[j];
         const float dx = a.x - fpx, dy = a.y - fpy;
-        const float power = -0.5f * (b.x * dx * dx + b.z * dy * dy) - b.y * dx * dy;
-        const float ag = a.w * __expf(power);
-        if (ag < r.alpha_min) continue;
-        const float alpha = fminf(r.alpha_max, ag);
+        const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+        if (p < r.log2_alpha_min) continue;               // alpha < alpha_min
+        const float alpha = fminf(r.alpha_max, exp2f(p));
         const float tt = T * (1.f - alpha);
-        if (tt < r.t_min) { done = true; break; }
+        if (tt < r.t_min) { done = true; continue; }
         const float w = alpha * T;
         const float4 c = s_c[j];
-        cr += c.x * w; cg += c.y * w; cb += c.z * w;
-        dd += a.z * w; oo += w; rm += b.w * w;
+        const uint32_t rg = __float_as_uint(c.z), bl = __float_as_uint(c.w);
+        cr += bf16_lo(rg) * w; cg += bf16_hi(rg) * w; cb += bf16_lo(bl) * w;
+        dd += c.x * w; oo += w; rm += c.y * w;
         T = tt;
         lastk = (int)(base - s) + j + 1;
       }
+      if (__all_sync(FULL, done)) break;
     }
   }
 

@@ -12,6 +12,10 @@ import oracle
 #  Elementwise rendered values therefore get rtol 2e-4 with a small absolute
 #  floor; the image as a whole (per channel, L2) must agree to 1e-5.
 IMG_RTOL, IMG_ATOL, IMG_NORM = 2e-4, 2e-6, 1e-5
+# The final transmittance is a product of (1 - alpha) factors: its relative
+# error is the sum of alpha/(1 - alpha) times each alpha's relative error,
+# up to ~1e-4 behind a few near-opaque layers; normwise it gets 1e-4.
+T_NORM = 1e-4
 GRAD_NORM = 1e-4          # per parameter group, L2, relative
 POSE_REL = 1e-4           # pose twist gradient, L2, relative
 LOSS_REL = 1e-5

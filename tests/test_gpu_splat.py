@@ -6,8 +6,8 @@ import oracle
 from oracle import pose as opose
 from paper_2602_21644_gb300 import synth
 
-from gpu_common import (GRAD_NORM, IMG_NORM, LOSS_REL, POSE_REL, compare_grads, compare_image, image_rows,
-                        mask_flagged_targets, oracle_views, to_dev)
+from gpu_common import (GRAD_NORM, IMG_NORM, LOSS_REL, POSE_REL, T_NORM, compare_grads, compare_image,
+                        image_rows, mask_flagged_targets, oracle_views, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +49,7 @@ def assert_image_parity(res, outs, label, report):
         worst, nflag = compare_image(image_rows(res["image"][v]), ref["pix"], ref["flags"], report, f"{label} v{v}")
         for c, (mx, nrm, bad) in worst.items():
             assert bad == 0, f"{label} view {v} channel {c}: {bad} pixels beyond tolerance (max {mx:.3e})"
-            assert nrm <= IMG_NORM, f"{label} view {v} channel {c}: normwise {nrm:.3e}"
+            assert nrm <= (T_NORM if c == 6 else IMG_NORM), f"{label} view {v} channel {c}: normwise {nrm:.3e}"
 
 
 def assert_bins_match(res, sc, dags, views_outs=None):
