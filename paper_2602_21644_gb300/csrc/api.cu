@@ -97,7 +97,7 @@ cudaError_t alloc(T **p, size_t count) {
 void free_ws(Workspace &w) {
   void *ptrs[] = {w.rec2d, w.rect, w.grad2d, w.tile_count, w.tile_start, w.tile_cursor, w.keys,
                   w.keys_tmp, w.sorted_ids, w.big_tiles, w.loss_partial, w.pose_partial, w.pose32,
-                  w.counters};
+                  w.vis_ids, w.vis_append, w.vis_n, w.counters};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -242,10 +242,15 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&w.loss_partial, vt));
   A(alloc(&w.pose_partial, (size_t)w.bwd_prep_blocks * w.max_v * 6));
   A(alloc(&w.pose32, (size_t)w.max_v * 12));
+  A(alloc(&w.vis_ids, vn));
+  A(alloc(&w.vis_append, (size_t)w.max_v));
+  A(alloc(&w.vis_n, (size_t)w.max_v));
   A(alloc(&w.counters, (size_t)CNT_N));
   if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.counters, 0, CNT_N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(w.vis_append, 0, (size_t)w.max_v * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(w.vis_n, 0, (size_t)w.max_v * sizeof(uint32_t));
   if (e == cudaSuccess) e = configure_fwd_kernels();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {

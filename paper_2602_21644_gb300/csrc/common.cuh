@@ -68,6 +68,9 @@ struct Workspace {
   float *loss_partial = nullptr;  // [V * T]
   double *pose_partial = nullptr; // [bwd_prep_blocks][V][6]
   float *pose32 = nullptr;        // [V][12] FP32 copy of the poses of the last forward
+  uint32_t *vis_ids = nullptr;    // [V][N] ids of the Gaussians with a non-empty candidate range
+  uint32_t *vis_append = nullptr; // [V] append cursors (zero between calls)
+  uint32_t *vis_n = nullptr;      // [V] visible counts of the last forward
   uint32_t *counters = nullptr;   // [CNT_N]
 };
 
@@ -251,6 +254,39 @@ __device__ __forceinline__ bool ellipse_reaches_rect(float u, float v, float A2,
   return best <= thr;
 }
 
+// Reduce-scatter of 8 values over the 32 lanes of a warp: 4 + 2 + 1 + 1 + 1
+// shuffles instead of 8 x 5. On return, lane l holds in x the full warp sum
+// of component ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1)
+// (lanes differing only in bits 0-1 hold the same sum).
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
+  const unsigned F = 0xffffffffu;
+  const bool h16 = (lane & 16) != 0;
+  float a[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = h16 ? v[i + 4] : v[i];
+    const float send = h16 ? v[i] : v[i + 4];
+    a[i] = keep + __shfl_xor_sync(F, send, 16);
+  }
+  const bool h8 = (lane & 8) != 0;
+  float b[2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = h8 ? a[i + 2] : a[i];
+    const float send = h8 ? a[i] : a[i + 2];
+    b[i] = keep + __shfl_xor_sync(F, send, 8);
+  }
+  const bool h4 = (lane & 4) != 0;
+  float c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(F, h4 ? b[0] : b[1], 4);
+  c += __shfl_xor_sync(F, c, 2);
+  c += __shfl_xor_sync(F, c, 1);
+  return c;
+}
+
+__device__ __forceinline__ int scatter8_component(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
 // FP64 Adam step on the twist of one pose followed by T <- exp(xi^) T, with
 // no transcendental on the common path (GB300's FP64 units are few): the
 // bias corrections beta^k by binary powering, and sin/cos of |phi| < 0.25 by
@@ -315,6 +351,65 @@ __device__ inline void pose_adam_exp(double *T, const double *grad, double *st, 
     out[4 * i + 3] = Re[3 * i] * T[3] + Re[3 * i + 1] * T[7] + Re[3 * i + 2] * T[11] + te[i];
   }
   for (int e = 0; e < 12; ++e) T[e] = out[e];
+}
+
+// The same pose step spread over the first 12 threads of a CTA (dependent
+// FP64 chains are what costs on GB300): threads 0-5 update one twist
+// component's Adam moments each, thread 0 the scalar series, threads 0-11
+// one entry of the new 3x4 pose each. Must be called by all threads of the
+// CTA (it synchronises); xi_s, sc_s are shared scratch of 6 and 3 doubles.
+__device__ inline void pose_adam_exp_cta(double *T, const double *grad, double *st, const dags_pose_cfg &cfg,
+                                         double *xi_s, double *sc_s) {
+  const int t = threadIdx.x;
+  const double k = st[12] + 1.0;
+  if (t < 6) {
+    const double bc1 = 1.0 - pow_int(cfg.beta1, k), bc2 = 1.0 - pow_int(cfg.beta2, k);
+    const double g = grad[t];
+    const double m = cfg.beta1 * st[t] + (1.0 - cfg.beta1) * g;
+    const double s2 = cfg.beta2 * st[6 + t] + (1.0 - cfg.beta2) * g * g;
+    st[t] = m;
+    st[6 + t] = s2;
+    xi_s[t] = -cfg.lr[t] * (m / bc1) / (sqrt(s2 / bc2) + cfg.eps);
+  }
+  __syncthreads();
+  if (t == 0) {
+    st[12] = k;
+    const double t2 = xi_s[3] * xi_s[3] + xi_s[4] * xi_s[4] + xi_s[5] * xi_s[5];
+    double a, b, c;
+    if (t2 < 0.0625) {
+      a = 1.0 + t2 * (-1.0 / 6 + t2 * (1.0 / 120 + t2 * (-1.0 / 5040 + t2 * (1.0 / 362880 + t2 * (-1.0 / 39916800 +
+          t2 * (1.0 / 6227020800.0))))));
+      b = 0.5 + t2 * (-1.0 / 24 + t2 * (1.0 / 720 + t2 * (-1.0 / 40320 + t2 * (1.0 / 3628800 + t2 * (-1.0 / 479001600 +
+          t2 * (1.0 / 87178291200.0))))));
+      c = 1.0 / 6 + t2 * (-1.0 / 120 + t2 * (1.0 / 5040 + t2 * (-1.0 / 362880 + t2 * (1.0 / 39916800 +
+          t2 * (-1.0 / 6227020800.0 + t2 * (1.0 / 1307674368000.0))))));
+    } else {
+      const double th = sqrt(t2);
+      a = sin(th) / th;
+      b = (1.0 - cos(th)) / t2;
+      c = (th - sin(th)) / (t2 * th);
+    }
+    sc_s[0] = a; sc_s[1] = b; sc_s[2] = c;
+  }
+  __syncthreads();
+  double out = 0.0;
+  if (t < 12) {
+    const int i = t >> 2, j = t & 3;
+    const double px = xi_s[3], py = xi_s[4], pz = xi_s[5];
+    const double Kh[9] = {0.0, -pz, py, pz, 0.0, -px, -py, px, 0.0};
+    double Re[3], V[3];
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+      const double K2 = Kh[3 * i] * Kh[kk] + Kh[3 * i + 1] * Kh[3 + kk] + Kh[3 * i + 2] * Kh[6 + kk];
+      const double I = (i == kk) ? 1.0 : 0.0;
+      Re[kk] = I + sc_s[0] * Kh[3 * i + kk] + sc_s[1] * K2;
+      V[kk] = I + sc_s[1] * Kh[3 * i + kk] + sc_s[2] * K2;
+    }
+    out = Re[0] * T[j] + Re[1] * T[4 + j] + Re[2] * T[8 + j];
+    if (j == 3) out += V[0] * xi_s[0] + V[1] * xi_s[1] + V[2] * xi_s[2];
+  }
+  __syncthreads();
+  if (t < 12) T[t] = out;
 }
 
 }  // namespace dags

@@ -151,18 +151,17 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
           }
         }
         if (__any_sync(FULLM, contrib)) {
-          gu = warp_sum(gu); gv = warp_sum(gv); ga = warp_sum(ga);
-          gb = warp_sum(gb); gc = warp_sum(gc); gz = warp_sum(gz);
-          if (FULL) { go = warp_sum(go); gr = warp_sum(gr); gg = warp_sum(gg); gbl = warp_sum(gbl); }
-          if (lane == 0) {
-            float *dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
-            atomicAdd(dst + G2_U, gu); atomicAdd(dst + G2_V, gv);
-            atomicAdd(dst + G2_A, ga); atomicAdd(dst + G2_B, gb);
-            atomicAdd(dst + G2_C, gc); atomicAdd(dst + G2_Z, gz);
-            if (FULL) {
-              atomicAdd(dst + G2_O, go); atomicAdd(dst + G2_R, gr);
-              atomicAdd(dst + G2_G, gg); atomicAdd(dst + G2_BL, gbl);
-            }
+          // reduce-scatter over the warp; lanes 0, 4, ..., 28 then hold one
+          // component's sum each and add it with one atomic
+          float* dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
+          const int comp = scatter8_component(lane);
+          const float v8[8] = {gu, gv, ga, gb, gc, gz, go, gr};
+          const float sum8 = warp_reduce_scatter8(v8, lane);
+          if ((lane & 3) == 0 && (FULL || comp < 6)) atomicAdd(dst + comp, sum8);
+          if (FULL) {
+            const float w8[8] = {gg, gbl, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float sum2 = warp_reduce_scatter8(w8, lane);
+            if ((lane & 3) == 0 && comp < 2) atomicAdd(dst + G2_G + comp, sum2);
           }
         }
       }
@@ -334,9 +333,14 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       out[3] = make_float4(acc[12], acc[13], acc[14], 0.f);
     }
   } else {
+    // pose only: the visible Gaussians of each view (the others have no
+    // 2D gradient)
     for (int v = 0; v < views; ++v) {
       float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + tid; i < n; i += (int64_t)nb * blockDim.x) {
+      const int64_t nv = ws.vis_n[v];
+      const uint32_t *vis = ws.vis_ids + (size_t)v * ws.max_n;
+      for (int64_t k = (int64_t)blockIdx.x * blockDim.x + tid; k < nv; k += (int64_t)nb * blockDim.x) {
+        const int64_t i = vis[k];
         const float4 g0 = __ldg(gauss + 4 * i + 0), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
         chain_one<false>(ws, r, g0, g1, g2, sp + v * 12, (size_t)v * ws.max_n + i, pg, nullptr);
       }
@@ -344,15 +348,16 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     }
   }
   if (!grad_pose) return;
-  __threadfence();
+  // last CTA: barrier, then one thread's fence and counter increment
   __syncthreads();
   if (tid == 0) {
+    __threadfence();
     const unsigned t = atomicAdd(ws.counters + CNT_DONE_BWDPREP, 1u);
     s_last = (t == gridDim.x - 1);
+    if (s_last) __threadfence();
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   // one warp per (view, component): lane-strided partial sums in a fixed
   // order, then a fixed shuffle tree
   for (int vc = wid; vc < views * 6; vc += kBwdPrepBlock / 32) {
@@ -365,8 +370,9 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   __syncthreads();
   if (tid == 0) ws.counters[CNT_DONE_BWDPREP] = 0u;
   if (ps.poses) {
-    __threadfence_block();
-    if (tid < views) pose_adam_exp(ps.poses + 12 * tid, grad_pose + 6 * tid, ps.state + 13 * tid, ps.cfg);
+    __shared__ double s_xi[6], s_sc[3];
+    for (int v = 0; v < views; ++v)
+      pose_adam_exp_cta(ps.poses + 12 * v, grad_pose + 6 * v, ps.state + 13 * v, ps.cfg, s_xi, s_sc);
   }
 }
 

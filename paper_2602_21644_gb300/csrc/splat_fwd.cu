@@ -38,48 +38,45 @@ __device__ __forceinline__ int clampi(float x, int lo, int hi) {
   return c != c ? lo : (int)c;
 }
 
-// Exclusive scan of `total` uint32 counts by one CTA, in rounds of blockDim.
+// Exclusive scan of `total` uint32 counts by one CTA in one round: each
+// thread scans a contiguous chunk, the chunk sums are scanned across the CTA.
 // Also clears the counts and cursors for the next call. Returns the sum.
 __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total) {
-  __shared__ uint32_t warp_tot[32];
-  __shared__ uint64_t s_carry;
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long s_total;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  if (tid == 0) s_carry = 0;
+  const int per = (total + blockDim.x - 1) / blockDim.x;
+  const int b = min(total, tid * per), e = min(total, b + per);
+  unsigned long long mine = 0;
+  for (int k = b; k < e; ++k) mine += __ldcg(count + k);
+  unsigned long long inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[wid] = inc;
   __syncthreads();
-  for (int base = 0; base < total; base += blockDim.x) {
-    int idx = base + tid;
-    uint32_t val = idx < total ? __ldcg(count + idx) : 0u;
-    uint32_t inc = val;
+  if (wid == 0) {
+    unsigned long long t = lane < nw ? warp_tot[lane] : 0ull;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
     }
-    if (lane == 31) warp_tot[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-      uint32_t t = lane < nw ? warp_tot[lane] : 0u;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      if (lane < nw) warp_tot[lane] = t;  // inclusive warp prefix
-    }
-    __syncthreads();
-    uint32_t before = (wid > 0 ? warp_tot[wid - 1] : 0u) + inc - val;
-    uint64_t carry = s_carry;
-    if (idx < total) {
-      uint64_t st = carry + before;
-      start[idx] = (uint32_t)(st > 0xFFFFFFFFull ? 0xFFFFFFFFull : st);
-      count[idx] = 0u;
-      cursor[idx] = 0u;
-    }
-    __syncthreads();
-    if (tid == 0) s_carry = carry + warp_tot[nw - 1];
-    __syncthreads();
+    if (lane < nw) warp_tot[lane] = t;
+    if (lane == nw - 1) s_total = t;
   }
-  return s_carry;
+  __syncthreads();
+  unsigned long long run = (wid > 0 ? warp_tot[wid - 1] : 0ull) + inc - mine;
+  for (int k = b; k < e; ++k) {
+    const uint32_t c = __ldcg(count + k);
+    start[k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
+    run += c;
+    count[k] = 0u;
+    cursor[k] = 0u;
+  }
+  return s_total;
 }
 
 // The 32 lanes of a warp walk the candidate tiles of their 32 Gaussians
@@ -204,20 +201,38 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     my_r0 = o0;
     my_r1 = o1;
   }
+  // Visible Gaussians (non-empty candidate range) are appended to the view's
+  // list, one atomic per warp.
+  {
+    const bool visible = (my_rect.x >> 16) > (my_rect.x & 0xFFFF);
+    const unsigned ball = __ballot_sync(0xffffffffu, visible);
+    const int lane = threadIdx.x & 31;
+    uint32_t basev = 0;
+    if (ball && lane == __ffs(ball) - 1) basev = atomicAdd(ws.vis_append + v, (uint32_t)__popc(ball));
+    basev = __shfl_sync(0xffffffffu, basev, __ffs(ball | 1u) - 1);
+    if (visible)
+      ws.vis_ids[(size_t)v * ws.max_n + basev + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+  }
   // Warp-cooperative walk over the candidate tiles of the warp's Gaussians.
   walk_tiles<false>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, 0.f);
 
-  // The last CTA to finish turns the per-tile counts into offsets.
-  __threadfence();
+  // The last CTA to finish turns the per-tile counts into offsets (CTA
+  // barrier, then one thread's fence and counter increment publish the
+  // whole CTA's atomics).
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     unsigned int t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
     s_last = (t == gridDim.x * gridDim.y - 1);
+    if (s_last) __threadfence();
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T);
+  for (int k = threadIdx.x; k < views; k += blockDim.x) {
+    ws.vis_n[k] = __ldcg(ws.vis_append + k);
+    ws.vis_append[k] = 0u;
+  }
   if (threadIdx.x == 0) {
     ws.tile_start[views * r.T] = (uint32_t)(total > 0xFFFFFFFFull ? 0xFFFFFFFFull : total);
     ws.counters[CNT_REQ_LO] = (uint32_t)total;
@@ -239,17 +254,22 @@ emit_kernel(Workspace ws, int64_t n, Raster r) {
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (pairs_overflow(ws, 0)) return;
+  const int64_t nv = ws.vis_n[v];
+  if ((int64_t)blockIdx.x * blockDim.x >= nv) return;   // whole CTA past the visible list
   uint2 rect = make_uint2(0u, 0u);
   float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
   float z = 0.f;
-  if (i < n) {
-    const size_t slot = (size_t)v * ws.max_n + i;
+  uint32_t id = 0;
+  if (i < nv) {
+    id = ws.vis_ids[(size_t)v * ws.max_n + i];
+    const size_t slot = (size_t)v * ws.max_n + id;
     rect = ws.rect[slot];
     r0 = ws.rec2d[slot * 3 + 0];
     r1 = ws.rec2d[slot * 3 + 1];
     z = ws.rec2d[slot * 3 + 2].x;
   }
-  walk_tiles<true>(ws, r, v, (uint32_t)(i < n ? i : 0), rect, r0, r1, z);
+  walk_tiles<true>(ws, r, v, id, rect, r0, r1, z);
+  (void)n;
 }
 
 // Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
@@ -446,10 +466,10 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     __threadfence();
     unsigned int done_ctas = atomicAdd(ws.counters + CNT_DONE_RENDER, 1u);
     s_last = (done_ctas == gridDim.x * gridDim.y * gridDim.z - 1);
+    if (s_last) __threadfence();
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
   // Deterministic FP64 sum of the per-tile partials: fixed strided
   // assignment, then a fixed tree.
   __shared__ double s_d[kTilePix];
