@@ -96,7 +96,7 @@ cudaError_t alloc(T **p, size_t count) {
 
 void free_ws(Workspace &w) {
   void *ptrs[] = {w.rec2d, w.rect, w.grad2d, w.tile_count, w.tile_start, w.tile_cursor, w.keys,
-                  w.keys_tmp, w.sorted_ids, w.big_tiles, w.loss_partial, w.pose_partial, w.pose32,
+                  w.keys_tmp, w.sorted_ids, w.tile_order, w.loss_partial, w.pose_partial, w.pose32,
                   w.vis_ids, w.vis_append, w.vis_n, w.counters};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -238,7 +238,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&w.keys, (size_t)max_pairs));
   A(alloc(&w.keys_tmp, (size_t)max_pairs));
   A(alloc(&w.sorted_ids, (size_t)max_pairs));
-  A(alloc(&w.big_tiles, vt));
+  A(alloc(&w.tile_order, vt));
   A(alloc(&w.loss_partial, vt));
   A(alloc(&w.pose_partial, (size_t)w.bwd_prep_blocks * w.max_v * 6));
   A(alloc(&w.pose32, (size_t)w.max_v * 12));
@@ -251,7 +251,6 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   if (e == cudaSuccess) e = cudaMemset(w.counters, 0, CNT_N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.vis_append, 0, (size_t)w.max_v * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.vis_n, 0, (size_t)w.max_v * sizeof(uint32_t));
-  if (e == cudaSuccess) e = configure_fwd_kernels();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? DAGS_E_NOMEM : DAGS_E_CUDA;
@@ -318,11 +317,6 @@ int splat_forward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camer
   if (e == cudaSuccess && n > 0) {
     ev = tm.begin(DAGS_K_EMIT, s);
     e = launch_emit(w, n, n_views, r, s);
-    tm.end(ev, s);
-  }
-  if (e == cudaSuccess) {
-    ev = tm.begin(DAGS_K_TILE_SORT, s);
-    e = launch_tile_sort(w, n_views, r, s);
     tm.end(ev, s);
   }
   if (e == cudaSuccess) {

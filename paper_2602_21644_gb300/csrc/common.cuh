@@ -12,8 +12,7 @@ namespace dags {
 constexpr int kTile = 16;               // tile edge in pixels
 constexpr int kTilePix = kTile * kTile; // pixels (= threads) per render CTA
 constexpr int kGradWords = 12;          // per (view, Gaussian) 2D gradient slots
-constexpr int kSortSmallCap = 4096;     // per-tile list length sorted in one pass
-constexpr int kSortBigChunk = 16384;    // chunk of the out-of-core merge sort
+constexpr int kSortSmallCap = 1024;     // tile lists up to this length are sorted by the render CTA
 constexpr int kPrepBlock = 256;         // threads per preprocess CTA
 constexpr int kBwdPrepBlock = 128;      // threads per preprocess-backward CTA
 constexpr int kBwdPoseBlocks = 608;     // CTAs of the pose-only preprocess backward (4 per SM)
@@ -30,7 +29,7 @@ enum {
   CNT_DONE_PREP = 0,   // CTAs of the preprocess kernel that finished
   CNT_DONE_RENDER,     // CTAs of the forward render that finished
   CNT_DONE_BWDPREP,    // CTAs of the preprocess backward that finished
-  CNT_BIG_TILES,       // tiles whose lists exceed kSortSmallCap
+  CNT_UNUSED,
   CNT_STATUS,          // status bits
   CNT_REQ_LO,          // pairs required by the last forward (low / high word)
   CNT_REQ_HI,
@@ -64,7 +63,7 @@ struct Workspace {
   uint64_t *keys = nullptr;       // [max_pairs]: depth bits << 32 | Gaussian id
   uint64_t *keys_tmp = nullptr;   // [max_pairs]: merge ping-pong
   uint32_t *sorted_ids = nullptr; // [max_pairs]
-  uint32_t *big_tiles = nullptr;  // [V * T]
+  uint32_t *tile_order = nullptr; // [V * T] tiles by descending list length (launch order of the renders)
   float *loss_partial = nullptr;  // [V * T]
   double *pose_partial = nullptr; // [bwd_prep_blocks][V][6]
   float *pose32 = nullptr;        // [V][12] FP32 copy of the poses of the last forward
@@ -95,11 +94,9 @@ struct PoseStep {
 };
 
 // ---- launchers (defined in the .cu files) ----
-cudaError_t configure_fwd_kernels();  // once per device, at context creation
 cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t n, const double *poses,
                               int views, const Raster &r, int zero_grad_words, cudaStream_t s);
 cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s);
-cudaError_t launch_tile_sort(const Workspace &ws, int views, const Raster &r, cudaStream_t s);
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s);

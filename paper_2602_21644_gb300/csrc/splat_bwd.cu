@@ -35,9 +35,10 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   const uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
   if (tot > (uint64_t)ws.max_pairs) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int v = blockIdx.z;
-  const int tile = v * r.T + blockIdx.y * r.tiles_x + blockIdx.x;
-  const int bx0 = blockIdx.x * kTile + (warp & 1) * 8, by0 = blockIdx.y * kTile + (warp >> 1) * 4;
+  const int tile = (int)ws.tile_order[blockIdx.x];   // longest lists first
+  const int v = tile / r.T, tv = tile - v * r.T;
+  const int tx = tv % r.tiles_x, ty = tv / r.tiles_x;
+  const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
   const uint32_t s = ws.tile_start[tile];
@@ -382,7 +383,7 @@ cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const R
                               const float4 *targets, const float *image, const int32_t *last, bool full,
                               cudaStream_t s) {
   (void)n;
-  dim3 grid((unsigned)r.tiles_x, (unsigned)r.tiles_y, (unsigned)views);
+  const unsigned grid = (unsigned)(views * r.T);
   if (full) render_bwd_kernel<true><<<grid, kTilePix, 0, s>>>(ws, r, l, targets, image, last);
   else render_bwd_kernel<false><<<grid, kTilePix, 0, s>>>(ws, r, l, targets, image, last);
   return cudaGetLastError();

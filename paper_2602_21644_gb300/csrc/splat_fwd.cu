@@ -10,12 +10,12 @@
 //   emit_kernel         the same warp-cooperative walk, writing (depth bits
 //                       << 32 | id) keys into per-tile buckets (order inside a
 //                       bucket is arbitrary).
-//   tile_sort_kernel    sorts each bucket in shared memory (bitonic) and
-//                       writes the depth-ordered Gaussian ids; oversized
-//                       buckets are queued for tile_sort_big_kernel, which
-//                       sorts 16k-key chunks in shared memory and merges them.
-//   render_fwd_kernel   one CTA per 16x16 tile, one warp per 8x4 pixel block:
-//                       the tile's sorted list is staged through shared memory
+//   render_fwd_kernel   one CTA per 16x16 tile (launched longest list first),
+//                       one warp per 8x4 pixel block: the CTA first sorts its
+//                       tile's bucket (bitonic in shared memory; long buckets
+//                       in 1024-key chunks merged through global memory) and
+//                       writes the depth-ordered ids for the backward; the
+//                       list is then staged through shared memory
 //                       in batches of 256; each warp keeps (by ballot) only the
 //                       entries whose ellipse box meets its block, tests alpha
 //                       in the exponent before exponentiating, and leaves when
@@ -41,14 +41,25 @@ __device__ __forceinline__ int clampi(float x, int lo, int hi) {
 // Exclusive scan of `total` uint32 counts by one CTA in one round: each
 // thread scans a contiguous chunk, the chunk sums are scanned across the CTA.
 // Also clears the counts and cursors for the next call. Returns the sum.
-__device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total) {
+// Also writes order[]: the tiles by descending list length (coarsely, by
+// floor(log2(length)); empty tiles last), the launch order of the renders so
+// that long tiles start first.
+__device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total,
+                                     uint32_t *order) {
   __shared__ unsigned long long warp_tot[32];
   __shared__ unsigned long long s_total;
+  __shared__ uint32_t s_bin[34];
+  if (threadIdx.x < 34) s_bin[threadIdx.x] = 0u;
+  __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   const int per = (total + blockDim.x - 1) / blockDim.x;
   const int b = min(total, tid * per), e = min(total, b + per);
   unsigned long long mine = 0;
-  for (int k = b; k < e; ++k) mine += __ldcg(count + k);
+  for (int k = b; k < e; ++k) {
+    const uint32_t c = __ldcg(count + k);
+    mine += c;
+    atomicAdd(&s_bin[c ? 31 - __clz(c) : 32], 1u);   // bin = floor(log2(c)), 32 = empty
+  }
   unsigned long long inc = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -67,12 +78,19 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
     if (lane < nw) warp_tot[lane] = t;
     if (lane == nw - 1) s_total = t;
   }
+  if (threadIdx.x == 0) {
+    // bins in descending length: 31, 30, ..., 0, then empty (32)
+    uint32_t run = 0;
+    for (int bb = 31; bb >= 0; --bb) { const uint32_t c = s_bin[bb]; s_bin[bb] = run; run += c; }
+    s_bin[32] = run;
+  }
   __syncthreads();
   unsigned long long run = (wid > 0 ? warp_tot[wid - 1] : 0ull) + inc - mine;
   for (int k = b; k < e; ++k) {
     const uint32_t c = __ldcg(count + k);
     start[k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
     run += c;
+    order[atomicAdd(&s_bin[c ? 31 - __clz(c) : 32], 1u)] = (uint32_t)k;
     count[k] = 0u;
     cursor[k] = 0u;
   }
@@ -170,8 +188,6 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     float4 g1 = __ldg(gauss + 4 * i + 1);
     float4 g2 = __ldg(gauss + 4 * i + 2);
     float4 g3 = __ldg(gauss + 4 * i + 3);
-    float4 *gz = reinterpret_cast<float4 *>(ws.grad2d + slot * kGradWords);
-    for (int w = 0; w < zero_words / 4; ++w) gz[w] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
     uint2 rect = make_uint2(0u, 0u);
@@ -193,9 +209,15 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
         rect = make_uint2((uint32_t)x0 | ((uint32_t)x1 << 16), (uint32_t)y0 | ((uint32_t)y1 << 16));
       }
     }
-    ws.rec2d[slot * 3 + 0] = o0;
-    ws.rec2d[slot * 3 + 1] = o1;
-    ws.rec2d[slot * 3 + 2] = o2;
+    // invisible Gaussians only need their empty rect: nothing reads their
+    // projected record or 2D gradient
+    if ((rect.x >> 16) > (rect.x & 0xFFFF)) {
+      ws.rec2d[slot * 3 + 0] = o0;
+      ws.rec2d[slot * 3 + 1] = o1;
+      ws.rec2d[slot * 3 + 2] = o2;
+      float4 *gz = reinterpret_cast<float4 *>(ws.grad2d + slot * kGradWords);
+      for (int w = 0; w < zero_words / 4; ++w) gz[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     ws.rect[slot] = rect;
     my_rect = rect;
     my_r0 = o0;
@@ -209,7 +231,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     const int lane = threadIdx.x & 31;
     uint32_t basev = 0;
     if (ball && lane == __ffs(ball) - 1) basev = atomicAdd(ws.vis_append + v, (uint32_t)__popc(ball));
-    basev = __shfl_sync(0xffffffffu, basev, __ffs(ball | 1u) - 1);
+    basev = __shfl_sync(0xffffffffu, basev, ball ? __ffs(ball) - 1 : 0);
     if (visible)
       ws.vis_ids[(size_t)v * ws.max_n + basev + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
   }
@@ -228,7 +250,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   }
   __syncthreads();
   if (!s_last) return;
-  const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T);
+  const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T, ws.tile_order);
   for (int k = threadIdx.x; k < views; k += blockDim.x) {
     ws.vis_n[k] = __ldcg(ws.vis_append + k);
     ws.vis_append[k] = 0u;
@@ -238,7 +260,6 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     ws.counters[CNT_REQ_LO] = (uint32_t)total;
     ws.counters[CNT_REQ_HI] = (uint32_t)(total >> 32);
     if (total > (uint64_t)ws.max_pairs) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
-    ws.counters[CNT_BIG_TILES] = 0u;
     ws.counters[CNT_DONE_PREP] = 0u;
   }
 }
@@ -294,25 +315,6 @@ __device__ __forceinline__ int next_pow2(int x) {
   return p;
 }
 
-__global__ void __launch_bounds__(256)
-tile_sort_kernel(Workspace ws, int entries) {
-  __shared__ uint64_t sk[kSortSmallCap];
-  const int tile = blockIdx.x;
-  if (pairs_overflow(ws, entries)) return;
-  const uint32_t s = ws.tile_start[tile], e = ws.tile_start[tile + 1];
-  const int len = (int)(e - s);
-  if (len == 0) return;
-  if (len > kSortSmallCap) {
-    if (threadIdx.x == 0) ws.big_tiles[atomicAdd(ws.counters + CNT_BIG_TILES, 1u)] = (uint32_t)tile;
-    return;
-  }
-  const int len2 = next_pow2(len);
-  for (int k = threadIdx.x; k < len2; k += blockDim.x) sk[k] = k < len ? ws.keys[s + k] : ~0ull;
-  __syncthreads();
-  bitonic_smem(sk, len2);
-  for (int k = threadIdx.x; k < len; k += blockDim.x) ws.sorted_ids[s + k] = (uint32_t)sk[k];
-}
-
 // Merge sorted runs a[0, la) and b[0, lb) into out[0, la + lb) with the CTA
 // (merge path: each thread finds its split by binary search, then merges its
 // slice sequentially). Keys are unique within a tile.
@@ -336,26 +338,52 @@ __device__ void merge_runs(const uint64_t *a, int la, const uint64_t *b, int lb,
   }
 }
 
-__global__ void __launch_bounds__(1024)
-tile_sort_big_kernel(Workspace ws, int entries) {
-  extern __shared__ uint64_t sbig[];
-  if (pairs_overflow(ws, entries)) return;
-  const uint32_t nbig = ws.counters[CNT_BIG_TILES];
-  for (uint32_t b = blockIdx.x; b < nbig; b += gridDim.x) {
-    const uint32_t tile = ws.big_tiles[b];
-    const uint32_t s = ws.tile_start[tile], e = ws.tile_start[tile + 1];
-    const int len = (int)(e - s);
+__global__ void __launch_bounds__(kTilePix)
+render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
+                  float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
+  __shared__ uint64_t s_key[kSortSmallCap];
+  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
+  __shared__ float s_red[kTilePix / 32];
+  __shared__ int s_last;
+  const unsigned FULL = 0xffffffffu;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool ovf = pairs_overflow(ws, views * r.T);
+  // blocks are launched in order of descending list length
+  const int tile = ovf ? (int)blockIdx.x : (int)ws.tile_order[blockIdx.x];
+  const int v = tile / r.T, tv = tile - v * r.T;
+  const int tx = tv % r.tiles_x, ty = tv / r.tiles_x;
+  // warp w covers the 8x4 pixel block (w % 2, w / 2) of the tile
+  const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
+  const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
+  const bool inside = px < r.W && py < r.H;
+  const uint32_t s = ovf ? 0u : ws.tile_start[tile];
+  const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
+  const size_t vbase = (size_t)v * ws.max_n;
+  const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
+
+  // depth-sort the tile's bucket and publish the order for the backward: in
+  // shared memory up to kSortSmallCap keys, else out of core (chunks sorted in
+  // shared memory, then merged pairwise through global memory)
+  const int len = (int)(e - s);
+  const bool own_sort = len <= kSortSmallCap;
+  if (own_sort && len > 0) {
+    const int len2 = next_pow2(len);
+    for (int k = tid; k < len2; k += kTilePix) s_key[k] = k < len ? ws.keys[s + k] : ~0ull;
+    __syncthreads();
+    bitonic_smem(s_key, len2);
+    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)s_key[k];
+  } else if (len > 0) {
     uint64_t *src = ws.keys + s, *dst = ws.keys_tmp + s;
-    for (int c0 = 0; c0 < len; c0 += kSortBigChunk) {
-      const int cl = min(kSortBigChunk, len - c0);
+    for (int c0 = 0; c0 < len; c0 += kSortSmallCap) {
+      const int cl = min(kSortSmallCap, len - c0);
       const int cl2 = next_pow2(cl);
-      for (int k = threadIdx.x; k < cl2; k += blockDim.x) sbig[k] = k < cl ? src[c0 + k] : ~0ull;
+      for (int k = tid; k < cl2; k += kTilePix) s_key[k] = k < cl ? src[c0 + k] : ~0ull;
       __syncthreads();
-      bitonic_smem(sbig, cl2);
-      for (int k = threadIdx.x; k < cl; k += blockDim.x) src[c0 + k] = sbig[k];
+      bitonic_smem(s_key, cl2);
+      for (int k = tid; k < cl; k += kTilePix) src[c0 + k] = s_key[k];
       __syncthreads();
     }
-    for (int width = kSortBigChunk; width < len; width <<= 1) {
+    for (int width = kSortSmallCap; width < len; width <<= 1) {
       for (int lo = 0; lo < len; lo += 2 * width) {
         const int la = min(width, len - lo);
         const int lb = max(0, min(width, len - lo - width));
@@ -364,30 +392,9 @@ tile_sort_big_kernel(Workspace ws, int entries) {
       __syncthreads();
       uint64_t *t = src; src = dst; dst = t;
     }
-    for (int k = threadIdx.x; k < len; k += blockDim.x) ws.sorted_ids[s + k] = (uint32_t)src[k];
+    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)src[k];
     __syncthreads();
   }
-}
-
-__global__ void __launch_bounds__(kTilePix)
-render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
-                  float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
-  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
-  __shared__ float s_red[kTilePix / 32];
-  __shared__ int s_last;
-  const unsigned FULL = 0xffffffffu;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int v = blockIdx.z;
-  const int tile = v * r.T + blockIdx.y * r.tiles_x + blockIdx.x;
-  // warp w covers the 8x4 pixel block (w % 2, w / 2) of the tile
-  const int bx0 = blockIdx.x * kTile + (warp & 1) * 8, by0 = blockIdx.y * kTile + (warp >> 1) * 4;
-  const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
-  const bool inside = px < r.W && py < r.H;
-  const bool ovf = pairs_overflow(ws, views * r.T);
-  const uint32_t s = ovf ? 0u : ws.tile_start[tile];
-  const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
-  const size_t vbase = (size_t)v * ws.max_n;
-  const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, oo = 0.f, rm = 0.f;
   int lastk = 0;
@@ -397,7 +404,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     if (__syncthreads_count(!done) == 0) break;
     const uint32_t k = base + tid;
     if (k < e) {
-      const size_t slot = vbase + ws.sorted_ids[k];
+      const size_t slot = vbase + (own_sort ? (uint32_t)s_key[k - s] : ws.sorted_ids[k]);
       s_a[tid] = ws.rec2d[slot * 3 + 0];
       s_b[tid] = ws.rec2d[slot * 3 + 1];
       s_c[tid] = ws.rec2d[slot * 3 + 2];
@@ -465,7 +472,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     ws.loss_partial[tile] = t;
     __threadfence();
     unsigned int done_ctas = atomicAdd(ws.counters + CNT_DONE_RENDER, 1u);
-    s_last = (done_ctas == gridDim.x * gridDim.y * gridDim.z - 1);
+    s_last = (done_ctas == gridDim.x - 1);
     if (s_last) __threadfence();
   }
   __syncthreads();
@@ -506,27 +513,11 @@ cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster 
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_sort(const Workspace &ws, int views, const Raster &r, cudaStream_t s) {
-  const int entries = views * r.T;
-  tile_sort_kernel<<<entries, 256, 0, s>>>(ws, entries);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int smem = kSortBigChunk * (int)sizeof(uint64_t);
-  tile_sort_big_kernel<<<32, 1024, smem, s>>>(ws, entries);
-  return cudaGetLastError();
-}
-
-cudaError_t configure_fwd_kernels() {
-  return cudaFuncSetAttribute(tile_sort_big_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              kSortBigChunk * (int)sizeof(uint64_t));
-}
-
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s) {
   (void)n;
-  dim3 grid((unsigned)r.tiles_x, (unsigned)r.tiles_y, (unsigned)views);
-  render_fwd_kernel<<<grid, kTilePix, 0, s>>>(ws, views, r, l, targets, image, last, loss);
+  render_fwd_kernel<<<(unsigned)(views * r.T), kTilePix, 0, s>>>(ws, views, r, l, targets, image, last, loss);
   return cudaGetLastError();
 }
 
