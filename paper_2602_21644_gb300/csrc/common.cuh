@@ -15,7 +15,7 @@ constexpr int kGradWords = 12;          // per (view, Gaussian) 2D gradient slot
 constexpr int kSortSmallCap = 1024;     // tile lists up to this length are sorted by the render CTA
 constexpr int kPrepBlock = 256;         // threads per preprocess CTA
 constexpr int kBwdPrepBlock = 128;      // threads per preprocess-backward CTA
-constexpr int kBwdPoseBlocks = 608;     // CTAs of the pose-only preprocess backward (4 per SM)
+constexpr int kBwdPoseBlocks = 304;     // CTAs of the pose-only preprocess backward (2 per SM)
 
 // Status word bits (device).
 constexpr uint32_t kStatusCapacity = 1u;

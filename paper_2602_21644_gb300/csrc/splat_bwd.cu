@@ -363,8 +363,19 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   // order, then a fixed shuffle tree
   for (int vc = wid; vc < views * 6; vc += kBwdPrepBlock / 32) {
     const int v = vc / 6, c = vc % 6;
+    const double *src = ws.pose_partial + (size_t)v * nb * 6 + c;
     double a = 0.0;
-    for (int b = lane; b < nb; b += 32) a += __ldcg(ws.pose_partial + ((size_t)v * nb + b) * 6 + c);
+    // loads issued in groups of 8 before they are summed (fixed order)
+    for (int b0 = lane; b0 < nb; b0 += 32 * 8) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + 32 * u;
+        t[u] = b < nb ? __ldcg(src + (size_t)b * 6) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a += t[u];
+    }
     a = warp_sum_d(a);
     if (lane == 0) grad_pose[v * 6 + c] = a;
   }

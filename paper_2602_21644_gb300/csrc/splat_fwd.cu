@@ -38,63 +38,88 @@ __device__ __forceinline__ int clampi(float x, int lo, int hi) {
   return c != c ? lo : (int)c;
 }
 
-// Exclusive scan of `total` uint32 counts by one CTA in one round: each
-// thread scans a contiguous chunk, the chunk sums are scanned across the CTA.
-// Also clears the counts and cursors for the next call. Returns the sum.
-// Also writes order[]: the tiles by descending list length (coarsely, by
-// floor(log2(length)); empty tiles last), the launch order of the renders so
-// that long tiles start first.
+// Exclusive scan of `total` uint32 per-tile counts by one CTA, through a
+// shared-memory stage of kScanChunk counts (coalesced loads, then each thread
+// scans a contiguous slice and the slice sums are scanned across the CTA).
+// Also clears the counts and cursors for the next call, and writes order[]:
+// the tiles by descending list length (coarsely, by floor(log2(length));
+// empty tiles last), the launch order of the renders so that long tiles
+// start first. Returns the sum.
+constexpr int kScanChunk = 4096;
+
+__device__ __forceinline__ int length_bin(uint32_t c) { return c ? 31 - __clz(c) : 32; }
+
 __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total,
                                      uint32_t *order) {
+  __shared__ uint32_t s_c[kScanChunk];
   __shared__ unsigned long long warp_tot[32];
-  __shared__ unsigned long long s_total;
+  __shared__ unsigned long long s_carry;
   __shared__ uint32_t s_bin[34];
-  if (threadIdx.x < 34) s_bin[threadIdx.x] = 0u;
-  __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  const int per = (total + blockDim.x - 1) / blockDim.x;
-  const int b = min(total, tid * per), e = min(total, b + per);
-  unsigned long long mine = 0;
-  for (int k = b; k < e; ++k) {
-    const uint32_t c = __ldcg(count + k);
-    mine += c;
-    atomicAdd(&s_bin[c ? 31 - __clz(c) : 32], 1u);   // bin = floor(log2(c)), 32 = empty
-  }
-  unsigned long long inc = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) warp_tot[wid] = inc;
+  if (tid < 34) s_bin[tid] = 0u;
+  if (tid == 0) s_carry = 0ull;
   __syncthreads();
-  if (wid == 0) {
-    unsigned long long t = lane < nw ? warp_tot[lane] : 0ull;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
+  // pass 1: length bins
+  for (int c0 = 0; c0 < total; c0 += kScanChunk) {
+    const int n = min(kScanChunk, total - c0);
+    for (int k = tid; k < n; k += blockDim.x) {
+      const uint32_t c = __ldcg(count + c0 + k);
+      s_c[k] = c;
+      atomicAdd(&s_bin[length_bin(c)], 1u);
     }
-    if (lane < nw) warp_tot[lane] = t;
-    if (lane == nw - 1) s_total = t;
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    // bins in descending length: 31, 30, ..., 0, then empty (32)
-    uint32_t run = 0;
+  if (tid == 0) {
+    uint32_t run = 0;   // descending length: bins 31 .. 0, then empty (32)
     for (int bb = 31; bb >= 0; --bb) { const uint32_t c = s_bin[bb]; s_bin[bb] = run; run += c; }
     s_bin[32] = run;
   }
   __syncthreads();
-  unsigned long long run = (wid > 0 ? warp_tot[wid - 1] : 0ull) + inc - mine;
-  for (int k = b; k < e; ++k) {
-    const uint32_t c = __ldcg(count + k);
-    start[k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
-    run += c;
-    order[atomicAdd(&s_bin[c ? 31 - __clz(c) : 32], 1u)] = (uint32_t)k;
-    count[k] = 0u;
-    cursor[k] = 0u;
+  // pass 2: offsets, order, clearing
+  for (int c0 = 0; c0 < total; c0 += kScanChunk) {
+    const int n = min(kScanChunk, total - c0);
+    if (total > kScanChunk) {
+      for (int k = tid; k < n; k += blockDim.x) s_c[k] = __ldcg(count + c0 + k);
+      __syncthreads();
+    }
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b = min(n, tid * per), e = min(n, b + per);
+    unsigned long long mine = 0;
+    for (int k = b; k < e; ++k) mine += s_c[k];
+    unsigned long long inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    if (lane == 31) warp_tot[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      unsigned long long t = lane < nw ? warp_tot[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) warp_tot[lane] = t;
+    }
+    __syncthreads();
+    unsigned long long run = s_carry + (wid > 0 ? warp_tot[wid - 1] : 0ull) + inc - mine;
+    for (int k = b; k < e; ++k) {
+      const uint32_t c = s_c[k];
+      start[c0 + k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
+      run += c;
+      order[atomicAdd(&s_bin[length_bin(c)], 1u)] = (uint32_t)(c0 + k);
+    }
+    for (int k = tid; k < n; k += blockDim.x) {
+      count[c0 + k] = 0u;
+      cursor[c0 + k] = 0u;
+    }
+    __syncthreads();
+    if (tid == 0) s_carry += warp_tot[nw - 1];
+    __syncthreads();
   }
-  return s_total;
+  return s_carry;
 }
 
 // The 32 lanes of a warp walk the candidate tiles of their 32 Gaussians

@@ -52,9 +52,11 @@ def test_graph_and_direct_tracking_agree_with_oracle_loop(dags):
         torch.cuda.synchronize()
         ctx.check()
         results.setdefault(use_graph, []).append(t["pose"].cpu().numpy()[0].copy())
-    # float atomics in the adjoint make repeated runs agree to rounding only
-    np.testing.assert_allclose(results[True][0], results[True][1], rtol=0, atol=1e-8)
-    np.testing.assert_allclose(results[True][0], results[False][0], rtol=0, atol=1e-8)
+    # float atomics in the adjoint make repeated runs differ at rounding level;
+    # after a step the runs sit at slightly different poses, where a pixel
+    # decision near its threshold may flip, so runs agree to the oracle bound
+    np.testing.assert_allclose(results[True][0], results[True][1], rtol=0, atol=1e-6)
+    np.testing.assert_allclose(results[True][0], results[False][0], rtol=0, atol=1e-6)
     # the oracle's loop: FP64 render + adjoint + pose step, same number of iterations
     G = oracle.params_from_records(sc.records)
     ocam = oracle.camera_vec(*sc.camera.as_tuple())
