@@ -188,6 +188,29 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
 int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state,
               int32_t n_views, const dags_pose_cfg *cfg, void *stream);
 
+/* Allocation-free forward: splat_forward for one view with no dags_ctx. No
+ * paper counterpart. It is for callers that must not allocate device memory
+ * once they run (a real-time pipeline that forbids allocation after
+ * start-up, a plugin whose host owns all device memory): it calls no
+ * cudaMalloc, cudaFree or allocating library routine. Its workspace is one
+ * file-scope device array of about 4.4 MB, shared by every call in the
+ * process; every GPU that loads the library holds it until the process
+ * exits. Limits: n <= 16384 Gaussians, width and height <= 256, at most
+ * 131072 (tile, Gaussian) pairs; larger n, width or height return
+ * DAGS_E_INVAL before any launch. The first call on a device resolves the
+ * array's device address (cudaGetSymbolAddress) for that device; make that
+ * first call before any stream capture. Each call clears the array's
+ * counters and leaves its other contents in place; calls whose work
+ * overlaps on the GPU (different streams, or devices sharing nothing but
+ * this process) race on the shared array and must be ordered by the caller.
+ * Arguments are those of splat_forward with n_views = 1 (pose: device, 12
+ * doubles); status: device, 2 int64 or NULL, receives DAGS_OK or
+ * DAGS_E_CAPACITY (pairs beyond the limit: image, last and loss are then
+ * undefined) and the number of pairs the call needed. */
+int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
+                         const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                         float *image, int32_t *last, double *loss, int64_t *status, void *stream);
+
 /* Tracking loop: iters x { splat_forward with loss, splat_backward
  * (DAGS_GRAD_POSE), pose_step } on one view, enqueued by the library -- the
  * pose refinement of the tracking thread (Sec. III) with the pose part of

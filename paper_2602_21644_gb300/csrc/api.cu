@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -524,3 +525,123 @@ int dags_timing_read(dags_ctx *ctx, double *ms, int64_t *launches, int32_t count
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward. The paper has no counterpart: this serves callers
+// that must not allocate device memory once they are running (a real-time
+// pipeline that forbids allocation after start-up, a plugin whose host owns
+// all device memory). Its workspace is one file-scope device array of fixed
+// size, shared by every call in the process; each GPU that loads the library
+// holds it until the process exits.
+namespace {
+
+constexpr int64_t kStaticMaxN = 16384;
+constexpr int kStaticMaxW = 256, kStaticMaxH = 256;
+constexpr int64_t kStaticMaxPairs = 131072;
+constexpr int kStaticTiles = (kStaticMaxW / kTile) * (kStaticMaxH / kTile);
+
+constexpr size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+// Regions, in order; the first four must be zero when a call starts.
+constexpr size_t kOffCount = 0;
+constexpr size_t kOffCursor = kOffCount + al256(kStaticTiles * 4);
+constexpr size_t kOffVisAppend = kOffCursor + al256(kStaticTiles * 4);
+constexpr size_t kOffCounters = kOffVisAppend + al256(4);
+constexpr size_t kZeroBytes = kOffCounters + al256(CNT_N * 4);
+constexpr size_t kOffStart = kZeroBytes;
+constexpr size_t kOffOrder = kOffStart + al256((kStaticTiles + 1) * 4);
+constexpr size_t kOffLossPartial = kOffOrder + al256(kStaticTiles * 4);
+constexpr size_t kOffVisN = kOffLossPartial + al256(kStaticTiles * 4);
+constexpr size_t kOffPose32 = kOffVisN + al256(4);
+constexpr size_t kOffRec2d = kOffPose32 + al256(12 * 4);
+constexpr size_t kOffRect = kOffRec2d + al256(kStaticMaxN * 3 * 16);
+constexpr size_t kOffGrad2d = kOffRect + al256(kStaticMaxN * 8);
+constexpr size_t kOffVisIds = kOffGrad2d + al256(kStaticMaxN * kGradWords * 4);
+constexpr size_t kOffKeys = kOffVisIds + al256(kStaticMaxN * 4);
+constexpr size_t kOffKeysTmp = kOffKeys + al256(kStaticMaxPairs * 8);
+constexpr size_t kOffSorted = kOffKeysTmp + al256(kStaticMaxPairs * 8);
+constexpr size_t kStaticBytes = kOffSorted + al256(kStaticMaxPairs * 4);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+// Per-device device address of g_static_scratch (host code cannot use the
+// symbol itself: on the host it names a stand-in, not device memory).
+std::mutex g_static_mu;
+unsigned char *g_static_addr[256] = {};
+
+int static_scratch(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return DAGS_E_CUDA;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DAGS_E_CUDA;
+    }
+    g_static_addr[dev] = static_cast<unsigned char *>(p);
+  }
+  *out = g_static_addr[dev];
+  return DAGS_OK;
+}
+
+__global__ void static_status_kernel(const uint32_t *counters, int64_t *status, int64_t max_pairs) {
+  const uint64_t req = (uint64_t)counters[CNT_REQ_LO] | ((uint64_t)counters[CNT_REQ_HI] << 32);
+  status[0] = req > (uint64_t)max_pairs ? DAGS_E_CAPACITY : DAGS_OK;
+  status[1] = (int64_t)req;
+}
+
+}  // namespace
+
+extern "C" int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
+                                    const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                                    float *image, int32_t *last, double *loss, int64_t *status, void *stream) {
+  if (n < 0 || n > kStaticMaxN || (n > 0 && !gauss) || !cam || !pose || !image || !last || (loss && !targets))
+    return DAGS_E_INVAL;
+  if (cam->width <= 0 || cam->height <= 0 || cam->width > kStaticMaxW || cam->height > kStaticMaxH)
+    return DAGS_E_INVAL;
+  if (!finite_pos(cam->fx) || !finite_pos(cam->fy) || !isfinite(cam->cx) || !isfinite(cam->cy))
+    return DAGS_E_INVAL;
+  if (((uintptr_t)gauss & 15u) != 0 || ((uintptr_t)targets & 15u) != 0) return DAGS_E_INVAL;
+  Raster r;
+  Loss l;
+  int rc = make_raster(cam, rcfg, &r);
+  if (rc) return rc;
+  if ((rc = make_loss(lcfg, &l))) return rc;
+  unsigned char *base = nullptr;
+  if ((rc = static_scratch(&base))) return rc;
+  Workspace w;
+  w.max_n = kStaticMaxN;
+  w.max_w = kStaticMaxW;
+  w.max_h = kStaticMaxH;
+  w.max_v = 1;
+  w.max_tiles = kStaticTiles;
+  w.max_pairs = kStaticMaxPairs;
+  w.tile_count = reinterpret_cast<uint32_t *>(base + kOffCount);
+  w.tile_cursor = reinterpret_cast<uint32_t *>(base + kOffCursor);
+  w.vis_append = reinterpret_cast<uint32_t *>(base + kOffVisAppend);
+  w.counters = reinterpret_cast<uint32_t *>(base + kOffCounters);
+  w.tile_start = reinterpret_cast<uint32_t *>(base + kOffStart);
+  w.tile_order = reinterpret_cast<uint32_t *>(base + kOffOrder);
+  w.loss_partial = reinterpret_cast<float *>(base + kOffLossPartial);
+  w.vis_n = reinterpret_cast<uint32_t *>(base + kOffVisN);
+  w.pose32 = reinterpret_cast<float *>(base + kOffPose32);
+  w.rec2d = reinterpret_cast<float4 *>(base + kOffRec2d);
+  w.rect = reinterpret_cast<uint2 *>(base + kOffRect);
+  w.grad2d = reinterpret_cast<float *>(base + kOffGrad2d);
+  w.vis_ids = reinterpret_cast<uint32_t *>(base + kOffVisIds);
+  w.keys = reinterpret_cast<uint64_t *>(base + kOffKeys);
+  w.keys_tmp = reinterpret_cast<uint64_t *>(base + kOffKeysTmp);
+  w.sorted_ids = reinterpret_cast<uint32_t *>(base + kOffSorted);
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: clear the counters
+  cudaError_t e = cudaMemsetAsync(base, 0, kZeroBytes, s);
+  if (e == cudaSuccess) e = launch_preprocess(w, reinterpret_cast<const float4 *>(gauss), n, pose, 1, r, kGradWords, s);
+  if (e == cudaSuccess && n > 0) e = launch_emit(w, n, 1, r, s);
+  if (e == cudaSuccess)
+    e = launch_render_fwd(w, 1, n, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
+  if (e == cudaSuccess && status) {
+    static_status_kernel<<<1, 1, 0, s>>>(w.counters, status, kStaticMaxPairs);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? DAGS_OK : DAGS_E_CUDA;
+}

@@ -57,7 +57,7 @@ class CPoseCfg(ctypes.Structure):
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
-           "splat_track"]
+           "splat_track", "splat_forward_static"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet"]
@@ -105,6 +105,9 @@ def load(path: str = LIB_PATH):
     lib.splat_track.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
                                 ctypes.POINTER(CLossCfg), ctypes.POINTER(CPoseCfg), I32, P, P, P, P, P, I32, P]
     lib.splat_track.restype = ctypes.c_int
+    lib.splat_forward_static.argtypes = [P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
+                                         ctypes.POINTER(CLossCfg), P, P, P, P, P]
+    lib.splat_forward_static.restype = ctypes.c_int
     _lib = lib
     return lib
 
