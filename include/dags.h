@@ -227,6 +227,67 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
                 const dags_pose_cfg *pcfg, int32_t iters, double *adam_state, float *image, int32_t *last,
                 double *loss, double *grad_pose, int32_t use_graph, void *stream);
 
+/* Spatiotemporal MP update constants (Sec. IV-A, Eq. (17)). The paper gives
+ * none of their values ("unified configuration", Sec. V-A(c)); defaults
+ * from dags_default_mp_cfg. */
+typedef struct {
+  float kappa_c;     /* m of residual per unit of L1 colour residual in e(p) (0.05)       */
+  float lam;         /* lambda of e_ub = mu_e + lambda sigma_e, Eq. (4) (2)                */
+  float sigma_min;   /* instance with sigma_e below this uses its mean error, m (0.005)    */
+  float e_floor;     /* floor on e_ub, m (0.05)                                            */
+  float sigma_g;     /* Gamma_geo = exp(-sigma_e,k / sigma_g), Eq. (7), m (0.05)           */
+  float sigma_c;     /* C = exp(-sigma_e,G / sigma_c), Eq. (11), m (0.05)                  */
+  float lam_u;       /* lambda_u, Eq. (10) (1)                                             */
+  float eps;         /* epsilon, Eq. (10) (1e-6)                                           */
+  float alpha_min, alpha_max;  /* Eq. (11) (0.05, 0.6)                                     */
+  float rho;         /* stale-prior rate factor, Eq. (17) (0.5)                            */
+  float r_s;         /* association radius, Eq. (1), px (2)                                */
+  float sigma_w;     /* association kernel width, px (1)                                   */
+  float vis_tol;     /* observed iff z <= max rendered depth over N(G) + vis_tol, m (0.1) */
+  float z_near;      /* m (0.2)                                                            */
+  float tau_floor;   /* Eq. (12) (0.5)                                                     */
+  int32_t fusion_mode;  /* 0 fused, 1 K = 0 (MP_ins only), 2 K = 1 (MP_geo only)           */
+} dags_mp_cfg;
+
+void dags_default_mp_cfg(dags_mp_cfg *cfg);
+
+#define DAGS_MP_MAX_REGIONS 256
+#define DAGS_MP_STATS_HEAD 6
+
+/* Spatiotemporal MP update of one view (Sec. IV-A, Eqs. (1)-(12); Eq. (17)).
+ * Per pixel p (the hot path's "features"): residual e(p) = |D_obs - D_rend|
+ * (where D_obs > 0) + kappa_c ||C_obs - C_rend||_1; region k = inst[p]
+ * (0 = background, its own region); region mean/std of e, Eq. (4) (e_ub
+ * floored at e_floor; an instance with sigma_e < sigma_min uses its mean);
+ * MP_geo, Eq. (5); MP_ins and Gamma_ins from the region table, Eq. (2);
+ * fusion, Eqs. (6),(7). Per Gaussian (in FP32): the pixels within r_s of its
+ * projected mean, Eq. (1), weighted exp(-d^2 / (2 sigma_w^2)); observed iff
+ * z > z_near, the disk is non-empty and z <= max rendered depth over the disk
+ * + vis_tol; M_hat, Eq. (8); U, Eq. (10), min-max normalised over the
+ * observed Gaussians; alpha, Eq. (11), times rho unless seg_refreshed,
+ * Eq. (17); M^t, Eq. (9), written into word 11 of each observed record.
+ * Per frame: tau = max(lower median of M^t over observed, tau_floor), Eq. (12);
+ * labels[i] = M^t > tau for observed Gaussians (others keep theirs);
+ * U_bar = lower median of U_tilde over observed, Eq. (13).
+ *
+ * gauss     device in/out, n records (the MP word is updated)
+ * pose      device, 12 doubles (world -> camera)
+ * targets   device, H*W float4: observed r, g, b, depth (depth <= 0 invalid)
+ * image     device, DAGS_IMG_CHANNELS x H*W: a splat_forward image of this
+ *           view (rendered colour planes 0-2 and depth plane 3 are read)
+ * inst      device, H*W uint8 region labels, each < n_regions
+ * table     device, n_regions x 2 floats: (mu, c) of the region's class;
+ *           row 0 = background (mu(bg), c_bg)
+ * labels    device in/out, n uint8 (1 = dynamic)
+ * stats     device out, DAGS_MP_STATS_HEAD + 4 * n_regions doubles: tau,
+ *           U_bar, median M^t, U_min, U_max, number observed; then per region
+ *           count, mean e, std e, e_ub.
+ * Needs a ctx created with max_views >= 1 and images at least H x W. */
+int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, const double *pose,
+              const float *targets, const float *image, const uint8_t *inst, const float *table,
+              int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
+              double *stats, void *stream);
+
 /* Per-kernel device timing (tracing). When enabled, every kernel the
  * library launches on a stream that is not being captured into a CUDA graph
  * is bracketed by a pair of CUDA events on that stream. dags_timing_read

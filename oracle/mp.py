@@ -143,37 +143,50 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
     sig_e = np.zeros(n)
     disk_flag = np.zeros(n, bool)
     vis_flag = np.zeros(n, bool)
+    # Eq. (1) for all Gaussians at once: the candidate pixels are a square of
+    # integer offsets around the projected mean; N(G) keeps those inside the
+    # image within r_s.
     R = int(np.ceil(cfg.r_s)) + 1
-    for g in range(n):
-        x, y, z = pc[g]
-        if not z > cfg.z_near:
-            continue
-        u = fx * x / z + cx
-        v = fy * y / z + cy
-        i0, j0 = int(np.floor(u)), int(np.floor(v))
-        ii, jj = np.meshgrid(np.arange(i0 - R, i0 + R + 2), np.arange(j0 - R, j0 + R + 2), indexing="xy")
-        ii, jj = ii.ravel(), jj.ravel()
-        inside = (ii >= 0) & (ii < W) & (jj >= 0) & (jj < H)
-        d2 = (ii - u) ** 2 + (jj - v) ** 2
-        if np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= 1e-5 * cfg.r_s ** 2)):
-            disk_flag[g] = True
+    off = np.arange(-R, R + 2)
+    oi, oj = np.meshgrid(off, off, indexing="xy")
+    oi, oj = oi.ravel(), oj.ravel()
+    for c0 in range(0, n, 20000):
+        c1 = min(n, c0 + 20000)
+        x, y, z = pc[c0:c1, 0], pc[c0:c1, 1], pc[c0:c1, 2]
+        front = z > cfg.z_near
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = np.where(front, fx * x / z + cx, 0.0)
+            v = np.where(front, fy * y / z + cy, 0.0)
+        ok_uv = front & np.isfinite(u) & np.isfinite(v) & (np.abs(u) < 1e7) & (np.abs(v) < 1e7)
+        u = np.where(ok_uv, u, -1e6)
+        v = np.where(ok_uv, v, -1e6)
+        ii = np.floor(u).astype(np.int64)[:, None] + oi[None, :]
+        jj = np.floor(v).astype(np.int64)[:, None] + oj[None, :]
+        inside = (ii >= 0) & (ii < W) & (jj >= 0) & (jj < H) & ok_uv[:, None]
+        d2 = (ii - u[:, None]) ** 2 + (jj - v[:, None]) ** 2
+        disk_flag[c0:c1] = np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= 1e-5 * cfg.r_s ** 2), axis=1)
         sel = inside & (d2 <= cfg.r_s ** 2)
-        if not np.any(sel):
-            continue
-        pidx = jj[sel] * W + ii[sel]
-        dmax = d_rend[pidx].max()
-        if cfg.vis_tol > 0 and dmax > 0:
-            if abs(z - (dmax + cfg.vis_tol)) <= 1e-5 * (dmax + cfg.vis_tol):
-                vis_flag[g] = True
-            if z > dmax + cfg.vis_tol:
-                continue
-        w = np.exp(-d2[sel] / (2.0 * cfg.sigma_w ** 2))
-        mp_set = M_p[pidx]
-        m_hat[g] = np.sum(w * mp_set) / np.sum(w)
-        var[g] = np.mean((mp_set - mp_set.mean()) ** 2)
-        es = e[pidx]
-        sig_e[g] = np.sqrt(np.mean((es - es.mean()) ** 2))
-        observed[g] = True
+        cnt = sel.sum(1)
+        pidx = np.where(sel, jj * W + ii, 0)
+        dmax = np.where(sel, d_rend[pidx], -np.inf).max(1)
+        lim = dmax + cfg.vis_tol
+        occl = (cfg.vis_tol > 0) & (dmax > 0) & (z > lim)
+        vis_flag[c0:c1] = (cfg.vis_tol > 0) & (dmax > 0) & (np.abs(z - lim) <= 1e-5 * np.abs(lim))
+        obs = (cnt > 0) & ~occl
+        w = np.where(sel, np.exp(-d2 / (2.0 * cfg.sigma_w ** 2)), 0.0)
+        mps = np.where(sel, M_p[pidx], 0.0)
+        es = np.where(sel, e[pidx], 0.0)
+        cntf = np.maximum(cnt, 1)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            mh = (w * mps).sum(1) / w.sum(1)                      # Eq. (8)
+        mm = mps.sum(1) / cntf
+        vv = np.where(sel, (mps - mm[:, None]) ** 2, 0.0).sum(1) / cntf
+        me = es.sum(1) / cntf
+        se = np.sqrt(np.where(sel, (es - me[:, None]) ** 2, 0.0).sum(1) / cntf)
+        observed[c0:c1] = obs
+        m_hat[c0:c1] = np.where(obs, mh, 0.0)
+        var[c0:c1] = np.where(obs, vv, 0.0)
+        sig_e[c0:c1] = np.where(obs, se, 0.0)
     M0 = mp_prev
     ent = -M0 * np.log(M0 + cfg.eps) - (1.0 - M0) * np.log(1.0 - M0 + cfg.eps)
     U = ent + cfg.lam_u * var

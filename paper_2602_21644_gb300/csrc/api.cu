@@ -78,6 +78,7 @@ struct dags_ctx {
   Workspace ws;
   KernelTimer timer;
   TrackGraph graph;
+  MpBuffers mp;
   PoseStep fused_step;            // set only inside the tracking loop
   cudaStream_t last_stream = nullptr;
   // the buffers of the latest forward (backward must follow its forward)
@@ -102,6 +103,13 @@ void free_ws(Workspace &w) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
+}
+
+void free_mp(MpBuffers &b) {
+  void *ptrs[] = {b.e, b.acc, b.mhat, b.sige, b.U, b.Mt, b.Ut, b.obs, b.hist, b.sel};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  b = MpBuffers();
 }
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
@@ -249,6 +257,17 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&w.counters, (size_t)CNT_N));
   if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
+  MpBuffers &mb = c->mp;
+  A(alloc(&mb.e, (size_t)max_width * max_height));
+  A(alloc(&mb.acc, (size_t)DAGS_MP_MAX_REGIONS * 4));
+  A(alloc(&mb.mhat, (size_t)w.max_n));
+  A(alloc(&mb.sige, (size_t)w.max_n));
+  A(alloc(&mb.U, (size_t)w.max_n));
+  A(alloc(&mb.Mt, (size_t)w.max_n));
+  A(alloc(&mb.Ut, (size_t)w.max_n));
+  A(alloc(&mb.obs, (size_t)w.max_n));
+  A(alloc(&mb.hist, (size_t)2 * 2048));
+  A(alloc(&mb.sel, (size_t)8));
   if (e == cudaSuccess) e = cudaMemset(w.counters, 0, CNT_N * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.vis_append, 0, (size_t)w.max_v * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.vis_n, 0, (size_t)w.max_v * sizeof(uint32_t));
@@ -256,6 +275,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   if (e != cudaSuccess) {
     const int code = (e == cudaErrorMemoryAllocation) ? DAGS_E_NOMEM : DAGS_E_CUDA;
     cudaGetLastError();
+    free_mp(c->mp);
     free_ws(w);
     delete c;
     return code;
@@ -273,6 +293,7 @@ void dags_destroy(dags_ctx *ctx) {
   ctx->timer.release();
   if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
   if (ctx->graph.cap) cudaStreamDestroy(ctx->graph.cap);
+  free_mp(ctx->mp);
   free_ws(ctx->ws);
   cudaSetDevice(cur);
   delete ctx;
@@ -500,6 +521,54 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   for (int k = 0; k < iters; ++k)
     if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return DAGS_E_CUDA;
   return DAGS_OK;
+}
+
+void dags_default_mp_cfg(dags_mp_cfg *c) {
+  if (!c) return;
+  c->kappa_c = 0.05f;
+  c->lam = 2.f;
+  c->sigma_min = 0.005f;
+  c->e_floor = 0.05f;
+  c->sigma_g = 0.05f;
+  c->sigma_c = 0.05f;
+  c->lam_u = 1.f;
+  c->eps = 1e-6f;
+  c->alpha_min = 0.05f;
+  c->alpha_max = 0.6f;
+  c->rho = 0.5f;
+  c->r_s = 2.f;
+  c->sigma_w = 1.f;
+  c->vis_tol = 0.1f;
+  c->z_near = 0.2f;
+  c->tau_floor = 0.5f;
+  c->fusion_mode = 0;
+}
+
+int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, const double *pose,
+              const float *targets, const float *image, const uint8_t *inst, const float *table,
+              int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
+              double *stats, void *stream) {
+  int rc = common_args(ctx, gauss, n, cam, pose, 1);
+  if (rc) return rc;
+  if (!targets || !image || !inst || !table || !labels || !stats) return DAGS_E_INVAL;
+  if (n_regions < 1 || n_regions > DAGS_MP_MAX_REGIONS) return DAGS_E_INVAL;
+  if (((uintptr_t)targets & 15u) != 0 || ((uintptr_t)table & 7u) != 0) return DAGS_E_INVAL;
+  dags_mp_cfg c;
+  if (cfg) c = *cfg;
+  else dags_default_mp_cfg(&c);
+  if (!(c.r_s > 0.f) || !(c.sigma_w > 0.f) || !(c.sigma_g > 0.f) || !(c.sigma_c > 0.f) || !(c.e_floor > 0.f) ||
+      !(c.alpha_min >= 0.f && c.alpha_min <= c.alpha_max && c.alpha_max <= 1.f) || !(c.rho >= 0.f && c.rho <= 1.f) ||
+      c.fusion_mode < 0 || c.fusion_mode > 2 || c.r_s > 64.f)
+    return DAGS_E_INVAL;
+  Raster r;
+  if ((rc = make_raster(cam, nullptr, &r))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_MP_GAUSS, s);
+  const cudaError_t e = launch_mp_update(ctx->mp, gauss, n, pose, r, reinterpret_cast<const float4 *>(targets),
+                                         image, inst, table, n_regions, c, seg_refreshed ? 1 : 0, labels, stats, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
 }
 
 int dags_timing_enable(dags_ctx *ctx, int enable) {

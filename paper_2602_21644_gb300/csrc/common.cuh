@@ -109,6 +109,20 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
 cudaError_t launch_pose_step(double *poses, const double *grad, double *state, int views,
                              const dags_pose_cfg &cfg, cudaStream_t s);
 
+// Buffers of the MP update (owned by the ctx).
+struct MpBuffers {
+  float *e = nullptr;                 // [max_w * max_h]
+  double *acc = nullptr;              // [DAGS_MP_MAX_REGIONS * 4]
+  float *mhat = nullptr, *sige = nullptr, *U = nullptr, *Mt = nullptr, *Ut = nullptr;  // [max_n]
+  uint8_t *obs = nullptr;             // [max_n]
+  uint32_t *hist = nullptr;           // [2 * 2048]
+  uint32_t *sel = nullptr;            // [8]
+};
+cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
+                             const float4 *targets, const float *image, const uint8_t *inst, const float *table,
+                             int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
+                             double *stats, cudaStream_t s);
+
 // ---- device helpers ----
 
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }

@@ -1,0 +1,420 @@
+// Spatiotemporal motion-probability update (Sec. IV-A, Eq. (17)) on sm_103a.
+//
+//   mp_pixel_sum_kernel   per pixel: residual e(p) between the observed and
+//                         the rendered RGB-D, stored; per-region count and sum
+//                         (shared-memory partials, one FP64 atomic per region
+//                         per CTA)
+//   mp_pixel_var_kernel   per pixel: centred squares (e - mean_k)^2 summed per
+//                         region the same way (two passes: no cancellation)
+//   mp_gauss_kernel       per Gaussian: projection, the association disk
+//                         N(G), Eq. (1), with the fused per-pixel MP M_p,
+//                         Eqs. (2)-(7), computed on the fly from the region
+//                         statistics; M_hat, Eq. (8); Var{M_p}; sigma_e,G;
+//                         U, Eq. (10); CTA min/max of U -> global
+//   mp_apply_kernel       per observed Gaussian: normalised U, C, alpha,
+//                         Eqs. (11), (17); M^t, Eq. (9), written into the
+//                         record; first radix-select level of the two medians
+//   mp_select_kernel      further radix-select levels (exact lower medians of
+//                         M^t and U_tilde over the observed Gaussians, bits
+//                         31-21, 20-10, 9-0 of the non-negative floats);
+//                         the last CTA of the last level writes tau, U_bar
+//   mp_labels_kernel      labels, Eq. (12)
+// The last CTA of each histogram kernel finds the bin holding the median's
+// rank (one warp scans the bins).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace dags {
+
+namespace {
+
+constexpr int kMpBlock = 256;
+constexpr int kSelBins = 2048;
+
+struct MpCfg {
+  float kappa_c, lam, sigma_min, e_floor, sigma_g, sigma_c, lam_u, eps, alpha_min, alpha_max, rho, r_s, sigma_w,
+      vis_tol, z_near, tau_floor;
+  int fusion_mode, seg_refreshed, n_regions;
+};
+
+// Workspace of the update (carved from the ctx's MP buffers).
+struct MpWs {
+  float *e;              // [P] residual per pixel
+  double *acc;           // [256][4] region count, sum, centred sum of squares, -
+  float *mhat, *sige, *U, *Mt, *Ut;  // [N]
+  uint8_t *obs;          // [N]
+  uint32_t *hist;        // [2][kSelBins]
+  uint32_t *sel;         // select state: [0] n_obs, [1] Umin bits, [2] Umax bits, [3] done counter,
+                         // [4..5] prefix (M, U), [6..7] remaining rank (M, U)
+  double *stats;         // caller's output
+};
+
+// Order-preserving map of floats to uint32 (for atomic min/max of values
+// that may be slightly negative).
+__device__ __forceinline__ uint32_t f2o(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float o2f(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__device__ __forceinline__ float residual(const float4 tg, const float *img, size_t P, size_t p, float kappa_c) {
+  const float dr = img[3 * P + p];
+  float e = tg.w > 0.f ? fabsf(tg.w - dr) : 0.f;
+  e += kappa_c * (fabsf(tg.x - img[p]) + fabsf(tg.y - img[P + p]) + fabsf(tg.z - img[2 * P + p]));
+  return e;
+}
+
+__global__ void __launch_bounds__(kMpBlock)
+mp_pixel_sum_kernel(MpWs m, const float4 *__restrict__ targets, const float *__restrict__ image,
+                    const uint8_t *__restrict__ inst, int P, MpCfg c) {
+  __shared__ float s_cnt[DAGS_MP_MAX_REGIONS], s_sum[DAGS_MP_MAX_REGIONS];
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) { s_cnt[k] = 0.f; s_sum[k] = 0.f; }
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  // select state and histograms start cleared (used from mp_gauss_kernel on)
+  for (int k = p; k < 2 * kSelBins; k += gridDim.x * blockDim.x) m.hist[k] = 0u;
+  if (p == 0) {
+    m.sel[0] = 0u;            // observed count
+    m.sel[1] = 0xFFFFFFFFu;   // min of U (ordered key)
+    m.sel[2] = 0u;            // max of U (ordered key)
+    m.sel[3] = 0u;            // CTA counter
+  }
+  __syncthreads();
+  if (p < P) {
+    const float e = residual(targets[p], image, (size_t)P, (size_t)p, c.kappa_c);
+    m.e[p] = e;
+    const int k = inst[p];
+    atomicAdd(&s_cnt[k], 1.f);
+    atomicAdd(&s_sum[k], e);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x)
+    if (s_cnt[k] > 0.f) {
+      atomicAdd(&m.acc[4 * k + 0], (double)s_cnt[k]);
+      atomicAdd(&m.acc[4 * k + 1], (double)s_sum[k]);
+    }
+}
+
+__global__ void __launch_bounds__(kMpBlock)
+mp_pixel_var_kernel(MpWs m, const uint8_t *__restrict__ inst, int P, MpCfg c) {
+  __shared__ float s_mean[DAGS_MP_MAX_REGIONS], s_sq[DAGS_MP_MAX_REGIONS];
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
+    const double cnt = m.acc[4 * k + 0];
+    s_mean[k] = cnt > 0.0 ? (float)(m.acc[4 * k + 1] / cnt) : 0.f;
+    s_sq[k] = 0.f;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) {
+    const int k = inst[p];
+    const float d = m.e[p] - s_mean[k];
+    atomicAdd(&s_sq[k], d * d);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x)
+    if (s_sq[k] != 0.f) atomicAdd(&m.acc[4 * k + 2], (double)s_sq[k]);
+}
+
+// Region parameters used per pixel: mean, e_ub, Gamma_geo, use-mean flag.
+__device__ __forceinline__ void region_params(const MpWs &m, const MpCfg &c, int k, float4 *out) {
+  const double cnt = m.acc[4 * k + 0];
+  const float mean = cnt > 0.0 ? (float)(m.acc[4 * k + 1] / cnt) : 0.f;
+  const float sd = cnt > 0.0 ? sqrtf((float)(m.acc[4 * k + 2] / cnt)) : 0.f;
+  const float eub = fmaxf(mean + c.lam * sd, c.e_floor);
+  const float ggeo = expf(-sd / c.sigma_g);
+  const float use_mean = (k >= 1 && sd < c.sigma_min) ? 1.f : 0.f;
+  *out = make_float4(mean, eub, ggeo, use_mean);
+}
+
+__device__ __forceinline__ float pixel_mp(float e, const float4 reg, const float2 tab, int fusion_mode) {
+  const float e_used = reg.w != 0.f ? reg.x : e;
+  const float mp_geo = fminf(fmaxf(e_used / reg.y, 0.f), 1.f);
+  float K = reg.z / (tab.y + reg.z);
+  if (fusion_mode == 1) K = 0.f;
+  else if (fusion_mode == 2) K = 1.f;
+  return (1.f - K) * tab.x + K * mp_geo;
+}
+
+__global__ void __launch_bounds__(kMpBlock)
+mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
+                const float *__restrict__ image, const uint8_t *__restrict__ inst, const float2 *__restrict__ table,
+                Raster r, MpCfg c) {
+  __shared__ float4 s_reg[DAGS_MP_MAX_REGIONS];
+  __shared__ float2 s_tab[DAGS_MP_MAX_REGIONS];
+  __shared__ float sp[12];
+  __shared__ uint32_t s_min, s_max, s_cnt;
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
+    region_params(m, c, k, &s_reg[k]);
+    s_tab[k] = table[k];
+  }
+  if (threadIdx.x < 12) sp[threadIdx.x] = (float)pose[threadIdx.x];
+  if (threadIdx.x == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_cnt = 0u; }
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float4 g0 = __ldg(gauss + 4 * i), g2 = __ldg(gauss + 4 * i + 2);
+    const float x = sp[0] * g0.x + sp[1] * g0.y + sp[2] * g0.z + sp[3];
+    const float y = sp[4] * g0.x + sp[5] * g0.y + sp[6] * g0.z + sp[7];
+    const float z = depth_key(g0, sp);
+    bool observed = false;
+    float mhat = 0.f, var = 0.f, sige = 0.f;
+    const float u = r.fx * x / z + r.cx, v = r.fy * y / z + r.cy;
+    if (z > c.z_near && u > -c.r_s - 1.f && u < (float)r.W + c.r_s && v > -c.r_s - 1.f &&
+        v < (float)r.H + c.r_s) {
+      const size_t P = (size_t)r.W * r.H;
+      const float rs2 = c.r_s * c.r_s, inv2s2 = 1.f / (2.f * c.sigma_w * c.sigma_w);
+      const int i0 = (int)fmaxf(ceilf(u - c.r_s), 0.f), i1 = (int)fminf(floorf(u + c.r_s), (float)(r.W - 1));
+      const int j0 = (int)fmaxf(ceilf(v - c.r_s), 0.f), j1 = (int)fminf(floorf(v + c.r_s), (float)(r.H - 1));
+      float sw = 0.f, swm = 0.f, sm = 0.f, se = 0.f, dmax = -INFINITY;
+      int cnt = 0;
+      if (i0 <= i1 && j0 <= j1) {
+        for (int jj = j0; jj <= j1; ++jj)
+          for (int ii = i0; ii <= i1; ++ii) {
+            const float dx = (float)ii - u, dy = (float)jj - v, d2 = dx * dx + dy * dy;
+            if (d2 > rs2) continue;
+            const size_t p = (size_t)jj * r.W + ii;
+            const float e = m.e[p];
+            const int k = inst[p];
+            const float mp = pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
+            const float w = expf(-d2 * inv2s2);
+            sw += w; swm += w * mp; sm += mp; se += e; ++cnt;
+            dmax = fmaxf(dmax, image[3 * P + p]);
+          }
+      }
+      observed = cnt > 0 && !(c.vis_tol > 0.f && dmax > 0.f && z > dmax + c.vis_tol);
+      if (observed) {
+        mhat = swm / sw;
+        const float mm = sm / cnt, me = se / cnt;
+        float vm = 0.f, ve = 0.f;
+        for (int jj = j0; jj <= j1; ++jj)
+          for (int ii = i0; ii <= i1; ++ii) {
+            const float dx = (float)ii - u, dy = (float)jj - v;
+            if (dx * dx + dy * dy > rs2) continue;
+            const size_t p = (size_t)jj * r.W + ii;
+            const float e = m.e[p];
+            const int k = inst[p];
+            const float mp = pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
+            vm += (mp - mm) * (mp - mm);
+            ve += (e - me) * (e - me);
+          }
+        var = vm / cnt;
+        sige = sqrtf(ve / cnt);
+      }
+    }
+    float U = 0.f;
+    if (observed) {
+      const float M0 = g2.w;
+      U = -M0 * logf(M0 + c.eps) - (1.f - M0) * logf(1.f - M0 + c.eps) + c.lam_u * var;
+      atomicMin(&s_min, f2o(U));
+      atomicMax(&s_max, f2o(U));
+      atomicAdd(&s_cnt, 1u);
+    }
+    m.obs[i] = observed ? 1 : 0;
+    m.mhat[i] = mhat;
+    m.sige[i] = sige;
+    m.U[i] = U;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && s_cnt) {
+    atomicMin(&m.sel[1], s_min);
+    atomicMax(&m.sel[2], s_max);
+    atomicAdd(&m.sel[0], s_cnt);
+  }
+}
+
+// One warp finds, for rank r, the bin b with cum(b - 1) <= r < cum(b) of a
+// kSelBins histogram; returns b and writes the rank within the bin.
+__device__ __forceinline__ int find_bin(const uint32_t *hist, uint32_t r, uint32_t *r_in_bin) {
+  const int lane = threadIdx.x & 31;
+  constexpr int per = kSelBins / 32;
+  uint32_t mine = 0;
+  for (int b = 0; b < per; ++b) mine += __ldcg(hist + lane * per + b);
+  uint32_t inc = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const uint32_t before = inc - mine;
+  const unsigned hit = __ballot_sync(0xffffffffu, before <= r && r < inc);
+  const int owner = __ffs(hit) - 1;
+  int bin = -1;
+  uint32_t rr = 0;
+  if (lane == owner) {
+    uint32_t run = before;
+    for (int b = 0; b < per; ++b) {
+      const uint32_t hcount = __ldcg(hist + lane * per + b);
+      if (r < run + hcount) { bin = lane * per + b; rr = r - run; break; }
+      run += hcount;
+    }
+  }
+  bin = __shfl_sync(0xffffffffu, bin, owner < 0 ? 0 : owner);
+  rr = __shfl_sync(0xffffffffu, rr, owner < 0 ? 0 : owner);
+  *r_in_bin = rr;
+  return bin;
+}
+
+// Level-l radix select step over the observed Gaussians' (M^t, U_tilde):
+// level 0 uses bits 31-21, level 1 bits 20-10, level 2 bits 9-0.
+__device__ __forceinline__ void select_shift(int level, int *shift, uint32_t *mask) {
+  *shift = level == 0 ? 21 : (level == 1 ? 10 : 0);
+  *mask = level == 2 ? 0x3FFu : 0x7FFu;
+}
+
+__device__ bool last_cta(uint32_t *counter) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(counter, 1u);
+    s_last = (t == gridDim.x - 1);
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// After a histogram level: the last CTA finds both medians' bins, advances
+// their prefixes and remaining ranks, clears the histograms; after the last
+// level it writes the statistics.
+__device__ void select_finish(const MpWs &m, int level, const MpCfg &c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 2) {
+    const uint32_t nobs = __ldcg(m.sel + 0);
+    if (nobs > 0) {
+      const uint32_t rank = level == 0 ? (nobs - 1) / 2 : __ldcg(m.sel + 6 + warp);
+      uint32_t rin = 0;
+      const int bin = find_bin(m.hist + warp * kSelBins, rank, &rin);
+      int shift;
+      uint32_t mask;
+      select_shift(level, &shift, &mask);
+      if (lane == 0) {
+        const uint32_t prefix = (level == 0 ? 0u : __ldcg(m.sel + 4 + warp)) | ((uint32_t)bin << shift);
+        m.sel[4 + warp] = prefix;
+        m.sel[6 + warp] = rin;
+      }
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x) m.hist[k] = 0u;
+  if (level == 2 && threadIdx.x == 0) {
+    const uint32_t nobs = __ldcg(m.sel + 0);
+    const float medM = nobs ? __uint_as_float(__ldcg(m.sel + 4)) : nanf("");
+    const float medU = nobs ? __uint_as_float(__ldcg(m.sel + 5)) : 0.f;
+    m.stats[0] = nobs ? fmax((double)medM, (double)c.tau_floor) : (double)c.tau_floor;
+    m.stats[1] = medU;
+    m.stats[2] = medM;
+    m.stats[3] = nobs ? (double)o2f(__ldcg(m.sel + 1)) : 0.0;
+    m.stats[4] = nobs ? (double)o2f(__ldcg(m.sel + 2)) : 0.0;
+    m.stats[5] = (double)nobs;
+  }
+  if (threadIdx.x == 0) m.sel[3] = 0u;
+}
+
+__global__ void __launch_bounds__(kMpBlock)
+mp_apply_kernel(MpWs m, float4 *__restrict__ gauss, int64_t n, MpCfg c) {
+  __shared__ uint32_t s_h[2 * kSelBins];
+  for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x) s_h[k] = 0u;
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && m.obs[i]) {
+    const float umin = o2f(m.sel[1]), umax = o2f(m.sel[2]);
+    const float ut = umax > umin ? (m.U[i] - umin) / (umax - umin) : 0.f;
+    const float C = expf(-m.sige[i] / c.sigma_c);
+    float a = c.alpha_min + (c.alpha_max - c.alpha_min) * (1.f - ut) * C;
+    a = fminf(fmaxf(a, c.alpha_min), c.alpha_max);
+    if (!c.seg_refreshed) a *= c.rho;
+    float *rec = reinterpret_cast<float *>(gauss + 4 * i);
+    const float M0 = rec[11];
+    const float Mt = (1.f - a) * M0 + a * m.mhat[i];
+    rec[11] = Mt;
+    m.Mt[i] = Mt;
+    m.Ut[i] = ut;
+    atomicAdd(&s_h[__float_as_uint(Mt) >> 21], 1u);
+    atomicAdd(&s_h[kSelBins + (__float_as_uint(ut) >> 21)], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x)
+    if (s_h[k]) atomicAdd(&m.hist[k], s_h[k]);
+  if (last_cta(m.sel + 3)) select_finish(m, 0, c);
+}
+
+__global__ void __launch_bounds__(kMpBlock)
+mp_select_kernel(MpWs m, int64_t n, int level, MpCfg c) {
+  __shared__ uint32_t s_h[2 * kSelBins];
+  for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x) s_h[k] = 0u;
+  __syncthreads();
+  int shift;
+  uint32_t mask;
+  select_shift(level, &shift, &mask);
+  const int top = shift + (level == 2 ? 10 : 11);   // bits above this level are the prefix
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && m.obs[i]) {
+    const uint32_t pm = m.sel[4], pu = m.sel[5];
+    const uint32_t bm = __float_as_uint(m.Mt[i]), bu = __float_as_uint(m.Ut[i]);
+    if ((bm >> top) == (pm >> top)) atomicAdd(&s_h[(bm >> shift) & mask], 1u);
+    if ((bu >> top) == (pu >> top)) atomicAdd(&s_h[kSelBins + ((bu >> shift) & mask)], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x)
+    if (s_h[k]) atomicAdd(&m.hist[k], s_h[k]);
+  if (last_cta(m.sel + 3)) select_finish(m, level, c);
+}
+
+__global__ void __launch_bounds__(kMpBlock)
+mp_labels_kernel(MpWs m, int64_t n, uint8_t *__restrict__ labels) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !m.obs[i]) return;
+  labels[i] = (double)m.Mt[i] > m.stats[0] ? 1 : 0;
+}
+
+__global__ void mp_region_stats_kernel(MpWs m, MpCfg c) {
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
+    float4 reg;
+    region_params(m, c, k, &reg);
+    const double cnt = m.acc[4 * k + 0];
+    double *o = m.stats + DAGS_MP_STATS_HEAD + 4 * k;
+    o[0] = cnt;
+    o[1] = cnt > 0.0 ? m.acc[4 * k + 1] / cnt : 0.0;
+    o[2] = cnt > 0.0 ? sqrt(m.acc[4 * k + 2] / cnt) : 0.0;
+    o[3] = reg.y;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
+                             const float4 *targets, const float *image, const uint8_t *inst, const float *table,
+                             int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
+                             double *stats, cudaStream_t s) {
+  MpWs m;
+  m.e = b.e; m.acc = b.acc; m.mhat = b.mhat; m.sige = b.sige; m.U = b.U; m.Mt = b.Mt; m.Ut = b.Ut;
+  m.obs = b.obs; m.hist = b.hist; m.sel = b.sel; m.stats = stats;
+  MpCfg c;
+  c.kappa_c = cfg.kappa_c; c.lam = cfg.lam; c.sigma_min = cfg.sigma_min; c.e_floor = cfg.e_floor;
+  c.sigma_g = cfg.sigma_g; c.sigma_c = cfg.sigma_c; c.lam_u = cfg.lam_u; c.eps = cfg.eps;
+  c.alpha_min = cfg.alpha_min; c.alpha_max = cfg.alpha_max; c.rho = cfg.rho; c.r_s = cfg.r_s;
+  c.sigma_w = cfg.sigma_w; c.vis_tol = cfg.vis_tol; c.z_near = cfg.z_near; c.tau_floor = cfg.tau_floor;
+  c.fusion_mode = cfg.fusion_mode; c.seg_refreshed = seg_refreshed; c.n_regions = n_regions;
+  const int P = r.W * r.H;
+  // the region accumulators start at zero (the select state is cleared by
+  // the first kernel)
+  cudaError_t e = cudaMemsetAsync(b.acc, 0, DAGS_MP_MAX_REGIONS * 4 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const unsigned gp = (unsigned)((P + kMpBlock - 1) / kMpBlock);
+  const unsigned gg = (unsigned)((n + kMpBlock - 1) / kMpBlock > 0 ? (n + kMpBlock - 1) / kMpBlock : 1);
+  mp_pixel_sum_kernel<<<gp, kMpBlock, 0, s>>>(m, targets, image, inst, P, c);
+  mp_pixel_var_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, P, c);
+  mp_gauss_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<const float4 *>(gauss), n, pose, image, inst,
+                                          reinterpret_cast<const float2 *>(table), r, c);
+  mp_apply_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<float4 *>(gauss), n, c);
+  mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 1, c);
+  mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 2, c);
+  mp_labels_kernel<<<gg, kMpBlock, 0, s>>>(m, n, labels);
+  mp_region_stats_kernel<<<1, 256, 0, s>>>(m, c);
+  return cudaGetLastError();
+}
+
+}  // namespace dags

@@ -49,6 +49,15 @@ class CLossCfg(ctypes.Structure):
                 ("weight_grad", ctypes.c_int32), ("o_eps", ctypes.c_float)]
 
 
+class CMpCfg(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("kappa_c", "lam", "sigma_min", "e_floor", "sigma_g", "sigma_c",
+                                              "lam_u", "eps", "alpha_min", "alpha_max", "rho", "r_s", "sigma_w",
+                                              "vis_tol", "z_near", "tau_floor")] + [("fusion_mode", ctypes.c_int32)]
+
+
+MP_STATS_HEAD = 6
+
+
 class CPoseCfg(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double * 6), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double)]
@@ -57,7 +66,7 @@ class CPoseCfg(ctypes.Structure):
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
-           "splat_track", "splat_forward_static"]
+           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet"]
@@ -108,6 +117,10 @@ def load(path: str = LIB_PATH):
     lib.splat_forward_static.argtypes = [P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
                                          ctypes.POINTER(CLossCfg), P, P, P, P, P]
     lib.splat_forward_static.restype = ctypes.c_int
+    lib.dags_default_mp_cfg.argtypes = [ctypes.POINTER(CMpCfg)]
+    lib.mp_update.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, P, P, P, I32, ctypes.POINTER(CMpCfg), I32, P,
+                              P, P]
+    lib.mp_update.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -158,6 +171,14 @@ def default_pose_cfg(lr=None, **kw) -> CPoseCfg:
     if lr is not None:
         for k in range(6):
             c.lr[k] = float(lr[k] if hasattr(lr, "__len__") else lr)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_mp_cfg(**kw) -> CMpCfg:
+    c = CMpCfg()
+    load().dags_default_mp_cfg(ctypes.byref(c))
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -288,6 +309,24 @@ class Context:
                                     ctypes.byref(rc), ctypes.byref(lc), ctypes.byref(pc), int(iters),
                                     _ptr(adam_state), _ptr(image), _ptr(last), _ptr(loss), _ptr(grad_pose),
                                     int(bool(use_graph)), _stream()), "splat_track")
+
+    def mp_update(self, gauss, cam: Camera, pose, targets, image, inst, table, labels, cfg=None, seg_refreshed=True,
+                  stats=None):
+        """Spatiotemporal MP update of one view; gauss's MP words and labels are
+        updated in place. Returns the stats tensor (float64)."""
+        _need(gauss, torch.float32, "gauss")
+        _need(inst, torch.uint8, "inst")
+        _need(labels, torch.uint8, "labels")
+        _need(table, torch.float32, "table")
+        nreg = table.shape[0]
+        if stats is None:
+            stats = torch.empty(MP_STATS_HEAD + 4 * nreg, dtype=torch.float64, device=gauss.device)
+        c = cam.c()
+        mc = cfg if cfg is not None else default_mp_cfg()
+        _check(self.lib.mp_update(self.h, _ptr(gauss), gauss.shape[0], ctypes.byref(c), _ptr(pose), _ptr(targets),
+                                  _ptr(image), _ptr(inst), _ptr(table), nreg, ctypes.byref(mc), int(bool(seg_refreshed)),
+                                  _ptr(labels), _ptr(stats), _stream()), "mp_update")
+        return stats
 
     def pose_step(self, poses, grad_pose, adam_state, cfg=None):
         _need(poses, torch.float64, "poses")

@@ -1,0 +1,128 @@
+"""GPU MP update (mp_update, C ABI) against the FP64 oracle (oracle/mp.py).
+
+Inputs are synthetic and identical on both sides: observed RGB-D = the
+ray-cast frame with moved objects; 'rendered' RGB-D = the ray-cast of the
+map's static geometry at the same pose (the analytic stand-in for a render,
+so that no oracle input comes from the CUDA path); instance labels with 5%
+flips."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import mp as omp
+from paper_2602_21644_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+M_ABS = 1e-5           # per-Gaussian M^t and the medians (FP32 vs FP64)
+
+
+@pytest.fixture(scope="module")
+def dags():
+    from paper_2602_21644_gb300 import build
+    build.build()
+    from paper_2602_21644_gb300 import dags as d
+    d.load()
+    return d
+
+
+def mp_scene(n, frame, width, height, seed=0):
+    sc = synth.tracking_scene(n, frame=frame, width=width, height=height, seed=seed)
+    pose = sc.extra["gt_pose"]
+    static, _ = synth.raycast(sc.camera, pose, sc.extra["objects"], 0.0)     # map geometry (frame 0)
+    obs = sc.targets[0].copy()
+    rng = np.random.default_rng(seed + 3)
+    mp0 = rng.uniform(0.05, 0.95, n).astype(np.float32)
+    rec = sc.records.copy()
+    rec[:, 11] = mp0
+    labels0 = (rng.random(n) < 0.3).astype(np.uint8)
+    table = np.array([[0.1, 0.05]] + [[0.9, 0.8]] * sc.extra["n_instances"], np.float32)
+    return dict(rec=rec, cam=sc.camera, pose=pose, obs=obs, rend=static, inst=sc.extra["instance"], table=table,
+                labels0=labels0)
+
+
+def run_both(dags, d, cfg_kw=None, seg_refreshed=True):
+    cfg_kw = cfg_kw or {}
+    cam = dags.Camera(*d["cam"].as_tuple())
+    P = cam.width * cam.height
+    dev = "cuda"
+    gauss = torch.from_numpy(d["rec"].copy()).to(dev)
+    image = torch.zeros((8, P), dtype=torch.float32)
+    image[0:3] = torch.from_numpy(d["rend"][:, 0:3].T.copy())
+    image[3] = torch.from_numpy(d["rend"][:, 3].copy())
+    image = image.to(dev)
+    tg = torch.from_numpy(d["obs"].copy()).to(dev)
+    inst = torch.from_numpy(d["inst"].copy()).to(dev)
+    table = torch.from_numpy(d["table"].copy()).to(dev)
+    labels = torch.from_numpy(d["labels0"].copy()).to(dev)
+    pose = torch.from_numpy(np.ascontiguousarray(d["pose"])).to(dev)
+    ctx = dags.Context(gauss.shape[0], cam.width, cam.height, 1)
+    stats = ctx.mp_update(gauss, cam, pose, tg, image, inst, table, labels, dags.default_mp_cfg(**cfg_kw),
+                          seg_refreshed)
+    torch.cuda.synchronize()
+    gpu = dict(mp=gauss[:, 11].cpu().numpy().astype(np.float64), labels=labels.cpu().numpy(),
+               stats=stats.cpu().numpy())
+    cfg = dataclasses.replace(omp.MPConfig(), **cfg_kw)
+    ref = omp.mp_update(d["rec"][:, 0:3], d["rec"][:, 11], d["labels0"], d["cam"].as_tuple(), d["pose"], d["inst"],
+                        d["obs"][:, 3], d["obs"][:, 0:3], d["rend"][:, 3], d["rend"][:, 0:3], d["table"], cfg,
+                        seg_refreshed)
+    return gpu, ref
+
+
+def check(gpu, ref, nreg):
+    flag = ref["disk_flag"] | ref["vis_flag"]
+    ok = ~flag
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(gpu["mp"][ok], ref["mp"][ok], rtol=0, atol=M_ABS)
+    st = gpu["stats"]
+    assert st[5] == ref["observed"].sum() or abs(st[5] - ref["observed"].sum()) <= flag.sum()
+    assert abs(st[0] - ref["tau"]) <= M_ABS
+    assert abs(st[1] - ref["U_bar"]) <= M_ABS
+    lab_ok = ok & ~ref["label_flag"] & (np.abs(gpu["mp"] - st[0]) > M_ABS)
+    np.testing.assert_array_equal(gpu["labels"][lab_ok], ref["labels"][lab_ok])
+    px = ref["pixel"]
+    for k in range(nreg):
+        r = st[6 + 4 * k: 10 + 4 * k]
+        assert r[0] == px["count"][k]
+        np.testing.assert_allclose(r[1:4], [px["mean"][k], px["std"][k], px["e_ub"][k]], rtol=1e-5, atol=1e-7)
+    assert np.all((gpu["mp"] >= 0) & (gpu["mp"] <= 1))
+    assert st[0] >= 0.5
+
+
+@pytest.mark.parametrize("frame", [6, 30])
+def test_mp_update_matches_oracle(dags, frame):
+    d = mp_scene(60_000, frame, 320, 240)
+    gpu, ref = run_both(dags, d)
+    check(gpu, ref, d["table"].shape[0])
+    # the moving objects' Gaussians end with higher MP than the room's
+    dyn = synth.tracking_scene(60_000, frame=frame, width=320, height=240).dynamic
+    obs = ref["observed"]
+    assert gpu["mp"][dyn & obs].mean() > gpu["mp"][~dyn & obs].mean()
+
+
+@pytest.mark.parametrize("kw,refreshed", [({"fusion_mode": 1}, True), ({"fusion_mode": 2}, True),
+                                          ({"alpha_min": 0.3, "alpha_max": 0.3}, False), ({}, False),
+                                          ({"vis_tol": 0.0}, True)])
+def test_mp_update_variants(dags, kw, refreshed):
+    d = mp_scene(40_000, 12, 256, 192, seed=1)
+    gpu, ref = run_both(dags, d, kw, refreshed)
+    check(gpu, ref, d["table"].shape[0])
+
+
+def test_mp_update_full_size(dags):
+    d = mp_scene(300_000, 20, 640, 480, seed=2)
+    gpu, ref = run_both(dags, d)
+    check(gpu, ref, d["table"].shape[0])
+
+
+def test_mp_update_nothing_observed(dags):
+    d = mp_scene(2_000, 5, 160, 120)
+    d["pose"] = d["pose"].copy()
+    d["pose"][:, 3] += np.array([0.0, 0.0, -100.0])    # everything behind the camera
+    gpu, ref = run_both(dags, d)
+    assert not ref["observed"].any()
+    np.testing.assert_array_equal(gpu["mp"], d["rec"][:, 11].astype(np.float64))
+    np.testing.assert_array_equal(gpu["labels"], d["labels0"])
+    assert gpu["stats"][0] == 0.5 and gpu["stats"][5] == 0
