@@ -121,8 +121,8 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
     Returns dict with mp (n), labels (n, uint8), observed (n bool), m_hat,
     U, U_tilde, alpha (after Eq. (17)), tau, U_bar, median_M, the pixel dict,
     and decision-margin flags: label_flag (|M^t - tau| small), disk_flag (a
-    pixel within 1e-5 of the association radius), vis_flag (occlusion test
-    within 1e-5).
+    pixel within FP32 coordinate rounding of the association radius),
+    vis_flag (occlusion test within 1e-5).
     """
     cfg = MPConfig() if cfg is None else cfg
     fx, fy, cx, cy, W, H = cam
@@ -164,7 +164,11 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
         jj = np.floor(v).astype(np.int64)[:, None] + oj[None, :]
         inside = (ii >= 0) & (ii < W) & (jj >= 0) & (jj < H) & ok_uv[:, None]
         d2 = (ii - u[:, None]) ** 2 + (jj - v[:, None]) ** 2
-        disk_flag[c0:c1] = np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= 1e-5 * cfg.r_s ** 2), axis=1)
+        # a pixel whose distance lies within the FP32 rounding of the projected
+        # centre (a few ulps of |u|, |v|) of the radius is an undecided member
+        ecoord = 2.0 ** -22 * np.maximum(np.maximum(np.abs(u), np.abs(v)), 1.0)[:, None]
+        dmarg = 4.0 * cfg.r_s * ecoord + 1e-5 * cfg.r_s ** 2
+        disk_flag[c0:c1] = np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= dmarg), axis=1)
         sel = inside & (d2 <= cfg.r_s ** 2)
         cnt = sel.sum(1)
         pidx = np.where(sel, jj * W + ii, 0)
