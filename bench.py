@@ -4,8 +4,7 @@
 Metric: splat fwd+bwd iterations/s at 300k Gaussians, 640x480 (the tracking
 workload: one step = one tracking frame = `--iters` (100) pose-only
 forward + backward + FP64 pose-step iterations through the C ABI, plus the
-per-frame MP update when the library has it), and the fraction of the HBM
-roofline.
+per-frame MP update), and the fraction of the HBM roofline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -150,7 +149,7 @@ def run_reference(args):
 def workload_config(args):
     return {"workload": f"tracking frame of the synthetic room: {args.gaussians} Gaussians, "
                         f"{args.width}x{args.height} RGB-D, {args.iters} pose-only fwd+bwd iterations "
-                        f"with FP64 pose steps per step",
+                        f"with FP64 pose steps and one MP update per step",
             "gaussians": args.gaussians, "width": args.width, "height": args.height,
             "iters_per_step": args.iters,
             "l2": "flushed between steps by a 256 MiB write; inside a step the iterations re-read the "
@@ -201,6 +200,11 @@ def run_ours(args):
     gpose = torch.empty((1, 6), dtype=torch.float64, device=dev)
     ctx = dags.Context(n, cam.width, cam.height, 1)
     pcfg = dags.default_pose_cfg(lr=[1e-3, 1e-3, 1e-3, 5e-4, 5e-4, 5e-4])
+    # per-frame MP update inputs: the frame's instance prior and class table
+    inst = torch.from_numpy(sc.extra["instance"]).to(dev)
+    table = torch.tensor([[0.1, 0.05]] + [[0.9, 0.8]] * sc.extra["n_instances"], dtype=torch.float32, device=dev)
+    labels = torch.zeros(n, dtype=torch.uint8, device=dev)
+    mp_stats = torch.empty(dags.MP_STATS_HEAD + 4 * table.shape[0], dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def frame(use_graph=True):
@@ -208,6 +212,7 @@ def run_ours(args):
         state.zero_()
         ctx.track(gauss, cam, poses, targets, args.iters, state, image, last, loss, gpose, pcfg=pcfg,
                   use_graph=use_graph)
+        ctx.mp_update(gauss, cam, poses, targets, image, inst, table, labels, stats=mp_stats)
 
     # warm-up (captures the iteration graph; checks the device status once)
     for _ in range(max(1, args.warmup)):
@@ -271,6 +276,7 @@ def run_ours(args):
         poses.copy_(pose_host, non_blocking=True)
         state.zero_()
         ctx.track(gauss, cam, poses, targets, args.iters, state, image, last, loss, gpose, pcfg=pcfg)
+        ctx.mp_update(gauss, cam, poses, targets, image, inst, table, labels, stats=mp_stats)
         pose_out.copy_(poses, non_blocking=True)
         loss_out.copy_(loss, non_blocking=True)
 
@@ -304,7 +310,9 @@ def run_ours(args):
                 "alg_bytes_per_launch": ab[dom]}
     iter_bytes = sum(ab.values())
     iter_us = 1e3 * t_ms / (args.iters * args.steps)
-    gpu_launches = sum(c for _, (_, c) in kt.items()) + kt["tile_sort"][1]   # tile sort = 2 kernels
+    # kernels per step: per iteration preprocess, emit, render_fwd, render_bwd,
+    # preprocess_bwd (pose step fused); per frame the MP update's 8 kernels
+    gpu_launches = args.steps * (args.iters * 5 + 8)
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
