@@ -288,6 +288,31 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
               int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
               double *stats, void *stream);
 
+/* Learned per-pixel MP proposal network (not in the paper: the task's
+ * learned stand-in for the stale instance prior between scheduled semantic
+ * invocations, Sec. IV-B). Per pixel, NHWC:
+ *   z1 = W1 x + b1 (1x1, 8 -> 32), a1 = bf16(relu(z1))
+ *   z2 = conv3x3(a1) + b2 (32 -> 32, zero padding), a2 = bf16(relu(z2))
+ *   z3 = W3 a2 + b3 (1x1), a3 = bf16(relu(z3))
+ *   y  = sigmoid(w4 . a3 + b4)
+ * BF16 operands on the tensor cores (tcgen05) with FP32 accumulation.
+ * Input channels: rendered MP, |dR|, |dG|, |dB|, |dDepth|, depth, rendered
+ * opacity, prior mask.
+ * Weight blob (device, DAGS_MPNET_WEIGHT_BYTES, 16-byte aligned), byte
+ * offsets: W1 bf16 [32][16] at 0 (input channels 8-15 zero), W2 bf16
+ * [32][288] at 1024 (column (ky * 3 + kx) * 32 + in), W3 bf16 [32][32] at
+ * 19456, w4 bf16 [32] at 21504, b1 f32 [32] at 21568, b2 at 21696, b3 at
+ * 21824, b4 f32 at 21952. */
+#define DAGS_MPNET_WEIGHT_BYTES 22016
+#define DAGS_MPNET_ACT_WORDS 96
+
+/* Inference: feats device, batch x height x width x 8 bf16 (16-byte
+ * aligned); mp_out device, batch x height x width float; acts device or NULL:
+ * per pixel 96 bf16 (a1, a2, a3) for training. A wait that gives up records
+ * DAGS_E_TIMEOUT in the status word. */
+int mpnet_infer(dags_ctx *ctx, const void *weights, const uint16_t *feats, int32_t batch, int32_t width,
+                int32_t height, float *mp_out, uint16_t *acts, void *stream);
+
 /* Per-kernel device timing (tracing). When enabled, every kernel the
  * library launches on a stream that is not being captured into a CUDA graph
  * is bracketed by a pair of CUDA events on that stream. dags_timing_read

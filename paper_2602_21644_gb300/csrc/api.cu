@@ -75,6 +75,7 @@ struct TrackGraph {
 
 struct dags_ctx {
   int device = 0;
+  int num_sms = 0;
   Workspace ws;
   KernelTimer timer;
   TrackGraph graph;
@@ -225,7 +226,11 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   if (max_pairs > (int64_t)0xFFFFFFFE) return DAGS_E_INVAL;
   dags_ctx *c = new (std::nothrow) dags_ctx();
   if (!c) return DAGS_E_NOMEM;
-  if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return DAGS_E_CUDA; }
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return DAGS_E_CUDA;
+  }
   Workspace &w = c->ws;
   w.max_n = max_gaussians > 0 ? max_gaussians : 1;
   w.max_w = max_width;
@@ -567,6 +572,20 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
   const int ev = ctx->timer.begin(DAGS_K_MP_GAUSS, s);
   const cudaError_t e = launch_mp_update(ctx->mp, gauss, n, pose, r, reinterpret_cast<const float4 *>(targets),
                                          image, inst, table, n_regions, c, seg_refreshed ? 1 : 0, labels, stats, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+int mpnet_infer(dags_ctx *ctx, const void *weights, const uint16_t *feats, int32_t batch, int32_t width,
+                int32_t height, float *mp_out, uint16_t *acts, void *stream) {
+  if (!ctx || !weights || !feats || !mp_out || batch < 1 || width < 1 || height < 1) return DAGS_E_INVAL;
+  if (((uintptr_t)feats & 15u) != 0 || ((uintptr_t)weights & 15u) != 0 || ((uintptr_t)acts & 15u) != 0)
+    return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_MPNET, s);
+  const cudaError_t e = launch_mpnet_forward(weights, feats, batch, width, height, mp_out, acts,
+                                             ctx->ws.counters + CNT_STATUS, ctx->num_sms, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

@@ -109,6 +109,9 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
 cudaError_t launch_pose_step(double *poses, const double *grad, double *state, int views,
                              const dags_pose_cfg &cfg, cudaStream_t s);
 
+cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
+                                 uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s);
+
 // Buffers of the MP update (owned by the ctx).
 struct MpBuffers {
   float *e = nullptr;                 // [max_w * max_h]

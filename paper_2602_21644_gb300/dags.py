@@ -56,6 +56,8 @@ class CMpCfg(ctypes.Structure):
 
 
 MP_STATS_HEAD = 6
+MPNET_WEIGHT_BYTES = 22016
+MPNET_ACT_WORDS = 96
 
 
 class CPoseCfg(ctypes.Structure):
@@ -66,7 +68,7 @@ class CPoseCfg(ctypes.Structure):
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
-           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update"]
+           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_infer"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet"]
@@ -121,6 +123,8 @@ def load(path: str = LIB_PATH):
     lib.mp_update.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, P, P, P, I32, ctypes.POINTER(CMpCfg), I32, P,
                               P, P]
     lib.mp_update.restype = ctypes.c_int
+    lib.mpnet_infer.argtypes = [P, P, P, I32, I32, I32, P, P, P]
+    lib.mpnet_infer.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -327,6 +331,18 @@ class Context:
                                   _ptr(image), _ptr(inst), _ptr(table), nreg, ctypes.byref(mc), int(bool(seg_refreshed)),
                                   _ptr(labels), _ptr(stats), _stream()), "mp_update")
         return stats
+
+    def mpnet_infer(self, weights, feats, out=None, acts=None):
+        """feats: [B, H, W, 8] bfloat16 CUDA tensor; weights: uint8 blob of
+        MPNET_WEIGHT_BYTES. Returns the [B, H, W] float MP map."""
+        B, H, W, C = feats.shape
+        if C != 8 or feats.dtype != torch.bfloat16 or not feats.is_contiguous():
+            raise ValueError("feats must be a contiguous [B, H, W, 8] bfloat16 tensor")
+        if out is None:
+            out = torch.empty((B, H, W), dtype=torch.float32, device=feats.device)
+        _check(self.lib.mpnet_infer(self.h, _ptr(weights), _ptr(feats), B, W, H, _ptr(out), _ptr(acts), _stream()),
+               "mpnet_infer")
+        return out
 
     def pose_step(self, poses, grad_pose, adam_state, cfg=None):
         _need(poses, torch.float64, "poses")
