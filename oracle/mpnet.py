@@ -23,10 +23,15 @@ the backward treats the BF16 rounding of activations as the identity.
 Input channels (per pixel): rendered MP, |dR|, |dG|, |dB|, |dDepth|, depth,
 rendered opacity, prior mask. Tensors are NHWC.
 
+Training step: Adam (Kingma and Ba, 2015) with beta1 0.9, beta2 0.999,
+eps 1e-8 on FP32 master weights; the network's optimiser is not in the paper
+and this is the reading taken.
+
 Pins (tests/test_oracle_mpnet.py): conv3x3 against torch.nn.functional.conv2d
 in float64, the BF16 rounding against torch's bfloat16 conversion, the
-parameter count (10,625), and central finite differences of the loss with
-rounding off.
+parameter count (10,625), central finite differences of the loss with
+rounding off, and Adam against torch.optim.Adam and its first-step closed
+form (every parameter moves by lr against the sign of its gradient).
 """
 from __future__ import annotations
 
@@ -120,6 +125,21 @@ def loss_and_grads(x, target, p, rounding=True):
     g["b1"] = dz1.sum((0, 1, 2))
     g["W1"] = np.einsum("bhwo,bhwi->oi", dz1, np.asarray(x, np.float64))
     return L, g, f
+
+
+def adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma and Ba, 2015, Algorithm 1) on dicts of arrays:
+    first and second moment estimates with bias correction by the step count
+    (step >= 1). Returns (params, m, v) as new dicts."""
+    out_p, out_m, out_v = {}, {}, {}
+    for k in params:
+        g = np.asarray(grads[k], np.float64)
+        out_m[k] = beta1 * m[k] + (1 - beta1) * g
+        out_v[k] = beta2 * v[k] + (1 - beta2) * g * g
+        mhat = out_m[k] / (1 - beta1 ** step)
+        vhat = out_v[k] / (1 - beta2 ** step)
+        out_p[k] = params[k] - lr * mhat / (np.sqrt(vhat) + eps)
+    return out_p, out_m, out_v
 
 
 def pack_weights(p):

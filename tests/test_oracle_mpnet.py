@@ -72,3 +72,29 @@ def test_pack_layout():
     assert w["W1"].shape == (32, 16) and np.all(w["W1"][:, 8:] == 0)
     o, i, ky, kx = 5, 7, 2, 0
     assert w["W2"][o, (ky * 3 + kx) * 32 + i] == p["W2"][o, i, ky, kx]
+
+
+def test_adam_first_step_closed_form():
+    # after one step, m_hat = g and v_hat = g^2, so every weight moves by
+    # lr * g / (|g| + eps)
+    rng = np.random.default_rng(8)
+    p = {"a": rng.normal(0, 1, 50)}
+    g = {"a": rng.normal(0, 1, 50)}
+    z = {"a": np.zeros(50)}
+    q, m, v = N.adam_step(p, g, z, z, 1, 0.01)
+    np.testing.assert_allclose(q["a"], p["a"] - 0.01 * g["a"] / (np.abs(g["a"]) + 1e-8), rtol=0, atol=1e-15)
+
+
+def test_adam_matches_torch_optim():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(9)
+    w0 = rng.normal(0, 1, 40)
+    gs = [rng.normal(0, 1, 40) for _ in range(5)]
+    t = torch.tensor(w0.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([t], lr=3e-3, betas=(0.9, 0.999), eps=1e-8)
+    p, m, v = {"w": w0.copy()}, {"w": np.zeros(40)}, {"w": np.zeros(40)}
+    for k, g in enumerate(gs, start=1):
+        t.grad = torch.tensor(g)
+        opt.step()
+        p, m, v = N.adam_step(p, {"w": g}, m, v, k, 3e-3)
+    np.testing.assert_allclose(p["w"], t.detach().numpy(), rtol=0, atol=1e-14)
