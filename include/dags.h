@@ -313,6 +313,30 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
 int mpnet_infer(dags_ctx *ctx, const void *weights, const uint16_t *feats, int32_t batch, int32_t width,
                 int32_t height, float *mp_out, uint16_t *acts, void *stream);
 
+/* Training step (mean binary cross-entropy over pixels whose target is
+ * >= 0, then one Adam step, beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected
+ * with `step` >= 1). Gradients flow through the BF16 activations as if their
+ * rounding were the identity; the pixel reductions of the weight gradients
+ * run on the tensor cores in BF16 with FP32 accumulation.
+ * Parameter vector (FP32, DAGS_MPNET_PARAMS floats, layout of master, adam_m,
+ * adam_v and grad_out): W1 [32][16] at 0, W2 [32][288] at 512, W3 [32][32]
+ * at 9728, w4 [32] at 10752, b1 [32] at 10784, b2 at 10816, b3 at 10848, b4
+ * at 10880 (same row/column order as the blob). master holds the FP32
+ * weights; the step updates master, adam_m and adam_v in place and rewrites
+ * the blob from master (weights rounded to BF16). W1's padded input
+ * channels 8-15 stay zero.
+ * feats as for mpnet_infer; target device float [batch][height][width],
+ * negative = pixel excluded; loss device double (written: the loss at the
+ * weights before the step); grad_out device float [DAGS_MPNET_PARAMS] or
+ * NULL. Scratch of 2 + 2 * 96 + 2 * 32 bytes per pixel is owned by the ctx
+ * and grows on demand (synchronising the stream); the call is not
+ * capturable when it grows. lr >= 0. Errors: DAGS_E_INVAL for NULL or
+ * unaligned buffers or bad sizes, DAGS_E_NOMEM, DAGS_E_CUDA. */
+#define DAGS_MPNET_PARAMS 10881
+int mpnet_train_step(dags_ctx *ctx, void *weights, float *master, float *adam_m, float *adam_v, int32_t step,
+                     const uint16_t *feats, const float *target, int32_t batch, int32_t width, int32_t height,
+                     float lr, double *loss, float *grad_out, void *stream);
+
 /* Per-kernel device timing (tracing). When enabled, every kernel the
  * library launches on a stream that is not being captured into a CUDA graph
  * is bracketed by a pair of CUDA events on that stream. dags_timing_read
@@ -330,7 +354,8 @@ enum {
   DAGS_K_POSE_STEP,        /* FP64 pose step                               */
   DAGS_K_MP_PIXEL,         /* MP update: per-pixel observation             */
   DAGS_K_MP_GAUSS,         /* MP update: per-Gaussian update and medians   */
-  DAGS_K_MPNET,            /* learned MP network                           */
+  DAGS_K_MPNET,            /* learned MP network, inference                */
+  DAGS_K_MPNET_TRAIN,      /* learned MP network, training step            */
   DAGS_KERNEL_COUNT
 };
 int dags_timing_enable(dags_ctx *ctx, int enable);

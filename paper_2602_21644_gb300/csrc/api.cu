@@ -80,6 +80,7 @@ struct dags_ctx {
   KernelTimer timer;
   TrackGraph graph;
   MpBuffers mp;
+  MpnetScratch net;
   PoseStep fused_step;            // set only inside the tracking loop
   cudaStream_t last_stream = nullptr;
   // the buffers of the latest forward (backward must follow its forward)
@@ -111,6 +112,13 @@ void free_mp(MpBuffers &b) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   b = MpBuffers();
+}
+
+void free_net(MpnetScratch &b) {
+  void *ptrs[] = {b.y, b.acts, b.dz2, b.grad, b.inv_n};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  b = MpnetScratch();
 }
 
 bool finite_pos(float x) { return isfinite(x) && x > 0.f; }
@@ -299,6 +307,7 @@ void dags_destroy(dags_ctx *ctx) {
   if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
   if (ctx->graph.cap) cudaStreamDestroy(ctx->graph.cap);
   free_mp(ctx->mp);
+  free_net(ctx->net);
   free_ws(ctx->ws);
   cudaSetDevice(cur);
   delete ctx;
@@ -586,6 +595,41 @@ int mpnet_infer(dags_ctx *ctx, const void *weights, const uint16_t *feats, int32
   const int ev = ctx->timer.begin(DAGS_K_MPNET, s);
   const cudaError_t e = launch_mpnet_forward(weights, feats, batch, width, height, mp_out, acts,
                                              ctx->ws.counters + CNT_STATUS, ctx->num_sms, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+int mpnet_train_step(dags_ctx *ctx, void *weights, float *master, float *adam_m, float *adam_v, int32_t step,
+                     const uint16_t *feats, const float *target, int32_t batch, int32_t width, int32_t height,
+                     float lr, double *loss, float *grad_out, void *stream) {
+  if (!ctx || !weights || !master || !adam_m || !adam_v || !feats || !target || !loss) return DAGS_E_INVAL;
+  if (batch < 1 || width < 1 || height < 1 || step < 1 || !isfinite(lr) || lr < 0.f) return DAGS_E_INVAL;
+  if (((uintptr_t)feats & 15u) != 0 || ((uintptr_t)weights & 15u) != 0) return DAGS_E_INVAL;
+  const long long npix = (long long)batch * width * height;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  MpnetScratch &sc = ctx->net;
+  if (sc.cap < npix) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    free_net(sc);
+    e = alloc(&sc.y, (size_t)npix);
+    if (e == cudaSuccess) e = alloc(&sc.acts, (size_t)npix * DAGS_MPNET_ACT_WORDS);
+    if (e == cudaSuccess) e = alloc(&sc.dz2, (size_t)npix * 32);
+    if (e == cudaSuccess) e = alloc(&sc.grad, DAGS_MPNET_PARAMS);
+    if (e == cudaSuccess) e = alloc(&sc.inv_n, 2);
+    if (e != cudaSuccess) {
+      free_net(sc);
+      cudaGetLastError();
+      return DAGS_E_NOMEM;
+    }
+    sc.cap = npix;
+  }
+  const int ev = ctx->timer.begin(DAGS_K_MPNET_TRAIN, s);
+  cudaError_t e = launch_mpnet_train(weights, master, adam_m, adam_v, step, feats, target, batch, width, height, lr,
+                                     loss, sc, ctx->ws.counters + CNT_STATUS, ctx->num_sms, s);
+  if (e == cudaSuccess && grad_out)
+    e = cudaMemcpyAsync(grad_out, sc.grad, DAGS_MPNET_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

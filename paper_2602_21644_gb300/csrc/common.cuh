@@ -112,6 +112,19 @@ cudaError_t launch_pose_step(double *poses, const double *grad, double *state, i
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s);
 
+// Scratch of a training step of the MP network (owned by the ctx).
+struct MpnetScratch {
+  float *y = nullptr;        // [pixels]
+  uint16_t *acts = nullptr;  // [pixels][96] bf16
+  uint16_t *dz2 = nullptr;   // [pixels][32] bf16
+  float *grad = nullptr;     // [10881]
+  float *inv_n = nullptr;    // [2]: 1 / valid pixels, valid count
+  long long cap = 0;         // pixels
+};
+cudaError_t launch_mpnet_train(void *weights, float *master, float *adam_m, float *adam_v, int step,
+                               const uint16_t *feats, const float *target, int batch, int W, int H, float lr,
+                               double *loss, const MpnetScratch &sc, uint32_t *status, int num_sms, cudaStream_t s);
+
 // Buffers of the MP update (owned by the ctx).
 struct MpBuffers {
   float *e = nullptr;                 // [max_w * max_h]

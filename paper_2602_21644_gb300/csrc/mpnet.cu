@@ -326,7 +326,7 @@ mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ 
       }
     }
     tc_before_sync();
-    __syncthreads();
+    ok = __syncthreads_and(ok) != 0;   // uniform loop exit
   }
   if (!ok) {
     // a wait gave up: record it and give in-flight MMAs one more bounded wait
@@ -339,6 +339,445 @@ mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ 
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
+
+// ----------------------------------------------------------------- training
+//
+// Mean binary cross-entropy over pixels with target >= 0; the backward
+// treats the BF16 rounding of activations as the identity. Weight gradients
+// reduce over pixels: per 128-pixel tile they are UMMAs with the pixels as
+// the K dimension (A = activations channel-major, B = upstream gradients
+// channel-major), accumulated in TMEM across all tiles of a persistent CTA
+// and added to the global FP32 gradient once per CTA. A row of ones appended
+// to A gives the bias gradients from the same MMAs. Only M = 128 MMAs are
+// used; A rows past the real ones are don't-care rows whose D rows are
+// ignored.
+
+constexpr int kGW1 = 0, kGW2 = 512, kGW3 = 512 + 9216, kGw4 = 512 + 9216 + 1024, kGb1 = kGw4 + 32,
+              kGb2 = kGb1 + 32, kGb3 = kGb2 + 32, kGb4 = kGb3 + 32, kGTotal = kGb4 + 1;   // 10881 floats
+
+// Planar (channel-major) K-major operand: row = channel, K = the tile's 128
+// pixels: SBO = 16 * 128 = 2048 B.
+__device__ __forceinline__ uint32_t planar_off(int row, int px) { return core_off(row, px, kTileW); }
+
+__global__ void mpnet_count_kernel(const float *__restrict__ target, long long n, float *__restrict__ inv_n,
+                                   float *__restrict__ loss_acc) {
+  __shared__ unsigned s_cnt;
+  if (threadIdx.x == 0) s_cnt = 0u;
+  __syncthreads();
+  unsigned c = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    c += target[i] >= 0.f ? 1u : 0u;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_cnt, c);
+  __syncthreads();
+  if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned *>(inv_n) + 1, s_cnt);   // count in word 1
+  (void)loss_acc;
+}
+
+__global__ void mpnet_count_finish_kernel(float *inv_n) {
+  const unsigned c = reinterpret_cast<unsigned *>(inv_n)[1];
+  inv_n[0] = c ? 1.f / (float)c : 0.f;
+}
+
+// bwd1 smem layout
+constexpr int kB1W3T = 0;                         // [32 i][32 o] = W3[o][i]
+constexpr int kB1Adz3 = kB1W3T + 2048;            // [128 px][32 o]
+constexpr int kB1Pdz3 = kB1Adz3 + 8192;           // planar [32 o][128 px]
+constexpr int kB1Pdz4 = kB1Pdz3 + 8192;           // planar [16][128 px], row 0 = dz4
+constexpr int kB1Pa2 = kB1Pdz4 + 4096;            // planar [128 rows][128 px]: a2 rows 0-31, ones row 32
+constexpr int kB1Pa3 = kB1Pa2 + 32768;            // planar [128][128]: a3 rows 0-31, ones row 32
+constexpr int kB1Par = kB1Pa3 + 32768;            // w4 f32 [32]
+constexpr int kB1Bar = kB1Par + 128;
+constexpr int kB1Smem = kB1Bar + 64;
+
+__global__ void __launch_bounds__(kNetThreads, 1)
+mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__ y, const float *__restrict__ target,
+                  const uint16_t *__restrict__ acts, int batch, int W, int H, const float *__restrict__ inv_n,
+                  uint16_t *__restrict__ dz2_out, float *__restrict__ grad, double *__restrict__ loss,
+                  uint32_t *__restrict__ status) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t *sW3T = smem + kB1W3T, *sAdz3 = smem + kB1Adz3, *sPdz3 = smem + kB1Pdz3, *sPdz4 = smem + kB1Pdz4;
+  uint8_t *sPa2 = smem + kB1Pa2, *sPa3 = smem + kB1Pa3;
+  float *sw4 = reinterpret_cast<float *>(smem + kB1Par);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kB1Bar);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kB1Bar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint16_t *gw3 = reinterpret_cast<const uint16_t *>(weights + kOffW3);
+  for (int e = tid; e < 32 * 32; e += kNetThreads) {
+    const int o = e / 32, i = e % 32;
+    *reinterpret_cast<uint16_t *>(sW3T + core_off(i, o, 32)) = gw3[e];
+  }
+  if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
+  // static parts: zero the planar operands, ones rows, dz4 rows 1-15
+  for (int e = tid; e < (32768 * 2 + 4096) / 16; e += kNetThreads)
+    reinterpret_cast<uint4 *>(sPdz4)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  {
+    const uint16_t one = 0x3F80;   // bf16 1.0
+    *reinterpret_cast<uint16_t *>(sPa2 + planar_off(32, tid)) = one;
+    *reinterpret_cast<uint16_t *>(sPa3 + planar_off(32, tid)) = one;
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)), "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  const uint32_t tmem = *s_tmem;   // D: dW3^T cols 0-31, da2 cols 32-63, dw4 cols 64-79
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  uint32_t phase = 0;
+  bool ok = true, first = true;
+  float lsum = 0.f;
+  const float invn = inv_n[0];
+  const int tiles_x = (W + kTileW - 1) / kTileW;
+  const long long ntiles = (long long)batch * H * tiles_x;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const int tx = (int)(t % tiles_x), yy = (int)((t / tiles_x) % H), b = (int)(t / ((long long)tiles_x * H));
+    const int p = tid, x = tx * kTileW + p;
+    const bool in = x < W;
+    const size_t pix = ((size_t)b * H + yy) * W + x;
+    float dz4 = 0.f;
+    uint32_t a2w[16], a3w[16];
+    if (in) {
+      const float tg = target[pix], yv = y[pix];
+      if (tg >= 0.f) {
+        dz4 = (yv - tg) * invn;
+        const float yc = fminf(fmaxf(yv, 1e-12f), 0.99999994f);   // largest float below 1
+        lsum -= (tg * logf(yc) + (1.f - tg) * logf(1.f - yc)) * invn;
+      }
+      const uint4 *ga = reinterpret_cast<const uint4 *>(acts + pix * 96);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const uint4 u2 = ga[4 + g], u3 = ga[8 + g];
+        a2w[4 * g] = u2.x; a2w[4 * g + 1] = u2.y; a2w[4 * g + 2] = u2.z; a2w[4 * g + 3] = u2.w;
+        a3w[4 * g] = u3.x; a3w[4 * g + 1] = u3.y; a3w[4 * g + 2] = u3.z; a3w[4 * g + 3] = u3.w;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 16; ++k) { a2w[k] = 0u; a3w[k] = 0u; }
+    }
+    // dz3 = dz4 w4 [a3 > 0]; operands for da2 (pixel-major dz3), dW3^T and dw4 (planar)
+    uint32_t dzw[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      const float a3lo = __uint_as_float(a3w[k] << 16), a3hi = __uint_as_float(a3w[k] & 0xFFFF0000u);
+      const float d0 = a3lo > 0.f ? dz4 * sw4[2 * k] : 0.f, d1 = a3hi > 0.f ? dz4 * sw4[2 * k + 1] : 0.f;
+      dzw[k] = pack_bf16x2(d0, d1);
+    }
+    store_row32(sAdz3, p, 0, 32, dzw);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      *reinterpret_cast<uint16_t *>(sPdz3 + planar_off(2 * k, p)) = (uint16_t)(dzw[k] & 0xFFFFu);
+      *reinterpret_cast<uint16_t *>(sPdz3 + planar_off(2 * k + 1, p)) = (uint16_t)(dzw[k] >> 16);
+      *reinterpret_cast<uint16_t *>(sPa2 + planar_off(2 * k, p)) = (uint16_t)(a2w[k] & 0xFFFFu);
+      *reinterpret_cast<uint16_t *>(sPa2 + planar_off(2 * k + 1, p)) = (uint16_t)(a2w[k] >> 16);
+      *reinterpret_cast<uint16_t *>(sPa3 + planar_off(2 * k, p)) = (uint16_t)(a3w[k] & 0xFFFFu);
+      *reinterpret_cast<uint16_t *>(sPa3 + planar_off(2 * k + 1, p)) = (uint16_t)(a3w[k] >> 16);
+    }
+    *reinterpret_cast<uint16_t *>(sPdz4 + planar_off(0, p)) = __bfloat16_as_ushort(__float2bfloat16_rn(dz4));
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+      for (int c = 0; c < 2; ++c)
+        mma_bf16(tmem + 32, sdesc(smem_u32(sAdz3) + c * 256, 128, 512), sdesc(smem_u32(sW3T) + c * 256, 128, 512),
+                 idesc_bf16(128, 32), c > 0 ? 1u : 0u);
+      for (int c = 0; c < kTileW / 16; ++c) {
+        const uint32_t acc = (!first || c > 0) ? 1u : 0u;
+        mma_bf16(tmem + 0, sdesc(smem_u32(sPa2) + c * 256, 128, 2048), sdesc(smem_u32(sPdz3) + c * 256, 128, 2048),
+                 idesc_bf16(128, 32), acc);
+        mma_bf16(tmem + 64, sdesc(smem_u32(sPa3) + c * 256, 128, 2048), sdesc(smem_u32(sPdz4) + c * 256, 128, 2048),
+                 idesc_bf16(128, 16), acc);
+      }
+      mma_commit(bar);
+    }
+    ok = bar_wait(bar, phase);
+    phase ^= 1u;
+    tc_after_sync();
+    first = false;
+    // dz2 = (dz3 W3) [a2 > 0] -> global (bf16) for the second backward kernel
+    {
+      float da[32];
+      tmem_ld32(tmem + lane_base + 32, da);
+      if (in) {
+        uint32_t w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const float a2lo = __uint_as_float(a2w[k] << 16), a2hi = __uint_as_float(a2w[k] & 0xFFFF0000u);
+          w[k] = pack_bf16x2(a2lo > 0.f ? da[2 * k] : 0.f, a2hi > 0.f ? da[2 * k + 1] : 0.f);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(dz2_out + pix * 32);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+      }
+    }
+    tc_before_sync();
+    ok = __syncthreads_and(ok) != 0;   // uniform loop exit
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(status, kStatusTimeout);
+    bar_wait(bar, phase ^ 1u);
+  }
+  // the CTA's accumulated weight gradients: row r of D = input channel (or the
+  // ones row), column = output channel
+  if (!first) {
+    tc_after_sync();
+    float d[32];
+    tmem_ld32(tmem + lane_base + 0, d);
+    const int r = tid;
+    if (r < 32) {
+      for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW3 + o * 32 + r, d[o]);
+    } else if (r == 32) {
+      for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb3 + o, d[o]);
+    }
+    tmem_ld32(tmem + lane_base + 64, d);
+    if (r < 32) atomicAdd(grad + kGw4 + r, d[0]);
+    else if (r == 32) atomicAdd(grad + kGb4, d[0]);
+  }
+  lsum = warp_sum(lsum);
+  if (lane == 0 && lsum != 0.f) atomicAdd(loss, (double)lsum);
+  tc_before_sync();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+}
+
+// bwd2 smem layout
+constexpr int kB2W2t = 0;                          // [32 i][288 (tap, o)] = W2[o][tap * 32 + i]
+constexpr int kB2Px = kB2W2t + 18432;              // planar x: rows 0-15 channels, row 16 ones (6 KB)
+constexpr int kB2R = kB2Px + 6144;                 // im2col(dz2) [128 x 288] / planar im2col(a1) [296 rows]
+constexpr int kB2Halo = kB2R + 37 * 2048;          // halo rows of 64 B (390)
+constexpr int kB2Pdz2 = kB2Halo + 24960;           // planar dz2 [32 o][128 px]
+constexpr int kB2Pdz1 = kB2Pdz2 + 8192;            // planar dz1 [32 o][128 px]
+constexpr int kB2Bar = kB2Pdz1 + 8192;
+constexpr int kB2Smem = kB2Bar + 64;
+
+__global__ void __launch_bounds__(kNetThreads, 1)
+mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ feats, const uint16_t *__restrict__ acts,
+                  const uint16_t *__restrict__ dz2, int batch, int W, int H, float *__restrict__ grad,
+                  uint32_t *__restrict__ status) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint8_t *sW2t = smem + kB2W2t, *sPx = smem + kB2Px, *sR = smem + kB2R, *sHalo = smem + kB2Halo;
+  uint8_t *sPdz2 = smem + kB2Pdz2, *sPdz1 = smem + kB2Pdz1;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kB2Bar);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kB2Bar + 8);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint16_t *gw2 = reinterpret_cast<const uint16_t *>(weights + kOffW2);
+  for (int e = tid; e < 32 * kK2; e += kNetThreads) {
+    const int o = e / kK2, col = e % kK2, tap = col / 32, i = col % 32;
+    *reinterpret_cast<uint16_t *>(sW2t + core_off(i, tap * 32 + o, kK2)) = gw2[e];
+  }
+  // planar x: channels 8-15 zero, row 16 ones, rows 17-23 zero; planar
+  // im2col(a1) rows 288 (ones) to 295 (zero) lie past the im2col(dz2) area
+  for (int e = tid; e < 6144 / 16; e += kNetThreads) reinterpret_cast<uint4 *>(sPx)[e] = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = tid; e < 2048 / 16; e += kNetThreads)
+    reinterpret_cast<uint4 *>(sR + 36 * 2048)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  *reinterpret_cast<uint16_t *>(sPx + planar_off(16, tid)) = 0x3F80;
+  *reinterpret_cast<uint16_t *>(sR + planar_off(288, tid)) = 0x3F80;
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)), "r"(256));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_before_sync();
+  __syncthreads();
+  tc_after_sync();
+  // D: da1 cols 0-31; dW2^T blocks (A rows 0, 128, 168) cols 32-127; dW1^T cols 128-159
+  const uint32_t tmem = *s_tmem;
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  uint32_t phase = 0;
+  bool ok = true, first = true;
+  const int tiles_x = (W + kTileW - 1) / kTileW;
+  const long long ntiles = (long long)batch * H * tiles_x;
+  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const int tx = (int)(t % tiles_x), y = (int)((t / tiles_x) % H), b = (int)(t / ((long long)tiles_x * H));
+    const int x0 = tx * kTileW, p = tid, x = x0 + p;
+    // 1. dz2 halo (zero outside the image)
+    for (int h = tid; h < kHaloRows; h += kNetThreads) {
+      const int r = h / kHaloW, c = h % kHaloW, yy = y - 1 + r, xx = x0 - 1 + c;
+      uint4 *dst = reinterpret_cast<uint4 *>(sHalo + (size_t)h * 64);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(dz2 + (((size_t)b * H + yy) * W + xx) * 32);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) dst[g] = src[g];
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    __syncthreads();
+    // 2. im2col of dz2 for the transposed convolution: row q, column
+    // (tap, o) = dz2 at pixel q - offset(tap) = halo (2 - ky, q + 2 - kx)
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
+      const uint4 *src = reinterpret_cast<const uint4 *>(sHalo + (size_t)((2 - ky) * kHaloW + p + 2 - kx) * 64);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) *reinterpret_cast<uint4 *>(sR + core_off(p, tap * 32 + 8 * g, kK2)) = src[g];
+    }
+    // planar dz2 of the tile's own pixels (halo row 1) and planar x
+    {
+      const uint32_t *own = reinterpret_cast<const uint32_t *>(sHalo + (size_t)(kHaloW + p + 1) * 64);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t w = own[k];
+        *reinterpret_cast<uint16_t *>(sPdz2 + planar_off(2 * k, p)) = (uint16_t)(w & 0xFFFFu);
+        *reinterpret_cast<uint16_t *>(sPdz2 + planar_off(2 * k + 1, p)) = (uint16_t)(w >> 16);
+      }
+      uint4 xv = make_uint4(0u, 0u, 0u, 0u);
+      if (x < W) xv = __ldg(feats + ((size_t)b * H + y) * W + x);
+      const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        *reinterpret_cast<uint16_t *>(sPx + planar_off(2 * k, p)) = (uint16_t)(xw[k] & 0xFFFFu);
+        *reinterpret_cast<uint16_t *>(sPx + planar_off(2 * k + 1, p)) = (uint16_t)(xw[k] >> 16);
+      }
+    }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+      for (int c = 0; c < kK2 / 16; ++c)
+        mma_bf16(tmem + 0, sdesc(smem_u32(sR) + c * 256, 128, (kK2 / 8) * 128),
+                 sdesc(smem_u32(sW2t) + c * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32), c > 0 ? 1u : 0u);
+      mma_commit(bar);
+    }
+    ok = bar_wait(bar, phase);
+    phase ^= 1u;
+    tc_after_sync();
+    // 3. dz1 = da1 [a1 > 0] -> planar dz1
+    {
+      float da[32];
+      tmem_ld32(tmem + lane_base + 0, da);
+      uint32_t a1w[16];
+      if (x < W) {
+        const uint4 *ga = reinterpret_cast<const uint4 *>(acts + (((size_t)b * H + y) * W + x) * 96);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const uint4 u = ga[g];
+          a1w[4 * g] = u.x; a1w[4 * g + 1] = u.y; a1w[4 * g + 2] = u.z; a1w[4 * g + 3] = u.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a1w[k] = 0u;
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float lo = __uint_as_float(a1w[k] << 16), hi = __uint_as_float(a1w[k] & 0xFFFF0000u);
+        *reinterpret_cast<uint16_t *>(sPdz1 + planar_off(2 * k, p)) =
+            __bfloat16_as_ushort(__float2bfloat16_rn(lo > 0.f ? da[2 * k] : 0.f));
+        *reinterpret_cast<uint16_t *>(sPdz1 + planar_off(2 * k + 1, p)) =
+            __bfloat16_as_ushort(__float2bfloat16_rn(hi > 0.f ? da[2 * k + 1] : 0.f));
+      }
+    }
+    tc_before_sync();
+    __syncthreads();
+    // 4. a1 halo (zero outside the image) -> planar im2col(a1): row
+    // tap * 32 + i, column q = a1 at halo (ky, q + kx)
+    for (int h = tid; h < kHaloRows; h += kNetThreads) {
+      const int r = h / kHaloW, c = h % kHaloW, yy = y - 1 + r, xx = x0 - 1 + c;
+      uint4 *dst = reinterpret_cast<uint4 *>(sHalo + (size_t)h * 64);
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(acts + (((size_t)b * H + yy) * W + xx) * 96);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) dst[g] = src[g];
+      } else {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap % 3;
+      const uint32_t *src = reinterpret_cast<const uint32_t *>(sHalo + (size_t)(ky * kHaloW + p + kx) * 64);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t w = src[k];
+        *reinterpret_cast<uint16_t *>(sR + planar_off(tap * 32 + 2 * k, p)) = (uint16_t)(w & 0xFFFFu);
+        *reinterpret_cast<uint16_t *>(sR + planar_off(tap * 32 + 2 * k + 1, p)) = (uint16_t)(w >> 16);
+      }
+    }
+    fence_async_smem();
+    tc_before_sync();
+    __syncthreads();
+    tc_after_sync();
+    if (tid == 0) {
+      const int mrow[3] = {0, 128, 168};
+      for (int c = 0; c < kTileW / 16; ++c) {
+        const uint32_t acc = (!first || c > 0) ? 1u : 0u;
+        for (int mb = 0; mb < 3; ++mb)
+          mma_bf16(tmem + 32 + 32 * mb, sdesc(smem_u32(sR) + (mrow[mb] / 8) * 2048 + c * 256, 128, 2048),
+                   sdesc(smem_u32(sPdz2) + c * 256, 128, 2048), idesc_bf16(128, 32), acc);
+        mma_bf16(tmem + 128, sdesc(smem_u32(sPx) + c * 256, 128, 2048), sdesc(smem_u32(sPdz1) + c * 256, 128, 2048),
+                 idesc_bf16(128, 32), acc);
+      }
+      mma_commit(bar);
+    }
+    ok = ok && bar_wait(bar, phase);
+    phase ^= 1u;
+    tc_after_sync();
+    first = false;
+    tc_before_sync();
+    ok = __syncthreads_and(ok) != 0;   // uniform loop exit
+  }
+  if (!ok) {
+    if (tid == 0) atomicOr(status, kStatusTimeout);
+    bar_wait(bar, phase ^ 1u);
+  }
+  if (!first) {
+    tc_after_sync();
+    float d[32];
+    const int r = tid;
+    for (int mb = 0; mb < 3; ++mb) {
+      tmem_ld32(tmem + lane_base + 32 + 32 * mb, d);
+      const int row = (mb == 0 ? 0 : (mb == 1 ? 128 : 168)) + r;
+      const bool take = mb < 2 || row >= 256;        // block 2 repeats rows 168-255 of block 1
+      if (take && row < 288) {
+        for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW2 + o * 288 + row, d[o]);
+      } else if (take && row == 288) {
+        for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb2 + o, d[o]);
+      }
+    }
+    tmem_ld32(tmem + lane_base + 128, d);
+    if (r < 16) {
+      for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW1 + o * 16 + r, d[o]);
+    } else if (r == 16) {
+      for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb1 + o, d[o]);
+    }
+  }
+  tc_before_sync();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
+// Adam on the FP32 master parameters (gradient layout), refreshing the BF16
+// weights and FP32 biases of the blob.
+__global__ void mpnet_adam_kernel(uint8_t *__restrict__ weights, float *__restrict__ master, float *__restrict__ m,
+                                  float *__restrict__ v, const float *__restrict__ grad, float lr, float beta1,
+                                  float beta2, float eps, float bc1, float bc2) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= kGTotal) return;
+  const float g = grad[k];
+  const float mk = beta1 * m[k] + (1.f - beta1) * g;
+  const float vk = beta2 * v[k] + (1.f - beta2) * g * g;
+  m[k] = mk;
+  v[k] = vk;
+  float w = master[k] - lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+  if (k < kGW2 && (k % 16) >= 8) w = 0.f;   // padded input channels of W1 stay zero
+  master[k] = w;
+  __nv_bfloat16 *wb = reinterpret_cast<__nv_bfloat16 *>(weights);
+  if (k < kGw4 + 32) {
+    // W1, W2, W3, w4 are contiguous in both layouts (1024 + 18432 + 2048 + 64 bytes)
+    wb[k] = __float2bfloat16_rn(w);
+  } else {
+    reinterpret_cast<float *>(weights + kOffB1)[k - kGb1] = w;   // b1 b2 b3 b4 contiguous too
+  }
+}
 }  // namespace
 
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
@@ -351,6 +790,39 @@ cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int
   mpnet_fwd_kernel<<<grid, kNetThreads, kSmemBytes, s>>>(static_cast<const uint8_t *>(weights),
                                                          reinterpret_cast<const uint4 *>(feats), batch, W, H, out,
                                                          acts, status);
+  return cudaGetLastError();
+}
+
+}  // namespace dags
+
+namespace dags {
+
+cudaError_t launch_mpnet_train(void *weights, float *master, float *adam_m, float *adam_v, int step,
+                               const uint16_t *feats, const float *target, int batch, int W, int H, float lr,
+                               double *loss, const MpnetScratch &sc, uint32_t *status, int num_sms, cudaStream_t s) {
+  const long long npix = (long long)batch * H * W;
+  cudaError_t e = cudaMemsetAsync(sc.grad, 0, kGTotal * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sc.inv_n, 0, 2 * sizeof(float), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  mpnet_count_kernel<<<num_sms, 256, 0, s>>>(target, npix, sc.inv_n, nullptr);
+  mpnet_count_finish_kernel<<<1, 1, 0, s>>>(sc.inv_n);
+  e = launch_mpnet_forward(weights, feats, batch, W, H, sc.y, sc.acts, status, num_sms, s);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)batch * H * ((W + kTileW - 1) / kTileW);
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  e = cudaFuncSetAttribute(mpnet_bwd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kB1Smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(mpnet_bwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kB2Smem);
+  if (e != cudaSuccess) return e;
+  mpnet_bwd1_kernel<<<grid, kNetThreads, kB1Smem, s>>>(static_cast<const uint8_t *>(weights), sc.y, target, sc.acts,
+                                                       batch, W, H, sc.inv_n, sc.dz2, sc.grad, loss, status);
+  mpnet_bwd2_kernel<<<grid, kNetThreads, kB2Smem, s>>>(static_cast<const uint8_t *>(weights),
+                                                       reinterpret_cast<const uint4 *>(feats), sc.acts, sc.dz2, batch,
+                                                       W, H, sc.grad, status);
+  const float beta1 = 0.9f, beta2 = 0.999f;
+  const float bc1 = 1.f - powf(beta1, (float)step), bc2 = 1.f - powf(beta2, (float)step);
+  mpnet_adam_kernel<<<(kGTotal + 255) / 256, 256, 0, s>>>(static_cast<uint8_t *>(weights), master, adam_m, adam_v,
+                                                          sc.grad, lr, beta1, beta2, 1e-8f, bc1, bc2);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,7 @@ class CMpCfg(ctypes.Structure):
 MP_STATS_HEAD = 6
 MPNET_WEIGHT_BYTES = 22016
 MPNET_ACT_WORDS = 96
+MPNET_PARAMS = 10881
 
 
 class CPoseCfg(ctypes.Structure):
@@ -68,10 +69,10 @@ class CPoseCfg(ctypes.Structure):
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
-           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_infer"]
+           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_infer", "mpnet_train_step"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
-           "mp_pixel", "mp_gauss", "mpnet"]
+           "mp_pixel", "mp_gauss", "mpnet", "mpnet_train"]
 
 _lib = None
 
@@ -125,6 +126,8 @@ def load(path: str = LIB_PATH):
     lib.mp_update.restype = ctypes.c_int
     lib.mpnet_infer.argtypes = [P, P, P, I32, I32, I32, P, P, P]
     lib.mpnet_infer.restype = ctypes.c_int
+    lib.mpnet_train_step.argtypes = [P, P, P, P, P, I32, P, P, I32, I32, I32, ctypes.c_float, P, P, P]
+    lib.mpnet_train_step.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -343,6 +346,30 @@ class Context:
         _check(self.lib.mpnet_infer(self.h, _ptr(weights), _ptr(feats), B, W, H, _ptr(out), _ptr(acts), _stream()),
                "mpnet_infer")
         return out
+
+    def mpnet_train_step(self, weights, master, adam_m, adam_v, step, feats, target, lr, loss=None, grad=None):
+        """One training step (BCE + Adam) of the MP network; updates weights,
+        master, adam_m and adam_v in place. master/adam_m/adam_v/grad: float32
+        CUDA tensors of MPNET_PARAMS; target: [B, H, W] float32 (negative =
+        excluded). Returns the loss (float64 CUDA tensor of 1) at the weights
+        before the step."""
+        B, H, W, C = feats.shape
+        if C != 8 or feats.dtype != torch.bfloat16 or not feats.is_contiguous():
+            raise ValueError("feats must be a contiguous [B, H, W, 8] bfloat16 tensor")
+        if tuple(target.shape) != (B, H, W):
+            raise ValueError("target must be [B, H, W]")
+        _need(target, torch.float32, "target")
+        for name, t in (("master", master), ("adam_m", adam_m), ("adam_v", adam_v)) + \
+                ((("grad", grad),) if grad is not None else ()):
+            _need(t, torch.float32, name)
+            if t.numel() != MPNET_PARAMS:
+                raise ValueError(f"{name} must hold {MPNET_PARAMS} floats")
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float64, device=feats.device)
+        _check(self.lib.mpnet_train_step(self.h, _ptr(weights), _ptr(master), _ptr(adam_m), _ptr(adam_v), int(step),
+                                         _ptr(feats), _ptr(target), B, W, H, float(lr), _ptr(loss), _ptr(grad),
+                                         _stream()), "mpnet_train_step")
+        return loss
 
     def pose_step(self, poses, grad_pose, adam_state, cfg=None):
         _need(poses, torch.float64, "poses")
