@@ -36,9 +36,13 @@ Follows Sec. IV-A and Eq. (17) step by step, one view:
     labels      dynamic iff M^t > tau; unobserved Gaussians keep M and label
     U_bar       Eq. (13): lower median of U_tilde over observed Gaussians
 
+An external per-pixel MP map (the learned proposal between semantic
+invocations, not in the paper) may replace M_p in the association.
+
 Pins: the K = 0 / K = 1 special cases, fixed and instant rates, the rho
-scaling, M in [0, 1], tau >= 0.5, unobserved unchanged, and closed-form cases
-in tests/test_oracle_mp.py.
+scaling, M in [0, 1], tau >= 0.5, unobserved unchanged, the external map
+reducing to the fused M_p and to a constant, and closed-form cases in
+tests/test_oracle_mp.py.
 """
 from __future__ import annotations
 
@@ -115,8 +119,13 @@ def pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg: MPConfig):
 
 
 def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend, c_rend, table,
-              cfg: MPConfig = None, seg_refreshed: bool = True):
+              cfg: MPConfig = None, seg_refreshed: bool = True, mp_map=None):
     """One MP update. cam = (fx, fy, cx, cy, W, H); pose 3x4 world->camera.
+
+    mp_map: optional per-pixel MP (e.g. the learned network's proposal
+    between semantic invocations); when given it stands in for the fused M_p
+    of Eqs. (2)-(7) in the association of Eqs. (8) and (10). The residuals
+    (sigma_e,G, C) and the region statistics still come from the frame.
 
     Returns dict with mp (n), labels (n, uint8), observed (n bool), m_hat,
     U, U_tilde, alpha (after Eq. (17)), tau, U_bar, median_M, the pixel dict,
@@ -129,6 +138,8 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
     W, H = int(W), int(H)
     px = pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg)
     M_p, e = px["M_p"], px["e"]
+    if mp_map is not None:
+        M_p = np.asarray(mp_map, np.float64).ravel()
     d_rend = np.asarray(d_rend, np.float64).ravel()
     means = np.asarray(means, np.float64).reshape(-1, 3)
     n = means.shape[0]

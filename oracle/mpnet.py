@@ -20,8 +20,9 @@ nearest, ties to even) where the kernel rounds them. Training loss: mean
 binary cross-entropy against a target MP map over valid pixels (target >= 0);
 the backward treats the BF16 rounding of activations as the identity.
 
-Input channels (per pixel): rendered MP, |dR|, |dG|, |dB|, |dDepth|, depth,
-rendered opacity, prior mask. Tensors are NHWC.
+Input channels (per pixel, `features`): rendered MP, |dR|, |dG|, |dB|,
+|dDepth|, observed depth, rendered opacity, prior mask (the MP_ins of the
+pixel's instance region, Eq. (2)). Tensors are NHWC.
 
 Training step: Adam (Kingma and Ba, 2015) with beta1 0.9, beta2 0.999,
 eps 1e-8 on FP32 master weights; the network's optimiser is not in the paper
@@ -47,6 +48,27 @@ def bf16_round(x):
     u = f.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint32) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def features(r_mp, c_rend, d_rend, o_rend, c_obs, d_obs, inst, table):
+    """Per-pixel input of the network (P x 8, BF16 values): rendered MP,
+    |C_obs - C_rend| per channel, |D_obs - D_rend| where the observed depth is
+    valid (> 0, else 0), observed depth (0 where invalid), rendered opacity,
+    and the prior MP of the pixel's instance region (table[inst, 0], the
+    MP_ins of Eq. (2)). Differences are taken in FP32 (the kernel's inputs)
+    and rounded to BF16 once."""
+    f32 = lambda v: np.asarray(v, np.float32)
+    c_rend, c_obs = f32(c_rend).reshape(-1, 3), f32(c_obs).reshape(-1, 3)
+    d_rend, d_obs = f32(d_rend).ravel(), f32(d_obs).ravel()
+    valid = d_obs > 0
+    out = np.zeros((d_obs.size, 8), np.float64)
+    out[:, 0] = f32(r_mp).ravel()
+    out[:, 1:4] = np.abs(c_obs - c_rend)
+    out[:, 4] = np.where(valid, np.abs(d_obs - d_rend), np.float32(0))
+    out[:, 5] = np.where(valid, d_obs, np.float32(0))
+    out[:, 6] = f32(o_rend).ravel()
+    out[:, 7] = np.asarray(table, np.float64).reshape(-1, 2)[np.asarray(inst).astype(np.int64).ravel(), 0]
+    return bf16_round(out)
 
 
 def init_params(seed=0):

@@ -170,3 +170,42 @@ def test_unobserved_unchanged_and_bounds():
         assert np.all((r["alpha"][obs] >= (0.5 if not refreshed else 1) * 0.05 - 1e-15))
         assert np.all(r["alpha"][obs] <= 0.6 + 1e-15)
         np.testing.assert_array_equal(r["labels"][obs], (r["mp"][obs] > r["tau"]).astype(np.uint8))
+
+
+def test_external_map_reduces_to_fused_mp():
+    # passing the frame's own fused M_p as the external map changes nothing
+    rng = np.random.default_rng(12)
+    n = 60
+    means = points_on_grid(n, seed=3)
+    inst = (rng.random(W * H) < 0.3).astype(np.uint8)
+    d_rend = rng.uniform(1.9, 2.1, W * H)
+    d_obs = d_rend + rng.normal(0, 0.05, W * H)
+    c_obs, c_rend = rng.uniform(0, 1, (W * H, 3)), rng.uniform(0, 1, (W * H, 3))
+    prev = rng.uniform(0.05, 0.95, n)
+    args = (means, prev, np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c_obs, d_rend, c_rend, TABLE)
+    a = M.mp_update(*args)
+    b = M.mp_update(*args, mp_map=M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig())["M_p"])
+    for k in ("mp", "m_hat", "var", "U", "alpha"):
+        np.testing.assert_array_equal(a[k], b[k])
+    np.testing.assert_array_equal(a["labels"], b["labels"])
+
+
+def test_external_map_closed_forms():
+    # a constant map gives M_hat = c and Var = 0; a one-pixel map at the
+    # projected centre gives the kernel-weight closed form of Eq. (8)
+    n = 1
+    z = 2.0
+    means = np.array([[(15 - 12.0) * z / 30.0, (9 - 10.0) * z / 30.0, z]])
+    inst, d_obs, c, d_rend, c2 = flat_obs()
+    cfg = M.MPConfig(alpha_min=1.0, alpha_max=1.0)
+    args = (means, np.array([0.5]), np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c, d_rend, c2,
+            TABLE, cfg)
+    r = M.mp_update(*args, mp_map=np.full(W * H, 0.8))
+    np.testing.assert_allclose(r["m_hat"], 0.8, rtol=1e-14)
+    np.testing.assert_allclose(r["var"], 0.0, atol=1e-15)
+    np.testing.assert_allclose(r["mp"], 0.8, rtol=1e-14)
+    one = np.zeros(W * H)
+    one[9 * W + 15] = 1.0
+    r = M.mp_update(*args, mp_map=one)
+    d2 = np.array([0, 1, 1, 1, 1, 2, 2, 2, 2, 4, 4, 4, 4], float)
+    np.testing.assert_allclose(r["m_hat"], 1.0 / np.exp(-d2 / 2).sum(), rtol=1e-12)

@@ -98,3 +98,16 @@ def test_adam_matches_torch_optim():
         opt.step()
         p, m, v = N.adam_step(p, {"w": g}, m, v, k, 3e-3)
     np.testing.assert_allclose(p["w"], t.detach().numpy(), rtol=0, atol=1e-14)
+
+
+def test_features_closed_form():
+    # three pixels: valid depth, invalid depth (0), and an instance pixel
+    table = np.array([[0.1, 0.05], [0.9, 0.8]])
+    f = N.features(r_mp=[0.25, 0.0, 0.5], c_rend=[[0.5, 0.5, 0.5], [0.2, 0.3, 0.4], [1, 1, 1]],
+                   d_rend=[2.0, 3.0, 1.5], o_rend=[1.0, 0.5, 0.75],
+                   c_obs=[[0.75, 0.25, 0.5], [0.2, 0.3, 0.4], [0, 1, 0.5]], d_obs=[2.5, 0.0, 1.0],
+                   inst=[0, 0, 1], table=table)
+    want = np.array([[0.25, 0.25, 0.25, 0.0, 0.5, 2.5, 1.0, 0.1],
+                     [0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.5, 0.1],
+                     [0.5, 1.0, 0.0, 0.5, 0.5, 1.0, 0.75, 0.9]])
+    np.testing.assert_array_equal(f, N.bf16_round(want))
