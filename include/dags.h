@@ -282,11 +282,17 @@ void dags_default_mp_cfg(dags_mp_cfg *cfg);
  * stats     device out, DAGS_MP_STATS_HEAD + 4 * n_regions doubles: tau,
  *           U_bar, median M^t, U_min, U_max, number observed; then per region
  *           count, mean e, std e, e_ub.
+ * mp_map    device, H*W floats, or NULL: an external per-pixel MP (the
+ *           learned proposal between semantic invocations, not in the paper)
+ *           used in place of the fused M_p in Eqs. (8) and (10); the
+ *           residual terms and region statistics are the frame's own.
+ * mp_pixel  device out, H*W floats, or NULL: the fused M_p of Eq. (7) per
+ *           pixel (the method's own map, e.g. a training target).
  * Needs a ctx created with max_views >= 1 and images at least H x W. */
 int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, const double *pose,
               const float *targets, const float *image, const uint8_t *inst, const float *table,
               int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
-              double *stats, void *stream);
+              double *stats, const float *mp_map, float *mp_pixel, void *stream);
 
 /* Learned per-pixel MP proposal network (not in the paper: the task's
  * learned stand-in for the stale instance prior between scheduled semantic
@@ -305,6 +311,15 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
  * 21824, b4 f32 at 21952. */
 #define DAGS_MPNET_WEIGHT_BYTES 22016
 #define DAGS_MPNET_ACT_WORDS 96
+
+/* Network input of one view (height x width pixels): per pixel 8 BF16
+ * (rendered MP R_MP, |C_obs - C_rend| r g b, |D_obs - D_rend| where D_obs >
+ * 0 else 0, D_obs where > 0 else 0, rendered opacity O, table[inst].mu, the
+ * MP_ins of the pixel's region, Eq. (2)). image, targets, inst, table as for
+ * mp_update; feats device out, 16-byte aligned, H*W*8 bf16. */
+int mpnet_features(dags_ctx *ctx, const float *image, const float *targets, const uint8_t *inst,
+                   const float *table, int32_t n_regions, int32_t width, int32_t height, uint16_t *feats,
+                   void *stream);
 
 /* Inference: feats device, batch x height x width x 8 bf16 (16-byte
  * aligned); mp_out device, batch x height x width float; acts device or NULL:

@@ -561,7 +561,7 @@ void dags_default_mp_cfg(dags_mp_cfg *c) {
 int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, const double *pose,
               const float *targets, const float *image, const uint8_t *inst, const float *table,
               int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
-              double *stats, void *stream) {
+              double *stats, const float *mp_map, float *mp_pixel, void *stream) {
   int rc = common_args(ctx, gauss, n, cam, pose, 1);
   if (rc) return rc;
   if (!targets || !image || !inst || !table || !labels || !stats) return DAGS_E_INVAL;
@@ -580,7 +580,26 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
   ctx->last_stream = s;
   const int ev = ctx->timer.begin(DAGS_K_MP_GAUSS, s);
   const cudaError_t e = launch_mp_update(ctx->mp, gauss, n, pose, r, reinterpret_cast<const float4 *>(targets),
-                                         image, inst, table, n_regions, c, seg_refreshed ? 1 : 0, labels, stats, s);
+                                         image, inst, table, n_regions, c, seg_refreshed ? 1 : 0, labels, stats,
+                                         mp_map, mp_pixel, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+int mpnet_features(dags_ctx *ctx, const float *image, const float *targets, const uint8_t *inst,
+                   const float *table, int32_t n_regions, int32_t width, int32_t height, uint16_t *feats,
+                   void *stream) {
+  if (!ctx || !image || !targets || !inst || !table || !feats || width < 1 || height < 1) return DAGS_E_INVAL;
+  if (n_regions < 1 || n_regions > DAGS_MP_MAX_REGIONS) return DAGS_E_INVAL;
+  if (((uintptr_t)targets & 15u) != 0 || ((uintptr_t)feats & 15u) != 0 || ((uintptr_t)table & 7u) != 0)
+    return DAGS_E_INVAL;
+  const long long P = (long long)width * height;
+  if (P > INT32_MAX) return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_MPNET, s);
+  const cudaError_t e = launch_mpnet_features(image, reinterpret_cast<const float4 *>(targets), inst, table,
+                                              n_regions, (int)P, feats, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

@@ -137,7 +137,9 @@ struct MpBuffers {
 cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
-                             double *stats, cudaStream_t s);
+                             double *stats, const float *mp_map, float *mp_pixel, cudaStream_t s);
+cudaError_t launch_mpnet_features(const float *image, const float4 *targets, const uint8_t *inst, const float *table,
+                                  int n_regions, int P, uint16_t *feats, cudaStream_t s);
 
 // ---- device helpers ----
 

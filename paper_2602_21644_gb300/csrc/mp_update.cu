@@ -21,6 +21,7 @@
 //   mp_labels_kernel      labels, Eq. (12)
 // The last CTA of each histogram kernel finds the bin holding the median's
 // rank (one warp scans the bins).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -48,6 +49,8 @@ struct MpWs {
   uint32_t *sel;         // select state: [0] n_obs, [1] Umin bits, [2] Umax bits, [3] done counter,
                          // [4..5] prefix (M, U), [6..7] remaining rank (M, U)
   double *stats;         // caller's output
+  const float *mp_map;   // [P] external per-pixel MP replacing M_p, or null
+  float *mp_pixel;       // [P] out: the fused M_p, or null
 };
 
 // Order-preserving map of floats to uint32 (for atomic min/max of values
@@ -137,6 +140,24 @@ __device__ __forceinline__ float pixel_mp(float e, const float4 reg, const float
   return (1.f - K) * tab.x + K * mp_geo;
 }
 
+// The fused per-pixel M_p map, Eqs. (2)-(7) (an output for callers that
+// train or judge a learned proposal against the method).
+__global__ void __launch_bounds__(kMpBlock)
+mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int P, MpCfg c) {
+  __shared__ float4 s_reg[DAGS_MP_MAX_REGIONS];
+  __shared__ float2 s_tab[DAGS_MP_MAX_REGIONS];
+  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
+    region_params(m, c, k, &s_reg[k]);
+    s_tab[k] = table[k];
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) {
+    const int k = inst[p];
+    m.mp_pixel[p] = pixel_mp(m.e[p], s_reg[k], s_tab[k], c.fusion_mode);
+  }
+}
+
 __global__ void __launch_bounds__(kMpBlock)
 mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
                 const float *__restrict__ image, const uint8_t *__restrict__ inst, const float2 *__restrict__ table,
@@ -177,7 +198,7 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
             const size_t p = (size_t)jj * r.W + ii;
             const float e = m.e[p];
             const int k = inst[p];
-            const float mp = pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
+            const float mp = m.mp_map ? __ldg(m.mp_map + p) : pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
             const float w = expf(-d2 * inv2s2);
             sw += w; swm += w * mp; sm += mp; se += e; ++cnt;
             dmax = fmaxf(dmax, image[3 * P + p]);
@@ -195,7 +216,7 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
             const size_t p = (size_t)jj * r.W + ii;
             const float e = m.e[p];
             const int k = inst[p];
-            const float mp = pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
+            const float mp = m.mp_map ? __ldg(m.mp_map + p) : pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
             vm += (mp - mm) * (mp - mm);
             ve += (e - me) * (e - me);
           }
@@ -388,8 +409,10 @@ __global__ void mp_region_stats_kernel(MpWs m, MpCfg c) {
 cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
-                             double *stats, cudaStream_t s) {
+                             double *stats, const float *mp_map, float *mp_pixel, cudaStream_t s) {
   MpWs m;
+  m.mp_map = mp_map;
+  m.mp_pixel = mp_pixel;
   m.e = b.e; m.acc = b.acc; m.mhat = b.mhat; m.sige = b.sige; m.U = b.U; m.Mt = b.Mt; m.Ut = b.Ut;
   m.obs = b.obs; m.hist = b.hist; m.sel = b.sel; m.stats = stats;
   MpCfg c;
@@ -407,6 +430,8 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   const unsigned gg = (unsigned)((n + kMpBlock - 1) / kMpBlock > 0 ? (n + kMpBlock - 1) / kMpBlock : 1);
   mp_pixel_sum_kernel<<<gp, kMpBlock, 0, s>>>(m, targets, image, inst, P, c);
   mp_pixel_var_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, P, c);
+  if (mp_pixel)
+    mp_pixel_map_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, reinterpret_cast<const float2 *>(table), P, c);
   mp_gauss_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<const float4 *>(gauss), n, pose, image, inst,
                                           reinterpret_cast<const float2 *>(table), r, c);
   mp_apply_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<float4 *>(gauss), n, c);
@@ -414,6 +439,50 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 2, c);
   mp_labels_kernel<<<gg, kMpBlock, 0, s>>>(m, n, labels);
   mp_region_stats_kernel<<<1, 256, 0, s>>>(m, c);
+  return cudaGetLastError();
+}
+
+}  // namespace dags
+
+namespace dags {
+
+namespace {
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return a | (b << 16);
+}
+
+// Per-pixel input of the learned MP network: rendered MP, |dC| (3), |dD|
+// where the observed depth is valid, observed depth, rendered opacity, the
+// MP_ins of the pixel's region (Eq. (2)); one 16-byte BF16 row per pixel.
+__global__ void __launch_bounds__(kMpBlock)
+mpnet_features_kernel(const float *__restrict__ image, const float4 *__restrict__ targets,
+                      const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int n_regions, int P,
+                      uint4 *__restrict__ feats) {
+  __shared__ float s_mu[DAGS_MP_MAX_REGIONS];
+  for (int k = threadIdx.x; k < n_regions; k += blockDim.x) s_mu[k] = table[k].x;
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const size_t Q = (size_t)P;
+  const float4 t = __ldg(targets + p);
+  const float cr = __ldg(image + p), cg = __ldg(image + Q + p), cb = __ldg(image + 2 * Q + p);
+  const float d = __ldg(image + 3 * Q + p), o = __ldg(image + 4 * Q + p), rmp = __ldg(image + 5 * Q + p);
+  const bool valid = t.w > 0.f;
+  const int k = inst[p];
+  feats[p] = make_uint4(bf16x2_bits(rmp, fabsf(t.x - cr)), bf16x2_bits(fabsf(t.y - cg), fabsf(t.z - cb)),
+                        bf16x2_bits(valid ? fabsf(t.w - d) : 0.f, valid ? t.w : 0.f), bf16x2_bits(o, s_mu[k]));
+}
+
+}  // namespace
+
+cudaError_t launch_mpnet_features(const float *image, const float4 *targets, const uint8_t *inst, const float *table,
+                                  int n_regions, int P, uint16_t *feats, cudaStream_t s) {
+  if (P <= 0) return cudaSuccess;
+  mpnet_features_kernel<<<(P + kMpBlock - 1) / kMpBlock, kMpBlock, 0, s>>>(
+      image, targets, inst, reinterpret_cast<const float2 *>(table), n_regions, P, reinterpret_cast<uint4 *>(feats));
   return cudaGetLastError();
 }
 

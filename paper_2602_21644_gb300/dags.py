@@ -69,7 +69,8 @@ class CPoseCfg(ctypes.Structure):
 EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "dags_sync_status",
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
-           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_infer", "mpnet_train_step"]
+           "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
+           "mpnet_train_step"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train"]
@@ -122,7 +123,9 @@ def load(path: str = LIB_PATH):
     lib.splat_forward_static.restype = ctypes.c_int
     lib.dags_default_mp_cfg.argtypes = [ctypes.POINTER(CMpCfg)]
     lib.mp_update.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, P, P, P, I32, ctypes.POINTER(CMpCfg), I32, P,
-                              P, P]
+                              P, P, P, P]
+    lib.mpnet_features.argtypes = [P, P, P, P, P, I32, I32, I32, P, P]
+    lib.mpnet_features.restype = ctypes.c_int
     lib.mp_update.restype = ctypes.c_int
     lib.mpnet_infer.argtypes = [P, P, P, I32, I32, I32, P, P, P]
     lib.mpnet_infer.restype = ctypes.c_int
@@ -318,9 +321,16 @@ class Context:
                                     int(bool(use_graph)), _stream()), "splat_track")
 
     def mp_update(self, gauss, cam: Camera, pose, targets, image, inst, table, labels, cfg=None, seg_refreshed=True,
-                  stats=None):
+                  stats=None, mp_map=None, mp_pixel=None):
         """Spatiotemporal MP update of one view; gauss's MP words and labels are
-        updated in place. Returns the stats tensor (float64)."""
+        updated in place. mp_map (float32 [H*W], optional) replaces the fused
+        per-pixel M_p in the association; mp_pixel (float32 [H*W], optional)
+        receives the fused M_p. Returns the stats tensor (float64)."""
+        for name, t in (("mp_map", mp_map), ("mp_pixel", mp_pixel)):
+            if t is not None:
+                _need(t, torch.float32, name)
+                if t.numel() != cam.width * cam.height:
+                    raise ValueError(f"{name} must hold H*W floats")
         _need(gauss, torch.float32, "gauss")
         _need(inst, torch.uint8, "inst")
         _need(labels, torch.uint8, "labels")
@@ -332,8 +342,20 @@ class Context:
         mc = cfg if cfg is not None else default_mp_cfg()
         _check(self.lib.mp_update(self.h, _ptr(gauss), gauss.shape[0], ctypes.byref(c), _ptr(pose), _ptr(targets),
                                   _ptr(image), _ptr(inst), _ptr(table), nreg, ctypes.byref(mc), int(bool(seg_refreshed)),
-                                  _ptr(labels), _ptr(stats), _stream()), "mp_update")
+                                  _ptr(labels), _ptr(stats), _ptr(mp_map), _ptr(mp_pixel), _stream()), "mp_update")
         return stats
+
+    def mpnet_features(self, image, targets, inst, table, cam: Camera, out=None):
+        """8-channel bfloat16 network input [H, W, 8] of one view."""
+        _need(image, torch.float32, "image")
+        _need(targets, torch.float32, "targets")
+        _need(inst, torch.uint8, "inst")
+        _need(table, torch.float32, "table")
+        if out is None:
+            out = torch.empty((cam.height, cam.width, 8), dtype=torch.bfloat16, device=image.device)
+        _check(self.lib.mpnet_features(self.h, _ptr(image), _ptr(targets), _ptr(inst), _ptr(table), table.shape[0],
+                                       cam.width, cam.height, _ptr(out), _stream()), "mpnet_features")
+        return out
 
     def mpnet_infer(self, weights, feats, out=None, acts=None):
         """feats: [B, H, W, 8] bfloat16 CUDA tensor; weights: uint8 blob of

@@ -43,7 +43,7 @@ def mp_scene(n, frame, width, height, seed=0):
                 labels0=labels0)
 
 
-def run_both(dags, d, cfg_kw=None, seg_refreshed=True):
+def run_both(dags, d, cfg_kw=None, seg_refreshed=True, mp_map=None):
     cfg_kw = cfg_kw or {}
     cam = dags.Camera(*d["cam"].as_tuple())
     P = cam.width * cam.height
@@ -59,15 +59,17 @@ def run_both(dags, d, cfg_kw=None, seg_refreshed=True):
     labels = torch.from_numpy(d["labels0"].copy()).to(dev)
     pose = torch.from_numpy(np.ascontiguousarray(d["pose"])).to(dev)
     ctx = dags.Context(gauss.shape[0], cam.width, cam.height, 1)
+    mp_pixel = torch.full((P,), -1.0, dtype=torch.float32, device=dev)
+    gmap = None if mp_map is None else torch.from_numpy(np.asarray(mp_map, np.float32)).to(dev)
     stats = ctx.mp_update(gauss, cam, pose, tg, image, inst, table, labels, dags.default_mp_cfg(**cfg_kw),
-                          seg_refreshed)
+                          seg_refreshed, mp_map=gmap, mp_pixel=mp_pixel)
     torch.cuda.synchronize()
     gpu = dict(mp=gauss[:, 11].cpu().numpy().astype(np.float64), labels=labels.cpu().numpy(),
-               stats=stats.cpu().numpy())
+               stats=stats.cpu().numpy(), mp_pixel=mp_pixel.cpu().numpy().astype(np.float64))
     cfg = dataclasses.replace(omp.MPConfig(), **cfg_kw)
     ref = omp.mp_update(d["rec"][:, 0:3], d["rec"][:, 11], d["labels0"], d["cam"].as_tuple(), d["pose"], d["inst"],
                         d["obs"][:, 3], d["obs"][:, 0:3], d["rend"][:, 3], d["rend"][:, 0:3], d["table"], cfg,
-                        seg_refreshed)
+                        seg_refreshed, mp_map=None if mp_map is None else np.asarray(mp_map, np.float32))
     return gpu, ref
 
 
@@ -89,6 +91,8 @@ def check(gpu, ref, nreg):
         np.testing.assert_allclose(r[1:4], [px["mean"][k], px["std"][k], px["e_ub"][k]], rtol=1e-5, atol=1e-7)
     assert np.all((gpu["mp"] >= 0) & (gpu["mp"] <= 1))
     assert st[0] >= 0.5
+    # the fused per-pixel M_p map (FP32 vs FP64)
+    np.testing.assert_allclose(gpu["mp_pixel"], ref["pixel"]["M_p"], rtol=0, atol=M_ABS)
 
 
 @pytest.mark.parametrize("frame", [40, 59])
@@ -128,3 +132,39 @@ def test_mp_update_nothing_observed(dags):
     np.testing.assert_array_equal(gpu["mp"], d["rec"][:, 11].astype(np.float64))
     np.testing.assert_array_equal(gpu["labels"], d["labels0"])
     assert gpu["stats"][0] == 0.5 and gpu["stats"][5] == 0
+
+
+def test_mp_update_external_map(dags):
+    # a smooth external per-pixel MP map (the learned proposal's role) in
+    # place of the fused M_p
+    d = mp_scene(60_000, 33, 320, 240, seed=4)
+    cam = d["cam"]
+    jj, ii = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    mp_map = (0.5 + 0.45 * np.sin(ii / 17.0) * np.cos(jj / 23.0)).astype(np.float32).ravel()
+    gpu, ref = run_both(dags, d, mp_map=mp_map)
+    check(gpu, ref, d["table"].shape[0])
+    plain, _ = run_both(dags, d)
+    assert np.abs(gpu["mp"] - plain["mp"]).max() > 0.01       # the map is used
+
+
+def test_mpnet_features_match_oracle(dags):
+    from oracle import mpnet as N
+    rng = np.random.default_rng(5)
+    W, H = 333, 77
+    P = W * H
+    image = rng.uniform(0, 1, (8, P)).astype(np.float32)
+    image[3] = rng.uniform(0.5, 5, P)
+    tg = rng.uniform(0, 1, (P, 4)).astype(np.float32)
+    tg[:, 3] = rng.uniform(0.5, 5, P)
+    tg[rng.random(P) < 0.2, 3] = 0.0
+    nreg = 7
+    inst = rng.integers(0, nreg, P).astype(np.uint8)
+    table = rng.uniform(0, 1, (nreg, 2)).astype(np.float32)
+    ctx = dags.Context(16, W, H, 1)
+    cam = dags.Camera(300.0, 300.0, W / 2, H / 2, W, H)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    f = ctx.mpnet_features(t(image), t(tg), t(inst), t(table), cam)
+    torch.cuda.synchronize()
+    ctx.check()
+    ref = N.features(image[5], image[0:3].T, image[3], image[4], tg[:, 0:3], tg[:, 3], inst, table)
+    np.testing.assert_array_equal(f.float().cpu().numpy().reshape(P, 8), ref)
