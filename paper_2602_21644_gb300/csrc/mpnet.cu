@@ -20,6 +20,8 @@
 // Shared-memory operands use the canonical no-swizzle K-major layout: 8x16-
 // byte core matrices, row groups of 8 rows, LBO = 128 B between core
 // matrices along K, SBO = (K / 8) * 128 B between row groups.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -35,24 +37,11 @@ constexpr int kHaloRows = 3 * kHaloW;     // 390
 constexpr int kHaloPad = 512;             // rows of the first operand (4 M-blocks)
 constexpr int kCh = 32;
 constexpr int kK2 = 9 * kCh;              // 288
-constexpr uint32_t kTmemCols = 256;       // D1: 0..127, D2: 128..159, D3: 160..191
 constexpr long long kSpinLimit = 1ll << 22;
 
 // Byte offsets inside the weight blob (declared in dags.h).
 constexpr int kOffW1 = 0, kOffW2 = 1024, kOffW3 = 19456, kOffW4 = 21504, kOffB1 = 21568, kOffB2 = 21696,
               kOffB3 = 21824, kOffB4 = 21952;
-
-// Dynamic shared-memory layout (bytes, 128-aligned).
-constexpr int kSW1 = 0;                                   // 32 x 16 bf16
-constexpr int kSW2 = kSW1 + 1024;                         // 32 x 288
-constexpr int kSW3 = kSW2 + 32 * kK2 * 2;                 // 32 x 32
-constexpr int kSA1 = kSW3 + 2048;                         // 512 x 16
-constexpr int kSH1 = kSA1 + kHaloPad * 16 * 2;            // 390 x 32 (plain rows of 64 B)
-constexpr int kSA2 = kSH1 + ((kHaloRows * 64 + 127) / 128) * 128;  // 128 x 288
-constexpr int kSA3 = kSA2 + kTileW * kK2 * 2;             // 128 x 32
-constexpr int kSPar = kSA3 + kTileW * kCh * 2;            // b1 b2 b3 w4 (fp32) b4
-constexpr int kSBar = kSPar + (4 * kCh + 4) * 4;          // mbarrier + tmem address
-constexpr int kSmemBytes = kSBar + 64;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -139,27 +128,62 @@ __device__ __forceinline__ void store_row32(uint8_t *base, int row, int k0, int 
         make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
 }
 
-__global__ void __launch_bounds__(kNetThreads, 1)
-mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ feats, int batch, int W, int H,
-                 float *__restrict__ out, uint16_t *__restrict__ acts, uint32_t *__restrict__ status) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *sW1 = smem + kSW1, *sW2 = smem + kSW2, *sW3 = smem + kSW3;
-  uint8_t *sA1 = smem + kSA1, *sH1 = smem + kSH1, *sA2 = smem + kSA2, *sA3 = smem + kSA3;
-  float *sb1 = reinterpret_cast<float *>(smem + kSPar), *sb2 = sb1 + kCh, *sb3 = sb2 + kCh, *sw4 = sb3 + kCh;
-  float *sb4 = sw4 + kCh;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kSBar);
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kSBar + 8);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// Forward kernel: two warpgroups per CTA, each running its own tile stream
+// (tiles 2i + g) with its own operands, TMEM columns and mbarriers, so that
+// one warpgroup's epilogue overlaps the other's MMAs; the next tile's input
+// halo is fetched by TMA while the current tile is in flight.
+//
+// Operand layouts of the forward (no swizzle): "row-contiguous chunks" -
+// chunk c holds channels 8c..8c+7 of every row as one 16-byte line, rows
+// consecutive (SBO = 128 B between 8-row groups, LBO = the chunk stride).
+// An MMA may then start at any row, which makes the 3 x 3 convolution an
+// implicit GEMM: tap (ky, kx) reads the a1 rows ky * 130 + kx + p directly,
+// with no im2col copy.
+constexpr int kFwdThreads = 256;
+constexpr int kInBytes = 2 * kHaloPad * 16;           // chunk 0 = TMA halo (390 rows), chunk 1 = zeros
+constexpr int kA1Chunk = 392 * 16;                     // 6272
+constexpr int kWgIn = 0, kWgA1 = kInBytes, kWgA2 = kWgA1 + 4 * kA1Chunk;
+constexpr int kWgBytes = kWgA2 + 4 * kTileW * 16;       // 49664
+constexpr int kFW1 = 2 * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFPar = kFW3 + 2048;
+constexpr int kFBar = kFPar + (4 * kCh + 4) * 4;
+constexpr int kFwdSmem = kFBar + 64 + 1024;             // + alignment slack
+constexpr int kHaloBytes = kHaloRows * 16;              // 6240 = the TMA box (8 x 130 x 3 x 1 bf16)
 
-  // weights into the K-major operand layouts; biases and w4 as FP32
+__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+__device__ __forceinline__ void tma_halo(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y, int b) {
+  const uint32_t mb = smem_u32(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(kHaloBytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(x), "r"(y), "r"(b), "r"(mb)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
+mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__restrict__ weights, int batch, int W,
+                 int H, float *__restrict__ out, uint16_t *__restrict__ acts, uint32_t *__restrict__ status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3;
+  float *sb1 = reinterpret_cast<float *>(smem + kFPar), *sb2 = sb1 + kCh, *sb3 = sb2 + kCh, *sw4 = sb3 + kCh;
+  float *sb4 = sw4 + kCh;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);   // [g]: tma, mma
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 32);
+  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 40);
+  const int tid = threadIdx.x, g = tid >> 7, t = tid & 127, warp = t >> 5, lane = tid & 31;
+  uint8_t *sIn = smem + g * kWgBytes + kWgIn, *sA1 = smem + g * kWgBytes + kWgA1, *sA2 = smem + g * kWgBytes + kWgA2;
+  uint64_t *bar_tma = bars + 2 * g, *bar_mma = bars + 2 * g + 1;
+
   const uint16_t *gw1 = reinterpret_cast<const uint16_t *>(weights + kOffW1);
   const uint16_t *gw2 = reinterpret_cast<const uint16_t *>(weights + kOffW2);
   const uint16_t *gw3 = reinterpret_cast<const uint16_t *>(weights + kOffW3);
-  for (int e = tid; e < 32 * 16; e += kNetThreads)
-    *reinterpret_cast<uint16_t *>(sW1 + core_off(e / 16, e % 16, 16)) = gw1[e];
-  for (int e = tid; e < 32 * kK2; e += kNetThreads)
+  for (int e = tid; e < 32 * 16; e += kFwdThreads)
+    *reinterpret_cast<uint16_t *>(sW1 + core_off(e / 16, e % 16, 16)) = (e % 16) < 8 ? gw1[e] : (uint16_t)0;
+  for (int e = tid; e < 32 * kK2; e += kFwdThreads)
     *reinterpret_cast<uint16_t *>(sW2 + core_off(e / kK2, e % kK2, kK2)) = gw2[e];
-  for (int e = tid; e < 32 * 32; e += kNetThreads)
+  for (int e = tid; e < 32 * 32; e += kFwdThreads)
     *reinterpret_cast<uint16_t *>(sW3 + core_off(e / 32, e % 32, 32)) = gw3[e];
   if (tid < kCh) {
     sb1[tid] = reinterpret_cast<const float *>(weights + kOffB1)[tid];
@@ -167,61 +191,83 @@ mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ 
     sb3[tid] = reinterpret_cast<const float *>(weights + kOffB3)[tid];
     sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
   }
+  // input buffers: rows 390-511 of chunk 0 and all of chunk 1 are never
+  // written by the TMA and stay zero
+  for (int e = t; e < (kInBytes - kHaloBytes) / 16; e += 128)
+    *reinterpret_cast<uint4 *>(sIn + kHaloBytes + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     sb4[0] = reinterpret_cast<const float *>(weights + kOffB4)[0];
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
+    for (int k = 0; k < 4; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail[0] = 0u;
+    s_fail[1] = 0u;
   }
-  if (warp == 0) {
+  if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
-                 "r"(kTmemCols));
+                 "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // the zero half of the first operand (input channels 8-15) never changes
-  for (int h = tid; h < kHaloPad; h += kNetThreads)
-    *reinterpret_cast<uint4 *>(sA1 + core_off(h, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+  fence_async_smem();
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  const uint32_t tmem = *s_tmem;
+  const uint32_t tmem = *s_tmem + (uint32_t)(256 * g);   // D1: +0..127, D2: +128, D3: +160
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  uint32_t phase = 0;
+  uint32_t ph_tma = 0, ph_mma = 0;
   bool ok = true;
+  bool tma_inflight = false, mma_inflight = false;   // thread 0's outstanding async work
 
   const int tiles_x = (W + kTileW - 1) / kTileW;
   const long long ntiles = (long long)batch * H * tiles_x;
-  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int tx = (int)(t % tiles_x);
-    const int y = (int)((t / tiles_x) % H);
-    const int b = (int)(t / ((long long)tiles_x * H));
-    const int x0 = tx * kTileW;
-    const uint4 *fb = feats + (size_t)b * H * W;
-
-    // 1. halo inputs -> first operand (rows h = r * 130 + c; x = x0 - 1 + c)
-    for (int h = tid; h < kHaloPad; h += kNetThreads) {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (h < kHaloRows) {
-        const int r = h / kHaloW, c = h % kHaloW;
-        const int yy = y - 1 + r, xx = x0 - 1 + c;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = __ldg(fb + (size_t)yy * W + xx);
-      }
-      *reinterpret_cast<uint4 *>(sA1 + core_off(h, 0, 16)) = v;
-    }
-    fence_async_smem();
-    tc_before_sync();
-    __syncthreads();
-    tc_after_sync();
-    if (tid == 0) {
+  const long long stride = 2ll * gridDim.x;
+  auto coords = [&](long long T, int *b, int *y, int *x0) {
+    *x0 = (int)(T % tiles_x) * kTileW;
+    *y = (int)((T / tiles_x) % H);
+    *b = (int)(T / ((long long)tiles_x * H));
+  };
+  long long T = 2ll * blockIdx.x + g;
+  if (T < ntiles && t == 0) {
+    int b, y, x0;
+    coords(T, &b, &y, &x0);
+    tma_halo(&in_map, smem_u32(sIn), bar_tma, x0 - 1, y - 1, b);
+    tma_inflight = true;
+  }
+  for (; T < ntiles; T += stride) {
+    int b, y, x0;
+    coords(T, &b, &y, &x0);
+    // 1. z1 over the 390 halo pixels: 4 MMAs (M = 128, N = 32, K = 16)
+    if (t == 0) {
+      ok = bar_wait(bar_tma, ph_tma);
+      tma_inflight = !ok;
+      if (ok) {
+        tc_after_sync();
 #pragma unroll
-      for (int mb = 0; mb < 4; ++mb)
-        mma_bf16(tmem + mb * 32, sdesc(smem_u32(sA1) + mb * 4096, 128, 256), sdesc(smem_u32(sW1), 128, 256),
-                 idesc_bf16(128, 32), 0u);
-      mma_commit(bar);
+        for (int mb = 0; mb < 4; ++mb)
+          mma_bf16(tmem + mb * 32, sdesc(smem_u32(sIn) + mb * 2048, kHaloPad * 16, 128), sdesc(smem_u32(sW1), 128, 256),
+                   idesc_bf16(128, 32), 0u);
+        mma_commit(bar_mma);
+        mma_inflight = true;
+      }
     }
-    ok = bar_wait(bar, phase);
-    phase ^= 1u;
+    ph_tma ^= 1u;
+    {
+      const bool done = ok && bar_wait(bar_mma, ph_mma);
+      if (done) mma_inflight = false;
+      ok = done && ok;
+    }
+    ph_mma ^= 1u;
     tc_after_sync();
-
-    // 2. z1 -> a1 (zero outside the image) -> halo buffer
+    // the input buffer is free: prefetch the next tile's halo
+    if (T + stride < ntiles) {
+      if (t == 0 && ok) {
+        int nb, ny, nx0;
+        coords(T + stride, &nb, &ny, &nx0);
+        tma_halo(&in_map, smem_u32(sIn), bar_tma, nx0 - 1, ny - 1, nb);
+        tma_inflight = true;
+      }
+    }
+    // 2. a1 = bf16(relu(z1 + b1)), zero outside the image, into chunks
+#pragma unroll 1
     for (int mb = 0; mb < 4; ++mb) {
       float z[32];
       tmem_ld32(tmem + lane_base + mb * 32, z);
@@ -234,45 +280,41 @@ mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ 
 #pragma unroll
         for (int k = 0; k < 16; ++k)
           w[k] = in ? pack_bf16x2(fmaxf(z[2 * k] + sb1[2 * k], 0.f), fmaxf(z[2 * k + 1] + sb1[2 * k + 1], 0.f)) : 0u;
-        uint4 *dst = reinterpret_cast<uint4 *>(sH1 + (size_t)h * 64);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4 *>(sA1 + q * kA1Chunk + h * 16) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         if (acts && r == 1 && c >= 1 && c <= kTileW && xx < W) {
           uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + xx) * 96);
 #pragma unroll
-          for (int g = 0; g < 4; ++g) ga[g] = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+          for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
       }
     }
+    fence_async_smem();
     tc_before_sync();
-    __syncthreads();
-    // im2col: row p, columns tap * 32 + channel, tap = ky * 3 + kx -> halo
-    // pixel (ky, p + kx)
-    {
-      const int p = tid;
+    wg_sync(g);
+    tc_after_sync();
+    // 3. z2: implicit-GEMM 3 x 3 convolution, 9 taps x 2 K-halves
+    if (t == 0 && ok) {
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
-        const uint4 *src = reinterpret_cast<const uint4 *>(sH1 + (size_t)(ky * kHaloW + p + kx) * 64);
 #pragma unroll
-        for (int g = 0; g < 4; ++g)
-          *reinterpret_cast<uint4 *>(sA2 + core_off(p, tap * 32 + 8 * g, kK2)) = src[g];
+        for (int j = 0; j < 2; ++j)
+          mma_bf16(tmem + 128, sdesc(smem_u32(sA1) + 2 * j * kA1Chunk + (ky * kHaloW + kx) * 16, kA1Chunk, 128),
+                   sdesc(smem_u32(sW2) + (2 * tap + j) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
+                   (tap | j) ? 1u : 0u);
       }
+      mma_commit(bar_mma);
+      mma_inflight = true;
     }
-    fence_async_smem();
-    __syncthreads();
-    tc_after_sync();
-    if (tid == 0) {
-      for (int c = 0; c < kK2 / 16; ++c)
-        mma_bf16(tmem + 128, sdesc(smem_u32(sA2) + c * 256, 128, (kK2 / 8) * 128),
-                 sdesc(smem_u32(sW2) + c * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32), c > 0 ? 1u : 0u);
-      mma_commit(bar);
+    {
+      const bool done = ok && bar_wait(bar_mma, ph_mma);
+      if (done) mma_inflight = false;
+      ok = done && ok;
     }
-    ok = ok && bar_wait(bar, phase);
-    phase ^= 1u;
+    ph_mma ^= 1u;
     tc_after_sync();
-
-    // 3. z2 -> a2 -> third operand
     const int p = 32 * warp + lane;
     {
       float z[32];
@@ -281,28 +323,36 @@ mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ 
 #pragma unroll
       for (int k = 0; k < 16; ++k)
         w[k] = pack_bf16x2(fmaxf(z[2 * k] + sb2[2 * k], 0.f), fmaxf(z[2 * k + 1] + sb2[2 * k + 1], 0.f));
-      store_row32(sA3, p, 0, 32, w);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4 *>(sA2 + q * (kTileW * 16) + p * 16) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       if (acts && x0 + p < W) {
         uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) ga[g] = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+        for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
       }
     }
     fence_async_smem();
     tc_before_sync();
-    __syncthreads();
+    wg_sync(g);
     tc_after_sync();
-    if (tid == 0) {
-      for (int c = 0; c < 2; ++c)
-        mma_bf16(tmem + 160, sdesc(smem_u32(sA3) + c * 256, 128, 512), sdesc(smem_u32(sW3) + c * 256, 128, 512),
-                 idesc_bf16(128, 32), c > 0 ? 1u : 0u);
-      mma_commit(bar);
+    // 4. z3: 2 MMAs
+    if (t == 0 && ok) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j)
+        mma_bf16(tmem + 160, sdesc(smem_u32(sA2) + 2 * j * (kTileW * 16), kTileW * 16, 128),
+                 sdesc(smem_u32(sW3) + j * 256, 128, 512), idesc_bf16(128, 32), j ? 1u : 0u);
+      mma_commit(bar_mma);
+      mma_inflight = true;
     }
-    ok = ok && bar_wait(bar, phase);
-    phase ^= 1u;
+    {
+      const bool done = ok && bar_wait(bar_mma, ph_mma);
+      if (done) mma_inflight = false;
+      ok = done && ok;
+    }
+    ph_mma ^= 1u;
     tc_after_sync();
-
-    // 4. z3 -> a3 -> y
+    // 5. a3, the dot product with w4 and the sigmoid
     {
       float z[32];
       tmem_ld32(tmem + lane_base + 160, z);
@@ -321,24 +371,28 @@ mpnet_fwd_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ 
         if (acts) {
           uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
 #pragma unroll
-          for (int g = 0; g < 4; ++g) ga[g] = make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
+          for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
       }
     }
+    if (!ok) s_fail[g] = 1u;
     tc_before_sync();
-    ok = __syncthreads_and(ok) != 0;   // uniform loop exit
+    wg_sync(g);
+    if (s_fail[g]) break;
   }
-  if (!ok) {
-    // a wait gave up: record it and give in-flight MMAs one more bounded wait
-    // before the tensor memory is released
-    if (tid == 0) atomicOr(status, kStatusTimeout);
-    bar_wait(bar, phase ^ 1u);
+  if (s_fail[g]) {
+    // a wait gave up: record it; give what may still be in flight one more
+    // bounded wait before the tensor memory is released
+    if (t == 0) {
+      atomicOr(status, kStatusTimeout);
+      if (tma_inflight) bar_wait(bar_tma, ph_tma ^ 1u);
+      if (mma_inflight) bar_wait(bar_mma, ph_mma ^ 1u);
+    }
   }
   tc_before_sync();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem), "r"(512));
 }
-
 
 // ----------------------------------------------------------------- training
 //
@@ -782,14 +836,34 @@ __global__ void mpnet_adam_kernel(uint8_t *__restrict__ weights, float *__restri
 
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(mpnet_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (e != cudaSuccess) return e;
   const long long ntiles = (long long)batch * H * ((W + kTileW - 1) / kTileW);
-  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  const long long pairs = (ntiles + 1) / 2;
+  const int grid = (int)(pairs < num_sms ? pairs : num_sms);
   if (grid <= 0) return cudaSuccess;
-  mpnet_fwd_kernel<<<grid, kNetThreads, kSmemBytes, s>>>(static_cast<const uint8_t *>(weights),
-                                                         reinterpret_cast<const uint4 *>(feats), batch, W, H, out,
-                                                         acts, status);
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return cudaErrorNotSupported;
+  // the input as a 4-D tensor (channel, x, y, image); box = the 8 x 130 x 3
+  // halo of one tile; out-of-range elements (image borders) read as zero
+  CUtensorMap map;
+  const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, 3, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(feats), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(mpnet_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
+  if (e != cudaSuccess) return e;
+  mpnet_fwd_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(map, static_cast<const uint8_t *>(weights), batch, W, H, out,
+                                                       acts, status);
   return cudaGetLastError();
 }
 
