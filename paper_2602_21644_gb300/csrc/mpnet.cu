@@ -128,10 +128,11 @@ __device__ __forceinline__ void store_row32(uint8_t *base, int row, int k0, int 
         make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
 }
 
-// Forward kernel: two warpgroups per CTA, each running its own tile stream
-// (tiles 2i + g) with its own operands, TMEM columns and mbarriers, so that
-// one warpgroup's epilogue overlaps the other's MMAs; the next tile's input
-// halo is fetched by TMA while the current tile is in flight.
+// Forward kernel: kGroups warpgroups per CTA, each running its own tile
+// stream (tiles kGroups * i + g) with its own operands, TMEM columns and
+// mbarriers, so that one warpgroup's epilogue overlaps the others' MMAs; the
+// next tile's input halo is fetched by TMA while the current tile is in
+// flight.
 //
 // Operand layouts of the forward (no swizzle): "row-contiguous chunks" -
 // chunk c holds channels 8c..8c+7 of every row as one 16-byte line, rows
@@ -139,17 +140,33 @@ __device__ __forceinline__ void store_row32(uint8_t *base, int row, int k0, int 
 // An MMA may then start at any row, which makes the 3 x 3 convolution an
 // implicit GEMM: tap (ky, kx) reads the a1 rows ky * 130 + kx + p directly,
 // with no im2col copy.
-constexpr int kFwdThreads = 256;
-constexpr int kInBytes = 2 * kHaloPad * 16;           // chunk 0 = TMA halo (390 rows), chunk 1 = zeros
+//
+// Biases ride in the MMAs: a K-chunk of per-row constants (1, 1, 0, ..., 0)
+// meets a B column pair (hi, lo) with hi = bf16(b), lo = bf16(b - hi), so
+// that z = W a + hi + lo accumulates in FP32 in the tensor core (|hi + lo -
+// b| <= 2^-17 |b|); the epilogues are then ReLU + BF16 rounding in one
+// conversion per pair.
+constexpr int kGroups = 3;
+constexpr int kFwdThreads = 128 * kGroups;
+constexpr int kInBytes = 2 * kHaloPad * 16;           // chunk 0 = TMA halo (390 rows), chunk 1 = (1, 1, 0...)
 constexpr int kA1Chunk = 392 * 16;                     // 6272
 constexpr int kWgIn = 0, kWgA1 = kInBytes, kWgA2 = kWgA1 + 4 * kA1Chunk;
 constexpr int kWgBytes = kWgA2 + 4 * kTileW * 16;       // 49664
-constexpr int kFW1 = 2 * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFPar = kFW3 + 2048;
-constexpr int kFBar = kFPar + (4 * kCh + 4) * 4;
-constexpr int kFwdSmem = kFBar + 64 + 1024;             // + alignment slack
+constexpr int kFW1 = kGroups * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFB2 = kFW3 + 2048,
+              kFB3 = kFB2 + 1024, kFPar = kFB3 + 1024;
+constexpr int kFBar = kFPar + (kCh + 4) * 4;
+constexpr int kFwdSmem = kFBar + 128 + 1024;            // + alignment slack
 constexpr int kHaloBytes = kHaloRows * 16;              // 6240 = the TMA box (8 x 130 x 3 x 1 bf16)
+constexpr uint32_t kWgCols = 160;                       // D1 +0..127 (D3 reuses +0..31), D2 +128..159
 
 __device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+
+// BF16 pair (lo, hi) of relu(lo), relu(hi), round to nearest even.
+__device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
 
 __device__ __forceinline__ void tma_halo(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y, int b) {
   const uint32_t mb = smem_u32(bar);
@@ -161,46 +178,58 @@ __device__ __forceinline__ void tma_halo(const CUtensorMap *map, uint32_t dst, u
       : "memory");
 }
 
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+
 __global__ void __launch_bounds__(kFwdThreads, 1)
 mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__restrict__ weights, int batch, int W,
                  int H, float *__restrict__ out, uint16_t *__restrict__ acts, uint32_t *__restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3;
-  float *sb1 = reinterpret_cast<float *>(smem + kFPar), *sb2 = sb1 + kCh, *sb3 = sb2 + kCh, *sw4 = sb3 + kCh;
-  float *sb4 = sw4 + kCh;
+  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3, *sB2 = smem + kFB2, *sB3 = smem + kFB3;
+  float *sw4 = reinterpret_cast<float *>(smem + kFPar), *sb4 = sw4 + kCh;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);   // [g]: tma, mma
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 32);
-  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 40);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 64);
+  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 72);
   const int tid = threadIdx.x, g = tid >> 7, t = tid & 127, warp = t >> 5, lane = tid & 31;
   uint8_t *sIn = smem + g * kWgBytes + kWgIn, *sA1 = smem + g * kWgBytes + kWgA1, *sA2 = smem + g * kWgBytes + kWgA2;
   uint64_t *bar_tma = bars + 2 * g, *bar_mma = bars + 2 * g + 1;
 
+  // weights into the K-major core-matrix layouts; bias columns (hi, lo)
   const uint16_t *gw1 = reinterpret_cast<const uint16_t *>(weights + kOffW1);
   const uint16_t *gw2 = reinterpret_cast<const uint16_t *>(weights + kOffW2);
   const uint16_t *gw3 = reinterpret_cast<const uint16_t *>(weights + kOffW3);
-  for (int e = tid; e < 32 * 16; e += kFwdThreads)
-    *reinterpret_cast<uint16_t *>(sW1 + core_off(e / 16, e % 16, 16)) = (e % 16) < 8 ? gw1[e] : (uint16_t)0;
+  const float *gb1 = reinterpret_cast<const float *>(weights + kOffB1);
+  const float *gb2 = reinterpret_cast<const float *>(weights + kOffB2);
+  const float *gb3 = reinterpret_cast<const float *>(weights + kOffB3);
+  for (int e = tid; e < 32 * 16; e += kFwdThreads) {
+    const int o = e / 16, k = e % 16;
+    const float bias = gb1[o], hi = __bfloat162float(__float2bfloat16_rn(bias));
+    const uint16_t v = k < 8 ? gw1[e] : k == 8 ? bf16_bits(bias) : k == 9 ? bf16_bits(bias - hi) : (uint16_t)0;
+    *reinterpret_cast<uint16_t *>(sW1 + core_off(o, k, 16)) = v;
+  }
   for (int e = tid; e < 32 * kK2; e += kFwdThreads)
     *reinterpret_cast<uint16_t *>(sW2 + core_off(e / kK2, e % kK2, kK2)) = gw2[e];
   for (int e = tid; e < 32 * 32; e += kFwdThreads)
     *reinterpret_cast<uint16_t *>(sW3 + core_off(e / 32, e % 32, 32)) = gw3[e];
-  if (tid < kCh) {
-    sb1[tid] = reinterpret_cast<const float *>(weights + kOffB1)[tid];
-    sb2[tid] = reinterpret_cast<const float *>(weights + kOffB2)[tid];
-    sb3[tid] = reinterpret_cast<const float *>(weights + kOffB3)[tid];
-    sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
+  for (int e = tid; e < 2 * 32 * 16; e += kFwdThreads) {
+    const int which = e / 512, o = (e / 16) % 32, k = e % 16;
+    const float bias = which ? gb3[o] : gb2[o], hi = __bfloat162float(__float2bfloat16_rn(bias));
+    const uint16_t v = k == 0 ? bf16_bits(bias) : k == 1 ? bf16_bits(bias - hi) : (uint16_t)0;
+    *reinterpret_cast<uint16_t *>((which ? sB3 : sB2) + core_off(o, k, 16)) = v;
   }
-  // input buffers: rows 390-511 of chunk 0 and all of chunk 1 are never
-  // written by the TMA and stay zero
-  for (int e = t; e < (kInBytes - kHaloBytes) / 16; e += 128)
+  if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
+  // input buffers: rows 390-511 of chunk 0 are never written by the TMA
+  // (zero); chunk 1 holds the bias constants (1, 1, 0, ..., 0) of every row
+  for (int e = t; e < (kHaloPad * 16 - kHaloBytes) / 16; e += 128)
     *reinterpret_cast<uint4 *>(sIn + kHaloBytes + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = t; e < kHaloPad; e += 128)
+    *reinterpret_cast<uint4 *>(sIn + kHaloPad * 16 + 16 * e) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
   if (tid == 0) {
     sb4[0] = reinterpret_cast<const float *>(weights + kOffB4)[0];
-    for (int k = 0; k < 4; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)));
+    for (int k = 0; k < 2 * kGroups; ++k)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_fail[0] = 0u;
-    s_fail[1] = 0u;
+    for (int k = 0; k < kGroups; ++k) s_fail[k] = 0u;
   }
   if (tid < 32) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
@@ -211,21 +240,22 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  const uint32_t tmem = *s_tmem + (uint32_t)(256 * g);   // D1: +0..127, D2: +128, D3: +160
+  const uint32_t tmem = *s_tmem + kWgCols * (uint32_t)g;
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  const uint32_t ones = smem_u32(sIn) + kHaloPad * 16;   // 128+ rows of (1, 1, 0, ...)
   uint32_t ph_tma = 0, ph_mma = 0;
   bool ok = true;
   bool tma_inflight = false, mma_inflight = false;   // thread 0's outstanding async work
 
   const int tiles_x = (W + kTileW - 1) / kTileW;
   const long long ntiles = (long long)batch * H * tiles_x;
-  const long long stride = 2ll * gridDim.x;
+  const long long stride = (long long)kGroups * gridDim.x;
   auto coords = [&](long long T, int *b, int *y, int *x0) {
     *x0 = (int)(T % tiles_x) * kTileW;
     *y = (int)((T / tiles_x) % H);
     *b = (int)(T / ((long long)tiles_x * H));
   };
-  long long T = 2ll * blockIdx.x + g;
+  long long T = (long long)kGroups * blockIdx.x + g;
   if (T < ntiles && t == 0) {
     int b, y, x0;
     coords(T, &b, &y, &x0);
@@ -235,7 +265,8 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   for (; T < ntiles; T += stride) {
     int b, y, x0;
     coords(T, &b, &y, &x0);
-    // 1. z1 over the 390 halo pixels: 4 MMAs (M = 128, N = 32, K = 16)
+    // 1. z1 over the 390 halo pixels: 4 MMAs (M = 128, N = 32, K = 16:
+    //    8 input channels + the bias chunk)
     if (t == 0) {
       ok = bar_wait(bar_tma, ph_tma);
       tma_inflight = !ok;
@@ -258,15 +289,13 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     ph_mma ^= 1u;
     tc_after_sync();
     // the input buffer is free: prefetch the next tile's halo
-    if (T + stride < ntiles) {
-      if (t == 0 && ok) {
-        int nb, ny, nx0;
-        coords(T + stride, &nb, &ny, &nx0);
-        tma_halo(&in_map, smem_u32(sIn), bar_tma, nx0 - 1, ny - 1, nb);
-        tma_inflight = true;
-      }
+    if (T + stride < ntiles && t == 0 && ok) {
+      int nb, ny, nx0;
+      coords(T + stride, &nb, &ny, &nx0);
+      tma_halo(&in_map, smem_u32(sIn), bar_tma, nx0 - 1, ny - 1, nb);
+      tma_inflight = true;
     }
-    // 2. a1 = bf16(relu(z1 + b1)), zero outside the image, into chunks
+    // 2. a1 = bf16(relu(z1)), zero outside the image, into chunks
 #pragma unroll 1
     for (int mb = 0; mb < 4; ++mb) {
       float z[32];
@@ -278,8 +307,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
         uint32_t w[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k)
-          w[k] = in ? pack_bf16x2(fmaxf(z[2 * k] + sb1[2 * k], 0.f), fmaxf(z[2 * k + 1] + sb1[2 * k + 1], 0.f)) : 0u;
+        for (int k = 0; k < 16; ++k) w[k] = in ? relu_bf16x2(z[2 * k], z[2 * k + 1]) : 0u;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           *reinterpret_cast<uint4 *>(sA1 + q * kA1Chunk + h * 16) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
@@ -294,7 +322,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     tc_before_sync();
     wg_sync(g);
     tc_after_sync();
-    // 3. z2: implicit-GEMM 3 x 3 convolution, 9 taps x 2 K-halves
+    // 3. z2: implicit-GEMM 3 x 3 convolution, 9 taps x 2 K-halves, + bias
     if (t == 0 && ok) {
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
@@ -305,6 +333,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
                    sdesc(smem_u32(sW2) + (2 * tap + j) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
                    (tap | j) ? 1u : 0u);
       }
+      mma_bf16(tmem + 128, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256), idesc_bf16(128, 32), 1u);
       mma_commit(bar_mma);
       mma_inflight = true;
     }
@@ -321,8 +350,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
       tmem_ld32(tmem + lane_base + 128, z);
       uint32_t w[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k)
-        w[k] = pack_bf16x2(fmaxf(z[2 * k] + sb2[2 * k], 0.f), fmaxf(z[2 * k + 1] + sb2[2 * k + 1], 0.f));
+      for (int k = 0; k < 16; ++k) w[k] = relu_bf16x2(z[2 * k], z[2 * k + 1]);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         *reinterpret_cast<uint4 *>(sA2 + q * (kTileW * 16) + p * 16) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
@@ -336,12 +364,13 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     tc_before_sync();
     wg_sync(g);
     tc_after_sync();
-    // 4. z3: 2 MMAs
+    // 4. z3: 2 MMAs + bias, into the (consumed) D1 columns
     if (t == 0 && ok) {
 #pragma unroll
       for (int j = 0; j < 2; ++j)
-        mma_bf16(tmem + 160, sdesc(smem_u32(sA2) + 2 * j * (kTileW * 16), kTileW * 16, 128),
+        mma_bf16(tmem + 0, sdesc(smem_u32(sA2) + 2 * j * (kTileW * 16), kTileW * 16, 128),
                  sdesc(smem_u32(sW3) + j * 256, 128, 512), idesc_bf16(128, 32), j ? 1u : 0u);
+      mma_bf16(tmem + 0, sdesc(ones, 2048, 128), sdesc(smem_u32(sB3), 128, 256), idesc_bf16(128, 32), 1u);
       mma_commit(bar_mma);
       mma_inflight = true;
     }
@@ -355,15 +384,13 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     // 5. a3, the dot product with w4 and the sigmoid
     {
       float z[32];
-      tmem_ld32(tmem + lane_base + 160, z);
+      tmem_ld32(tmem + lane_base + 0, z);
       float acc = sb4[0];
       uint32_t w[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const float a0 = bf16_round_f(fmaxf(z[2 * k] + sb3[2 * k], 0.f));
-        const float a1v = bf16_round_f(fmaxf(z[2 * k + 1] + sb3[2 * k + 1], 0.f));
-        acc += a0 * sw4[2 * k] + a1v * sw4[2 * k + 1];
-        w[k] = pack_bf16x2(a0, a1v);
+        w[k] = relu_bf16x2(z[2 * k], z[2 * k + 1]);
+        acc += __uint_as_float(w[k] << 16) * sw4[2 * k] + __uint_as_float(w[k] & 0xFFFF0000u) * sw4[2 * k + 1];
       }
       if (x0 + p < W) {
         const size_t pix = ((size_t)b * H + y) * W + x0 + p;
@@ -377,7 +404,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     }
     if (!ok) s_fail[g] = 1u;
     tc_before_sync();
-    wg_sync(g);
+    wg_sync(g);   // D3 (= D1 columns) read by all before the next tile's first MMAs
     if (s_fail[g]) break;
   }
   if (s_fail[g]) {
@@ -837,8 +864,8 @@ __global__ void mpnet_adam_kernel(uint8_t *__restrict__ weights, float *__restri
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s) {
   const long long ntiles = (long long)batch * H * ((W + kTileW - 1) / kTileW);
-  const long long pairs = (ntiles + 1) / 2;
-  const int grid = (int)(pairs < num_sms ? pairs : num_sms);
+  const long long groups = (ntiles + kGroups - 1) / kGroups;
+  const int grid = (int)(groups < num_sms ? groups : num_sms);
   if (grid <= 0) return cudaSuccess;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void *fn = nullptr;
