@@ -128,36 +128,45 @@ __device__ __forceinline__ void store_row32(uint8_t *base, int row, int k0, int 
         make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
 }
 
-// Forward kernel: kGroups warpgroups per CTA, each running its own tile
-// stream (tiles kGroups * i + g) with its own operands, TMEM columns and
-// mbarriers, so that one warpgroup's epilogue overlaps the others' MMAs; the
-// next tile's input halo is fetched by TMA while the current tile is in
-// flight.
+// Forward kernel: kGroups warpgroups per CTA, each running its own stream
+// of work units with its own operands, TMEM columns and mbarriers, so that
+// one warpgroup's epilogues overlap the others' MMAs.
 //
-// Operand layouts of the forward (no swizzle): "row-contiguous chunks" -
-// chunk c holds channels 8c..8c+7 of every row as one 16-byte line, rows
-// consecutive (SBO = 128 B between 8-row groups, LBO = the chunk stride).
-// An MMA may then start at any row, which makes the 3 x 3 convolution an
-// implicit GEMM: tap (ky, kx) reads the a1 rows ky * 130 + kx + p directly,
-// with no im2col copy.
+// Work unit: a 128-pixel-wide column strip of one image over a segment of
+// rows [y0, y1). The warpgroup walks down the strip: it computes a1 for one
+// halo row at a time (130 pixels, x0 - 1 .. x0 + 128; rows y0 - 1 .. y1) into
+// a ring of three row slots, and as soon as rows y - 1, y, y + 1 are there it
+// computes output row y. Every a1 row is thus computed once per unit (plus
+// the two boundary rows), not three times as with independent row tiles.
+// The next a1 row's input (8 x 130 BF16) is fetched by TMA while the current
+// row is in flight; out-of-image rows and columns read as zero.
+//
+// Operand layouts (no swizzle): "row-contiguous chunks" - chunk c holds
+// channels 8c..8c+7 of every row as one 16-byte line, rows consecutive (SBO =
+// 128 B between 8-row groups, LBO = the chunk stride). An MMA may then start
+// at any row, which makes the 3 x 3 convolution an implicit GEMM: tap (ky, kx)
+// reads slot (y - 1 + ky) at rows kx + p directly, with no im2col copy.
 //
 // Biases ride in the MMAs: a K-chunk of per-row constants (1, 1, 0, ..., 0)
 // meets a B column pair (hi, lo) with hi = bf16(b), lo = bf16(b - hi), so
 // that z = W a + hi + lo accumulates in FP32 in the tensor core (|hi + lo -
 // b| <= 2^-17 |b|); the epilogues are then ReLU + BF16 rounding in one
 // conversion per pair.
-constexpr int kGroups = 3;
+constexpr int kGroups = 4;
 constexpr int kFwdThreads = 128 * kGroups;
-constexpr int kInBytes = 2 * kHaloPad * 16;           // chunk 0 = TMA halo (390 rows), chunk 1 = (1, 1, 0...)
-constexpr int kA1Chunk = 392 * 16;                     // 6272
-constexpr int kWgIn = 0, kWgA1 = kInBytes, kWgA2 = kWgA1 + 4 * kA1Chunk;
-constexpr int kWgBytes = kWgA2 + 4 * kTileW * 16;       // 49664
+constexpr int kInRows = 256;                            // 2 M-blocks; rows 0..129 from the TMA
+constexpr int kInBytes = 2 * kInRows * 16;              // chunk 0 = input, chunk 1 = (1, 1, 0, ...)
+constexpr int kSlotRows = 136;
+constexpr int kSlotChunk = kSlotRows * 16;              // 2176
+constexpr int kSlotBytes = 4 * kSlotChunk;              // 8704
+constexpr int kWgIn = 0, kWgRing = kInBytes, kWgA2 = kWgRing + 3 * kSlotBytes;
+constexpr int kWgBytes = kWgA2 + 4 * kTileW * 16;       // 42496
 constexpr int kFW1 = kGroups * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFB2 = kFW3 + 2048,
               kFB3 = kFB2 + 1024, kFPar = kFB3 + 1024;
-constexpr int kFBar = kFPar + (kCh + 4) * 4;
+constexpr int kFBar = kFPar + 256;
 constexpr int kFwdSmem = kFBar + 128 + 1024;            // + alignment slack
-constexpr int kHaloBytes = kHaloRows * 16;              // 6240 = the TMA box (8 x 130 x 3 x 1 bf16)
-constexpr uint32_t kWgCols = 160;                       // D1 +0..127 (D3 reuses +0..31), D2 +128..159
+constexpr int kRowBytes = kHaloW * 16;                  // 2080 = the TMA box (8 x 130 x 1 x 1 bf16)
+constexpr uint32_t kWgCols = 96;                        // D1 +0..63 (D3 reuses +0..31), D2 +64..95
 
 __device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
@@ -168,9 +177,9 @@ __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
   return r;
 }
 
-__device__ __forceinline__ void tma_halo(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y, int b) {
+__device__ __forceinline__ void tma_row(const CUtensorMap *map, uint32_t dst, uint64_t *bar, int x, int y, int b) {
   const uint32_t mb = smem_u32(bar);
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(kHaloBytes) : "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(kRowBytes) : "memory");
   asm volatile(
       "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
       "%5}], [%6];" ::"r"(dst),
@@ -180,9 +189,15 @@ __device__ __forceinline__ void tma_halo(const CUtensorMap *map, uint32_t dst, u
 
 __device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
 
+struct FwdUnits {
+  int tiles_x, segs, seg_rows;
+  long long count;
+};
+
 __global__ void __launch_bounds__(kFwdThreads, 1)
 mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__restrict__ weights, int batch, int W,
-                 int H, float *__restrict__ out, uint16_t *__restrict__ acts, uint32_t *__restrict__ status) {
+                 int H, FwdUnits units, float *__restrict__ out, uint16_t *__restrict__ acts,
+                 uint32_t *__restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3, *sB2 = smem + kFB2, *sB3 = smem + kFB3;
@@ -191,7 +206,8 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 64);
   volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 72);
   const int tid = threadIdx.x, g = tid >> 7, t = tid & 127, warp = t >> 5, lane = tid & 31;
-  uint8_t *sIn = smem + g * kWgBytes + kWgIn, *sA1 = smem + g * kWgBytes + kWgA1, *sA2 = smem + g * kWgBytes + kWgA2;
+  uint8_t *sIn = smem + g * kWgBytes + kWgIn, *sRing = smem + g * kWgBytes + kWgRing;
+  uint8_t *sA2 = smem + g * kWgBytes + kWgA2;
   uint64_t *bar_tma = bars + 2 * g, *bar_mma = bars + 2 * g + 1;
 
   // weights into the K-major core-matrix layouts; bias columns (hi, lo)
@@ -218,12 +234,12 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     *reinterpret_cast<uint16_t *>((which ? sB3 : sB2) + core_off(o, k, 16)) = v;
   }
   if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
-  // input buffers: rows 390-511 of chunk 0 are never written by the TMA
+  // input buffer: rows 130-255 of chunk 0 are never written by the TMA
   // (zero); chunk 1 holds the bias constants (1, 1, 0, ..., 0) of every row
-  for (int e = t; e < (kHaloPad * 16 - kHaloBytes) / 16; e += 128)
-    *reinterpret_cast<uint4 *>(sIn + kHaloBytes + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = t; e < kHaloPad; e += 128)
-    *reinterpret_cast<uint4 *>(sIn + kHaloPad * 16 + 16 * e) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+  for (int e = t; e < (kInRows * 16 - kRowBytes) / 16; e += 128)
+    *reinterpret_cast<uint4 *>(sIn + kRowBytes + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
+  for (int e = t; e < kInRows; e += 128)
+    *reinterpret_cast<uint4 *>(sIn + kInRows * 16 + 16 * e) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
   if (tid == 0) {
     sb4[0] = reinterpret_cast<const float *>(weights + kOffB4)[0];
     for (int k = 0; k < 2 * kGroups; ++k)
@@ -242,169 +258,195 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   tc_after_sync();
   const uint32_t tmem = *s_tmem + kWgCols * (uint32_t)g;
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  const uint32_t ones = smem_u32(sIn) + kHaloPad * 16;   // 128+ rows of (1, 1, 0, ...)
+  const uint32_t ones = smem_u32(sIn) + kInRows * 16;   // rows of (1, 1, 0, ...)
   uint32_t ph_tma = 0, ph_mma = 0;
   bool ok = true;
   bool tma_inflight = false, mma_inflight = false;   // thread 0's outstanding async work
 
-  const int tiles_x = (W + kTileW - 1) / kTileW;
-  const long long ntiles = (long long)batch * H * tiles_x;
   const long long stride = (long long)kGroups * gridDim.x;
-  auto coords = [&](long long T, int *b, int *y, int *x0) {
-    *x0 = (int)(T % tiles_x) * kTileW;
-    *y = (int)((T / tiles_x) % H);
-    *b = (int)(T / ((long long)tiles_x * H));
+  // unit u -> image b, strip x0, rows [y0, y1)
+  auto unit = [&](long long u, int *b, int *x0, int *y0, int *y1) {
+    const int seg = (int)(u % units.segs);
+    const long long rest = u / units.segs;
+    *x0 = (int)(rest % units.tiles_x) * kTileW;
+    *b = (int)(rest / units.tiles_x);
+    *y0 = seg * units.seg_rows;
+    *y1 = min(*y0 + units.seg_rows, H);
   };
-  long long T = (long long)kGroups * blockIdx.x + g;
-  if (T < ntiles && t == 0) {
-    int b, y, x0;
-    coords(T, &b, &y, &x0);
-    tma_halo(&in_map, smem_u32(sIn), bar_tma, x0 - 1, y - 1, b);
+  long long u = (long long)kGroups * blockIdx.x + g;
+  if (u < units.count && t == 0) {
+    int b, x0, y0, y1;
+    unit(u, &b, &x0, &y0, &y1);
+    tma_row(&in_map, smem_u32(sIn), bar_tma, x0 - 1, y0 - 1, b);
     tma_inflight = true;
   }
-  for (; T < ntiles; T += stride) {
-    int b, y, x0;
-    coords(T, &b, &y, &x0);
-    // 1. z1 over the 390 halo pixels: 4 MMAs (M = 128, N = 32, K = 16:
-    //    8 input channels + the bias chunk)
-    if (t == 0) {
-      ok = bar_wait(bar_tma, ph_tma);
-      tma_inflight = !ok;
-      if (ok) {
-        tc_after_sync();
-#pragma unroll
-        for (int mb = 0; mb < 4; ++mb)
-          mma_bf16(tmem + mb * 32, sdesc(smem_u32(sIn) + mb * 2048, kHaloPad * 16, 128), sdesc(smem_u32(sW1), 128, 256),
+  for (; u < units.count; u += stride) {
+    int b, x0, y0, y1;
+    unit(u, &b, &x0, &y0, &y1);
+    const int nrows = y1 - y0 + 2;   // a1 rows y0 - 1 .. y1
+    for (int k = 0; k < nrows; ++k) {
+      const int r = y0 - 1 + k;
+      uint8_t *slot = sRing + ((r + 3) % 3) * kSlotBytes;
+      // 1. z1 of a1 row r (130 pixels): 2 MMAs (M = 128, N = 32, K = 16:
+      //    8 input channels + the bias chunk)
+      if (t == 0) {
+        ok = ok && bar_wait(bar_tma, ph_tma);
+        tma_inflight = !ok;
+        if (ok) {
+          tc_after_sync();
+          mma_bf16(tmem + 0, sdesc(smem_u32(sIn), kInRows * 16, 128), sdesc(smem_u32(sW1), 128, 256),
                    idesc_bf16(128, 32), 0u);
+          mma_bf16(tmem + 32, sdesc(smem_u32(sIn) + 2048, kInRows * 16, 128), sdesc(smem_u32(sW1), 128, 256),
+                   idesc_bf16(128, 32), 0u);
+          mma_commit(bar_mma);
+          mma_inflight = true;
+        }
+      }
+      ph_tma ^= 1u;
+      {
+        const bool done = ok && bar_wait(bar_mma, ph_mma);
+        if (done) mma_inflight = false;
+        ok = done && ok;
+      }
+      ph_mma ^= 1u;
+      tc_after_sync();
+      // the input buffer is free: fetch the next a1 row's input (this unit's
+      // next row, else the next unit's first)
+      if (t == 0 && ok) {
+        if (k + 1 < nrows) {
+          tma_row(&in_map, smem_u32(sIn), bar_tma, x0 - 1, r + 1, b);
+          tma_inflight = true;
+        } else if (u + stride < units.count) {
+          int nb, nx0, ny0, ny1;
+          unit(u + stride, &nb, &nx0, &ny0, &ny1);
+          tma_row(&in_map, smem_u32(sIn), bar_tma, nx0 - 1, ny0 - 1, nb);
+          tma_inflight = true;
+        }
+      }
+      // 2. a1 = bf16(relu(z1)), zero outside the image, into the row's slot;
+      //    pixel i of the slot is x = x0 - 1 + i
+      {
+        const bool row_in = r >= 0 && r < H;
+        const bool own_row = r >= y0 && r < y1;
+#pragma unroll 1
+        for (int mb = 0; mb < 2; ++mb) {
+          if (mb == 1 && warp != 0) break;
+          float z[32];
+          tmem_ld32(tmem + lane_base + mb * 32, z);
+          const int i = mb * 128 + 32 * warp + lane;
+          if (i < kHaloW) {
+            const int xx = x0 - 1 + i;
+            const bool in = row_in && xx >= 0 && xx < W;
+            uint32_t w[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) w[q] = in ? relu_bf16x2(z[2 * q], z[2 * q + 1]) : 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              *reinterpret_cast<uint4 *>(slot + q * kSlotChunk + i * 16) =
+                  make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            if (acts && own_row && i >= 1 && i <= kTileW && xx < W) {
+              uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
+#pragma unroll
+              for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            }
+          }
+        }
+      }
+      fence_async_smem();
+      tc_before_sync();
+      wg_sync(g);
+      tc_after_sync();
+      if (k < 2) continue;   // output row r - 1 needs a1 rows r - 2, r - 1, r
+      const int y = r - 1;
+      // 3. z2 of output row y: implicit-GEMM 3 x 3 convolution, 9 taps x 2
+      //    K-halves, + bias
+      if (t == 0 && ok) {
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap % 3;
+          const uint32_t sl = smem_u32(sRing) + ((y + 2 + ky) % 3) * kSlotBytes;
+#pragma unroll
+          for (int j = 0; j < 2; ++j)
+            mma_bf16(tmem + 64, sdesc(sl + 2 * j * kSlotChunk + kx * 16, kSlotChunk, 128),
+                     sdesc(smem_u32(sW2) + (2 * tap + j) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
+                     (tap | j) ? 1u : 0u);
+        }
+        mma_bf16(tmem + 64, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256), idesc_bf16(128, 32), 1u);
         mma_commit(bar_mma);
         mma_inflight = true;
       }
-    }
-    ph_tma ^= 1u;
-    {
-      const bool done = ok && bar_wait(bar_mma, ph_mma);
-      if (done) mma_inflight = false;
-      ok = done && ok;
-    }
-    ph_mma ^= 1u;
-    tc_after_sync();
-    // the input buffer is free: prefetch the next tile's halo
-    if (T + stride < ntiles && t == 0 && ok) {
-      int nb, ny, nx0;
-      coords(T + stride, &nb, &ny, &nx0);
-      tma_halo(&in_map, smem_u32(sIn), bar_tma, nx0 - 1, ny - 1, nb);
-      tma_inflight = true;
-    }
-    // 2. a1 = bf16(relu(z1)), zero outside the image, into chunks
-#pragma unroll 1
-    for (int mb = 0; mb < 4; ++mb) {
-      float z[32];
-      tmem_ld32(tmem + lane_base + mb * 32, z);
-      const int h = mb * 128 + 32 * warp + lane;
-      if (h < kHaloRows) {
-        const int r = h / kHaloW, c = h % kHaloW;
-        const int yy = y - 1 + r, xx = x0 - 1 + c;
-        const bool in = yy >= 0 && yy < H && xx >= 0 && xx < W;
+      {
+        const bool done = ok && bar_wait(bar_mma, ph_mma);
+        if (done) mma_inflight = false;
+        ok = done && ok;
+      }
+      ph_mma ^= 1u;
+      tc_after_sync();
+      const int p = 32 * warp + lane;
+      {
+        float z[32];
+        tmem_ld32(tmem + lane_base + 64, z);
         uint32_t w[16];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) w[k] = in ? relu_bf16x2(z[2 * k], z[2 * k + 1]) : 0u;
+        for (int q = 0; q < 16; ++q) w[q] = relu_bf16x2(z[2 * q], z[2 * q + 1]);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4 *>(sA1 + q * kA1Chunk + h * 16) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-        if (acts && r == 1 && c >= 1 && c <= kTileW && xx < W) {
-          uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + xx) * 96);
+          *reinterpret_cast<uint4 *>(sA2 + q * (kTileW * 16) + p * 16) =
+              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        if (acts && x0 + p < W) {
+          uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
 #pragma unroll
           for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
         }
       }
-    }
-    fence_async_smem();
-    tc_before_sync();
-    wg_sync(g);
-    tc_after_sync();
-    // 3. z2: implicit-GEMM 3 x 3 convolution, 9 taps x 2 K-halves, + bias
-    if (t == 0 && ok) {
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
+      fence_async_smem();
+      tc_before_sync();
+      wg_sync(g);
+      tc_after_sync();
+      // 4. z3: 2 MMAs + bias, into the (consumed) D1 columns
+      if (t == 0 && ok) {
 #pragma unroll
         for (int j = 0; j < 2; ++j)
-          mma_bf16(tmem + 128, sdesc(smem_u32(sA1) + 2 * j * kA1Chunk + (ky * kHaloW + kx) * 16, kA1Chunk, 128),
-                   sdesc(smem_u32(sW2) + (2 * tap + j) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
-                   (tap | j) ? 1u : 0u);
+          mma_bf16(tmem + 0, sdesc(smem_u32(sA2) + 2 * j * (kTileW * 16), kTileW * 16, 128),
+                   sdesc(smem_u32(sW3) + j * 256, 128, 512), idesc_bf16(128, 32), j ? 1u : 0u);
+        mma_bf16(tmem + 0, sdesc(ones, 2048, 128), sdesc(smem_u32(sB3), 128, 256), idesc_bf16(128, 32), 1u);
+        mma_commit(bar_mma);
+        mma_inflight = true;
       }
-      mma_bf16(tmem + 128, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256), idesc_bf16(128, 32), 1u);
-      mma_commit(bar_mma);
-      mma_inflight = true;
-    }
-    {
-      const bool done = ok && bar_wait(bar_mma, ph_mma);
-      if (done) mma_inflight = false;
-      ok = done && ok;
-    }
-    ph_mma ^= 1u;
-    tc_after_sync();
-    const int p = 32 * warp + lane;
-    {
-      float z[32];
-      tmem_ld32(tmem + lane_base + 128, z);
-      uint32_t w[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) w[k] = relu_bf16x2(z[2 * k], z[2 * k + 1]);
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4 *>(sA2 + q * (kTileW * 16) + p * 16) = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
-      if (acts && x0 + p < W) {
-        uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+      {
+        const bool done = ok && bar_wait(bar_mma, ph_mma);
+        if (done) mma_inflight = false;
+        ok = done && ok;
       }
-    }
-    fence_async_smem();
-    tc_before_sync();
-    wg_sync(g);
-    tc_after_sync();
-    // 4. z3: 2 MMAs + bias, into the (consumed) D1 columns
-    if (t == 0 && ok) {
+      ph_mma ^= 1u;
+      tc_after_sync();
+      // 5. a3, the dot product with w4 and the sigmoid
+      {
+        float z[32];
+        tmem_ld32(tmem + lane_base + 0, z);
+        float acc = sb4[0];
+        uint32_t w[16];
 #pragma unroll
-      for (int j = 0; j < 2; ++j)
-        mma_bf16(tmem + 0, sdesc(smem_u32(sA2) + 2 * j * (kTileW * 16), kTileW * 16, 128),
-                 sdesc(smem_u32(sW3) + j * 256, 128, 512), idesc_bf16(128, 32), j ? 1u : 0u);
-      mma_bf16(tmem + 0, sdesc(ones, 2048, 128), sdesc(smem_u32(sB3), 128, 256), idesc_bf16(128, 32), 1u);
-      mma_commit(bar_mma);
-      mma_inflight = true;
-    }
-    {
-      const bool done = ok && bar_wait(bar_mma, ph_mma);
-      if (done) mma_inflight = false;
-      ok = done && ok;
-    }
-    ph_mma ^= 1u;
-    tc_after_sync();
-    // 5. a3, the dot product with w4 and the sigmoid
-    {
-      float z[32];
-      tmem_ld32(tmem + lane_base + 0, z);
-      float acc = sb4[0];
-      uint32_t w[16];
+        for (int q = 0; q < 16; ++q) {
+          w[q] = relu_bf16x2(z[2 * q], z[2 * q + 1]);
+          acc += __uint_as_float(w[q] << 16) * sw4[2 * q] + __uint_as_float(w[q] & 0xFFFF0000u) * sw4[2 * q + 1];
+        }
+        if (x0 + p < W) {
+          const size_t pix = ((size_t)b * H + y) * W + x0 + p;
+          out[pix] = 1.f / (1.f + expf(-acc));
+          if (acts) {
+            uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        w[k] = relu_bf16x2(z[2 * k], z[2 * k + 1]);
-        acc += __uint_as_float(w[k] << 16) * sw4[2 * k] + __uint_as_float(w[k] & 0xFFFF0000u) * sw4[2 * k + 1];
-      }
-      if (x0 + p < W) {
-        const size_t pix = ((size_t)b * H + y) * W + x0 + p;
-        out[pix] = 1.f / (1.f + expf(-acc));
-        if (acts) {
-          uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          }
         }
       }
+      tc_before_sync();
+      wg_sync(g);   // D3 (= D1 columns) read by all before the next row's first MMAs
+      tc_after_sync();
     }
     if (!ok) s_fail[g] = 1u;
-    tc_before_sync();
-    wg_sync(g);   // D3 (= D1 columns) read by all before the next tile's first MMAs
+    wg_sync(g);
     if (s_fail[g]) break;
   }
   if (s_fail[g]) {
@@ -863,10 +905,27 @@ __global__ void mpnet_adam_kernel(uint8_t *__restrict__ weights, float *__restri
 
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s) {
-  const long long ntiles = (long long)batch * H * ((W + kTileW - 1) / kTileW);
-  const long long groups = (ntiles + kGroups - 1) / kGroups;
-  const int grid = (int)(groups < num_sms ? groups : num_sms);
-  if (grid <= 0) return cudaSuccess;
+  if (batch <= 0 || W <= 0 || H <= 0) return cudaSuccess;
+  // units: strips x row segments; the segment length balances the units over
+  // the warpgroups (cost of a unit ~ its output rows + a quarter of its a1
+  // rows, two of which are boundary recomputation)
+  FwdUnits un;
+  un.tiles_x = (W + kTileW - 1) / kTileW;
+  const long long strips = (long long)batch * un.tiles_x;
+  const long long slots = (long long)num_sms * kGroups;
+  double best = 1e300;
+  un.seg_rows = H;
+  for (int S = 4; S <= 64; ++S) {
+    const long long segs = (H + S - 1) / S;
+    const long long rounds = (strips * segs + slots - 1) / slots;
+    const double cost = (double)rounds * (S + 0.25 * (S + 2));
+    if (cost < best - 1e-9) { best = cost; un.seg_rows = S; }
+    if (S >= H) break;
+  }
+  un.segs = (H + un.seg_rows - 1) / un.seg_rows;
+  un.count = strips * un.segs;
+  const long long ctas = (un.count + kGroups - 1) / kGroups;
+  const int grid = (int)(ctas < num_sms ? ctas : num_sms);
   static PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -876,12 +935,12 @@ cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int
     return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }();
   if (!encode) return cudaErrorNotSupported;
-  // the input as a 4-D tensor (channel, x, y, image); box = the 8 x 130 x 3
-  // halo of one tile; out-of-range elements (image borders) read as zero
+  // the input as a 4-D tensor (channel, x, y, image); box = one 130-pixel
+  // halo row; out-of-range elements (image borders) read as zero
   CUtensorMap map;
   const cuuint64_t dims[4] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
   const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
-  const cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, 3, 1};
+  const cuuint32_t box[4] = {8, (cuuint32_t)kHaloW, 1, 1};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<uint16_t *>(feats), dims, strides, box, estr,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -889,8 +948,8 @@ cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int
     return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(mpnet_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem);
   if (e != cudaSuccess) return e;
-  mpnet_fwd_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(map, static_cast<const uint8_t *>(weights), batch, W, H, out,
-                                                       acts, status);
+  mpnet_fwd_kernel<<<grid, kFwdThreads, kFwdSmem, s>>>(map, static_cast<const uint8_t *>(weights), batch, W, H, un,
+                                                       out, acts, status);
   return cudaGetLastError();
 }
 
