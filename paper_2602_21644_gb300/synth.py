@@ -389,3 +389,27 @@ def tracking_scene(n: int = 300_000, frame: int = 10, seed: int = 0, width: int 
     prev = path[frame - 1] if frame > 0 else path[0]
     return Scene(rec, cam, prev[None], tg[None], np.isin(oid, moving),
                  dict(objects=objs, object_id=oid, gt_pose=path[frame], instance=inst, n_instances=len(moving)))
+
+
+# ------------------------------------------------------------------ learned MP network
+
+MPNET_BLOB_BYTES = 22016
+MPNET_PARAMS = 10881
+
+
+def mpnet_init(seed: int = 0):
+    """Seeded He-style initial weights of the per-pixel MP network in the
+    library's layouts: (blob uint8[22016] with BF16 weights and FP32 biases,
+    master float32[10881] parameter vector). Biases start at zero."""
+    rng = np.random.default_rng(seed)
+    W1 = np.zeros((32, 16), np.float32)
+    W1[:, :8] = rng.normal(0, np.sqrt(2.0 / 8), (32, 8))
+    W2 = rng.normal(0, np.sqrt(2.0 / 288), (32, 288)).astype(np.float32)   # column (ky * 3 + kx) * 32 + in
+    W3 = rng.normal(0, np.sqrt(2.0 / 32), (32, 32)).astype(np.float32)
+    w4 = rng.normal(0, np.sqrt(1.0 / 32), 32).astype(np.float32)
+    wb = np.concatenate([f32_to_bf16_bits(a.ravel()) for a in (W1, W2, W3, w4)])
+    blob = np.zeros(MPNET_BLOB_BYTES, np.uint8)
+    blob[:wb.size * 2] = wb.view(np.uint8)
+    master = np.zeros(MPNET_PARAMS, np.float32)
+    master[:wb.size] = bf16_bits_to_f32(wb)
+    return blob, master

@@ -130,7 +130,7 @@ class Runner:
         return hist
 
 
-def train_net(dags, runner, steps=400, lr=3e-3, batch=16, seed=0):
+def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0):
     from oracle import mpnet as N          # initial weights only (a seeded draw)
     hist = runner.run("stale", collect=True)
     feats = torch.stack([h["feats"] for h in hist])                    # [T, H, W, 8]
