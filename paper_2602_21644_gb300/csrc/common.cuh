@@ -143,6 +143,20 @@ cudaError_t launch_mpnet_features(const float *image, const float4 *targets, con
 
 // ---- device helpers ----
 
+// Hardware base-2 exponential and reciprocal (MUFU, flush-to-zero, about
+// 2^-22 relative error). The compositing loops take the exponential only for
+// exponents in [log2(1/255), 0] and the reciprocal of 1 - alpha in [0.01, 1].
+__device__ __forceinline__ float hw_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float hw_rcp(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 

@@ -84,7 +84,9 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   __syncthreads();
   const int kmax = s_max;
 
-  float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f, S4 = 0.f, S5 = 0.f;
+  // Sg = sum over channels of g_ch * S_ch, S_ch the channel's composited sum
+  // behind the current Gaussian: dL/dalpha needs only this contraction
+  float Sg = 0.f;
   const float fpx = (float)px, fpy = (float)py;
   for (int end = kmax; end > 0; end -= kTilePix) {
     const int beg = max(0, end - kTilePix);
@@ -122,17 +124,17 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
           const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
           if (p >= r.log2_alpha_min) {
             contrib = true;
-            const float ag = exp2f(p);
+            const float ag = hw_exp2(p);
             const float alpha = fminf(r.alpha_max, ag);
-            const float inv = 1.f / (1.f - alpha);
+            const float inv = hw_rcp(1.f - alpha);
             T *= inv;                       // transmittance in front of this Gaussian
             const float wk = alpha * T;
             const float4 c = s_c[j];
             const uint32_t rgb = __float_as_uint(c.z), blb = __float_as_uint(c.w);
             const float fr = bf16_lo(rgb), fg = bf16_hi(rgb), fb = bf16_lo(blb);
-            const float dal = g0 * (fr * T - S0 * inv) + g1 * (fg * T - S1 * inv) +
-                              g2 * (fb * T - S2 * inv) + g3 * (c.x * T - S3 * inv) +
-                              g4 * (T - S4 * inv) + g5 * (c.y * T - S5 * inv);
+            // dL/dalpha = sum_ch g_ch (c_ch T - S_ch / (1 - alpha))
+            const float gcv = fmaf(g0, fr, fmaf(g1, fg, fmaf(g2, fb, fmaf(g3, c.x, fmaf(g5, c.y, g4)))));
+            const float dal = fmaf(gcv, T, -Sg * inv);
             gz = g3 * wk;
             if (FULL) { gr = g0 * wk; gg = g1 * wk; gbl = g2 * wk; }
             if (ag <= r.alpha_max) {
@@ -145,10 +147,9 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
               ga = -0.5f * dpw * dx * dx;
               gb = -dpw * dx * dy;
               gc = -0.5f * dpw * dy * dy;
-              if (FULL) go = dal * exp2f(p - b.w);
+              if (FULL) go = dal * hw_exp2(p - b.w);
             }
-            S0 += fr * wk; S1 += fg * wk; S2 += fb * wk;
-            S3 += c.x * wk; S4 += wk; S5 += c.y * wk;
+            Sg = fmaf(gcv, wk, Sg);
           }
         }
         if (__any_sync(FULLM, contrib)) {

@@ -454,7 +454,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
         const float dx = a.x - fpx, dy = a.y - fpy;
         const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
         if (p < r.log2_alpha_min) continue;               // alpha < alpha_min
-        const float alpha = fminf(r.alpha_max, exp2f(p));
+        const float alpha = fminf(r.alpha_max, hw_exp2(p));
         const float tt = T * (1.f - alpha);
         if (tt < r.t_min) { done = true; continue; }
         const float w = alpha * T;
