@@ -376,7 +376,8 @@ def run_ours(args):
             kernels[name]["evaluations"] = E
             kernels[name]["alu_tops"] = round(E * ops / t_s / 1e12, 3)
             kernels[name]["alu_frac"] = round(E * ops / t_s / 1e12 / alu_peak, 4)
-    dom = max(kernels, key=lambda k: kt[k][0]) if kernels else None
+    modelled = [k for k in kernels if k in ab]
+    dom = max(modelled, key=lambda k: kt[k][0]) if modelled else None
     roof = None
     if dom in ("render_fwd", "render_bwd"):
         ops = OPS_FWD if dom == "render_fwd" else OPS_BWD

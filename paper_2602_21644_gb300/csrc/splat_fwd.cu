@@ -62,10 +62,16 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
   // pass 1: length bins
   for (int c0 = 0; c0 < total; c0 += kScanChunk) {
     const int n = min(kScanChunk, total - c0);
-    for (int k = tid; k < n; k += blockDim.x) {
-      const uint32_t c = __ldcg(count + c0 + k);
-      s_c[k] = c;
-      atomicAdd(&s_bin[length_bin(c)], 1u);
+    for (int k0 = 0; k0 < n; k0 += blockDim.x) {
+      const int k = k0 + tid;
+      int bin = 64 + lane;   // no element: a key of its own
+      if (k < n) {
+        const uint32_t c = __ldcg(count + c0 + k);
+        s_c[k] = c;
+        bin = length_bin(c);
+      }
+      const unsigned grp = __match_any_sync(0xffffffffu, bin);
+      if (bin < 64 && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
     }
     __syncthreads();
   }
@@ -105,11 +111,22 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
     }
     __syncthreads();
     unsigned long long run = s_carry + (wid > 0 ? warp_tot[wid - 1] : 0ull) + inc - mine;
-    for (int k = b; k < e; ++k) {
-      const uint32_t c = s_c[k];
-      start[c0 + k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
-      run += c;
-      order[atomicAdd(&s_bin[length_bin(c)], 1u)] = (uint32_t)(c0 + k);
+    for (int j = 0; j < per; ++j) {
+      const int k = b + j;
+      int bin = 64 + lane;   // no element: a key of its own
+      if (k < e) {
+        const uint32_t c = s_c[k];
+        start[c0 + k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
+        run += c;
+        bin = length_bin(c);
+      }
+      // slot in the launch order: one shared atomic per distinct bin per warp
+      const unsigned grp = __match_any_sync(0xffffffffu, bin);
+      const int leader = __ffs(grp) - 1;
+      uint32_t slot = 0;
+      if (bin < 64 && lane == leader) slot = atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+      slot = __shfl_sync(0xffffffffu, slot, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+      if (k < e) order[slot] = (uint32_t)(c0 + k);
     }
     for (int k = tid; k < n; k += blockDim.x) {
       count[c0 + k] = 0u;
@@ -180,13 +197,16 @@ __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r,
     if (!EMIT) {
       if (keep && lane == leader) atomicAdd(ws.tile_count + key, (uint32_t)__popc(grp));
     } else {
+      // the bucket bounds are loaded before the cursor atomic so that the
+      // two round trips overlap
+      uint32_t t0 = 0, t1 = 0;
+      if (keep) { t0 = ws.tile_start[key]; t1 = ws.tile_start[key + 1]; }
       uint32_t basepos = 0;
       if (keep && lane == leader) basepos = atomicAdd(ws.tile_cursor + key, (uint32_t)__popc(grp));
       basepos = __shfl_sync(FULL, basepos, leader);
       if (keep) {
-        const uint32_t dst = ws.tile_start[key] + basepos + (uint32_t)__popc(grp & ((1u << lane) - 1u));
-        if (dst < ws.tile_start[key + 1])
-          ws.keys[dst] = ((uint64_t)__float_as_uint(o_z) << 32) | (uint64_t)o_id;
+        const uint32_t dst = t0 + basepos + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+        if (dst < t1) ws.keys[dst] = ((uint64_t)__float_as_uint(o_z) << 32) | (uint64_t)o_id;
       }
     }
   }
@@ -196,7 +216,6 @@ __global__ void __launch_bounds__(kPrepBlock)
 preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
   __shared__ float sp[kMaxViewsSmem * 12];
-  __shared__ int s_last;
   for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = (float)poses[k];
   __syncthreads();
   if (blockIdx.x == 0 && blockIdx.y == 0)
@@ -263,21 +282,17 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   // Warp-cooperative walk over the candidate tiles of the warp's Gaussians.
   walk_tiles<false>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, 0.f);
 
-  // The last CTA to finish turns the per-tile counts into offsets (CTA
-  // barrier, then one thread's fence and counter increment publish the
-  // whole CTA's atomics).
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
-    s_last = (t == gridDim.x * gridDim.y - 1);
-    if (s_last) __threadfence();
-  }
-  __syncthreads();
-  if (!s_last) return;
+}
+
+// One CTA turns the per-tile counts into offsets and the launch order, and
+// publishes the visible-list lengths and the pair total.
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads)
+tile_scan_kernel(Workspace ws, int views, Raster r) {
   const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T, ws.tile_order);
   for (int k = threadIdx.x; k < views; k += blockDim.x) {
-    ws.vis_n[k] = __ldcg(ws.vis_append + k);
+    ws.vis_n[k] = ws.vis_append[k];
     ws.vis_append[k] = 0u;
   }
   if (threadIdx.x == 0) {
@@ -285,7 +300,6 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     ws.counters[CNT_REQ_LO] = (uint32_t)total;
     ws.counters[CNT_REQ_HI] = (uint32_t)(total >> 32);
     if (total > (uint64_t)ws.max_pairs) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
-    ws.counters[CNT_DONE_PREP] = 0u;
   }
 }
 
@@ -299,23 +313,27 @@ __global__ void __launch_bounds__(kPrepBlock)
 emit_kernel(Workspace ws, int64_t n, Raster r) {
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pairs_overflow(ws, 0)) return;
+  // the pair total, the list length and this thread's list entry are loaded
+  // together (the entry speculatively: i < n <= max_n is always in the
+  // buffer; a stale value is clamped to a valid slot and discarded below)
+  const uint32_t req_lo = ws.counters[CNT_REQ_LO], req_hi = ws.counters[CNT_REQ_HI];
   const int64_t nv = ws.vis_n[v];
+  uint32_t id = i < n ? ws.vis_ids[(size_t)v * ws.max_n + i] : 0u;
+  if ((((uint64_t)req_hi << 32) | req_lo) > (uint64_t)ws.max_pairs) return;
   if ((int64_t)blockIdx.x * blockDim.x >= nv) return;   // whole CTA past the visible list
   uint2 rect = make_uint2(0u, 0u);
   float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
   float z = 0.f;
-  uint32_t id = 0;
   if (i < nv) {
-    id = ws.vis_ids[(size_t)v * ws.max_n + i];
-    const size_t slot = (size_t)v * ws.max_n + id;
+    const size_t slot = (size_t)v * ws.max_n + min(id, (uint32_t)(n - 1));
     rect = ws.rect[slot];
     r0 = ws.rec2d[slot * 3 + 0];
     r1 = ws.rec2d[slot * 3 + 1];
     z = ws.rec2d[slot * 3 + 2].x;
+  } else {
+    id = 0;
   }
   walk_tiles<true>(ws, r, v, id, rect, r0, r1, z);
-  (void)n;
 }
 
 // Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
@@ -528,6 +546,7 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
   dim3 grid(gx > 0 ? gx : 1u, (unsigned)views);
   preprocess_kernel<<<grid, kPrepBlock, 0, s>>>(ws, gauss, n, poses, views, r, zero_grad_words);
+  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(ws, views, r);
   return cudaGetLastError();
 }
 
