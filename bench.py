@@ -176,6 +176,9 @@ def algorithmic_bytes(n, nv, K, P):
 # accumulations; backward alpha and T recovery, dL/dalpha over six channels,
 # suffix sums and the chain to the conic, mean, opacity, colour, depth, MP
 OPS_FWD, OPS_BWD = 16, 41
+# DRAM bytes (read + write) per launch at this workload from one ncu capture
+# of the current kernels (profiles/tracking_frame_300k_640x480.md)
+DRAM_TRAFFIC = {"render_fwd": 10438912 + 15616, "render_bwd": 19878144}
 ALU_LANES = 152 * 128          # FP32 lanes: 152 SMs x 128
 MPNET_FLOP_PER_PX = 2 * (8 * 32 + 288 * 32 + 32 * 32 + 32)   # 21,056: the network's multiply-adds x 2
 
@@ -383,7 +386,9 @@ def run_ours(args):
         ops = OPS_FWD if dom == "render_fwd" else OPS_BWD
         ach = kernels[dom]["alu_tops"]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / alu_peak, 4), "traffic": None,
+                "frac": round(ach / alu_peak, 4),
+                "traffic": DRAM_TRAFFIC.get(dom) if (args.width, args.height, args.gaussians) == (640, 480, 300_000)
+                else None,
                 "peak_source": f"derived: {ALU_LANES} FP32 lanes x {src} sm_max_mhz",
                 "alg_ops_per_launch": E * ops, "ops_per_evaluation": ops, "evaluations_per_launch": E,
                 "hbm_frac": kernels[dom].get("hbm_frac")}
