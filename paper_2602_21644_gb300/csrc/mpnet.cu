@@ -502,16 +502,44 @@ __global__ void mpnet_count_finish_kernel(float *inv_n) {
   inv_n[0] = c ? 1.f / (float)c : 0.f;
 }
 
-// bwd1 smem layout
-constexpr int kB1W3T = 0;                         // [32 i][32 o] = W3[o][i]
-constexpr int kB1Adz3 = kB1W3T + 2048;            // [128 px][32 o]
-constexpr int kB1Pdz3 = kB1Adz3 + 8192;           // planar [32 o][128 px]
-constexpr int kB1Pdz4 = kB1Pdz3 + 8192;           // planar [16][128 px], row 0 = dz4
-constexpr int kB1Pa2 = kB1Pdz4 + 4096;            // planar [128 rows][128 px]: a2 rows 0-31, ones row 32
-constexpr int kB1Pa3 = kB1Pa2 + 32768;            // planar [128][128]: a3 rows 0-31, ones row 32
-constexpr int kB1Par = kB1Pa3 + 32768;            // w4 f32 [32]
+// Backward operand layouts. All activations and gradients are staged as
+// row-contiguous chunks (chunk c = channels 8c..8c+7 of every pixel as one
+// 16-byte line, pixels consecutive), straight from their pixel-major (NHWC)
+// form with 16-byte copies. The same buffer is read two ways:
+//   K-major, M = pixels, K = channels: SBO = 128 B (8 pixels), LBO = chunk
+//     stride (the next 8 channels) - the data GEMMs (da2, the transposed
+//     convolution for da1, with shifted start rows as in the forward);
+//   MN-major, MN = channels, K = pixels (instruction-descriptor bits 15/16):
+//     SBO = chunk stride (the next 8 channels), LBO = 128 B (the next 8
+//     pixels) - the weight-gradient GEMMs, which reduce over pixels.
+// Weight-gradient MMAs are M = 128 over 32 (+1) real channel rows: the rows
+// past them read whatever follows in shared memory (in bounds), and their D
+// rows are never read. A chunk of (1, 0, ..., 0) after the real channels
+// gives the bias gradient in D row 32.
+
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+  return idesc_bf16(M, N) | (1u << 15) | (1u << 16);   // A and B MN-major
+}
+
+constexpr int kChunkPx = kTileW * 16;                    // 2048: one chunk of a 128-pixel tile
+
+// bwd1 shared memory: a2 and a3 (5 chunks each: 4 real + ones, then 11 more
+// readable chunks for the M = 128 MMA), dz3 (4 chunks), dz4 (2 chunks), W3^T
+constexpr int kB1A2 = 0;
+constexpr int kB1A3 = kB1A2 + 5 * kChunkPx;
+constexpr int kB1Dz3 = kB1A3 + 5 * kChunkPx;
+constexpr int kB1Dz4 = kB1Dz3 + 4 * kChunkPx;
+constexpr int kB1W3T = kB1Dz4 + 2 * kChunkPx;
+constexpr int kB1Par = kB1W3T + 2048;
 constexpr int kB1Bar = kB1Par + 128;
-constexpr int kB1Smem = kB1Bar + 64;
+constexpr int kB1Span = 16 * kChunkPx;                    // the farthest MN-major read from kB1A3
+constexpr int kB1Smem = (kB1A3 + kB1Span > kB1Bar + 64 ? kB1A3 + kB1Span : kB1Bar + 64);
+
+__device__ __forceinline__ void st_chunks(uint8_t *base, int stride, int row, const uint32_t *w) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    *reinterpret_cast<uint4 *>(base + c * stride + row * 16) = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+}
 
 __global__ void __launch_bounds__(kNetThreads, 1)
 mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__ y, const float *__restrict__ target,
@@ -519,36 +547,34 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
                   uint16_t *__restrict__ dz2_out, float *__restrict__ grad, double *__restrict__ loss,
                   uint32_t *__restrict__ status) {
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *sW3T = smem + kB1W3T, *sAdz3 = smem + kB1Adz3, *sPdz3 = smem + kB1Pdz3, *sPdz4 = smem + kB1Pdz4;
-  uint8_t *sPa2 = smem + kB1Pa2, *sPa3 = smem + kB1Pa3;
+  uint8_t *sA2 = smem + kB1A2, *sA3 = smem + kB1A3, *sDz3 = smem + kB1Dz3, *sDz4 = smem + kB1Dz4;
+  uint8_t *sW3T = smem + kB1W3T;
   float *sw4 = reinterpret_cast<float *>(smem + kB1Par);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kB1Bar);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kB1Bar + 8);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint16_t *gw3 = reinterpret_cast<const uint16_t *>(weights + kOffW3);
+  // everything starts at zero (the M = 128 reads past the real rows see finite
+  // values); the ones chunks; W3^T in the K-major core-matrix layout
+  for (int e = tid; e < kB1Smem / 16; e += kNetThreads) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
   for (int e = tid; e < 32 * 32; e += kNetThreads) {
     const int o = e / 32, i = e % 32;
     *reinterpret_cast<uint16_t *>(sW3T + core_off(i, o, 32)) = gw3[e];
   }
+  *reinterpret_cast<uint4 *>(sA2 + 4 * kChunkPx + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4 *>(sA3 + 4 * kChunkPx + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
   if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
-  // static parts: zero the planar operands, ones rows, dz4 rows 1-15
-  for (int e = tid; e < (32768 * 2 + 4096) / 16; e += kNetThreads)
-    reinterpret_cast<uint4 *>(sPdz4)[e] = make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
-  {
-    const uint16_t one = 0x3F80;   // bf16 1.0
-    *reinterpret_cast<uint16_t *>(sPa2 + planar_off(32, tid)) = one;
-    *reinterpret_cast<uint16_t *>(sPa3 + planar_off(32, tid)) = one;
-  }
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)), "r"(128));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  fence_async_smem();
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  const uint32_t tmem = *s_tmem;   // D: dW3^T cols 0-31, da2 cols 32-63, dw4 cols 64-79
+  const uint32_t tmem = *s_tmem;   // D: da2 cols 0-31, dW3^T cols 32-63, dw4 cols 64-79
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
   uint32_t phase = 0;
   bool ok = true, first = true;
@@ -581,39 +607,33 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
 #pragma unroll
       for (int k = 0; k < 16; ++k) { a2w[k] = 0u; a3w[k] = 0u; }
     }
-    // dz3 = dz4 w4 [a3 > 0]; operands for da2 (pixel-major dz3), dW3^T and dw4 (planar)
+    // dz3 = dz4 w4 [a3 > 0]
     uint32_t dzw[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
       const float a3lo = __uint_as_float(a3w[k] << 16), a3hi = __uint_as_float(a3w[k] & 0xFFFF0000u);
-      const float d0 = a3lo > 0.f ? dz4 * sw4[2 * k] : 0.f, d1 = a3hi > 0.f ? dz4 * sw4[2 * k + 1] : 0.f;
-      dzw[k] = pack_bf16x2(d0, d1);
+      dzw[k] = pack_bf16x2(a3lo > 0.f ? dz4 * sw4[2 * k] : 0.f, a3hi > 0.f ? dz4 * sw4[2 * k + 1] : 0.f);
     }
-    store_row32(sAdz3, p, 0, 32, dzw);
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      *reinterpret_cast<uint16_t *>(sPdz3 + planar_off(2 * k, p)) = (uint16_t)(dzw[k] & 0xFFFFu);
-      *reinterpret_cast<uint16_t *>(sPdz3 + planar_off(2 * k + 1, p)) = (uint16_t)(dzw[k] >> 16);
-      *reinterpret_cast<uint16_t *>(sPa2 + planar_off(2 * k, p)) = (uint16_t)(a2w[k] & 0xFFFFu);
-      *reinterpret_cast<uint16_t *>(sPa2 + planar_off(2 * k + 1, p)) = (uint16_t)(a2w[k] >> 16);
-      *reinterpret_cast<uint16_t *>(sPa3 + planar_off(2 * k, p)) = (uint16_t)(a3w[k] & 0xFFFFu);
-      *reinterpret_cast<uint16_t *>(sPa3 + planar_off(2 * k + 1, p)) = (uint16_t)(a3w[k] >> 16);
-    }
-    *reinterpret_cast<uint16_t *>(sPdz4 + planar_off(0, p)) = __bfloat16_as_ushort(__float2bfloat16_rn(dz4));
+    st_chunks(sA2, kChunkPx, p, a2w);
+    st_chunks(sA3, kChunkPx, p, a3w);
+    st_chunks(sDz3, kChunkPx, p, dzw);
+    *reinterpret_cast<uint4 *>(sDz4 + p * 16) = make_uint4(__bfloat16_as_ushort(__float2bfloat16_rn(dz4)), 0u, 0u, 0u);
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     if (tid == 0) {
+      // da2 = dz3 W3 (M = pixels, K = o)
       for (int c = 0; c < 2; ++c)
-        mma_bf16(tmem + 32, sdesc(smem_u32(sAdz3) + c * 256, 128, 512), sdesc(smem_u32(sW3T) + c * 256, 128, 512),
-                 idesc_bf16(128, 32), c > 0 ? 1u : 0u);
-      for (int c = 0; c < kTileW / 16; ++c) {
-        const uint32_t acc = (!first || c > 0) ? 1u : 0u;
-        mma_bf16(tmem + 0, sdesc(smem_u32(sPa2) + c * 256, 128, 2048), sdesc(smem_u32(sPdz3) + c * 256, 128, 2048),
-                 idesc_bf16(128, 32), acc);
-        mma_bf16(tmem + 64, sdesc(smem_u32(sPa3) + c * 256, 128, 2048), sdesc(smem_u32(sPdz4) + c * 256, 128, 2048),
-                 idesc_bf16(128, 16), acc);
+        mma_bf16(tmem + 0, sdesc(smem_u32(sDz3) + 2 * c * kChunkPx, kChunkPx, 128),
+                 sdesc(smem_u32(sW3T) + c * 256, 128, 512), idesc_bf16(128, 32), c > 0 ? 1u : 0u);
+      // dW3^T (M = i, N = o) and dw4 (M = i, N = 16) over the tile's pixels
+      for (int s = 0; s < kTileW / 16; ++s) {
+        const uint32_t acc = (!first || s > 0) ? 1u : 0u;
+        mma_bf16(tmem + 32, sdesc(smem_u32(sA2) + s * 256, 128, kChunkPx),
+                 sdesc(smem_u32(sDz3) + s * 256, 128, kChunkPx), idesc_bf16_mn(128, 32), acc);
+        mma_bf16(tmem + 64, sdesc(smem_u32(sA3) + s * 256, 128, kChunkPx),
+                 sdesc(smem_u32(sDz4) + s * 256, 128, kChunkPx), idesc_bf16_mn(128, 16), acc);
       }
       mma_commit(bar);
     }
@@ -624,7 +644,7 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
     // dz2 = (dz3 W3) [a2 > 0] -> global (bf16) for the second backward kernel
     {
       float da[32];
-      tmem_ld32(tmem + lane_base + 32, da);
+      tmem_ld32(tmem + lane_base + 0, da);
       if (in) {
         uint32_t w[16];
 #pragma unroll
@@ -649,7 +669,7 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
   if (!first) {
     tc_after_sync();
     float d[32];
-    tmem_ld32(tmem + lane_base + 0, d);
+    tmem_ld32(tmem + lane_base + 32, d);
     const int r = tid;
     if (r < 32) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW3 + o * 32 + r, d[o]);
@@ -667,48 +687,49 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
-// bwd2 smem layout
-constexpr int kB2W2t = 0;                          // [32 i][288 (tap, o)] = W2[o][tap * 32 + i]
-constexpr int kB2Px = kB2W2t + 18432;              // planar x: rows 0-15 channels, row 16 ones (6 KB)
-constexpr int kB2R = kB2Px + 6144;                 // im2col(dz2) [128 x 288] / planar im2col(a1) [296 rows]
-constexpr int kB2Halo = kB2R + 37 * 2048;          // halo rows of 64 B (390)
-constexpr int kB2Pdz2 = kB2Halo + 24960;           // planar dz2 [32 o][128 px]
-constexpr int kB2Pdz1 = kB2Pdz2 + 8192;            // planar dz1 [32 o][128 px]
-constexpr int kB2Bar = kB2Pdz1 + 8192;
-constexpr int kB2Smem = kB2Bar + 64;
+// bwd2 shared memory: dz2 and a1 halos (3 rows x 130 pixels; 4 chunks + the
+// a1 ones chunk, then readable space for the M = 128 MN-major reads), x and
+// its ones chunk, dz1, W2 rearranged as B[i][(tap, o)]
+constexpr int kHaloChunk = 392 * 16;                     // 6272
+constexpr int kB2A1 = 0;                                 // a1 halo: 5 chunks (+ 11 readable)
+constexpr int kB2Dz2 = kB2A1 + 5 * kHaloChunk;           // dz2 halo: 4 chunks
+constexpr int kB2X = kB2Dz2 + 4 * kHaloChunk;            // x: chunk 0, ones chunk 1 (+ 14 readable)
+constexpr int kB2Dz1 = kB2X + 2 * kChunkPx;              // dz1: 4 chunks
+constexpr int kB2W2t = kB2Dz1 + 4 * kChunkPx;            // [32 i][288 (tap, o)]
+constexpr int kB2Bar = kB2W2t + 32 * kK2 * 2;
+constexpr int kB2End = kB2Bar + 64;
+constexpr int kB2Smem = (kB2A1 + 16 * kHaloChunk > kB2End ? kB2A1 + 16 * kHaloChunk : kB2End);
+static_assert(kB2X + 16 * kChunkPx <= kB2Smem, "MN-major reads of x stay in shared memory");
 
 __global__ void __launch_bounds__(kNetThreads, 1)
 mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ feats, const uint16_t *__restrict__ acts,
                   const uint16_t *__restrict__ dz2, int batch, int W, int H, float *__restrict__ grad,
                   uint32_t *__restrict__ status) {
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *sW2t = smem + kB2W2t, *sPx = smem + kB2Px, *sR = smem + kB2R, *sHalo = smem + kB2Halo;
-  uint8_t *sPdz2 = smem + kB2Pdz2, *sPdz1 = smem + kB2Pdz1;
+  uint8_t *sA1 = smem + kB2A1, *sDz2 = smem + kB2Dz2, *sX = smem + kB2X, *sDz1 = smem + kB2Dz1, *sW2t = smem + kB2W2t;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kB2Bar);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kB2Bar + 8);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int e = tid; e < kB2Smem / 16; e += kNetThreads) reinterpret_cast<uint4 *>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
   const uint16_t *gw2 = reinterpret_cast<const uint16_t *>(weights + kOffW2);
   for (int e = tid; e < 32 * kK2; e += kNetThreads) {
     const int o = e / kK2, col = e % kK2, tap = col / 32, i = col % 32;
     *reinterpret_cast<uint16_t *>(sW2t + core_off(i, tap * 32 + o, kK2)) = gw2[e];
   }
-  // planar x: channels 8-15 zero, row 16 ones, rows 17-23 zero; planar
-  // im2col(a1) rows 288 (ones) to 295 (zero) lie past the im2col(dz2) area
-  for (int e = tid; e < 6144 / 16; e += kNetThreads) reinterpret_cast<uint4 *>(sPx)[e] = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = tid; e < 2048 / 16; e += kNetThreads)
-    reinterpret_cast<uint4 *>(sR + 36 * 2048)[e] = make_uint4(0u, 0u, 0u, 0u);
-  __syncthreads();
-  *reinterpret_cast<uint16_t *>(sPx + planar_off(16, tid)) = 0x3F80;
-  *reinterpret_cast<uint16_t *>(sR + planar_off(288, tid)) = 0x3F80;
+  for (int h = tid; h < 392; h += kNetThreads)
+    *reinterpret_cast<uint4 *>(sA1 + 4 * kHaloChunk + h * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+  *reinterpret_cast<uint4 *>(sX + kChunkPx + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)), "r"(256));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)), "r"(512));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  fence_async_smem();
   tc_before_sync();
   __syncthreads();
   tc_after_sync();
-  // D: da1 cols 0-31; dW2^T blocks (A rows 0, 128, 168) cols 32-127; dW1^T cols 128-159
+  // D: da1 cols 0-31; dW2^T of tap t cols 32 + 32 t (t = 0..8, to 319); dW1^T cols 320-351
   const uint32_t tmem = *s_tmem;
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
   uint32_t phase = 0;
@@ -718,126 +739,81 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
   for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const int tx = (int)(t % tiles_x), y = (int)((t / tiles_x) % H), b = (int)(t / ((long long)tiles_x * H));
     const int x0 = tx * kTileW, p = tid, x = x0 + p;
-    // 1. dz2 halo (zero outside the image)
+    // 1. dz2 and a1 halos (zero outside the image), x of the centre row
     for (int h = tid; h < kHaloRows; h += kNetThreads) {
       const int r = h / kHaloW, c = h % kHaloW, yy = y - 1 + r, xx = x0 - 1 + c;
-      uint4 *dst = reinterpret_cast<uint4 *>(sHalo + (size_t)h * 64);
+      uint4 d[4], a[4];
       if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(dz2 + (((size_t)b * H + yy) * W + xx) * 32);
+        const size_t q = ((size_t)b * H + yy) * W + xx;
+        const uint4 *sd = reinterpret_cast<const uint4 *>(dz2 + q * 32);
+        const uint4 *sa = reinterpret_cast<const uint4 *>(acts + q * 96);
 #pragma unroll
-        for (int g = 0; g < 4; ++g) dst[g] = src[g];
+        for (int g = 0; g < 4; ++g) { d[g] = sd[g]; a[g] = sa[g]; }
       } else {
 #pragma unroll
-        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(0u, 0u, 0u, 0u);
+        for (int g = 0; g < 4; ++g) { d[g] = make_uint4(0u, 0u, 0u, 0u); a[g] = d[g]; }
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        *reinterpret_cast<uint4 *>(sDz2 + g * kHaloChunk + h * 16) = d[g];
+        *reinterpret_cast<uint4 *>(sA1 + g * kHaloChunk + h * 16) = a[g];
       }
     }
-    __syncthreads();
-    // 2. im2col of dz2 for the transposed convolution: row q, column
-    // (tap, o) = dz2 at pixel q - offset(tap) = halo (2 - ky, q + 2 - kx)
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap % 3;
-      const uint4 *src = reinterpret_cast<const uint4 *>(sHalo + (size_t)((2 - ky) * kHaloW + p + 2 - kx) * 64);
-#pragma unroll
-      for (int g = 0; g < 4; ++g) *reinterpret_cast<uint4 *>(sR + core_off(p, tap * 32 + 8 * g, kK2)) = src[g];
-    }
-    // planar dz2 of the tile's own pixels (halo row 1) and planar x
-    {
-      const uint32_t *own = reinterpret_cast<const uint32_t *>(sHalo + (size_t)(kHaloW + p + 1) * 64);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const uint32_t w = own[k];
-        *reinterpret_cast<uint16_t *>(sPdz2 + planar_off(2 * k, p)) = (uint16_t)(w & 0xFFFFu);
-        *reinterpret_cast<uint16_t *>(sPdz2 + planar_off(2 * k + 1, p)) = (uint16_t)(w >> 16);
-      }
-      uint4 xv = make_uint4(0u, 0u, 0u, 0u);
-      if (x < W) xv = __ldg(feats + ((size_t)b * H + y) * W + x);
-      const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        *reinterpret_cast<uint16_t *>(sPx + planar_off(2 * k, p)) = (uint16_t)(xw[k] & 0xFFFFu);
-        *reinterpret_cast<uint16_t *>(sPx + planar_off(2 * k + 1, p)) = (uint16_t)(xw[k] >> 16);
-      }
-    }
+    *reinterpret_cast<uint4 *>(sX + p * 16) = x < W ? __ldg(feats + ((size_t)b * H + y) * W + x) : make_uint4(0u, 0u, 0u, 0u);
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
+    // 2. da1: the transposed 3 x 3 convolution as an implicit GEMM - tap
+    //    (ky, kx) reads dz2 at halo row (2 - ky) * 130 + (2 - kx) + q
     if (tid == 0) {
-      for (int c = 0; c < kK2 / 16; ++c)
-        mma_bf16(tmem + 0, sdesc(smem_u32(sR) + c * 256, 128, (kK2 / 8) * 128),
-                 sdesc(smem_u32(sW2t) + c * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32), c > 0 ? 1u : 0u);
+      for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        for (int j = 0; j < 2; ++j)
+          mma_bf16(tmem + 0, sdesc(smem_u32(sDz2) + 2 * j * kHaloChunk + ((2 - ky) * kHaloW + (2 - kx)) * 16, kHaloChunk, 128),
+                   sdesc(smem_u32(sW2t) + (2 * tap + j) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
+                   (tap | j) ? 1u : 0u);
+      }
       mma_commit(bar);
     }
     ok = bar_wait(bar, phase);
     phase ^= 1u;
     tc_after_sync();
-    // 3. dz1 = da1 [a1 > 0] -> planar dz1
+    // 3. dz1 = da1 [a1 > 0] (a1 of the centre row: halo row 131 + q)
     {
       float da[32];
       tmem_ld32(tmem + lane_base + 0, da);
-      uint32_t a1w[16];
-      if (x < W) {
-        const uint4 *ga = reinterpret_cast<const uint4 *>(acts + (((size_t)b * H + y) * W + x) * 96);
+      uint32_t a1w[16], w[16];
 #pragma unroll
-        for (int g = 0; g < 4; ++g) {
-          const uint4 u = ga[g];
-          a1w[4 * g] = u.x; a1w[4 * g + 1] = u.y; a1w[4 * g + 2] = u.z; a1w[4 * g + 3] = u.w;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) a1w[k] = 0u;
+      for (int g = 0; g < 4; ++g) {
+        const uint4 u = *reinterpret_cast<const uint4 *>(sA1 + g * kHaloChunk + (kHaloW + 1 + p) * 16);
+        a1w[4 * g] = u.x; a1w[4 * g + 1] = u.y; a1w[4 * g + 2] = u.z; a1w[4 * g + 3] = u.w;
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const float lo = __uint_as_float(a1w[k] << 16), hi = __uint_as_float(a1w[k] & 0xFFFF0000u);
-        *reinterpret_cast<uint16_t *>(sPdz1 + planar_off(2 * k, p)) =
-            __bfloat16_as_ushort(__float2bfloat16_rn(lo > 0.f ? da[2 * k] : 0.f));
-        *reinterpret_cast<uint16_t *>(sPdz1 + planar_off(2 * k + 1, p)) =
-            __bfloat16_as_ushort(__float2bfloat16_rn(hi > 0.f ? da[2 * k + 1] : 0.f));
+        w[k] = pack_bf16x2(lo > 0.f ? da[2 * k] : 0.f, hi > 0.f ? da[2 * k + 1] : 0.f);
       }
-    }
-    tc_before_sync();
-    __syncthreads();
-    // 4. a1 halo (zero outside the image) -> planar im2col(a1): row
-    // tap * 32 + i, column q = a1 at halo (ky, q + kx)
-    for (int h = tid; h < kHaloRows; h += kNetThreads) {
-      const int r = h / kHaloW, c = h % kHaloW, yy = y - 1 + r, xx = x0 - 1 + c;
-      uint4 *dst = reinterpret_cast<uint4 *>(sHalo + (size_t)h * 64);
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(acts + (((size_t)b * H + yy) * W + xx) * 96);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) dst[g] = src[g];
-      } else {
-#pragma unroll
-        for (int g = 0; g < 4; ++g) dst[g] = make_uint4(0u, 0u, 0u, 0u);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int ky = tap / 3, kx = tap % 3;
-      const uint32_t *src = reinterpret_cast<const uint32_t *>(sHalo + (size_t)(ky * kHaloW + p + kx) * 64);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const uint32_t w = src[k];
-        *reinterpret_cast<uint16_t *>(sR + planar_off(tap * 32 + 2 * k, p)) = (uint16_t)(w & 0xFFFFu);
-        *reinterpret_cast<uint16_t *>(sR + planar_off(tap * 32 + 2 * k + 1, p)) = (uint16_t)(w >> 16);
-      }
+      st_chunks(sDz1, kChunkPx, p, w);
     }
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
+    // 4. weight gradients over the tile's 128 pixels (MN-major operands):
+    //    dW2^T per tap: a1 at halo row ky * 130 + kx + q against dz2 of the
+    //    centre row (halo row 131 + q); dW1^T: x against dz1
     if (tid == 0) {
-      const int mrow[3] = {0, 128, 168};
-      for (int c = 0; c < kTileW / 16; ++c) {
-        const uint32_t acc = (!first || c > 0) ? 1u : 0u;
-        for (int mb = 0; mb < 3; ++mb)
-          mma_bf16(tmem + 32 + 32 * mb, sdesc(smem_u32(sR) + (mrow[mb] / 8) * 2048 + c * 256, 128, 2048),
-                   sdesc(smem_u32(sPdz2) + c * 256, 128, 2048), idesc_bf16(128, 32), acc);
-        mma_bf16(tmem + 128, sdesc(smem_u32(sPx) + c * 256, 128, 2048), sdesc(smem_u32(sPdz1) + c * 256, 128, 2048),
-                 idesc_bf16(128, 32), acc);
+      for (int s = 0; s < kTileW / 16; ++s) {
+        const uint32_t acc = (!first || s > 0) ? 1u : 0u;
+        const uint32_t bdz2 = smem_u32(sDz2) + (kHaloW + 1) * 16 + s * 256;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap % 3;
+          mma_bf16(tmem + 32 + 32 * tap, sdesc(smem_u32(sA1) + (ky * kHaloW + kx) * 16 + s * 256, 128, kHaloChunk),
+                   sdesc(bdz2, 128, kHaloChunk), idesc_bf16_mn(128, 32), acc);
+        }
+        mma_bf16(tmem + 320, sdesc(smem_u32(sX) + s * 256, 128, kChunkPx),
+                 sdesc(smem_u32(sDz1) + s * 256, 128, kChunkPx), idesc_bf16_mn(128, 32), acc);
       }
       mma_commit(bar);
     }
@@ -856,26 +832,24 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
     tc_after_sync();
     float d[32];
     const int r = tid;
-    for (int mb = 0; mb < 3; ++mb) {
-      tmem_ld32(tmem + lane_base + 32 + 32 * mb, d);
-      const int row = (mb == 0 ? 0 : (mb == 1 ? 128 : 168)) + r;
-      const bool take = mb < 2 || row >= 256;        // block 2 repeats rows 168-255 of block 1
-      if (take && row < 288) {
-        for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW2 + o * 288 + row, d[o]);
-      } else if (take && row == 288) {
+    for (int tap = 0; tap < 9; ++tap) {
+      tmem_ld32(tmem + lane_base + 32 + 32 * tap, d);
+      if (r < 32) {
+        for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW2 + o * 288 + tap * 32 + r, d[o]);
+      } else if (r == 32 && tap == 0) {
         for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb2 + o, d[o]);
       }
     }
-    tmem_ld32(tmem + lane_base + 128, d);
-    if (r < 16) {
+    tmem_ld32(tmem + lane_base + 320, d);
+    if (r < 8) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW1 + o * 16 + r, d[o]);
-    } else if (r == 16) {
+    } else if (r == 8) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb1 + o, d[o]);
     }
   }
   tc_before_sync();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
 // Adam on the FP32 master parameters (gradient layout), refreshing the BF16
