@@ -34,7 +34,6 @@ constexpr int kNetThreads = 128;          // 4 warps = one warpgroup over the 12
 constexpr int kTileW = 128;               // pixels per tile (MMA M)
 constexpr int kHaloW = kTileW + 2;        // 130
 constexpr int kHaloRows = 3 * kHaloW;     // 390
-constexpr int kHaloPad = 512;             // rows of the first operand (4 M-blocks)
 constexpr int kCh = 32;
 constexpr int kK2 = 9 * kCh;              // 288
 constexpr long long kSpinLimit = 1ll << 22;
@@ -117,16 +116,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__device__ __forceinline__ float bf16_round_f(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// Writes 32 bf16 (as 16 packed words) into row `row` of a K-major operand
-// with K columns, at column offset k0 (multiple of 8).
-__device__ __forceinline__ void store_row32(uint8_t *base, int row, int k0, int K, const uint32_t *w) {
-#pragma unroll
-  for (int g = 0; g < 4; ++g)
-    *reinterpret_cast<uint4 *>(base + core_off(row, k0 + 8 * g, K)) =
-        make_uint4(w[4 * g], w[4 * g + 1], w[4 * g + 2], w[4 * g + 3]);
-}
 
 // Forward kernel: kGroups warpgroups per CTA, each running its own stream
 // of work units with its own operands, TMEM columns and mbarriers, so that
@@ -478,9 +468,6 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
 constexpr int kGW1 = 0, kGW2 = 512, kGW3 = 512 + 9216, kGw4 = 512 + 9216 + 1024, kGb1 = kGw4 + 32,
               kGb2 = kGb1 + 32, kGb3 = kGb2 + 32, kGb4 = kGb3 + 32, kGTotal = kGb4 + 1;   // 10881 floats
 
-// Planar (channel-major) K-major operand: row = channel, K = the tile's 128
-// pixels: SBO = 16 * 128 = 2048 B.
-__device__ __forceinline__ uint32_t planar_off(int row, int px) { return core_off(row, px, kTileW); }
 
 __global__ void mpnet_count_kernel(const float *__restrict__ target, long long n, float *__restrict__ inv_n,
                                    float *__restrict__ loss_acc) {
@@ -541,7 +528,7 @@ __device__ __forceinline__ void st_chunks(uint8_t *base, int stride, int row, co
     *reinterpret_cast<uint4 *>(base + c * stride + row * 16) = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
 }
 
-__global__ void __launch_bounds__(kNetThreads, 1)
+__global__ void __launch_bounds__(kNetThreads)
 mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__ y, const float *__restrict__ target,
                   const uint16_t *__restrict__ acts, int batch, int W, int H, const float *__restrict__ inv_n,
                   uint16_t *__restrict__ dz2_out, float *__restrict__ grad, double *__restrict__ loss,
@@ -687,26 +674,32 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
 }
 
-// bwd2 shared memory: dz2 and a1 halos (3 rows x 130 pixels; 4 chunks + the
-// a1 ones chunk, then readable space for the M = 128 MN-major reads), x and
-// its ones chunk, dz1, W2 rearranged as B[i][(tap, o)]
+// bwd2 shared memory: two sets (double buffering) of the dz2 and a1 halos
+// (3 rows x 130 pixels; a1 with its ones chunk 4) and of x (chunk 0, ones
+// chunk 1), then dz1 and W2 rearranged as B[i][(tap, o)]. The M = 128
+// MN-major reads of a1 and x run past their real chunks into what follows
+// (in bounds, finite).
 constexpr int kHaloChunk = 392 * 16;                     // 6272
-constexpr int kB2A1 = 0;                                 // a1 halo: 5 chunks (+ 11 readable)
-constexpr int kB2Dz2 = kB2A1 + 5 * kHaloChunk;           // dz2 halo: 4 chunks
-constexpr int kB2X = kB2Dz2 + 4 * kHaloChunk;            // x: chunk 0, ones chunk 1 (+ 14 readable)
-constexpr int kB2Dz1 = kB2X + 2 * kChunkPx;              // dz1: 4 chunks
+constexpr int kB2SetA1 = 0, kB2SetDz2 = 5 * kHaloChunk, kB2SetBytes = 9 * kHaloChunk;   // 56448
+constexpr int kB2X = 2 * kB2SetBytes;                    // 2 x (x chunk, ones chunk)
+constexpr int kB2Dz1 = kB2X + 4 * kChunkPx;              // dz1: 4 chunks
 constexpr int kB2W2t = kB2Dz1 + 4 * kChunkPx;            // [32 i][288 (tap, o)]
 constexpr int kB2Bar = kB2W2t + 32 * kK2 * 2;
 constexpr int kB2End = kB2Bar + 64;
-constexpr int kB2Smem = (kB2A1 + 16 * kHaloChunk > kB2End ? kB2A1 + 16 * kHaloChunk : kB2End);
-static_assert(kB2X + 16 * kChunkPx <= kB2Smem, "MN-major reads of x stay in shared memory");
+constexpr int kB2Span = kB2SetBytes + 16 * kHaloChunk;   // the farthest MN-major read of a1 (set 1)
+constexpr int kB2Smem = (kB2Span > kB2End ? kB2Span : kB2End);
+static_assert(kB2X + 2 * kChunkPx + 16 * kChunkPx <= kB2Smem, "MN-major reads of x stay in shared memory");
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
 
 __global__ void __launch_bounds__(kNetThreads, 1)
 mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__ feats, const uint16_t *__restrict__ acts,
                   const uint16_t *__restrict__ dz2, int batch, int W, int H, float *__restrict__ grad,
                   uint32_t *__restrict__ status) {
   extern __shared__ __align__(128) uint8_t smem[];
-  uint8_t *sA1 = smem + kB2A1, *sDz2 = smem + kB2Dz2, *sX = smem + kB2X, *sDz1 = smem + kB2Dz1, *sW2t = smem + kB2W2t;
+  uint8_t *sDz1 = smem + kB2Dz1, *sW2t = smem + kB2W2t;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + kB2Bar);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kB2Bar + 8);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -717,9 +710,12 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
     const int o = e / kK2, col = e % kK2, tap = col / 32, i = col % 32;
     *reinterpret_cast<uint16_t *>(sW2t + core_off(i, tap * 32 + o, kK2)) = gw2[e];
   }
-  for (int h = tid; h < 392; h += kNetThreads)
-    *reinterpret_cast<uint4 *>(sA1 + 4 * kHaloChunk + h * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
-  *reinterpret_cast<uint4 *>(sX + kChunkPx + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+  for (int set = 0; set < 2; ++set) {
+    for (int h = tid; h < 392; h += kNetThreads)
+      *reinterpret_cast<uint4 *>(smem + set * kB2SetBytes + kB2SetA1 + 4 * kHaloChunk + h * 16) =
+          make_uint4(0x3F80u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4 *>(smem + kB2X + set * 2 * kChunkPx + kChunkPx + tid * 16) = make_uint4(0x3F80u, 0u, 0u, 0u);
+  }
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)), "r"(512));
@@ -736,30 +732,41 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
   bool ok = true, first = true;
   const int tiles_x = (W + kTileW - 1) / kTileW;
   const long long ntiles = (long long)batch * H * tiles_x;
-  for (long long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-    const int tx = (int)(t % tiles_x), y = (int)((t / tiles_x) % H), b = (int)(t / ((long long)tiles_x * H));
-    const int x0 = tx * kTileW, p = tid, x = x0 + p;
-    // 1. dz2 and a1 halos (zero outside the image), x of the centre row
+  // asynchronous copies of tile T's halos and x into buffer set `set`
+  // (zero-filled outside the image)
+  auto fetch = [&](long long T, int set) {
+    const int tx = (int)(T % tiles_x), y = (int)((T / tiles_x) % H), b = (int)(T / ((long long)tiles_x * H));
+    const int x0 = tx * kTileW;
+    const uint32_t base = smem_u32(smem) + set * kB2SetBytes;
     for (int h = tid; h < kHaloRows; h += kNetThreads) {
       const int r = h / kHaloW, c = h % kHaloW, yy = y - 1 + r, xx = x0 - 1 + c;
-      uint4 d[4], a[4];
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-        const size_t q = ((size_t)b * H + yy) * W + xx;
-        const uint4 *sd = reinterpret_cast<const uint4 *>(dz2 + q * 32);
-        const uint4 *sa = reinterpret_cast<const uint4 *>(acts + q * 96);
-#pragma unroll
-        for (int g = 0; g < 4; ++g) { d[g] = sd[g]; a[g] = sa[g]; }
-      } else {
-#pragma unroll
-        for (int g = 0; g < 4; ++g) { d[g] = make_uint4(0u, 0u, 0u, 0u); a[g] = d[g]; }
-      }
+      const bool v = yy >= 0 && yy < H && xx >= 0 && xx < W;
+      const size_t q = v ? ((size_t)b * H + yy) * W + xx : 0;
 #pragma unroll
       for (int g = 0; g < 4; ++g) {
-        *reinterpret_cast<uint4 *>(sDz2 + g * kHaloChunk + h * 16) = d[g];
-        *reinterpret_cast<uint4 *>(sA1 + g * kHaloChunk + h * 16) = a[g];
+        cp_async16(base + kB2SetDz2 + g * kHaloChunk + h * 16, dz2 + q * 32 + 8 * g, v);
+        cp_async16(base + kB2SetA1 + g * kHaloChunk + h * 16, acts + q * 96 + 8 * g, v);
       }
     }
-    *reinterpret_cast<uint4 *>(sX + p * 16) = x < W ? __ldg(feats + ((size_t)b * H + y) * W + x) : make_uint4(0u, 0u, 0u, 0u);
+    const int x = x0 + tid;
+    cp_async16(smem_u32(smem) + kB2X + set * 2 * kChunkPx + tid * 16, feats + (x < W ? ((size_t)b * H + y) * W + x : 0),
+               x < W);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  long long t = blockIdx.x;
+  if (t < ntiles) fetch(t, 0);
+  for (int it = 0; t < ntiles && ok; t += gridDim.x, ++it) {
+    const int set = it & 1;
+    const int tx = (int)(t % tiles_x), y = (int)((t / tiles_x) % H);
+    (void)y;
+    const int p = tid;
+    (void)tx;
+    uint8_t *sA1 = smem + set * kB2SetBytes + kB2SetA1, *sDz2 = smem + set * kB2SetBytes + kB2SetDz2;
+    uint8_t *sX = smem + kB2X + set * 2 * kChunkPx;
+    // 1. this tile's halos have landed; the next tile's start now
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    if (t + gridDim.x < ntiles) fetch(t + gridDim.x, set ^ 1);
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
@@ -824,6 +831,7 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
     tc_before_sync();
     ok = __syncthreads_and(ok) != 0;   // uniform loop exit
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
   if (!ok) {
     if (tid == 0) atomicOr(status, kStatusTimeout);
     bar_wait(bar, phase ^ 1u);
@@ -945,10 +953,13 @@ cudaError_t launch_mpnet_train(void *weights, float *master, float *adam_m, floa
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)batch * H * ((W + kTileW - 1) / kTileW);
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);
+  // bwd1 holds 128 TMEM columns and 43 KB of shared memory: four CTAs per SM
+  // give four independent tile streams
+  const int grid1 = (int)(ntiles < 4ll * num_sms ? ntiles : 4ll * num_sms);
   e = cudaFuncSetAttribute(mpnet_bwd1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kB1Smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(mpnet_bwd2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kB2Smem);
   if (e != cudaSuccess) return e;
-  mpnet_bwd1_kernel<<<grid, kNetThreads, kB1Smem, s>>>(static_cast<const uint8_t *>(weights), sc.y, target, sc.acts,
+  mpnet_bwd1_kernel<<<grid1, kNetThreads, kB1Smem, s>>>(static_cast<const uint8_t *>(weights), sc.y, target, sc.acts,
                                                        batch, W, H, sc.inv_n, sc.dz2, sc.grad, loss, status);
   mpnet_bwd2_kernel<<<grid, kNetThreads, kB2Smem, s>>>(static_cast<const uint8_t *>(weights),
                                                        reinterpret_cast<const uint4 *>(feats), sc.acts, sc.dz2, batch,
