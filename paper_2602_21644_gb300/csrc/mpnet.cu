@@ -753,26 +753,28 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
                x < W);
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
+  // Per tile: da1 (18 MMAs) is committed on its own and the dW2 MMAs (72)
+  // queue behind it, so the dz1 epilogue runs while the tensor core
+  // accumulates dW2; dW1 (8 MMAs) follows the epilogue. The next tile's da1
+  // commit covers all of them (one thread's MMAs complete in order), so its
+  // wait also frees this tile's buffers for the prefetch two tiles ahead.
   long long t = blockIdx.x;
   if (t < ntiles) fetch(t, 0);
+  bool pending = false;   // MMAs issued and not yet covered by a completed wait
   for (int it = 0; t < ntiles && ok; t += gridDim.x, ++it) {
-    const int set = it & 1;
-    const int tx = (int)(t % tiles_x), y = (int)((t / tiles_x) % H);
-    (void)y;
-    const int p = tid;
-    (void)tx;
+    const int set = it & 1, p = tid;
     uint8_t *sA1 = smem + set * kB2SetBytes + kB2SetA1, *sDz2 = smem + set * kB2SetBytes + kB2SetDz2;
     uint8_t *sX = smem + kB2X + set * 2 * kChunkPx;
-    // 1. this tile's halos have landed; the next tile's start now
+    // 1. this tile's halos and x have landed
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    if (t + gridDim.x < ntiles) fetch(t + gridDim.x, set ^ 1);
     fence_async_smem();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     // 2. da1: the transposed 3 x 3 convolution as an implicit GEMM - tap
-    //    (ky, kx) reads dz2 at halo row (2 - ky) * 130 + (2 - kx) + q
+    //    (ky, kx) reads dz2 at halo row (2 - ky) * 130 + (2 - kx) + q; then
+    //    dW2^T per tap: a1 at halo row ky * 130 + kx + q against dz2 of the
+    //    centre row (halo row 131 + q), MN-major over the tile's pixels
     if (tid == 0) {
       for (int tap = 0; tap < 9; ++tap) {
         const int ky = tap / 3, kx = tap % 3;
@@ -782,11 +784,23 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
                    (tap | j) ? 1u : 0u);
       }
       mma_commit(bar);
+      for (int s2 = 0; s2 < kTileW / 16; ++s2) {
+        const uint32_t acc = (!first || s2 > 0) ? 1u : 0u;
+        const uint32_t bdz2 = smem_u32(sDz2) + (kHaloW + 1) * 16 + s2 * 256;
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap % 3;
+          mma_bf16(tmem + 32 + 32 * tap, sdesc(smem_u32(sA1) + (ky * kHaloW + kx) * 16 + s2 * 256, 128, kHaloChunk),
+                   sdesc(bdz2, 128, kHaloChunk), idesc_bf16_mn(128, 32), acc);
+        }
+      }
     }
-    ok = bar_wait(bar, phase);
+    pending = true;
+    ok = bar_wait(bar, phase);   // da1 done, and every MMA of the previous tile
     phase ^= 1u;
     tc_after_sync();
-    // 3. dz1 = da1 [a1 > 0] (a1 of the centre row: halo row 131 + q)
+    // 3. the previous tile's buffer set is free: prefetch the next tile
+    if (t + gridDim.x < ntiles) fetch(t + gridDim.x, set ^ 1);
+    // 4. dz1 = da1 [a1 > 0] (a1 of the centre row: halo row 131 + q)
     {
       float da[32];
       tmem_ld32(tmem + lane_base + 0, da);
@@ -807,35 +821,27 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
-    // 4. weight gradients over the tile's 128 pixels (MN-major operands):
-    //    dW2^T per tap: a1 at halo row ky * 130 + kx + q against dz2 of the
-    //    centre row (halo row 131 + q); dW1^T: x against dz1
+    // 5. dW1^T: x against dz1
     if (tid == 0) {
-      for (int s = 0; s < kTileW / 16; ++s) {
-        const uint32_t acc = (!first || s > 0) ? 1u : 0u;
-        const uint32_t bdz2 = smem_u32(sDz2) + (kHaloW + 1) * 16 + s * 256;
-        for (int tap = 0; tap < 9; ++tap) {
-          const int ky = tap / 3, kx = tap % 3;
-          mma_bf16(tmem + 32 + 32 * tap, sdesc(smem_u32(sA1) + (ky * kHaloW + kx) * 16 + s * 256, 128, kHaloChunk),
-                   sdesc(bdz2, 128, kHaloChunk), idesc_bf16_mn(128, 32), acc);
-        }
-        mma_bf16(tmem + 320, sdesc(smem_u32(sX) + s * 256, 128, kChunkPx),
-                 sdesc(smem_u32(sDz1) + s * 256, 128, kChunkPx), idesc_bf16_mn(128, 32), acc);
-      }
-      mma_commit(bar);
+      for (int s2 = 0; s2 < kTileW / 16; ++s2)
+        mma_bf16(tmem + 320, sdesc(smem_u32(sX) + s2 * 256, 128, kChunkPx),
+                 sdesc(smem_u32(sDz1) + s2 * 256, 128, kChunkPx), idesc_bf16_mn(128, 32),
+                 (!first || s2 > 0) ? 1u : 0u);
     }
-    ok = ok && bar_wait(bar, phase);
-    phase ^= 1u;
-    tc_after_sync();
     first = false;
     tc_before_sync();
     ok = __syncthreads_and(ok) != 0;   // uniform loop exit
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
-  if (!ok) {
-    if (tid == 0) atomicOr(status, kStatusTimeout);
-    bar_wait(bar, phase ^ 1u);
+  // the last tile's dW MMAs (after a wait that gave up: everything still in
+  // flight) under one more commit and one more bounded wait
+  if (pending) {
+    if (tid == 0) mma_commit(bar);
+    const bool done = bar_wait(bar, phase);
+    phase ^= 1u;
+    ok = __syncthreads_and(ok && done) != 0;
   }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
+  if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
   if (!first) {
     tc_after_sync();
     float d[32];
