@@ -32,7 +32,7 @@ UNIT = "iters/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--height", type=int, default=480)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def load_peaks():
@@ -155,6 +155,26 @@ def workload_config(args):
             "l2": "flushed between steps by a 256 MiB write; inside a step the iterations re-read the "
                   "L2-resident map as the tracking loop does",
             "parallelism": f"replicas x{args.gpus}"}
+
+
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The largest of the ranks' values (the slowest rank's time); the
+    value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(iters_per_step: int, steps: int, world: int, t_ms_max: float) -> float:
+    """Whole-job iterations per second: every replica runs the same steps;
+    the job takes the slowest rank's time."""
+    return iters_per_step * steps * world / (t_ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ our arm
@@ -314,13 +334,10 @@ def run_ours(args):
     t_ms = timed(args.steps, frame)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    t_ms = max_over_ranks(t_ms, world, dev)
     if world > 1:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
         dist.barrier()
-    total_iters = args.iters * args.steps * world
-    value = total_iters / (t_ms / 1e3)
+    value = replica_throughput(args.iters, args.steps, world, t_ms)
 
     # per-kernel device times: the same steps with every kernel launched
     # directly (no graph) between a pair of CUDA events on its stream
@@ -345,11 +362,7 @@ def run_ours(args):
         pose_out.copy_(poses, non_blocking=True)
         loss_out.copy_(loss, non_blocking=True)
 
-    t_e2e = timed(args.steps, frame_e2e)
-    if world > 1:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(timed(args.steps, frame_e2e), world, dev)
     h2d = tg_host.numel() * 4 + pose_host.numel() * 8
     d2h = pose_out.numel() * 8 + 8
 
@@ -414,7 +427,7 @@ def run_ours(args):
             "kernel_timing": {"how": "same steps, kernels launched directly by the library with a CUDA event "
                                      "pair around each on its stream; value above is from CUDA-graph replay",
                               "ms_per_step_direct": round(t_direct / args.steps, 4)},
-            "e2e": {"value": round(args.iters * args.steps * world / (t_e2e / 1e3), 2), "unit": UNIT,
+            "e2e": {"value": round(replica_throughput(args.iters, args.steps, world, t_e2e), 2), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk}
     bf16 = float(peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"]))
