@@ -381,7 +381,7 @@ __device__ void merge_runs(const uint64_t *a, int la, const uint64_t *b, int lb,
   }
 }
 
-__global__ void __launch_bounds__(kTilePix)
+__global__ void __launch_bounds__(kTilePix, 6)
 render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
                   float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
   __shared__ uint64_t s_key[kSortSmallCap];
