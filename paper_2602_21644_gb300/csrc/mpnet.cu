@@ -123,19 +123,25 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // one warpgroup's epilogues overlap the others' MMAs.
 //
 // Work unit: a 128-pixel-wide column strip of one image over a segment of
-// rows [y0, y1). The warpgroup walks down the strip: it computes a1 for one
-// halo row at a time (130 pixels, x0 - 1 .. x0 + 128; rows y0 - 1 .. y1) into
-// a ring of three row slots, and as soon as rows y - 1, y, y + 1 are there it
-// computes output row y. Every a1 row is thus computed once per unit (plus
-// the two boundary rows), not three times as with independent row tiles.
-// The next a1 row's input (8 x 130 BF16) is fetched by TMA while the current
-// row is in flight; out-of-image rows and columns read as zero.
+// output rows [y0, y1). The warpgroup walks down the strip computing a1 for
+// one 130-pixel halo row at a time (rows y0 - 1 .. y1; x0 - 1 .. x0 + 128)
+// into a ring of row slots; every a1 row is computed once per unit (plus two
+// boundary rows), not three times as with independent row tiles.
+//
+// Software pipeline: step k issues, under one commit, z1 of a1 row k, z2 of
+// output row k - 3 (its a1 rows k - 3 .. k - 1 were written by earlier
+// steps) and z3 of output row k - 4 (its a2 by the previous step), then runs
+// the three epilogues. One MMA round trip per output row. The epilogues run
+// after the step's wait, when every MMA that read their target buffers has
+// completed, so three ring slots and one a2 buffer suffice; the input of a1
+// row k + 2 is fetched by TMA (two input buffers) while step k + 1 runs, and
+// out-of-image rows and columns read as zero.
 //
 // Operand layouts (no swizzle): "row-contiguous chunks" - chunk c holds
 // channels 8c..8c+7 of every row as one 16-byte line, rows consecutive (SBO =
 // 128 B between 8-row groups, LBO = the chunk stride). An MMA may then start
 // at any row, which makes the 3 x 3 convolution an implicit GEMM: tap (ky, kx)
-// reads slot (y - 1 + ky) at rows kx + p directly, with no im2col copy.
+// reads the slot of a1 row y - 1 + ky at rows kx + p directly, no im2col.
 //
 // Biases ride in the MMAs: a K-chunk of per-row constants (1, 1, 0, ..., 0)
 // meets a B column pair (hi, lo) with hi = bf16(b), lo = bf16(b - hi), so
@@ -144,19 +150,24 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // conversion per pair.
 constexpr int kGroups = 4;
 constexpr int kFwdThreads = 128 * kGroups;
-constexpr int kInRows = 256;                            // 2 M-blocks; rows 0..129 from the TMA
-constexpr int kInBytes = 2 * kInRows * 16;              // chunk 0 = input, chunk 1 = (1, 1, 0, ...)
+constexpr int kRowBytes = kHaloW * 16;                  // 2080 = the TMA box (8 x 130 x 1 x 1 bf16)
+constexpr int kInBuf = 2176;                            // one input row (+ pad)
 constexpr int kSlotRows = 136;
 constexpr int kSlotChunk = kSlotRows * 16;              // 2176
 constexpr int kSlotBytes = 4 * kSlotChunk;              // 8704
-constexpr int kWgIn = 0, kWgRing = kInBytes, kWgA2 = kWgRing + 3 * kSlotBytes;
-constexpr int kWgBytes = kWgA2 + 4 * kTileW * 16;       // 42496
+constexpr int kSlots = 3;
+constexpr int kA2Bytes = 4 * kTileW * 16;               // 8192
+// per warpgroup: in0, in1, ones (256 rows of (1, 1, 0, ...)), ring, a2 x 2.
+// An L1 MMA reads 256 rows from an input buffer; rows past 129 are
+// don't-care rows (they land in D rows that are never read).
+constexpr int kWgIn0 = 0, kWgIn1 = kInBuf, kWgOnes = 2 * kInBuf, kWgRing = kWgOnes + 4096;
+constexpr int kWgA2 = kWgRing + kSlots * kSlotBytes;
+constexpr int kWgBytes = kWgA2 + kA2Bytes;              // 42752
 constexpr int kFW1 = kGroups * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFB2 = kFW3 + 2048,
               kFB3 = kFB2 + 1024, kFPar = kFB3 + 1024;
 constexpr int kFBar = kFPar + 256;
-constexpr int kFwdSmem = kFBar + 128 + 1024;            // + alignment slack
-constexpr int kRowBytes = kHaloW * 16;                  // 2080 = the TMA box (8 x 130 x 1 x 1 bf16)
-constexpr uint32_t kWgCols = 96;                        // D1 +0..63 (D3 reuses +0..31), D2 +64..95
+constexpr int kFwdSmem = kFBar + 256 + 1024;            // + alignment slack
+constexpr uint32_t kWgCols = 128;                       // D1 +0..63, D2 +64..95, D3 +96..127
 
 __device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
@@ -192,13 +203,13 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3, *sB2 = smem + kFB2, *sB3 = smem + kFB3;
   float *sw4 = reinterpret_cast<float *>(smem + kFPar), *sb4 = sw4 + kCh;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);   // [g]: tma, mma
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 64);
-  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 72);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);   // [g]: in0, in1, mma
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 128);
+  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 136);
   const int tid = threadIdx.x, g = tid >> 7, t = tid & 127, warp = t >> 5, lane = tid & 31;
-  uint8_t *sIn = smem + g * kWgBytes + kWgIn, *sRing = smem + g * kWgBytes + kWgRing;
-  uint8_t *sA2 = smem + g * kWgBytes + kWgA2;
-  uint64_t *bar_tma = bars + 2 * g, *bar_mma = bars + 2 * g + 1;
+  uint8_t *wg = smem + g * kWgBytes;
+  uint8_t *sRing = wg + kWgRing, *sA2 = wg + kWgA2;
+  uint64_t *bar_in = bars + 3 * g, *bar_mma = bars + 3 * g + 2;
 
   // weights into the K-major core-matrix layouts; bias columns (hi, lo)
   const uint16_t *gw1 = reinterpret_cast<const uint16_t *>(weights + kOffW1);
@@ -224,15 +235,15 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     *reinterpret_cast<uint16_t *>((which ? sB3 : sB2) + core_off(o, k, 16)) = v;
   }
   if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
-  // input buffer: rows 130-255 of chunk 0 are never written by the TMA
-  // (zero); chunk 1 holds the bias constants (1, 1, 0, ..., 0) of every row
-  for (int e = t; e < (kInRows * 16 - kRowBytes) / 16; e += 128)
-    *reinterpret_cast<uint4 *>(sIn + kRowBytes + 16 * e) = make_uint4(0u, 0u, 0u, 0u);
-  for (int e = t; e < kInRows; e += 128)
-    *reinterpret_cast<uint4 *>(sIn + kInRows * 16 + 16 * e) = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+  // the whole warpgroup area starts at zero (don't-care rows stay finite);
+  // then the bias constants (1, 1, 0, ..., 0) of every row
+  for (int e = t; e < kWgBytes / 16; e += 128) {
+    const bool one = e >= kWgOnes / 16 && e < kWgOnes / 16 + 256;   // one writer per line
+    *reinterpret_cast<uint4 *>(wg + 16 * e) = make_uint4(one ? 0x3F803F80u : 0u, 0u, 0u, 0u);
+  }
   if (tid == 0) {
     sb4[0] = reinterpret_cast<const float *>(weights + kOffB4)[0];
-    for (int k = 0; k < 2 * kGroups; ++k)
+    for (int k = 0; k < 3 * kGroups; ++k)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int k = 0; k < kGroups; ++k) s_fail[k] = 0u;
@@ -248,10 +259,14 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   tc_after_sync();
   const uint32_t tmem = *s_tmem + kWgCols * (uint32_t)g;
   const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-  const uint32_t ones = smem_u32(sIn) + kInRows * 16;   // rows of (1, 1, 0, ...)
-  uint32_t ph_tma = 0, ph_mma = 0;
+  const uint32_t wg_u32 = smem_u32(wg);
+  const uint32_t ones = wg_u32 + kWgOnes;
+  uint32_t ph_mma = 0;
+  uint32_t qbase = 0;          // a1 rows of the earlier units (input buffer parity)
   bool ok = true;
-  bool tma_inflight = false, mma_inflight = false;   // thread 0's outstanding async work
+  // thread 0: bit 0/1 = TMA into in0/in1 pending (bit 8/9 = the parity of
+  // that fetch's phase), bit 2 = MMA pending
+  uint32_t in_flight = 0;
 
   const long long stride = (long long)kGroups * gridDim.x;
   // unit u -> image b, strip x0, rows [y0, y1)
@@ -263,163 +278,141 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     *y0 = seg * units.seg_rows;
     *y1 = min(*y0 + units.seg_rows, H);
   };
+  auto fetch = [&](uint32_t q, int x0, int r, int b) {   // input of the q-th a1 row of this warpgroup
+    const uint32_t buf = q & 1u;
+    tma_row(&in_map, wg_u32 + buf * kInBuf, bar_in + buf, x0 - 1, r, b);
+    in_flight = (in_flight & ~(0x101u << buf)) | (1u << buf) | (((q >> 1) & 1u) << (8 + buf));
+  };
   long long u = (long long)kGroups * blockIdx.x + g;
   if (u < units.count && t == 0) {
     int b, x0, y0, y1;
     unit(u, &b, &x0, &y0, &y1);
-    tma_row(&in_map, smem_u32(sIn), bar_tma, x0 - 1, y0 - 1, b);
-    tma_inflight = true;
+    fetch(0, x0, y0 - 1, b);
+    fetch(1, x0, y0, b);
   }
   for (; u < units.count; u += stride) {
     int b, x0, y0, y1;
     unit(u, &b, &x0, &y0, &y1);
-    const int nrows = y1 - y0 + 2;   // a1 rows y0 - 1 .. y1
-    for (int k = 0; k < nrows; ++k) {
-      const int r = y0 - 1 + k;
-      uint8_t *slot = sRing + ((r + 3) % 3) * kSlotBytes;
-      // 1. z1 of a1 row r (130 pixels): 2 MMAs (M = 128, N = 32, K = 16:
-      //    8 input channels + the bias chunk)
+    const int nO = y1 - y0, nA = nO + 2;   // output rows; a1 rows y0 - 1 .. y1
+    int nb = 0, nx0 = 0, ny0 = 0, ny1 = 0;
+    const bool has_next = u + stride < units.count;
+    if (has_next) unit(u + stride, &nb, &nx0, &ny0, &ny1);
+    for (int k = 0; k < nA + 2; ++k) {
+      const bool d1 = k < nA, d2 = k >= 3 && k < nO + 3, d3 = k >= 4;
+      const uint32_t q = qbase + (uint32_t)k;
+      // MMAs of this step under one commit
       if (t == 0) {
-        ok = ok && bar_wait(bar_tma, ph_tma);
-        tma_inflight = !ok;
+        if (d1 && ok) {
+          ok = bar_wait(bar_in + (q & 1u), (q >> 1) & 1u);
+          if (ok) in_flight &= ~(1u << (q & 1u));
+        }
         if (ok) {
           tc_after_sync();
-          mma_bf16(tmem + 0, sdesc(smem_u32(sIn), kInRows * 16, 128), sdesc(smem_u32(sW1), 128, 256),
-                   idesc_bf16(128, 32), 0u);
-          mma_bf16(tmem + 32, sdesc(smem_u32(sIn) + 2048, kInRows * 16, 128), sdesc(smem_u32(sW1), 128, 256),
-                   idesc_bf16(128, 32), 0u);
+          if (d1) {
+            const uint32_t in = wg_u32 + (q & 1u) * kInBuf, lbo = ones - in;
+            mma_bf16(tmem + 0, sdesc(in, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
+            mma_bf16(tmem + 32, sdesc(in + 2048, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
+          }
+          if (d2) {
+            const int j = k - 3;   // output row y0 + j from a1 rows j .. j + 2 of this unit
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+              const int ky = tap / 3, kx = tap % 3;
+              const uint32_t sl = smem_u32(sRing) + ((j + ky) % kSlots) * kSlotBytes;
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+                mma_bf16(tmem + 64, sdesc(sl + 2 * h * kSlotChunk + kx * 16, kSlotChunk, 128),
+                         sdesc(smem_u32(sW2) + (2 * tap + h) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
+                         (tap | h) ? 1u : 0u);
+            }
+            mma_bf16(tmem + 64, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256), idesc_bf16(128, 32), 1u);
+          }
+          if (d3) {
+            const uint32_t a2 = smem_u32(sA2);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+              mma_bf16(tmem + 96, sdesc(a2 + 2 * h * (kTileW * 16), kTileW * 16, 128),
+                       sdesc(smem_u32(sW3) + h * 256, 128, 512), idesc_bf16(128, 32), h ? 1u : 0u);
+            mma_bf16(tmem + 96, sdesc(ones, 2048, 128), sdesc(smem_u32(sB3), 128, 256), idesc_bf16(128, 32), 1u);
+          }
           mma_commit(bar_mma);
-          mma_inflight = true;
+          in_flight |= 4u;
         }
       }
-      ph_tma ^= 1u;
       {
         const bool done = ok && bar_wait(bar_mma, ph_mma);
-        if (done) mma_inflight = false;
+        if (done && t == 0) in_flight &= ~4u;
         ok = done && ok;
       }
       ph_mma ^= 1u;
       tc_after_sync();
-      // the input buffer is free: fetch the next a1 row's input (this unit's
-      // next row, else the next unit's first)
-      if (t == 0 && ok) {
-        if (k + 1 < nrows) {
-          tma_row(&in_map, smem_u32(sIn), bar_tma, x0 - 1, r + 1, b);
-          tma_inflight = true;
-        } else if (u + stride < units.count) {
-          int nb, nx0, ny0, ny1;
-          unit(u + stride, &nb, &nx0, &ny0, &ny1);
-          tma_row(&in_map, smem_u32(sIn), bar_tma, nx0 - 1, ny0 - 1, nb);
-          tma_inflight = true;
-        }
+      // the input buffer of a1 row k is free: fetch a1 row k + 2 (of this
+      // unit, else of the next)
+      if (t == 0 && ok && d1) {
+        if (k + 2 < nA) fetch(q + 2, x0, y0 + k + 1, b);
+        else if (has_next) fetch(q + 2, nx0, ny0 - 1 + (k + 2 - nA), nb);
       }
-      // 2. a1 = bf16(relu(z1)), zero outside the image, into the row's slot;
-      //    pixel i of the slot is x = x0 - 1 + i
-      {
-        const bool row_in = r >= 0 && r < H;
-        const bool own_row = r >= y0 && r < y1;
+      const int p = 32 * warp + lane;
+      // epilogue 1: a1 row r = y0 - 1 + k (zero outside the image) -> slot
+      if (d1) {
+        const int r = y0 - 1 + k;
+        const bool row_in = r >= 0 && r < H, own_row = r >= y0 && r < y1;
+        uint8_t *slot = sRing + (k % kSlots) * kSlotBytes;
 #pragma unroll 1
         for (int mb = 0; mb < 2; ++mb) {
           if (mb == 1 && warp != 0) break;
           float z[32];
           tmem_ld32(tmem + lane_base + mb * 32, z);
-          const int i = mb * 128 + 32 * warp + lane;
+          const int i = mb * 128 + p;   // slot pixel i <-> x = x0 - 1 + i
           if (i < kHaloW) {
             const int xx = x0 - 1 + i;
             const bool in = row_in && xx >= 0 && xx < W;
             uint32_t w[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q) w[q] = in ? relu_bf16x2(z[2 * q], z[2 * q + 1]) : 0u;
+            for (int e = 0; e < 16; ++e) w[e] = in ? relu_bf16x2(z[2 * e], z[2 * e + 1]) : 0u;
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-              *reinterpret_cast<uint4 *>(slot + q * kSlotChunk + i * 16) =
-                  make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            for (int c = 0; c < 4; ++c)
+              *reinterpret_cast<uint4 *>(slot + c * kSlotChunk + i * 16) =
+                  make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
             if (acts && own_row && i >= 1 && i <= kTileW && xx < W) {
               uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
 #pragma unroll
-              for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+              for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
             }
           }
         }
       }
-      fence_async_smem();
-      tc_before_sync();
-      wg_sync(g);
-      tc_after_sync();
-      if (k < 2) continue;   // output row r - 1 needs a1 rows r - 2, r - 1, r
-      const int y = r - 1;
-      // 3. z2 of output row y: implicit-GEMM 3 x 3 convolution, 9 taps x 2
-      //    K-halves, + bias
-      if (t == 0 && ok) {
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const int ky = tap / 3, kx = tap % 3;
-          const uint32_t sl = smem_u32(sRing) + ((y + 2 + ky) % 3) * kSlotBytes;
-#pragma unroll
-          for (int j = 0; j < 2; ++j)
-            mma_bf16(tmem + 64, sdesc(sl + 2 * j * kSlotChunk + kx * 16, kSlotChunk, 128),
-                     sdesc(smem_u32(sW2) + (2 * tap + j) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
-                     (tap | j) ? 1u : 0u);
-        }
-        mma_bf16(tmem + 64, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256), idesc_bf16(128, 32), 1u);
-        mma_commit(bar_mma);
-        mma_inflight = true;
-      }
-      {
-        const bool done = ok && bar_wait(bar_mma, ph_mma);
-        if (done) mma_inflight = false;
-        ok = done && ok;
-      }
-      ph_mma ^= 1u;
-      tc_after_sync();
-      const int p = 32 * warp + lane;
-      {
+      // epilogue 2: a2 of output row y0 + k - 3 -> a2 buffer
+      if (d2) {
+        const int y = y0 + k - 3;
         float z[32];
         tmem_ld32(tmem + lane_base + 64, z);
         uint32_t w[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) w[q] = relu_bf16x2(z[2 * q], z[2 * q + 1]);
+        for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e], z[2 * e + 1]);
+        uint8_t *a2 = sA2;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-          *reinterpret_cast<uint4 *>(sA2 + q * (kTileW * 16) + p * 16) =
-              make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+        for (int c = 0; c < 4; ++c)
+          *reinterpret_cast<uint4 *>(a2 + c * (kTileW * 16) + p * 16) =
+              make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
         if (acts && x0 + p < W) {
           uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+          for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
         }
       }
-      fence_async_smem();
-      tc_before_sync();
-      wg_sync(g);
-      tc_after_sync();
-      // 4. z3: 2 MMAs + bias, into the (consumed) D1 columns
-      if (t == 0 && ok) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-          mma_bf16(tmem + 0, sdesc(smem_u32(sA2) + 2 * j * (kTileW * 16), kTileW * 16, 128),
-                   sdesc(smem_u32(sW3) + j * 256, 128, 512), idesc_bf16(128, 32), j ? 1u : 0u);
-        mma_bf16(tmem + 0, sdesc(ones, 2048, 128), sdesc(smem_u32(sB3), 128, 256), idesc_bf16(128, 32), 1u);
-        mma_commit(bar_mma);
-        mma_inflight = true;
-      }
-      {
-        const bool done = ok && bar_wait(bar_mma, ph_mma);
-        if (done) mma_inflight = false;
-        ok = done && ok;
-      }
-      ph_mma ^= 1u;
-      tc_after_sync();
-      // 5. a3, the dot product with w4 and the sigmoid
-      {
+      // epilogue 3: a3, the dot product with w4 and the sigmoid of output
+      // row y0 + k - 4
+      if (d3) {
+        const int y = y0 + k - 4;
         float z[32];
-        tmem_ld32(tmem + lane_base + 0, z);
+        tmem_ld32(tmem + lane_base + 96, z);
         float acc = sb4[0];
         uint32_t w[16];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          w[q] = relu_bf16x2(z[2 * q], z[2 * q + 1]);
-          acc += __uint_as_float(w[q] << 16) * sw4[2 * q] + __uint_as_float(w[q] & 0xFFFF0000u) * sw4[2 * q + 1];
+        for (int e = 0; e < 16; ++e) {
+          w[e] = relu_bf16x2(z[2 * e], z[2 * e + 1]);
+          acc += __uint_as_float(w[e] << 16) * sw4[2 * e] + __uint_as_float(w[e] & 0xFFFF0000u) * sw4[2 * e + 1];
         }
         if (x0 + p < W) {
           const size_t pix = ((size_t)b * H + y) * W + x0 + p;
@@ -427,25 +420,28 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
           if (acts) {
             uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) ga[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+            for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
           }
         }
       }
+      fence_async_smem();
       tc_before_sync();
-      wg_sync(g);   // D3 (= D1 columns) read by all before the next row's first MMAs
-      tc_after_sync();
+      wg_sync(g);   // slots, a2 and all D columns consumed before the next step's MMAs
     }
+    qbase += (uint32_t)nA;
     if (!ok) s_fail[g] = 1u;
     wg_sync(g);
     if (s_fail[g]) break;
   }
   if (s_fail[g]) {
     // a wait gave up: record it; give what may still be in flight one more
-    // bounded wait before the tensor memory is released
+    // bounded wait before the tensor memory is released (the in-flight
+    // phase of each barrier is the one after its last completed phase)
     if (t == 0) {
       atomicOr(status, kStatusTimeout);
-      if (tma_inflight) bar_wait(bar_tma, ph_tma ^ 1u);
-      if (mma_inflight) bar_wait(bar_mma, ph_mma ^ 1u);
+      for (uint32_t buf = 0; buf < 2; ++buf)
+        if (in_flight & (1u << buf)) bar_wait(bar_in + buf, (in_flight >> (8 + buf)) & 1u);
+      if (in_flight & 4u) bar_wait(bar_mma, ph_mma ^ 1u);
     }
   }
   tc_before_sync();
@@ -895,18 +891,17 @@ cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s) {
   if (batch <= 0 || W <= 0 || H <= 0) return cudaSuccess;
   // units: strips x row segments; the segment length balances the units over
-  // the warpgroups (cost of a unit ~ its output rows + a quarter of its a1
-  // rows, two of which are boundary recomputation)
+  // the warpgroups (a unit of S output rows takes S + 4 pipeline steps)
   FwdUnits un;
   un.tiles_x = (W + kTileW - 1) / kTileW;
   const long long strips = (long long)batch * un.tiles_x;
   const long long slots = (long long)num_sms * kGroups;
   double best = 1e300;
   un.seg_rows = H;
-  for (int S = 4; S <= 64; ++S) {
+  for (int S = 4; S <= 96; ++S) {
     const long long segs = (H + S - 1) / S;
     const long long rounds = (strips * segs + slots - 1) / slots;
-    const double cost = (double)rounds * (S + 0.25 * (S + 2));
+    const double cost = (double)rounds * (S + 4);   // pipeline fill and drain: 4 steps
     if (cost < best - 1e-9) { best = cost; un.seg_rows = S; }
     if (S >= H) break;
   }
