@@ -1,0 +1,61 @@
+"""torch.autograd wrapper of the splatting path: the forward kernels render and
+reduce the MP-weighted loss of Eqs. (20)-(22); the hand-written adjoint
+kernels give its gradient with respect to the Gaussian records and to the
+camera poses. No arithmetic of the path runs here: both directions call the
+library through the C ABI.
+
+Pose gradient convention: the poses are world-to-camera T_CW (V x 12
+doubles); their gradient is taken with respect to a left-perturbation twist
+xi = (rho, phi) applied as T <- exp(xi^) T, evaluated at xi = 0. The twist is
+therefore an explicit input that must be zero when the loss is evaluated
+(pose_step applies a step and folds it back into T).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import dags
+
+
+class SplatLoss(torch.autograd.Function):
+    """loss = SplatLoss.apply(gauss, xi, ctx, cam, poses, targets, rcfg, lcfg)
+
+    gauss   [N, 16] float32 CUDA records (gradient: same slots, see dags.h)
+    xi      [V, 6] float64 CUDA twist, all zero (gradient: dL/dxi)
+    ctx     dags.Context; cam dags.Camera; poses [V, 12] float64 CUDA
+    targets [V, H*W, 4] float32 CUDA; rcfg / lcfg optional configs
+    Returns the loss as a [1] float64 tensor."""
+
+    @staticmethod
+    def forward(fctx, gauss, xi, ctx, cam, poses, targets, rcfg=None, lcfg=None):
+        image, last, loss = ctx.forward(gauss, cam, poses, targets, rcfg=rcfg, lcfg=lcfg)
+        fctx.save_for_backward(gauss, poses, targets, image, last)
+        fctx.dags_ctx, fctx.cam, fctx.rcfg, fctx.lcfg = ctx, cam, rcfg, lcfg
+        return loss
+
+    @staticmethod
+    def backward(fctx, gloss):
+        gauss, poses, targets, image, last = fctx.saved_tensors
+        flags = 0
+        if fctx.needs_input_grad[0]:
+            flags |= dags.GRAD_GAUSS
+        if fctx.needs_input_grad[1]:
+            flags |= dags.GRAD_POSE
+        gg = gp = None
+        if flags:
+            gg, gp = fctx.dags_ctx.backward(gauss, fctx.cam, poses, targets, image, last, flags=flags,
+                                            rcfg=fctx.rcfg, lcfg=fctx.lcfg)
+        s = gloss.reshape(())
+        if gg is not None:
+            gg = gg * s.to(gg.dtype)
+        if gp is not None:
+            gp = gp * s
+        return gg, gp, None, None, None, None, None, None
+
+
+def splat_loss(ctx, cam, gauss, poses, targets, xi=None, rcfg=None, lcfg=None):
+    """Differentiable MP-weighted loss; pass xi (zeros, requires_grad) to get
+    the pose-twist gradient."""
+    if xi is None:
+        xi = torch.zeros((poses.shape[0], 6), dtype=torch.float64, device=poses.device)
+    return SplatLoss.apply(gauss, xi, ctx, cam, poses, targets, rcfg, lcfg)
