@@ -352,6 +352,14 @@ int mpnet_train_step(dags_ctx *ctx, void *weights, float *master, float *adam_m,
                      const uint16_t *feats, const float *target, int32_t batch, int32_t width, int32_t height,
                      float lr, double *loss, float *grad_out, void *stream);
 
+/* Failure-path self-test (no paper counterpart): one device thread waits,
+ * for `spins` bounded iterations, on an mbarrier phase that nothing
+ * completes - the same bounded wait the tensor-core kernels use - and records
+ * DAGS_E_TIMEOUT in the ctx's status word, which the next dags_sync_status
+ * returns and clears. Nothing hangs or faults; the ctx stays usable.
+ * 0 <= spins <= 2^24, else DAGS_E_INVAL. */
+int dags_selftest_timeout(dags_ctx *ctx, int64_t spins, void *stream);
+
 /* Per-kernel device timing (tracing). When enabled, every kernel the
  * library launches on a stream that is not being captured into a CUDA graph
  * is bracketed by a pair of CUDA events on that stream. dags_timing_read

@@ -10,6 +10,8 @@
 
 #include "common.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace dags;
 
 // Opt-in per-kernel device timing: a pair of CUDA events around every
@@ -177,6 +179,15 @@ int common_args(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
 
 }  // namespace
 
+// An NVTX range around each ABI call (header-only NVTX 3: a no-op unless a
+// profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 extern "C" {
 
 void dags_default_raster_cfg(dags_raster_cfg *c) {
@@ -224,6 +235,7 @@ const char *dags_status_string(int code) {
 
 int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_t max_height,
                 int32_t max_views, int64_t max_pairs) {
+  NvtxRange nv("dags_create");
   if (!out) return DAGS_E_INVAL;
   *out = nullptr;
   if (max_gaussians < 0 || max_gaussians > (int64_t)0x7FFFFFFF || max_width <= 0 || max_height <= 0 ||
@@ -298,6 +310,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
 }
 
 void dags_destroy(dags_ctx *ctx) {
+  NvtxRange nv("dags_destroy");
   if (!ctx) return;
   int cur = 0;
   cudaGetDevice(&cur);
@@ -314,6 +327,7 @@ void dags_destroy(dags_ctx *ctx) {
 }
 
 int dags_sync_status(dags_ctx *ctx, int64_t *required_pairs) {
+  NvtxRange nv("dags_sync_status");
   if (!ctx) return DAGS_E_INVAL;
   if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return DAGS_E_CUDA;
   uint32_t cnt[CNT_N];
@@ -334,6 +348,7 @@ int dags_sync_status(dags_ctx *ctx, int64_t *required_pairs) {
 int splat_forward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *poses,
                   int32_t n_views, const float *targets, const dags_raster_cfg *rcfg,
                   const dags_loss_cfg *lcfg, float *image, int32_t *last, double *loss, void *stream) {
+  NvtxRange nv("splat_forward");
   int rc = common_args(ctx, gauss, n, cam, poses, n_views);
   if (rc) return rc;
   if (!image || !last || (loss && !targets)) return DAGS_E_INVAL;
@@ -374,6 +389,7 @@ int splat_forward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camer
 
 int dags_copy_bins(dags_ctx *ctx, uint32_t *tile_start, int64_t n_start, uint32_t *ids, int64_t cap,
                    int64_t *n_pairs) {
+  NvtxRange nv("dags_copy_bins");
   if (!ctx || !tile_start || !ctx->fwd_image || cap < 0 || (cap > 0 && !ids)) return DAGS_E_INVAL;
   if (n_start != (int64_t)ctx->fwd_views * ctx->fwd_tiles + 1) return DAGS_E_INVAL;
   int64_t req = 0;
@@ -394,6 +410,7 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
                    int32_t n_views, const float *targets, const dags_raster_cfg *rcfg,
                    const dags_loss_cfg *lcfg, const float *image, const int32_t *last, uint32_t grad_flags,
                    float *grad_gauss, double *grad_pose, void *stream) {
+  NvtxRange nv("splat_backward");
   int rc = common_args(ctx, gauss, n, cam, poses, n_views);
   if (rc) return rc;
   if (!targets || !image || !last) return DAGS_E_INVAL;
@@ -427,6 +444,7 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
 
 int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state, int32_t n_views,
               const dags_pose_cfg *cfg, void *stream) {
+  NvtxRange nv("pose_step");
   if (!ctx || !poses || !grad || !adam_state || n_views < 1 || n_views > ctx->ws.max_v) return DAGS_E_INVAL;
   dags_pose_cfg c;
   if (cfg) c = *cfg;
@@ -477,6 +495,7 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
                 const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                 const dags_pose_cfg *pcfg, int32_t iters, double *adam_state, float *image, int32_t *last,
                 double *loss, double *grad_pose, int32_t use_graph, void *stream) {
+  NvtxRange nv("splat_track");
   if (!ctx || iters < 0 || !pose || !targets || !adam_state || !image || !last || !loss || !grad_pose)
     return DAGS_E_INVAL;
   int rc = common_args(ctx, gauss, n, cam, pose, 1);
@@ -562,6 +581,7 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
               const float *targets, const float *image, const uint8_t *inst, const float *table,
               int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
               double *stats, const float *mp_map, float *mp_pixel, void *stream) {
+  NvtxRange nv("mp_update");
   int rc = common_args(ctx, gauss, n, cam, pose, 1);
   if (rc) return rc;
   if (!targets || !image || !inst || !table || !labels || !stats) return DAGS_E_INVAL;
@@ -589,6 +609,7 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
 int mpnet_features(dags_ctx *ctx, const float *image, const float *targets, const uint8_t *inst,
                    const float *table, int32_t n_regions, int32_t width, int32_t height, uint16_t *feats,
                    void *stream) {
+  NvtxRange nv("mpnet_features");
   if (!ctx || !image || !targets || !inst || !table || !feats || width < 1 || height < 1) return DAGS_E_INVAL;
   if (n_regions < 1 || n_regions > DAGS_MP_MAX_REGIONS) return DAGS_E_INVAL;
   if (((uintptr_t)targets & 15u) != 0 || ((uintptr_t)feats & 15u) != 0 || ((uintptr_t)table & 7u) != 0)
@@ -606,6 +627,7 @@ int mpnet_features(dags_ctx *ctx, const float *image, const float *targets, cons
 
 int mpnet_infer(dags_ctx *ctx, const void *weights, const uint16_t *feats, int32_t batch, int32_t width,
                 int32_t height, float *mp_out, uint16_t *acts, void *stream) {
+  NvtxRange nv("mpnet_infer");
   if (!ctx || !weights || !feats || !mp_out || batch < 1 || width < 1 || height < 1) return DAGS_E_INVAL;
   if (((uintptr_t)feats & 15u) != 0 || ((uintptr_t)weights & 15u) != 0 || ((uintptr_t)acts & 15u) != 0)
     return DAGS_E_INVAL;
@@ -621,6 +643,7 @@ int mpnet_infer(dags_ctx *ctx, const void *weights, const uint16_t *feats, int32
 int mpnet_train_step(dags_ctx *ctx, void *weights, float *master, float *adam_m, float *adam_v, int32_t step,
                      const uint16_t *feats, const float *target, int32_t batch, int32_t width, int32_t height,
                      float lr, double *loss, float *grad_out, void *stream) {
+  NvtxRange nv("mpnet_train_step");
   if (!ctx || !weights || !master || !adam_m || !adam_v || !feats || !target || !loss) return DAGS_E_INVAL;
   if (batch < 1 || width < 1 || height < 1 || step < 1 || !isfinite(lr) || lr < 0.f) return DAGS_E_INVAL;
   if (((uintptr_t)feats & 15u) != 0 || ((uintptr_t)weights & 15u) != 0) return DAGS_E_INVAL;
@@ -653,7 +676,16 @@ int mpnet_train_step(dags_ctx *ctx, void *weights, float *master, float *adam_m,
   return cuda_status(e);
 }
 
+int dags_selftest_timeout(dags_ctx *ctx, int64_t spins, void *stream) {
+  NvtxRange nv("dags_selftest_timeout");
+  if (!ctx || spins < 0 || spins > (1ll << 24)) return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return cuda_status(launch_selftest_wait(ctx->ws.counters + CNT_STATUS, (long long)spins, s));
+}
+
 int dags_timing_enable(dags_ctx *ctx, int enable) {
+  NvtxRange nv("dags_timing_enable");
   if (!ctx) return DAGS_E_INVAL;
   int rc = DAGS_OK;
   if (!enable && ctx->timer.used) rc = ctx->timer.collect();
@@ -662,6 +694,7 @@ int dags_timing_enable(dags_ctx *ctx, int enable) {
 }
 
 int dags_timing_read(dags_ctx *ctx, double *ms, int64_t *launches, int32_t count) {
+  NvtxRange nv("dags_timing_read");
   if (!ctx || count < 0 || (count > 0 && (!ms || !launches))) return DAGS_E_INVAL;
   const int rc = ctx->timer.collect();
   if (rc != DAGS_OK) return rc;
@@ -746,6 +779,7 @@ __global__ void static_status_kernel(const uint32_t *counters, int64_t *status, 
 extern "C" int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
                                     const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                                     float *image, int32_t *last, double *loss, int64_t *status, void *stream) {
+  NvtxRange nv("splat_forward_static");
   if (n < 0 || n > kStaticMaxN || (n > 0 && !gauss) || !cam || !pose || !image || !last || (loss && !targets))
     return DAGS_E_INVAL;
   if (cam->width <= 0 || cam->height <= 0 || cam->width > kStaticMaxW || cam->height > kStaticMaxH)

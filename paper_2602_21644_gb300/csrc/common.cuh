@@ -121,6 +121,7 @@ struct MpnetScratch {
   float *inv_n = nullptr;    // [2]: 1 / valid pixels, valid count
   long long cap = 0;         // pixels
 };
+cudaError_t launch_selftest_wait(uint32_t *status, long long limit, cudaStream_t s);
 cudaError_t launch_mpnet_train(void *weights, float *master, float *adam_m, float *adam_v, int step,
                                const uint16_t *feats, const float *target, int batch, int W, int H, float lr,
                                double *loss, const MpnetScratch &sc, uint32_t *status, int num_sms, cudaStream_t s);

@@ -80,9 +80,9 @@ __device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::a
 __device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
 // Bounded wait on an mbarrier phase; false if the limit ran out.
-__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_wait_n(uint64_t *bar, uint32_t parity, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kSpinLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
@@ -93,6 +93,17 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
     if (done) return true;
   }
   return false;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) { return bar_wait_n(bar, parity, kSpinLimit); }
+
+// Failure-path self-test: one thread waits, with the given iteration limit,
+// on an mbarrier phase that nothing completes, then records the timeout in
+// the status word as every kernel's bounded waits do.
+__global__ void selftest_wait_kernel(uint32_t *status, long long limit) {
+  __shared__ uint64_t bar;
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  if (!bar_wait_n(&bar, 0u, limit)) atomicOr(status, kStatusTimeout);
 }
 
 // 32 consecutive FP32 columns of this thread's TMEM lane.
@@ -886,6 +897,11 @@ __global__ void mpnet_adam_kernel(uint8_t *__restrict__ weights, float *__restri
   }
 }
 }  // namespace
+
+cudaError_t launch_selftest_wait(uint32_t *status, long long limit, cudaStream_t s) {
+  selftest_wait_kernel<<<1, 1, 0, s>>>(status, limit);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s) {

@@ -70,7 +70,7 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
            "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
-           "mpnet_train_step"]
+           "mpnet_train_step", "dags_selftest_timeout"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train"]
@@ -131,6 +131,8 @@ def load(path: str = LIB_PATH):
     lib.mpnet_infer.restype = ctypes.c_int
     lib.mpnet_train_step.argtypes = [P, P, P, P, P, I32, P, P, I32, I32, I32, ctypes.c_float, P, P, P]
     lib.mpnet_train_step.restype = ctypes.c_int
+    lib.dags_selftest_timeout.argtypes = [P, I64, P]
+    lib.dags_selftest_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -392,6 +394,11 @@ class Context:
                                          _ptr(feats), _ptr(target), B, W, H, float(lr), _ptr(loss), _ptr(grad),
                                          _stream()), "mpnet_train_step")
         return loss
+
+    def selftest_timeout(self, spins: int = 1000):
+        """Run the failure-path self-test (a bounded wait that runs out); the
+        next check() raises with DAGS_E_TIMEOUT."""
+        _check(self.lib.dags_selftest_timeout(self.h, int(spins), _stream()), "dags_selftest_timeout")
 
     def pose_step(self, poses, grad_pose, adam_state, cfg=None):
         _need(poses, torch.float64, "poses")
