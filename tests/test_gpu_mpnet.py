@@ -239,3 +239,35 @@ def test_train_reduces_loss_and_agrees_with_oracle(dags):
     grad = torch.empty(10881, dtype=torch.float32, device="cuda")
     last = ctx.mpnet_train_step(wt, master, m, v, 301, feats, tg, 0.0, grad=grad).item()
     assert last == pytest.approx(L, rel=1e-3)
+
+
+def test_train_gradients_full_frame(dags):
+    # one 640 x 480 frame in the launch configuration of the training step
+    # (persistent CTAs over 2400 tiles, several tiles per CTA)
+    B, H, W = 1, 480, 640
+    rng = np.random.default_rng(77)
+    p = random_params(14)
+    x = N.bf16_round(rng.uniform(0, 1, (B, H, W, 8)))
+    target = random_targets(rng, (B, H, W))
+    wt, master, m, v, feats, tg = train_setup(p, x, target)
+    grad = torch.empty(10881, dtype=torch.float32, device="cuda")
+    ctx = dags.Context(16, 16, 16, 1)
+    loss = ctx.mpnet_train_step(wt, master, m, v, 1, feats, tg, 0.0, grad=grad)
+    torch.cuda.synchronize()
+    ctx.check()
+    L, g, _ = N.loss_and_grads(x, target, p)
+    assert loss.item() == pytest.approx(L, rel=1e-4)
+    errs = group_errors(grad.cpu().numpy().astype(np.float64), to_vec(g))
+    assert max(errs.values()) <= GRAD_REL, errs
+
+
+def test_inference_is_deterministic(dags):
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 1, (2, 48, 300, 8)).astype(np.float32)
+    feats = to_bf16_tensor(x)
+    wt = torch.from_numpy(weight_blob(random_params(5))).cuda()
+    ctx = dags.Context(16, 16, 16, 1)
+    a = ctx.mpnet_infer(wt, feats).clone()
+    b = ctx.mpnet_infer(wt, feats)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)

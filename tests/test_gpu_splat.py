@@ -303,3 +303,21 @@ def test_invalid_colour_pixels_leave_the_loss(dags):
     g = compare_grads(res["gg"], outs[0]["grad"])
     for k, v in g.items():
         assert v <= GRAD_NORM, k
+
+
+def test_forward_is_deterministic(dags):
+    # the forward has no order-dependent reduction: depth keys with id
+    # tie-breaks, per-pixel compositing, fixed-order FP64 loss
+    from paper_2602_21644_gb300 import synth
+    sc = synth.tracking_scene(60_000, frame=7, width=320, height=240)
+    cam = dags.Camera(*sc.camera.as_tuple())
+    gauss = torch.from_numpy(sc.records).cuda()
+    poses = torch.from_numpy(np.ascontiguousarray(sc.poses)).cuda()
+    targets = torch.from_numpy(sc.targets).cuda()
+    ctx = dags.Context(gauss.shape[0], cam.width, cam.height, 1)
+    i1, l1, s1 = [t.clone() for t in ctx.forward(gauss, cam, poses, targets)]
+    i2, l2, s2 = ctx.forward(gauss, cam, poses, targets)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert torch.equal(i1, i2) and torch.equal(l1, l2) and torch.equal(s1, s2)
+    ctx.close()
