@@ -413,9 +413,11 @@ def run_ours(args):
                 "alg_bytes_per_launch": ab[dom]}
     iter_bytes = sum(ab.values())
     iter_us = 1e3 * t_ms / (args.iters * args.steps)
-    # kernels per step: per iteration preprocess, emit, render_fwd, render_bwd,
-    # preprocess_bwd (pose step fused); per frame the MP update's 8 kernels
-    gpu_launches = args.steps * (args.iters * 5 + 8)
+    # kernels per step: per iteration preprocess, tile scan, emit, render_fwd,
+    # render_bwd, preprocess_bwd (pose step fused); per frame the MP update's 8
+    # kernels (pixel sum, pixel var, gauss, apply, 2 select levels, labels,
+    # region stats)
+    gpu_launches = args.steps * (args.iters * 6 + 8)
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
