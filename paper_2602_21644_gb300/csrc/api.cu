@@ -259,6 +259,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   w.max_tiles = ((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
   w.max_pairs = max_pairs;
   w.bwd_prep_blocks = (int)((w.max_n + kBwdPrepBlock - 1) / kBwdPrepBlock);
+  w.band = c->num_sms;
   const size_t vn = (size_t)w.max_v * (size_t)w.max_n;
   const size_t vt = (size_t)w.max_v * (size_t)w.max_tiles;
   cudaError_t e = cudaSuccess;
@@ -801,6 +802,11 @@ extern "C" int splat_forward_static(const float *gauss, int64_t n, const dags_ca
   w.max_v = 1;
   w.max_tiles = kStaticTiles;
   w.max_pairs = kStaticMaxPairs;
+  {
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      w.band = sms;
+  }
   w.tile_count = reinterpret_cast<uint32_t *>(base + kOffCount);
   w.tile_cursor = reinterpret_cast<uint32_t *>(base + kOffCursor);
   w.vis_append = reinterpret_cast<uint32_t *>(base + kOffVisAppend);

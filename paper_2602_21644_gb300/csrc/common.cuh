@@ -54,6 +54,7 @@ struct Workspace {
   int max_w = 0, max_h = 0, max_v = 0, max_tiles = 0;
   int64_t max_pairs = 0;
   int bwd_prep_blocks = 0;
+  int band = 1;                   // CTAs per dispatch round of the renders (the SM count)
   float4 *rec2d = nullptr;        // [V][N][3], see above
   uint2 *rect = nullptr;          // [V][N]: {x0 | x1 << 16, y0 | y1 << 16}, candidate tiles [x0, x1) x [y0, y1)
   float *grad2d = nullptr;        // [V][N][kGradWords]
@@ -63,7 +64,7 @@ struct Workspace {
   uint64_t *keys = nullptr;       // [max_pairs]: depth bits << 32 | Gaussian id
   uint64_t *keys_tmp = nullptr;   // [max_pairs]: merge ping-pong
   uint32_t *sorted_ids = nullptr; // [max_pairs]
-  uint32_t *tile_order = nullptr; // [V * T] tiles by descending list length (launch order of the renders)
+  uint32_t *tile_order = nullptr; // [V * T] launch order of the renders (length-ranked, band-reversed)
   float *loss_partial = nullptr;  // [V * T]
   double *pose_partial = nullptr; // [bwd_prep_blocks][V][6]
   float *pose32 = nullptr;        // [V][12] FP32 copy of the poses of the last forward

@@ -42,21 +42,31 @@ __device__ __forceinline__ int clampi(float x, int lo, int hi) {
 // shared-memory stage of kScanChunk counts (coalesced loads, then each thread
 // scans a contiguous slice and the slice sums are scanned across the CTA).
 // Also clears the counts and cursors for the next call, and writes order[]:
-// the tiles by descending list length (coarsely, by floor(log2(length));
-// empty tiles last), the launch order of the renders so that long tiles
-// start first. Returns the sum.
+// the launch order of the renders. Tiles are ranked by descending list
+// length (bins of 8 entries; empty tiles last), and each band of `band`
+// consecutive ranks (one CTA per SM in a dispatch round) is reversed every
+// other band, so that the SM that receives a band's longest tile receives the
+// next band's shortest one. Returns the sum.
 constexpr int kScanChunk = 4096;
+constexpr int kLenBins = 257;   // 256 length bins (descending) + empty tiles
 
-__device__ __forceinline__ int length_bin(uint32_t c) { return c ? 31 - __clz(c) : 32; }
+__device__ __forceinline__ int length_bin(uint32_t c) { return c ? 255 - (int)min(c >> 3, 255u) : 256; }
+
+// Slot of rank `pos` in the band-reversed ("snake") order of `total` ranks.
+__device__ __forceinline__ uint32_t snake_slot(uint32_t pos, uint32_t total, uint32_t band) {
+  const uint32_t b = pos / band, q = pos - b * band, base = b * band;
+  const uint32_t width = min(band, total - base);
+  return base + ((b & 1u) ? width - 1u - q : q);
+}
 
 __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total,
-                                     uint32_t *order) {
+                                     uint32_t *order, int band) {
   __shared__ uint32_t s_c[kScanChunk];
   __shared__ unsigned long long warp_tot[32];
   __shared__ unsigned long long s_carry;
-  __shared__ uint32_t s_bin[34];
+  __shared__ uint32_t s_bin[kLenBins];
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  if (tid < 34) s_bin[tid] = 0u;
+  for (int k = tid; k < kLenBins; k += blockDim.x) s_bin[k] = 0u;
   if (tid == 0) s_carry = 0ull;
   __syncthreads();
   // pass 1: length bins
@@ -64,21 +74,40 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
     const int n = min(kScanChunk, total - c0);
     for (int k0 = 0; k0 < n; k0 += blockDim.x) {
       const int k = k0 + tid;
-      int bin = 64 + lane;   // no element: a key of its own
+      int bin = 1024 + lane;   // no element: a key of its own
       if (k < n) {
         const uint32_t c = __ldcg(count + c0 + k);
         s_c[k] = c;
         bin = length_bin(c);
       }
       const unsigned grp = __match_any_sync(0xffffffffu, bin);
-      if (bin < 64 && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+      if (bin < kLenBins && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
     }
     __syncthreads();
   }
-  if (tid == 0) {
-    uint32_t run = 0;   // descending length: bins 31 .. 0, then empty (32)
-    for (int bb = 31; bb >= 0; --bb) { const uint32_t c = s_bin[bb]; s_bin[bb] = run; run += c; }
-    s_bin[32] = run;
+  if (wid == 0) {
+    // exclusive prefix over the bins (ascending bin = descending length):
+    // lane l takes the bins [9 l, 9 l + 9)
+    uint32_t loc[9], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int bb = 9 * lane + j;
+      loc[j] = bb < kLenBins ? s_bin[bb] : 0u;
+      sum += loc[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int bb = 9 * lane + j;
+      if (bb < kLenBins) s_bin[bb] = run;
+      run += loc[j];
+    }
   }
   __syncthreads();
   // pass 2: offsets, order, clearing
@@ -113,20 +142,20 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
     unsigned long long run = s_carry + (wid > 0 ? warp_tot[wid - 1] : 0ull) + inc - mine;
     for (int j = 0; j < per; ++j) {
       const int k = b + j;
-      int bin = 64 + lane;   // no element: a key of its own
+      int bin = 1024 + lane;   // no element: a key of its own
       if (k < e) {
         const uint32_t c = s_c[k];
         start[c0 + k] = (uint32_t)(run > 0xFFFFFFFFull ? 0xFFFFFFFFull : run);
         run += c;
         bin = length_bin(c);
       }
-      // slot in the launch order: one shared atomic per distinct bin per warp
+      // rank in the length order: one shared atomic per distinct bin per warp
       const unsigned grp = __match_any_sync(0xffffffffu, bin);
       const int leader = __ffs(grp) - 1;
-      uint32_t slot = 0;
-      if (bin < 64 && lane == leader) slot = atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
-      slot = __shfl_sync(0xffffffffu, slot, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
-      if (k < e) order[slot] = (uint32_t)(c0 + k);
+      uint32_t pos = 0;
+      if (bin < kLenBins && lane == leader) pos = atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+      pos = __shfl_sync(0xffffffffu, pos, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+      if (k < e) order[snake_slot(pos, (uint32_t)total, (uint32_t)band)] = (uint32_t)(c0 + k);
     }
     for (int k = tid; k < n; k += blockDim.x) {
       count[c0 + k] = 0u;
@@ -290,7 +319,8 @@ constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads)
 tile_scan_kernel(Workspace ws, int views, Raster r) {
-  const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T, ws.tile_order);
+  const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T, ws.tile_order,
+                                          ws.band > 0 ? ws.band : 1);
   for (int k = threadIdx.x; k < views; k += blockDim.x) {
     ws.vis_n[k] = ws.vis_append[k];
     ws.vis_append[k] = 0u;
