@@ -1,25 +1,26 @@
 // Learned per-pixel MP proposal network on the 5th-generation tensor cores
 // (tcgen05, sm_103a): BF16 operands staged in shared memory, FP32
-// accumulators in tensor memory (TMEM), one elected thread issuing the MMAs,
-// completion tracked by an mbarrier.
+// accumulators in tensor memory (TMEM), one elected thread per warpgroup
+// issuing the MMAs, completion tracked by mbarriers, inputs fetched by TMA or
+// cp.async.
 //
 // Network (per pixel, NHWC): z1 = W1 x + b1 (1x1, 8 -> 32), a1 = bf16(relu);
 // z2 = conv3x3(a1) + b2 (32 -> 32, zero pad), a2 = bf16(relu); z3 = W3 a2 +
 // b3, a3 = bf16(relu); y = sigmoid(w4 . a3 + b4).
 //
-// mpnet_fwd_kernel: persistent, one CTA (4 warps) per SM; a tile is 128
-// consecutive pixels of one image row. Per tile:
-//   1. the 3 x 130 halo pixels' inputs (8 channels, padded to K = 16) are
-//      staged as a K-major operand; 4 MMAs (M = 128, N = 32, K = 16) give z1;
-//   2. the epilogue applies bias, ReLU and BF16 rounding (zero outside the
-//      image: the convolution pads a1 with zeros) into a halo buffer, from
-//      which the im2col operand (128 x 288) is gathered; 18 MMAs give z2;
-//   3. a2 is staged (128 x 32); 2 MMAs give z3;
-//   4. the last epilogue computes a3, the 32-term dot product with w4 and
-//      the sigmoid in FP32 and writes y (and, for training, a1 a2 a3).
-// Shared-memory operands use the canonical no-swizzle K-major layout: 8x16-
-// byte core matrices, row groups of 8 rows, LBO = 128 B between core
-// matrices along K, SBO = (K / 8) * 128 B between row groups.
+// mpnet_fwd_kernel   inference (and the training forward): four warpgroups
+//                    per CTA walk 128-pixel column strips row by row in a
+//                    three-stage software pipeline (see its comment).
+// mpnet_bwd1_kernel  training: BCE gradient, dz3, da2 = dz3 W3 and dz2; the
+//                    weight gradients dW3, dw4 accumulated in TMEM.
+// mpnet_bwd2_kernel  training: da1 by the transposed 3x3 convolution, dz1;
+//                    dW2 per tap and dW1 accumulated in TMEM.
+// mpnet_adam_kernel  Adam on the FP32 master weights, BF16 blob refresh.
+//
+// Weights are staged once per CTA in the canonical no-swizzle K-major
+// layout (8x16-byte core matrices, LBO = 128 B between core matrices along K,
+// SBO = (K / 8) * 128 B between 8-row groups); activations use the
+// row-contiguous chunk layout described at the forward kernel.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
