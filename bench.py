@@ -146,10 +146,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+MAX_FRAMES = 50   # frames 10-59 of the 60-frame sequence
+
+
 def workload_config(args):
-    return {"workload": f"tracking frame of the synthetic room: {args.gaussians} Gaussians, "
-                        f"{args.width}x{args.height} RGB-D, {args.iters} pose-only fwd+bwd iterations "
-                        f"with FP64 pose steps and one MP update per step",
+    F = max(1, min(args.steps, MAX_FRAMES))
+    return {"workload": f"tracking frames 10-{9 + F} of a synthetic room sequence (two objects at 0.3 m/s, "
+                        f"30 Hz): {args.gaussians} Gaussians, {args.width}x{args.height} RGB-D, {args.iters} "
+                        f"pose-only fwd+bwd iterations with FP64 pose steps and one MP update per frame (step)",
             "gaussians": args.gaussians, "width": args.width, "height": args.height,
             "iters_per_step": args.iters,
             "l2": "flushed between steps by a 256 MiB write; inside a step the iterations re-read the "
@@ -270,14 +274,23 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    sc = synth.tracking_scene(args.gaussians, frame=10, width=args.width, height=args.height)
-    cam = dags.Camera(*sc.camera.as_tuple())
-    n = sc.records.shape[0]
+    # frames 10 .. 10 + F - 1 of the sequence; step k tracks frame k mod F
+    # (its RGB-D target, instance prior and starting pose, all resident on
+    # the device and copied into the working buffers as the step begins)
+    F = max(1, min(args.steps, MAX_FRAMES))
+    records, scam, seq, sx = synth.tracking_sequence(args.gaussians, frames=range(10, 10 + F), width=args.width,
+                                                     height=args.height)
+    cam = dags.Camera(*scam.as_tuple())
+    n = records.shape[0]
     P = cam.width * cam.height
-    gauss = torch.from_numpy(sc.records).to(dev)
-    pose0 = torch.from_numpy(np.ascontiguousarray(sc.poses)).to(dev)
-    targets = torch.from_numpy(np.ascontiguousarray(sc.targets)).to(dev)
-    poses = pose0.clone()
+    gauss = torch.from_numpy(records).to(dev)
+    tg_all = torch.from_numpy(np.stack([f["target"] for f in seq])[:, None]).to(dev)       # F x 1 x P x 4
+    pose_all = torch.from_numpy(np.stack([f["pose"] for f in seq])[:, None]).to(dev)      # F x 1 x 3 x 4
+    inst_all = torch.from_numpy(np.stack([f["instance"] for f in seq])).to(dev)           # F x P
+    targets = tg_all[0].clone()
+    poses = pose_all[0].clone()
+    inst = inst_all[0].clone()
+    fidx = [0]
     state = torch.zeros((1, 13), dtype=torch.float64, device=dev)
     image = torch.empty((1, dags.IMG_CHANNELS, cam.height, cam.width), dtype=torch.float32, device=dev)
     last = torch.empty((1, cam.height, cam.width), dtype=torch.int32, device=dev)
@@ -286,14 +299,17 @@ def run_ours(args):
     ctx = dags.Context(n, cam.width, cam.height, 1)
     pcfg = dags.default_pose_cfg(lr=[1e-3, 1e-3, 1e-3, 5e-4, 5e-4, 5e-4])
     # per-frame MP update inputs: the frame's instance prior and class table
-    inst = torch.from_numpy(sc.extra["instance"]).to(dev)
-    table = torch.tensor([[0.1, 0.05]] + [[0.9, 0.8]] * sc.extra["n_instances"], dtype=torch.float32, device=dev)
+    table = torch.tensor([[0.1, 0.05]] + [[0.9, 0.8]] * sx["n_instances"], dtype=torch.float32, device=dev)
     labels = torch.zeros(n, dtype=torch.uint8, device=dev)
     mp_stats = torch.empty(dags.MP_STATS_HEAD + 4 * table.shape[0], dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def frame(use_graph=True):
-        poses.copy_(pose0)
+        k = fidx[0] % F
+        fidx[0] += 1
+        targets.copy_(tg_all[k])
+        poses.copy_(pose_all[k])
+        inst.copy_(inst_all[k])
         state.zero_()
         ctx.track(gauss, cam, poses, targets, args.iters, state, image, last, loss, gpose, pcfg=pcfg,
                   use_graph=use_graph)
@@ -348,14 +364,18 @@ def run_ours(args):
     # e2e: public API with host buffers; every step copies the frame (RGB-D
     # target) and the starting pose from pinned host memory and reads back the
     # refined pose and the loss
-    tg_host = torch.from_numpy(np.ascontiguousarray(sc.targets)).pin_memory()
-    pose_host = torch.from_numpy(np.ascontiguousarray(sc.poses)).pin_memory()
-    pose_out = torch.empty_like(pose_host).pin_memory()
+    tg_host = torch.from_numpy(np.stack([f["target"] for f in seq])[:, None]).pin_memory()
+    pose_host = torch.from_numpy(np.stack([f["pose"] for f in seq])[:, None]).pin_memory()
+    inst_host = torch.from_numpy(np.stack([f["instance"] for f in seq])).pin_memory()
+    pose_out = torch.empty_like(pose_host[0]).pin_memory()
     loss_out = torch.empty(1, dtype=torch.float64).pin_memory()
 
     def frame_e2e():
-        targets.copy_(tg_host, non_blocking=True)
-        poses.copy_(pose_host, non_blocking=True)
+        k = fidx[0] % F
+        fidx[0] += 1
+        targets.copy_(tg_host[k], non_blocking=True)
+        poses.copy_(pose_host[k], non_blocking=True)
+        inst.copy_(inst_host[k], non_blocking=True)
         state.zero_()
         ctx.track(gauss, cam, poses, targets, args.iters, state, image, last, loss, gpose, pcfg=pcfg)
         ctx.mp_update(gauss, cam, poses, targets, image, inst, table, labels, stats=mp_stats)
@@ -363,7 +383,7 @@ def run_ours(args):
         loss_out.copy_(loss, non_blocking=True)
 
     t_e2e = max_over_ranks(timed(args.steps, frame_e2e), world, dev)
-    h2d = tg_host.numel() * 4 + pose_host.numel() * 8
+    h2d = tg_host[0].numel() * 4 + pose_host[0].numel() * 8 + inst_host[0].numel()
     d2h = pose_out.numel() * 8 + 8
 
     learned = learned_mp_section(args, ctx, dags, synth, image, targets, inst, table, cam, flush, stream)

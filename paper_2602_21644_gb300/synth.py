@@ -363,16 +363,10 @@ def mapping_scene(n: int = 200_000, views: int = 8, seed: int = 0, width: int = 
     return Scene(rec, cam, np.stack(poses), np.stack(tgs), oid >= 0, dict(objects=objs, object_id=oid))
 
 
-def tracking_scene(n: int = 300_000, frame: int = 10, seed: int = 0, width: int = 640, height: int = 480,
-                   fps: float = 30.0, flip: float = 0.05) -> Scene:
-    """Tracking + MP update: the map holds the objects at their frame-0
-    positions; the target of `frame` is ray-cast with the two moving objects
-    translated at 0.3 m/s; the pose is the previous frame's (the tracking
-    starting point) and extra['gt_pose'] the frame's own. Also returns the
-    instance label map of the moving objects with `flip` pixel flip noise."""
-    rec, oid, objs = room_scene(n, seed)
-    cam = room_camera(width, height)
-    path = camera_path(frame + 1, fps)
+def _tracking_frame(cam: Camera, objs, path, frame: int, seed: int, fps: float, flip: float):
+    """Observed RGB-D of `frame` (moving objects translated), the instance
+    label map of the moving objects with `flip` pixel flip noise, and the
+    previous frame's pose (the tracking starting point)."""
     rng = np.random.default_rng(seed + 7 + frame)
     tg, hit = raycast(cam, path[frame], objs, frame / fps, 0.01, rng)
     tg[(tg[:, 3] < 0.5) | (tg[:, 3] > 5.0), 3] = 0.0
@@ -387,8 +381,40 @@ def tracking_scene(n: int = 300_000, frame: int = 10, seed: int = 0, width: int 
         repl[same] = (repl[same] + 1) % (len(moving) + 1)
         inst = np.where(fl, repl, inst).astype(np.uint8)
     prev = path[frame - 1] if frame > 0 else path[0]
+    return tg, inst, prev, path[frame], moving
+
+
+def tracking_scene(n: int = 300_000, frame: int = 10, seed: int = 0, width: int = 640, height: int = 480,
+                   fps: float = 30.0, flip: float = 0.05) -> Scene:
+    """Tracking + MP update: the map holds the objects at their frame-0
+    positions; the target of `frame` is ray-cast with the two moving objects
+    translated at 0.3 m/s; the pose is the previous frame's (the tracking
+    starting point) and extra['gt_pose'] the frame's own. Also returns the
+    instance label map of the moving objects with `flip` pixel flip noise."""
+    rec, oid, objs = room_scene(n, seed)
+    cam = room_camera(width, height)
+    path = camera_path(frame + 1, fps)
+    tg, inst, prev, gt, moving = _tracking_frame(cam, objs, path, frame, seed, fps, flip)
     return Scene(rec, cam, prev[None], tg[None], np.isin(oid, moving),
-                 dict(objects=objs, object_id=oid, gt_pose=path[frame], instance=inst, n_instances=len(moving)))
+                 dict(objects=objs, object_id=oid, gt_pose=gt, instance=inst, n_instances=len(moving)))
+
+
+def tracking_sequence(n: int = 300_000, frames=range(10, 60), seed: int = 0, width: int = 640, height: int = 480,
+                      fps: float = 30.0, flip: float = 0.05):
+    """The tracking workload over several frames of one sequence: one map
+    (records, camera) and, per frame, dict(target, instance, pose (the
+    previous frame's: the starting point), gt_pose). Each frame equals
+    tracking_scene(n, frame, seed, ...)'s."""
+    rec, oid, objs = room_scene(n, seed)
+    cam = room_camera(width, height)
+    frames = list(frames)
+    path = camera_path(max(frames) + 1, fps)
+    out = []
+    moving = []
+    for f in frames:
+        tg, inst, prev, gt, moving = _tracking_frame(cam, objs, path, f, seed, fps, flip)
+        out.append(dict(frame=f, target=tg, instance=inst, pose=prev, gt_pose=gt))
+    return rec, cam, out, dict(objects=objs, object_id=oid, n_instances=len(moving))
 
 
 # ------------------------------------------------------------------ learned MP network
