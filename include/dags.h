@@ -63,7 +63,8 @@ enum {
   DAGS_E_CAPACITY = -3,  /* tile/Gaussian pairs exceeded the ctx's max_pairs  */
   DAGS_E_TIMEOUT = -4,   /* a bounded device wait gave up                     */
   DAGS_E_NOMEM = -5,     /* workspace allocation failed                       */
-  DAGS_E_ORDER = -6      /* splat_backward without its matching splat_forward */
+  DAGS_E_ORDER = -6,     /* splat_backward without its matching splat_forward */
+  DAGS_E_BOUNDS = -7     /* a DAGS_CHECK build found an index out of range    */
 };
 
 typedef struct dags_ctx dags_ctx;

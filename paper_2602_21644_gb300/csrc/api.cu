@@ -229,6 +229,7 @@ const char *dags_status_string(int code) {
     case DAGS_E_TIMEOUT: return "a bounded device wait gave up";
     case DAGS_E_NOMEM: return "workspace allocation failed";
     case DAGS_E_ORDER: return "splat_backward does not follow its splat_forward on this context";
+    case DAGS_E_BOUNDS: return "an index check of a DAGS_CHECK build failed (the access was skipped)";
     default: return "unknown status";
   }
 }
@@ -343,6 +344,7 @@ int dags_sync_status(dags_ctx *ctx, int64_t *required_pairs) {
   }
   if (st & kStatusCapacity) return DAGS_E_CAPACITY;
   if (st & kStatusTimeout) return DAGS_E_TIMEOUT;
+  if (st & kStatusBounds) return DAGS_E_BOUNDS;
   return DAGS_OK;
 }
 
@@ -602,7 +604,7 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
   const int ev = ctx->timer.begin(DAGS_K_MP_GAUSS, s);
   const cudaError_t e = launch_mp_update(ctx->mp, gauss, n, pose, r, reinterpret_cast<const float4 *>(targets),
                                          image, inst, table, n_regions, c, seg_refreshed ? 1 : 0, labels, stats,
-                                         mp_map, mp_pixel, s);
+                                         mp_map, mp_pixel, ctx->ws.counters + CNT_STATUS, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }
@@ -621,7 +623,7 @@ int mpnet_features(dags_ctx *ctx, const float *image, const float *targets, cons
   ctx->last_stream = s;
   const int ev = ctx->timer.begin(DAGS_K_MPNET, s);
   const cudaError_t e = launch_mpnet_features(image, reinterpret_cast<const float4 *>(targets), inst, table,
-                                              n_regions, (int)P, feats, s);
+                                              n_regions, (int)P, feats, ctx->ws.counters + CNT_STATUS, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

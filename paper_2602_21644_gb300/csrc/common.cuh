@@ -20,6 +20,21 @@ constexpr int kBwdPoseBlocks = 304;     // CTAs of the pose-only preprocess back
 // Status word bits (device).
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
+constexpr uint32_t kStatusBounds = 4u;
+
+// Index checks of a DAGS_CHECK build (nvcc -DDAGS_CHECK=1): a failed check
+// records kStatusBounds in the status word and the access is skipped (the
+// caller takes the `false` branch). In the normal build the checks compile
+// away to `true`.
+#ifdef DAGS_CHECK
+__device__ __forceinline__ bool dags_in_bounds(bool ok, uint32_t *status) {
+  if (!ok) atomicOr(status, kStatusBounds);
+  return ok;
+}
+#define DAGS_IN_BOUNDS(cond, status) dags_in_bounds((cond), (status))
+#else
+#define DAGS_IN_BOUNDS(cond, status) true
+#endif
 
 // 2D gradient slots per (view, Gaussian).
 enum { G2_U = 0, G2_V, G2_A, G2_B, G2_C, G2_Z, G2_O, G2_R, G2_G, G2_BL };
@@ -139,9 +154,10 @@ struct MpBuffers {
 cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
-                             double *stats, const float *mp_map, float *mp_pixel, cudaStream_t s);
+                             double *stats, const float *mp_map, float *mp_pixel, uint32_t *status,
+                             cudaStream_t s);
 cudaError_t launch_mpnet_features(const float *image, const float4 *targets, const uint8_t *inst, const float *table,
-                                  int n_regions, int P, uint16_t *feats, cudaStream_t s);
+                                  int n_regions, int P, uint16_t *feats, uint32_t *status, cudaStream_t s);
 
 // ---- device helpers ----
 

@@ -51,7 +51,17 @@ struct MpWs {
   double *stats;         // caller's output
   const float *mp_map;   // [P] external per-pixel MP replacing M_p, or null
   float *mp_pixel;       // [P] out: the fused M_p, or null
+  uint32_t *status;      // the ctx's status word (index checks of a DAGS_CHECK build)
 };
+
+// The region of pixel p (its instance label; checked against the table size
+// in a DAGS_CHECK build, where an out-of-range label counts as background).
+__device__ __forceinline__ int region_of(const uint8_t *inst, size_t p, int n_regions, uint32_t *status) {
+  int k = inst[p];
+  if (!DAGS_IN_BOUNDS(k < n_regions, status)) k = 0;
+  (void)status;
+  return k;
+}
 
 // Order-preserving map of floats to uint32 (for atomic min/max of values
 // that may be slightly negative).
@@ -88,7 +98,7 @@ mp_pixel_sum_kernel(MpWs m, const float4 *__restrict__ targets, const float *__r
   if (p < P) {
     const float e = residual(targets[p], image, (size_t)P, (size_t)p, c.kappa_c);
     m.e[p] = e;
-    const int k = inst[p];
+    const int k = region_of(inst, p, c.n_regions, m.status);
     atomicAdd(&s_cnt[k], 1.f);
     atomicAdd(&s_sum[k], e);
   }
@@ -111,7 +121,7 @@ mp_pixel_var_kernel(MpWs m, const uint8_t *__restrict__ inst, int P, MpCfg c) {
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < P) {
-    const int k = inst[p];
+    const int k = region_of(inst, p, c.n_regions, m.status);
     const float d = m.e[p] - s_mean[k];
     atomicAdd(&s_sq[k], d * d);
   }
@@ -153,7 +163,7 @@ mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__re
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p < P) {
-    const int k = inst[p];
+    const int k = region_of(inst, p, c.n_regions, m.status);
     m.mp_pixel[p] = pixel_mp(m.e[p], s_reg[k], s_tab[k], c.fusion_mode);
   }
 }
@@ -197,7 +207,7 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
             if (d2 > rs2) continue;
             const size_t p = (size_t)jj * r.W + ii;
             const float e = m.e[p];
-            const int k = inst[p];
+            const int k = region_of(inst, p, c.n_regions, m.status);
             const float mp = m.mp_map ? __ldg(m.mp_map + p) : pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
             const float w = expf(-d2 * inv2s2);
             sw += w; swm += w * mp; sm += mp; se += e; ++cnt;
@@ -215,7 +225,7 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
             if (dx * dx + dy * dy > rs2) continue;
             const size_t p = (size_t)jj * r.W + ii;
             const float e = m.e[p];
-            const int k = inst[p];
+            const int k = region_of(inst, p, c.n_regions, m.status);
             const float mp = m.mp_map ? __ldg(m.mp_map + p) : pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
             vm += (mp - mm) * (mp - mm);
             ve += (e - me) * (e - me);
@@ -409,8 +419,10 @@ __global__ void mp_region_stats_kernel(MpWs m, MpCfg c) {
 cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
-                             double *stats, const float *mp_map, float *mp_pixel, cudaStream_t s) {
+                             double *stats, const float *mp_map, float *mp_pixel, uint32_t *status,
+                             cudaStream_t s) {
   MpWs m;
+  m.status = status;
   m.mp_map = mp_map;
   m.mp_pixel = mp_pixel;
   m.e = b.e; m.acc = b.acc; m.mhat = b.mhat; m.sige = b.sige; m.U = b.U; m.Mt = b.Mt; m.Ut = b.Ut;
@@ -460,7 +472,7 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float lo, float hi) {
 __global__ void __launch_bounds__(kMpBlock)
 mpnet_features_kernel(const float *__restrict__ image, const float4 *__restrict__ targets,
                       const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int n_regions, int P,
-                      uint4 *__restrict__ feats) {
+                      uint4 *__restrict__ feats, uint32_t *status) {
   __shared__ float s_mu[DAGS_MP_MAX_REGIONS];
   for (int k = threadIdx.x; k < n_regions; k += blockDim.x) s_mu[k] = table[k].x;
   __syncthreads();
@@ -471,7 +483,7 @@ mpnet_features_kernel(const float *__restrict__ image, const float4 *__restrict_
   const float cr = __ldg(image + p), cg = __ldg(image + Q + p), cb = __ldg(image + 2 * Q + p);
   const float d = __ldg(image + 3 * Q + p), o = __ldg(image + 4 * Q + p), rmp = __ldg(image + 5 * Q + p);
   const bool valid = t.w > 0.f;
-  const int k = inst[p];
+  const int k = region_of(inst, p, n_regions, status);
   feats[p] = make_uint4(bf16x2_bits(rmp, fabsf(t.x - cr)), bf16x2_bits(fabsf(t.y - cg), fabsf(t.z - cb)),
                         bf16x2_bits(valid ? fabsf(t.w - d) : 0.f, valid ? t.w : 0.f), bf16x2_bits(o, s_mu[k]));
 }
@@ -479,10 +491,11 @@ mpnet_features_kernel(const float *__restrict__ image, const float4 *__restrict_
 }  // namespace
 
 cudaError_t launch_mpnet_features(const float *image, const float4 *targets, const uint8_t *inst, const float *table,
-                                  int n_regions, int P, uint16_t *feats, cudaStream_t s) {
+                                  int n_regions, int P, uint16_t *feats, uint32_t *status, cudaStream_t s) {
   if (P <= 0) return cudaSuccess;
   mpnet_features_kernel<<<(P + kMpBlock - 1) / kMpBlock, kMpBlock, 0, s>>>(
-      image, targets, inst, reinterpret_cast<const float2 *>(table), n_regions, P, reinterpret_cast<uint4 *>(feats));
+      image, targets, inst, reinterpret_cast<const float2 *>(table), n_regions, P, reinterpret_cast<uint4 *>(feats),
+      status);
   return cudaGetLastError();
 }
 

@@ -91,8 +91,9 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   for (int end = kmax; end > 0; end -= kTilePix) {
     const int beg = max(0, end - kTilePix);
     __syncthreads();
-    if (beg + tid < end) {
-      const uint32_t id = ws.sorted_ids[s + beg + tid];
+    if (beg + tid < end && DAGS_IN_BOUNDS((uint64_t)s + beg + tid < (uint64_t)ws.max_pairs, ws.counters + CNT_STATUS)) {
+      uint32_t id = ws.sorted_ids[s + beg + tid];
+      if (!DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n, ws.counters + CNT_STATUS)) id = 0;
       const size_t slot = vbase + id;
       s_id[tid] = id;
       s_a[tid] = ws.rec2d[slot * 3 + 0];
@@ -342,7 +343,8 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       const int64_t nv = ws.vis_n[v];
       const uint32_t *vis = ws.vis_ids + (size_t)v * ws.max_n;
       for (int64_t k = (int64_t)blockIdx.x * blockDim.x + tid; k < nv; k += (int64_t)nb * blockDim.x) {
-        const int64_t i = vis[k];
+        int64_t i = vis[k];
+        if (!DAGS_IN_BOUNDS(i >= 0 && i < n, ws.counters + CNT_STATUS)) continue;
         const float4 g0 = __ldg(gauss + 4 * i + 0), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
         chain_one<false>(ws, r, g0, g1, g2, sp + v * 12, (size_t)v * ws.max_n + i, pg, nullptr);
       }

@@ -476,8 +476,9 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   for (uint32_t base = s; base < e; base += kTilePix) {
     if (__syncthreads_count(!done) == 0) break;
     const uint32_t k = base + tid;
-    if (k < e) {
-      const size_t slot = vbase + (own_sort ? (uint32_t)s_key[k - s] : ws.sorted_ids[k]);
+    const uint32_t id = k < e ? (own_sort ? (uint32_t)s_key[k - s] : ws.sorted_ids[k]) : 0u;
+    if (k < e && DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n && k < (uint64_t)ws.max_pairs, ws.counters + CNT_STATUS)) {
+      const size_t slot = vbase + id;
       s_a[tid] = ws.rec2d[slot * 3 + 0];
       s_b[tid] = ws.rec2d[slot * 3 + 1];
       s_c[tid] = ws.rec2d[slot * 3 + 2];

@@ -24,7 +24,7 @@ GRAD_POSE = 2
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA runtime error", -3: "pair capacity exceeded",
           -4: "device wait timed out", -5: "workspace allocation failed",
-          -6: "backward does not follow its forward"}
+          -6: "backward does not follow its forward", -7: "index check failed (DAGS_CHECK build)"}
 
 
 class DagsError(RuntimeError):
