@@ -260,6 +260,61 @@ def learned_mp_section(args, ctx, dags, synth, image, targets, inst, table, cam,
             "train_step_us": round(t_tr, 2), "gpu_launches_infer": 1, "gpu_launches_train": 6}
 
 
+def splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, flush, stream):
+    """The other two splatting workloads, each timed with CUDA events around
+    direct launches, L2 flushed before every timed iteration:
+    - the full-parameter fwd+bwd variant at the tracking size (one view;
+      gradients of every Gaussian parameter and of the pose);
+    - the mapping step: 200k Gaussians, 8 keyframes of 640x480, one iteration
+      = render + backward of all 8 views w.r.t. all parameters."""
+    import torch
+
+    def time_it(fn, reps=10):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    flags = dags.GRAD_GAUSS | dags.GRAD_POSE
+
+    def full_iter():
+        image, last, _ = ctx.forward(gauss, cam, poses, targets)
+        ctx.backward(gauss, cam, poses, targets, image, last, flags)
+
+    t_full = time_it(full_iter)
+    ms = synth.mapping_scene(200_000, views=8, width=args.width, height=args.height)
+    mcam = dags.Camera(*ms.camera.as_tuple())
+    mg = torch.from_numpy(ms.records).cuda()
+    mp = torch.from_numpy(np.ascontiguousarray(ms.poses)).cuda()
+    mt = torch.from_numpy(np.ascontiguousarray(ms.targets)).cuda()
+    mctx = dags.Context(mg.shape[0], mcam.width, mcam.height, ms.poses.shape[0])
+
+    def map_iter():
+        image, last, _ = mctx.forward(mg, mcam, mp, mt)
+        mctx.backward(mg, mcam, mp, mt, image, last, flags)
+
+    t_map = time_it(map_iter)
+    torch.cuda.synchronize()
+    ctx.check()
+    mctx.check()
+    mctx.close()
+    return {"full_param_fwd_bwd": {"workload": f"{gauss.shape[0]} Gaussians, {cam.width}x{cam.height}, one view, "
+                                               "gradients of all Gaussian parameters and the pose",
+                                   "ms_per_iter": round(t_full, 4), "iters_per_s": round(1e3 / t_full, 2)},
+            "mapping": {"workload": f"200000 Gaussians, 8 keyframes of {mcam.width}x{mcam.height}, render + "
+                                    "backward of all views w.r.t. all parameters",
+                        "ms_per_iter": round(t_map, 4), "iters_per_s": round(1e3 / t_map, 2)}}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -387,6 +442,7 @@ def run_ours(args):
     d2h = pose_out.numel() * 8 + 8
 
     learned = learned_mp_section(args, ctx, dags, synth, image, targets, inst, table, cam, flush, stream)
+    variants = splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, flush, stream)
 
     peaks, src = load_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -457,6 +513,7 @@ def run_ours(args):
                            "frac": round(learned["infer_tflops"] / bf16, 4),
                            "peak_source": f"{src} bf16_tflops (burst: the launch is timed alone)"}
     line["learned_mp"] = learned
+    line["splat_variants"] = variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(args, args.cpu_seconds)
     if rank == 0:
