@@ -13,7 +13,7 @@ constexpr int kTile = 16;               // tile edge in pixels
 constexpr int kTilePix = kTile * kTile; // pixels (= threads) per render CTA
 constexpr int kGradWords = 12;          // per (view, Gaussian) 2D gradient slots
 constexpr int kSortSmallCap = 1024;     // tile lists up to this length are sorted by the render CTA
-constexpr int kPrepBlock = 256;         // threads per preprocess CTA
+constexpr int kPrepBlock = 128;         // threads per preprocess / emit CTA
 constexpr int kBwdPrepBlock = 128;      // threads per preprocess-backward CTA
 constexpr int kBwdPoseBlocks = 304;     // CTAs of the pose-only preprocess backward (2 per SM)
 

@@ -245,22 +245,27 @@ __global__ void __launch_bounds__(kPrepBlock)
 preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
   __shared__ float sp[kMaxViewsSmem * 12];
+  const int v = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // the record loads are issued before the pose barrier, so that the two
+  // memory round trips overlap
+  float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
+  if (i < n) {
+    g0 = __ldg(gauss + 4 * i + 0);
+    g1 = __ldg(gauss + 4 * i + 1);
+    g2 = __ldg(gauss + 4 * i + 2);
+    g3 = __ldg(gauss + 4 * i + 3);
+  }
   for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = (float)poses[k];
   __syncthreads();
   if (blockIdx.x == 0 && blockIdx.y == 0)
     for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
 
-  const int v = blockIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   uint2 my_rect = make_uint2(0u, 0u);
   float4 my_r0 = make_float4(0.f, 0.f, 0.f, 0.f), my_r1 = my_r0;
   if (i < n) {
     const float *P = sp + v * 12;
     const size_t slot = (size_t)v * ws.max_n + i;
-    float4 g0 = __ldg(gauss + 4 * i + 0);
-    float4 g1 = __ldg(gauss + 4 * i + 1);
-    float4 g2 = __ldg(gauss + 4 * i + 2);
-    float4 g3 = __ldg(gauss + 4 * i + 3);
 
     float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
     uint2 rect = make_uint2(0u, 0u);
