@@ -161,6 +161,30 @@ cudaError_t launch_mpnet_features(const float *image, const float4 *targets, con
 
 // ---- device helpers ----
 
+// Programmatic dependent launch: the splatting kernels are launched with
+// programmatic stream serialization, so that a kernel's CTAs may be scheduled
+// while its predecessor drains; each of them waits for the predecessor's
+// memory (griddepcontrol.wait) before its first global access, which keeps
+// the stream order of all reads and writes. Without the launch attribute the
+// wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Hardware base-2 exponential and reciprocal (MUFU, flush-to-zero, about
 // 2^-22 relative error). The compositing loops take the exponential only for
 // exponents in [log2(1/255), 0] and the reciprocal of 1 - alpha in [0.01, 1].

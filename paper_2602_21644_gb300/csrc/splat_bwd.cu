@@ -28,6 +28,7 @@ template <bool FULL>
 __global__ void __launch_bounds__(kTilePix)
 render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ targets,
                   const float *__restrict__ image, const int32_t *__restrict__ last) {
+  pdl_wait();
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
   __shared__ uint32_t s_id[kTilePix];
   __shared__ int s_max;
@@ -305,6 +306,7 @@ template <bool FULL>
 __global__ void __launch_bounds__(kBwdPrepBlock)
 preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, int views, Raster r,
                       float *__restrict__ grad_gauss, double *__restrict__ grad_pose, PoseStep ps) {
+  pdl_wait();
   __shared__ float sp[kMaxViewsSmem * 12];
   __shared__ float s_red[kBwdPrepBlock / 32][6];
   __shared__ int s_last;
@@ -398,9 +400,8 @@ cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const R
                               cudaStream_t s) {
   (void)n;
   const unsigned grid = (unsigned)(views * r.T);
-  if (full) render_bwd_kernel<true><<<grid, kTilePix, 0, s>>>(ws, r, l, targets, image, last);
-  else render_bwd_kernel<false><<<grid, kTilePix, 0, s>>>(ws, r, l, targets, image, last);
-  return cudaGetLastError();
+  if (full) return launch_pdl(render_bwd_kernel<true>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last);
+  return launch_pdl(render_bwd_kernel<false>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last);
 }
 
 cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int64_t n, int views,
@@ -410,11 +411,13 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
   const unsigned gx = (unsigned)((n + kBwdPrepBlock - 1) / kBwdPrepBlock);
   unsigned grid = gx > 0 ? gx : 1u;
   if (grad_gauss) {
-    preprocess_bwd_kernel<true><<<grid, kBwdPrepBlock, 0, s>>>(ws, gauss, n, views, r, grad_gauss, grad_pose, ps);
+    return launch_pdl(preprocess_bwd_kernel<true>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,
+                      grad_gauss, grad_pose, ps);
   } else {
     // pose only: a fixed grid of kBwdPoseBlocks CTAs strides over the Gaussians
     if (grid > (unsigned)kBwdPoseBlocks) grid = kBwdPoseBlocks;
-    preprocess_bwd_kernel<false><<<grid, kBwdPrepBlock, 0, s>>>(ws, gauss, n, views, r, grad_gauss, grad_pose, ps);
+    return launch_pdl(preprocess_bwd_kernel<false>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,
+                      grad_gauss, grad_pose, ps);
   }
   return cudaGetLastError();
 }

@@ -244,6 +244,7 @@ __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r,
 __global__ void __launch_bounds__(kPrepBlock)
 preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
+  pdl_wait();
   __shared__ float sp[kMaxViewsSmem * 12];
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -324,6 +325,7 @@ constexpr int kScanThreads = 1024;
 
 __global__ void __launch_bounds__(kScanThreads)
 tile_scan_kernel(Workspace ws, int views, Raster r) {
+  pdl_wait();
   const uint64_t total = block_scan_tiles(ws.tile_count, ws.tile_start, ws.tile_cursor, views * r.T, ws.tile_order,
                                           ws.band > 0 ? ws.band : 1);
   for (int k = threadIdx.x; k < views; k += blockDim.x) {
@@ -346,6 +348,7 @@ __device__ __forceinline__ bool pairs_overflow(const Workspace &ws, int entries)
 
 __global__ void __launch_bounds__(kPrepBlock)
 emit_kernel(Workspace ws, int64_t n, Raster r) {
+  pdl_wait();
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // the pair total, the list length and this thread's list entry are loaded
@@ -419,6 +422,7 @@ __device__ void merge_runs(const uint64_t *a, int la, const uint64_t *b, int lb,
 __global__ void __launch_bounds__(kTilePix, 6)
 render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
                   float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
+  pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
   __shared__ float s_red[kTilePix / 32];
@@ -581,24 +585,24 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
   if (views > kMaxViewsSmem) return cudaErrorInvalidValue;
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
   dim3 grid(gx > 0 ? gx : 1u, (unsigned)views);
-  preprocess_kernel<<<grid, kPrepBlock, 0, s>>>(ws, gauss, n, poses, views, r, zero_grad_words);
-  tile_scan_kernel<<<1, kScanThreads, 0, s>>>(ws, views, r);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(preprocess_kernel, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, poses, views, r,
+                             zero_grad_words);
+  if (e == cudaSuccess) e = launch_pdl(tile_scan_kernel, dim3(1), dim3(kScanThreads), 0, s, ws, views, r);
+  return e;
 }
 
 cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   dim3 grid((unsigned)((n + kPrepBlock - 1) / kPrepBlock), (unsigned)views);
-  emit_kernel<<<grid, kPrepBlock, 0, s>>>(ws, n, r);
-  return cudaGetLastError();
+  return launch_pdl(emit_kernel, grid, dim3(kPrepBlock), 0, s, ws, n, r);
 }
 
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s) {
   (void)n;
-  render_fwd_kernel<<<(unsigned)(views * r.T), kTilePix, 0, s>>>(ws, views, r, l, targets, image, last, loss);
-  return cudaGetLastError();
+  return launch_pdl(render_fwd_kernel, dim3((unsigned)(views * r.T)), dim3(kTilePix), 0, s, ws, views, r, l, targets,
+                    image, last, loss);
 }
 
 }  // namespace dags
