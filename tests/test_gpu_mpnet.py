@@ -60,7 +60,8 @@ def ulp_close(a, b):
     return np.mean(np.abs(ai - bi) <= (1 << 16))
 
 
-@pytest.mark.parametrize("B,H,W", [(1, 6, 128), (2, 9, 300), (1, 3, 700)])
+@pytest.mark.parametrize("B,H,W", [(1, 6, 128), (2, 9, 300), (1, 3, 700), (1, 2, 1), (1, 1, 5), (3, 4, 17),
+                                   (1, 70, 129)])
 def test_forward_matches_oracle(dags, B, H, W):
     rng = np.random.default_rng(B * 100 + H)
     p = random_params(7)
