@@ -1,0 +1,199 @@
+"""Learned MP proposal against the method without it (used by the tests and
+the bench).
+
+Between scheduled semantic invocations (every REFRESH frames) the plain
+update reuses the last instance prior (stale) with its rate scaled by rho,
+Eq. (17). The learned network proposes the per-pixel MP from the frame's
+rendered MP, residuals, depth, opacity and the stale prior. The judge is the
+plain method itself with a fresh prior at every frame. The network is trained
+on the GPU, by the library's own kernels, on the judge's per-pixel maps of a
+training sequence, then evaluated on a held-out sequence with other
+Gaussians, other noise and other object motions.
+
+Synthetic stand-in for an indoor RGB-D sequence: the analytic room of
+synth.room_scene at 320 x 240 (f = 262.5, the 640 x 480 field of view), two
+moving ellipsoids at 0.3 m/s at 30 Hz, the map holding the objects at their
+frame-0 positions, the camera on synth.camera_path at the ground-truth pose,
+instance masks of the moving objects with 5% pixel flips.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import synth
+
+W, H, F = 320, 240, 262.5
+N_GAUSS = 80_000
+REFRESH = 10
+TABLE = np.array([[0.1, 0.05], [0.9, 0.8], [0.9, 0.8]], np.float32)
+
+
+def objects(velocities):
+    objs = synth.default_objects()
+    for ob, v in zip(objs, velocities):
+        ob.velocity = np.asarray(v, np.float64)
+    return objs
+
+
+class Sequence:
+    """Frames of the room with moving objects: observed RGB-D and noisy
+    instance masks (label k for the k-th moving object)."""
+
+    def __init__(self, seed, velocities, n_frames):
+        self.objs = objects(velocities)
+        self.rec, self.oid, _ = synth.room_scene(N_GAUSS, seed, objects=self.objs)
+        self.rec[:, 11] = 0.2                      # uninformed initial MP
+        moving = [k for k, ob in enumerate(self.objs) if np.any(ob.velocity != 0)]
+        self.dynamic = np.isin(self.oid, moving)
+        self.cam = synth.Camera(F, F, W / 2.0, H / 2.0, W, H)
+        self.poses = synth.camera_path(n_frames)
+        rng = np.random.default_rng(seed + 100)
+        self.obs, self.inst = [], []
+        for f in range(n_frames):
+            tg, hit = synth.raycast(self.cam, self.poses[f], self.objs, f / 30.0, 0.01, rng)
+            tg[(tg[:, 3] < 0.5) | (tg[:, 3] > 5.0), 3] = 0.0
+            inst = np.zeros(hit.shape, np.uint8)
+            for lab, k in enumerate(moving, start=1):
+                inst[hit == k] = lab
+            fl = rng.random(inst.shape) < 0.05
+            repl = rng.integers(0, len(moving) + 1, inst.shape).astype(np.uint8)
+            same = repl == inst
+            repl[same] = (repl[same] + 1) % (len(moving) + 1)
+            self.obs.append(tg)
+            self.inst.append(np.where(fl, repl, inst).astype(np.uint8))
+
+
+class Runner:
+    """One sequence through the library: render, MP update (judge, stale or
+    learned), network features and inference."""
+
+    def __init__(self, dags, seq):
+        self.d, self.seq = dags, seq
+        self.cam = dags.Camera(*seq.cam.as_tuple())
+        self.ctx = dags.Context(N_GAUSS, W, H, 1)
+        self.table = torch.from_numpy(TABLE).cuda()
+        self.P = W * H
+
+    def frame_inputs(self, f):
+        pose = torch.from_numpy(np.ascontiguousarray(self.seq.poses[f])[None]).cuda()
+        tg = torch.from_numpy(self.seq.obs[f]).cuda()
+        return pose, tg
+
+    def render(self, gauss, pose):
+        image, _, _ = self.ctx.forward(gauss, self.cam, pose)
+        return image[0].reshape(8, self.P).contiguous()
+
+    def fresh_map(self, gauss, pose, tg, image, f):
+        """The judge's per-pixel M_p (fresh prior) at frame f."""
+        g = gauss.clone()
+        lab = torch.zeros(N_GAUSS, dtype=torch.uint8, device="cuda")
+        out = torch.empty(self.P, dtype=torch.float32, device="cuda")
+        inst = torch.from_numpy(self.seq.inst[f]).cuda()
+        self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out)
+        return out
+
+    def run(self, mode, net=None, collect=False):
+        """mode: 'judge' (fresh prior every frame), 'stale' (the method without
+        the network), 'learned' (network proposal between refreshes)."""
+        gauss = torch.from_numpy(self.seq.rec.copy()).cuda()
+        labels = torch.zeros(N_GAUSS, dtype=torch.uint8, device="cuda")
+        hist = []
+        for f in range(len(self.seq.poses)):
+            pose, tg = self.frame_inputs(f)
+            image = self.render(gauss, pose)
+            refreshed = f % REFRESH == 0 or mode == "judge"
+            inst = torch.from_numpy(self.seq.inst[f if refreshed else f - f % REFRESH]).cuda()
+            rec = {}
+            if collect or (mode == "learned" and not refreshed):
+                feats = self.ctx.mpnet_features(image, tg, inst, self.table, self.cam)
+                rec["feats"] = feats
+            if collect:
+                rec["target"] = self.fresh_map(gauss, pose, tg, image, f)
+            mp_map = None
+            if mode == "learned" and not refreshed:
+                mp_map = self.ctx.mpnet_infer(net, rec["feats"][None]).reshape(-1)
+                rec["net"] = mp_map
+            stale_px = torch.empty(self.P, dtype=torch.float32, device="cuda")
+            self.ctx.mp_update(gauss, self.cam, pose, tg, image, inst, self.table, labels,
+                               seg_refreshed=refreshed, mp_map=mp_map, mp_pixel=stale_px)
+            rec["pixel"] = stale_px
+            rec["labels"] = labels.clone()
+            hist.append(rec)
+        torch.cuda.synchronize()
+        self.ctx.check()
+        return hist
+
+
+def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0):
+    """Adam training on the judge's maps of the runner's sequence; returns
+    (weight blob, per-step losses)."""
+    hist = runner.run("stale", collect=True)
+    feats = torch.stack([h["feats"] for h in hist])                    # [T, H, W, 8]
+    target = torch.stack([h["target"].reshape(H, W) for h in hist])    # [T, H, W]
+    blob, vec = synth.mpnet_init(seed)
+    net = torch.from_numpy(blob).cuda()
+    master = torch.from_numpy(vec).cuda()
+    m = torch.zeros_like(master)
+    v = torch.zeros_like(master)
+    gen = torch.Generator().manual_seed(seed)
+    losses = []
+    for step in range(1, steps + 1):
+        idx = torch.randperm(feats.shape[0], generator=gen)[:batch].cuda()
+        fb = feats.index_select(0, idx).contiguous()
+        tb = target.index_select(0, idx).contiguous()
+        losses.append(runner.ctx.mpnet_train_step(net, master, m, v, step, fb, tb, lr))
+    torch.cuda.synchronize()
+    runner.ctx.check()
+    return net, [l.item() for l in losses]
+
+
+def iou(a, b):
+    u = np.logical_or(a, b).sum()
+    return np.logical_and(a, b).sum() / u if u else 1.0
+
+
+def experiment(dags, steps=1000):
+    """Train on one sequence, run judge / stale / learned on the held-out one."""
+    train_seq = Sequence(seed=11, velocities=[(0.0, 0.0, 0.3), (-0.3, 0.0, 0.0)], n_frames=60)
+    tr = Runner(dags, train_seq)
+    net, losses = train_net(dags, tr, steps=steps)
+    tr.ctx.close()
+    eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=40)
+    ev = Runner(dags, eval_seq)
+    out = dict(losses=losses, judge=ev.run("judge"), stale=ev.run("stale"), learned=ev.run("learned", net=net),
+               seq=eval_seq)
+    ev.ctx.close()
+    return out
+
+
+def metrics(ex):
+    """Means over the held-out frames between refreshes: per-pixel MP against
+    the judge's map (MAE, IoU of M > 0.5) and dynamic-label IoU with the
+    judge's labels and with the ground-truth dynamic Gaussians."""
+    j, s, l = ex["judge"], ex["stale"], ex["learned"]
+    gt = ex["seq"].dynamic
+    acc = {k: [] for k in ("mae_s", "mae_l", "iou_s", "iou_l", "agree_s", "agree_l", "gt_j", "gt_s", "gt_l")}
+    for f in range(len(j)):
+        if f % REFRESH == 0:
+            continue
+        ref = j[f]["pixel"].cpu().numpy()
+        ps = s[f]["pixel"].cpu().numpy()
+        pl = l[f]["net"].cpu().numpy()
+        acc["mae_s"].append(np.abs(ps - ref).mean())
+        acc["mae_l"].append(np.abs(pl - ref).mean())
+        acc["iou_s"].append(iou(ps > 0.5, ref > 0.5))
+        acc["iou_l"].append(iou(pl > 0.5, ref > 0.5))
+        lj = j[f]["labels"].cpu().numpy() == 1
+        ls = s[f]["labels"].cpu().numpy() == 1
+        ll = l[f]["labels"].cpu().numpy() == 1
+        acc["agree_s"].append(iou(ls, lj))
+        acc["agree_l"].append(iou(ll, lj))
+        acc["gt_j"].append(iou(lj, gt))
+        acc["gt_s"].append(iou(ls, gt))
+        acc["gt_l"].append(iou(ll, gt))
+    m = {k: float(np.mean(v)) for k, v in acc.items()}
+    L = ex["losses"]
+    m["loss_first"] = float(np.mean(L[:5]))
+    m["loss_last"] = float(np.mean(L[-20:]))
+    return m
