@@ -12,6 +12,7 @@ Contents
                           exponential (Sec. V-A(c) pose refinement)
   mp                      the spatiotemporal MP update, Eqs. (2)-(12), (17)
   mpnet                   the small per-pixel MP proposal network
+  schedule                the semantic-on-demand trigger, Eqs. (13)-(16)
 
 Parity status of each function is listed in the module that defines it.
 """
