@@ -295,6 +295,40 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
               int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
               double *stats, const float *mp_map, float *mp_pixel, void *stream);
 
+/* Semantic-on-demand trigger constants (Sec. IV-B). The paper gives none of
+ * their values; defaults from dags_default_sched_cfg. */
+typedef struct {
+  double w_u, w_r;   /* weights of U_bar and R, Eq. (15) (0.5, 0.5): >= 0, summing to 1 */
+  double theta;      /* trigger threshold, Eq. (16) (0.35)                               */
+  double e_ref;      /* reference residual of Eq. (14), m (0.05)                         */
+  int32_t n_max;     /* maximum skip interval of Eq. (16), frames (10)                   */
+} dags_sched_cfg;
+
+void dags_default_sched_cfg(dags_sched_cfg *cfg);
+
+/* Uncertainty-aware semantic-on-demand trigger of one frame (Sec. IV-B,
+ * Eqs. (13)-(16)), enqueued after the frame's mp_update; one thread, FP64.
+ *   e_bar = the frame's mean residual e(p) over the background region (label
+ *           0, the pixels no instance mask claims; 0 if it is empty): the hot
+ *           path's stand-in for the mean reprojection error over verified
+ *           correspondences
+ *   R     = clip(e_bar / e_ref, 0, 1), Eq. (14)
+ *   S     = w_u U_bar + w_r R, Eq. (15), U_bar from Eq. (13)
+ *   since = 0 if seg_refreshed else since + 1
+ *   next  = S > theta or since + 1 >= n_max, Eq. (16): whether the NEXT frame
+ *           should invoke segmentation (the score of frame t serves frame t+1)
+ * stats     device, the frame's mp_update stats (U_bar at [1], region 0's
+ *           count and mean residual at [DAGS_MP_STATS_HEAD] and [+1])
+ * seg_refreshed  nonzero if this frame's prior was fresh
+ * state     device in/out, 2 int32: [0] since (frames since the last refresh
+ *           as of the previous frame; any value before a refreshed first
+ *           frame), [1] out: next (0 or 1)
+ * score     device out, 3 doubles (e_bar, R, S), or NULL
+ * Returns DAGS_E_INVAL for a NULL ctx/stats/state, negative weights, weights
+ * not summing to 1 (within 1e-6), e_ref <= 0 or n_max < 1. */
+int semantic_trigger(dags_ctx *ctx, const double *stats, const dags_sched_cfg *cfg, int32_t seg_refreshed,
+                     int32_t *state, double *score, void *stream);
+
 /* Learned per-pixel MP proposal network (not in the paper: the task's
  * learned stand-in for the stale instance prior between scheduled semantic
  * invocations, Sec. IV-B). Per pixel, NHWC:

@@ -609,6 +609,30 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
   return cuda_status(e);
 }
 
+void dags_default_sched_cfg(dags_sched_cfg *c) {
+  if (!c) return;
+  c->w_u = 0.5;
+  c->w_r = 0.5;
+  c->theta = 0.35;
+  c->e_ref = 0.05;
+  c->n_max = 10;
+}
+
+int semantic_trigger(dags_ctx *ctx, const double *stats, const dags_sched_cfg *cfg, int32_t seg_refreshed,
+                     int32_t *state, double *score, void *stream) {
+  NvtxRange nv("semantic_trigger");
+  if (!ctx || !stats || !state) return DAGS_E_INVAL;
+  dags_sched_cfg c;
+  if (cfg) c = *cfg;
+  else dags_default_sched_cfg(&c);
+  if (!(c.w_u >= 0.0) || !(c.w_r >= 0.0) || !(fabs(c.w_u + c.w_r - 1.0) <= 1e-6) || !(c.e_ref > 0.0) ||
+      c.n_max < 1 || !(c.theta == c.theta))
+    return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return cuda_status(launch_semantic_trigger(stats, c, seg_refreshed, state, score, s));
+}
+
 int mpnet_features(dags_ctx *ctx, const float *image, const float *targets, const uint8_t *inst,
                    const float *table, int32_t n_regions, int32_t width, int32_t height, uint16_t *feats,
                    void *stream) {

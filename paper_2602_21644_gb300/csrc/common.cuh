@@ -151,6 +151,8 @@ struct MpBuffers {
   uint32_t *hist = nullptr;           // [2 * 2048]
   uint32_t *sel = nullptr;            // [8]
 };
+cudaError_t launch_semantic_trigger(const double *stats, const dags_sched_cfg &cfg, int seg_refreshed,
+                                    int32_t *state, double *score, cudaStream_t s);
 cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,

@@ -414,6 +414,27 @@ __global__ void mp_region_stats_kernel(MpWs m, MpCfg c) {
   }
 }
 
+// Semantic-on-demand trigger, Eqs. (13)-(16): one thread reads the frame's
+// U_bar and background residual mean from the MP statistics.
+__global__ void semantic_trigger_kernel(const double *__restrict__ stats, double w_u, double w_r, double theta,
+                                        double e_ref, int n_max, int seg_refreshed, int32_t *state,
+                                        double *score) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double u_bar = stats[1];
+  const double cnt0 = stats[DAGS_MP_STATS_HEAD + 0];
+  const double e_bar = cnt0 > 0.0 ? stats[DAGS_MP_STATS_HEAD + 1] : 0.0;
+  const double R = fmin(fmax(e_bar / e_ref, 0.0), 1.0);
+  const double S = w_u * u_bar + w_r * R;
+  const int since = seg_refreshed ? 0 : state[0] + 1;
+  state[0] = since;
+  state[1] = (S > theta || since + 1 >= n_max) ? 1 : 0;
+  if (score) {
+    score[0] = e_bar;
+    score[1] = R;
+    score[2] = S;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const double *pose, const Raster &r,
@@ -451,6 +472,13 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 2, c);
   mp_labels_kernel<<<gg, kMpBlock, 0, s>>>(m, n, labels);
   mp_region_stats_kernel<<<1, 256, 0, s>>>(m, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_semantic_trigger(const double *stats, const dags_sched_cfg &cfg, int seg_refreshed,
+                                    int32_t *state, double *score, cudaStream_t s) {
+  semantic_trigger_kernel<<<1, 32, 0, s>>>(stats, cfg.w_u, cfg.w_r, cfg.theta, cfg.e_ref, cfg.n_max,
+                                           seg_refreshed ? 1 : 0, state, score);
   return cudaGetLastError();
 }
 

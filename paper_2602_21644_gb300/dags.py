@@ -55,6 +55,11 @@ class CMpCfg(ctypes.Structure):
                                               "vis_tol", "z_near", "tau_floor")] + [("fusion_mode", ctypes.c_int32)]
 
 
+class CSchedCfg(ctypes.Structure):
+    _fields_ = [("w_u", ctypes.c_double), ("w_r", ctypes.c_double), ("theta", ctypes.c_double),
+                ("e_ref", ctypes.c_double), ("n_max", ctypes.c_int32)]
+
+
 MP_STATS_HEAD = 6
 MPNET_WEIGHT_BYTES = 22016
 MPNET_ACT_WORDS = 96
@@ -70,7 +75,7 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
            "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
-           "mpnet_train_step", "dags_selftest_timeout"]
+           "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train"]
@@ -132,6 +137,10 @@ def load(path: str = LIB_PATH):
     lib.mpnet_train_step.argtypes = [P, P, P, P, P, I32, P, P, I32, I32, I32, ctypes.c_float, P, P, P]
     lib.mpnet_train_step.restype = ctypes.c_int
     lib.dags_selftest_timeout.argtypes = [P, I64, P]
+    lib.dags_default_sched_cfg.argtypes = [ctypes.POINTER(CSchedCfg)]
+    lib.dags_default_sched_cfg.restype = None
+    lib.semantic_trigger.argtypes = [P, P, ctypes.POINTER(CSchedCfg), I32, P, P, P]
+    lib.semantic_trigger.restype = ctypes.c_int
     lib.dags_selftest_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -191,6 +200,14 @@ def default_pose_cfg(lr=None, **kw) -> CPoseCfg:
 def default_mp_cfg(**kw) -> CMpCfg:
     c = CMpCfg()
     load().dags_default_mp_cfg(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_sched_cfg(**kw) -> CSchedCfg:
+    c = CSchedCfg()
+    load().dags_default_sched_cfg(ctypes.byref(c))
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -346,6 +363,24 @@ class Context:
                                   _ptr(image), _ptr(inst), _ptr(table), nreg, ctypes.byref(mc), int(bool(seg_refreshed)),
                                   _ptr(labels), _ptr(stats), _ptr(mp_map), _ptr(mp_pixel), _stream()), "mp_update")
         return stats
+
+    def semantic_trigger(self, stats, state, seg_refreshed, cfg=None, score=None):
+        """Semantic-on-demand trigger of one frame (Eqs. (13)-(16)) from the
+        frame's mp_update stats. state: int32 [2] device tensor (frames since
+        the last refresh; out: 1 if the next frame should refresh). score:
+        optional float64 [3] (e_bar, R, S). Returns score (or None)."""
+        _need(stats, torch.float64, "stats")
+        _need(state, torch.int32, "state")
+        if state.numel() < 2:
+            raise ValueError("state must hold 2 int32")
+        if score is not None:
+            _need(score, torch.float64, "score")
+            if score.numel() < 3:
+                raise ValueError("score must hold 3 doubles")
+        sc = cfg if cfg is not None else default_sched_cfg()
+        _check(self.lib.semantic_trigger(self.h, _ptr(stats), ctypes.byref(sc), int(bool(seg_refreshed)), _ptr(state),
+                                         _ptr(score), _stream()), "semantic_trigger")
+        return score
 
     def mpnet_features(self, image, targets, inst, table, cam: Camera, out=None):
         """8-channel bfloat16 network input [H, W, 8] of one view."""

@@ -8,7 +8,9 @@ rendered MP, residuals, depth, opacity and the stale prior. The judge is the
 plain method itself with a fresh prior at every frame. The network is trained
 on the GPU, by the library's own kernels, on the judge's per-pixel maps of a
 training sequence, then evaluated on a held-out sequence with other
-Gaussians, other noise and other object motions.
+Gaussians, other noise and other object motions. Both the plain and the
+learned arm also run with the semantic-on-demand trigger of Eqs. (13)-(16)
+deciding the refreshes instead of the fixed cadence.
 
 Synthetic stand-in for an indoor RGB-D sequence: the analytic room of
 synth.room_scene at 320 x 240 (f = 262.5, the 640 x 480 field of view), two
@@ -93,18 +95,30 @@ class Runner:
         self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out)
         return out
 
-    def run(self, mode, net=None, collect=False):
+    def run(self, mode, net=None, collect=False, schedule=None):
         """mode: 'judge' (fresh prior every frame), 'stale' (the method without
-        the network), 'learned' (network proposal between refreshes)."""
+        the network), 'learned' (network proposal between refreshes).
+        Refreshes come every REFRESH frames, or from the semantic-on-demand
+        trigger (Eqs. (13)-(16)) when schedule (a dags_sched_cfg) is given."""
         gauss = torch.from_numpy(self.seq.rec.copy()).cuda()
         labels = torch.zeros(N_GAUSS, dtype=torch.uint8, device="cuda")
+        state = torch.zeros(2, dtype=torch.int32, device="cuda")
+        score = torch.zeros(3, dtype=torch.float64, device="cuda")
         hist = []
+        nxt, last_ref = True, 0
         for f in range(len(self.seq.poses)):
             pose, tg = self.frame_inputs(f)
             image = self.render(gauss, pose)
-            refreshed = f % REFRESH == 0 or mode == "judge"
-            inst = torch.from_numpy(self.seq.inst[f if refreshed else f - f % REFRESH]).cuda()
-            rec = {}
+            if mode == "judge":
+                refreshed = True
+            elif schedule is not None:
+                refreshed = nxt
+            else:
+                refreshed = f % REFRESH == 0
+            if refreshed:
+                last_ref = f
+            inst = torch.from_numpy(self.seq.inst[last_ref]).cuda()
+            rec = {"refreshed": refreshed}
             if collect or (mode == "learned" and not refreshed):
                 feats = self.ctx.mpnet_features(image, tg, inst, self.table, self.cam)
                 rec["feats"] = feats
@@ -115,8 +129,12 @@ class Runner:
                 mp_map = self.ctx.mpnet_infer(net, rec["feats"][None]).reshape(-1)
                 rec["net"] = mp_map
             stale_px = torch.empty(self.P, dtype=torch.float32, device="cuda")
-            self.ctx.mp_update(gauss, self.cam, pose, tg, image, inst, self.table, labels,
-                               seg_refreshed=refreshed, mp_map=mp_map, mp_pixel=stale_px)
+            stats = self.ctx.mp_update(gauss, self.cam, pose, tg, image, inst, self.table, labels,
+                                       seg_refreshed=refreshed, mp_map=mp_map, mp_pixel=stale_px)
+            if schedule is not None:
+                self.ctx.semantic_trigger(stats, state, refreshed, cfg=schedule, score=score)
+                nxt = bool(state[1].item())
+                rec["score"] = score.clone()
             rec["pixel"] = stale_px
             rec["labels"] = labels.clone()
             hist.append(rec)
@@ -162,7 +180,8 @@ def experiment(dags, steps=1000):
     eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=40)
     ev = Runner(dags, eval_seq)
     out = dict(losses=losses, judge=ev.run("judge"), stale=ev.run("stale"), learned=ev.run("learned", net=net),
-               seq=eval_seq)
+               scheduled=ev.run("stale", schedule=dags.default_sched_cfg()),
+               scheduled_learned=ev.run("learned", net=net, schedule=dags.default_sched_cfg()), seq=eval_seq)
     ev.ctx.close()
     return out
 
@@ -197,3 +216,25 @@ def metrics(ex):
     m["loss_first"] = float(np.mean(L[:5]))
     m["loss_last"] = float(np.mean(L[-20:]))
     return m
+
+
+def schedule_metrics(ex):
+    """The semantic-on-demand trigger against the fixed cadence on the
+    held-out sequence: segmentation calls, and over frames 1.. the per-pixel
+    MP MAE against the judge and the label IoU with the judge's labels (the
+    learned proposal's map where it stands in for M_p)."""
+    j = ex["judge"]
+    out = {}
+    for name in ("stale", "scheduled", "learned", "scheduled_learned"):
+        h = ex[name]
+        mae, agree = [], []
+        for f in range(1, len(j)):
+            ref = j[f]["pixel"].cpu().numpy()
+            px = (h[f]["net"] if "net" in h[f] else h[f]["pixel"]).cpu().numpy()
+            mae.append(np.abs(px - ref).mean())
+            agree.append(iou(h[f]["labels"].cpu().numpy() == 1, j[f]["labels"].cpu().numpy() == 1))
+        out[name] = {"calls": int(sum(r["refreshed"] for r in h)), "mp_mae": float(np.mean(mae)),
+                     "label_iou_vs_fresh_prior": float(np.mean(agree))}
+        if "score" in h[0]:
+            out[name]["mean_S"] = float(np.mean([r["score"][2].item() for r in h]))
+    return out

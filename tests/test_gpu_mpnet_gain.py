@@ -19,11 +19,32 @@ def dags():
 
 
 @pytest.fixture(scope="module")
-def result(dags):
+def experiment(dags):
     from paper_2602_21644_gb300 import mp_eval
-    m = mp_eval.metrics(mp_eval.experiment(dags))
+    return mp_eval.experiment(dags)
+
+
+@pytest.fixture(scope="module")
+def result(experiment):
+    from paper_2602_21644_gb300 import mp_eval
+    m = mp_eval.metrics(experiment)
     print("\n" + ", ".join(f"{k} {v:.4f}" for k, v in m.items()))
     return m
+
+
+def test_scheduled_refreshes(experiment):
+    # the trigger refreshes at frame 0 and at least every N_max = 10 frames;
+    # the frames it refreshes are those its previous frame decided
+    from paper_2602_21644_gb300 import mp_eval
+    sm = mp_eval.schedule_metrics(experiment)
+    print("\n" + repr(sm))
+    T = len(experiment["judge"])
+    for name in ("scheduled", "scheduled_learned"):
+        h = experiment[name]
+        ref = [f for f, r in enumerate(h) if r["refreshed"]]
+        assert ref[0] == 0 and all(b - a <= 10 for a, b in zip(ref, ref[1:] + [T]))
+        assert sm[name]["calls"] == len(ref) <= T
+    assert sm["stale"]["calls"] == (T + 9) // 10
 
 
 def test_training_converges(result):
