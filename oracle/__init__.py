@@ -11,6 +11,10 @@ Contents
   pose                    FP64 Adam step on the 6-DoF twist and the SE(3)
                           exponential (Sec. V-A(c) pose refinement)
   mp                      the spatiotemporal MP update, Eqs. (2)-(12), (17)
+  splat.render_jac (C)    forward-mode derivative of the rendered colour and
+                          depth along the pose twist, and the IRLS normal
+                          equations of the MP-weighted L1 loss
+  lm                      Levenberg-Marquardt pose refinement (Sec. V-A(c))
   mpnet                   the small per-pixel MP proposal network
   schedule                the semantic-on-demand trigger, Eqs. (13)-(16)
 
@@ -72,6 +76,8 @@ def _load():
         lib.oracle_render.restype = ctypes.c_int
         lib.oracle_render_pixel.argtypes = [I64, P, P, P, P, ctypes.c_int, ctypes.c_int, P]
         lib.oracle_render_pixel.restype = ctypes.c_int
+        lib.oracle_render_jac.argtypes = [I64, P, P, P, P, P, P, ctypes.c_double, P, P, P, P]
+        lib.oracle_render_jac.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -193,3 +199,41 @@ def render_pixel(G, cam, pose, i, j, rc=None):
     fl = lib.oracle_render_pixel(G.shape[0], _ptr(G), _ptr(_f64(cam)), _ptr(_f64(pose, (12,))), _ptr(rc),
                                  int(i), int(j), _ptr(out))
     return out, fl
+
+
+def render_jac(G, cam, pose, targets, rc=None, lc=None, delta=0.01):
+    """Forward-mode pose Jacobian of one view and the IRLS normal equations
+    of the MP-weighted L1 loss (w(u) held constant):
+      J[u, ch, k] = d(rendered channel ch at pixel u) / d xi_k, ch = r, g, b,
+                    depth; xi = (rho, phi), left perturbation
+      W = c / max(|r|, delta), H = sum W J J^T, g = sum W r J, L the loss.
+    Returns dict(pix, J (H*W x 4 x 6), flags, L, H (6 x 6), g (6,))."""
+    lib = _load()
+    G = _f64(G, (-1, G_STRIDE))
+    rc = raster_vec() if rc is None else _f64(rc)
+    lc = loss_vec() if lc is None else _f64(lc)
+    cam = _f64(cam)
+    W, H = int(cam[4]), int(cam[5])
+    pix = np.zeros((W * H, PX_STRIDE))
+    J = np.zeros((W * H, 4, 6))
+    flags = np.zeros(W * H, np.int32)
+    normal = np.zeros(28)
+    tg = _f64(targets, (W * H, 4))
+    rcode = lib.oracle_render_jac(G.shape[0], _ptr(G), _ptr(cam), _ptr(_f64(pose, (12,))), _ptr(rc), _ptr(lc),
+                                  _ptr(tg), float(delta), _ptr(pix), _ptr(J), _ptr(flags), _ptr(normal))
+    if rcode != 0:
+        raise MemoryError("oracle_render_jac failed")
+    Hm, g = unpack_normal(normal)
+    return dict(pix=pix, J=J, flags=flags, L=float(normal[0]), H=Hm, g=g, normal=normal)
+
+
+def unpack_normal(normal):
+    """(H 6x6 symmetric, g 6) from the packed (L, upper triangle of H, g)."""
+    normal = np.asarray(normal, np.float64)
+    Hm = np.zeros((6, 6))
+    e = 1
+    for k in range(6):
+        for m in range(k, 6):
+            Hm[k, m] = Hm[m, k] = normal[e]
+            e += 1
+    return Hm, normal[22:28].copy()

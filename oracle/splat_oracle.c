@@ -792,3 +792,207 @@ int oracle_render_pixel(int64_t n, const double *G, const double *cam, const dou
   free(P);
   return flags;
 }
+
+/* ---- forward-mode pose Jacobian and the IRLS normal equations ----
+ *
+ * Levenberg-Marquardt pose refinement (Sec. V-A(c)) of the MP-weighted L1
+ * objective of Eqs. (20)-(22). The paper names the method only; the reading:
+ * each channel residual r_i of a pixel (colour r, g, b with coefficient
+ * c_i = lambda_pho w(u); depth with lambda_depth w(u) where D_gt > 0; w(u)
+ * held constant, as in the stop-gradient adjoint) enters a weighted least
+ * squares problem with the iteratively-reweighted weight
+ * W_i = c_i / max(|r_i|, delta), whose gradient equals that of c_i |r_i|
+ * wherever |r_i| > delta. The Gauss-Newton model needs J_i = d r_i / d xi,
+ * the derivative of the rendered channel along the twist xi = (rho, phi) of
+ * the left perturbation T <- exp(xi^) T, at the current discrete decisions
+ * (which Gaussians contribute, the alpha clamp, where the walk stops).
+ *   H = sum_i W_i J_i J_i^T,   g = sum_i W_i r_i J_i,   L = sum_u w(u) l(u). */
+
+/* d(u, v, a, b, c, z) / d xi_k of one projected Gaussian, k = 0..5 (conic in
+ * natural units: power = -(a dx^2 + c dy^2)/2 - b dx dy). */
+static void project_tangents(const proj_t *P, const double *cam, double tan[6][6]) {
+  const double fx = cam[CAM_FX], fy = cam[CAM_FY];
+  const double x = P->p[0], y = P->p[1], z = P->p[2];
+  const double *J = P->J;
+  for (int k = 0; k < 6; k++) {
+    double dp[3] = {0, 0, 0}, dSc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < 3) {
+      dp[k] = 1.0;
+    } else {
+      double ph[3] = {0, 0, 0};
+      ph[k - 3] = 1.0;
+      /* camera mean: phi x p; camera covariance: [phi]x Sc - Sc [phi]x */
+      dp[0] = ph[1] * z - ph[2] * y;
+      dp[1] = ph[2] * x - ph[0] * z;
+      dp[2] = ph[0] * y - ph[1] * x;
+      double Kx[9] = {0, -ph[2], ph[1], ph[2], 0, -ph[0], -ph[1], ph[0], 0};
+      double A1[9], A2[9];
+      mm3(Kx, P->Sc, A1);
+      mm3(P->Sc, Kx, A2);
+      for (int e = 0; e < 9; e++) dSc[e] = A1[e] - A2[e];
+    }
+    /* the guard clamp freezes x/z (y/z) in the Jacobian */
+    double dtx = P->clx ? 0.0 : (dp[0] * z - x * dp[2]) / (z * z);
+    double dty = P->cly ? 0.0 : (dp[1] * z - y * dp[2]) / (z * z);
+    double dJ[6] = {-fx * dp[2] / (z * z), 0.0, -fx * (dtx * z - P->tx * dp[2]) / (z * z),
+                    0.0, -fy * dp[2] / (z * z), -fy * (dty * z - P->ty * dp[2]) / (z * z)};
+    /* d(J Sc J^T) */
+    double dS2[4];
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) {
+        double s = 0;
+        for (int a = 0; a < 3; a++)
+          for (int b = 0; b < 3; b++)
+            s += dJ[3 * i + a] * P->Sc[3 * a + b] * J[3 * j + b] + J[3 * i + a] * dSc[3 * a + b] * J[3 * j + b] +
+                 J[3 * i + a] * P->Sc[3 * a + b] * dJ[3 * j + b];
+        dS2[2 * i + j] = s;
+      }
+    /* conic Q = (2D covariance)^-1: dQ = -Q dS2 Q */
+    double Q[4] = {P->a, P->b, P->b, P->c}, QdS[4], dQ[4];
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) QdS[2 * i + j] = Q[2 * i] * dS2[j] + Q[2 * i + 1] * dS2[2 + j];
+    for (int i = 0; i < 2; i++)
+      for (int j = 0; j < 2; j++) dQ[2 * i + j] = -(QdS[2 * i] * Q[j] + QdS[2 * i + 1] * Q[2 + j]);
+    tan[k][0] = fx * (dp[0] * z - x * dp[2]) / (z * z);
+    tan[k][1] = fy * (dp[1] * z - y * dp[2]) / (z * z);
+    tan[k][2] = dQ[0];
+    tan[k][3] = dQ[1];
+    tan[k][4] = dQ[3];
+    tan[k][5] = dp[2];
+  }
+}
+
+/* Render one view with the tangents of colour and depth and reduce the
+ * normal equations. targets (P x 4) required. out_px[P * PX_STRIDE] or NULL,
+ * out_J[P * 24] or NULL (per pixel: channels r, g, b, depth, each 6 twist
+ * components), out_flags[P] (as oracle_render), normal[28] = L, H (upper
+ * triangle, row-major, 21), g (6). Returns 0, or -1 on allocation failure. */
+int oracle_render_jac(int64_t n, const double *G, const double *cam, const double *pose,
+                      const double *rc, const double *lc, const double *targets, double delta,
+                      double *out_px, double *out_J, int32_t *out_flags, double *normal) {
+  int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
+  proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
+  zkey_t *zk = (zkey_t *)malloc(sizeof(zkey_t) * (size_t)(n > 0 ? n : 1));
+  int64_t *order = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  double (*tan)[6][6] = (double (*)[6][6])malloc(sizeof(double) * 36 * (size_t)(n > 0 ? n : 1));
+  if (!P || !zk || !order || !tan) return -1;
+  int64_t nv = 0;
+  for (int64_t i = 0; i < n; i++) {
+    project_one(G + i * G_STRIDE, cam, pose, rc, &P[i]);
+    if (P[i].vis) {
+      zk[nv].z = P[i].zkey; zk[nv].id = i; nv++;
+      project_tangents(&P[i], cam, tan[i]);
+    }
+  }
+  qsort(zk, (size_t)nv, sizeof(zkey_t), cmp_zkey);
+  for (int64_t k = 0; k < nv; k++) order[k] = zk[k].id;
+  cells_t cs;
+  build_cells(nv, P, order, W, H, 8, 1, &cs);
+
+  const double amin = rc[RC_ALPHA_MIN], amax = rc[RC_ALPHA_MAX], tmin = rc[RC_T_MIN];
+  double L = 0.0, Hm[36], gv[6];
+  for (int k = 0; k < 36; k++) Hm[k] = 0.0;
+  for (int k = 0; k < 6; k++) gv[k] = 0.0;
+
+  for (int j = 0; j < H; j++)
+    for (int i = 0; i < W; i++) {
+      int c = (j / cs.cell) * cs.cw + (i / cs.cell);
+      double T = 1.0, acc[6] = {0, 0, 0, 0, 0, 0}, eT = 0.0;
+      double dT[6] = {0, 0, 0, 0, 0, 0}, dC[4][6];
+      for (int a = 0; a < 4; a++)
+        for (int k = 0; k < 6; k++) dC[a][k] = 0.0;
+      int flags = 0;
+      int64_t nl = 0, last = -1;
+      for (int64_t q = cs.start[c]; q < cs.start[c + 1]; q++) {
+        int64_t id = cs.ids[q];
+        const proj_t *p = &P[id];
+        double dx = p->u - i, dy = p->v - j;
+        double power = -0.5 * (p->a * dx * dx + p->c * dy * dy) - p->b * dx * dy;
+        double ag = p->o * exp(power);
+        double em = exponent_margin(p, dx, dy, power);
+        double lag = power + log(p->o);
+        if (fabs(lag - log(amin)) <= em) flags |= FL_ALPHA;
+        if (fabs(lag - log(amax)) <= em) flags |= FL_AMAX;
+        if (ag < amin) continue;
+        int clamped = ag > amax;
+        double alpha = clamped ? amax : ag;
+        double testT = T * (1.0 - alpha);
+        double eTk = eT + (clamped ? 0.0 : alpha / (1.0 - alpha) * em) + 1e-6;
+        if (fabs(log(testT) - log(tmin)) <= eTk) flags |= FL_TSTOP;
+        if (testT < tmin) break;
+        eT = eTk;
+        const double *g = G + id * G_STRIDE;
+        double wgt = alpha * T;
+        acc[0] += g[G_CR] * wgt;
+        acc[1] += g[G_CG] * wgt;
+        acc[2] += g[G_CB] * wgt;
+        acc[3] += p->p[2] * wgt;
+        acc[4] += wgt;
+        acc[5] += g[G_MP] * wgt;
+        /* tangents: alpha' = alpha power' (0 where clamped); the weight
+         * alpha T has tangent alpha' T + alpha T'; T' of the next entry is
+         * T' (1 - alpha) - T alpha' */
+        for (int k = 0; k < 6; k++) {
+          const double *t = tan[id][k];
+          double dpow = -0.5 * (t[2] * dx * dx + t[4] * dy * dy) - t[3] * dx * dy -
+                        (p->a * dx + p->b * dy) * t[0] - (p->b * dx + p->c * dy) * t[1];
+          double da = clamped ? 0.0 : alpha * dpow;
+          double dw = da * T + alpha * dT[k];
+          dC[0][k] += g[G_CR] * dw;
+          dC[1][k] += g[G_CG] * dw;
+          dC[2][k] += g[G_CB] * dw;
+          dC[3][k] += p->p[2] * dw + wgt * t[5];
+          dT[k] = dT[k] * (1.0 - alpha) - T * da;
+        }
+        nl++;
+        last = id;
+        T = testT;
+      }
+      int64_t pix = (int64_t)j * W + i;
+      if (out_px) {
+        double *o = out_px + pix * PX_STRIDE;
+        for (int k = 0; k < 6; k++) o[k] = acc[k];
+        o[PX_T] = T; o[PX_N] = (double)nl; o[PX_LAST] = (double)last; o[PX_W] = 0.0;
+      }
+      if (out_J)
+        for (int a = 0; a < 4; a++)
+          for (int k = 0; k < 6; k++) out_J[pix * 24 + a * 6 + k] = dC[a][k];
+      const double *tg = targets + pix * 4;
+      double O = acc[4], Rm = acc[5], w = 0.0;
+      if (lc[LC_WMODE] == 0) {
+        if (near_rel(O, lc[LC_OEPS])) flags |= FL_OEPS;
+        if (O > lc[LC_OEPS]) w = (O - Rm) / O;
+      } else {
+        w = O - Rm;
+      }
+      if (out_px) out_px[pix * PX_STRIDE + PX_W] = w;
+      out_flags[pix] = flags;
+      if (!(tg[0] >= 0)) continue;
+      const int dvalid = tg[3] > 0;
+      double l1 = 0.0;
+      for (int a = 0; a < 4; a++) {
+        double r = acc[a] - tg[a];
+        double cc = a < 3 ? lc[LC_LPHO] * w : (dvalid ? lc[LC_LDEPTH] * w : 0.0);
+        if (a < 3) l1 += fabs(r);
+        if (cc == 0.0) continue;
+        double Wt = cc / fmax(fabs(r), delta);
+        for (int k = 0; k < 6; k++) {
+          gv[k] += Wt * r * dC[a][k];
+          for (int m = k; m < 6; m++) Hm[6 * k + m] += Wt * dC[a][k] * dC[a][m];
+        }
+      }
+      L += w * (lc[LC_LPHO] * l1 + (dvalid ? lc[LC_LDEPTH] * fabs(acc[3] - tg[3]) : 0.0));
+    }
+  normal[0] = L;
+  int e = 1;
+  for (int k = 0; k < 6; k++)
+    for (int m = k; m < 6; m++) normal[e++] = Hm[6 * k + m];
+  for (int k = 0; k < 6; k++) normal[22 + k] = gv[k];
+  free(cs.start);
+  free(cs.ids);
+  free(tan);
+  free(order);
+  free(zk);
+  free(P);
+  return 0;
+}
