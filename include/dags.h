@@ -295,6 +295,71 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
               int32_t n_regions, const dags_mp_cfg *cfg, int32_t seg_refreshed, uint8_t *labels,
               double *stats, const float *mp_map, float *mp_pixel, void *stream);
 
+/* Levenberg-Marquardt pose refinement (Sec. V-A(c), which names the method
+ * and gives no constants; defaults from dags_default_lm_cfg). The objective
+ * is the MP-weighted L1 loss of Eqs. (20)-(22) with the static weight w(u)
+ * held constant in the linearisation. Each channel residual r (r, g, b with
+ * c = lambda_pho w; depth with c = lambda_depth w where the observed depth
+ * is > 0) enters by iterative reweighting, W = c / max(|r|, delta):
+ *   H = sum W J J^T,  g = sum W r J,  J = d(rendered channel) / d xi
+ * for the left-perturbation twist xi = (rho, phi), T <- exp(xi^) T, taken at
+ * the render's discrete decisions. One iteration linearises at T_try; the
+ * point is accepted if its loss is below the best so far (mu <- max(mu down,
+ * mu_min)), else rejected (mu <- min(mu up, mu_max)); then
+ * (H_best + mu diag(H_best) + floor tr(H_best)/6 I) Delta = -g_best is solved
+ * in FP64 (Delta = 0 if tr H_best <= 0 or the factorisation fails) and
+ * T_try = exp(Delta^) T_best. */
+typedef struct {
+  double mu0;             /* initial damping (1e-2)                               */
+  double mu_min, mu_max;  /* damping bounds (1e-9, 1e9)                           */
+  double down, up;        /* damping factors after accept / reject (0.1, 10)      */
+  double delta;           /* IRLS floor on |r|, colour units and metres (0.01)    */
+  double floor;           /* ridge relative to tr(H) / 6 (1e-9)                   */
+} dags_lm_cfg;
+
+void dags_default_lm_cfg(dags_lm_cfg *cfg);
+
+#define DAGS_LM_NORMAL 28 /* L, upper triangle of H row-major (21), g (6) */
+#define DAGS_LM_STATE 48  /* T_best[12], L_best, mu, H_best[21], g_best[6], accepted, iterations,
+                             last L, last accepted (0/1), unused */
+
+/* The normal equations of one view at pose (device, 12 doubles): the
+ * preprocess and binning of splat_forward, the twist tangents of every
+ * visible Gaussian, and the forward-mode compositing of colour and depth.
+ * normal  device out, DAGS_LM_NORMAL doubles, summed in FP64 in a fixed
+ *         order (deterministic); L is NaN after a pair-capacity overflow
+ * jac     device out, H*W*24 floats (per pixel: r, g, b, depth, each the 6
+ *         twist components), 16-byte aligned, or NULL
+ * image   device out, DAGS_IMG_CHANNELS x H*W as splat_forward, or NULL
+ * last    device out, H*W int32 as splat_forward, or NULL
+ * targets required (H*W float4, 16-byte aligned); delta > 0. The first LM
+ * call on a ctx allocates its buffers (before any stream capture).
+ * splat_backward does not follow this call (DAGS_E_ORDER). */
+int splat_normal_equations(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam,
+                           const double *pose, const float *targets, const dags_raster_cfg *rcfg,
+                           const dags_loss_cfg *lcfg, double delta, double *normal, float *jac, float *image,
+                           int32_t *last, void *stream);
+
+/* Starts an LM refinement: state (device, DAGS_LM_STATE doubles) takes
+ * T_best = pose, L_best = +inf, mu = mu0; pose_try (device, 12) = pose. */
+int lm_init(dags_ctx *ctx, const double *pose, const dags_lm_cfg *cfg, double *state, double *pose_try,
+            void *stream);
+
+/* One LM decision and step from the normal equations at pose_try (one FP64
+ * thread): accept or reject, adapt mu, solve, write the next pose_try and
+ * T_best into pose_best (device, 12 doubles). */
+int lm_pose_step(dags_ctx *ctx, const double *normal, const dags_lm_cfg *cfg, double *state, double *pose_try,
+                 double *pose_best, void *stream);
+
+/* iters LM iterations of one view starting from pose (device in/out, 12
+ * doubles; out: T_best): lm_init, then per iteration splat_normal_equations
+ * at the ctx's pose_try and lm_pose_step. state: device, DAGS_LM_STATE
+ * doubles. With use_graph the iteration is captured once per argument set
+ * into a CUDA graph and replayed (the first call is not captured). */
+int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
+                   const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                   const dags_lm_cfg *lmcfg, int32_t iters, double *state, int32_t use_graph, void *stream);
+
 /* Semantic-on-demand trigger constants (Sec. IV-B). The paper gives none of
  * their values; defaults from dags_default_sched_cfg. */
 typedef struct {
@@ -414,6 +479,9 @@ enum {
   DAGS_K_MP_GAUSS,         /* MP update: per-Gaussian update and medians   */
   DAGS_K_MPNET,            /* learned MP network, inference                */
   DAGS_K_MPNET_TRAIN,      /* learned MP network, training step            */
+  DAGS_K_POSE_TANGENT,     /* LM: twist tangents of the visible Gaussians  */
+  DAGS_K_RENDER_JAC,       /* LM: forward-mode compositing + normal eqs.   */
+  DAGS_K_LM_STEP,          /* LM: FP64 decision, solve and pose step       */
   DAGS_KERNEL_COUNT
 };
 int dags_timing_enable(dags_ctx *ctx, int enable);

@@ -81,6 +81,8 @@ struct dags_ctx {
   Workspace ws;
   KernelTimer timer;
   TrackGraph graph;
+  TrackGraph graph_lm;            // captured LM iteration
+  LmBuffers lm;                   // allocated by the first LM call
   MpBuffers mp;
   MpnetScratch net;
   PoseStep fused_step;            // set only inside the tracking loop
@@ -114,6 +116,13 @@ void free_mp(MpBuffers &b) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   b = MpBuffers();
+}
+
+void free_lm(LmBuffers &b) {
+  void *ptrs[] = {b.tan, b.partial, b.normal, b.pose_try};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  b = LmBuffers();
 }
 
 void free_net(MpnetScratch &b) {
@@ -321,6 +330,9 @@ void dags_destroy(dags_ctx *ctx) {
   ctx->timer.release();
   if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
   if (ctx->graph.cap) cudaStreamDestroy(ctx->graph.cap);
+  if (ctx->graph_lm.exec) cudaGraphExecDestroy(ctx->graph_lm.exec);
+  if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
+  free_lm(ctx->lm);
   free_mp(ctx->mp);
   free_net(ctx->net);
   free_ws(ctx->ws);
@@ -540,6 +552,197 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
     if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
     rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
                          grad_pose, g.cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
+    if (rc != DAGS_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return rc != DAGS_OK ? rc : DAGS_E_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) { g.exec = nullptr; return DAGS_E_CUDA; }
+    memcpy(g.key, key, kl < 512 ? kl : 512);
+    g.key_len = kl;
+  }
+  ctx->last_stream = s;
+  for (int k = 0; k < iters; ++k)
+    if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return DAGS_E_CUDA;
+  return DAGS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The LM buffers, allocated by the first LM call on the ctx.
+int ensure_lm(dags_ctx *ctx) {
+  LmBuffers &b = ctx->lm;
+  if (b.tan) return DAGS_OK;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+  A(alloc(&b.tan, (size_t)ctx->ws.max_n * 9));
+  A(alloc(&b.partial, (size_t)ctx->ws.max_tiles * DAGS_LM_NORMAL));
+  A(alloc(&b.normal, (size_t)DAGS_LM_NORMAL));
+  A(alloc(&b.pose_try, (size_t)12));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_lm(b);
+    return e == cudaErrorMemoryAllocation ? DAGS_E_NOMEM : DAGS_E_CUDA;
+  }
+  return DAGS_OK;
+}
+
+int make_lm_cfg(const dags_lm_cfg *in, dags_lm_cfg *c) {
+  if (in) *c = *in;
+  else dags_default_lm_cfg(c);
+  if (!(c->mu0 >= 0.0) || !(c->mu_min >= 0.0) || !(c->mu_max >= c->mu_min) || !(c->down > 0.0) ||
+      !(c->down <= 1.0) || !(c->up >= 1.0) || !(c->delta > 0.0) || !(c->floor >= 0.0) || !isfinite(c->mu_max) ||
+      !isfinite(c->up) || !isfinite(c->delta) || !isfinite(c->floor) || !isfinite(c->mu0))
+    return DAGS_E_INVAL;
+  return DAGS_OK;
+}
+
+// Enqueues the normal equations of one view at `pose` (arguments checked).
+int normal_core(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
+                const float *targets, const Raster &r, const Loss &l, float delta, double *normal, float *jac,
+                float *image, int32_t *last, cudaStream_t s) {
+  ctx->last_stream = s;
+  ctx->fwd_image = nullptr;     // the workspace no longer holds a forward for splat_backward
+  const Workspace &w = ctx->ws;
+  const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
+  KernelTimer &tm = ctx->timer;
+  int ev = tm.begin(DAGS_K_PREPROCESS, s);
+  cudaError_t e = launch_preprocess(w, g4, n, pose, 1, r, 0, s);
+  tm.end(ev, s);
+  if (e == cudaSuccess && n > 0) {
+    ev = tm.begin(DAGS_K_EMIT, s);
+    e = launch_emit(w, n, 1, r, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_POSE_TANGENT, s);
+    e = launch_pose_tangents(w, g4, n, r, ctx->lm.tan, ctx->num_sms, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_RENDER_JAC, s);
+    e = launch_render_jac(w, r, l, delta, reinterpret_cast<const float4 *>(targets), ctx->lm.tan, ctx->lm.partial,
+                          normal, jac, image, last, s);
+    tm.end(ev, s);
+  }
+  (void)cam;
+  return cuda_status(e);
+}
+
+int lm_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
+                 const float *targets, const Raster &r, const Loss &l, const dags_lm_cfg &c, double *state,
+                 cudaStream_t s) {
+  int rc = normal_core(ctx, gauss, n, cam, ctx->lm.pose_try, targets, r, l, (float)c.delta, ctx->lm.normal,
+                       nullptr, nullptr, nullptr, s);
+  if (rc) return rc;
+  const int ev = ctx->timer.begin(DAGS_K_LM_STEP, s);
+  const cudaError_t e = launch_lm_step(ctx->lm.normal, state, ctx->lm.pose_try, pose, c, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+void dags_default_lm_cfg(dags_lm_cfg *c) {
+  if (!c) return;
+  c->mu0 = 1e-2;
+  c->mu_min = 1e-9;
+  c->mu_max = 1e9;
+  c->down = 0.1;
+  c->up = 10.0;
+  c->delta = 0.01;
+  c->floor = 1e-9;
+}
+
+int splat_normal_equations(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam,
+                           const double *pose, const float *targets, const dags_raster_cfg *rcfg,
+                           const dags_loss_cfg *lcfg, double delta, double *normal, float *jac, float *image,
+                           int32_t *last, void *stream) {
+  NvtxRange nv("splat_normal_equations");
+  int rc = common_args(ctx, gauss, n, cam, pose, 1);
+  if (rc) return rc;
+  if (!targets || !normal || !(delta > 0.0) || !isfinite(delta)) return DAGS_E_INVAL;
+  if (((uintptr_t)targets & 15u) != 0 || ((uintptr_t)jac & 15u) != 0) return DAGS_E_INVAL;
+  Raster r;
+  Loss l;
+  if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
+  if ((rc = ensure_lm(ctx))) return rc;
+  return normal_core(ctx, gauss, n, cam, pose, targets, r, l, (float)delta, normal, jac, image, last,
+                     (cudaStream_t)stream);
+}
+
+int lm_init(dags_ctx *ctx, const double *pose, const dags_lm_cfg *cfg, double *state, double *pose_try,
+            void *stream) {
+  NvtxRange nv("lm_init");
+  if (!ctx || !pose || !state || !pose_try) return DAGS_E_INVAL;
+  dags_lm_cfg c;
+  int rc = make_lm_cfg(cfg, &c);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return cuda_status(launch_lm_init(pose, state, pose_try, c.mu0, s));
+}
+
+int lm_pose_step(dags_ctx *ctx, const double *normal, const dags_lm_cfg *cfg, double *state, double *pose_try,
+                 double *pose_best, void *stream) {
+  NvtxRange nv("lm_pose_step");
+  if (!ctx || !normal || !state || !pose_try || !pose_best) return DAGS_E_INVAL;
+  dags_lm_cfg c;
+  int rc = make_lm_cfg(cfg, &c);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_LM_STEP, s);
+  const cudaError_t e = launch_lm_step(normal, state, pose_try, pose_best, c, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
+                   const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
+                   const dags_lm_cfg *lmcfg, int32_t iters, double *state, int32_t use_graph, void *stream) {
+  NvtxRange nv("splat_track_lm");
+  if (!ctx || iters < 0 || !pose || !targets || !state) return DAGS_E_INVAL;
+  int rc = common_args(ctx, gauss, n, cam, pose, 1);
+  if (rc) return rc;
+  if (((uintptr_t)targets & 15u) != 0) return DAGS_E_INVAL;
+  Raster r;
+  Loss l;
+  dags_lm_cfg c;
+  if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l)) || (rc = make_lm_cfg(lmcfg, &c))) return rc;
+  if ((rc = ensure_lm(ctx))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  if (launch_lm_init(pose, state, ctx->lm.pose_try, c.mu0, s) != cudaSuccess) return DAGS_E_CUDA;
+  if (!use_graph || ctx->timer.on) {
+    for (int k = 0; k < iters; ++k)
+      if ((rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, s))) return rc;
+    return DAGS_OK;
+  }
+  dags_raster_cfg rc_v;
+  dags_loss_cfg lc_v;
+  if (rcfg) rc_v = *rcfg; else dags_default_raster_cfg(&rc_v);
+  if (lcfg) lc_v = *lcfg; else dags_default_loss_cfg(&lc_v);
+  unsigned char key[512];
+  size_t kl = 0;
+  key_put(key, kl, gauss); key_put(key, kl, n); key_put(key, kl, *cam); key_put(key, kl, pose);
+  key_put(key, kl, targets); key_put(key, kl, rc_v); key_put(key, kl, lc_v); key_put(key, kl, c);
+  key_put(key, kl, state);
+  TrackGraph &g = ctx->graph_lm;
+  if (!g.exec || g.key_len != kl || memcmp(g.key, key, kl) != 0) {
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return DAGS_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return DAGS_E_CUDA;
+    if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
+    rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, g.cap);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
     if (rc != DAGS_OK || ce != cudaSuccess) {

@@ -125,6 +125,22 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
 cudaError_t launch_pose_step(double *poses, const double *grad, double *state, int views,
                              const dags_pose_cfg &cfg, cudaStream_t s);
 
+// Levenberg-Marquardt pose refinement (lm.cu).
+struct LmBuffers {
+  float4 *tan = nullptr;      // [max_n][9] twist tangents of the projected records (view 0)
+  float *partial = nullptr;   // [max_tiles][28] tile partials of the normal equations
+  double *normal = nullptr;   // [28] the loop's normal equations
+  double *pose_try = nullptr; // [12] the loop's linearisation point
+};
+cudaError_t launch_pose_tangents(const Workspace &ws, const float4 *gauss, int64_t n, const Raster &r, float4 *tan,
+                                 int num_sms, cudaStream_t s);
+cudaError_t launch_render_jac(const Workspace &ws, const Raster &r, const Loss &l, float delta,
+                              const float4 *targets, const float4 *tan, float *partial, double *normal, float *jac,
+                              float *image, int32_t *last, cudaStream_t s);
+cudaError_t launch_lm_init(const double *pose, double *state, double *pose_try, double mu0, cudaStream_t s);
+cudaError_t launch_lm_step(const double *normal, double *state, double *pose_try, double *pose_best,
+                           const dags_lm_cfg &c, cudaStream_t s);
+
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s);
 
@@ -389,19 +405,10 @@ __device__ inline double pow_int(double b, double kd) {
   return r;
 }
 
-__device__ inline void pose_adam_exp(double *T, const double *grad, double *st, const dags_pose_cfg &cfg) {
-  const double k = st[12] + 1.0;
-  const double bc1 = 1.0 - pow_int(cfg.beta1, k), bc2 = 1.0 - pow_int(cfg.beta2, k);
-  double xi[6];
-  for (int c = 0; c < 6; ++c) {
-    const double g = grad[c];
-    const double m = cfg.beta1 * st[c] + (1.0 - cfg.beta1) * g;
-    const double s2 = cfg.beta2 * st[6 + c] + (1.0 - cfg.beta2) * g * g;
-    st[c] = m;
-    st[6 + c] = s2;
-    xi[c] = -cfg.lr[c] * (m / bc1) / (sqrt(s2 / bc2) + cfg.eps);
-  }
-  st[12] = k;
+// T <- exp(xi^) T for the twist xi = (rho, phi) (translation first), FP64:
+// Rodrigues' formula for the rotation and the left Jacobian of SO(3) for the
+// translation, with series forms for small angles.
+__device__ inline void se3_exp_left(double *T, const double *xi) {
   const double px = xi[3], py = xi[4], pz = xi[5];
   const double t2 = px * px + py * py + pz * pz;
   double a, b, c;
@@ -438,6 +445,22 @@ __device__ inline void pose_adam_exp(double *T, const double *grad, double *st, 
     out[4 * i + 3] = Re[3 * i] * T[3] + Re[3 * i + 1] * T[7] + Re[3 * i + 2] * T[11] + te[i];
   }
   for (int e = 0; e < 12; ++e) T[e] = out[e];
+}
+
+__device__ inline void pose_adam_exp(double *T, const double *grad, double *st, const dags_pose_cfg &cfg) {
+  const double k = st[12] + 1.0;
+  const double bc1 = 1.0 - pow_int(cfg.beta1, k), bc2 = 1.0 - pow_int(cfg.beta2, k);
+  double xi[6];
+  for (int c = 0; c < 6; ++c) {
+    const double g = grad[c];
+    const double m = cfg.beta1 * st[c] + (1.0 - cfg.beta1) * g;
+    const double s2 = cfg.beta2 * st[6 + c] + (1.0 - cfg.beta2) * g * g;
+    st[c] = m;
+    st[6 + c] = s2;
+    xi[c] = -cfg.lr[c] * (m / bc1) / (sqrt(s2 / bc2) + cfg.eps);
+  }
+  st[12] = k;
+  se3_exp_left(T, xi);
 }
 
 // The same pose step spread over the first 12 threads of a CTA (dependent

@@ -25,6 +25,7 @@
 //                       L1 loss of Eqs. (20)-(22) in the epilogue; the last
 //                       CTA sums the loss in FP64.
 #include "common.cuh"
+#include "tile_sort.cuh"
 
 namespace dags {
 
@@ -374,51 +375,6 @@ emit_kernel(Workspace ws, int64_t n, Raster r) {
   walk_tiles<true>(ws, r, v, id, rect, r0, r1, z);
 }
 
-// Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
-__device__ __forceinline__ void bitonic_smem(uint64_t *s, int len2) {
-  for (int k = 2; k <= len2; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < (len2 >> 1); t += blockDim.x) {
-        const int i = 2 * t - (t & (j - 1));
-        const int p = i + j;
-        const uint64_t a = s[i], b = s[p];
-        const bool up = (i & k) == 0;
-        if ((a > b) == up) { s[i] = b; s[p] = a; }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-__device__ __forceinline__ int next_pow2(int x) {
-  int p = 1;
-  while (p < x) p <<= 1;
-  return p;
-}
-
-// Merge sorted runs a[0, la) and b[0, lb) into out[0, la + lb) with the CTA
-// (merge path: each thread finds its split by binary search, then merges its
-// slice sequentially). Keys are unique within a tile.
-__device__ void merge_runs(const uint64_t *a, int la, const uint64_t *b, int lb, uint64_t *out) {
-  const int m = la + lb;
-  const int per = (m + blockDim.x - 1) / blockDim.x;
-  const int k0 = min(m, (int)threadIdx.x * per);
-  const int k1 = min(m, k0 + per);
-  if (k0 < k1) {
-    int lo = max(0, k0 - lb), hi = min(k0, la);
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (a[mid] < b[k0 - mid - 1]) lo = mid + 1;
-      else hi = mid;
-    }
-    int ia = lo, ib = k0 - lo;
-    for (int k = k0; k < k1; ++k) {
-      const bool take_a = ib >= lb || (ia < la && a[ia] < b[ib]);
-      out[k] = take_a ? a[ia++] : b[ib++];
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kTilePix, 6)
 render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
                   float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
@@ -446,37 +402,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   // depth-sort the tile's bucket and publish the order for the backward: in
   // shared memory up to kSortSmallCap keys, else out of core (chunks sorted in
   // shared memory, then merged pairwise through global memory)
-  const int len = (int)(e - s);
-  const bool own_sort = len <= kSortSmallCap;
-  if (own_sort && len > 0) {
-    const int len2 = next_pow2(len);
-    for (int k = tid; k < len2; k += kTilePix) s_key[k] = k < len ? ws.keys[s + k] : ~0ull;
-    __syncthreads();
-    bitonic_smem(s_key, len2);
-    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)s_key[k];
-  } else if (len > 0) {
-    uint64_t *src = ws.keys + s, *dst = ws.keys_tmp + s;
-    for (int c0 = 0; c0 < len; c0 += kSortSmallCap) {
-      const int cl = min(kSortSmallCap, len - c0);
-      const int cl2 = next_pow2(cl);
-      for (int k = tid; k < cl2; k += kTilePix) s_key[k] = k < cl ? src[c0 + k] : ~0ull;
-      __syncthreads();
-      bitonic_smem(s_key, cl2);
-      for (int k = tid; k < cl; k += kTilePix) src[c0 + k] = s_key[k];
-      __syncthreads();
-    }
-    for (int width = kSortSmallCap; width < len; width <<= 1) {
-      for (int lo = 0; lo < len; lo += 2 * width) {
-        const int la = min(width, len - lo);
-        const int lb = max(0, min(width, len - lo - width));
-        merge_runs(src + lo, la, src + lo + la, lb, dst + lo);
-      }
-      __syncthreads();
-      uint64_t *t = src; src = dst; dst = t;
-    }
-    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)src[k];
-    __syncthreads();
-  }
+  const bool own_sort = sort_tile_bucket(ws, s, (int)(e - s), s_key);
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, oo = 0.f, rm = 0.f;
   int lastk = 0;

@@ -1,0 +1,102 @@
+// Per-tile depth sort shared by the render kernels (sm_103a): one CTA of
+// kTilePix threads sorts its tile's bucket of (depth bits << 32 | id) keys.
+#pragma once
+
+#include "common.cuh"
+
+namespace dags {
+
+// Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
+__device__ __forceinline__ void bitonic_smem(uint64_t *s, int len2) {
+  for (int k = 2; k <= len2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < (len2 >> 1); t += blockDim.x) {
+        const int i = 2 * t - (t & (j - 1));
+        const int p = i + j;
+        const uint64_t a = s[i], b = s[p];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) { s[i] = b; s[p] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Merge sorted runs a[0, la) and b[0, lb) into out[0, la + lb) with the CTA
+// (merge path: each thread finds its split by binary search, then merges its
+// slice sequentially). Keys are unique within a tile.
+__device__ inline void merge_runs(const uint64_t *a, int la, const uint64_t *b, int lb, uint64_t *out) {
+  const int m = la + lb;
+  const int per = (m + blockDim.x - 1) / blockDim.x;
+  const int k0 = min(m, (int)threadIdx.x * per);
+  const int k1 = min(m, k0 + per);
+  if (k0 < k1) {
+    int lo = max(0, k0 - lb), hi = min(k0, la);
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (a[mid] < b[k0 - mid - 1]) lo = mid + 1;
+      else hi = mid;
+    }
+    int ia = lo, ib = k0 - lo;
+    for (int k = k0; k < k1; ++k) {
+      const bool take_a = ib >= lb || (ia < la && a[ia] < b[ib]);
+      out[k] = take_a ? a[ia++] : b[ib++];
+    }
+  }
+}
+
+// True when the last preprocess needed more (tile, Gaussian) pairs than the
+// workspace holds: the buckets are then incomplete and nothing is rendered.
+__device__ __forceinline__ bool pairs_overflow_ws(const Workspace &ws) {
+  const uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
+  return tot > (uint64_t)ws.max_pairs;
+}
+
+// Depth-sorts the tile bucket keys[s, s + len) and publishes the ordered ids
+// in sorted_ids[s, s + len): in shared memory (s_key, kSortSmallCap keys) when
+// the bucket fits, then the sorted keys stay in s_key and the function
+// returns true; otherwise out of core (chunks sorted in shared memory, then
+// merged pairwise through global memory) and it returns false. Called by all
+// threads of the CTA.
+__device__ __forceinline__ bool sort_tile_bucket(const Workspace &ws, uint32_t s, int len, uint64_t *s_key) {
+  const int tid = threadIdx.x;
+  const bool own_sort = len <= kSortSmallCap;
+  if (own_sort && len > 0) {
+    const int len2 = next_pow2(len);
+    for (int k = tid; k < len2; k += kTilePix) s_key[k] = k < len ? ws.keys[s + k] : ~0ull;
+    __syncthreads();
+    bitonic_smem(s_key, len2);
+    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)s_key[k];
+  } else if (len > 0) {
+    uint64_t *src = ws.keys + s, *dst = ws.keys_tmp + s;
+    for (int c0 = 0; c0 < len; c0 += kSortSmallCap) {
+      const int cl = min(kSortSmallCap, len - c0);
+      const int cl2 = next_pow2(cl);
+      for (int k = tid; k < cl2; k += kTilePix) s_key[k] = k < cl ? src[c0 + k] : ~0ull;
+      __syncthreads();
+      bitonic_smem(s_key, cl2);
+      for (int k = tid; k < cl; k += kTilePix) src[c0 + k] = s_key[k];
+      __syncthreads();
+    }
+    for (int width = kSortSmallCap; width < len; width <<= 1) {
+      for (int lo = 0; lo < len; lo += 2 * width) {
+        const int la = min(width, len - lo);
+        const int lb = max(0, min(width, len - lo - width));
+        merge_runs(src + lo, la, src + lo + la, lb, dst + lo);
+      }
+      __syncthreads();
+      uint64_t *t = src; src = dst; dst = t;
+    }
+    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)src[k];
+    __syncthreads();
+  }
+  return own_sort;
+}
+
+}  // namespace dags

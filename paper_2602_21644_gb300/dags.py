@@ -60,6 +60,12 @@ class CSchedCfg(ctypes.Structure):
                 ("e_ref", ctypes.c_double), ("n_max", ctypes.c_int32)]
 
 
+class CLmCfg(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("mu0", "mu_min", "mu_max", "down", "up", "delta", "floor")]
+
+
+LM_NORMAL = 28
+LM_STATE = 48
 MP_STATS_HEAD = 6
 MPNET_WEIGHT_BYTES = 22016
 MPNET_ACT_WORDS = 96
@@ -75,10 +81,11 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "dags_default_raster_cfg", "dags_default_loss_cfg", "dags_default_pose_cfg", "splat_forward",
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
            "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
-           "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger"]
+           "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
+           "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
-           "mp_pixel", "mp_gauss", "mpnet", "mpnet_train"]
+           "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step"]
 
 _lib = None
 
@@ -141,6 +148,18 @@ def load(path: str = LIB_PATH):
     lib.dags_default_sched_cfg.restype = None
     lib.semantic_trigger.argtypes = [P, P, ctypes.POINTER(CSchedCfg), I32, P, P, P]
     lib.semantic_trigger.restype = ctypes.c_int
+    lib.dags_default_lm_cfg.argtypes = [ctypes.POINTER(CLmCfg)]
+    lib.dags_default_lm_cfg.restype = None
+    lib.splat_normal_equations.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
+                                           ctypes.POINTER(CLossCfg), ctypes.c_double, P, P, P, P, P]
+    lib.splat_normal_equations.restype = ctypes.c_int
+    lib.lm_init.argtypes = [P, P, ctypes.POINTER(CLmCfg), P, P, P]
+    lib.lm_init.restype = ctypes.c_int
+    lib.lm_pose_step.argtypes = [P, P, ctypes.POINTER(CLmCfg), P, P, P, P]
+    lib.lm_pose_step.restype = ctypes.c_int
+    lib.splat_track_lm.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
+                                   ctypes.POINTER(CLossCfg), ctypes.POINTER(CLmCfg), I32, P, I32, P]
+    lib.splat_track_lm.restype = ctypes.c_int
     lib.dags_selftest_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -208,6 +227,14 @@ def default_mp_cfg(**kw) -> CMpCfg:
 def default_sched_cfg(**kw) -> CSchedCfg:
     c = CSchedCfg()
     load().dags_default_sched_cfg(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_lm_cfg(**kw) -> CLmCfg:
+    c = CLmCfg()
+    load().dags_default_lm_cfg(ctypes.byref(c))
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -338,6 +365,56 @@ class Context:
                                     ctypes.byref(rc), ctypes.byref(lc), ctypes.byref(pc), int(iters),
                                     _ptr(adam_state), _ptr(image), _ptr(last), _ptr(loss), _ptr(grad_pose),
                                     int(bool(use_graph)), _stream()), "splat_track")
+
+    def normal_equations(self, gauss, cam: Camera, pose, targets, delta=0.01, rcfg=None, lcfg=None, jac=False,
+                         image=None, last=None, normal=None):
+        """IRLS normal equations of the MP-weighted L1 loss at pose (Levenberg-
+        Marquardt linearisation). Returns (normal float64 [28]: L, upper
+        triangle of H, g; jac float32 [H*W, 4, 6] or None)."""
+        _need(gauss, torch.float32, "gauss")
+        _need(targets, torch.float32, "targets")
+        _need(pose, torch.float64, "pose")
+        dev = gauss.device
+        if normal is None:
+            normal = torch.empty(LM_NORMAL, dtype=torch.float64, device=dev)
+        J = torch.empty((cam.width * cam.height, 4, 6), dtype=torch.float32, device=dev) if jac else None
+        c = cam.c()
+        rc = rcfg if rcfg is not None else default_raster_cfg()
+        lc = lcfg if lcfg is not None else default_loss_cfg()
+        _check(self.lib.splat_normal_equations(self.h, _ptr(gauss), gauss.shape[0], ctypes.byref(c), _ptr(pose),
+                                               _ptr(targets), ctypes.byref(rc), ctypes.byref(lc), float(delta),
+                                               _ptr(normal), _ptr(J), _ptr(image), _ptr(last), _stream()),
+               "splat_normal_equations")
+        return normal, J
+
+    def lm_init(self, pose, state, pose_try, cfg=None):
+        lc = cfg if cfg is not None else default_lm_cfg()
+        _check(self.lib.lm_init(self.h, _ptr(pose), ctypes.byref(lc), _ptr(state), _ptr(pose_try), _stream()),
+               "lm_init")
+
+    def lm_step(self, normal, state, pose_try, pose_best, cfg=None):
+        """One LM decision and damped step (FP64) from the normal equations."""
+        lc = cfg if cfg is not None else default_lm_cfg()
+        _check(self.lib.lm_pose_step(self.h, _ptr(normal), ctypes.byref(lc), _ptr(state), _ptr(pose_try),
+                                     _ptr(pose_best), _stream()), "lm_pose_step")
+
+    def track_lm(self, gauss, cam: Camera, pose, targets, iters, state=None, cfg=None, rcfg=None, lcfg=None,
+                 use_graph=True):
+        """iters Levenberg-Marquardt iterations from pose (in place: the best
+        pose). Returns the state tensor (float64 [48])."""
+        _need(gauss, torch.float32, "gauss")
+        _need(targets, torch.float32, "targets")
+        _need(pose, torch.float64, "pose")
+        if state is None:
+            state = torch.empty(LM_STATE, dtype=torch.float64, device=gauss.device)
+        c = cam.c()
+        rc = rcfg if rcfg is not None else default_raster_cfg()
+        lc = lcfg if lcfg is not None else default_loss_cfg()
+        mc = cfg if cfg is not None else default_lm_cfg()
+        _check(self.lib.splat_track_lm(self.h, _ptr(gauss), gauss.shape[0], ctypes.byref(c), _ptr(pose), _ptr(targets),
+                                       ctypes.byref(rc), ctypes.byref(lc), ctypes.byref(mc), int(iters), _ptr(state),
+                                       int(bool(use_graph)), _stream()), "splat_track_lm")
+        return state
 
     def mp_update(self, gauss, cam: Camera, pose, targets, image, inst, table, labels, cfg=None, seg_refreshed=True,
                   stats=None, mp_map=None, mp_pixel=None):
