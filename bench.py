@@ -202,6 +202,11 @@ def algorithmic_bytes(n, nv, K, P):
 # accumulations; backward alpha and T recovery, dL/dalpha over six channels,
 # suffix sums and the chain to the conic, mean, opacity, colour, depth, MP
 OPS_FWD, OPS_BWD = 16, 41
+# the LM Jacobian compositing: the forward's 16, 11 shared per evaluation
+# (exponent gradient, squared offsets, ln2 alpha, 1 - alpha) and 15 per twist
+# direction (the exponent's tangent, alpha', the weight's tangent, four
+# channel accumulations, T') over six directions
+OPS_JAC = 16 + 11 + 6 * 15
 # DRAM bytes (read + write) per launch at this workload from one ncu capture
 # of the current kernels (profiles/tracking_frame_300k_640x480.md)
 DRAM_TRAFFIC = {"render_fwd": 9212160, "render_bwd": 19869696}
@@ -260,6 +265,113 @@ def learned_mp_section(args, ctx, dags, synth, image, targets, inst, table, cam,
             "infer_us": round(t_inf, 2), "infer_frames_per_s": round(B / (t_inf * 1e-6), 1),
             "infer_tflops": round(flop / (t_inf * 1e-6) / 1e12, 2), "alg_flop_per_launch": flop,
             "train_step_us": round(t_tr, 2), "gpu_launches_infer": 1, "gpu_launches_train": 6}
+
+
+def lm_section(args, ctx, dags, gauss, cam, targets0, pose0, gt_pose, pcfg, flush, stream, alu_peak):
+    """Levenberg-Marquardt pose refinement (the second-order tracker) on the
+    bench's first tracking frame (300k Gaussians, 640x480, its ray-cast
+    target): device time per LM iteration through the captured loop (graph
+    replay, L2 flushed before every timed call) and per kernel (direct
+    launches with CUDA events). Then convergence on the same map with a
+    self-consistent target (the map rendered at the ground-truth pose; the
+    ray-cast target's loss minimum lies centimetres from the ground truth for
+    any optimiser): pose error after 15 LM iterations against 100 iterations
+    of the first-order tracker, and the device time of each."""
+    import torch
+    iters = 15
+    P = cam.width * cam.height
+    pose = pose0.clone().contiguous()
+    state = torch.empty(dags.LM_STATE, dtype=torch.float64, device=gauss.device)
+
+    def run_lm(tg, graph=True):
+        pose.copy_(pose0)
+        ctx.track_lm(gauss, cam, pose, tg, iters, state=state, use_graph=graph)
+
+    def time_it(fn, reps):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_frame = time_it(lambda: run_lm(targets0), 10)
+    ctx.timing_read()
+    ctx.timing(True)
+    for _ in range(3):
+        run_lm(targets0, graph=False)
+    torch.cuda.synchronize()
+    ctx.timing(False)
+    kt = ctx.timing_read()
+    kern = {}
+    for name in ("preprocess", "emit", "pose_tangent", "render_jac", "lm_step"):
+        ms, cnt = kt.get(name, (0.0, 0))
+        if cnt:
+            kern[name] = {"launches": cnt, "avg_us": round(1e3 * ms / cnt, 3)}
+    # evaluations of one Jacobian compositing launch at the starting pose
+    last = torch.empty(P, dtype=torch.int32, device=gauss.device)
+    ctx.normal_equations(gauss, cam, pose0.contiguous(), targets0, last=last)
+    E = int(last.to(torch.int64).sum().item())
+    jac_us = kern["render_jac"]["avg_us"]
+    jac_tops = E * OPS_JAC / (jac_us * 1e-6) / 1e12
+    roof = {"kernel": "render_jac", "bound": "alu", "achieved": round(jac_tops, 3), "peak": round(alu_peak, 2),
+            "unit": "TFLOP/s", "frac": round(jac_tops / alu_peak, 4), "ops_per_evaluation": OPS_JAC,
+            "evaluations_per_launch": E}
+
+    # convergence against a self-consistent target
+    image = torch.empty((1, dags.IMG_CHANNELS, cam.height, cam.width), dtype=torch.float32, device=gauss.device)
+    lastf = torch.empty((1, cam.height, cam.width), dtype=torch.int32, device=gauss.device)
+    ctx.forward(gauss, cam, gt_pose[None].contiguous(), None, image=image, last=lastf)
+    tg2 = torch.empty_like(targets0)
+    im = image[0].reshape(dags.IMG_CHANNELS, P)
+    tg2[:, 0:4] = im[0:4].t()
+    tg2[:, 3] = torch.where(im[4] > 0.5, im[3], torch.zeros_like(im[3]))
+    t_lm = time_it(lambda: run_lm(tg2), 5)
+    torch.cuda.synchronize()
+    e_lm = pose_error(pose.cpu().numpy(), gt_pose.cpu().numpy())
+    pa = pose0[None].clone().contiguous()
+    adam = torch.zeros((1, 13), dtype=torch.float64, device=gauss.device)
+    loss = torch.empty(1, dtype=torch.float64, device=gauss.device)
+    gp = torch.empty((1, 6), dtype=torch.float64, device=gauss.device)
+    tgb = tg2[None].contiguous()
+
+    def run_adam():
+        pa.copy_(pose0[None])
+        adam.zero_()
+        ctx.track(gauss, cam, pa, tgb, 100, adam, image, lastf, loss, gp, pcfg=pcfg)
+
+    t_adam = time_it(run_adam, 5)
+    torch.cuda.synchronize()
+    e_adam = pose_error(pa[0].cpu().numpy(), gt_pose.cpu().numpy())
+    e0 = pose_error(pose0.cpu().numpy(), gt_pose.cpu().numpy())
+    ctx.check()
+    return {"workload": "tracking frame 10: 300k Gaussians, 640x480, 15 LM iterations per frame",
+            "us_per_iter": round(1e3 * t_frame / iters, 3), "iters_per_s": round(iters / (t_frame * 1e-3), 1),
+            "kernels": kern, "roofline": roof,
+            "gpu_launches_per_iter": 5,
+            "convergence": {"target": "the map rendered at the ground-truth pose",
+                            "start_error": {"mm": round(1e3 * e0[0], 4), "deg": round(float(np.degrees(e0[1])), 5)},
+                            "lm_15_iters": {"mm": round(1e3 * e_lm[0], 4), "deg": round(float(np.degrees(e_lm[1])), 5),
+                                            "ms": round(t_lm, 3), "accepted": int(state[41].item())},
+                            "adam_100_iters": {"mm": round(1e3 * e_adam[0], 4),
+                                               "deg": round(float(np.degrees(e_adam[1])), 5), "ms": round(t_adam, 3)}}}
+
+
+def pose_error(T, T_gt):
+    """(camera-centre distance in m, rotation angle in rad) of world-to-camera poses."""
+    T = np.asarray(T, np.float64).reshape(3, 4)
+    T_gt = np.asarray(T_gt, np.float64).reshape(3, 4)
+    c = -T[:, :3].T @ T[:, 3]
+    c_gt = -T_gt[:, :3].T @ T_gt[:, 3]
+    R = T[:, :3] @ T_gt[:, :3].T
+    return float(np.linalg.norm(c - c_gt)), float(np.arccos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0)))
 
 
 def gain_section(dags):
@@ -474,6 +586,9 @@ def run_ours(args):
     if not args.no_gain and rank == 0:
         learned["gain"] = gain_section(dags)
     variants = splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, flush, stream)
+    lm = lm_section(args, ctx, dags, gauss, cam, tg_all[0, 0].contiguous(), pose_all[0, 0].contiguous(),
+                    torch.from_numpy(np.ascontiguousarray(seq[0]["gt_pose"])).to(dev), pcfg, flush, stream,
+                    ALU_LANES * float(load_peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6 / 1e12)
 
     peaks, src = load_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -545,6 +660,7 @@ def run_ours(args):
                            "peak_source": f"{src} bf16_tflops (burst: the launch is timed alone)"}
     line["learned_mp"] = learned
     line["splat_variants"] = variants
+    line["lm_tracking"] = lm
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(args, args.cpu_seconds)
     if rank == 0:
