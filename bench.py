@@ -202,11 +202,11 @@ def algorithmic_bytes(n, nv, K, P):
 # accumulations; backward alpha and T recovery, dL/dalpha over six channels,
 # suffix sums and the chain to the conic, mean, opacity, colour, depth, MP
 OPS_FWD, OPS_BWD = 16, 41
-# the LM Jacobian compositing: the forward's 16, 11 shared per evaluation
-# (exponent gradient, squared offsets, ln2 alpha, 1 - alpha) and 15 per twist
-# direction (the exponent's tangent, alpha', the weight's tangent, four
-# channel accumulations, T') over six directions
-OPS_JAC = 16 + 11 + 6 * 15
+# the LM Jacobian compositing: the forward's 16, 10 shared per evaluation
+# (exponent gradient, squared offsets, ln2 alpha) and 14 per twist direction
+# (the exponent's tangent 5, alpha' 1, the weight's tangent 2, four channel
+# accumulations 5, T' 1) over six directions
+OPS_JAC = 16 + 10 + 6 * 14
 # DRAM bytes (read + write) per launch at this workload from one ncu capture
 # of the current kernels (profiles/tracking_frame_300k_640x480.md)
 DRAM_TRAFFIC = {"render_fwd": 9212160, "render_bwd": 19869696}
@@ -355,7 +355,7 @@ def lm_section(args, ctx, dags, gauss, cam, targets0, pose0, gt_pose, pcfg, flus
     return {"workload": "tracking frame 10: 300k Gaussians, 640x480, 15 LM iterations per frame",
             "us_per_iter": round(1e3 * t_frame / iters, 3), "iters_per_s": round(iters / (t_frame * 1e-3), 1),
             "kernels": kern, "roofline": roof,
-            "gpu_launches_per_iter": 5,
+            "gpu_launches_per_iter": 4,
             "convergence": {"target": "the map rendered at the ground-truth pose",
                             "start_error": {"mm": round(1e3 * e0[0], 4), "deg": round(float(np.degrees(e0[1])), 5)},
                             "lm_15_iters": {"mm": round(1e3 * e_lm[0], 4), "deg": round(float(np.degrees(e_lm[1])), 5),

@@ -606,7 +606,7 @@ int make_lm_cfg(const dags_lm_cfg *in, dags_lm_cfg *c) {
 // Enqueues the normal equations of one view at `pose` (arguments checked).
 int normal_core(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
                 const float *targets, const Raster &r, const Loss &l, float delta, double *normal, float *jac,
-                float *image, int32_t *last, cudaStream_t s) {
+                float *image, int32_t *last, const LmFuse &fuse, cudaStream_t s) {
   ctx->last_stream = s;
   ctx->fwd_image = nullptr;     // the workspace no longer holds a forward for splat_backward
   const Workspace &w = ctx->ws;
@@ -628,7 +628,7 @@ int normal_core(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   if (e == cudaSuccess) {
     ev = tm.begin(DAGS_K_RENDER_JAC, s);
     e = launch_render_jac(w, r, l, delta, reinterpret_cast<const float4 *>(targets), ctx->lm.tan, ctx->lm.partial,
-                          normal, jac, image, last, s);
+                          normal, jac, image, last, fuse, s);
     tm.end(ev, s);
   }
   (void)cam;
@@ -638,13 +638,14 @@ int normal_core(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
 int lm_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                  const float *targets, const Raster &r, const Loss &l, const dags_lm_cfg &c, double *state,
                  cudaStream_t s) {
-  int rc = normal_core(ctx, gauss, n, cam, ctx->lm.pose_try, targets, r, l, (float)c.delta, ctx->lm.normal,
-                       nullptr, nullptr, nullptr, s);
-  if (rc) return rc;
-  const int ev = ctx->timer.begin(DAGS_K_LM_STEP, s);
-  const cudaError_t e = launch_lm_step(ctx->lm.normal, state, ctx->lm.pose_try, pose, c, s);
-  ctx->timer.end(ev, s);
-  return cuda_status(e);
+  // the LM step runs in the last CTA of the Jacobian render
+  LmFuse fuse;
+  fuse.state = state;
+  fuse.pose_try = ctx->lm.pose_try;
+  fuse.pose_best = pose;
+  fuse.cfg = c;
+  return normal_core(ctx, gauss, n, cam, ctx->lm.pose_try, targets, r, l, (float)c.delta, ctx->lm.normal, nullptr,
+                     nullptr, nullptr, fuse, s);
 }
 
 }  // namespace
@@ -675,7 +676,7 @@ int splat_normal_equations(dags_ctx *ctx, const float *gauss, int64_t n, const d
   Loss l;
   if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
   if ((rc = ensure_lm(ctx))) return rc;
-  return normal_core(ctx, gauss, n, cam, pose, targets, r, l, (float)delta, normal, jac, image, last,
+  return normal_core(ctx, gauss, n, cam, pose, targets, r, l, (float)delta, normal, jac, image, last, LmFuse(),
                      (cudaStream_t)stream);
 }
 

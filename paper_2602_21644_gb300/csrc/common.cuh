@@ -134,9 +134,16 @@ struct LmBuffers {
 };
 cudaError_t launch_pose_tangents(const Workspace &ws, const float4 *gauss, int64_t n, const Raster &r, float4 *tan,
                                  int num_sms, cudaStream_t s);
+// Optional LM step fused into the last CTA of the Jacobian render.
+struct LmFuse {
+  double *state = nullptr;      // nullptr: no step
+  double *pose_try = nullptr;
+  double *pose_best = nullptr;
+  dags_lm_cfg cfg;
+};
 cudaError_t launch_render_jac(const Workspace &ws, const Raster &r, const Loss &l, float delta,
                               const float4 *targets, const float4 *tan, float *partial, double *normal, float *jac,
-                              float *image, int32_t *last, cudaStream_t s);
+                              float *image, int32_t *last, const LmFuse &fuse, cudaStream_t s);
 cudaError_t launch_lm_init(const double *pose, double *state, double *pose_try, double mu0, cudaStream_t s);
 cudaError_t launch_lm_step(const double *normal, double *state, double *pose_try, double *pose_best,
                            const dags_lm_cfg &c, cudaStream_t s);

@@ -19,9 +19,12 @@
 //                         pixel the loss and W J J^T, W r J; tile partials in
 //                         FP32, the last CTA sums them in FP64 in a fixed order
 //                         into (L, H, g)
-//   lm_step_kernel        FP64, one thread: accept the linearisation point if
-//                         its loss is lower, adapt the damping, solve the
-//                         damped 6x6 system by Cholesky and step the pose
+//   LM step               FP64, one thread on shared-memory copies: accept the
+//                         linearisation point if its loss is lower, adapt the
+//                         damping, solve the damped 6x6 system by Cholesky and
+//                         step the pose; inside the tracking loop it runs in
+//                         the last CTA of render_jac_kernel, on its own as
+//                         lm_step_kernel
 //
 // The kernels use programmatic dependent launch like the other splatting
 // kernels: each waits for its predecessor's memory before its first access.
@@ -120,10 +123,101 @@ pose_tangent_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, R
 // Index of H[a][b] (a <= b) in the packed upper triangle.
 __host__ __device__ constexpr int tri(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }
 
+// LM state (DAGS_LM_STATE doubles): T_best[12], L_best, mu, H_best[21],
+// g_best[6], accepted count, iteration count, last L, last accepted flag.
+enum { ST_T = 0, ST_L = 12, ST_MU = 13, ST_H = 14, ST_G = 35, ST_ACC = 41, ST_IT = 42, ST_LAST_L = 43,
+       ST_LAST_A = 44 };
+
+// One LM decision and damped step by one thread, on shared-memory copies:
+// n the normal equations at p (the linearisation point), st the state; on
+// return st is updated and p holds the next linearisation point.
+__device__ void lm_decide_solve(const double *n, double *st, double *p, const dags_lm_cfg &c) {
+  const double L = n[0];
+  double mu = st[ST_MU];
+  const bool accept = L < st[ST_L];
+  if (accept) {
+    for (int k = 0; k < 12; ++k) st[ST_T + k] = p[k];
+    st[ST_L] = L;
+    for (int k = 0; k < 21; ++k) st[ST_H + k] = n[1 + k];
+    for (int k = 0; k < 6; ++k) st[ST_G + k] = n[22 + k];
+    mu = fmax(mu * c.down, c.mu_min);
+    st[ST_ACC] += 1.0;
+  } else {
+    mu = fmin(mu * c.up, c.mu_max);
+  }
+  st[ST_MU] = mu;
+  st[ST_IT] += 1.0;
+  st[ST_LAST_L] = L;
+  st[ST_LAST_A] = accept ? 1.0 : 0.0;
+  // (H + mu diag(H) + floor tr(H)/6 I) delta = -g by Cholesky
+  double A[6][6], d[6];
+  double tr = 0.0;
+  for (int a = 0; a < 6; ++a) tr += st[ST_H + tri(a, a)];
+  bool ok = tr > 0.0;
+  if (ok) {
+    for (int a = 0; a < 6; ++a)
+      for (int b = a; b < 6; ++b) A[a][b] = A[b][a] = st[ST_H + tri(a, b)];
+    for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a] + c.floor * (tr / 6.0);
+    for (int j = 0; j < 6 && ok; ++j) {
+      double sjj = A[j][j];
+      for (int k = 0; k < j; ++k) sjj -= A[j][k] * A[j][k];
+      if (!(sjj > 0.0)) { ok = false; break; }
+      // the diagonal holds 1 / l_jj: one reciprocal square root per pivot and
+      // multiplications elsewhere (dependent FP64 divisions are what costs)
+      const double inv = rsqrt(sjj);
+      A[j][j] = inv;
+      for (int i = j + 1; i < 6; ++i) {
+        double sij = A[i][j];
+        for (int k = 0; k < j; ++k) sij -= A[i][k] * A[j][k];
+        A[i][j] = sij * inv;
+      }
+    }
+  }
+  if (ok) {
+    double y[6];
+    for (int i = 0; i < 6; ++i) {
+      double t = -st[ST_G + i];
+      for (int k = 0; k < i; ++k) t -= A[i][k] * y[k];
+      y[i] = t * A[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+      double t = y[i];
+      for (int k = i + 1; k < 6; ++k) t -= A[k][i] * d[k];
+      d[i] = t * A[i][i];
+    }
+  } else {
+    for (int i = 0; i < 6; ++i) d[i] = 0.0;
+  }
+  double T[12];
+  for (int k = 0; k < 12; ++k) T[k] = st[ST_T + k];
+  se3_exp_left(T, d);
+  for (int k = 0; k < 12; ++k) p[k] = T[k];
+}
+
+// The LM step by a CTA of at least 48 threads (all must call it): the inputs
+// are staged in shared memory by parallel loads, one thread decides and
+// solves, and the results are written back in parallel.
+__device__ void lm_step_cta(const double *nrm, double *state, double *pose_try, double *pose_best,
+                            const dags_lm_cfg &c) {
+  __shared__ double s_n[kNormal], s_st[DAGS_LM_STATE], s_p[12];
+  const int t = threadIdx.x;
+  if (t < kNormal) s_n[t] = nrm[t];
+  if (t < DAGS_LM_STATE) s_st[t] = state[t];
+  if (t < 12) s_p[t] = pose_try[t];
+  __syncthreads();
+  if (t == 0) lm_decide_solve(s_n, s_st, s_p, c);
+  __syncthreads();
+  if (t < DAGS_LM_STATE) state[t] = s_st[t];
+  if (t < 12) {
+    pose_try[t] = s_p[t];
+    pose_best[t] = s_st[ST_T + t];
+  }
+}
+
 __global__ void __launch_bounds__(kTilePix, 2)
 render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__restrict__ targets,
                   const float4 *__restrict__ tan, float *__restrict__ partial, double *__restrict__ normal,
-                  float *__restrict__ jac, float *__restrict__ image, int32_t *__restrict__ last) {
+                  float *__restrict__ jac, float *__restrict__ image, int32_t *__restrict__ last, LmFuse fuse) {
   pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
   __shared__ uint32_t s_id[kJacBatch];
@@ -198,12 +292,11 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
         cr += cR * w; cg += cG * w; cb += cB * w;
         dd += c.x * w; oo += w; rm += c.y * w;
         // tangents: p' = da' dx^2 + db' dx dy + dc' dy^2 + dp/du du + dp/dv dv,
-        // alpha' = alpha ln2 p' (0 where clamped), weight' = alpha' T + alpha T',
-        // T' of the next entry = T' (1 - alpha) - T alpha'
+        // alpha' = alpha ln2 p' (0 where clamped), weight' = alpha' T + alpha T';
+        // the next entry's T = T - weight, so its T' = T' - weight'
         const float gx = fmaf(2.f * b.x, dx, b.y * dy), gy = fmaf(b.y, dx, 2.f * b.z * dy);
         const float dx2 = dx * dx, dxy = dx * dy, dy2 = dy * dy;
         const float aln = clamped ? 0.f : alpha * kLn2;
-        const float om = 1.f - alpha;
         const float4 *t4 = s_t + j * kTan4;
         float tv[36];
 #pragma unroll
@@ -221,7 +314,7 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
           jg[k] = fmaf(cG, dw, jg[k]);
           jb[k] = fmaf(cB, dw, jb[k]);
           jd[k] = fmaf(c.x, dw, fmaf(w, t[5], jd[k]));
-          dT[k] = fmaf(dT[k], om, -T * da);
+          dT[k] -= dw;
         }
         T = tt;
         lastk = (int)(base - s) + j + 1;
@@ -308,21 +401,22 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
     s_d[tid] = a2;
   }
   __syncthreads();
+  __shared__ double s_nrm[kNormal];
   if (tid < kNormal) {
     double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += s_d[tid * 8 + k];
     // a pair-capacity overflow leaves nothing rendered: the loss is NaN, so
     // the LM step rejects this point
-    normal[tid] = (ovf && tid == 0) ? __longlong_as_double(0x7ff8000000000000ll) : t;
+    if (ovf && tid == 0) t = __longlong_as_double(0x7ff8000000000000ll);
+    normal[tid] = t;
+    s_nrm[tid] = t;
   }
   if (tid == 0) ws.counters[CNT_DONE_RENDER] = 0u;
+  __syncthreads();
+  // inside the LM loop the step runs here, in the last CTA
+  if (fuse.state) lm_step_cta(s_nrm, fuse.state, fuse.pose_try, fuse.pose_best, fuse.cfg);
 }
-
-// LM state (DAGS_LM_STATE doubles): T_best[12], L_best, mu, H_best[21],
-// g_best[6], accepted count, iteration count, last L, last accepted flag.
-enum { ST_T = 0, ST_L = 12, ST_MU = 13, ST_H = 14, ST_G = 35, ST_ACC = 41, ST_IT = 42, ST_LAST_L = 43,
-       ST_LAST_A = 44 };
 
 __global__ void lm_init_kernel(const double *__restrict__ pose, double *__restrict__ state,
                                double *__restrict__ pose_try, double mu0) {
@@ -343,68 +437,7 @@ __global__ void lm_init_kernel(const double *__restrict__ pose, double *__restri
 __global__ void lm_step_kernel(const double *__restrict__ normal, double *__restrict__ state,
                                double *__restrict__ pose_try, double *__restrict__ pose_best, dags_lm_cfg c) {
   pdl_wait();
-  if (threadIdx.x != 0) return;
-  const double L = normal[0];
-  double mu = state[ST_MU];
-  const bool accept = L < state[ST_L];
-  if (accept) {
-    for (int k = 0; k < 12; ++k) state[ST_T + k] = pose_try[k];
-    state[ST_L] = L;
-    for (int k = 0; k < 21; ++k) state[ST_H + k] = normal[1 + k];
-    for (int k = 0; k < 6; ++k) state[ST_G + k] = normal[22 + k];
-    mu = fmax(mu * c.down, c.mu_min);
-    state[ST_ACC] += 1.0;
-  } else {
-    mu = fmin(mu * c.up, c.mu_max);
-  }
-  state[ST_MU] = mu;
-  state[ST_IT] += 1.0;
-  state[ST_LAST_L] = L;
-  state[ST_LAST_A] = accept ? 1.0 : 0.0;
-  // (H + mu diag(H) + floor tr(H)/6 I) delta = -g by Cholesky
-  double A[6][6], d[6];
-  double tr = 0.0;
-  for (int a = 0; a < 6; ++a) tr += state[ST_H + tri(a, a)];
-  bool ok = tr > 0.0;
-  if (ok) {
-    for (int a = 0; a < 6; ++a)
-      for (int b = a; b < 6; ++b) A[a][b] = A[b][a] = state[ST_H + tri(a, b)];
-    for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a] + c.floor * (tr / 6.0);
-    for (int j = 0; j < 6 && ok; ++j) {
-      double sjj = A[j][j];
-      for (int k = 0; k < j; ++k) sjj -= A[j][k] * A[j][k];
-      if (!(sjj > 0.0)) { ok = false; break; }
-      const double ljj = sqrt(sjj);
-      A[j][j] = ljj;
-      for (int i = j + 1; i < 6; ++i) {
-        double sij = A[i][j];
-        for (int k = 0; k < j; ++k) sij -= A[i][k] * A[j][k];
-        A[i][j] = sij / ljj;
-      }
-    }
-  }
-  if (ok) {
-    double y[6];
-    for (int i = 0; i < 6; ++i) {
-      double t = -state[ST_G + i];
-      for (int k = 0; k < i; ++k) t -= A[i][k] * y[k];
-      y[i] = t / A[i][i];
-    }
-    for (int i = 5; i >= 0; --i) {
-      double t = y[i];
-      for (int k = i + 1; k < 6; ++k) t -= A[k][i] * d[k];
-      d[i] = t / A[i][i];
-    }
-  } else {
-    for (int i = 0; i < 6; ++i) d[i] = 0.0;
-  }
-  double T[12];
-  for (int k = 0; k < 12; ++k) {
-    T[k] = state[ST_T + k];
-    pose_best[k] = T[k];
-  }
-  se3_exp_left(T, d);
-  for (int k = 0; k < 12; ++k) pose_try[k] = T[k];
+  lm_step_cta(normal, state, pose_try, pose_best, c);
 }
 
 }  // namespace
@@ -419,9 +452,9 @@ cudaError_t launch_pose_tangents(const Workspace &ws, const float4 *gauss, int64
 
 cudaError_t launch_render_jac(const Workspace &ws, const Raster &r, const Loss &l, float delta,
                               const float4 *targets, const float4 *tan, float *partial, double *normal, float *jac,
-                              float *image, int32_t *last, cudaStream_t s) {
+                              float *image, int32_t *last, const LmFuse &fuse, cudaStream_t s) {
   return launch_pdl(render_jac_kernel, dim3((unsigned)r.T), dim3(kTilePix), 0, s, ws, r, l, delta, targets, tan,
-                    partial, normal, jac, image, last);
+                    partial, normal, jac, image, last, fuse);
 }
 
 cudaError_t launch_lm_init(const double *pose, double *state, double *pose_try, double mu0, cudaStream_t s) {
@@ -430,7 +463,7 @@ cudaError_t launch_lm_init(const double *pose, double *state, double *pose_try, 
 
 cudaError_t launch_lm_step(const double *normal, double *state, double *pose_try, double *pose_best,
                            const dags_lm_cfg &c, cudaStream_t s) {
-  return launch_pdl(lm_step_kernel, dim3(1), dim3(32), 0, s, normal, state, pose_try, pose_best, c);
+  return launch_pdl(lm_step_kernel, dim3(1), dim3(64), 0, s, normal, state, pose_try, pose_best, c);
 }
 
 }  // namespace dags
