@@ -15,6 +15,7 @@ Contents
                           depth along the pose twist, and the IRLS normal
                           equations of the MP-weighted L1 loss
   lm                      Levenberg-Marquardt pose refinement (Sec. V-A(c))
+  regular                 the MP motion-consistency regulariser, Eqs. (23), (24)
   mpnet                   the small per-pixel MP proposal network
   schedule                the semantic-on-demand trigger, Eqs. (13)-(16)
 
