@@ -407,7 +407,9 @@ def splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, f
     - the full-parameter fwd+bwd variant at the tracking size (one view;
       gradients of every Gaussian parameter and of the pose);
     - the mapping step: 200k Gaussians, 8 keyframes of 640x480, one iteration
-      = render + backward of all 8 views w.r.t. all parameters."""
+      = render + backward of all 8 views w.r.t. all parameters, plus the
+      lambda_3 L_MP gradient;
+    - the L_MP regulariser alone at the tracking map's size."""
     import torch
 
     def time_it(fn, reps=10):
@@ -439,11 +441,24 @@ def splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, f
     mt = torch.from_numpy(np.ascontiguousarray(ms.targets)).cuda()
     mctx = dags.Context(mg.shape[0], mcam.width, mcam.height, ms.poses.shape[0])
 
+    mprev = mg.clone()          # the records after the previous mapping update (Eq. (23))
+
     def map_iter():
+        # Eq. (27) without the edge term: MP-weighted L1 of every view, then
+        # lambda_3 L_MP added into the Gaussian gradient
         image, last, _ = mctx.forward(mg, mcam, mp, mt)
-        mctx.backward(mg, mcam, mp, mt, image, last, flags)
+        gg, _ = mctx.backward(mg, mcam, mp, mt, image, last, flags)
+        mctx.mp_consistency(mg, mprev, 500.0, grad=gg, want_loss=False)
 
     t_map = time_it(map_iter)
+    # the regulariser alone at the tracking map's size: HBM-bound, 80 bytes
+    # per Gaussian (two float4 of the record, one of the snapshot, the
+    # gradient's first float4 read and written)
+    prev = gauss.clone()
+    greg = torch.zeros_like(gauss)
+    t_reg = time_it(lambda: ctx.mp_consistency(gauss, prev, 500.0, grad=greg), reps=20)
+    reg_bytes = 80 * gauss.shape[0]
+    hbm = float(load_peaks()[0]["hbm_gbs"])
     torch.cuda.synchronize()
     ctx.check()
     mctx.check()
@@ -453,7 +468,11 @@ def splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, f
                                    "ms_per_iter": round(t_full, 4), "iters_per_s": round(1e3 / t_full, 2)},
             "mapping": {"workload": f"200000 Gaussians, 8 keyframes of {mcam.width}x{mcam.height}, render + "
                                     "backward of all views w.r.t. all parameters",
-                        "ms_per_iter": round(t_map, 4), "iters_per_s": round(1e3 / t_map, 2)}}
+                        "ms_per_iter": round(t_map, 4), "iters_per_s": round(1e3 / t_map, 2),
+                        "includes": "lambda_3 L_MP gradient (Eqs. (23), (24))"},
+            "mp_consistency": {"workload": f"lambda_3 L_MP and its gradient over {gauss.shape[0]} Gaussians",
+                               "us": round(1e3 * t_reg, 3), "alg_bytes": reg_bytes,
+                               "hbm_frac": round(reg_bytes / (t_reg * 1e-3) / 1e9 / hbm, 4)}}
 
 
 def run_ours(args):

@@ -360,6 +360,25 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
                    const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                    const dags_lm_cfg *lmcfg, int32_t iters, double *state, int32_t use_graph, void *stream);
 
+/* MP-based motion-consistency regulariser (Sec. IV-D, Eqs. (23), (24)):
+ *   mu_hat_k = T_rel mu_k^{t-1},  lambda L_MP = lambda sum_k (1 - M_k) |mu_k - mu_hat_k|^2
+ * over all n Gaussians, M_k = the record's MP (word 11, held constant).
+ * gauss      device, n records (the current means, words 0-2)
+ * prev       device, n records: the snapshot after the previous mapping
+ *            update (only words 0-2 are read), 16-byte aligned
+ * rel_pose   device, 12 doubles [R | t] mapping the previous frame's
+ *            coordinates to the current ones, or NULL: identity (a map in
+ *            world coordinates, as this library keeps it)
+ * lambda     the weight (the paper's lambda_3 = 500)
+ * grad_gauss device, n x 16 floats, or NULL: d(lambda L_MP)/d mu is ADDED to
+ *            words 0-2 (the splat_backward layout), other words untouched
+ * loss       device, 1 double, or NULL: lambda L_MP, summed in FP64 in a
+ *            fixed order (deterministic)
+ * The first call on a ctx allocates a small buffer (before any stream
+ * capture). */
+int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const float *prev, const double *rel_pose,
+                         float lambda, float *grad_gauss, double *loss, void *stream);
+
 /* Semantic-on-demand trigger constants (Sec. IV-B). The paper gives none of
  * their values; defaults from dags_default_sched_cfg. */
 typedef struct {
@@ -482,6 +501,7 @@ enum {
   DAGS_K_POSE_TANGENT,     /* LM: twist tangents of the visible Gaussians  */
   DAGS_K_RENDER_JAC,       /* LM: forward-mode compositing + normal eqs.   */
   DAGS_K_LM_STEP,          /* LM: FP64 decision, solve and pose step       */
+  DAGS_K_REGULARISER,      /* L_MP motion-consistency regulariser          */
   DAGS_KERNEL_COUNT
 };
 int dags_timing_enable(dags_ctx *ctx, int enable);

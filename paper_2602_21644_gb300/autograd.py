@@ -59,3 +59,32 @@ def splat_loss(ctx, cam, gauss, poses, targets, xi=None, rcfg=None, lcfg=None):
     if xi is None:
         xi = torch.zeros((poses.shape[0], 6), dtype=torch.float64, device=poses.device)
     return SplatLoss.apply(gauss, xi, ctx, cam, poses, targets, rcfg, lcfg)
+
+
+class MPConsistency(torch.autograd.Function):
+    """loss = MPConsistency.apply(gauss, ctx, prev, lam, rel_pose)
+
+    lambda * L_MP of Eqs. (23), (24) over all Gaussians, with its gradient
+    with respect to the means (record words 0-2; the MP word is held
+    constant). prev: the records after the previous mapping update. Returns a
+    [1] float64 tensor."""
+
+    @staticmethod
+    def forward(fctx, gauss, ctx, prev, lam, rel_pose=None):
+        loss = ctx.mp_consistency(gauss, prev, lam, rel_pose=rel_pose)
+        fctx.save_for_backward(gauss, prev)
+        fctx.dags_ctx, fctx.lam, fctx.rel_pose = ctx, lam, rel_pose
+        return loss
+
+    @staticmethod
+    def backward(fctx, gloss):
+        gauss, prev = fctx.saved_tensors
+        grad = torch.zeros_like(gauss)
+        fctx.dags_ctx.mp_consistency(gauss, prev, fctx.lam, rel_pose=fctx.rel_pose, grad=grad, want_loss=False)
+        return grad * gloss.reshape(()).to(grad.dtype), None, None, None, None
+
+
+def mp_consistency(ctx, gauss, prev, lam=500.0, rel_pose=None):
+    """Differentiable lambda * L_MP (Sec. IV-D): add it to splat_loss's value
+    for the mapping objective of Eq. (27)."""
+    return MPConsistency.apply(gauss, ctx, prev, lam, rel_pose)

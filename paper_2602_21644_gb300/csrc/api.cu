@@ -83,6 +83,7 @@ struct dags_ctx {
   TrackGraph graph;
   TrackGraph graph_lm;            // captured LM iteration
   LmBuffers lm;                   // allocated by the first LM call
+  double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
   MpBuffers mp;
   MpnetScratch net;
   PoseStep fused_step;            // set only inside the tracking loop
@@ -333,6 +334,7 @@ void dags_destroy(dags_ctx *ctx) {
   if (ctx->graph_lm.exec) cudaGraphExecDestroy(ctx->graph_lm.exec);
   if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
   free_lm(ctx->lm);
+  if (ctx->reg_partial) cudaFree(ctx->reg_partial);
   free_mp(ctx->mp);
   free_net(ctx->net);
   free_ws(ctx->ws);
@@ -761,6 +763,31 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   for (int k = 0; k < iters; ++k)
     if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return DAGS_E_CUDA;
   return DAGS_OK;
+}
+
+int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const float *prev, const double *rel_pose,
+                         float lambda, float *grad_gauss, double *loss, void *stream) {
+  NvtxRange nv("splat_mp_consistency");
+  if (!ctx || n < 0 || n > ctx->ws.max_n || (n > 0 && (!gauss || !prev)) || !isfinite(lambda) || lambda < 0.f)
+    return DAGS_E_INVAL;
+  if (((uintptr_t)gauss & 15u) != 0 || ((uintptr_t)prev & 15u) != 0 || ((uintptr_t)grad_gauss & 15u) != 0)
+    return DAGS_E_INVAL;
+  if (!ctx->reg_partial) {
+    const cudaError_t a = alloc(&ctx->reg_partial, (size_t)mp_consistency_blocks(ctx->ws.max_n) + 1);
+    if (a != cudaSuccess) {
+      cudaGetLastError();
+      ctx->reg_partial = nullptr;
+      return a == cudaErrorMemoryAllocation ? DAGS_E_NOMEM : DAGS_E_CUDA;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_REGULARISER, s);
+  const cudaError_t e = launch_mp_consistency(reinterpret_cast<const float4 *>(gauss),
+                                              reinterpret_cast<const float4 *>(prev), n, rel_pose, lambda,
+                                              grad_gauss, ctx->reg_partial, ctx->ws.counters + CNT_DONE_REG, loss, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
 }
 
 void dags_default_mp_cfg(dags_mp_cfg *c) {

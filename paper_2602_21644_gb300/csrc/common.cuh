@@ -44,7 +44,7 @@ enum {
   CNT_DONE_PREP = 0,   // CTAs of the preprocess kernel that finished
   CNT_DONE_RENDER,     // CTAs of the forward render that finished
   CNT_DONE_BWDPREP,    // CTAs of the preprocess backward that finished
-  CNT_UNUSED,
+  CNT_DONE_REG,        // CTAs of the regulariser that finished
   CNT_STATUS,          // status bits
   CNT_REQ_LO,          // pairs required by the last forward (low / high word)
   CNT_REQ_HI,
@@ -147,6 +147,11 @@ cudaError_t launch_render_jac(const Workspace &ws, const Raster &r, const Loss &
 cudaError_t launch_lm_init(const double *pose, double *state, double *pose_try, double mu0, cudaStream_t s);
 cudaError_t launch_lm_step(const double *normal, double *state, double *pose_try, double *pose_best,
                            const dags_lm_cfg &c, cudaStream_t s);
+
+// MP motion-consistency regulariser (regular.cu).
+int64_t mp_consistency_blocks(int64_t n);
+cudaError_t launch_mp_consistency(const float4 *gauss, const float4 *prev, int64_t n, const double *rel, float lam,
+                                  float *grad, double *partial, uint32_t *done, double *loss, cudaStream_t s);
 
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s);

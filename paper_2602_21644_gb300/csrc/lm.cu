@@ -36,6 +36,7 @@ namespace dags {
 namespace {
 
 constexpr int kJacBatch = 128;   // list entries staged in shared memory per round
+static_assert(2 * kJacBatch == kTilePix, "two threads stage each entry");
 constexpr int kTan4 = 9;         // float4 per Gaussian tangent record (36 floats)
 constexpr int kNormal = 28;      // L, the upper triangle of H (21), g (6)
 
@@ -220,7 +221,6 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
                   float *__restrict__ jac, float *__restrict__ image, int32_t *__restrict__ last, LmFuse fuse) {
   pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
-  __shared__ uint32_t s_id[kJacBatch];
   __shared__ float4 s_a[kJacBatch], s_b[kJacBatch], s_c[kJacBatch];
   __shared__ float4 s_t[kJacBatch * kTan4];
   __shared__ float s_red[kTilePix / 32][kNormal];
@@ -248,19 +248,25 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   for (uint32_t base = s; base < e; base += kJacBatch) {
     if (__syncthreads_count(!done) == 0) break;
     const int cnt = (int)min((uint32_t)kJacBatch, e - base);
-    if (tid < cnt) {
-      const uint32_t k = base + tid;
+    // entry q is staged by threads q (its record and tangent words 0-3) and
+    // q + kJacBatch (tangent words 4-8)
+    const int q = tid & (kJacBatch - 1);
+    if (q < cnt) {
+      const uint32_t k = base + q;
       uint32_t id = own_sort ? (uint32_t)s_key[k - s] : ws.sorted_ids[k];
       if (!DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n, ws.counters + CNT_STATUS)) id = 0;
-      s_id[tid] = id;
-      s_a[tid] = ws.rec2d[(size_t)id * 3 + 0];
-      s_b[tid] = ws.rec2d[(size_t)id * 3 + 1];
-      s_c[tid] = ws.rec2d[(size_t)id * 3 + 2];
-    }
-    __syncthreads();
-    for (int q = tid; q < cnt * kTan4; q += kTilePix) {
-      const int ent = q / kTan4, w = q - ent * kTan4;
-      s_t[q] = tan[(size_t)s_id[ent] * kTan4 + w];
+      const float4 *tg = tan + (size_t)id * kTan4;
+      float4 *st = s_t + q * kTan4;
+      if (tid < kJacBatch) {
+        s_a[q] = ws.rec2d[(size_t)id * 3 + 0];
+        s_b[q] = ws.rec2d[(size_t)id * 3 + 1];
+        s_c[q] = ws.rec2d[(size_t)id * 3 + 2];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) st[w] = tg[w];
+      } else {
+#pragma unroll
+        for (int w = 4; w < kTan4; ++w) st[w] = tg[w];
+      }
     }
     __syncthreads();
     if (__all_sync(FULL, done)) continue;

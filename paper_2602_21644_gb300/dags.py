@@ -82,10 +82,12 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "splat_backward", "pose_step", "dags_copy_bins", "dags_timing_enable", "dags_timing_read",
            "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
            "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
-           "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm"]
+           "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
+           "splat_mp_consistency"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
-           "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step"]
+           "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
+           "regulariser"]
 
 _lib = None
 
@@ -160,6 +162,8 @@ def load(path: str = LIB_PATH):
     lib.splat_track_lm.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
                                    ctypes.POINTER(CLossCfg), ctypes.POINTER(CLmCfg), I32, P, I32, P]
     lib.splat_track_lm.restype = ctypes.c_int
+    lib.splat_mp_consistency.argtypes = [P, P, I64, P, P, ctypes.c_float, P, P, P]
+    lib.splat_mp_consistency.restype = ctypes.c_int
     lib.dags_selftest_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -415,6 +419,25 @@ class Context:
                                        ctypes.byref(rc), ctypes.byref(lc), ctypes.byref(mc), int(iters), _ptr(state),
                                        int(bool(use_graph)), _stream()), "splat_track_lm")
         return state
+
+    def mp_consistency(self, gauss, prev, lam=500.0, rel_pose=None, grad=None, loss=None, want_loss=True):
+        """MP motion-consistency regulariser lambda * L_MP (Eqs. (23), (24)).
+        prev: the records after the previous mapping update (n x 16 float32).
+        grad (n x 16 float32, optional) receives d/d mean added into words
+        0-2. Returns the loss tensor (float64 [1]) or None."""
+        _need(gauss, torch.float32, "gauss")
+        _need(prev, torch.float32, "prev")
+        if prev.shape != gauss.shape:
+            raise ValueError("prev must have the records' shape")
+        if grad is not None:
+            _need(grad, torch.float32, "grad")
+        if rel_pose is not None:
+            _need(rel_pose, torch.float64, "rel_pose")
+        if loss is None and want_loss:
+            loss = torch.empty(1, dtype=torch.float64, device=gauss.device)
+        _check(self.lib.splat_mp_consistency(self.h, _ptr(gauss), gauss.shape[0], _ptr(prev), _ptr(rel_pose),
+                                             float(lam), _ptr(grad), _ptr(loss), _stream()), "splat_mp_consistency")
+        return loss
 
     def mp_update(self, gauss, cam: Camera, pose, targets, image, inst, table, labels, cfg=None, seg_refreshed=True,
                   stats=None, mp_map=None, mp_pixel=None):
