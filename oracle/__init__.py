@@ -16,6 +16,7 @@ Contents
                           equations of the MP-weighted L1 loss
   lm                      Levenberg-Marquardt pose refinement (Sec. V-A(c))
   regular                 the MP motion-consistency regulariser, Eqs. (23), (24)
+  edge                    the MP-guided edge-warp regulariser, Eqs. (25), (26)
   mpnet                   the small per-pixel MP proposal network
   schedule                the semantic-on-demand trigger, Eqs. (13)-(16)
 
