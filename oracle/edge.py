@@ -11,9 +11,10 @@ For an edge pixel u of frame i, with the aligned depth observation D_i(u):
   L   = lambda_4 sum_u rho(r)                        Eq. (26), rho Huber
 
 Readings (the paper leaves these open):
-- Edge pixels E_i: depth discontinuities of the observation. u is an edge if
-  D_i(u) > 0 and some 4-neighbour n with D_i(n) > 0 has
-  |D_i(n) - D_i(u)| > edge_thr (0.05 m).
+- Edge pixels E_i: depth discontinuities of the observation, relative to the
+  depth (sensor noise grows with it). u is an edge if D_i(u) > 0 and some
+  4-neighbour n with D_i(n) > 0 has |D_i(n) - D_i(u)| > edge_rel D_i(u)
+  (edge_rel = 0.05).
 - z_ref: the depth of the warped point in frame j, Y_z. Eq. (26) writes
   D_i(u), which equals Y_z only when the relative motion has no component
   along the viewing direction; literal=True uses D_i(u).
@@ -28,14 +29,14 @@ Readings (the paper leaves these open):
   world-to-camera poses, T <- exp(xi^) T.
 
 Decisions that a float can take differently are flagged: an edge test within
-1e-5 relative of edge_thr, u' within 1e-3 px of a cell boundary or the image
+1e-5 relative of its threshold, u' within 1e-3 px of a cell boundary or the image
 border, Y_z within 1e-5 of z_near, |r| within 1e-5 relative of delta_h.
 
-Pins (tests/test_oracle_edge.py): identical frames with the identity pose give
-zero; a fronto-parallel plane under a lateral translation gives zero (the
-warp lands on the same plane) and a forward translation gives zero with
-z_ref = Y_z but not literally; the Huber branches; central differences of
-both twist gradients.
+Pins (tests/test_oracle_edge.py): the Huber kernel against scipy; identical
+frames under one pose give zero; invariance under a global rigid motion of
+both poses; L scales by s^2 when depths, translations and thresholds scale
+by s; the literal reading equals the default under lateral motion and not
+under forward motion; central differences of both twist gradients.
 """
 from __future__ import annotations
 
@@ -46,15 +47,16 @@ import numpy as np
 
 @dataclass
 class EdgeConfig:
-    edge_thr: float = 0.05
+    edge_rel: float = 0.05
     huber: float = 0.05
     z_near: float = 0.2
     lam: float = 300.0
     literal: bool = False
 
 
-def edge_mask(D, W, H, thr):
-    """(edge bool [H*W], flag bool [H*W]) of the depth discontinuities."""
+def edge_mask(D, W, H, rel):
+    """(edge bool [H*W], flag bool [H*W]) of the depth discontinuities:
+    a valid 4-neighbour differs by more than rel D(u)."""
     D = np.asarray(D, np.float64).reshape(H, W)
     edge = np.zeros((H, W), bool)
     flag = np.zeros((H, W), bool)
@@ -69,6 +71,7 @@ def edge_mask(D, W, H, thr):
         n[yd, xd] = D[ys, xs]
         nv[yd, xd] = valid[ys, xs]
         diff = np.abs(n - D)
+        thr = rel * D
         ok = valid & nv
         edge |= ok & (diff > thr)
         flag |= ok & (np.abs(diff - thr) <= 1e-5 * thr)
@@ -78,10 +81,6 @@ def edge_mask(D, W, H, thr):
 def huber(r, d):
     a = np.abs(r)
     return np.where(a <= d, 0.5 * r * r, d * (a - 0.5 * d)), np.where(a <= d, r, d * np.sign(r))
-
-
-def _hat(v):
-    return np.array([[0.0, -v[2], v[1]], [v[2], 0.0, -v[0]], [-v[1], v[0], 0.0]])
 
 
 def edge_warp(cam, Di, Dj, wj, pose_i, pose_j, cfg: EdgeConfig = None):
@@ -98,7 +97,7 @@ def edge_warp(cam, Di, Dj, wj, pose_i, pose_j, cfg: EdgeConfig = None):
     Ri, ti, Rj, tj = Ti[:, :3], Ti[:, 3], Tj[:, :3], Tj[:, 3]
     R = Rj @ Ri.T
     t = tj - R @ ti
-    edge, flag = edge_mask(Di, W, H, cfg.edge_thr)
+    edge, flag = edge_mask(Di, W, H, cfg.edge_rel)
     L = 0.0
     gi = np.zeros(6)
     gj = np.zeros(6)
@@ -144,8 +143,8 @@ def edge_warp(cam, Di, Dj, wj, pose_i, pose_j, cfg: EdgeConfig = None):
         if not cfg.literal:
             drY = drY - ws * np.array([0.0, 0.0, 1.0])
         gY = float(drho) * drY
-        # Y <- exp(xi_j) Y: dY = rho_j + phi_j x Y; Y = R exp(-xi_i) X ... : dY = -R (rho_i + phi_i x X_w)
-        # with X_w = X in frame i coordinates
+        # pose j: Y <- exp(xi_j) Y, dY = rho_j + phi_j x Y;
+        # pose i: Y = T_ji exp(-xi_i) X, dY = -R (rho_i + phi_i x X)
         gj[:3] += gY
         gj[3:] += np.cross(Y, gY)
         gR = R.T @ gY

@@ -59,8 +59,9 @@ def test_global_rigid_motion_invariance():
 
 
 def test_depth_and_translation_scaling():
-    # scaling depths, translations and the Huber threshold by s leaves u'
-    # unchanged and scales every residual by s: L scales by s^2
+    # scaling depths, translations and the Huber threshold by s leaves u' and
+    # the (relative) edge set unchanged and scales every residual by s: L
+    # scales by s^2
     Di, Dj, wj = step_scene(2)
     Ti, Tj = poses(2)
     s = 1.7
@@ -68,7 +69,7 @@ def test_depth_and_translation_scaling():
     Ti2, Tj2 = Ti.copy(), Tj.copy()
     Ti2[:, 3] *= s
     Tj2[:, 3] *= s
-    cfg = E.EdgeConfig(huber=0.05 * s, edge_thr=0.05 * s, z_near=0.2 * s)
+    cfg = E.EdgeConfig(huber=0.05 * s, z_near=0.2 * s)
     b = E.edge_warp(CAM, s * Di, s * Dj, wj, Ti2, Tj2, cfg)
     assert a["n"] == b["n"]
     assert abs(b["L"] - s * s * a["L"]) <= 1e-9 * b["L"]
