@@ -364,6 +364,42 @@ def lm_section(args, ctx, dags, gauss, cam, targets0, pose0, gt_pose, pcfg, flus
                                                "deg": round(float(np.degrees(e_adam[1])), 5), "ms": round(t_adam, 3)}}}
 
 
+def edge_section(ctx, dags, gauss, cam, tg_all, pose_all, flush, stream):
+    """The edge-warp regulariser (Eqs. (25), (26)) between the sequence's
+    first two frames at 640x480: the observed depths of frames 10 and 11, the
+    static weight w^j of frame 11's render (channel 7), their starting poses;
+    CUDA events around the launch, L2 flushed before each. One thread per
+    pixel of frame i: the edge test reads four neighbours, the warp and the
+    bilinear samples touch the few edge pixels, so the launch is latency-bound
+    (about 1.2 MB of depth read)."""
+    import torch
+    P = cam.width * cam.height
+    Di = tg_all[0, 0, :, 3].contiguous()
+    Dj = tg_all[1, 0, :, 3].contiguous()
+    image, _, _ = ctx.forward(gauss, cam, pose_all[1].contiguous(), tg_all[1].contiguous())
+    wj = image[0, 7].reshape(P).contiguous()
+    pi = pose_all[0, 0].contiguous()
+    pj = pose_all[1, 0].contiguous()
+    out = torch.empty(13, dtype=torch.float64, device=gauss.device)
+    fn = lambda: ctx.edge_warp(cam, Di, Dj, wj, pi, pj, 300.0, out=out)
+    for _ in range(3):
+        fn()
+    ts = []
+    for _ in range(20):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.check()
+    return {"workload": f"frames 10 -> 11, {cam.width}x{cam.height}, w^j from frame 11's render",
+            "us": round(1e3 * float(np.median(ts)), 3), "loss": round(float(out[0].item()), 4),
+            "bound": "latency (one pass over the depth image; edge pixels only beyond the test)"}
+
+
 def pose_error(T, T_gt):
     """(camera-centre distance in m, rotation angle in rad) of world-to-camera poses."""
     T = np.asarray(T, np.float64).reshape(3, 4)
@@ -680,6 +716,8 @@ def run_ours(args):
     line["learned_mp"] = learned
     line["splat_variants"] = variants
     line["lm_tracking"] = lm
+    if F >= 2:
+        variants["edge_warp"] = edge_section(ctx, dags, gauss, cam, tg_all, pose_all, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(args, args.cpu_seconds)
     if rank == 0:

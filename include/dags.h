@@ -379,6 +379,39 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
 int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const float *prev, const double *rel_pose,
                          float lambda, float *grad_gauss, double *loss, void *stream);
 
+/* MP-guided edge-warp regulariser constants (Sec. IV-D; defaults from
+ * dags_default_edge_cfg). */
+typedef struct {
+  float edge_rel;   /* depth step that makes an edge pixel, relative to D_i(u) (0.05) */
+  float huber;      /* Huber threshold of rho, m (0.05)                           */
+  float z_near;     /* warped points at or before this depth are skipped (0.2)   */
+  int32_t literal;  /* 0: compare D_j(u') with the warped depth Y_z; 1: with D_i(u),
+                       as Eq. (26) prints it (0)                                  */
+} dags_edge_cfg;
+
+void dags_default_edge_cfg(dags_edge_cfg *cfg);
+
+/* Edge-warp regulariser from frame i to frame j (Sec. IV-D, Eqs. (25), (26)):
+ * every pixel u of frame i with D_i(u) > 0 and a valid 4-neighbour more than
+ * edge_rel D_i(u) away is back-projected with D_i(u), moved by T_ji = T_jW T_iW^-1,
+ * projected to u' (Eq. (25)); D_j and w^j are sampled bilinearly over the four
+ * pixels around u' (all inside the image with D_j > 0, else u is skipped) and
+ *   lambda L_edge = lambda sum_u rho(w^j(u') (D_j(u') - z_ref)),
+ * rho the Huber kernel, z_ref per cfg->literal (Eq. (26)). Pixel centres are
+ * the integer coordinates.
+ * depth_i, depth_j   device, H*W floats (observed depth, <= 0 invalid)
+ * weight_j           device, H*W floats: the static weight w^j of Eq. (20),
+ *                    e.g. channel 7 of frame j's splat_forward image
+ * pose_i, pose_j     device, 12 doubles each (world -> camera)
+ * out                device, 13 doubles: lambda L_edge, then its gradient
+ *                    with respect to the left twist of pose_i (6) and of
+ *                    pose_j (6); FP64 sums in a fixed order (deterministic)
+ * The first call on a ctx allocates a small buffer (before any stream
+ * capture). */
+int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i, const float *depth_j,
+                    const float *weight_j, const double *pose_i, const double *pose_j, const dags_edge_cfg *cfg,
+                    float lambda, double *out, void *stream);
+
 /* Semantic-on-demand trigger constants (Sec. IV-B). The paper gives none of
  * their values; defaults from dags_default_sched_cfg. */
 typedef struct {

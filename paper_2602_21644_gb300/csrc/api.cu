@@ -84,6 +84,7 @@ struct dags_ctx {
   TrackGraph graph_lm;            // captured LM iteration
   LmBuffers lm;                   // allocated by the first LM call
   double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
+  double *edge_partial = nullptr; // per-CTA sums of the edge-warp term (first call)
   MpBuffers mp;
   MpnetScratch net;
   PoseStep fused_step;            // set only inside the tracking loop
@@ -335,6 +336,7 @@ void dags_destroy(dags_ctx *ctx) {
   if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
   free_lm(ctx->lm);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
+  if (ctx->edge_partial) cudaFree(ctx->edge_partial);
   free_mp(ctx->mp);
   free_net(ctx->net);
   free_ws(ctx->ws);
@@ -786,6 +788,47 @@ int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const flo
   const cudaError_t e = launch_mp_consistency(reinterpret_cast<const float4 *>(gauss),
                                               reinterpret_cast<const float4 *>(prev), n, rel_pose, lambda,
                                               grad_gauss, ctx->reg_partial, ctx->ws.counters + CNT_DONE_REG, loss, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+void dags_default_edge_cfg(dags_edge_cfg *c) {
+  if (!c) return;
+  c->edge_rel = 0.05f;
+  c->huber = 0.05f;
+  c->z_near = 0.2f;
+  c->literal = 0;
+}
+
+int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i, const float *depth_j,
+                    const float *weight_j, const double *pose_i, const double *pose_j, const dags_edge_cfg *cfg,
+                    float lambda, double *out, void *stream) {
+  NvtxRange nv("splat_edge_warp");
+  if (!ctx || !depth_i || !depth_j || !weight_j || !pose_i || !pose_j || !out || !isfinite(lambda) || lambda < 0.f)
+    return DAGS_E_INVAL;
+  int rc = check_camera(ctx, cam);
+  if (rc) return rc;
+  dags_edge_cfg c;
+  if (cfg) c = *cfg;
+  else dags_default_edge_cfg(&c);
+  if (!(c.edge_rel > 0.f) || !(c.huber > 0.f) || !(c.z_near > 0.f) || !isfinite(c.edge_rel) || !isfinite(c.huber))
+    return DAGS_E_INVAL;
+  Raster r;
+  if ((rc = make_raster(cam, nullptr, &r))) return rc;
+  if (!ctx->edge_partial) {
+    const cudaError_t a =
+        alloc(&ctx->edge_partial, (size_t)edge_warp_blocks((int64_t)ctx->ws.max_w * ctx->ws.max_h) * 13);
+    if (a != cudaSuccess) {
+      cudaGetLastError();
+      ctx->edge_partial = nullptr;
+      return a == cudaErrorMemoryAllocation ? DAGS_E_NOMEM : DAGS_E_CUDA;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_REGULARISER, s);
+  const cudaError_t e = launch_edge_warp(r, depth_i, depth_j, weight_j, pose_i, pose_j, c, lambda,
+                                         ctx->edge_partial, ctx->ws.counters + CNT_DONE_REG, out, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

@@ -150,6 +150,10 @@ cudaError_t launch_lm_step(const double *normal, double *state, double *pose_try
 
 // MP motion-consistency regulariser (regular.cu).
 int64_t mp_consistency_blocks(int64_t n);
+int64_t edge_warp_blocks(int64_t pixels);
+cudaError_t launch_edge_warp(const Raster &r, const float *Di, const float *Dj, const float *wj, const double *pose_i,
+                             const double *pose_j, const dags_edge_cfg &c, float lam, double *partial, uint32_t *done,
+                             double *out, cudaStream_t s);
 cudaError_t launch_mp_consistency(const float4 *gauss, const float4 *prev, int64_t n, const double *rel, float lam,
                                   float *grad, double *partial, uint32_t *done, double *loss, cudaStream_t s);
 

@@ -10,6 +10,16 @@
 // record, the first of the previous record, a read-modify-write of the first
 // float4 of the gradient). The loss is summed per CTA in FP64 by a fixed tree
 // and across CTAs in a fixed order by the last CTA.
+//
+// MP-guided edge-warp regulariser (Sec. IV-D, Eqs. (25), (26)): one thread
+// per pixel u of frame i. An edge pixel (a valid 4-neighbour differs by more
+// than edge_rel times its depth) is back-projected with its observed depth, moved by
+// T_ji = T_jW T_iW^-1 (computed once per CTA in FP64) and projected into frame
+// j; D_j and w^j are sampled bilinearly at u', r = w^j (D_j - z_ref) enters
+// the Huber kernel, and the gradients with respect to both poses' left
+// twists follow by the chain rule through the bilinear cell, the projection
+// and the rigid motion. Per-CTA sums in FP64 in a fixed order, combined by the
+// last CTA in a fixed order.
 #include "common.cuh"
 
 namespace dags {
@@ -78,7 +88,143 @@ mp_consistency_kernel(const float4 *__restrict__ gauss, const float4 *__restrict
   }
 }
 
+constexpr int kEdgeBlock = 256;
+constexpr int kEdgeOut = 13;     // lambda L_edge, d/d xi_i (6), d/d xi_j (6)
+
+__global__ void __launch_bounds__(kEdgeBlock)
+edge_warp_kernel(Raster r, const float *__restrict__ Di, const float *__restrict__ Dj,
+                 const float *__restrict__ wj, const double *__restrict__ pose_i, const double *__restrict__ pose_j,
+                 dags_edge_cfg c, float lam, double *__restrict__ partial, uint32_t *__restrict__ done,
+                 double *__restrict__ out) {
+  __shared__ float s_T[12];
+  __shared__ double s_red[kEdgeBlock / 32][kEdgeOut];
+  __shared__ int s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    // T_ji = T_jW T_iW^-1: R = Rj Ri^T, t = tj - R ti
+    double R[9], t[3];
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b)
+        R[3 * a + b] = pose_j[4 * a] * pose_i[4 * b] + pose_j[4 * a + 1] * pose_i[4 * b + 1] +
+                       pose_j[4 * a + 2] * pose_i[4 * b + 2];
+    }
+    for (int a = 0; a < 3; ++a)
+      t[a] = pose_j[4 * a + 3] - (R[3 * a] * pose_i[3] + R[3 * a + 1] * pose_i[7] + R[3 * a + 2] * pose_i[11]);
+    for (int a = 0; a < 3; ++a) {
+      for (int b = 0; b < 3; ++b) s_T[4 * a + b] = (float)R[3 * a + b];
+      s_T[4 * a + 3] = (float)t[a];
+    }
+  }
+  __syncthreads();
+  const int W = r.W, H = r.H;
+  const int p = blockIdx.x * kEdgeBlock + tid;
+  float v[kEdgeOut];
+#pragma unroll
+  for (int k = 0; k < kEdgeOut; ++k) v[k] = 0.f;
+  if (p < W * H) {
+    const int y = p / W, x = p - y * W;
+    const float d = Di[p];
+    bool edge = false;
+    if (d > 0.f) {
+      const int nx[4] = {x + 1, x - 1, x, x}, ny[4] = {y, y, y + 1, y - 1};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (nx[k] < 0 || nx[k] >= W || ny[k] < 0 || ny[k] >= H) continue;
+        const float dn = Di[ny[k] * W + nx[k]];
+        if (dn > 0.f && fabsf(dn - d) > c.edge_rel * d) edge = true;
+      }
+    }
+    if (edge) {
+      const float X0 = d * ((float)x - r.cx) / r.fx, X1 = d * ((float)y - r.cy) / r.fy, X2 = d;
+      const float Y0 = s_T[0] * X0 + s_T[1] * X1 + s_T[2] * X2 + s_T[3];
+      const float Y1 = s_T[4] * X0 + s_T[5] * X1 + s_T[6] * X2 + s_T[7];
+      const float Y2 = s_T[8] * X0 + s_T[9] * X1 + s_T[10] * X2 + s_T[11];
+      if (Y2 > c.z_near) {
+        const float iz = 1.f / Y2;
+        const float u = r.fx * Y0 * iz + r.cx, vv = r.fy * Y1 * iz + r.cy;
+        const float fx0 = floorf(u), fy0 = floorf(vv);
+        if (fx0 >= 0.f && fy0 >= 0.f && fx0 + 1.f <= (float)(W - 1) && fy0 + 1.f <= (float)(H - 1)) {
+          const int x0 = (int)fx0, y0 = (int)fy0;
+          const int q0 = y0 * W + x0;
+          const float d00 = Dj[q0], d01 = Dj[q0 + 1], d10 = Dj[q0 + W], d11 = Dj[q0 + W + 1];
+          if (d00 > 0.f && d01 > 0.f && d10 > 0.f && d11 > 0.f) {
+            const float w00 = wj[q0], w01 = wj[q0 + 1], w10 = wj[q0 + W], w11 = wj[q0 + W + 1];
+            const float fu = u - fx0, fv = vv - fy0;
+            const float a0 = (1.f - fu) * (1.f - fv), a1 = fu * (1.f - fv), a2 = (1.f - fu) * fv, a3 = fu * fv;
+            const float Ds = a0 * d00 + a1 * d01 + a2 * d10 + a3 * d11;
+            const float ws = a0 * w00 + a1 * w01 + a2 * w10 + a3 * w11;
+            const float zref = c.literal ? d : Y2;
+            const float res = ws * (Ds - zref);
+            const float ar = fabsf(res);
+            const float rho = ar <= c.huber ? 0.5f * res * res : c.huber * (ar - 0.5f * c.huber);
+            const float drho = ar <= c.huber ? res : copysignf(c.huber, res);
+            // bilinear slopes along u and v
+            const float dDu = (1.f - fv) * (d01 - d00) + fv * (d11 - d10);
+            const float dDv = (1.f - fu) * (d10 - d00) + fu * (d11 - d01);
+            const float dwu = (1.f - fv) * (w01 - w00) + fv * (w11 - w10);
+            const float dwv = (1.f - fu) * (w10 - w00) + fu * (w11 - w01);
+            const float e = Ds - zref;
+            const float dru = dwu * e + ws * dDu, drv = dwv * e + ws * dDv;
+            // d(u, v)/dY, then dr/dY (the reference depth Y_z contributes -ws)
+            float g0 = dru * r.fx * iz, g1 = drv * r.fy * iz;
+            float g2 = -(dru * r.fx * Y0 + drv * r.fy * Y1) * iz * iz;
+            if (!c.literal) g2 -= ws;
+            g0 *= drho; g1 *= drho; g2 *= drho;
+            v[0] = rho;
+            // pose j: rho_j += gY, phi_j += Y x gY
+            v[7] = g0; v[8] = g1; v[9] = g2;
+            v[10] = Y1 * g2 - Y2 * g1; v[11] = Y2 * g0 - Y0 * g2; v[12] = Y0 * g1 - Y1 * g0;
+            // pose i: gR = R^T gY; rho_i -= gR, phi_i -= X x gR
+            const float r0 = s_T[0] * g0 + s_T[4] * g1 + s_T[8] * g2;
+            const float r1 = s_T[1] * g0 + s_T[5] * g1 + s_T[9] * g2;
+            const float r2 = s_T[2] * g0 + s_T[6] * g1 + s_T[10] * g2;
+            v[1] = -r0; v[2] = -r1; v[3] = -r2;
+            v[4] = -(X1 * r2 - X2 * r1); v[5] = -(X2 * r0 - X0 * r2); v[6] = -(X0 * r1 - X1 * r0);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kEdgeOut; ++k) {
+    const float sw = warp_sum(v[k]);
+    if (lane == 0) s_red[warp][k] = (double)sw;
+  }
+  __syncthreads();
+  if (tid < kEdgeOut) {
+    double a = 0.0;
+#pragma unroll
+    for (int w = 0; w < kEdgeBlock / 32; ++w) a += s_red[w][tid];
+    partial[(size_t)blockIdx.x * kEdgeOut + tid] = a;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (!s_last) return;
+  if (tid < kEdgeOut) {
+    double a = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) a += __ldcg(partial + (size_t)b * kEdgeOut + tid);
+    out[tid] = (double)lam * a;
+  }
+  __syncthreads();
+  if (tid == 0) *done = 0u;
+}
+
 }  // namespace
+
+int64_t edge_warp_blocks(int64_t pixels) { return (pixels + kEdgeBlock - 1) / kEdgeBlock; }
+
+cudaError_t launch_edge_warp(const Raster &r, const float *Di, const float *Dj, const float *wj, const double *pose_i,
+                             const double *pose_j, const dags_edge_cfg &c, float lam, double *partial, uint32_t *done,
+                             double *out, cudaStream_t s) {
+  edge_warp_kernel<<<(unsigned)edge_warp_blocks((int64_t)r.W * r.H), kEdgeBlock, 0, s>>>(r, Di, Dj, wj, pose_i, pose_j,
+                                                                                          c, lam, partial, done, out);
+  return cudaGetLastError();
+}
 
 int64_t mp_consistency_blocks(int64_t n) { return (n + kRegBlock - 1) / kRegBlock; }
 

@@ -60,6 +60,11 @@ class CSchedCfg(ctypes.Structure):
                 ("e_ref", ctypes.c_double), ("n_max", ctypes.c_int32)]
 
 
+class CEdgeCfg(ctypes.Structure):
+    _fields_ = [("edge_rel", ctypes.c_float), ("huber", ctypes.c_float), ("z_near", ctypes.c_float),
+                ("literal", ctypes.c_int32)]
+
+
 class CLmCfg(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("mu0", "mu_min", "mu_max", "down", "up", "delta", "floor")]
 
@@ -83,7 +88,7 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
            "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
            "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
-           "splat_mp_consistency"]
+           "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
@@ -164,6 +169,11 @@ def load(path: str = LIB_PATH):
     lib.splat_track_lm.restype = ctypes.c_int
     lib.splat_mp_consistency.argtypes = [P, P, I64, P, P, ctypes.c_float, P, P, P]
     lib.splat_mp_consistency.restype = ctypes.c_int
+    lib.dags_default_edge_cfg.argtypes = [ctypes.POINTER(CEdgeCfg)]
+    lib.dags_default_edge_cfg.restype = None
+    lib.splat_edge_warp.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, P, P, ctypes.POINTER(CEdgeCfg),
+                                    ctypes.c_float, P, P]
+    lib.splat_edge_warp.restype = ctypes.c_int
     lib.dags_selftest_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -231,6 +241,14 @@ def default_mp_cfg(**kw) -> CMpCfg:
 def default_sched_cfg(**kw) -> CSchedCfg:
     c = CSchedCfg()
     load().dags_default_sched_cfg(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_edge_cfg(**kw) -> CEdgeCfg:
+    c = CEdgeCfg()
+    load().dags_default_edge_cfg(ctypes.byref(c))
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -438,6 +456,25 @@ class Context:
         _check(self.lib.splat_mp_consistency(self.h, _ptr(gauss), gauss.shape[0], _ptr(prev), _ptr(rel_pose),
                                              float(lam), _ptr(grad), _ptr(loss), _stream()), "splat_mp_consistency")
         return loss
+
+    def edge_warp(self, cam: Camera, depth_i, depth_j, weight_j, pose_i, pose_j, lam=300.0, cfg=None, out=None):
+        """Edge-warp regulariser from frame i to frame j (Eqs. (25), (26)).
+        depth_*, weight_j: float32 [H*W] device tensors; poses float64 [12].
+        Returns float64 [13]: lambda L_edge, d/d xi_i (6), d/d xi_j (6)."""
+        for name, t in (("depth_i", depth_i), ("depth_j", depth_j), ("weight_j", weight_j)):
+            _need(t, torch.float32, name)
+            if t.numel() < cam.width * cam.height:
+                raise ValueError(f"{name} must hold H*W floats")
+        _need(pose_i, torch.float64, "pose_i")
+        _need(pose_j, torch.float64, "pose_j")
+        if out is None:
+            out = torch.empty(13, dtype=torch.float64, device=depth_i.device)
+        c = cam.c()
+        ec = cfg if cfg is not None else default_edge_cfg()
+        _check(self.lib.splat_edge_warp(self.h, ctypes.byref(c), _ptr(depth_i), _ptr(depth_j), _ptr(weight_j),
+                                        _ptr(pose_i), _ptr(pose_j), ctypes.byref(ec), float(lam), _ptr(out),
+                                        _stream()), "splat_edge_warp")
+        return out
 
     def mp_update(self, gauss, cam: Camera, pose, targets, image, inst, table, labels, cfg=None, seg_refreshed=True,
                   stats=None, mp_map=None, mp_pixel=None):
