@@ -17,6 +17,7 @@ Contents
   lm                      Levenberg-Marquardt pose refinement (Sec. V-A(c))
   regular                 the MP motion-consistency regulariser, Eqs. (23), (24)
   edge                    the MP-guided edge-warp regulariser, Eqs. (25), (26)
+  epipolar                epipolar verification and static recovery, Eqs. (18), (19)
   mpnet                   the small per-pixel MP proposal network
   schedule                the semantic-on-demand trigger, Eqs. (13)-(16)
 
