@@ -158,7 +158,7 @@ def workload_config(args):
                         f"pose-only fwd+bwd iterations with FP64 pose steps and one MP update per frame (step)",
             "gaussians": args.gaussians, "width": args.width, "height": args.height,
             "iters_per_step": args.iters,
-            "l2": "flushed between steps by a 256 MiB write; inside a step the iterations re-read the "
+            "l2": "flushed between steps by a 256 MiB write, then a 256 MiB read of a never-written buffer (L2 left clean); inside a step the iterations re-read the "
                   "L2-resident map as the tracking loop does",
             "parallelism": f"replicas x{args.gpus}"}
 
@@ -212,6 +212,22 @@ OPS_JAC = 16 + 10 + 6 * 14
 DRAM_TRAFFIC = {"render_fwd": 9212160, "render_bwd": 19869696}
 ALU_LANES = 152 * 128          # FP32 lanes: 152 SMs x 128
 MPNET_FLOP_PER_PX = 2 * (8 * 32 + 288 * 32 + 32 * 32 + 32)   # 21,056: the network's multiply-adds x 2
+
+
+class L2Flush:
+    """Between timed iterations: write a 256 MiB buffer (twice the 129 MB L2),
+    then read a second, never-written 256 MiB buffer, so that L2 holds clean
+    lines and the timed work does not pay the write-back of the flush."""
+
+    def __init__(self, torch, dev):
+        self.torch = torch
+        self.w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.r = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.out = None
+
+    def fill_(self, v):
+        self.w.fill_(v)
+        self.out = self.r.sum()
 
 
 def learned_mp_section(args, ctx, dags, synth, image, targets, inst, table, cam, flush, stream):
@@ -400,6 +416,47 @@ def edge_section(ctx, dags, gauss, cam, tg_all, pose_all, flush, stream):
             "bound": "latency (one pass over the depth image; edge pixels only beyond the test)"}
 
 
+def epipolar_section(dags, flush, stream):
+    """Epipolar verification and static recovery (Eqs. (18), (19)) on the
+    synthetic matches of frames 11 and 16 (300k-Gaussian map, 20k Gaussians
+    with 4 matches each, 0.3 px noise): CUDA events around the call (seven
+    launches: distances, three scan kernels, scatter, medians; one memset),
+    L2 flushed before each; and what the recovery does."""
+    import torch
+    from paper_2602_21644_gb300 import synth
+    d = synth.epipolar_matches()
+    cam = dags.Camera(*d["camera"].as_tuple())
+    n = d["records"].shape[0]
+    ctx = dags.Context(n, cam.width, cam.height, 1)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    g0, lab0 = t(d["records"]), t(d["labels"])
+    g, lab = g0.clone(), lab0.clone()
+    args = (cam, t(d["pose_1"].ravel()), t(d["pose_2"].ravel()), t(d["p1"]), t(d["p2"]), t(d["gid"]))
+    ctx.epipolar_verify(*args, g, lab)
+    torch.cuda.synchronize()
+    restored = ((lab0 == 1) & (lab == 0)).cpu().numpy()
+    ts = []
+    for _ in range(20):
+        g.copy_(g0)
+        lab.copy_(lab0)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.epipolar_verify(*args, g, lab, want_d=False, want_dbar=False)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.check()
+    ctx.close()
+    moving = d["moving"]
+    return {"workload": f"{len(d['gid'])} matches of {len(np.unique(d['gid']))} Gaussians, frames 11 -> 16, "
+                        f"{n} Gaussians",
+            "us": round(1e3 * float(np.median(ts)), 3), "gpu_launches": 7,
+            "restored_static": int((restored & ~moving).sum()), "restored_moving": int((restored & moving).sum()),
+            "suppressed_static": int(((d["labels"] == 1) & ~moving).sum())}
+
+
 def pose_error(T, T_gt):
     """(camera-centre distance in m, rotation angle in rad) of world-to-camera poses."""
     T = np.asarray(T, np.float64).reshape(3, 4)
@@ -553,7 +610,7 @@ def run_ours(args):
     table = torch.tensor([[0.1, 0.05]] + [[0.9, 0.8]] * sx["n_instances"], dtype=torch.float32, device=dev)
     labels = torch.zeros(n, dtype=torch.uint8, device=dev)
     mp_stats = torch.empty(dags.MP_STATS_HEAD + 4 * table.shape[0], dtype=torch.float64, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(torch, dev)
 
     def frame(use_graph=True):
         k = fidx[0] % F
@@ -718,6 +775,7 @@ def run_ours(args):
     line["lm_tracking"] = lm
     if F >= 2:
         variants["edge_warp"] = edge_section(ctx, dags, gauss, cam, tg_all, pose_all, flush, stream)
+    variants["epipolar_verify"] = epipolar_section(dags, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(args, args.cpu_seconds)
     if rank == 0:

@@ -412,6 +412,30 @@ int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i,
                     const float *weight_j, const double *pose_i, const double *pose_j, const dags_edge_cfg *cfg,
                     float lambda, double *out, void *stream);
 
+/* Epipolar verification and static recovery (Sec. IV-C, Eqs. (18), (19)).
+ * F = K^-T [t]x R K^-1 from the camera and the relative pose (R, t) =
+ * T_21 = T_2W T_1W^-1; for every match k, in FP64,
+ *   d_k = |p2^T F p1| / sqrt(a^2 + b^2),  (a, b, c) = F p1       Eq. (18)
+ * per Gaussian G the lower median dbar(G) of d over its matches (Eq. (19));
+ * G with dbar < eps that is labelled dynamic (1) is restored: label 0 and
+ * M <- min(M, m_static) (word 11 of its record). Gaussians without matches
+ * are unchanged. Densification is not part of this call.
+ * pose_1, pose_2  device, 12 doubles each (world -> camera)
+ * p1, p2          device, m x 2 floats: pixel coordinates in frames 1, 2
+ *                 (pixel i samples u = i), 8-byte aligned
+ * gid             device, m int32: the Gaussian of each match; an id outside
+ *                 [0, n) is skipped and reported as DAGS_E_BOUNDS at the next
+ *                 dags_sync_status
+ * gauss, labels   device in/out, n records and n uint8
+ * eps             the paper's 1 px (> 0); m_static in [0, 1] (0.1)
+ * d_out           device out, m floats, or NULL
+ * dbar_out        device out, n floats (NaN where G has no match), or NULL
+ * Buffers grow with m and n (allocations then, so not during a stream
+ * capture). */
+int epipolar_verify(dags_ctx *ctx, const dags_camera *cam, const double *pose_1, const double *pose_2,
+                    const float *p1, const float *p2, const int32_t *gid, int64_t m, float *gauss, int64_t n,
+                    uint8_t *labels, float eps, float m_static, float *d_out, float *dbar_out, void *stream);
+
 /* Semantic-on-demand trigger constants (Sec. IV-B). The paper gives none of
  * their values; defaults from dags_default_sched_cfg. */
 typedef struct {
@@ -534,7 +558,8 @@ enum {
   DAGS_K_POSE_TANGENT,     /* LM: twist tangents of the visible Gaussians  */
   DAGS_K_RENDER_JAC,       /* LM: forward-mode compositing + normal eqs.   */
   DAGS_K_LM_STEP,          /* LM: FP64 decision, solve and pose step       */
-  DAGS_K_REGULARISER,      /* L_MP motion-consistency regulariser          */
+  DAGS_K_REGULARISER,      /* L_MP and L_edge regularisers                 */
+  DAGS_K_EPIPOLAR,         /* epipolar verification and static recovery    */
   DAGS_KERNEL_COUNT
 };
 int dags_timing_enable(dags_ctx *ctx, int enable);

@@ -85,6 +85,7 @@ struct dags_ctx {
   LmBuffers lm;                   // allocated by the first LM call
   double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
   double *edge_partial = nullptr; // per-CTA sums of the edge-warp term (first call)
+  EpiBuffers epi;                 // epipolar verification, grown on demand
   MpBuffers mp;
   MpnetScratch net;
   PoseStep fused_step;            // set only inside the tracking loop
@@ -125,6 +126,13 @@ void free_lm(LmBuffers &b) {
   for (void *p : ptrs)
     if (p) cudaFree(p);
   b = LmBuffers();
+}
+
+void free_epi(EpiBuffers &b) {
+  void *ptrs[] = {b.count, b.off, b.block_sum, b.rank, b.vals, b.dist};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  b = EpiBuffers();
 }
 
 void free_net(MpnetScratch &b) {
@@ -240,7 +248,7 @@ const char *dags_status_string(int code) {
     case DAGS_E_TIMEOUT: return "a bounded device wait gave up";
     case DAGS_E_NOMEM: return "workspace allocation failed";
     case DAGS_E_ORDER: return "splat_backward does not follow its splat_forward on this context";
-    case DAGS_E_BOUNDS: return "an index check of a DAGS_CHECK build failed (the access was skipped)";
+    case DAGS_E_BOUNDS: return "an index was out of range (a DAGS_CHECK build's check, or a caller's id; the access was skipped)";
     default: return "unknown status";
   }
 }
@@ -337,6 +345,7 @@ void dags_destroy(dags_ctx *ctx) {
   free_lm(ctx->lm);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
   if (ctx->edge_partial) cudaFree(ctx->edge_partial);
+  free_epi(ctx->epi);
   free_mp(ctx->mp);
   free_net(ctx->net);
   free_ws(ctx->ws);
@@ -829,6 +838,51 @@ int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i,
   const int ev = ctx->timer.begin(DAGS_K_REGULARISER, s);
   const cudaError_t e = launch_edge_warp(r, depth_i, depth_j, weight_j, pose_i, pose_j, c, lambda,
                                          ctx->edge_partial, ctx->ws.counters + CNT_DONE_REG, out, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
+int epipolar_verify(dags_ctx *ctx, const dags_camera *cam, const double *pose_1, const double *pose_2,
+                    const float *p1, const float *p2, const int32_t *gid, int64_t m, float *gauss, int64_t n,
+                    uint8_t *labels, float eps, float m_static, float *d_out, float *dbar_out, void *stream) {
+  NvtxRange nv("epipolar_verify");
+  if (!ctx || !pose_1 || !pose_2 || m < 0 || n < 0 || n > ctx->ws.max_n || m > (int64_t)0x7FFFFFFF) return DAGS_E_INVAL;
+  if (m > 0 && (!p1 || !p2 || !gid)) return DAGS_E_INVAL;
+  if (n > 0 && (!gauss || !labels)) return DAGS_E_INVAL;
+  if (!(eps > 0.f) || !isfinite(eps) || !(m_static >= 0.f && m_static <= 1.f)) return DAGS_E_INVAL;
+  if (((uintptr_t)p1 & 7u) != 0 || ((uintptr_t)p2 & 7u) != 0 || ((uintptr_t)gauss & 15u) != 0) return DAGS_E_INVAL;
+  int rc = check_camera(ctx, cam);
+  if (rc) return rc;
+  Raster r;
+  if ((rc = make_raster(cam, nullptr, &r))) return rc;
+  EpiBuffers &b = ctx->epi;
+  if (n > b.cap_n || m > b.cap_m) {
+    const int64_t cn = n > b.cap_n ? n : b.cap_n, cm = m > b.cap_m ? m : b.cap_m;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return DAGS_E_CUDA;
+    free_epi(b);
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+    A(alloc(&b.count, (size_t)cn));
+    A(alloc(&b.off, (size_t)cn));
+    A(alloc(&b.block_sum, (size_t)epi_scan_blocks(cn) + 1));
+    A(alloc(&b.rank, (size_t)cm));
+    A(alloc(&b.vals, (size_t)cm));
+    A(alloc(&b.dist, (size_t)cm));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      free_epi(b);
+      return e == cudaErrorMemoryAllocation ? DAGS_E_NOMEM : DAGS_E_CUDA;
+    }
+    b.cap_n = cn;
+    b.cap_m = cm;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_EPIPOLAR, s);
+  const cudaError_t e = launch_epipolar(r, pose_1, pose_2, reinterpret_cast<const float2 *>(p1),
+                                        reinterpret_cast<const float2 *>(p2), gid, m, reinterpret_cast<float4 *>(gauss),
+                                        n, labels, eps, m_static, d_out ? d_out : b.dist, dbar_out, b,
+                                        ctx->ws.counters + CNT_STATUS, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

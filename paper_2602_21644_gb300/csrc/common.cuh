@@ -157,6 +157,21 @@ cudaError_t launch_edge_warp(const Raster &r, const float *Di, const float *Dj, 
 cudaError_t launch_mp_consistency(const float4 *gauss, const float4 *prev, int64_t n, const double *rel, float lam,
                                   float *grad, double *partial, uint32_t *done, double *loss, cudaStream_t s);
 
+// Epipolar verification (epipolar.cu): buffers owned by the ctx, grown on
+// demand.
+struct EpiBuffers {
+  uint32_t *count = nullptr, *off = nullptr;   // [cap_n]
+  uint32_t *block_sum = nullptr;               // [scan blocks of cap_n]
+  uint32_t *rank = nullptr;                    // [cap_m]
+  float *vals = nullptr, *dist = nullptr;      // [cap_m]
+  int64_t cap_n = 0, cap_m = 0;
+};
+int64_t epi_scan_blocks(int64_t n);
+cudaError_t launch_epipolar(const Raster &r, const double *pose_1, const double *pose_2, const float2 *p1,
+                            const float2 *p2, const int32_t *gid, int64_t m, float4 *gauss, int64_t n,
+                            uint8_t *labels, float eps, float m_static, float *dist, float *dbar, const EpiBuffers &b,
+                            uint32_t *status, cudaStream_t s);
+
 cudaError_t launch_mpnet_forward(const void *weights, const uint16_t *feats, int batch, int W, int H, float *out,
                                  uint16_t *acts, uint32_t *status, int num_sms, cudaStream_t s);
 

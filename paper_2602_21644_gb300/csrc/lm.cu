@@ -402,9 +402,12 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   __shared__ double s_d[kNormal * 8];
   if (tid < kNormal * 8) {
     const int c = tid >> 3, part = tid & 7;
-    double a2 = 0.0;
-    for (int k = part; k < (int)gridDim.x; k += 8) a2 += (double)__ldcg(partial + (size_t)k * kNormal + c);
-    s_d[tid] = a2;
+    // four independent accumulators per thread (dependent FP64 additions
+    // are slow on GB300), combined in a fixed order
+    double a4[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = 0;
+    for (int k = part; k < (int)gridDim.x; k += 8, ++j) a4[j & 3] += (double)__ldcg(partial + (size_t)k * kNormal + c);
+    s_d[tid] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
   }
   __syncthreads();
   __shared__ double s_nrm[kNormal];

@@ -205,9 +205,21 @@ edge_warp_kernel(Raster r, const float *__restrict__ Di, const float *__restrict
   }
   __syncthreads();
   if (!s_last) return;
+  // 16 threads per output with a fixed stride, four independent accumulators
+  // each (dependent FP64 additions are slow on GB300), then the 16 in order
+  __shared__ double s_col[kEdgeOut * 16];
+  if (tid < kEdgeOut * 16) {
+    const int c = tid >> 4, part = tid & 15;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    int j = 0;
+    for (int b = part; b < (int)gridDim.x; b += 16, ++j) a[j & 3] += __ldcg(partial + (size_t)b * kEdgeOut + c);
+    s_col[tid] = (a[0] + a[1]) + (a[2] + a[3]);
+  }
+  __syncthreads();
   if (tid < kEdgeOut) {
     double a = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) a += __ldcg(partial + (size_t)b * kEdgeOut + tid);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a += s_col[tid * 16 + k];
     out[tid] = (double)lam * a;
   }
   __syncthreads();

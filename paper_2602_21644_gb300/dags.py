@@ -88,11 +88,12 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "splat_track", "splat_forward_static", "dags_default_mp_cfg", "mp_update", "mpnet_features", "mpnet_infer",
            "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
            "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
-           "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp"]
+           "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp",
+           "epipolar_verify"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
-           "regulariser"]
+           "regulariser", "epipolar"]
 
 _lib = None
 
@@ -174,6 +175,9 @@ def load(path: str = LIB_PATH):
     lib.splat_edge_warp.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, P, P, ctypes.POINTER(CEdgeCfg),
                                     ctypes.c_float, P, P]
     lib.splat_edge_warp.restype = ctypes.c_int
+    lib.epipolar_verify.argtypes = [P, ctypes.POINTER(CCamera), P, P, P, P, P, I64, P, I64, P, ctypes.c_float,
+                                    ctypes.c_float, P, P, P]
+    lib.epipolar_verify.restype = ctypes.c_int
     lib.dags_selftest_timeout.restype = ctypes.c_int
     _lib = lib
     return lib
@@ -475,6 +479,30 @@ class Context:
                                         _ptr(pose_i), _ptr(pose_j), ctypes.byref(ec), float(lam), _ptr(out),
                                         _stream()), "splat_edge_warp")
         return out
+
+    def epipolar_verify(self, cam: Camera, pose_1, pose_2, p1, p2, gid, gauss, labels, eps=1.0, m_static=0.1,
+                        want_d=True, want_dbar=True):
+        """Epipolar verification and static recovery (Eqs. (18), (19)); gauss's
+        MP words and labels are updated in place. p1, p2: float32 [m, 2];
+        gid: int32 [m]. Returns (d float32 [m] or None, dbar float32 [n] or None)."""
+        _need(gauss, torch.float32, "gauss")
+        _need(labels, torch.uint8, "labels")
+        _need(pose_1, torch.float64, "pose_1")
+        _need(pose_2, torch.float64, "pose_2")
+        m = int(gid.shape[0])
+        if m:
+            _need(p1, torch.float32, "p1")
+            _need(p2, torch.float32, "p2")
+            _need(gid, torch.int32, "gid")
+        dev = gauss.device
+        d = torch.empty(m, dtype=torch.float32, device=dev) if want_d else None
+        dbar = torch.empty(gauss.shape[0], dtype=torch.float32, device=dev) if want_dbar else None
+        c = cam.c()
+        _check(self.lib.epipolar_verify(self.h, ctypes.byref(c), _ptr(pose_1), _ptr(pose_2), _ptr(p1) if m else None,
+                                        _ptr(p2) if m else None, _ptr(gid) if m else None, m, _ptr(gauss),
+                                        gauss.shape[0], _ptr(labels), float(eps), float(m_static), _ptr(d), _ptr(dbar),
+                                        _stream()), "epipolar_verify")
+        return d, dbar
 
     def mp_update(self, gauss, cam: Camera, pose, targets, image, inst, table, labels, cfg=None, seg_refreshed=True,
                   stats=None, mp_map=None, mp_pixel=None):

@@ -417,6 +417,52 @@ def tracking_sequence(n: int = 300_000, frames=range(10, 60), seed: int = 0, wid
     return rec, cam, out, dict(objects=objs, object_id=oid, n_instances=len(moving))
 
 
+def epipolar_matches(n: int = 300_000, frames=(11, 16), seed: int = 0, width: int = 640, height: int = 480,
+                     fps: float = 30.0, n_sample: int = 20_000, per_gauss: int = 4, noise_px: float = 0.3,
+                     suppressed: float = 0.1):
+    """Feature matches between two frames of the tracking sequence for the
+    epipolar verification: n_sample Gaussians visible in both frames, each
+    with per_gauss matches (the Gaussian's world position at each frame's
+    time projected with that frame's ground-truth pose, plus N(0, noise_px)
+    pixel noise per match; moving objects' Gaussians move between the frames).
+    Labels: the moving objects' Gaussians dynamic (1) and a `suppressed`
+    fraction of static ones also dynamic (static structure an MP prior
+    suppressed). Returns dict(records, camera, pose_1, pose_2, p1, p2 (m x 2
+    float32), gid (m int32), labels (n uint8), moving (n bool))."""
+    rng = np.random.default_rng(seed + 991)
+    rec, oid, objs = room_scene(n, seed)
+    cam = room_camera(width, height)
+    f1, f2 = frames
+    path = camera_path(max(frames) + 1, fps)
+    T1, T2 = path[f1], path[f2]
+    vel = np.zeros((n, 3))
+    for k, ob in enumerate(objs):
+        vel[oid == k] = ob.velocity
+    moving = np.linalg.norm(vel, axis=1) > 0
+
+    def project(T, X):
+        Y = X @ T[:, :3].T + T[:, 3]
+        z = Y[:, 2]
+        u = cam.fx * Y[:, 0] / np.maximum(z, 1e-9) + cam.cx
+        v = cam.fy * Y[:, 1] / np.maximum(z, 1e-9) + cam.cy
+        ok = (z > 0.3) & (u >= 0) & (u <= width - 1) & (v >= 0) & (v <= height - 1)
+        return np.stack([u, v], 1), ok
+
+    X1 = rec[:, 0:3].astype(np.float64) + vel * (f1 / fps)
+    X2 = rec[:, 0:3].astype(np.float64) + vel * (f2 / fps)
+    q1, ok1 = project(T1, X1)
+    q2, ok2 = project(T2, X2)
+    cand = np.nonzero(ok1 & ok2)[0]
+    pick = rng.choice(cand, size=min(n_sample, len(cand)), replace=False)
+    gid = np.repeat(pick, per_gauss).astype(np.int32)
+    p1 = (q1[gid] + rng.normal(0, noise_px, (len(gid), 2))).astype(np.float32)
+    p2 = (q2[gid] + rng.normal(0, noise_px, (len(gid), 2))).astype(np.float32)
+    labels = moving.astype(np.uint8)
+    labels[(~moving) & (rng.random(n) < suppressed)] = 1
+    return dict(records=rec, camera=cam, pose_1=T1, pose_2=T2, p1=p1, p2=p2, gid=gid, labels=labels,
+                moving=moving)
+
+
 # ------------------------------------------------------------------ learned MP network
 
 MPNET_BLOB_BYTES = 22016
