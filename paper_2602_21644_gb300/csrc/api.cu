@@ -85,6 +85,7 @@ struct dags_ctx {
   LmBuffers lm;                   // allocated by the first LM call
   double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
   double *edge_partial = nullptr; // per-CTA sums of the edge-warp term (first call)
+  float *rel32 = nullptr;         // [12] FP32 relative pose of the regularisers (first call)
   EpiBuffers epi;                 // epipolar verification, grown on demand
   MpBuffers mp;
   MpnetScratch net;
@@ -129,7 +130,7 @@ void free_lm(LmBuffers &b) {
 }
 
 void free_epi(EpiBuffers &b) {
-  void *ptrs[] = {b.count, b.off, b.block_sum, b.rank, b.vals, b.dist};
+  void *ptrs[] = {b.count, b.off, b.block_sum, b.rank, b.vals, b.dist, b.F};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   b = EpiBuffers();
@@ -345,6 +346,7 @@ void dags_destroy(dags_ctx *ctx) {
   free_lm(ctx->lm);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
   if (ctx->edge_partial) cudaFree(ctx->edge_partial);
+  if (ctx->rel32) cudaFree(ctx->rel32);
   free_epi(ctx->epi);
   free_mp(ctx->mp);
   free_net(ctx->net);
@@ -783,11 +785,12 @@ int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const flo
     return DAGS_E_INVAL;
   if (((uintptr_t)gauss & 15u) != 0 || ((uintptr_t)prev & 15u) != 0 || ((uintptr_t)grad_gauss & 15u) != 0)
     return DAGS_E_INVAL;
-  if (!ctx->reg_partial) {
-    const cudaError_t a = alloc(&ctx->reg_partial, (size_t)mp_consistency_blocks(ctx->ws.max_n) + 1);
+  if (!ctx->reg_partial || !ctx->rel32) {
+    cudaError_t a = ctx->reg_partial ? cudaSuccess
+                                     : alloc(&ctx->reg_partial, (size_t)mp_consistency_blocks(ctx->ws.max_n) + 1);
+    if (a == cudaSuccess && !ctx->rel32) a = alloc(&ctx->rel32, (size_t)12);
     if (a != cudaSuccess) {
       cudaGetLastError();
-      ctx->reg_partial = nullptr;
       return a == cudaErrorMemoryAllocation ? DAGS_E_NOMEM : DAGS_E_CUDA;
     }
   }
@@ -796,7 +799,8 @@ int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const flo
   const int ev = ctx->timer.begin(DAGS_K_REGULARISER, s);
   const cudaError_t e = launch_mp_consistency(reinterpret_cast<const float4 *>(gauss),
                                               reinterpret_cast<const float4 *>(prev), n, rel_pose, lambda,
-                                              grad_gauss, ctx->reg_partial, ctx->ws.counters + CNT_DONE_REG, loss, s);
+                                              grad_gauss, ctx->reg_partial, ctx->ws.counters + CNT_DONE_REG, loss,
+                                              ctx->rel32, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }
@@ -824,12 +828,13 @@ int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i,
     return DAGS_E_INVAL;
   Raster r;
   if ((rc = make_raster(cam, nullptr, &r))) return rc;
-  if (!ctx->edge_partial) {
-    const cudaError_t a =
-        alloc(&ctx->edge_partial, (size_t)edge_warp_blocks((int64_t)ctx->ws.max_w * ctx->ws.max_h) * 13);
+  if (!ctx->edge_partial || !ctx->rel32) {
+    cudaError_t a = ctx->edge_partial
+                        ? cudaSuccess
+                        : alloc(&ctx->edge_partial, (size_t)edge_warp_blocks((int64_t)ctx->ws.max_w * ctx->ws.max_h) * 13);
+    if (a == cudaSuccess && !ctx->rel32) a = alloc(&ctx->rel32, (size_t)12);
     if (a != cudaSuccess) {
       cudaGetLastError();
-      ctx->edge_partial = nullptr;
       return a == cudaErrorMemoryAllocation ? DAGS_E_NOMEM : DAGS_E_CUDA;
     }
   }
@@ -837,7 +842,7 @@ int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i,
   ctx->last_stream = s;
   const int ev = ctx->timer.begin(DAGS_K_REGULARISER, s);
   const cudaError_t e = launch_edge_warp(r, depth_i, depth_j, weight_j, pose_i, pose_j, c, lambda,
-                                         ctx->edge_partial, ctx->ws.counters + CNT_DONE_REG, out, s);
+                                         ctx->edge_partial, ctx->ws.counters + CNT_DONE_REG, out, ctx->rel32, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }
@@ -868,6 +873,7 @@ int epipolar_verify(dags_ctx *ctx, const dags_camera *cam, const double *pose_1,
     A(alloc(&b.rank, (size_t)cm));
     A(alloc(&b.vals, (size_t)cm));
     A(alloc(&b.dist, (size_t)cm));
+    A(alloc(&b.F, (size_t)9));
     if (e != cudaSuccess) {
       cudaGetLastError();
       free_epi(b);

@@ -153,9 +153,10 @@ int64_t mp_consistency_blocks(int64_t n);
 int64_t edge_warp_blocks(int64_t pixels);
 cudaError_t launch_edge_warp(const Raster &r, const float *Di, const float *Dj, const float *wj, const double *pose_i,
                              const double *pose_j, const dags_edge_cfg &c, float lam, double *partial, uint32_t *done,
-                             double *out, cudaStream_t s);
+                             double *out, float *tji, cudaStream_t s);
 cudaError_t launch_mp_consistency(const float4 *gauss, const float4 *prev, int64_t n, const double *rel, float lam,
-                                  float *grad, double *partial, uint32_t *done, double *loss, cudaStream_t s);
+                                  float *grad, double *partial, uint32_t *done, double *loss, float *rel32,
+                                  cudaStream_t s);
 
 // Epipolar verification (epipolar.cu): buffers owned by the ctx, grown on
 // demand.
@@ -164,6 +165,7 @@ struct EpiBuffers {
   uint32_t *block_sum = nullptr;               // [scan blocks of cap_n]
   uint32_t *rank = nullptr;                    // [cap_m]
   float *vals = nullptr, *dist = nullptr;      // [cap_m]
+  double *F = nullptr;                         // [9]
   int64_t cap_n = 0, cap_m = 0;
 };
 int64_t epi_scan_blocks(int64_t n);

@@ -1,9 +1,10 @@
 // Epipolar verification and static recovery (Sec. IV-C, Eqs. (18), (19)) on
 // sm_103a:
 //
-//   epi_dist_kernel     per match: F = K^-T [t]x R K^-1 (formed once per CTA
-//                       in FP64 from the two poses), the point-to-epipolar-
-//                       line distance d of Eq. (18) in FP64, and the match's
+//   epi_F_kernel        F = K^-T [t]x R K^-1 from the two poses, FP64, one
+//                       thread
+//   epi_dist_kernel     per match: the point-to-epipolar-line distance d of
+//                       Eq. (18) in FP64, and the match's
 //                       rank inside its Gaussian's group (one atomic per
 //                       match on the Gaussian's count)
 //   scan (3 kernels)    exclusive scan of the per-Gaussian counts into group
@@ -29,13 +30,13 @@ constexpr int kEpiBlock = 256;
 constexpr int kScanItems = 4;                  // counts per thread in the block scan
 constexpr int kScanTile = kEpiBlock * kScanItems;
 
-__global__ void __launch_bounds__(kEpiBlock)
-epi_dist_kernel(Raster r, const double *__restrict__ pose_1, const double *__restrict__ pose_2,
-                const float2 *__restrict__ p1, const float2 *__restrict__ p2, const int32_t *__restrict__ gid,
-                int64_t m, int64_t n, float *__restrict__ dist, uint32_t *__restrict__ count,
-                uint32_t *__restrict__ rank, uint32_t *status) {
-  __shared__ double s_F[9];
-  if (threadIdx.x == 0) {
+// F = K^-T [t]x R K^-1 of the relative pose (R, t) = T_2W T_1W^-1, in FP64
+// by one thread (FP64 instructions are scarce on GB300: the per-match kernel
+// only reads it).
+__global__ void epi_F_kernel(Raster r, const double *__restrict__ pose_1, const double *__restrict__ pose_2,
+                             double *__restrict__ F) {
+  if (threadIdx.x != 0) return;
+  {
     // R = R2 R1^T, t = t2 - R t1, E = [t]x R, F = K^-T E K^-1
     double R[9], t[3], E[9];
     for (int a = 0; a < 3; ++a)
@@ -58,11 +59,19 @@ epi_dist_kernel(Raster r, const double *__restrict__ pose_1, const double *__res
     }
     // K^-T (E K^-1): rows 0, 1 scale, row 2 combines
     for (int b = 0; b < 3; ++b) {
-      s_F[b] = EK[b] * ifx;
-      s_F[3 + b] = EK[3 + b] * ify;
-      s_F[6 + b] = EK[b] * kx + EK[3 + b] * ky + EK[6 + b];
+      F[b] = EK[b] * ifx;
+      F[3 + b] = EK[3 + b] * ify;
+      F[6 + b] = EK[b] * kx + EK[3 + b] * ky + EK[6 + b];
     }
   }
+}
+
+__global__ void __launch_bounds__(kEpiBlock)
+epi_dist_kernel(const double *__restrict__ F, const float2 *__restrict__ p1, const float2 *__restrict__ p2,
+                const int32_t *__restrict__ gid, int64_t m, int64_t n, float *__restrict__ dist,
+                uint32_t *__restrict__ count, uint32_t *__restrict__ rank, uint32_t *status) {
+  __shared__ double s_F[9];
+  if (threadIdx.x < 9) s_F[threadIdx.x] = F[threadIdx.x];
   __syncthreads();
   const int64_t k = (int64_t)blockIdx.x * kEpiBlock + threadIdx.x;
   if (k >= m) return;
@@ -201,8 +210,10 @@ cudaError_t launch_epipolar(const Raster &r, const double *pose_1, const double 
   const unsigned gm = (unsigned)((m + kEpiBlock - 1) / kEpiBlock);
   const unsigned gn = (unsigned)((n + kEpiBlock - 1) / kEpiBlock);
   const int nb = (int)epi_scan_blocks(n);
-  if (m > 0)
-    epi_dist_kernel<<<gm, kEpiBlock, 0, s>>>(r, pose_1, pose_2, p1, p2, gid, m, n, dist, b.count, b.rank, status);
+  if (m > 0) {
+    epi_F_kernel<<<1, 32, 0, s>>>(r, pose_1, pose_2, b.F);
+    epi_dist_kernel<<<gm, kEpiBlock, 0, s>>>(b.F, p1, p2, gid, m, n, dist, b.count, b.rank, status);
+  }
   if (n > 0) {
     scan_tiles_kernel<<<(unsigned)nb, kEpiBlock, 0, s>>>(b.count, n, b.off, b.block_sum);
     scan_sums_kernel<<<1, kEpiBlock, 0, s>>>(b.block_sum, nb);

@@ -14,7 +14,7 @@
 // MP-guided edge-warp regulariser (Sec. IV-D, Eqs. (25), (26)): one thread
 // per pixel u of frame i. An edge pixel (a valid 4-neighbour differs by more
 // than edge_rel times its depth) is back-projected with its observed depth, moved by
-// T_ji = T_jW T_iW^-1 (computed once per CTA in FP64) and projected into frame
+// T_ji = T_jW T_iW^-1 (formed once in FP64 by a one-thread kernel) and projected into frame
 // j; D_j and w^j are sampled bilinearly at u', r = w^j (D_j - z_ref) enters
 // the Huber kernel, and the gradients with respect to both poses' left
 // twists follow by the chain rule through the bilinear cell, the projection
@@ -30,25 +30,26 @@ constexpr int kRegBlock = 256;
 
 __global__ void __launch_bounds__(kRegBlock)
 mp_consistency_kernel(const float4 *__restrict__ gauss, const float4 *__restrict__ prev, int64_t n,
-                      const double *__restrict__ rel, float lam, float *__restrict__ grad,
+                      const float *__restrict__ rel, float lam, float *__restrict__ grad,
                       double *__restrict__ partial, uint32_t *__restrict__ done, double *__restrict__ loss) {
   __shared__ double s_sum[kRegBlock];
+  __shared__ float s_warp[kRegBlock / 32];
   __shared__ int s_last;
   const int tid = threadIdx.x;
   const int64_t i = (int64_t)blockIdx.x * kRegBlock + tid;
-  double term = 0.0;
+  float term = 0.f;
   if (i < n) {
     const float4 g0 = __ldg(gauss + 4 * i), g2 = __ldg(gauss + 4 * i + 2);
     const float4 p0 = __ldg(prev + 4 * i);
     float hx = p0.x, hy = p0.y, hz = p0.z;
     if (rel) {
-      hx = (float)(rel[0] * p0.x + rel[1] * p0.y + rel[2] * p0.z + rel[3]);
-      hy = (float)(rel[4] * p0.x + rel[5] * p0.y + rel[6] * p0.z + rel[7]);
-      hz = (float)(rel[8] * p0.x + rel[9] * p0.y + rel[10] * p0.z + rel[11]);
+      hx = rel[0] * p0.x + rel[1] * p0.y + rel[2] * p0.z + rel[3];
+      hy = rel[4] * p0.x + rel[5] * p0.y + rel[6] * p0.z + rel[7];
+      hz = rel[8] * p0.x + rel[9] * p0.y + rel[10] * p0.z + rel[11];
     }
     const float mbar = 1.f - g2.w;
     const float dx = g0.x - hx, dy = g0.y - hy, dz = g0.z - hz;
-    term = (double)(mbar * (dx * dx + dy * dy + dz * dz));
+    term = mbar * (dx * dx + dy * dy + dz * dz);
     if (grad) {
       float4 *gp = reinterpret_cast<float4 *>(grad) + 4 * i;
       float4 gv = *gp;
@@ -60,23 +61,28 @@ mp_consistency_kernel(const float4 *__restrict__ gauss, const float4 *__restrict
     }
   }
   if (!loss) return;
-  s_sum[tid] = term;
+  // FP32 warp sums (fixed shuffle order), then the CTA's warps in FP64 by one
+  // thread: FP64 instructions are scarce on GB300, so none per element
+  const float ws = warp_sum(term);
+  if ((tid & 31) == 0) s_warp[tid >> 5] = ws;
   __syncthreads();
-  for (int o = kRegBlock / 2; o > 0; o >>= 1) {
-    if (tid < o) s_sum[tid] += s_sum[tid + o];
-    __syncthreads();
-  }
   if (tid == 0) {
-    partial[blockIdx.x] = s_sum[0];
+    double b = 0.0;
+#pragma unroll
+    for (int w = 0; w < kRegBlock / 32; ++w) b += (double)s_warp[w];
+    partial[blockIdx.x] = b;
     __threadfence();
     s_last = atomicAdd(done, 1u) == gridDim.x - 1;
     if (s_last) __threadfence();
   }
   __syncthreads();
   if (!s_last) return;
-  double acc = 0.0;
-  for (int k = tid; k < (int)gridDim.x; k += kRegBlock) acc += __ldcg(partial + k);
-  s_sum[tid] = acc;
+  // the CTA sums in a fixed order: 256 strided threads, four accumulators
+  // each, then a fixed tree
+  double a4[4] = {0.0, 0.0, 0.0, 0.0};
+  int j = 0;
+  for (int k = tid; k < (int)gridDim.x; k += kRegBlock, ++j) a4[j & 3] += __ldcg(partial + k);
+  s_sum[tid] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
   __syncthreads();
   for (int o = kRegBlock / 2; o > 0; o >>= 1) {
     if (tid < o) s_sum[tid] += s_sum[tid + o];
@@ -88,33 +94,40 @@ mp_consistency_kernel(const float4 *__restrict__ gauss, const float4 *__restrict
   }
 }
 
+// T_ji = T_jW T_iW^-1 (R = Rj Ri^T, t = tj - R ti) of two world-to-camera
+// poses, or pose_j itself when pose_i is NULL, in FP64 by one thread, rounded
+// to FP32 for the per-element kernels.
+__global__ void rel_pose_kernel(const double *__restrict__ pose_i, const double *__restrict__ pose_j,
+                                float *__restrict__ out) {
+  if (threadIdx.x != 0) return;
+  if (!pose_i) {
+    for (int k = 0; k < 12; ++k) out[k] = (float)pose_j[k];
+    return;
+  }
+  double R[9];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      R[3 * a + b] = pose_j[4 * a] * pose_i[4 * b] + pose_j[4 * a + 1] * pose_i[4 * b + 1] +
+                     pose_j[4 * a + 2] * pose_i[4 * b + 2];
+  for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b < 3; ++b) out[4 * a + b] = (float)R[3 * a + b];
+    out[4 * a + 3] =
+        (float)(pose_j[4 * a + 3] - (R[3 * a] * pose_i[3] + R[3 * a + 1] * pose_i[7] + R[3 * a + 2] * pose_i[11]));
+  }
+}
+
 constexpr int kEdgeBlock = 256;
 constexpr int kEdgeOut = 13;     // lambda L_edge, d/d xi_i (6), d/d xi_j (6)
 
 __global__ void __launch_bounds__(kEdgeBlock)
 edge_warp_kernel(Raster r, const float *__restrict__ Di, const float *__restrict__ Dj,
-                 const float *__restrict__ wj, const double *__restrict__ pose_i, const double *__restrict__ pose_j,
-                 dags_edge_cfg c, float lam, double *__restrict__ partial, uint32_t *__restrict__ done,
-                 double *__restrict__ out) {
+                 const float *__restrict__ wj, const float *__restrict__ Tji, dags_edge_cfg c, float lam,
+                 double *__restrict__ partial, uint32_t *__restrict__ done, double *__restrict__ out) {
   __shared__ float s_T[12];
-  __shared__ double s_red[kEdgeBlock / 32][kEdgeOut];
+  __shared__ float s_red[kEdgeBlock / 32][kEdgeOut];
   __shared__ int s_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) {
-    // T_ji = T_jW T_iW^-1: R = Rj Ri^T, t = tj - R ti
-    double R[9], t[3];
-    for (int a = 0; a < 3; ++a) {
-      for (int b = 0; b < 3; ++b)
-        R[3 * a + b] = pose_j[4 * a] * pose_i[4 * b] + pose_j[4 * a + 1] * pose_i[4 * b + 1] +
-                       pose_j[4 * a + 2] * pose_i[4 * b + 2];
-    }
-    for (int a = 0; a < 3; ++a)
-      t[a] = pose_j[4 * a + 3] - (R[3 * a] * pose_i[3] + R[3 * a + 1] * pose_i[7] + R[3 * a + 2] * pose_i[11]);
-    for (int a = 0; a < 3; ++a) {
-      for (int b = 0; b < 3; ++b) s_T[4 * a + b] = (float)R[3 * a + b];
-      s_T[4 * a + 3] = (float)t[a];
-    }
-  }
+  if (tid < 12) s_T[tid] = Tji[tid];
   __syncthreads();
   const int W = r.W, H = r.H;
   const int p = blockIdx.x * kEdgeBlock + tid;
@@ -188,14 +201,14 @@ edge_warp_kernel(Raster r, const float *__restrict__ Di, const float *__restrict
 #pragma unroll
   for (int k = 0; k < kEdgeOut; ++k) {
     const float sw = warp_sum(v[k]);
-    if (lane == 0) s_red[warp][k] = (double)sw;
+    if (lane == 0) s_red[warp][k] = sw;
   }
   __syncthreads();
   if (tid < kEdgeOut) {
-    double a = 0.0;
+    float a = 0.f;
 #pragma unroll
     for (int w = 0; w < kEdgeBlock / 32; ++w) a += s_red[w][tid];
-    partial[(size_t)blockIdx.x * kEdgeOut + tid] = a;
+    partial[(size_t)blockIdx.x * kEdgeOut + tid] = (double)a;
   }
   __syncthreads();
   if (tid == 0) {
@@ -232,22 +245,25 @@ int64_t edge_warp_blocks(int64_t pixels) { return (pixels + kEdgeBlock - 1) / kE
 
 cudaError_t launch_edge_warp(const Raster &r, const float *Di, const float *Dj, const float *wj, const double *pose_i,
                              const double *pose_j, const dags_edge_cfg &c, float lam, double *partial, uint32_t *done,
-                             double *out, cudaStream_t s) {
-  edge_warp_kernel<<<(unsigned)edge_warp_blocks((int64_t)r.W * r.H), kEdgeBlock, 0, s>>>(r, Di, Dj, wj, pose_i, pose_j,
-                                                                                          c, lam, partial, done, out);
+                             double *out, float *tji, cudaStream_t s) {
+  rel_pose_kernel<<<1, 32, 0, s>>>(pose_i, pose_j, tji);
+  edge_warp_kernel<<<(unsigned)edge_warp_blocks((int64_t)r.W * r.H), kEdgeBlock, 0, s>>>(r, Di, Dj, wj, tji, c, lam,
+                                                                                          partial, done, out);
   return cudaGetLastError();
 }
 
 int64_t mp_consistency_blocks(int64_t n) { return (n + kRegBlock - 1) / kRegBlock; }
 
 cudaError_t launch_mp_consistency(const float4 *gauss, const float4 *prev, int64_t n, const double *rel, float lam,
-                                  float *grad, double *partial, uint32_t *done, double *loss, cudaStream_t s) {
+                                  float *grad, double *partial, uint32_t *done, double *loss, float *rel32,
+                                  cudaStream_t s) {
   if (n == 0) {
     if (loss) return cudaMemsetAsync(loss, 0, sizeof(double), s);
     return cudaSuccess;
   }
-  mp_consistency_kernel<<<(unsigned)mp_consistency_blocks(n), kRegBlock, 0, s>>>(gauss, prev, n, rel, lam, grad,
-                                                                                 partial, done, loss);
+  if (rel) rel_pose_kernel<<<1, 32, 0, s>>>(nullptr, rel, rel32);
+  mp_consistency_kernel<<<(unsigned)mp_consistency_blocks(n), kRegBlock, 0, s>>>(gauss, prev, n, rel ? rel32 : nullptr,
+                                                                                 lam, grad, partial, done, loss);
   return cudaGetLastError();
 }
 

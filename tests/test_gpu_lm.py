@@ -236,3 +236,48 @@ def test_track_lm_converges_and_replays_identically(dags):
         np.testing.assert_array_equal(q, p)
         np.testing.assert_array_equal(st2, st)
     ctx.close()
+
+
+def test_capacity_overflow_rejects_the_point(dags):
+    # a pair-capacity overflow renders nothing: the loss is NaN, the LM step
+    # rejects the point (the pose stays) and the status reports the capacity
+    sc = synth.tiny_scene(0)
+    cam = dags.Camera(*sc.camera.as_tuple())
+    gauss, poses, targets = to_dev(sc, torch)
+    ctx = dags.Context(gauss.shape[0], cam.width, cam.height, 1, max_pairs=2000)
+    normal, _ = ctx.normal_equations(gauss, cam, poses[0].contiguous(), targets[0].contiguous())
+    torch.cuda.synchronize()
+    assert np.isnan(normal[0].item())
+    assert ctx.sync_status()[0] == -3
+    pose = poses[0].clone().contiguous()
+    state = ctx.track_lm(gauss, cam, pose, targets[0].contiguous(), 3, use_graph=False)
+    torch.cuda.synchronize()
+    assert ctx.sync_status()[0] == -3
+    st = state.cpu().numpy()
+    assert st[41] == 0 and st[42] == 3                     # nothing accepted
+    np.testing.assert_array_equal(pose.cpu().numpy(), sc.poses[0])
+    ctx.close()
+
+
+def test_empty_map_and_argument_errors(dags):
+    sc = synth.tiny_scene(1)
+    cam = dags.Camera(*sc.camera.as_tuple())
+    _, poses, targets = to_dev(sc, torch)
+    ctx = dags.Context(100, cam.width, cam.height, 1)
+    empty = torch.zeros((0, 16), dtype=torch.float32, device="cuda")
+    normal, _ = ctx.normal_equations(empty, cam, poses[0].contiguous(), targets[0].contiguous())
+    torch.cuda.synchronize()
+    ctx.check()
+    assert np.all(normal.cpu().numpy() == 0.0)
+    pose = poses[0].clone().contiguous()
+    ctx.track_lm(empty, cam, pose, targets[0].contiguous(), 2, use_graph=False)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(pose.cpu().numpy(), sc.poses[0])    # tr H = 0: no step
+    g = torch.from_numpy(sc.records[:100]).cuda()
+    for kw in (dict(delta=0.0), dict(delta=float("inf"))):
+        with pytest.raises(dags.DagsError):
+            ctx.normal_equations(g, cam, poses[0].contiguous(), targets[0].contiguous(), **kw)
+    for kw in (dict(down=0.0), dict(up=0.5), dict(mu_max=1e-12, mu_min=1.0), dict(delta=-1.0)):
+        with pytest.raises(dags.DagsError):
+            ctx.track_lm(g, cam, pose, targets[0].contiguous(), 1, cfg=dags.default_lm_cfg(**kw))
+    ctx.close()
