@@ -417,6 +417,70 @@ def tracking_sequence(n: int = 300_000, frames=range(10, 60), seed: int = 0, wid
     return rec, cam, out, dict(objects=objs, object_id=oid, n_instances=len(moving))
 
 
+def spline_path(n_frames: int, fps: float = 30.0, seed: int = 0):
+    """Camera on a smooth closed Catmull-Rom spline through eight seeded
+    viewpoints inside the room (one loop per 10 s), looking at a target that
+    moves on a second spline; world-to-camera poses."""
+    rng = np.random.default_rng(seed + 555)
+    k = 8
+    ang = np.linspace(0, 2 * np.pi, k, endpoint=False)
+    eyes = np.stack([0.9 * np.cos(ang), -0.2 + rng.uniform(-0.15, 0.15, k), -1.2 + 0.6 * np.sin(ang)], 1)
+    tgts = np.stack([0.5 * np.sin(ang + 1.0), 0.3 + rng.uniform(-0.1, 0.1, k), 1.5 + 0.2 * np.cos(ang)], 1)
+
+    def cr(pts, u):
+        i = int(np.floor(u)) % k
+        t = u - np.floor(u)
+        p0, p1, p2, p3 = pts[(i - 1) % k], pts[i], pts[(i + 1) % k], pts[(i + 2) % k]
+        return 0.5 * ((2 * p1) + (-p0 + p2) * t + (2 * p0 - 5 * p1 + 4 * p2 - p3) * t * t +
+                      (-p0 + 3 * p1 - 3 * p2 + p3) * t ** 3)
+
+    poses = []
+    for f in range(n_frames):
+        u = (f / fps) / 10.0 * k
+        poses.append(look_at_pose(cr(eyes, u), cr(tgts, u)))
+    return poses
+
+
+def full_loop_sequence(n: int = 1_000_000, frames=range(0, 12), seed: int = 0, width: int = 1200, height: int = 680,
+                       fps: float = 30.0, flip: float = 0.05):
+    """The full loop at scale: n room Gaussians with three moving ellipsoids
+    (0.3 m/s along x, z and the xz diagonal) and one static one, a
+    width x height RGB-D camera with the 640x480 rig's horizontal field of
+    view (f = 525 * width / 640), the camera on spline_path. Per frame: the
+    ray-cast target (1% depth noise), the moving objects' instance map with
+    `flip` pixel flips, the ground-truth pose. Returns (records, camera,
+    [dict(frame, target, instance, gt_pose)], extra)."""
+    cs = [np.array([-1.2, 0.6, 0.8]), np.array([1.0, 0.5, -0.6]), np.array([0.1, 0.7, 0.2]),
+          np.array([0.2, 0.9, 1.6])]
+    ax = [np.array([0.35, 0.5, 0.3]), np.array([0.4, 0.3, 0.45]), np.array([0.3, 0.3, 0.3]),
+          np.array([0.5, 0.25, 0.2])]
+    vs = [np.array([0.3, 0.0, 0.0]), np.array([0.0, 0.0, 0.3]), np.array([0.21, 0.0, -0.21]), np.zeros(3)]
+    objs = [Ellipsoid(c.copy(), a.copy(), v.copy()) for c, a, v in zip(cs, ax, vs)]
+    rec, oid, objs = room_scene(n, seed, objects=objs)
+    f = 525.0 * width / 640.0
+    cam = Camera(f, f, width / 2.0, height / 2.0, width, height)
+    frames = list(frames)
+    path = spline_path(max(frames) + 1, fps, seed)
+    out = []
+    moving = [k for k, ob in enumerate(objs) if np.any(ob.velocity != 0)]
+    for fr in frames:
+        rng = np.random.default_rng(seed + 31 + fr)
+        tg, hit = raycast(cam, path[fr], objs, fr / fps, 0.01, rng)
+        tg[(tg[:, 3] < 0.5) | (tg[:, 3] > 5.0), 3] = 0.0
+        inst = np.zeros(hit.shape, np.uint8)
+        for lab, k in enumerate(moving, start=1):
+            inst[hit == k] = lab
+        if flip > 0:
+            fl = rng.random(inst.shape) < flip
+            repl = rng.integers(0, len(moving) + 1, inst.shape).astype(np.uint8)
+            same = repl == inst
+            repl[same] = (repl[same] + 1) % (len(moving) + 1)
+            inst = np.where(fl, repl, inst).astype(np.uint8)
+        out.append(dict(frame=fr, target=tg, instance=inst, gt_pose=path[fr]))
+    return rec, cam, out, dict(objects=objs, object_id=oid, n_instances=len(moving),
+                               dynamic=np.isin(oid, moving))
+
+
 def epipolar_matches(n: int = 300_000, frames=(11, 16), seed: int = 0, width: int = 640, height: int = 480,
                      fps: float = 30.0, n_sample: int = 20_000, per_gauss: int = 4, noise_px: float = 0.3,
                      suppressed: float = 0.1):

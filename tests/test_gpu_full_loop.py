@@ -1,0 +1,145 @@
+"""The full loop at scale (1M Gaussians, 1200x680 RGB-D, three moving
+ellipsoids, spline camera): full-image parity of one frame's forward and
+adjoint against the FP64 oracle, and the loop itself through the C ABI for a
+dozen frames. Per frame: tracking (LM), the MP update, semantic refreshes
+every 10 frames with the learned proposal in between, the trigger's score.
+Every 5th frame: mapping over a window of up to 8 keyframes, the MP-weighted
+loss and its Gaussian gradient with lambda_3 L_MP."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_21644_gb300 import synth
+
+from gpu_common import GRAD_NORM, LOSS_REL, POSE_REL, compare_grads, mask_flagged_targets, oracle_views
+from test_gpu_splat import assert_image_parity, run
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dags():
+    from paper_2602_21644_gb300 import build
+    build.build()
+    oracle.build()
+    from paper_2602_21644_gb300 import dags as d
+    d.load()
+    return d
+
+
+@pytest.fixture(scope="module")
+def sequence():
+    return synth.full_loop_sequence(frames=range(0, 12))
+
+
+def test_full_scale_frame_parity(dags, sequence):
+    rec, cam, seq, _ = sequence
+    # frame 10's target from frame 9's pose (the tracking starting point)
+    sc = synth.Scene(rec, cam, seq[9]["gt_pose"][None], seq[10]["target"][None].astype(np.float32))
+    sc, masked = mask_flagged_targets(sc)
+    assert masked < 0.01 * sc.targets.shape[1]
+    res = run(dags, sc, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
+    G, ocam, outs = oracle_views(sc)
+    report = []
+    assert_image_parity(res, outs, "full loop 1200x680", report)
+    assert abs(res["loss"] - outs[0]["loss"]) <= LOSS_REL * abs(outs[0]["loss"])
+    pg = np.linalg.norm(res["gp"][0] - outs[0]["pose_grad"]) / np.linalg.norm(outs[0]["pose_grad"])
+    g = compare_grads(res["gg"], outs[0]["grad"], report)
+    report.append(f"pose grad rel {pg:.3e}")
+    print("\n" + "\n".join(report))
+    # the twist gradient is one sum over every pixel-Gaussian term, accumulated
+    # in FP32 (atomics per Gaussian, then the per-Gaussian chain): rounding
+    # grows like the square root of the terms, so the 300k x 640x480 bound
+    # scales by sqrt(P N / (P0 N0))
+    scale = np.sqrt((cam.width * cam.height * rec.shape[0]) / (640 * 480 * 300_000))
+    assert pg <= POSE_REL * scale
+    for k, v in g.items():
+        assert v <= GRAD_NORM, f"gradient group {k}: {v:.3e}"
+    res["ctx"].close()
+
+
+def pose_error(T, T_gt):
+    T = np.asarray(T).reshape(3, 4)
+    T_gt = np.asarray(T_gt).reshape(3, 4)
+    return float(np.linalg.norm(T[:, :3].T @ T[:, 3] - T_gt[:, :3].T @ T_gt[:, 3]))
+
+
+def test_full_loop_runs_at_scale(dags, sequence):
+    rec, scam, seq, ex = sequence
+    cam = dags.Camera(*scam.as_tuple())
+    n, P, W, H = rec.shape[0], cam.width * cam.height, cam.width, cam.height
+    dev = "cuda"
+    gauss = torch.from_numpy(rec.copy()).to(dev)
+    gauss[:, 11] = 0.2                                   # uninformed initial MP
+    prev = gauss.clone()                                 # the snapshot of Eq. (23)
+    table = torch.tensor([[0.1, 0.05]] + [[0.9, 0.8]] * ex["n_instances"], dtype=torch.float32, device=dev)
+    labels = torch.zeros(n, dtype=torch.uint8, device=dev)
+    blob, _ = synth.mpnet_init(0)
+    net = torch.from_numpy(blob).to(dev)
+    tctx = dags.Context(n, W, H, 1)
+    mctx = dags.Context(n, W, H, 8)
+    state = torch.zeros(2, dtype=torch.int32, device=dev)
+    score = torch.zeros(3, dtype=torch.float64, device=dev)
+    image = torch.empty((1, dags.IMG_CHANNELS, H, W), dtype=torch.float32, device=dev)
+    last = torch.empty((1, H, W), dtype=torch.int32, device=dev)
+    pose = torch.from_numpy(seq[0]["gt_pose"].copy()).to(dev)
+    keyframes, errors, times, accepted = [], [], [], []
+    refresh_inst = None
+    for k, fr in enumerate(seq):
+        t0 = time.perf_counter()
+        tg = torch.from_numpy(fr["target"]).to(dev)
+        if k > 0:
+            st = tctx.track_lm(gauss, cam, pose, tg, 15)
+            accepted.append(int(st[41].item()))
+        tctx.forward(gauss, cam, pose[None], tg[None], image=image, last=last)
+        refreshed = k % 10 == 0
+        if refreshed:
+            refresh_inst = torch.from_numpy(fr["instance"]).to(dev)
+        mp_map = None
+        if not refreshed:
+            feats = tctx.mpnet_features(image[0].reshape(dags.IMG_CHANNELS, P), tg, refresh_inst, table, cam)
+            mp_map = tctx.mpnet_infer(net, feats[None]).reshape(-1)
+        stats = tctx.mp_update(gauss, cam, pose[None], tg, image[0].reshape(dags.IMG_CHANNELS, P), refresh_inst,
+                               table, labels, seg_refreshed=refreshed, mp_map=mp_map)
+        tctx.semantic_trigger(stats, state, refreshed, score=score)
+        if k % 5 == 0:
+            keyframes = (keyframes + [(pose.clone(), tg)])[-8:]
+            poses = torch.stack([p for p, _ in keyframes])
+            targets = torch.stack([t for _, t in keyframes])
+            img, lst, loss = mctx.forward(gauss, cam, poses, targets)
+            gg, gp = mctx.backward(gauss, cam, poses, targets, img, lst, dags.GRAD_GAUSS | dags.GRAD_POSE)
+            lmp = mctx.mp_consistency(gauss, prev, 500.0, grad=gg)
+            torch.cuda.synchronize()
+            assert np.isfinite(loss.item()) and np.isfinite(lmp.item())
+            assert torch.isfinite(gg).all() and torch.isfinite(gp).all()
+            prev.copy_(gauss)
+        torch.cuda.synchronize()
+        tctx.check()
+        mctx.check()
+        times.append(time.perf_counter() - t0)
+        if k == 10:
+            mp10 = gauss[:, 11].cpu().numpy()           # right after the second refresh
+        errors.append(pose_error(pose.cpu().numpy(), fr["gt_pose"]))
+    mp = gauss[:, 11].cpu().numpy()
+    dyn = ex["dynamic"]
+    seen = mp10 != np.float32(0.2)
+    print(f"\npose errors (mm): {' '.join(f'{1e3 * e:.1f}' for e in errors)}; LM accepted: {accepted}")
+    print(f"frame wall times (ms): {' '.join(f'{1e3 * t:.0f}' for t in times)}")
+    print(f"mean MP after the frame-10 refresh: dynamic {mp10[dyn & seen].mean():.3f}, "
+          f"static {mp10[~dyn & seen].mean():.3f}; last trigger score {score[2].item():.3f}")
+    assert np.all((mp >= 0) & (mp <= 1))
+    # the network is a seeded draw (untrained): the separation is the
+    # refreshed priors' work
+    assert mp10[dyn & seen].mean() > mp10[~dyn & seen].mean() + 0.1
+    # every frame's LM moved past its starting point (the first point is
+    # always accepted). Against these ray-cast targets the loss minimum lies
+    # centimetres from the ground truth and the IRLS steps are short, so the
+    # pose error drifts by millimetres per frame (as the oracle's LM does on
+    # the same frames): a loose sanity bound only
+    assert min(accepted) >= 2
+    assert max(errors) < 0.2
+    tctx.close()
+    mctx.close()
