@@ -131,15 +131,56 @@ def oracle_baseline(args, budget_s):
             break
     dt = time.perf_counter() - t0
     return {"value": it / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{it} full-image fwd+bwd iterations (pose gradient) of the 300k-Gaussian 640x480 frame, "
-                      f"single-threaded FP64 C, {dt:.1f} s"}
+            "sample": f"{it} full-image fwd+bwd iterations (pose gradient) of the {args.gaussians}-Gaussian "
+                      f"{args.width}x{args.height} tracking frame, single-threaded FP64 C, {dt:.1f} s"}
+
+
+def _oracle_worker(gaussians, width, height, budget_s):
+    """One host core's share of the all-cores oracle baseline: the same frame,
+    full-image fwd+bwd iterations for budget_s seconds (scene set-up and one
+    warm-up iteration excluded). Runs in a spawn-started process."""
+    import oracle
+    from paper_2602_21644_gb300 import synth
+    sc = synth.tracking_scene(gaussians, frame=10, width=width, height=height)
+    G = oracle.params_from_records(sc.records)
+    cam = oracle.camera_vec(*sc.camera.as_tuple())
+    oracle.render(G, cam, sc.poses[0], targets=sc.targets[0], grads=True)
+    t0 = time.perf_counter()
+    it = 0
+    while True:
+        oracle.render(G, cam, sc.poses[0], targets=sc.targets[0], grads=True)
+        it += 1
+        if time.perf_counter() - t0 >= budget_s and it >= 1:
+            break
+    return it, time.perf_counter() - t0
+
+
+def oracle_baseline_all_cores(args, budget_s):
+    """The oracle, as it stands, on every host core at once: one process per
+    core (spawn: the bench process already holds a CUDA context), each running
+    whole iterations of the frame; throughput = all iterations / the slowest
+    process's time."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as ex:
+        res = list(ex.map(_oracle_worker, [args.gaussians] * cores, [args.width] * cores, [args.height] * cores,
+                          [budget_s] * cores))
+    its = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return {"value": its / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{its} full-image fwd+bwd iterations (pose gradient) of the {args.gaussians}-Gaussian "
+                      f"{args.width}x{args.height} tracking frame in {cores} processes (one per host core), FP64 C, "
+                      f"{dt:.1f} s"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = oracle_baseline(args, max(5.0, args.cpu_seconds))
+    cb = oracle_baseline_all_cores(args, max(5.0, args.cpu_seconds))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -777,7 +818,8 @@ def run_ours(args):
         variants["edge_warp"] = edge_section(ctx, dags, gauss, cam, tg_all, pose_all, flush, stream)
     variants["epipolar_verify"] = epipolar_section(dags, flush, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline(args, args.cpu_seconds)
+        line["cpu_baseline"] = oracle_baseline_all_cores(args, args.cpu_seconds)
+        line["cpu_baseline"]["single_core"] = oracle_baseline(args, min(args.cpu_seconds, 10.0))
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
