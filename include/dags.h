@@ -218,10 +218,10 @@ int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, 
  * Eq. (27). pose (device, 12 doubles) and adam_state (device, 13 doubles)
  * are updated in place; image, last, loss and grad_pose hold the last
  * iteration's values. With use_graph != 0 (and timing off) one iteration
- * is captured once into a CUDA graph on a private stream, cached in the ctx
- * for exactly these arguments (pointers, sizes, camera, configs), and
- * replayed iters times on `stream`; (re)capturing synchronises `stream`
- * first. Capacity overflow is reported by dags_sync_status as for
+ * and a chunk of ten are captured once into CUDA graphs on a private stream,
+ * cached in the ctx for exactly these arguments (pointers, sizes, camera,
+ * configs), and replayed on `stream` (chunks, then single iterations);
+ * (re)capturing synchronises `stream` first. Capacity overflow is reported by dags_sync_status as for
  * splat_forward. */
 int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                 const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
@@ -354,8 +354,9 @@ int lm_pose_step(dags_ctx *ctx, const double *normal, const dags_lm_cfg *cfg, do
 /* iters LM iterations of one view starting from pose (device in/out, 12
  * doubles; out: T_best): lm_init, then per iteration splat_normal_equations
  * at the ctx's pose_try and lm_pose_step. state: device, DAGS_LM_STATE
- * doubles. With use_graph the iteration is captured once per argument set
- * into a CUDA graph and replayed (the first call is not captured). */
+ * doubles. With use_graph one iteration and a chunk of ten are captured once
+ * per argument set into CUDA graphs and replayed (chunks, then single
+ * iterations). */
 int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                    const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                    const dags_lm_cfg *lmcfg, int32_t iters, double *state, int32_t use_graph, void *stream);

@@ -67,9 +67,12 @@ struct KernelTimer {
   }
 };
 
-// A captured tracking iteration and the arguments it was captured with.
+// A captured tracking iteration (exec) and a captured chunk of kTrackUnroll
+// iterations (exec_chunk), and the arguments they were captured with.
+constexpr int kTrackUnroll = 10;
 struct TrackGraph {
   cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec_chunk = nullptr;
   cudaStream_t cap = nullptr;       // private stream used for capture
   unsigned char key[512];
   size_t key_len = 0;
@@ -340,8 +343,10 @@ void dags_destroy(dags_ctx *ctx) {
   cudaDeviceSynchronize();
   ctx->timer.release();
   if (ctx->graph.exec) cudaGraphExecDestroy(ctx->graph.exec);
+  if (ctx->graph.exec_chunk) cudaGraphExecDestroy(ctx->graph.exec_chunk);
   if (ctx->graph.cap) cudaStreamDestroy(ctx->graph.cap);
   if (ctx->graph_lm.exec) cudaGraphExecDestroy(ctx->graph_lm.exec);
+  if (ctx->graph_lm.exec_chunk) cudaGraphExecDestroy(ctx->graph_lm.exec_chunk);
   if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
   free_lm(ctx->lm);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
@@ -561,27 +566,39 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   TrackGraph &g = ctx->graph;
   if (!g.exec || g.key_len != kl || memcmp(g.key, key, kl) != 0) {
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (g.exec_chunk) { cudaGraphExecDestroy(g.exec_chunk); g.exec_chunk = nullptr; }
     if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return DAGS_E_CUDA;
     // order the capture after the caller's pending work on the workspace
     if (cudaStreamSynchronize(s) != cudaSuccess) return DAGS_E_CUDA;
-    if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
-    rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
-                         grad_pose, g.cap);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
-    if (rc != DAGS_OK || ce != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return rc != DAGS_OK ? rc : DAGS_E_CUDA;
+    // one iteration, and a chunk of kTrackUnroll iterations: inside a chunk
+    // each iteration's first kernel overlaps the previous one's drain
+    // (programmatic dependent launch), which a graph boundary prevents
+    for (int pass = 0; pass < 2; ++pass) {
+      const int reps = pass == 0 ? 1 : kTrackUnroll;
+      if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
+      for (int k = 0; k < reps && rc == DAGS_OK; ++k)
+        rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
+                             grad_pose, g.cap);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
+      if (rc != DAGS_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != DAGS_OK ? rc : DAGS_E_CUDA;
+      }
+      cudaGraphExec_t *dst = pass == 0 ? &g.exec : &g.exec_chunk;
+      const cudaError_t ie = cudaGraphInstantiate(dst, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) { *dst = nullptr; return DAGS_E_CUDA; }
     }
-    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) { g.exec = nullptr; return DAGS_E_CUDA; }
     memcpy(g.key, key, kl < 512 ? kl : 512);
     g.key_len = kl;
   }
   ctx->last_stream = s;
-  for (int k = 0; k < iters; ++k)
+  int left = iters;
+  for (; left >= kTrackUnroll; left -= kTrackUnroll)
+    if (cudaGraphLaunch(g.exec_chunk, s) != cudaSuccess) return DAGS_E_CUDA;
+  for (; left > 0; --left)
     if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return DAGS_E_CUDA;
   return DAGS_OK;
 }
@@ -755,25 +772,35 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   TrackGraph &g = ctx->graph_lm;
   if (!g.exec || g.key_len != kl || memcmp(g.key, key, kl) != 0) {
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    if (g.exec_chunk) { cudaGraphExecDestroy(g.exec_chunk); g.exec_chunk = nullptr; }
     if (!g.cap && cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess) return DAGS_E_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return DAGS_E_CUDA;
-    if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
-    rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, g.cap);
-    cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
-    if (rc != DAGS_OK || ce != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      cudaGetLastError();
-      return rc != DAGS_OK ? rc : DAGS_E_CUDA;
+    // one iteration and a chunk of kTrackUnroll, as for the first-order loop
+    for (int pass = 0; pass < 2; ++pass) {
+      const int reps = pass == 0 ? 1 : kTrackUnroll;
+      if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
+      for (int k = 0; k < reps && rc == DAGS_OK; ++k)
+        rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, g.cap);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
+      if (rc != DAGS_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != DAGS_OK ? rc : DAGS_E_CUDA;
+      }
+      cudaGraphExec_t *dst = pass == 0 ? &g.exec : &g.exec_chunk;
+      const cudaError_t ie = cudaGraphInstantiate(dst, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) { *dst = nullptr; return DAGS_E_CUDA; }
     }
-    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ie != cudaSuccess) { g.exec = nullptr; return DAGS_E_CUDA; }
     memcpy(g.key, key, kl < 512 ? kl : 512);
     g.key_len = kl;
   }
   ctx->last_stream = s;
-  for (int k = 0; k < iters; ++k)
+  int left = iters;
+  for (; left >= kTrackUnroll; left -= kTrackUnroll)
+    if (cudaGraphLaunch(g.exec_chunk, s) != cudaSuccess) return DAGS_E_CUDA;
+  for (; left > 0; --left)
     if (cudaGraphLaunch(g.exec, s) != cudaSuccess) return DAGS_E_CUDA;
   return DAGS_OK;
 }
