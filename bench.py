@@ -250,7 +250,7 @@ OPS_FWD, OPS_BWD = 16, 41
 OPS_JAC = 16 + 10 + 6 * 14
 # DRAM bytes (read + write) per launch at this workload from one ncu capture
 # of the current kernels (profiles/tracking_frame_300k_640x480.md)
-DRAM_TRAFFIC = {"render_fwd": 9212160, "render_bwd": 19869696}
+DRAM_TRAFFIC = {"render_fwd": 9209600, "render_bwd": 19880192}
 ALU_LANES = 152 * 128          # FP32 lanes: 152 SMs x 128
 MPNET_FLOP_PER_PX = 2 * (8 * 32 + 288 * 32 + 32 * 32 + 32)   # 21,056: the network's multiply-adds x 2
 
