@@ -49,6 +49,12 @@ def test_host_only_helpers(lib):
     assert rc.tile == 16 and abs(rc.alpha_min - 1 / 255) < 1e-9 and abs(rc.alpha_max - 0.99) < 1e-7
     lc = dags.default_loss_cfg()
     assert abs(lc.lambda_pho - 0.9) < 1e-7 and abs(lc.lambda_depth - 0.1) < 1e-7   # Sec. V-A(c)
+    sc = dags.default_sched_cfg()
+    assert (sc.w_u, sc.w_r, sc.theta, sc.e_ref, sc.n_max) == (0.5, 0.5, 0.35, 0.05, 10)
+    lm = dags.default_lm_cfg()
+    assert (lm.mu0, lm.delta, lm.down, lm.up) == (1e-2, 0.01, 0.1, 10.0)
+    ec = dags.default_edge_cfg()
+    assert abs(ec.edge_rel - 0.05) < 1e-7 and abs(ec.huber - 0.05) < 1e-7 and ec.literal == 0
     h = ctypes.c_void_p()
     lib.dags_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
                                 ctypes.c_int32, ctypes.c_int64]
