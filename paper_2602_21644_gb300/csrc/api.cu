@@ -617,6 +617,7 @@ int ensure_lm(dags_ctx *ctx) {
   A(alloc(&b.partial, (size_t)ctx->ws.max_tiles * DAGS_LM_NORMAL));
   A(alloc(&b.normal, (size_t)DAGS_LM_NORMAL));
   A(alloc(&b.pose_try, (size_t)12));
+  A(lm_kernel_setup());
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_lm(b);

@@ -132,6 +132,7 @@ struct LmBuffers {
   double *normal = nullptr;   // [28] the loop's normal equations
   double *pose_try = nullptr; // [12] the loop's linearisation point
 };
+cudaError_t lm_kernel_setup();
 cudaError_t launch_pose_tangents(const Workspace &ws, const float4 *gauss, int64_t n, const Raster &r, float4 *tan,
                                  int num_sms, cudaStream_t s);
 // Optional LM step fused into the last CTA of the Jacobian render.

@@ -35,8 +35,8 @@ namespace dags {
 
 namespace {
 
-constexpr int kJacBatch = 128;   // list entries staged in shared memory per round
-static_assert(2 * kJacBatch == kTilePix, "two threads stage each entry");
+constexpr int kJacBatch = kTilePix;   // list entries staged in shared memory per round (one per thread)
+constexpr int kJacTanBytes = kJacBatch * 9 * 16;   // their tangent records (dynamic shared memory)
 constexpr int kTan4 = 9;         // float4 per Gaussian tangent record (36 floats)
 constexpr int kNormal = 28;      // L, the upper triangle of H (21), g (6)
 
@@ -222,7 +222,7 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
   __shared__ float4 s_a[kJacBatch], s_b[kJacBatch], s_c[kJacBatch];
-  __shared__ float4 s_t[kJacBatch * kTan4];
+  extern __shared__ float4 s_t[];   // kJacBatch * kTan4
   __shared__ float s_red[kTilePix / 32][kNormal];
   __shared__ int s_last;
   const unsigned FULL = 0xffffffffu;
@@ -248,25 +248,19 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   for (uint32_t base = s; base < e; base += kJacBatch) {
     if (__syncthreads_count(!done) == 0) break;
     const int cnt = (int)min((uint32_t)kJacBatch, e - base);
-    // entry q is staged by threads q (its record and tangent words 0-3) and
-    // q + kJacBatch (tangent words 4-8)
-    const int q = tid & (kJacBatch - 1);
+    // thread q stages entry q: its record and its tangent record
+    const int q = tid;
     if (q < cnt) {
       const uint32_t k = base + q;
       uint32_t id = own_sort ? (uint32_t)s_key[k - s] : ws.sorted_ids[k];
       if (!DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n, ws.counters + CNT_STATUS)) id = 0;
       const float4 *tg = tan + (size_t)id * kTan4;
       float4 *st = s_t + q * kTan4;
-      if (tid < kJacBatch) {
-        s_a[q] = ws.rec2d[(size_t)id * 3 + 0];
-        s_b[q] = ws.rec2d[(size_t)id * 3 + 1];
-        s_c[q] = ws.rec2d[(size_t)id * 3 + 2];
+      s_a[q] = ws.rec2d[(size_t)id * 3 + 0];
+      s_b[q] = ws.rec2d[(size_t)id * 3 + 1];
+      s_c[q] = ws.rec2d[(size_t)id * 3 + 2];
 #pragma unroll
-        for (int w = 0; w < 4; ++w) st[w] = tg[w];
-      } else {
-#pragma unroll
-        for (int w = 4; w < kTan4; ++w) st[w] = tg[w];
-      }
+      for (int w = 0; w < kTan4; ++w) st[w] = tg[w];
     }
     __syncthreads();
     if (__all_sync(FULL, done)) continue;
@@ -459,10 +453,17 @@ cudaError_t launch_pose_tangents(const Workspace &ws, const float4 *gauss, int64
   return launch_pdl(pose_tangent_kernel, dim3(grid), dim3(kPrepBlock), 0, s, ws, gauss, n, r, tan);
 }
 
+// The Jacobian render's dynamic shared memory (the batch's tangent records)
+// exceeds the default 48 KB: raised once per device, at the ctx's first LM
+// call (before any stream capture).
+cudaError_t lm_kernel_setup() {
+  return cudaFuncSetAttribute(render_jac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kJacTanBytes);
+}
+
 cudaError_t launch_render_jac(const Workspace &ws, const Raster &r, const Loss &l, float delta,
                               const float4 *targets, const float4 *tan, float *partial, double *normal, float *jac,
                               float *image, int32_t *last, const LmFuse &fuse, cudaStream_t s) {
-  return launch_pdl(render_jac_kernel, dim3((unsigned)r.T), dim3(kTilePix), 0, s, ws, r, l, delta, targets, tan,
+  return launch_pdl(render_jac_kernel, dim3((unsigned)r.T), dim3(kTilePix), kJacTanBytes, s, ws, r, l, delta, targets, tan,
                     partial, normal, jac, image, last, fuse);
 }
 

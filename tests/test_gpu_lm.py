@@ -84,6 +84,37 @@ def test_normal_equations_ragged_and_delta(dags, delta):
     compare_normal(sc, normal, J, delta=delta, label=f"ragged delta {delta}")
 
 
+@pytest.mark.parametrize("wmode", [0, 1])
+def test_normal_equations_weight_modes_and_invalid_targets(dags, wmode):
+    # the unnormalised static weight (O - R_MP), 25% invalid depth, 10%
+    # pixels without a valid colour (r < 0: out of both terms)
+    sc = synth.tiny_scene(4, n=1800, width=120, height=88, f=100.0)
+    rng = np.random.default_rng(4)
+    tg = sc.targets.copy()
+    tg[0, rng.random(tg.shape[1]) < 0.25, 3] = 0.0
+    tg[0, rng.random(tg.shape[1]) < 0.10, 0] = -1.0
+    sc = synth.Scene(sc.records, sc.camera, sc.poses, tg)
+    lc = oracle.loss_vec(weight_mode=wmode)
+    sc, _ = mask_flagged_targets(sc, lc=lc)
+    cam = dags.Camera(*sc.camera.as_tuple())
+    gauss, poses, targets = to_dev(sc, torch)
+    ctx = dags.Context(gauss.shape[0], cam.width, cam.height, 1)
+    normal, J = ctx.normal_equations(gauss, cam, poses[0].contiguous(), targets[0].contiguous(), jac=True,
+                                     lcfg=dags.default_loss_cfg(weight_mode=wmode))
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.close()
+    G = oracle.params_from_records(sc.records)
+    ref = oracle.render_jac(G, oracle.camera_vec(*sc.camera.as_tuple()), sc.poses[0], sc.targets[0], lc=lc)
+    Hg, gg = oracle.unpack_normal(normal.cpu().numpy())
+    assert abs(normal[0].item() - ref["L"]) <= L_REL * abs(ref["L"])
+    assert np.linalg.norm(Hg - ref["H"]) <= H_REL * np.linalg.norm(ref["H"])
+    assert np.linalg.norm(gg - ref["g"]) <= G_REL * np.linalg.norm(ref["g"])
+    ok = (ref["flags"] & oracle.PIXEL_DECISION_FLAGS) == 0
+    Jg = J.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(Jg[ok] - ref["J"][ok]) <= JAC_NORM * np.linalg.norm(ref["J"][ok])
+
+
 def test_normal_equations_full_size_tracking_frame(dags):
     sc, masked = mask_flagged_targets(synth.tracking_scene(300_000, frame=10))
     assert masked < 0.01 * sc.targets.shape[1]
