@@ -514,7 +514,7 @@ def gain_section(dags):
     synthetic 60-frame sequence at 320x240 (80k Gaussians, semantic refresh
     every 10 frames), evaluated on a held-out 40-frame one. Means over the
     frames between refreshes: per-pixel MP MAE and IoU(M > 0.5) against the
-    fresh-prior judge, static/dynamic label IoU with the judge's labels and
+    fresh-prior arm, static/dynamic label IoU with the fresh-prior labels and
     with the ground-truth moving Gaussians."""
     import time
     from paper_2602_21644_gb300 import mp_eval

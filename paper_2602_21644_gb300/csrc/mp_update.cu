@@ -151,7 +151,7 @@ __device__ __forceinline__ float pixel_mp(float e, const float4 reg, const float
 }
 
 // The fused per-pixel M_p map, Eqs. (2)-(7) (an output for callers that
-// train or judge a learned proposal against the method).
+// train or evaluate a learned proposal against the method).
 __global__ void __launch_bounds__(kMpBlock)
 mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int P, MpCfg c) {
   __shared__ float4 s_reg[DAGS_MP_MAX_REGIONS];

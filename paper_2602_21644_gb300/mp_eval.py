@@ -4,9 +4,9 @@ the bench).
 Between scheduled semantic invocations (every REFRESH frames) the plain
 update reuses the last instance prior (stale) with its rate scaled by rho,
 Eq. (17). The learned network proposes the per-pixel MP from the frame's
-rendered MP, residuals, depth, opacity and the stale prior. The judge is the
+rendered MP, residuals, depth, opacity and the stale prior. The fresh-prior arm is the
 plain method itself with a fresh prior at every frame. The network is trained
-on the GPU, by the library's own kernels, on the judge's per-pixel maps of a
+on the GPU, by the library's own kernels, on the fresh-prior arm's per-pixel maps of a
 training sequence, then evaluated on a held-out sequence with other
 Gaussians, other noise and other object motions. Both the plain and the
 learned arm also run with the semantic-on-demand trigger of Eqs. (13)-(16)
@@ -67,7 +67,7 @@ class Sequence:
 
 
 class Runner:
-    """One sequence through the library: render, MP update (judge, stale or
+    """One sequence through the library: render, MP update (fresh, stale or
     learned), network features and inference."""
 
     def __init__(self, dags, seq):
@@ -87,7 +87,7 @@ class Runner:
         return image[0].reshape(8, self.P).contiguous()
 
     def fresh_map(self, gauss, pose, tg, image, f):
-        """The judge's per-pixel M_p (fresh prior) at frame f."""
+        """The fresh-prior arm's per-pixel M_p (fresh prior) at frame f."""
         g = gauss.clone()
         lab = torch.zeros(N_GAUSS, dtype=torch.uint8, device="cuda")
         out = torch.empty(self.P, dtype=torch.float32, device="cuda")
@@ -96,7 +96,7 @@ class Runner:
         return out
 
     def run(self, mode, net=None, collect=False, schedule=None):
-        """mode: 'judge' (fresh prior every frame), 'stale' (the method without
+        """mode: 'fresh' (fresh prior every frame), 'stale' (the method without
         the network), 'learned' (network proposal between refreshes).
         Refreshes come every REFRESH frames, or from the semantic-on-demand
         trigger (Eqs. (13)-(16)) when schedule (a dags_sched_cfg) is given."""
@@ -109,7 +109,7 @@ class Runner:
         for f in range(len(self.seq.poses)):
             pose, tg = self.frame_inputs(f)
             image = self.render(gauss, pose)
-            if mode == "judge":
+            if mode == "fresh":
                 refreshed = True
             elif schedule is not None:
                 refreshed = nxt
@@ -144,7 +144,7 @@ class Runner:
 
 
 def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0):
-    """Adam training on the judge's maps of the runner's sequence; returns
+    """Adam training on the fresh-prior maps of the runner's sequence; returns
     (weight blob, per-step losses)."""
     hist = runner.run("stale", collect=True)
     feats = torch.stack([h["feats"] for h in hist])                    # [T, H, W, 8]
@@ -172,14 +172,14 @@ def iou(a, b):
 
 
 def experiment(dags, steps=1000):
-    """Train on one sequence, run judge / stale / learned on the held-out one."""
+    """Train on one sequence, run fresh / stale / learned on the held-out one."""
     train_seq = Sequence(seed=11, velocities=[(0.0, 0.0, 0.3), (-0.3, 0.0, 0.0)], n_frames=60)
     tr = Runner(dags, train_seq)
     net, losses = train_net(dags, tr, steps=steps)
     tr.ctx.close()
     eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=40)
     ev = Runner(dags, eval_seq)
-    out = dict(losses=losses, judge=ev.run("judge"), stale=ev.run("stale"), learned=ev.run("learned", net=net),
+    out = dict(losses=losses, fresh=ev.run("fresh"), stale=ev.run("stale"), learned=ev.run("learned", net=net),
                scheduled=ev.run("stale", schedule=dags.default_sched_cfg()),
                scheduled_learned=ev.run("learned", net=net, schedule=dags.default_sched_cfg()), seq=eval_seq)
     ev.ctx.close()
@@ -188,9 +188,9 @@ def experiment(dags, steps=1000):
 
 def metrics(ex):
     """Means over the held-out frames between refreshes: per-pixel MP against
-    the judge's map (MAE, IoU of M > 0.5) and dynamic-label IoU with the
-    judge's labels and with the ground-truth dynamic Gaussians."""
-    j, s, l = ex["judge"], ex["stale"], ex["learned"]
+    the fresh-prior map (MAE, IoU of M > 0.5) and dynamic-label IoU with the
+    fresh-prior labels and with the ground-truth dynamic Gaussians."""
+    j, s, l = ex["fresh"], ex["stale"], ex["learned"]
     gt = ex["seq"].dynamic
     acc = {k: [] for k in ("mae_s", "mae_l", "iou_s", "iou_l", "agree_s", "agree_l", "gt_j", "gt_s", "gt_l")}
     for f in range(len(j)):
@@ -221,9 +221,9 @@ def metrics(ex):
 def schedule_metrics(ex):
     """The semantic-on-demand trigger against the fixed cadence on the
     held-out sequence: segmentation calls, and over frames 1.. the per-pixel
-    MP MAE against the judge and the label IoU with the judge's labels (the
+    MP MAE against the fresh-prior arm and the label IoU with the fresh-prior labels (the
     learned proposal's map where it stands in for M_p)."""
-    j = ex["judge"]
+    j = ex["fresh"]
     out = {}
     for name in ("stale", "scheduled", "learned", "scheduled_learned"):
         h = ex[name]

@@ -1,6 +1,6 @@
 """What the learned MP proposal gains over the method without it: the
 experiment of paper_2602_21644_gb300.mp_eval (train on one synthetic
-sequence, evaluate judge / stale prior / learned proposal on a held-out one)
+sequence, evaluate fresh prior / stale prior / learned proposal on a held-out one)
 and its assertions."""
 import numpy as np
 import pytest
@@ -38,7 +38,7 @@ def test_scheduled_refreshes(experiment):
     from paper_2602_21644_gb300 import mp_eval
     sm = mp_eval.schedule_metrics(experiment)
     print("\n" + repr(sm))
-    T = len(experiment["judge"])
+    T = len(experiment["fresh"])
     for name in ("scheduled", "scheduled_learned"):
         h = experiment[name]
         ref = [f for f, r in enumerate(h) if r["refreshed"]]
@@ -51,14 +51,14 @@ def test_training_converges(result):
     assert result["loss_last"] < 0.9 * result["loss_first"], result
 
 
-def test_learned_map_closer_to_judge_than_stale_prior(result):
-    # per-pixel MP between refreshes against the judge's fresh-prior map
+def test_learned_map_closer_to_fresh_prior_than_stale_prior(result):
+    # per-pixel MP between refreshes against the fresh-prior arm's fresh-prior map
     assert result["mae_l"] < result["mae_s"], result
     assert result["iou_l"] > result["iou_s"], result
 
 
 def test_label_agreement_does_not_drop(result):
-    # static/dynamic labels of the Gaussians: agreement with the judge's
+    # static/dynamic labels of the Gaussians: agreement with the fresh-prior arm's
     # labels between refreshes. The labels integrate the map over frames
     # through Eq. (9) and the median threshold, so the per-pixel gain shows
     # only weakly here: it must not lose agreement (training is not
