@@ -25,7 +25,7 @@ import torch
 
 from . import synth
 
-W, H, F = 320, 240, 262.5
+W, H = 320, 240
 N_GAUSS = 80_000
 REFRESH = 10
 TABLE = np.array([[0.1, 0.05], [0.9, 0.8], [0.9, 0.8]], np.float32)
@@ -42,13 +42,15 @@ class Sequence:
     """Frames of the room with moving objects: observed RGB-D and noisy
     instance masks (label k for the k-th moving object)."""
 
-    def __init__(self, seed, velocities, n_frames):
+    def __init__(self, seed, velocities, n_frames, width=W, height=H, n_gauss=N_GAUSS):
+        self.width, self.height, self.n = width, height, n_gauss
         self.objs = objects(velocities)
-        self.rec, self.oid, _ = synth.room_scene(N_GAUSS, seed, objects=self.objs)
+        self.rec, self.oid, _ = synth.room_scene(n_gauss, seed, objects=self.objs)
         self.rec[:, 11] = 0.2                      # uninformed initial MP
         moving = [k for k, ob in enumerate(self.objs) if np.any(ob.velocity != 0)]
         self.dynamic = np.isin(self.oid, moving)
-        self.cam = synth.Camera(F, F, W / 2.0, H / 2.0, W, H)
+        f = 525.0 * width / 640.0                  # the 640x480 rig's field of view
+        self.cam = synth.Camera(f, f, width / 2.0, height / 2.0, width, height)
         self.poses = synth.camera_path(n_frames)
         rng = np.random.default_rng(seed + 100)
         self.obs, self.inst = [], []
@@ -73,9 +75,9 @@ class Runner:
     def __init__(self, dags, seq):
         self.d, self.seq = dags, seq
         self.cam = dags.Camera(*seq.cam.as_tuple())
-        self.ctx = dags.Context(N_GAUSS, W, H, 1)
+        self.ctx = dags.Context(seq.n, seq.width, seq.height, 1)
         self.table = torch.from_numpy(TABLE).cuda()
-        self.P = W * H
+        self.P = seq.width * seq.height
 
     def frame_inputs(self, f):
         pose = torch.from_numpy(np.ascontiguousarray(self.seq.poses[f])[None]).cuda()
@@ -89,7 +91,7 @@ class Runner:
     def fresh_map(self, gauss, pose, tg, image, f):
         """The fresh-prior arm's per-pixel M_p (fresh prior) at frame f."""
         g = gauss.clone()
-        lab = torch.zeros(N_GAUSS, dtype=torch.uint8, device="cuda")
+        lab = torch.zeros(self.seq.n, dtype=torch.uint8, device="cuda")
         out = torch.empty(self.P, dtype=torch.float32, device="cuda")
         inst = torch.from_numpy(self.seq.inst[f]).cuda()
         self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out)
@@ -101,7 +103,7 @@ class Runner:
         Refreshes come every REFRESH frames, or from the semantic-on-demand
         trigger (Eqs. (13)-(16)) when schedule (a dags_sched_cfg) is given."""
         gauss = torch.from_numpy(self.seq.rec.copy()).cuda()
-        labels = torch.zeros(N_GAUSS, dtype=torch.uint8, device="cuda")
+        labels = torch.zeros(self.seq.n, dtype=torch.uint8, device="cuda")
         state = torch.zeros(2, dtype=torch.int32, device="cuda")
         score = torch.zeros(3, dtype=torch.float64, device="cuda")
         hist = []
@@ -148,7 +150,14 @@ def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0):
     (weight blob, per-step losses)."""
     hist = runner.run("stale", collect=True)
     feats = torch.stack([h["feats"] for h in hist])                    # [T, H, W, 8]
-    target = torch.stack([h["target"].reshape(H, W) for h in hist])    # [T, H, W]
+    target = torch.stack([h["target"].reshape(runner.seq.height, runner.seq.width) for h in hist])
+    return train_on(runner.ctx, feats, target, steps, lr, batch, seed)
+
+
+def train_on(ctx, feats, target, steps=1000, lr=2e-3, batch=16, seed=0):
+    """Adam training of a seeded network on (feats [T, H, W, 8] bf16, target
+    [T, H, W] f32), batches of `batch` frames drawn without replacement per
+    step; returns (weight blob, per-step losses)."""
     blob, vec = synth.mpnet_init(seed)
     net = torch.from_numpy(blob).cuda()
     master = torch.from_numpy(vec).cuda()
@@ -160,9 +169,9 @@ def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0):
         idx = torch.randperm(feats.shape[0], generator=gen)[:batch].cuda()
         fb = feats.index_select(0, idx).contiguous()
         tb = target.index_select(0, idx).contiguous()
-        losses.append(runner.ctx.mpnet_train_step(net, master, m, v, step, fb, tb, lr))
+        losses.append(ctx.mpnet_train_step(net, master, m, v, step, fb, tb, lr))
     torch.cuda.synchronize()
-    runner.ctx.check()
+    ctx.check()
     return net, [l.item() for l in losses]
 
 
@@ -237,4 +246,124 @@ def schedule_metrics(ex):
                      "label_iou_vs_fresh_prior": float(np.mean(agree))}
         if "score" in h[0]:
             out[name]["mean_S"] = float(np.mean([r["score"][2].item() for r in h]))
+    return out
+
+
+def rendered_training_set(dags, n_frames=10_000, n_gauss=200_000, width=640, height=480, seed=0, flip=0.05,
+                          max_stale=9, fps=30.0):
+    """Training frames the plain method generates on the mapping room (200k
+    Gaussians, 640x480), with the observations rendered by the library
+    instead of ray-cast (ray-casting 10k frames on the host would take hours).
+
+    Per frame, seeded: a viewpoint inside the room looking across it; an
+    object time t (the two moving objects displaced by v t) and a stale time
+    t - k / fps, k in 1..max_stale (the prior of the last refresh);
+      observation  the render of the displaced scene, colour + N(0, 0.01),
+                   depth x (1 + N(0, 0.01)) where opacity > 0.5 and depth in
+                   0.5-5 m (else invalid)
+      instance maps renders whose MP channel carries the object label (fresh
+                   at t, stale at t - k / fps), `flip` pixel flips
+      map render   the map as the tracker holds it (objects at their t = 0
+                   positions) with per-frame MP words (0.2 plus a random
+                   separation of the moving objects' Gaussians)
+      target       the plain method's fused M_p with the fresh prior
+                   (mp_update's per-pixel output)
+      features     mpnet_features with the stale prior.
+    Returns (feats [T, H, W, 8] bf16, target [T, H, W] f32), on the device."""
+    rec, oid, objs = synth.room_scene(n_gauss, seed)
+    cam_s = synth.room_camera(width, height)
+    cam = dags.Camera(*cam_s.as_tuple())
+    P = width * height
+    moving = [k for k, ob in enumerate(objs) if np.any(ob.velocity != 0)]
+    L = len(moving)
+    dev = "cuda"
+    base = torch.from_numpy(rec).to(dev)
+    idx = [torch.from_numpy(np.nonzero(oid == k)[0]).to(dev) for k in moving]
+    vel = [torch.tensor(objs[k].velocity, dtype=torch.float32, device=dev) for k in moving]
+    dyn = torch.from_numpy(np.isin(oid, moving)).to(dev)
+    table = torch.from_numpy(np.array([[0.1, 0.05]] + [[0.9, 0.8]] * L, np.float32)).to(dev)
+    ctx = dags.Context(n_gauss, width, height, 1)
+    feats = torch.empty((n_frames, height, width, 8), dtype=torch.bfloat16, device=dev)
+    target = torch.empty((n_frames, height, width), dtype=torch.float32, device=dev)
+    work = base.clone()
+    labels = torch.zeros(n_gauss, dtype=torch.uint8, device=dev)
+    rng = np.random.default_rng(seed + 4242)
+    gen = torch.Generator(device=dev).manual_seed(seed + 4243)
+
+    def displaced(t, label_mp):
+        work.copy_(base)
+        if label_mp:
+            work[:, 11] = 0.0
+        for j in range(L):
+            work[idx[j], 0:3] += vel[j] * t
+            if label_mp:
+                work[idx[j], 11] = (j + 1) / L
+        return work
+
+    def instance(t):
+        im, _, _ = ctx.forward(displaced(t, True), cam, pose_d[None], want_loss=False)
+        o = im[0, 4].reshape(P)
+        lab = torch.where(o > 0.5, torch.round(im[0, 5].reshape(P) / o.clamp_min(1e-6) * L), torch.zeros_like(o))
+        lab = lab.clamp(0, L).to(torch.uint8)
+        fl = torch.rand(P, generator=gen, device=dev) < flip
+        repl = torch.randint(0, L + 1, (P,), generator=gen, device=dev, dtype=torch.uint8)
+        repl = torch.where(repl == lab, (repl + 1) % (L + 1), repl)
+        return torch.where(fl, repl, lab).contiguous()
+
+    for f in range(n_frames):
+        a = rng.uniform(0, 2 * np.pi)
+        r = rng.uniform(1.0, 1.8)
+        eye = np.array([r * np.cos(a), rng.uniform(-0.5, 0.1), r * np.sin(a)])
+        b = a + rng.uniform(-0.6, 0.6)
+        look = np.array([-0.6 * np.cos(b), rng.uniform(0.2, 0.6), -0.6 * np.sin(b)])
+        pose_d = torch.from_numpy(synth.look_at_pose(eye, look)).to(dev)
+        t = rng.uniform(0.2, 3.0)
+        t_stale = t - rng.integers(1, max_stale + 1) / fps
+        # observation of the displaced scene
+        im, _, _ = ctx.forward(displaced(t, False), cam, pose_d[None], want_loss=False)
+        c = im[0, 0:3].reshape(3, P).t()
+        d = im[0, 3].reshape(P)
+        o = im[0, 4].reshape(P)
+        tg = torch.empty((P, 4), dtype=torch.float32, device=dev)
+        tg[:, 0:3] = (c + 0.01 * torch.randn((P, 3), generator=gen, device=dev)).clamp(0, 1)
+        dn = d * (1 + 0.01 * torch.randn(P, generator=gen, device=dev))
+        tg[:, 3] = torch.where((o > 0.5) & (dn > 0.5) & (dn < 5.0), dn, torch.zeros_like(dn))
+        inst_fresh = instance(t)
+        inst_stale = instance(t_stale)
+        # the map as tracked, its MP words, its render
+        work.copy_(base)
+        sep = float(rng.uniform(0.0, 0.7))
+        work[:, 11] = (0.2 + sep * dyn.float() + 0.1 * torch.randn(n_gauss, generator=gen, device=dev)).clamp(0, 1)
+        image, _, _ = ctx.forward(work, cam, pose_d[None], want_loss=False)
+        img = image[0].reshape(dags.IMG_CHANNELS, P)
+        ctx.mpnet_features(img, tg, inst_stale, table, cam, out=feats[f])
+        ctx.mp_update(work, cam, pose_d[None], tg, img, inst_fresh, table, labels, mp_pixel=target[f].reshape(P))
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.close()
+    return feats, target
+
+
+def experiment_rendered(dags, n_frames=10_000, steps=3000, lr=2e-3, batch=16, width=640, height=480,
+                        eval_frames=40):
+    """Train on `n_frames` rendered training frames (rendered_training_set),
+    then run fresh / stale / learned on a held-out ray-cast sequence at the
+    same resolution (other Gaussians, other object motions)."""
+    import time
+    t0 = time.perf_counter()
+    feats, target = rendered_training_set(dags, n_frames, width=width, height=height)
+    t_gen = time.perf_counter() - t0
+    tctx = dags.Context(16, width, height, 1)
+    t0 = time.perf_counter()
+    net, losses = train_on(tctx, feats, target, steps, lr, batch)
+    t_train = time.perf_counter() - t0
+    tctx.close()
+    del feats, target
+    torch.cuda.empty_cache()
+    eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=eval_frames,
+                        width=width, height=height, n_gauss=200_000)
+    ev = Runner(dags, eval_seq)
+    out = dict(losses=losses, fresh=ev.run("fresh"), stale=ev.run("stale"), learned=ev.run("learned", net=net),
+               seq=eval_seq, t_gen=t_gen, t_train=t_train)
+    ev.ctx.close()
     return out
