@@ -64,7 +64,8 @@ enum {
   DAGS_E_TIMEOUT = -4,   /* a bounded device wait gave up                     */
   DAGS_E_NOMEM = -5,     /* workspace allocation failed                       */
   DAGS_E_ORDER = -6,     /* splat_backward without its matching splat_forward */
-  DAGS_E_BOUNDS = -7     /* a DAGS_CHECK build found an index out of range    */
+  DAGS_E_BOUNDS = -7     /* an index out of range: a DAGS_CHECK build's check, or an
+                            epipolar_verify match id; the access was skipped */
 };
 
 typedef struct dags_ctx dags_ctx;
