@@ -68,11 +68,11 @@ def test_label_agreement_does_not_drop(result):
 
 
 def test_training_on_rendered_frames_generalises(dags):
-    # 1,000 frames the plain method generates on the mapping room at 640x480
+    # 2,000 frames the plain method generates on the mapping room at 640x480
     # (observations rendered by the library), then the held-out ray-cast
     # sequence at 640x480: the learned map beats the stale prior
     from paper_2602_21644_gb300 import mp_eval
-    ex = mp_eval.experiment_rendered(dags, n_frames=1000, steps=1500, eval_frames=30)
+    ex = mp_eval.experiment_rendered(dags, n_frames=2000, steps=2500, eval_frames=30)
     m = mp_eval.metrics(ex)
     print("\n" + ", ".join(f"{k} {v:.4f}" for k, v in m.items()))
     assert m["loss_last"] < 0.9 * m["loss_first"], m
