@@ -95,12 +95,27 @@ mp_pixel_sum_kernel(MpWs m, const float4 *__restrict__ targets, const float *__r
     m.sel[3] = 0u;            // CTA counter
   }
   __syncthreads();
+  float e = 0.f;
+  int k = -1;
   if (p < P) {
-    const float e = residual(targets[p], image, (size_t)P, (size_t)p, c.kappa_c);
+    e = residual(targets[p], image, (size_t)P, (size_t)p, c.kappa_c);
     m.e[p] = e;
-    const int k = region_of(inst, p, c.n_regions, m.status);
-    atomicAdd(&s_cnt[k], 1.f);
-    atomicAdd(&s_sum[k], e);
+    k = region_of(inst, p, c.n_regions, m.status);
+  }
+  // most pixels of a warp share a region: sum per region over the warp
+  // first, then one shared atomic per region per warp
+  unsigned pending = __ballot_sync(0xffffffffu, k >= 0);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int key = __shfl_sync(0xffffffffu, k, leader);
+    const bool mine = k == key;
+    const unsigned grp = __ballot_sync(0xffffffffu, mine);
+    const float sum = warp_sum(mine ? e : 0.f);
+    if ((int)(threadIdx.x & 31) == leader) {
+      atomicAdd(&s_cnt[key], (float)__popc(grp));
+      atomicAdd(&s_sum[key], sum);
+    }
+    pending &= ~grp;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x)
@@ -120,10 +135,23 @@ mp_pixel_var_kernel(MpWs m, const uint8_t *__restrict__ inst, int P, MpCfg c) {
   }
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  float sq = 0.f;
+  int k = -1;
   if (p < P) {
-    const int k = region_of(inst, p, c.n_regions, m.status);
+    k = region_of(inst, p, c.n_regions, m.status);
     const float d = m.e[p] - s_mean[k];
-    atomicAdd(&s_sq[k], d * d);
+    sq = d * d;
+  }
+  // per-region sums over the warp first, as in the pixel-sum pass
+  unsigned pending = __ballot_sync(0xffffffffu, k >= 0);
+  while (pending) {
+    const int leader = __ffs(pending) - 1;
+    const int key = __shfl_sync(0xffffffffu, k, leader);
+    const bool mine = k == key;
+    const unsigned grp = __ballot_sync(0xffffffffu, mine);
+    const float sum = warp_sum(mine ? sq : 0.f);
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&s_sq[key], sum);
+    pending &= ~grp;
   }
   __syncthreads();
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x)
