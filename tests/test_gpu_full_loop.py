@@ -1,6 +1,7 @@
 """The full loop at scale (1M Gaussians, 1200x680 RGB-D, three moving
 ellipsoids, spline camera): full-image parity of one frame's forward and
-adjoint against the FP64 oracle, and the loop itself through the C ABI for a
+adjoint against the FP64 oracle; the LM normal equations, lambda_3 L_MP and
+the edge warp at the same scale; and the loop itself through the C ABI for a
 dozen frames. Per frame: tracking (LM), the MP update, semantic refreshes
 every 10 frames with the learned proposal in between, the trigger's score.
 Every 5th frame: mapping over a window of up to 8 keyframes, the MP-weighted
@@ -143,3 +144,50 @@ def test_full_loop_runs_at_scale(dags, sequence):
     assert max(errors) < 0.2
     tctx.close()
     mctx.close()
+
+
+def test_full_scale_normal_equations_and_regularisers(dags, sequence):
+    # the next rows at the loop's scale: LM normal equations of frame 10 from
+    # frame 9's pose, lambda_3 L_MP over 1M Gaussians, the edge warp 9 -> 10
+    from oracle import edge as oedge
+    from oracle import regular as oreg
+    rec, scam, seq, _ = sequence
+    sc = synth.Scene(rec, scam, seq[9]["gt_pose"][None], seq[10]["target"][None].astype(np.float32))
+    sc, _ = mask_flagged_targets(sc)
+    cam = dags.Camera(*scam.as_tuple())
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    ctx = dags.Context(rec.shape[0], cam.width, cam.height, 1)
+    normal, _ = ctx.normal_equations(t(rec), cam, t(sc.poses[0]), t(sc.targets[0]))
+    rng = np.random.default_rng(5)
+    prev = rec.copy()
+    prev[:, 0:3] += rng.normal(0, 0.005, (rec.shape[0], 3)).astype(np.float32)
+    grad = torch.zeros((rec.shape[0], 16), dtype=torch.float32, device="cuda")
+    lmp = ctx.mp_consistency(t(rec), t(prev), 500.0, grad=grad)
+    Di, Dj = seq[9]["target"][:, 3].copy(), seq[10]["target"][:, 3].copy()
+    yy, xx = np.mgrid[0:cam.height, 0:cam.width]
+    wj = (0.6 + 0.3 * np.cos(0.02 * xx) * np.sin(0.03 * yy)).astype(np.float32).ravel()
+    eo = ctx.edge_warp(cam, t(Di), t(Dj), t(wj), t(seq[9]["gt_pose"].ravel()), t(seq[10]["gt_pose"].ravel()), 300.0)
+    torch.cuda.synchronize()
+    ctx.check()
+    ctx.close()
+    G = oracle.params_from_records(rec)
+    ref = oracle.render_jac(G, oracle.camera_vec(*scam.as_tuple()), sc.poses[0], sc.targets[0])
+    Hg, gg = oracle.unpack_normal(normal.cpu().numpy())
+    eL = abs(normal[0].item() - ref["L"]) / abs(ref["L"])
+    eH = np.linalg.norm(Hg - ref["H"]) / np.linalg.norm(ref["H"])
+    eg = np.linalg.norm(gg - ref["g"]) / np.linalg.norm(ref["g"])
+    L_ref, g_ref = oreg.mp_consistency(rec[:, 0:3], rec[:, 11], prev[:, 0:3], 500.0)
+    e_ref = oedge.edge_warp(scam.as_tuple(), Di, Dj, wj, seq[9]["gt_pose"], seq[10]["gt_pose"])
+    eo = eo.cpu().numpy()
+    print(f"\nnormal equations: L {eL:.2e} H {eH:.2e} g {eg:.2e}; L_MP {abs(lmp.item() - L_ref) / L_ref:.2e}; "
+          f"edge: {e_ref['n']} pixels, L {abs(eo[0] - e_ref['L']) / e_ref['L']:.2e}")
+    # the normal equations' sums run over 4x the pixels and 3x the Gaussians
+    # of the 300k frame: the bound on g scales as for the twist gradient
+    scale = np.sqrt((cam.width * cam.height * rec.shape[0]) / (640 * 480 * 300_000))
+    assert eL <= 1e-5 and eH <= 1e-3 * scale and eg <= 1e-3 * scale
+    assert abs(lmp.item() - L_ref) <= 1e-5 * L_ref
+    gm = grad.cpu().numpy()[:, 0:3].astype(np.float64)
+    assert np.linalg.norm(gm - g_ref) <= 1e-5 * np.linalg.norm(g_ref)
+    assert abs(eo[0] - e_ref["L"]) <= 2e-4 * e_ref["L"]
+    assert np.linalg.norm(eo[1:7] - e_ref["grad_i"]) <= 2e-3 * np.linalg.norm(e_ref["grad_i"])
+    assert np.linalg.norm(eo[7:13] - e_ref["grad_j"]) <= 2e-3 * np.linalg.norm(e_ref["grad_j"])
