@@ -8,8 +8,9 @@
 //
 // One thread per Gaussian, HBM-bound (the first and third float4 of the
 // record, the first of the previous record, a read-modify-write of the first
-// float4 of the gradient). The loss is summed per CTA in FP64 by a fixed tree
-// and across CTAs in a fixed order by the last CTA.
+// float4 of the gradient). The loss is summed per warp in FP32 (fixed
+// shuffle order), across a CTA's warps in FP64 by one thread, and across CTAs
+// in a fixed order by the last CTA.
 //
 // MP-guided edge-warp regulariser (Sec. IV-D, Eqs. (25), (26)): one thread
 // per pixel u of frame i. An edge pixel (a valid 4-neighbour differs by more
@@ -18,8 +19,9 @@
 // j; D_j and w^j are sampled bilinearly at u', r = w^j (D_j - z_ref) enters
 // the Huber kernel, and the gradients with respect to both poses' left
 // twists follow by the chain rule through the bilinear cell, the projection
-// and the rigid motion. Per-CTA sums in FP64 in a fixed order, combined by the
-// last CTA in a fixed order.
+// and the rigid motion. The 13 sums go per CTA in FP32 (warp shuffles, then
+// the CTA's 8 warps in order), and across CTAs in FP64 in a fixed order by
+// the last CTA.
 #include "common.cuh"
 
 namespace dags {
