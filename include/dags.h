@@ -374,8 +374,9 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
  * lambda     the weight (the paper's lambda_3 = 500)
  * grad_gauss device, n x 16 floats, or NULL: d(lambda L_MP)/d mu is ADDED to
  *            words 0-2 (the splat_backward layout), other words untouched
- * loss       device, 1 double, or NULL: lambda L_MP, summed in FP64 in a
- *            fixed order (deterministic)
+ * loss       device, 1 double, or NULL: lambda L_MP, summed in a fixed
+ *            order (FP32 within a warp, FP64 across warps and CTAs;
+ *            deterministic)
  * The first call on a ctx allocates a small buffer (before any stream
  * capture). */
 int splat_mp_consistency(dags_ctx *ctx, const float *gauss, int64_t n, const float *prev, const double *rel_pose,
@@ -407,7 +408,8 @@ void dags_default_edge_cfg(dags_edge_cfg *cfg);
  * pose_i, pose_j     device, 12 doubles each (world -> camera)
  * out                device, 13 doubles: lambda L_edge, then its gradient
  *                    with respect to the left twist of pose_i (6) and of
- *                    pose_j (6); FP64 sums in a fixed order (deterministic)
+ *                    pose_j (6); sums in a fixed order (FP32 within a
+ *                    CTA, FP64 across CTAs; deterministic)
  * The first call on a ctx allocates a small buffer (before any stream
  * capture). */
 int splat_edge_warp(dags_ctx *ctx, const dags_camera *cam, const float *depth_i, const float *depth_j,
