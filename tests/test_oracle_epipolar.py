@@ -72,6 +72,19 @@ def test_sliding_along_the_epipolar_line_keeps_zero():
     assert E.distances(E.fundamental(CAM, T1, T2), p1, p2).max() < 1e-9
 
 
+def test_rectified_stereo_lines_are_rows():
+    # textbook special case: same intrinsics, R = I, a baseline along x.
+    # The epipolar line of (u1, v1) is the row v = v1, so d = |v2 - v1| for
+    # any u1, u2, whatever fx != fy and the principal point
+    T1 = np.hstack([np.eye(3), [[0.0], [0.0], [0.0]]])
+    T2 = np.hstack([np.eye(3), [[-0.12], [0.0], [0.0]]])
+    rng = np.random.default_rng(7)
+    p1 = rng.uniform([0, 0], [320, 240], (40, 2))
+    p2 = rng.uniform([0, 0], [320, 240], (40, 2))
+    d = E.distances(E.fundamental(CAM, T1, T2), p1, p2)
+    np.testing.assert_allclose(d, np.abs(p2[:, 1] - p1[:, 1]), rtol=1e-12, atol=1e-10)
+
+
 def test_median_and_recovery_rule():
     T1, T2 = poses()
     rng = np.random.default_rng(3)
