@@ -248,9 +248,10 @@ OPS_FWD, OPS_BWD = 16, 41
 # (the exponent's tangent 5, alpha' 1, the weight's tangent 2, four channel
 # accumulations 5, T' 1) over six directions
 OPS_JAC = 16 + 10 + 6 * 14
-# DRAM bytes (read + write) per launch at this workload from one ncu capture
-# of the current kernels (profiles/tracking_frame_300k_640x480.md)
-DRAM_TRAFFIC = {"render_fwd": 9209600, "render_bwd": 19880192}
+# DRAM bytes (read + write) per launch at this workload, from one ncu capture
+# of each kernel; None where the kernel has changed since its capture
+# (render_bwd: 19,880,192 bytes before its 6- and 10-value reduce-scatter)
+DRAM_TRAFFIC = {"render_fwd": 9209600, "render_bwd": None}
 ALU_LANES = 152 * 128          # FP32 lanes: 152 SMs x 128
 MPNET_FLOP_PER_PX = 2 * (8 * 32 + 288 * 32 + 32 * 32 + 32)   # 21,056: the network's multiply-adds x 2
 

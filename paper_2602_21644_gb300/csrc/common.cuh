@@ -391,37 +391,55 @@ __device__ __forceinline__ bool ellipse_reaches_rect(float u, float v, float A2,
   return best <= thr;
 }
 
-// Reduce-scatter of 8 values over the 32 lanes of a warp: 4 + 2 + 1 + 1 + 1
-// shuffles instead of 8 x 5. On return, lane l holds in x the full warp sum
-// of component ((l >> 4) & 1) * 4 + ((l >> 3) & 1) * 2 + ((l >> 2) & 1)
-// (lanes differing only in bits 0-1 hold the same sum).
-__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
-  const unsigned F = 0xffffffffu;
-  const bool h16 = (lane & 16) != 0;
-  float a[4];
+// Reduce-scatter of K values over the 32 lanes of a warp. Each of the five
+// xor levels (16, 8, 4, 2, 1) halves the lane's list: the lane keeps one half
+// and adds its partner's copy of that half; an odd last entry is summed whole
+// and stays with both partners. On return every lane holds the full warp sum
+// of one component, rs_component<K>(lane). Shuffles: 8 for K = 6, 9 for
+// K = 8, 12 for K = 10 (against 5 K for separate warp sums).
+template <int K, int M = 16>
+__device__ __forceinline__ float warp_reduce_scatter(const float (&cur)[K], int lane) {
+  constexpr int P = K / 2, K2 = P + (K & 1);
+  static_assert(M > 1 || K2 == 1, "at most 32 components");
+  const bool hi = (lane & M) != 0;
+  float nxt[K2];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float keep = h16 ? v[i + 4] : v[i];
-    const float send = h16 ? v[i] : v[i + 4];
-    a[i] = keep + __shfl_xor_sync(F, send, 16);
+  for (int i = 0; i < P; ++i) {
+    const float keep = hi ? cur[i + P] : cur[i];
+    const float send = hi ? cur[i] : cur[i + P];
+    nxt[i] = keep + __shfl_xor_sync(0xffffffffu, send, M);
   }
-  const bool h8 = (lane & 8) != 0;
-  float b[2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const float keep = h8 ? a[i + 2] : a[i];
-    const float send = h8 ? a[i] : a[i + 2];
-    b[i] = keep + __shfl_xor_sync(F, send, 8);
+  if constexpr ((K & 1) != 0) nxt[P] = cur[K - 1] + __shfl_xor_sync(0xffffffffu, cur[K - 1], M);
+  if constexpr (M == 1) {
+    return nxt[0];
+  } else {
+    return warp_reduce_scatter<K2, M / 2>(nxt, lane);
   }
-  const bool h4 = (lane & 4) != 0;
-  float c = (h4 ? b[1] : b[0]) + __shfl_xor_sync(F, h4 ? b[0] : b[1], 4);
-  c += __shfl_xor_sync(F, c, 2);
-  c += __shfl_xor_sync(F, c, 1);
-  return c;
 }
 
-__device__ __forceinline__ int scatter8_component(int lane) {
-  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+// The component whose sum warp_reduce_scatter<K> leaves in lane `lane`: the
+// same selections applied to the component indices.
+template <int K, int M = 16>
+__device__ __forceinline__ int rs_component_of(const int (&cur)[K], int lane) {
+  constexpr int P = K / 2, K2 = P + (K & 1);
+  const bool hi = (lane & M) != 0;
+  int nxt[K2];
+#pragma unroll
+  for (int i = 0; i < P; ++i) nxt[i] = hi ? cur[i + P] : cur[i];
+  if constexpr ((K & 1) != 0) nxt[P] = cur[K - 1];
+  if constexpr (M == 1) {
+    return nxt[0];
+  } else {
+    return rs_component_of<K2, M / 2>(nxt, lane);
+  }
+}
+
+template <int K>
+__device__ __forceinline__ int rs_component(int lane) {
+  int ids[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) ids[i] = i;
+  return rs_component_of<K>(ids, lane);
 }
 
 // FP64 Adam step on the twist of one pose followed by T <- exp(xi^) T, with

@@ -23,6 +23,8 @@ namespace dags {
 namespace {
 
 constexpr int kMaxViewsSmem = 64;
+// the reduce-scatter's component k is 2D-gradient word k
+static_assert(G2_U == 0 && G2_Z == 5 && G2_BL == 9 && kGradWords >= 10, "2D-gradient word order");
 
 template <bool FULL>
 __global__ void __launch_bounds__(kTilePix)
@@ -36,6 +38,11 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   const uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
   if (tot > (uint64_t)ws.max_pairs) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // the 2D-gradient word whose warp sum this lane receives from the
+  // reduce-scatter below (words G2_U .. G2_Z, and with FULL up to G2_BL), and
+  // whether it is the lowest lane holding that word (the one that adds it)
+  const int comp = FULL ? rs_component<10>(lane) : rs_component<6>(lane);
+  const bool writer = __ffs(__match_any_sync(0xffffffffu, (unsigned)comp)) - 1 == lane;
   const int tile = (int)ws.tile_order[blockIdx.x];   // longest lists first
   const int v = tile / r.T, tv = tile - v * r.T;
   const int tx = tv % r.tiles_x, ty = tv / r.tiles_x;
@@ -155,18 +162,18 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
           }
         }
         if (__any_sync(FULLM, contrib)) {
-          // reduce-scatter over the warp; lanes 0, 4, ..., 28 then hold one
-          // component's sum each and add it with one atomic
-          float* dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
-          const int comp = scatter8_component(lane);
-          const float v8[8] = {gu, gv, ga, gb, gc, gz, go, gr};
-          const float sum8 = warp_reduce_scatter8(v8, lane);
-          if ((lane & 3) == 0 && (FULL || comp < 6)) atomicAdd(dst + comp, sum8);
-          if (FULL) {
-            const float w8[8] = {gg, gbl, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const float sum2 = warp_reduce_scatter8(w8, lane);
-            if ((lane & 3) == 0 && comp < 2) atomicAdd(dst + G2_G + comp, sum2);
+          // reduce-scatter over the warp: every lane then holds the warp sum
+          // of word `comp`, and one lane per word adds it with one atomic
+          float *dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
+          float sum;
+          if constexpr (FULL) {
+            const float v10[10] = {gu, gv, ga, gb, gc, gz, go, gr, gg, gbl};
+            sum = warp_reduce_scatter<10>(v10, lane);
+          } else {
+            const float v6[6] = {gu, gv, ga, gb, gc, gz};
+            sum = warp_reduce_scatter<6>(v6, lane);
           }
+          if (writer) atomicAdd(dst + comp, sum);
         }
       }
     }
