@@ -1,7 +1,6 @@
 """Pins of the FP64 MP-update oracle: special cases that reduce each step of
 Sec. IV-A to a closed form (no GPU)."""
 import numpy as np
-import pytest
 
 from oracle import mp as M
 from paper_2602_21644_gb300 import synth
