@@ -66,3 +66,33 @@ def test_host_only_helpers(lib):
 def test_oracle_builds_with_gcc():
     import oracle
     assert os.path.exists(oracle.build())
+
+
+def _zero_args(fn):
+    args = []
+    for t in fn.argtypes:
+        if t in (ctypes.c_float, ctypes.c_double):
+            args.append(0.0)
+        elif t in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_uint64):
+            args.append(0)
+        else:
+            args.append(None)          # pointers, structs by pointer, streams
+    return args
+
+
+def test_entry_points_reject_a_null_context():
+    # every call that takes a dags_ctx checks its arguments on the host before
+    # any CUDA call: a NULL context is DAGS_E_INVAL (-1), with nothing launched
+    from paper_2602_21644_gb300 import dags
+    lib = dags.load()
+    host_only = {"dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "splat_forward_static"}
+    checked = []
+    for name in dags.EXPORTS:
+        if name in host_only or name.startswith("dags_default_"):
+            continue
+        fn = getattr(lib, name)
+        assert fn.argtypes and fn.argtypes[0] is ctypes.c_void_p, name
+        assert fn(*_zero_args(fn)) == -1, name
+        checked.append(name)
+    assert len(checked) >= 20
+    lib.dags_destroy(None)             # destroying NULL is a no-op
