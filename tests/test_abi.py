@@ -96,3 +96,22 @@ def test_entry_points_reject_a_null_context():
         checked.append(name)
     assert len(checked) >= 20
     lib.dags_destroy(None)             # destroying NULL is a no-op
+
+
+def test_static_forward_limits_are_checked_on_the_host():
+    # splat_forward_static's workspace limits (n <= 16384, width and height
+    # <= 256) are argument errors, returned before its first CUDA call; the
+    # device pointers are never touched on the host, so stand-ins do
+    from paper_2602_21644_gb300 import dags
+    lib = dags.load()
+    dev = ctypes.c_void_p(256)                     # a 16-byte aligned stand-in device address
+    f = lib.splat_forward_static
+
+    def call(n, w, h, image=dev):
+        cam = dags.CCamera(200.0, 200.0, w / 2, h / 2, w, h)
+        return f(dev, n, ctypes.byref(cam), dev, None, None, None, image, dev, None, None, None)
+    assert call(16385, 64, 48) == -1
+    assert call(100, 257, 48) == -1
+    assert call(100, 64, 257) == -1
+    assert call(-1, 64, 48) == -1
+    assert call(100, 64, 48, image=None) == -1
