@@ -12,11 +12,19 @@ Follows Sec. IV-A and Eq. (17) step by step, one view:
     region k    the instance label of p (0 = background, its own region)
     mu_e, sigma_e, e_ub   Eq. (4) over the region's pixels (population std);
                 e_ub is floored at e_floor (a reading: without it a static
-                instance normalises its own noise to MP_geo ~ 1)
+                instance normalises its own noise to MP_geo ~ 1); the
+                background pixels normalise by the background region's e_ub
+                (Eq. (4) is a statistic of a region; the background is the
+                region no instance claims)
     MP_geo      Eq. (5); inside an instance whose sigma_e < sigma_min the
                 instance mean replaces e(p) ("use the instance-mean error")
     MP_ins, Gamma_ins     Eq. (2) from the instance table (row 0 = background)
-    Gamma_geo   exp(-sigma_e,k / sigma_g) of the pixel's region
+    Gamma_geo   exp(-sigma / sigma_g) (the sentence after Eq. (7)): for a
+                pixel of instance k, sigma = sigma_e,k of its region; for a
+                pixel no instance claims, sigma = the population std of e
+                over the pixel's associated neighbourhood, read as the disk
+                of Eq. (1) centred on the pixel: the pixels (i + di, j + dj)
+                of the image with di^2 + dj^2 <= r_s^2, whatever their label
     K_p, M_p    Eqs. (6), (7)  (fusion_mode 1 forces K = 0, 2 forces K = 1)
   per Gaussian G
     N(G)        pixels within r_s of the projected mean, Eq. (1), one scale;
@@ -81,9 +89,45 @@ def lower_median(x: np.ndarray) -> float:
     return float(s[(len(s) - 1) // 2])
 
 
-def pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg: MPConfig):
-    """Per-pixel fused MP observation. Returns dict(e, e_used, M_p, K,
+def neighbourhood_std(e, W, H, r_s):
+    """Population std of e over each pixel's disk {(di, dj): di^2 + dj^2 <=
+    r_s^2} clipped to the image (the associated neighbourhood of a pixel that
+    no instance claims, sentence after Eq. (7)). Two passes: the mean over
+    the disk, then the mean squared deviation from it."""
+    e = np.asarray(e, np.float64).reshape(H, W)
+    R = int(np.floor(r_s))
+    offs = [(di, dj) for dj in range(-R, R + 1) for di in range(-R, R + 1) if di * di + dj * dj <= r_s * r_s]
+
+    def shifted(a, di, dj):
+        # out[j, i] = a[j + dj, i + di] where that pixel exists, else nan
+        out = np.full((H, W), np.nan)
+        ys, ye = max(0, -dj), min(H, H - dj)
+        xs, xe = max(0, -di), min(W, W - di)
+        if ys < ye and xs < xe:
+            out[ys:ye, xs:xe] = a[ys + dj:ye + dj, xs + di:xe + di]
+        return out
+
+    cnt = np.zeros((H, W))
+    tot = np.zeros((H, W))
+    for di, dj in offs:
+        sv = shifted(e, di, dj)
+        ok = ~np.isnan(sv)
+        cnt += ok
+        tot += np.where(ok, sv, 0.0)
+    mean = tot / cnt
+    sq = np.zeros((H, W))
+    for di, dj in offs:
+        sv = shifted(e, di, dj)
+        ok = ~np.isnan(sv)
+        sq += np.where(ok, (sv - mean) ** 2, 0.0)
+    return np.sqrt(sq / cnt).ravel()
+
+
+def pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg: MPConfig, shape):
+    """Per-pixel fused MP observation on a W x H image (shape = (W, H)).
+    Returns dict(e, e_used, M_p, K, sigma_geo (the dispersion in Gamma_geo),
     region stats (count, mean, std, e_ub) per label)."""
+    W, H = int(shape[0]), int(shape[1])
     inst = np.asarray(inst).astype(np.int64).ravel()
     d_obs = np.asarray(d_obs, np.float64).ravel()
     d_rend = np.asarray(d_rend, np.float64).ravel()
@@ -107,7 +151,11 @@ def pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg: MPConfig):
     mp_geo = np.clip(e_used / e_ub[inst], 0.0, 1.0)
     mp_ins = table[inst, 0]
     g_ins = table[inst, 1]
-    g_geo = np.exp(-std[inst] / cfg.sigma_g)
+    sigma_geo = std[inst]
+    bg = inst == 0
+    if bg.any():
+        sigma_geo = np.where(bg, neighbourhood_std(e, W, H, cfg.r_s), sigma_geo)
+    g_geo = np.exp(-sigma_geo / cfg.sigma_g)
     K = g_geo / (g_ins + g_geo)
     if cfg.fusion_mode == 1:
         K = np.zeros_like(K)
@@ -115,7 +163,7 @@ def pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg: MPConfig):
         K = np.ones_like(K)
     M_p = (1.0 - K) * mp_ins + K * mp_geo
     return dict(e=e, e_used=e_used, mp_geo=mp_geo, mp_ins=mp_ins, K=K, M_p=M_p, count=cnt, mean=mean,
-                std=std, e_ub=e_ub)
+                std=std, e_ub=e_ub, sigma_geo=sigma_geo)
 
 
 def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend, c_rend, table,
@@ -136,7 +184,7 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
     cfg = MPConfig() if cfg is None else cfg
     fx, fy, cx, cy, W, H = cam
     W, H = int(W), int(H)
-    px = pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg)
+    px = pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, table, cfg, (W, H))
     M_p, e = px["M_p"], px["e"]
     if mp_map is not None:
         M_p = np.asarray(mp_map, np.float64).ravel()

@@ -40,11 +40,11 @@ def test_fusion_special_cases():
     d_rend = d_obs + rng.normal(0, 0.1, W * H)
     c_obs = rng.uniform(0, 1, (W * H, 3))
     c_rend = rng.uniform(0, 1, (W * H, 3))
-    k0 = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(fusion_mode=1))
+    k0 = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(fusion_mode=1), (W, H))
     np.testing.assert_array_equal(k0["M_p"], TABLE[inst, 0])          # K = 0: MP_ins, Eq. (2)
-    k1 = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(fusion_mode=2))
+    k1 = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(fusion_mode=2), (W, H))
     np.testing.assert_array_equal(k1["M_p"], k1["mp_geo"])             # K = 1: MP_geo
-    fz = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig())
+    fz = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(), (W, H))
     lo = np.minimum(fz["mp_ins"], fz["mp_geo"]) - 1e-15
     hi = np.maximum(fz["mp_ins"], fz["mp_geo"]) + 1e-15
     assert np.all((fz["M_p"] >= lo) & (fz["M_p"] <= hi))                # convex combination
@@ -62,19 +62,85 @@ def test_geometric_mp_closed_form():
     d_rend = np.full(W * H, 2.0)
     c = np.full((W * H, 3), 0.5)
     cfg = M.MPConfig()
-    px = M.pixel_mp(inst, d_rend + e, c, d_rend, c, TABLE, cfg)
+    px = M.pixel_mp(inst, d_rend + e, c, d_rend, c, TABLE, cfg, (W, H))
     np.testing.assert_allclose(px["mean"], [0.02, 0.3], rtol=1e-12)
     np.testing.assert_allclose(px["std"], [0.01, 0.0], atol=1e-12)
     np.testing.assert_allclose(px["e_ub"], [0.05, 0.3], rtol=1e-12)
     bg = inst == 0
     np.testing.assert_allclose(px["mp_geo"][bg], e[bg] / 0.05, rtol=1e-12)
     np.testing.assert_allclose(px["mp_geo"][~bg], 1.0, rtol=1e-12)
-    g_geo_bg = np.exp(-0.01 / 0.05)
+    # Gamma_geo of a background pixel uses the dispersion over its own disk of
+    # radius 2 (13 pixels): away from the instance and the image border, 7 of
+    # them share the pixel's column parity (di in {0, +-2}) and 6 do not, so
+    # sigma = |0.03 - 0.01| sqrt(p (1 - p)) with p = 7/13
+    jj, ii = np.divmod(np.arange(W * H), W)
+    interior = bg & (jj >= 6) & (jj <= H - 3) & (ii >= 2) & (ii <= W - 3)
+    sig = 0.02 * np.sqrt(7 * 6) / 13
+    np.testing.assert_allclose(px["sigma_geo"][interior], sig, rtol=1e-12)
+    g_geo_bg = np.exp(-sig / 0.05)
     K_bg = g_geo_bg / (0.05 + g_geo_bg)
-    np.testing.assert_allclose(px["K"][bg], K_bg, rtol=1e-12)
-    np.testing.assert_allclose(px["M_p"][bg], (1 - K_bg) * 0.1 + K_bg * e[bg] / 0.05, rtol=1e-12)
+    np.testing.assert_allclose(px["K"][interior], K_bg, rtol=1e-12)
+    np.testing.assert_allclose(px["M_p"][interior], (1 - K_bg) * 0.1 + K_bg * e[interior] / 0.05, rtol=1e-12)
     K_in = 1.0 / (0.8 + 1.0)
     np.testing.assert_allclose(px["M_p"][~bg], (1 - K_in) * 0.9 + K_in * 1.0, rtol=1e-12)
+
+
+def test_background_gamma_uses_the_pixel_neighbourhood():
+    # Sentence after Eq. (7): a pixel that no instance claims takes the
+    # dispersion of e "within the associated neighborhood", here its disk of
+    # radius r_s = 2 clipped to the image. One residual of 1 at pixel (0, 0)
+    # and a 3x3 patch of 1 at columns 10-12, rows 8-10; everything else 0.
+    e = np.zeros((H, W))
+    e[0, 0] = 1.0
+    e[8:11, 10:13] = 1.0
+    inst = np.zeros(W * H, np.uint8)
+    d_rend = np.full(W * H, 2.0)
+    c = np.full((W * H, 3), 0.5)
+    cfg = M.MPConfig()
+    px = M.pixel_mp(inst, d_rend + e.ravel(), c, d_rend, c, TABLE, cfg, (W, H))
+    sg = px["sigma_geo"].reshape(H, W)
+    # (0, 0): the disk clipped to 6 pixels, one of them 1
+    assert abs(sg[0, 0] - np.sqrt(5.0) / 6.0) < 1e-12
+    # (1, 1): 11 pixels ((-1, 1) and (1, -1) fall outside), one of them 1
+    assert abs(sg[1, 1] - np.sqrt(10.0) / 11.0) < 1e-12
+    # (14, 9): two to the right of the patch; only (12, 9) of its 13 is 1
+    assert abs(sg[9, 14] - np.sqrt(12.0) / 13.0) < 1e-12
+    # (15, 9): three to the right; nothing of the patch in its disk
+    assert sg[9, 15] == 0.0 and sg[4, 4] == 0.0
+    # inside the patch centre all 9 patch pixels and 4 zeros ((0, +-2), (+-2, 0))
+    assert abs(sg[9, 11] - np.sqrt(9 * 4) / 13.0) < 1e-12
+    # Gamma_geo and K follow: exp(-sigma / sigma_g), K = G / (c_bg + G)
+    g = np.exp(-px["sigma_geo"] / cfg.sigma_g)
+    np.testing.assert_allclose(px["K"], g / (TABLE[0, 1] + g), rtol=1e-13)
+    # the one-region reading would give every background pixel the same K
+    assert np.ptp(px["K"]) > 0.1
+
+
+def test_neighbourhood_std_against_brute_force():
+    rng = np.random.default_rng(5)
+    w, h = 9, 7
+    e = rng.uniform(0, 1, (h, w))
+    for r_s in (1.0, 2.0, 2.5):
+        got = M.neighbourhood_std(e.ravel(), w, h, r_s).reshape(h, w)
+        for y in range(h):
+            for x in range(w):
+                vals = [e[yy, xx] for yy in range(h) for xx in range(w)
+                        if (xx - x) ** 2 + (yy - y) ** 2 <= r_s * r_s]
+                assert abs(got[y, x] - np.std(vals)) < 1e-12
+
+
+def test_instance_pixels_keep_the_region_dispersion():
+    # an instance pixel's Gamma_geo is the region's: a single outlier inside
+    # the instance changes every instance pixel's K alike
+    inst = np.zeros(W * H, np.uint8)
+    inst[W * 10:W * 14] = 1
+    e = np.zeros(W * H)
+    e[W * 12 + 5] = 0.5
+    d_rend = np.full(W * H, 2.0)
+    c = np.full((W * H, 3), 0.5)
+    px = M.pixel_mp(inst, d_rend + e, c, d_rend, c, TABLE, M.MPConfig(), (W, H))
+    sel = e[inst == 1]
+    np.testing.assert_allclose(px["sigma_geo"][inst == 1], np.std(sel), rtol=1e-12)
 
 
 def test_instant_update_equals_observation():
@@ -183,7 +249,7 @@ def test_external_map_reduces_to_fused_mp():
     prev = rng.uniform(0.05, 0.95, n)
     args = (means, prev, np.zeros(n, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c_obs, d_rend, c_rend, TABLE)
     a = M.mp_update(*args)
-    b = M.mp_update(*args, mp_map=M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig())["M_p"])
+    b = M.mp_update(*args, mp_map=M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, M.MPConfig(), (W, H))["M_p"])
     for k in ("mp", "m_hat", "var", "U", "alpha"):
         np.testing.assert_array_equal(a[k], b[k])
     np.testing.assert_array_equal(a["labels"], b["labels"])

@@ -64,7 +64,7 @@ def test_residual_mean_is_the_background_region_mean():
     d_rend = np.full(W * H, 2.0)
     d_obs = d_rend + np.where(inst == 0, 0.03, 0.2)
     c = np.full((W * H, 3), 0.5)
-    px = M.pixel_mp(inst, d_obs, c, d_rend, c.copy(), np.array([[0.1, 0.05], [0.9, 0.8]]), M.MPConfig())
+    px = M.pixel_mp(inst, d_obs, c, d_rend, c.copy(), np.array([[0.1, 0.05], [0.9, 0.8]]), M.MPConfig(), (W, H))
     e_bar = S.residual_mean(px["e"], inst)
     assert abs(e_bar - 0.03) < 1e-12
     assert abs(e_bar - px["mean"][0]) < 1e-12
