@@ -237,7 +237,7 @@ typedef struct {
   float lam;         /* lambda of e_ub = mu_e + lambda sigma_e, Eq. (4) (2)                */
   float sigma_min;   /* instance with sigma_e below this uses its mean error, m (0.005)    */
   float e_floor;     /* floor on e_ub, m (0.05)                                            */
-  float sigma_g;     /* Gamma_geo = exp(-sigma_e,k / sigma_g), Eq. (7), m (0.05)           */
+  float sigma_g;     /* Gamma_geo = exp(-sigma / sigma_g), after Eq. (7), m (0.05)         */
   float sigma_c;     /* C = exp(-sigma_e,G / sigma_c), Eq. (11), m (0.05)                  */
   float lam_u;       /* lambda_u, Eq. (10) (1)                                             */
   float eps;         /* epsilon, Eq. (10) (1e-6)                                           */
@@ -261,8 +261,13 @@ void dags_default_mp_cfg(dags_mp_cfg *cfg);
  * (where D_obs > 0) + kappa_c ||C_obs - C_rend||_1; region k = inst[p]
  * (0 = background, its own region); region mean/std of e, Eq. (4) (e_ub
  * floored at e_floor; an instance with sigma_e < sigma_min uses its mean);
- * MP_geo, Eq. (5); MP_ins and Gamma_ins from the region table, Eq. (2);
- * fusion, Eqs. (6),(7). Per Gaussian (in FP32): the pixels within r_s of its
+ * MP_geo, Eq. (5), with the region's e_ub (background pixels: the
+ * background region's); MP_ins and Gamma_ins from the region table, Eq. (2);
+ * Gamma_geo = exp(-sigma / sigma_g) with sigma the region's sigma_e inside an
+ * instance and, for a background pixel, the population std of e over the
+ * pixel's own disk {di^2 + dj^2 <= r_s^2} clipped to the image (its
+ * associated neighbourhood, the sentence after Eq. (7)); fusion, Eqs. (6),(7),
+ * stored per pixel in the ctx. Per Gaussian (in FP32): the pixels within r_s of its
  * projected mean, Eq. (1), weighted exp(-d^2 / (2 sigma_w^2)); observed iff
  * z > z_near, the disk is non-empty and z <= max rendered depth over the disk
  * + vis_tol; M_hat, Eq. (8); U, Eq. (10), min-max normalised over the

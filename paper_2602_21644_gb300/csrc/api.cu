@@ -119,7 +119,7 @@ void free_ws(Workspace &w) {
 }
 
 void free_mp(MpBuffers &b) {
-  void *ptrs[] = {b.e, b.acc, b.mhat, b.sige, b.U, b.Mt, b.Ut, b.obs, b.hist, b.sel};
+  void *ptrs[] = {b.e, b.mpf, b.acc, b.mhat, b.sige, b.U, b.Mt, b.Ut, b.obs, b.hist, b.sel};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   b = MpBuffers();
@@ -309,6 +309,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
   MpBuffers &mb = c->mp;
   A(alloc(&mb.e, (size_t)max_width * max_height));
+  A(alloc(&mb.mpf, (size_t)max_width * max_height));
   A(alloc(&mb.acc, (size_t)DAGS_MP_MAX_REGIONS * 4));
   A(alloc(&mb.mhat, (size_t)w.max_n));
   A(alloc(&mb.sige, (size_t)w.max_n));

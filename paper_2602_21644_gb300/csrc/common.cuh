@@ -195,6 +195,7 @@ cudaError_t launch_mpnet_train(void *weights, float *master, float *adam_m, floa
 // Buffers of the MP update (owned by the ctx).
 struct MpBuffers {
   float *e = nullptr;                 // [max_w * max_h]
+  float *mpf = nullptr;               // [max_w * max_h] fused per-pixel M_p
   double *acc = nullptr;              // [DAGS_MP_MAX_REGIONS * 4]
   float *mhat = nullptr, *sige = nullptr, *U = nullptr, *Mt = nullptr, *Ut = nullptr;  // [max_n]
   uint8_t *obs = nullptr;             // [max_n]

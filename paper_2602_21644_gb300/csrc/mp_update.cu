@@ -6,11 +6,15 @@
 //                         per CTA)
 //   mp_pixel_var_kernel   per pixel: centred squares (e - mean_k)^2 summed per
 //                         region the same way (two passes: no cancellation)
+//   mp_pixel_map_kernel   per pixel: the fused MP M_p, Eqs. (2)-(7), from
+//                         the region statistics; Gamma_geo of a pixel that no
+//                         instance claims uses the dispersion of e over the
+//                         pixel's own disk of radius r_s (its associated
+//                         neighbourhood); stored for the gather
 //   mp_gauss_kernel       per Gaussian: projection, the association disk
-//                         N(G), Eq. (1), with the fused per-pixel MP M_p,
-//                         Eqs. (2)-(7), computed on the fly from the region
-//                         statistics; M_hat, Eq. (8); Var{M_p}; sigma_e,G;
-//                         U, Eq. (10); CTA min/max of U -> global
+//                         N(G), Eq. (1), over the stored M_p (or the caller's
+//                         map); M_hat, Eq. (8); Var{M_p}; sigma_e,G; U,
+//                         Eq. (10); CTA min/max of U -> global
 //   mp_apply_kernel       per observed Gaussian: normalised U, C, alpha,
 //                         Eqs. (11), (17); M^t, Eq. (9), written into the
 //                         record; first radix-select level of the two medians
@@ -51,6 +55,7 @@ struct MpWs {
   double *stats;         // caller's output
   const float *mp_map;   // [P] external per-pixel MP replacing M_p, or null
   float *mp_pixel;       // [P] out: the fused M_p, or null
+  float *mpf;            // [P] the fused M_p (workspace)
   uint32_t *status;      // the ctx's status word (index checks of a DAGS_CHECK build)
 };
 
@@ -178,10 +183,42 @@ __device__ __forceinline__ float pixel_mp(float e, const float4 reg, const float
   return (1.f - K) * tab.x + K * mp_geo;
 }
 
-// The fused per-pixel M_p map, Eqs. (2)-(7) (an output for callers that
-// train or evaluate a learned proposal against the method).
+// Population std of e over the disk {(di, dj): di^2 + dj^2 <= r_s^2} around
+// pixel (x, y), clipped to the image; two passes (mean, then centred squares).
+__device__ __forceinline__ float disk_std(const float *__restrict__ e, int x, int y, int W, int H, float r_s) {
+  const int R = (int)floorf(r_s);
+  const float rs2 = r_s * r_s;
+  const int y0 = max(y - R, 0), y1 = min(y + R, H - 1), x0 = max(x - R, 0), x1 = min(x + R, W - 1);
+  float s = 0.f;
+  int cnt = 0;
+  for (int yy = y0; yy <= y1; ++yy)
+    for (int xx = x0; xx <= x1; ++xx) {
+      const int di = xx - x, dj = yy - y;
+      if ((float)(di * di + dj * dj) > rs2) continue;
+      s += __ldg(e + (size_t)yy * W + xx);
+      ++cnt;
+    }
+  const float mean = s / (float)cnt;
+  float sq = 0.f;
+  for (int yy = y0; yy <= y1; ++yy)
+    for (int xx = x0; xx <= x1; ++xx) {
+      const int di = xx - x, dj = yy - y;
+      if ((float)(di * di + dj * dj) > rs2) continue;
+      const float d = __ldg(e + (size_t)yy * W + xx) - mean;
+      sq += d * d;
+    }
+  return sqrtf(sq / (float)cnt);
+}
+
+// The fused per-pixel M_p map, Eqs. (2)-(7): read by the gather and, when
+// asked for, returned to the caller (who may train or evaluate a learned
+// proposal against the method). Gamma_geo = exp(-sigma / sigma_g) takes the
+// region's sigma_e inside an instance and, for a pixel that no instance
+// claims, the dispersion over the pixel's associated neighbourhood (the
+// sentence after Eq. (7)), read as its disk of radius r_s.
 __global__ void __launch_bounds__(kMpBlock)
-mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int P, MpCfg c) {
+mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int W, int H,
+                    MpCfg c) {
   __shared__ float4 s_reg[DAGS_MP_MAX_REGIONS];
   __shared__ float2 s_tab[DAGS_MP_MAX_REGIONS];
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
@@ -190,24 +227,22 @@ mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__re
   }
   __syncthreads();
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < P) {
+  if (p < W * H) {
     const int k = region_of(inst, p, c.n_regions, m.status);
-    m.mp_pixel[p] = pixel_mp(m.e[p], s_reg[k], s_tab[k], c.fusion_mode);
+    float4 reg = s_reg[k];
+    if (k == 0) reg.z = expf(-disk_std(m.e, p % W, p / W, W, H, c.r_s) / c.sigma_g);
+    const float mp = pixel_mp(m.e[p], reg, s_tab[k], c.fusion_mode);
+    m.mpf[p] = mp;
+    if (m.mp_pixel) m.mp_pixel[p] = mp;
   }
 }
 
 __global__ void __launch_bounds__(kMpBlock)
 mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
-                const float *__restrict__ image, const uint8_t *__restrict__ inst, const float2 *__restrict__ table,
-                Raster r, MpCfg c) {
-  __shared__ float4 s_reg[DAGS_MP_MAX_REGIONS];
-  __shared__ float2 s_tab[DAGS_MP_MAX_REGIONS];
+                const float *__restrict__ image, Raster r, MpCfg c) {
   __shared__ float sp[12];
   __shared__ uint32_t s_min, s_max, s_cnt;
-  for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
-    region_params(m, c, k, &s_reg[k]);
-    s_tab[k] = table[k];
-  }
+  const float *__restrict__ mpsrc = m.mp_map ? m.mp_map : m.mpf;
   if (threadIdx.x < 12) sp[threadIdx.x] = (float)pose[threadIdx.x];
   if (threadIdx.x == 0) { s_min = 0xFFFFFFFFu; s_max = 0u; s_cnt = 0u; }
   __syncthreads();
@@ -235,8 +270,7 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
             if (d2 > rs2) continue;
             const size_t p = (size_t)jj * r.W + ii;
             const float e = m.e[p];
-            const int k = region_of(inst, p, c.n_regions, m.status);
-            const float mp = m.mp_map ? __ldg(m.mp_map + p) : pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
+            const float mp = mpsrc[p];
             const float w = expf(-d2 * inv2s2);
             sw += w; swm += w * mp; sm += mp; se += e; ++cnt;
             dmax = fmaxf(dmax, image[3 * P + p]);
@@ -253,8 +287,7 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
             if (dx * dx + dy * dy > rs2) continue;
             const size_t p = (size_t)jj * r.W + ii;
             const float e = m.e[p];
-            const int k = region_of(inst, p, c.n_regions, m.status);
-            const float mp = m.mp_map ? __ldg(m.mp_map + p) : pixel_mp(e, s_reg[k], s_tab[k], c.fusion_mode);
+            const float mp = mpsrc[p];
             vm += (mp - mm) * (mp - mm);
             ve += (e - me) * (e - me);
           }
@@ -474,6 +507,7 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   m.status = status;
   m.mp_map = mp_map;
   m.mp_pixel = mp_pixel;
+  m.mpf = b.mpf;
   m.e = b.e; m.acc = b.acc; m.mhat = b.mhat; m.sige = b.sige; m.U = b.U; m.Mt = b.Mt; m.Ut = b.Ut;
   m.obs = b.obs; m.hist = b.hist; m.sel = b.sel; m.stats = stats;
   MpCfg c;
@@ -491,10 +525,9 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   const unsigned gg = (unsigned)((n + kMpBlock - 1) / kMpBlock > 0 ? (n + kMpBlock - 1) / kMpBlock : 1);
   mp_pixel_sum_kernel<<<gp, kMpBlock, 0, s>>>(m, targets, image, inst, P, c);
   mp_pixel_var_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, P, c);
-  if (mp_pixel)
-    mp_pixel_map_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, reinterpret_cast<const float2 *>(table), P, c);
-  mp_gauss_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<const float4 *>(gauss), n, pose, image, inst,
-                                          reinterpret_cast<const float2 *>(table), r, c);
+  if (!mp_map || mp_pixel)
+    mp_pixel_map_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, reinterpret_cast<const float2 *>(table), r.W, r.H, c);
+  mp_gauss_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<const float4 *>(gauss), n, pose, image, r, c);
   mp_apply_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<float4 *>(gauss), n, c);
   mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 1, c);
   mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 2, c);
