@@ -574,6 +574,29 @@ enum {
 int dags_timing_enable(dags_ctx *ctx, int enable);
 int dags_timing_read(dags_ctx *ctx, double *ms, int64_t *launches, int32_t count);
 
+/* Evaluation counts of the compositing kernels (measurement; no paper
+ * counterpart). While enabled, splat_forward and splat_backward add, per
+ * launch, the pixel-Gaussian exponents they evaluate (the list entries a
+ * pixel's warp keeps after its box test and the pixel reaches before it
+ * saturates or passes its last contributor) and the contributions among them
+ * (alpha >= alpha_min). dags_eval_read waits for the ctx's last stream, writes
+ * counts[4] = {forward evaluations, forward contributions, backward
+ * evaluations, backward contributions} accumulated since the last read, and
+ * resets them. Counting costs one warp reduction and atomic per warp and
+ * launch. DAGS_E_INVAL on a NULL ctx or counts. */
+int dags_eval_counting(dags_ctx *ctx, int32_t enable);
+int dags_eval_read(dags_ctx *ctx, int64_t *counts);
+
+/* Throughput probe of the current device's FP32 pipe (kind 0: fused
+ * multiply-adds) or special-function pipe (kind 1: ex2.approx), for the
+ * roofline peaks of the ALU-bound kernels (measurement; no paper
+ * counterpart). Launches one warm-up and one timed grid of (SMs x resident
+ * CTAs) x 256 threads, each running 8 independent chains of `iters` dependent
+ * operations, on a private stream, and waits for it. ops_per_s (host out):
+ * lane operations per second; ms (host out, or NULL): the timed launch.
+ * 1 <= iters <= 2^24, kind 0 or 1, else DAGS_E_INVAL. */
+int dags_measure_alu(int32_t kind, int64_t iters, double *ops_per_s, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

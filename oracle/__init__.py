@@ -123,7 +123,10 @@ def params_from_records(rec: np.ndarray) -> np.ndarray:
 
 
 def camera_vec(fx, fy, cx, cy, width, height) -> np.ndarray:
-    return np.array([fx, fy, cx, cy, width, height], dtype=np.float64)
+    """The camera the C ABI receives: its intrinsics are FP32 fields, so the
+    oracle evaluates the FP32-rounded values (in FP64 arithmetic)."""
+    f32 = lambda x: float(np.float32(x))
+    return np.array([f32(fx), f32(fy), f32(cx), f32(cy), width, height], dtype=np.float64)
 
 
 def raster_vec(tile=16, alpha_min=1.0 / 255.0, alpha_max=0.99, t_min=1e-4, dilation=0.3,

@@ -110,9 +110,9 @@ cudaError_t alloc(T **p, size_t count) {
 }
 
 void free_ws(Workspace &w) {
-  void *ptrs[] = {w.rec2d, w.rect, w.grad2d, w.tile_count, w.tile_start, w.tile_cursor, w.keys,
+  void *ptrs[] = {w.rec2d, w.rec_lo, w.rect, w.grad2d, w.tile_count, w.tile_start, w.tile_cursor, w.keys,
                   w.keys_tmp, w.sorted_ids, w.tile_order, w.loss_partial, w.pose_partial, w.pose32,
-                  w.vis_ids, w.vis_append, w.vis_n, w.counters};
+                  w.vis_ids, w.vis_append, w.vis_n, w.counters, w.evals};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   w = Workspace();
@@ -289,6 +289,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
   A(alloc(&w.rec2d, vn * 3));
+  A(alloc(&w.rec_lo, vn));
   A(alloc(&w.rect, vn));
   A(alloc(&w.grad2d, vn * kGradWords));
   A(alloc(&w.tile_count, vt));
@@ -305,6 +306,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&w.vis_append, (size_t)w.max_v));
   A(alloc(&w.vis_n, (size_t)w.max_v));
   A(alloc(&w.counters, (size_t)CNT_N));
+  A(alloc(&w.evals, (size_t)4));
   if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
   MpBuffers &mb = c->mp;
@@ -320,6 +322,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&mb.hist, (size_t)2 * 2048));
   A(alloc(&mb.sel, (size_t)8));
   if (e == cudaSuccess) e = cudaMemset(w.counters, 0, CNT_N * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(w.evals, 0, 4 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(w.vis_append, 0, (size_t)w.max_v * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.vis_n, 0, (size_t)w.max_v * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -359,6 +362,24 @@ void dags_destroy(dags_ctx *ctx) {
   free_ws(ctx->ws);
   cudaSetDevice(cur);
   delete ctx;
+}
+
+int dags_eval_counting(dags_ctx *ctx, int32_t enable) {
+  NvtxRange nv("dags_eval_counting");
+  if (!ctx) return DAGS_E_INVAL;
+  ctx->ws.count_evals = enable ? 1 : 0;
+  return DAGS_OK;
+}
+
+int dags_eval_read(dags_ctx *ctx, int64_t *counts) {
+  NvtxRange nv("dags_eval_read");
+  if (!ctx || !counts) return DAGS_E_INVAL;
+  if (cudaStreamSynchronize(ctx->last_stream) != cudaSuccess) return DAGS_E_CUDA;
+  unsigned long long c[4];
+  if (cudaMemcpy(c, ctx->ws.evals, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return DAGS_E_CUDA;
+  if (cudaMemset(ctx->ws.evals, 0, sizeof(c)) != cudaSuccess) return DAGS_E_CUDA;
+  for (int k = 0; k < 4; ++k) counts[k] = (int64_t)c[k];
+  return DAGS_OK;
 }
 
 int dags_sync_status(dags_ctx *ctx, int64_t *required_pairs) {
@@ -1124,10 +1145,11 @@ constexpr size_t kZeroBytes = kOffCounters + al256(CNT_N * 4);
 constexpr size_t kOffStart = kZeroBytes;
 constexpr size_t kOffOrder = kOffStart + al256((kStaticTiles + 1) * 4);
 constexpr size_t kOffLossPartial = kOffOrder + al256(kStaticTiles * 4);
-constexpr size_t kOffVisN = kOffLossPartial + al256(kStaticTiles * 4);
+constexpr size_t kOffVisN = kOffLossPartial + al256(kStaticTiles * 8);
 constexpr size_t kOffPose32 = kOffVisN + al256(4);
 constexpr size_t kOffRec2d = kOffPose32 + al256(12 * 4);
-constexpr size_t kOffRect = kOffRec2d + al256(kStaticMaxN * 3 * 16);
+constexpr size_t kOffRecLo = kOffRec2d + al256(kStaticMaxN * 3 * 16);
+constexpr size_t kOffRect = kOffRecLo + al256(kStaticMaxN * 8);
 constexpr size_t kOffGrad2d = kOffRect + al256(kStaticMaxN * 8);
 constexpr size_t kOffVisIds = kOffGrad2d + al256(kStaticMaxN * kGradWords * 4);
 constexpr size_t kOffKeys = kOffVisIds + al256(kStaticMaxN * 4);
@@ -1202,10 +1224,11 @@ extern "C" int splat_forward_static(const float *gauss, int64_t n, const dags_ca
   w.counters = reinterpret_cast<uint32_t *>(base + kOffCounters);
   w.tile_start = reinterpret_cast<uint32_t *>(base + kOffStart);
   w.tile_order = reinterpret_cast<uint32_t *>(base + kOffOrder);
-  w.loss_partial = reinterpret_cast<float *>(base + kOffLossPartial);
+  w.loss_partial = reinterpret_cast<double *>(base + kOffLossPartial);
   w.vis_n = reinterpret_cast<uint32_t *>(base + kOffVisN);
   w.pose32 = reinterpret_cast<float *>(base + kOffPose32);
   w.rec2d = reinterpret_cast<float4 *>(base + kOffRec2d);
+  w.rec_lo = reinterpret_cast<float2 *>(base + kOffRecLo);
   w.rect = reinterpret_cast<uint2 *>(base + kOffRect);
   w.grad2d = reinterpret_cast<float *>(base + kOffGrad2d);
   w.vis_ids = reinterpret_cast<uint32_t *>(base + kOffVisIds);

@@ -61,6 +61,10 @@ enum {
 //                            lo = log2(opacity)
 //   r2 = {z, M, rg, bl}      depth, motion probability, colour as the
 //                            record's BF16 bit patterns
+// The centre (u, v) is computed in FP64 from the FP64 pose and stored as
+// u = r0.x + lo.x, v = r0.y + lo.y with the FP32 remainders in rec_lo, so
+// that a pixel offset (u - px) = (r0.x - px) + lo.x carries a relative
+// rounding of 2^-24 of the offset rather than an absolute ulp(u).
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 
@@ -71,6 +75,7 @@ struct Workspace {
   int bwd_prep_blocks = 0;
   int band = 1;                   // CTAs per dispatch round of the renders (the SM count)
   float4 *rec2d = nullptr;        // [V][N][3], see above
+  float2 *rec_lo = nullptr;       // [V][N] FP32 remainders of the FP64 centre
   uint2 *rect = nullptr;          // [V][N]: {x0 | x1 << 16, y0 | y1 << 16}, candidate tiles [x0, x1) x [y0, y1)
   float *grad2d = nullptr;        // [V][N][kGradWords]
   uint32_t *tile_count = nullptr; // [V * T]
@@ -80,14 +85,34 @@ struct Workspace {
   uint64_t *keys_tmp = nullptr;   // [max_pairs]: merge ping-pong
   uint32_t *sorted_ids = nullptr; // [max_pairs]
   uint32_t *tile_order = nullptr; // [V * T] launch order of the renders (length-ranked, band-reversed)
-  float *loss_partial = nullptr;  // [V * T]
+  double *loss_partial = nullptr; // [V * T] per-tile loss sums (FP64)
   double *pose_partial = nullptr; // [bwd_prep_blocks][V][6]
   float *pose32 = nullptr;        // [V][12] FP32 copy of the poses of the last forward
   uint32_t *vis_ids = nullptr;    // [V][N] ids of the Gaussians with a non-empty candidate range
   uint32_t *vis_append = nullptr; // [V] append cursors (zero between calls)
   uint32_t *vis_n = nullptr;      // [V] visible counts of the last forward
   uint32_t *counters = nullptr;   // [CNT_N]
+  // Evaluation counts (when count_evals is set): pixel-Gaussian exponents
+  // evaluated and contributions (alpha >= alpha_min) of the forward and the
+  // backward compositing, [fwd eval, fwd contrib, bwd eval, bwd contrib].
+  unsigned long long *evals = nullptr;
+  int count_evals = 0;
 };
+
+// Adds a lane's evaluation counts to the workspace totals (one atomic per
+// warp and counter); called by whole warps.
+__device__ __forceinline__ void add_eval_counts(const Workspace &ws, int which, unsigned ne, unsigned nc) {
+  if (!ws.count_evals) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ne += __shfl_xor_sync(0xffffffffu, ne, o);
+    nc += __shfl_xor_sync(0xffffffffu, nc, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(ws.evals + 2 * which, (unsigned long long)ne);
+    atomicAdd(ws.evals + 2 * which + 1, (unsigned long long)nc);
+  }
+}
 
 // Per-call constants handed to kernels by value.
 struct Raster {

@@ -221,7 +221,8 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
                   float *__restrict__ jac, float *__restrict__ image, int32_t *__restrict__ last, LmFuse fuse) {
   pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
-  __shared__ float4 s_a[kJacBatch], s_b[kJacBatch], s_c[kJacBatch];
+  __shared__ float4 s_a[kJacBatch], s_b[kJacBatch], s_c[kJacBatch];   // s_a: {u hi, v hi, u lo, v lo}
+  __shared__ float2 s_e[kJacBatch];                                   // box half extents
   extern __shared__ float4 s_t[];   // kJacBatch * kTan4
   __shared__ float s_red[kTilePix / 32][kNormal];
   __shared__ int s_last;
@@ -256,7 +257,10 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
       if (!DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n, ws.counters + CNT_STATUS)) id = 0;
       const float4 *tg = tan + (size_t)id * kTan4;
       float4 *st = s_t + q * kTan4;
-      s_a[q] = ws.rec2d[(size_t)id * 3 + 0];
+      const float4 r0 = ws.rec2d[(size_t)id * 3 + 0];
+      const float2 lo = ws.rec_lo[id];
+      s_a[q] = make_float4(r0.x, r0.y, lo.x, lo.y);
+      s_e[q] = make_float2(r0.z, r0.w);
       s_b[q] = ws.rec2d[(size_t)id * 3 + 1];
       s_c[q] = ws.rec2d[(size_t)id * 3 + 2];
 #pragma unroll
@@ -269,7 +273,8 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
       bool hit = false;
       if (jj < cnt) {
         const float4 a = s_a[jj];
-        hit = fabsf(a.x - bcx) <= a.z + 3.5f && fabsf(a.y - bcy) <= a.w + 1.5f;
+        const float2 ex = s_e[jj];
+        hit = fabsf(a.x - bcx) <= ex.x + 3.5f && fabsf(a.y - bcy) <= ex.y + 1.5f;
       }
       unsigned mask = __ballot_sync(FULL, hit);
       while (mask) {
@@ -277,7 +282,7 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
         mask &= mask - 1;
         if (done) continue;
         const float4 a = s_a[j], b = s_b[j];
-        const float dx = a.x - fpx, dy = a.y - fpy;
+        const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
         const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
         if (p < r.log2_alpha_min) continue;
         const float ag = hw_exp2(p);

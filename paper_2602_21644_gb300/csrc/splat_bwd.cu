@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(kTilePix)
 render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ targets,
                   const float *__restrict__ image, const int32_t *__restrict__ last) {
   pdl_wait();
-  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
+  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
+  __shared__ float2 s_e[kTilePix];                                  // box half extents
   __shared__ uint32_t s_id[kTilePix];
   __shared__ int s_max;
   const unsigned FULLM = 0xffffffffu;
@@ -95,6 +96,7 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   // Sg = sum over channels of g_ch * S_ch, S_ch the channel's composited sum
   // behind the current Gaussian: dL/dalpha needs only this contraction
   float Sg = 0.f;
+  unsigned n_eval = 0, n_contrib = 0;
   const float fpx = (float)px, fpy = (float)py;
   for (int end = kmax; end > 0; end -= kTilePix) {
     const int beg = max(0, end - kTilePix);
@@ -104,7 +106,10 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
       if (!DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n, ws.counters + CNT_STATUS)) id = 0;
       const size_t slot = vbase + id;
       s_id[tid] = id;
-      s_a[tid] = ws.rec2d[slot * 3 + 0];
+      const float4 r0 = ws.rec2d[slot * 3 + 0];
+      const float2 lo = ws.rec_lo[slot];
+      s_a[tid] = make_float4(r0.x, r0.y, lo.x, lo.y);
+      s_e[tid] = make_float2(r0.z, r0.w);
       s_b[tid] = ws.rec2d[slot * 3 + 1];
       s_c[tid] = ws.rec2d[slot * 3 + 2];
     }
@@ -116,7 +121,8 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
       bool hit = false;
       if (jj < cnt) {
         const float4 a = s_a[jj];
-        hit = fabsf(a.x - bcx) <= a.z + 3.5f && fabsf(a.y - bcy) <= a.w + 1.5f;
+        const float2 ex = s_e[jj];
+        hit = fabsf(a.x - bcx) <= ex.x + 3.5f && fabsf(a.y - bcy) <= ex.y + 1.5f;
       }
       unsigned mask = __ballot_sync(FULLM, hit);
       while (mask) {
@@ -129,10 +135,12 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
         float go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
         if (k < lastp) {
           const float4 a = s_a[j], b = s_b[j];
-          const float dx = a.x - fpx, dy = a.y - fpy;
+          const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
           const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+          ++n_eval;
           if (p >= r.log2_alpha_min) {
             contrib = true;
+            ++n_contrib;
             const float ag = hw_exp2(p);
             const float alpha = fminf(r.alpha_max, ag);
             const float inv = hw_rcp(1.f - alpha);
@@ -178,6 +186,7 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
       }
     }
   }
+  add_eval_counts(ws, 1, n_eval, n_contrib);
 }
 
 // Chains the 2D gradients of Gaussian i in view v (pose Pm) to the pose

@@ -247,6 +247,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
   pdl_wait();
   __shared__ float sp[kMaxViewsSmem * 12];
+  __shared__ double spd[kMaxViewsSmem * 12];
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // the record loads are issued before the pose barrier, so that the two
@@ -258,7 +259,11 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     g2 = __ldg(gauss + 4 * i + 2);
     g3 = __ldg(gauss + 4 * i + 3);
   }
-  for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = (float)poses[k];
+  for (int k = threadIdx.x; k < views * 12; k += blockDim.x) {
+    const double pk = poses[k];
+    spd[k] = pk;
+    sp[k] = (float)pk;
+  }
   __syncthreads();
   if (blockIdx.x == 0 && blockIdx.y == 0)
     for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
@@ -270,9 +275,24 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     const size_t slot = (size_t)v * ws.max_n + i;
 
     float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
+    float2 ulo = make_float2(0.f, 0.f);
     uint2 rect = make_uint2(0u, 0u);
     Proj q;
     if (project_gaussian(g0, g1, g2, P, r, q)) {
+      // the centre in FP64 from the FP64 pose, split into FP32 hi + lo
+      {
+        const double *Pd = spd + v * 12;
+        const double mx = g0.x, my = g0.y, mz = g0.z;
+        const double xd = Pd[0] * mx + Pd[1] * my + Pd[2] * mz + Pd[3];
+        const double yd = Pd[4] * mx + Pd[5] * my + Pd[6] * mz + Pd[7];
+        const double zd = Pd[8] * mx + Pd[9] * my + Pd[10] * mz + Pd[11];
+        const double izd = 1.0 / zd;
+        const double ud = (double)r.fx * xd * izd + (double)r.cx;
+        const double vd = (double)r.fy * yd * izd + (double)r.cy;
+        q.u = __double2float_rn(ud);
+        q.v = __double2float_rn(vd);
+        ulo = make_float2(__double2float_rn(ud - (double)q.u), __double2float_rn(vd - (double)q.v));
+      }
       const float lo = log2f(q.o);
       const float thr = lo - r.log2_alpha_min;             // ellipse: Q(d) <= thr
       const float cnat = 2.f * kLn2 * thr;                 // 2 ln(o / alpha_min)
@@ -295,6 +315,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       ws.rec2d[slot * 3 + 0] = o0;
       ws.rec2d[slot * 3 + 1] = o1;
       ws.rec2d[slot * 3 + 2] = o2;
+      ws.rec_lo[slot] = ulo;
       float4 *gz = reinterpret_cast<float4 *>(ws.grad2d + slot * kGradWords);
       for (int w = 0; w < zero_words / 4; ++w) gz[w] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -380,8 +401,9 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
                   float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
   pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
-  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];
-  __shared__ float s_red[kTilePix / 32];
+  __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
+  __shared__ float2 s_e[kTilePix];                                  // box half extents
+  __shared__ double s_red[kTilePix / 32];
   __shared__ int s_last;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -406,6 +428,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dd = 0.f, oo = 0.f, rm = 0.f;
   int lastk = 0;
+  unsigned n_eval = 0, n_contrib = 0;
   bool done = !inside;
   const float fpx = (float)px, fpy = (float)py;
   for (uint32_t base = s; base < e; base += kTilePix) {
@@ -414,7 +437,10 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     const uint32_t id = k < e ? (own_sort ? (uint32_t)s_key[k - s] : ws.sorted_ids[k]) : 0u;
     if (k < e && DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n && k < (uint64_t)ws.max_pairs, ws.counters + CNT_STATUS)) {
       const size_t slot = vbase + id;
-      s_a[tid] = ws.rec2d[slot * 3 + 0];
+      const float4 r0 = ws.rec2d[slot * 3 + 0];
+      const float2 lo = ws.rec_lo[slot];
+      s_a[tid] = make_float4(r0.x, r0.y, lo.x, lo.y);
+      s_e[tid] = make_float2(r0.z, r0.w);
       s_b[tid] = ws.rec2d[slot * 3 + 1];
       s_c[tid] = ws.rec2d[slot * 3 + 2];
     }
@@ -427,7 +453,8 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
       bool hit = false;
       if (jj < cnt) {
         const float4 a = s_a[jj];
-        hit = fabsf(a.x - bcx) <= a.z + 3.5f && fabsf(a.y - bcy) <= a.w + 1.5f;
+        const float2 ex = s_e[jj];
+        hit = fabsf(a.x - bcx) <= ex.x + 3.5f && fabsf(a.y - bcy) <= ex.y + 1.5f;
       }
       unsigned mask = __ballot_sync(FULL, hit);
       while (mask) {
@@ -435,9 +462,11 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
         mask &= mask - 1;
         if (done) continue;
         const float4 a = s_a[j], b = s_b[j];
-        const float dx = a.x - fpx, dy = a.y - fpy;
+        const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
         const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+        ++n_eval;
         if (p < r.log2_alpha_min) continue;               // alpha < alpha_min
+        ++n_contrib;
         const float alpha = fminf(r.alpha_max, hw_exp2(p));
         const float tt = T * (1.f - alpha);
         if (tt < r.t_min) { done = true; continue; }
@@ -453,6 +482,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     }
   }
 
+  add_eval_counts(ws, 0, n_eval, n_contrib);
   float lpx = 0.f;
   if (inside) {
     const size_t P = (size_t)r.W * r.H;
@@ -472,11 +502,13 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     last[(size_t)v * P + pix] = lastk;
   }
   if (!loss) return;
-  lpx = warp_sum(lpx);
-  if ((tid & 31) == 0) s_red[tid >> 5] = lpx;
+  // the tile's 256 pixel losses are summed in FP64 (fixed shuffle tree, then
+  // the 8 warps in order)
+  const double lsum = warp_sum_d((double)lpx);
+  if ((tid & 31) == 0) s_red[tid >> 5] = lsum;
   __syncthreads();
   if (tid == 0) {
-    float t = 0.f;
+    double t = 0.0;
     for (int w = 0; w < kTilePix / 32; ++w) t += s_red[w];
     ws.loss_partial[tile] = t;
     __threadfence();
@@ -491,7 +523,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   __shared__ double s_d[kTilePix];
   const int np = views * r.T;
   double acc = 0.0;
-  for (int k = tid; k < np; k += kTilePix) acc += (double)__ldcg(ws.loss_partial + k);
+  for (int k = tid; k < np; k += kTilePix) acc += __ldcg(ws.loss_partial + k);
   s_d[tid] = acc;
   __syncthreads();
   for (int o = kTilePix / 2; o > 0; o >>= 1) {

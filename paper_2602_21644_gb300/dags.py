@@ -89,13 +89,22 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
            "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
            "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp",
-           "epipolar_verify"]
+           "epipolar_verify", "dags_eval_counting", "dags_eval_read", "dags_measure_alu"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
            "regulariser", "epipolar"]
 
 _lib = None
+
+
+def measure_alu(kind: int, iters: int = 1 << 14):
+    """Measured lane operations per second of the current device's FP32 FMA
+    (kind 0) or ex2.approx (kind 1) pipe, and the timed launch's ms."""
+    lib = load()
+    ops, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.dags_measure_alu(int(kind), int(iters), ctypes.byref(ops), ctypes.byref(ms)), "dags_measure_alu")
+    return ops.value, ms.value
 
 
 def load(path: str = LIB_PATH):
@@ -135,6 +144,12 @@ def load(path: str = LIB_PATH):
     lib.dags_timing_enable.restype = ctypes.c_int
     lib.dags_timing_read.argtypes = [P, P, P, I32]
     lib.dags_timing_read.restype = ctypes.c_int
+    lib.dags_eval_counting.argtypes = [P, I32]
+    lib.dags_eval_counting.restype = ctypes.c_int
+    lib.dags_eval_read.argtypes = [P, P]
+    lib.dags_eval_read.restype = ctypes.c_int
+    lib.dags_measure_alu.argtypes = [I32, I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.dags_measure_alu.restype = ctypes.c_int
     lib.splat_track.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
                                 ctypes.POINTER(CLossCfg), ctypes.POINTER(CPoseCfg), I32, P, P, P, P, P, I32, P]
     lib.splat_track.restype = ctypes.c_int
@@ -318,6 +333,17 @@ class Context:
         _check(self.lib.dags_timing_read(self.h, ms.ctypes.data_as(ctypes.c_void_p),
                                          n.ctypes.data_as(ctypes.c_void_p), k), "dags_timing_read")
         return {KERNELS[i]: (float(ms[i]), int(n[i])) for i in range(k)}
+
+    def eval_counting(self, enable: bool):
+        """Count the compositing kernels' evaluations (see eval_read)."""
+        _check(self.lib.dags_eval_counting(self.h, int(bool(enable))), "dags_eval_counting")
+
+    def eval_read(self):
+        """{fwd_eval, fwd_contrib, bwd_eval, bwd_contrib} accumulated since the last read."""
+        import numpy as np
+        c = np.zeros(4, np.int64)
+        _check(self.lib.dags_eval_read(self.h, c.ctypes.data_as(ctypes.c_void_p)), "dags_eval_read")
+        return dict(zip(("fwd_eval", "fwd_contrib", "bwd_eval", "bwd_contrib"), (int(x) for x in c)))
 
     def copy_bins(self, views: int, cam: Camera):
         """(tile_start [views*T+1] uint32, ids [pairs] uint32) of the last forward."""

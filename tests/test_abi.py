@@ -85,7 +85,8 @@ def test_entry_points_reject_a_null_context():
     # any CUDA call: a NULL context is DAGS_E_INVAL (-1), with nothing launched
     from paper_2602_21644_gb300 import dags
     lib = dags.load()
-    host_only = {"dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "splat_forward_static"}
+    host_only = {"dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "splat_forward_static",
+                 "dags_measure_alu"}
     checked = []
     for name in dags.EXPORTS:
         if name in host_only or name.startswith("dags_default_"):
@@ -96,6 +97,12 @@ def test_entry_points_reject_a_null_context():
         checked.append(name)
     assert len(checked) >= 20
     lib.dags_destroy(None)             # destroying NULL is a no-op
+    # the ALU probe takes no context; its arguments are checked first too
+    ops = ctypes.c_double()
+    assert lib.dags_measure_alu(2, 1024, ctypes.byref(ops), None) == -1
+    assert lib.dags_measure_alu(0, 0, ctypes.byref(ops), None) == -1
+    assert lib.dags_measure_alu(1, 1 << 25, ctypes.byref(ops), None) == -1
+    assert lib.dags_measure_alu(0, 1024, None, None) == -1
 
 
 def test_static_forward_limits_are_checked_on_the_host():

@@ -64,7 +64,7 @@ def test_single_isotropic_on_axis_closed_form():
     G = gauss_row((0, 0, z), s, q / np.linalg.norm(q) * 3.0, logit, mp)[None]
     r = oracle.render(G, cam, ident())
     var = (f * s / z) ** 2 + 0.3
-    exp, ag = expected_single(W, H, 23.3, 19.6, var * np.eye(2), sigmoid(logit), G[0, 12:15], z, mp)
+    exp, ag = expected_single(W, H, cam[2], cam[3], var * np.eye(2), sigmoid(logit), G[0, 12:15], z, mp)
     keep = np.abs(ag - 1 / 255) > 1e-9
     np.testing.assert_allclose(r["pix"][keep, :7], exp[keep, :7], rtol=1e-12, atol=1e-14)
 
@@ -84,7 +84,7 @@ def test_anisotropic_rotated_about_axis(theta_deg):
     r = oracle.render(G, cam, ident())
     R2 = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
     cov = (f / z) ** 2 * R2 @ np.diag([sx ** 2, sy ** 2]) @ R2.T + 0.3 * np.eye(2)
-    exp, ag = expected_single(W, H, 31.7, 24.2, cov, sigmoid(2.0), G[0, 12:15], z, 0.3)
+    exp, ag = expected_single(W, H, cam[2], cam[3], cov, sigmoid(2.0), G[0, 12:15], z, 0.3)
     keep = (np.abs(ag - 1 / 255) > 1e-9) & (np.abs(ag - 0.99) > 1e-9)
     np.testing.assert_allclose(r["pix"][keep, :7], exp[keep, :7], rtol=1e-11, atol=1e-13)
 
