@@ -238,20 +238,51 @@ def algorithmic_bytes(n, nv, K, P):
             "pose_step": 6 * 8 + 13 * 8 * 2 + 12 * 8 * 2}
 
 
-# FP32 operations per pixel-Gaussian evaluation of the compositing loops
-# (an exp2 counted as one): forward alpha, transmittance and five
-# accumulations; backward alpha and T recovery, dL/dalpha over six channels,
-# suffix sums and the chain to the conic, mean, opacity, colour, depth, MP
-OPS_FWD, OPS_BWD = 16, 41
-# the LM Jacobian compositing: the forward's 16, 10 shared per evaluation
-# (exponent gradient, squared offsets, ln2 alpha) and 14 per twist direction
-# (the exponent's tangent 5, alpha' 1, the weight's tangent 2, four channel
-# accumulations 5, T' 1) over six directions
+# FP32 lane operations of the compositing loops (the method's arithmetic; an
+# exp2 or a reciprocal counts as one), per evaluated exponent: the pixel
+# offset 2, the quadratic form 6 and the alpha_min test 1; per contribution
+# (alpha >= alpha_min): forward alpha, its clamp, 1 - alpha, the new T and its
+# test, the weight and six accumulations (12); backward alpha, its clamp,
+# 1/(1 - alpha), the transmittance recovery, the weight, dL/dalpha over six
+# channels with its suffix term, the chain to centre, conic and depth, the
+# suffix update and the warp sums of the six gradient words (39). The
+# evaluation and contribution counts are counted by the kernels themselves.
+OPS_EVAL, OPS_FWD_CONTRIB, OPS_BWD_CONTRIB = 9, 12, 39
+# special-function operations per contribution: forward exp2; backward exp2
+# and the reciprocal of 1 - alpha
+SFU_FWD_CONTRIB, SFU_BWD_CONTRIB = 1, 2
+# the LM Jacobian compositing, per listed evaluation: the forward's 16, 10
+# shared per evaluation (exponent gradient, squared offsets, ln2 alpha) and 14
+# per twist direction (the exponent's tangent 5, alpha' 1, the weight's
+# tangent 2, four channel accumulations 5, T' 1) over six directions
 OPS_JAC = 16 + 10 + 6 * 14
-# DRAM bytes (read + write) per launch at this workload, from one ncu capture
-# of each kernel; None where the kernel has changed since its capture
-# (render_bwd: 19,880,192 bytes before its 6- and 10-value reduce-scatter)
-DRAM_TRAFFIC = {"render_fwd": 9209600, "render_bwd": None}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+
+
+def committed_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu summary, or (None, why) when there is no capture or the
+    kernel's source file has changed since it was taken (the file records the
+    source's SHA-256)."""
+    import hashlib
+    if not os.path.exists(TRAFFIC_FILE):
+        return None, "no committed capture"
+    for line in open(TRAFFIC_FILE):
+        if line.startswith("#") or "|" not in line:
+            continue
+        f = [x.strip() for x in line.split("|")]
+        if len(f) < 5 or f[0] != kernel or f[1] != workload:
+            continue
+        src = os.path.join(ROOT, f[3])
+        if not os.path.exists(src):
+            return None, f"source {f[3]} missing"
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if sha != f[4]:
+            return None, f"{f[3]} changed since the capture"
+        return int(f[2]), f"ncu capture of this source ({f[3]} sha256 {sha})"
+    return None, "no committed capture of this kernel and workload"
+
+
 ALU_LANES = 152 * 128          # FP32 lanes: 152 SMs x 128
 MPNET_FLOP_PER_PX = 2 * (8 * 32 + 288 * 32 + 32 * 32 + 32)   # 21,056: the network's multiply-adds x 2
 
@@ -696,6 +727,9 @@ def run_ours(args):
     start_bins, ids = ctx.copy_bins(1, cam)
     K = int(len(ids))
     nv = int(len(np.unique(ids)))
+    # measured FP32 FMA and ex2 lane rates (T ops/s) for the ALU roofline
+    alu_peak = max(dags.measure_alu(0, 1 << 15)[0] for _ in range(3)) / 1e12
+    sfu_peak = max(dags.measure_alu(1, 1 << 13)[0] for _ in range(3)) / 1e12
 
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
@@ -728,10 +762,16 @@ def run_ours(args):
     value = replica_throughput(args.iters, args.steps, world, t_ms)
 
     # per-kernel device times: the same steps with every kernel launched
-    # directly (no graph) between a pair of CUDA events on its stream
+    # directly (no graph) between a pair of CUDA events on its stream; the
+    # compositing kernels also count the exponents they evaluate and the
+    # contributions among them (one atomic per warp and counter)
     ctx.timing_read()
+    ctx.eval_read()
+    ctx.eval_counting(True)
     t_direct = timed(args.steps, lambda: frame(use_graph=False), timing=True)
+    ctx.eval_counting(False)
     kt = ctx.timing_read()
+    evals = ctx.eval_read()
 
     # e2e: public API with host buffers; every step copies the frame (RGB-D
     # target) and the starting pose from pinned host memory and reads back the
@@ -765,7 +805,7 @@ def run_ours(args):
     variants = splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, flush, stream)
     lm = lm_section(args, ctx, dags, gauss, cam, tg_all[0, 0].contiguous(), pose_all[0, 0].contiguous(),
                     torch.from_numpy(np.ascontiguousarray(seq[0]["gt_pose"])).to(dev), pcfg, flush, stream,
-                    ALU_LANES * float(load_peaks()[0].get("sm_max_mhz", 2070.0)) * 1e6 / 1e12)
+                    alu_peak)
 
     peaks, src = load_peaks()
     hbm = float(peaks["hbm_gbs"])
@@ -779,31 +819,43 @@ def run_ours(args):
             if name in ab:
                 kernels[name]["alg_bytes"] = ab[name]
                 kernels[name]["hbm_frac"] = round(ab[name] / (avg_us * 1e-6) / 1e9 / hbm, 4)
-    # the compositing kernels are ALU-bound: E pixel-Gaussian evaluations per
-    # launch (every list entry up to each pixel's last contributor, read from
-    # the forward's per-pixel count), OPS_* FP32 operations per evaluation,
-    # against the FP32 lane peak at the maximum SM clock
-    E = int(last.to(torch.int64).sum().item())
-    alu_peak = ALU_LANES * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-    for name, ops in (("render_fwd", OPS_FWD), ("render_bwd", OPS_BWD)):
+    # the compositing kernels are ALU-bound: per launch, E_eval evaluated
+    # exponents and E_contrib contributions (counted by the kernels), OPS_*
+    # FP32 lane operations per unit, against the measured FMA lane rate;
+    # E_listed (every list entry up to each pixel's last contributor) is
+    # reported beside them
+    E_listed = int(last.to(torch.int64).sum().item())
+    n_fwd = max(1, kt.get("render_fwd", (0, 0))[1])
+    n_bwd = max(1, kt.get("render_bwd", (0, 0))[1])
+    per = {"render_fwd": (evals["fwd_eval"] / n_fwd, evals["fwd_contrib"] / n_fwd, OPS_FWD_CONTRIB, SFU_FWD_CONTRIB),
+           "render_bwd": (evals["bwd_eval"] / n_bwd, evals["bwd_contrib"] / n_bwd, OPS_BWD_CONTRIB, SFU_BWD_CONTRIB)}
+    for name, (ee, ec, oc, sc) in per.items():
         if name in kernels:
             t_s = kernels[name]["avg_us"] * 1e-6
-            kernels[name]["evaluations"] = E
-            kernels[name]["alu_tops"] = round(E * ops / t_s / 1e12, 3)
-            kernels[name]["alu_frac"] = round(E * ops / t_s / 1e12 / alu_peak, 4)
+            ops = OPS_EVAL * ee + oc * ec
+            kernels[name].update({"evaluations_performed": int(round(ee)), "contributions": int(round(ec)),
+                                  "evaluations_listed": E_listed, "alg_ops": int(round(ops)),
+                                  "alu_tops": round(ops / t_s / 1e12, 3),
+                                  "alu_frac": round(ops / t_s / 1e12 / alu_peak, 4),
+                                  "sfu_frac": round(sc * ec / t_s / 1e12 / sfu_peak, 4)})
     modelled = [k for k in kernels if k in ab]
     dom = max(modelled, key=lambda k: kt[k][0]) if modelled else None
     roof = None
+    workload = f"tracking {args.gaussians // 1000}k {args.width}x{args.height}"
     if dom in ("render_fwd", "render_bwd"):
-        ops = OPS_FWD if dom == "render_fwd" else OPS_BWD
         ach = kernels[dom]["alu_tops"]
+        traffic, tnote = committed_traffic({"render_fwd": "render_fwd_kernel",
+                                            "render_bwd": "render_bwd_kernel<pose-only>"}[dom], workload)
+        ee, ec, oc, _ = per[dom]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / alu_peak, 4),
-                "traffic": DRAM_TRAFFIC.get(dom) if (args.width, args.height, args.gaussians) == (640, 480, 300_000)
-                else None,
-                "peak_source": f"derived: {ALU_LANES} FP32 lanes x {src} sm_max_mhz",
-                "alg_ops_per_launch": E * ops, "ops_per_evaluation": ops, "evaluations_per_launch": E,
-                "hbm_frac": kernels[dom].get("hbm_frac")}
+                "frac": round(ach / alu_peak, 4), "traffic": traffic, "traffic_source": tnote,
+                "peak_source": "measured in this run: FP32 FMA lane operations/s (dags_measure_alu), "
+                               "one FMA counted as one operation",
+                "alg_ops_per_launch": kernels[dom]["alg_ops"], "ops_per_evaluation": OPS_EVAL,
+                "ops_per_contribution": oc, "evaluations_performed": int(round(ee)),
+                "contributions": int(round(ec)), "evaluations_listed": E_listed,
+                "alg_bytes_per_launch": ab[dom], "hbm_frac": kernels[dom].get("hbm_frac"),
+                "sfu_frac": kernels[dom]["sfu_frac"], "sfu_peak": round(sfu_peak, 2)}
     elif dom:
         avg_s = kernels[dom]["avg_us"] * 1e-6
         ach = ab[dom] / avg_s / 1e9
@@ -825,6 +877,9 @@ def run_ours(args):
                                        "frac": round(iter_bytes / (iter_us * 1e-6) / 1e9 / hbm, 4),
                                        "peak_gbs": hbm, "pairs_K": K, "visible_Nv": nv, "pixels_P": P},
             "roofline": roof, "kernels": kernels, "gpu_launches": gpu_launches,
+            "alu_peaks_measured": {"fp32_fma_tops": round(alu_peak, 3), "ex2_tops": round(sfu_peak, 3),
+                                   "derived_fp32_lanes_at_max_clock": round(ALU_LANES * float(
+                                       peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12, 3)},
             "kernel_timing": {"how": "same steps, kernels launched directly by the library with a CUDA event "
                                      "pair around each on its stream; value above is from CUDA-graph replay",
                               "ms_per_step_direct": round(t_direct / args.steps, 4)},
