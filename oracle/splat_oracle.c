@@ -455,17 +455,56 @@ static void build_cells(int64_t n, const proj_t *P, const int64_t *order, int W,
   }
 }
 
+/* The adjoint of one pixel's front-to-back compositing, back to front:
+ * given the upstream gradients gF of its six composited channels and its
+ * contributor list, ADDS each contributor's gradients of (u, v, a, b, c, o,
+ * z, colour) to g2 (10 per Gaussian). With S the channels' sums over the
+ * contributors behind k, d/d alpha_k = sum_ch gF_ch (f_ch T_k - S_ch /
+ * (1 - alpha_k)); a clamped alpha passes nothing to its exponent. */
+static void adjoint_pixel(const contrib_t *list, int64_t nl, const proj_t *P, const double *G,
+                          const double *gF, double *g2) {
+  double S[6] = {0, 0, 0, 0, 0, 0}; /* sum over later contributors */
+  for (int64_t k = nl - 1; k >= 0; k--) {
+    const contrib_t *e = &list[k];
+    const proj_t *p = &P[e->id];
+    const double *g = G + e->id * G_STRIDE;
+    double f[6] = {g[G_CR], g[G_CG], g[G_CB], p->p[2], 1.0, g[G_MP]};
+    double wk = e->alpha * e->T;
+    double dal = 0;
+    for (int ch = 0; ch < 6; ch++)
+      dal += gF[ch] * (f[ch] * e->T - S[ch] / (1.0 - e->alpha));
+    double *gg = g2 + e->id * 10;
+    gg[7] += gF[0] * wk;
+    gg[8] += gF[1] * wk;
+    gg[9] += gF[2] * wk;
+    gg[6] += gF[3] * wk;
+    if (!e->clamped) {
+      gg[5] += dal * e->G;
+      double dpw = dal * e->alpha;
+      gg[0] += dpw * (-(p->a * e->dx + p->b * e->dy));
+      gg[1] += dpw * (-(p->b * e->dx + p->c * e->dy));
+      gg[2] += dpw * (-0.5 * e->dx * e->dx);
+      gg[3] += dpw * (-e->dx * e->dy);
+      gg[4] += dpw * (-0.5 * e->dy * e->dy);
+    }
+    for (int ch = 0; ch < 6; ch++) S[ch] += f[ch] * wk;
+  }
+}
+
 /* Render one view: out_px[P * PX_STRIDE], out_flags[P]; if targets
  * (P x 4: r, g, b, depth) is given, the loss goes to *loss and, if grads /
  * pose_grad are non-NULL, the adjoint is ADDED to grads[n * G_STRIDE] and
  * written to pose_grad[6] = (rho, phi) of the left-perturbation twist.
  * wfix (P, or NULL) replaces the static weight w(u) by given constants, so
  * that finite differences can check the stop-gradient adjoint.
+ * upstream (P x 6, or NULL) replaces the loss: the adjoint is that of
+ * sum_u upstream[u] . (C_r, C_g, C_b, D, O, R_MP)(u), a caller's gradient of
+ * its own function of the composited channels (targets are then unused).
  * Returns 0, or -1 on allocation failure. */
 int oracle_render(int64_t n, const double *G, const double *cam, const double *pose,
                   const double *rc, const double *lc, const double *targets, const double *wfix,
-                  int accel, double *out_px, int32_t *out_flags, double *loss, double *grads,
-                  double *pose_grad) {
+                  const double *upstream, int accel, double *out_px, int32_t *out_flags, double *loss,
+                  double *grads, double *pose_grad) {
   int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
   proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
   zkey_t *zk = (zkey_t *)malloc(sizeof(zkey_t) * (size_t)(n > 0 ? n : 1));
@@ -481,7 +520,8 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
   cells_t cs;
   build_cells(nv, P, order, W, H, 8, accel, &cs);
 
-  const int want_grad = (targets != NULL) && (grads != NULL || pose_grad != NULL);
+  if (upstream) targets = NULL;
+  const int want_grad = (targets != NULL || upstream != NULL) && (grads != NULL || pose_grad != NULL);
   /* per-Gaussian accumulated 2D gradients: u, v, a, b, c, o, z, cr, cg, cb */
   double *g2 = want_grad ? (double *)calloc((size_t)(n > 0 ? n : 1) * 10, sizeof(double)) : NULL;
   int64_t cap = 256;
@@ -538,6 +578,12 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
       for (int k = 0; k < 6; k++) o[k] = acc[k];
       o[PX_T] = T; o[PX_N] = (double)nl; o[PX_LAST] = (double)last; o[PX_W] = 0.0;
 
+      if (upstream && want_grad && nl > 0) {
+        /* the caller's upstream gradients of the six composited channels */
+        double gF[6];
+        for (int k = 0; k < 6; k++) gF[k] = upstream[pix * 6 + k];
+        adjoint_pixel(list, nl, P, G, gF, g2);
+      }
       if (targets) {
         const double *tg = targets + pix * 4;
         double O = acc[4], Rm = acc[5];
@@ -583,32 +629,7 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
               gF[4] += lw; gF[5] += -lw;
             }
           }
-          double S[6] = {0, 0, 0, 0, 0, 0}; /* sum over later contributors */
-          for (int64_t k = nl - 1; k >= 0; k--) {
-            const contrib_t *e = &list[k];
-            const proj_t *p = &P[e->id];
-            const double *g = G + e->id * G_STRIDE;
-            double f[6] = {g[G_CR], g[G_CG], g[G_CB], p->p[2], 1.0, g[G_MP]};
-            double wk = e->alpha * e->T;
-            double dal = 0;
-            for (int ch = 0; ch < 6; ch++)
-              dal += gF[ch] * (f[ch] * e->T - S[ch] / (1.0 - e->alpha));
-            double *gg = g2 + e->id * 10;
-            gg[7] += gF[0] * wk;
-            gg[8] += gF[1] * wk;
-            gg[9] += gF[2] * wk;
-            gg[6] += gF[3] * wk;
-            if (!e->clamped) {
-              gg[5] += dal * e->G;
-              double dpw = dal * e->alpha;
-              gg[0] += dpw * (-(p->a * e->dx + p->b * e->dy));
-              gg[1] += dpw * (-(p->b * e->dx + p->c * e->dy));
-              gg[2] += dpw * (-0.5 * e->dx * e->dx);
-              gg[3] += dpw * (-e->dx * e->dy);
-              gg[4] += dpw * (-0.5 * e->dy * e->dy);
-            }
-            for (int ch = 0; ch < 6; ch++) S[ch] += f[ch] * wk;
-          }
+          adjoint_pixel(list, nl, P, G, gF, g2);
         }
       }
       out_flags[pix] = flags;
