@@ -499,6 +499,41 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   return cuda_status(e);
 }
 
+int splat_backward_upstream(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam,
+                            const double *poses, int32_t n_views, const dags_raster_cfg *rcfg, const float *image,
+                            const int32_t *last, const float *grad_image, uint32_t grad_flags, float *grad_gauss,
+                            double *grad_pose, void *stream) {
+  NvtxRange nv("splat_backward_upstream");
+  int rc = common_args(ctx, gauss, n, cam, poses, n_views);
+  if (rc) return rc;
+  if (!image || !last || !grad_image) return DAGS_E_INVAL;
+  if ((grad_flags & ~(DAGS_GRAD_GAUSS | DAGS_GRAD_POSE)) || !grad_flags) return DAGS_E_INVAL;
+  if ((grad_flags & DAGS_GRAD_GAUSS) && !grad_gauss && n > 0) return DAGS_E_INVAL;
+  if ((grad_flags & DAGS_GRAD_POSE) && !grad_pose) return DAGS_E_INVAL;
+  if (((uintptr_t)grad_gauss & 15u) != 0) return DAGS_E_INVAL;
+  if (ctx->fwd_image != image || ctx->fwd_last != last || ctx->fwd_gauss != gauss || ctx->fwd_n != n ||
+      ctx->fwd_views != n_views || ctx->fwd_w != cam->width || ctx->fwd_h != cam->height)
+    return DAGS_E_ORDER;
+  Raster r;
+  Loss l;
+  if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(nullptr, &l))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const bool full = (grad_flags & DAGS_GRAD_GAUSS) != 0;
+  KernelTimer &tm = ctx->timer;
+  int ev = tm.begin(DAGS_K_RENDER_BWD, s);
+  cudaError_t e = launch_render_bwd(ctx->ws, n_views, n, r, l, nullptr, image, last, full, s, grad_image);
+  tm.end(ev, s);
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_PREPROCESS_BWD, s);
+    e = launch_preprocess_bwd(ctx->ws, reinterpret_cast<const float4 *>(gauss), n, n_views, r,
+                              full ? grad_gauss : nullptr, (grad_flags & DAGS_GRAD_POSE) ? grad_pose : nullptr,
+                              PoseStep(), s);
+    tm.end(ev, s);
+  }
+  return cuda_status(e);
+}
+
 int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state, int32_t n_views,
               const dags_pose_cfg *cfg, void *stream) {
   NvtxRange nv("pose_step");

@@ -141,9 +141,11 @@ cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster 
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s);
+// upstream (V x 6 x P, or null): a caller's gradients of the composited
+// channels (C_r, C_g, C_b, D, O, R_MP) used in place of the loss's
 cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, const float *image, const int32_t *last, bool full,
-                              cudaStream_t s);
+                              cudaStream_t s, const float *upstream = nullptr);
 cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int64_t n, int views,
                                   const Raster &r, float *grad_gauss, double *grad_pose, const PoseStep &ps,
                                   cudaStream_t s);
@@ -383,6 +385,56 @@ __device__ __forceinline__ bool project_gaussian(const float4 &g0, const float4 
   q.u = r.fx * q.x / q.z + r.cx;
   q.v = r.fy * q.y / q.z + r.cy;
   return true;
+}
+
+// Error-free transformations of FP32 sums and products (Knuth's two-sum,
+// and the fused multiply-add form of Dekker's two-product): a op b = s + e
+// exactly. Every operation is explicitly rounded, so nothing is contracted.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+}
+
+// One row of the FP64 pose applied to an FP32 mean, in double-FP32
+// arithmetic: (ph + pl) . m + (th + tl) = hi + lo with a relative error of a
+// few 2^-44 of the largest term. ph, pl: the row's rotation entries split
+// into FP32 high and low parts; th, tl: its translation.
+__device__ __forceinline__ void df_row(const float *ph, const float *pl, float th, float tl, float mx, float my,
+                                       float mz, float &hi, float &lo) {
+  float p0, e0, p1, e1, p2, e2, s, t;
+  two_prod(ph[0], mx, p0, e0);
+  two_prod(ph[1], my, p1, e1);
+  two_prod(ph[2], mz, p2, e2);
+  float acc = __fadd_rn(__fadd_rn(e0, e1), e2);
+  acc = __fadd_rn(acc, __fadd_rn(__fadd_rn(__fmul_rn(pl[0], mx), __fmul_rn(pl[1], my)), __fmul_rn(pl[2], mz)));
+  two_sum(p0, p1, s, t);
+  acc = __fadd_rn(acc, t);
+  two_sum(s, p2, s, t);
+  acc = __fadd_rn(acc, t);
+  two_sum(s, th, s, t);
+  acc = __fadd_rn(acc, __fadd_rn(t, tl));
+  two_sum(s, acc, hi, lo);
+}
+
+// The projected centre u = f x / z + c in double-FP32 from x = xh + xl,
+// z = zh + zl: the quotient's high part, its remainder through a fused
+// multiply-add, then f q + c with two-product and two-sum.
+__device__ __forceinline__ void df_project(float xh, float xl, float zh, float zl, float f, float c, float &uh,
+                                           float &ul) {
+  const float qh = __fdiv_rn(xh, zh);
+  // x - qh z = (xh - qh zh) + xl - qh zl; the first term is exact by FMA
+  const float rem = __fadd_rn(__fsub_rn(__fmaf_rn(-qh, zh, xh), __fmul_rn(qh, zl)), xl);
+  const float ql = __fdiv_rn(rem, zh);
+  float p, pe, s, se;
+  two_prod(f, qh, p, pe);
+  two_sum(p, c, s, se);
+  const float lo = __fadd_rn(__fadd_rn(pe, __fmul_rn(f, ql)), se);
+  two_sum(s, lo, uh, ul);
 }
 
 // Does the ellipse Q(d) = A2 dx^2 + B2 dx dy + C2 dy^2 <= thr (centre (u, v);

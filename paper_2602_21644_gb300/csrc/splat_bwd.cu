@@ -29,7 +29,8 @@ static_assert(G2_U == 0 && G2_Z == 5 && G2_BL == 9 && kGradWords >= 10, "2D-grad
 template <bool FULL>
 __global__ void __launch_bounds__(kTilePix)
 render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ targets,
-                  const float *__restrict__ image, const int32_t *__restrict__ last) {
+                  const float *__restrict__ image, const int32_t *__restrict__ last,
+                  const float *__restrict__ upstream) {
   pdl_wait();
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
   __shared__ float2 s_e[kTilePix];                                  // box half extents
@@ -58,7 +59,15 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   float T = 1.f;
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f, g4 = 0.f, g5 = 0.f;  // upstream per channel
   int lastp = 0;
-  if (inside) {
+  if (inside && upstream) {
+    // the caller's gradients of its own function of the six composited
+    // channels take the place of the loss's
+    const size_t pix = (size_t)py * r.W + px;
+    const float *up = upstream + (size_t)v * 6 * P + pix;
+    g0 = up[0]; g1 = up[P]; g2 = up[2 * P]; g3 = up[3 * P]; g4 = up[4 * P]; g5 = up[5 * P];
+    T = image[(size_t)v * DAGS_IMG_CHANNELS * P + 6 * P + pix];
+    lastp = last[(size_t)v * P + pix];
+  } else if (inside) {
     // a pixel whose target has negative red is outside the loss (no gradient)
     const size_t pix = (size_t)py * r.W + px;
     const float *img = image + (size_t)v * DAGS_IMG_CHANNELS * P + pix;
@@ -413,11 +422,14 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
 
 cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, const float *image, const int32_t *last, bool full,
-                              cudaStream_t s) {
+                              cudaStream_t s, const float *upstream) {
   (void)n;
   const unsigned grid = (unsigned)(views * r.T);
-  if (full) return launch_pdl(render_bwd_kernel<true>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last);
-  return launch_pdl(render_bwd_kernel<false>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last);
+  if (full)
+    return launch_pdl(render_bwd_kernel<true>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last,
+                      upstream);
+  return launch_pdl(render_bwd_kernel<false>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last,
+                    upstream);
 }
 
 cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int64_t n, int views,

@@ -247,7 +247,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
   pdl_wait();
   __shared__ float sp[kMaxViewsSmem * 12];
-  __shared__ double spd[kMaxViewsSmem * 12];
+  __shared__ float spl[kMaxViewsSmem * 12];   // FP32 remainders of the FP64 poses
   const int v = blockIdx.y;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   // the record loads are issued before the pose barrier, so that the two
@@ -261,8 +261,9 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   }
   for (int k = threadIdx.x; k < views * 12; k += blockDim.x) {
     const double pk = poses[k];
-    spd[k] = pk;
-    sp[k] = (float)pk;
+    const float hi = __double2float_rn(pk);
+    sp[k] = hi;
+    spl[k] = __double2float_rn(pk - (double)hi);
   }
   __syncthreads();
   if (blockIdx.x == 0 && blockIdx.y == 0)
@@ -279,19 +280,16 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     uint2 rect = make_uint2(0u, 0u);
     Proj q;
     if (project_gaussian(g0, g1, g2, P, r, q)) {
-      // the centre in FP64 from the FP64 pose, split into FP32 hi + lo
+      // the centre from the FP64 pose in double-FP32 arithmetic (a few
+      // 2^-44 relative), split into FP32 hi + lo
       {
-        const double *Pd = spd + v * 12;
-        const double mx = g0.x, my = g0.y, mz = g0.z;
-        const double xd = Pd[0] * mx + Pd[1] * my + Pd[2] * mz + Pd[3];
-        const double yd = Pd[4] * mx + Pd[5] * my + Pd[6] * mz + Pd[7];
-        const double zd = Pd[8] * mx + Pd[9] * my + Pd[10] * mz + Pd[11];
-        const double izd = 1.0 / zd;
-        const double ud = (double)r.fx * xd * izd + (double)r.cx;
-        const double vd = (double)r.fy * yd * izd + (double)r.cy;
-        q.u = __double2float_rn(ud);
-        q.v = __double2float_rn(vd);
-        ulo = make_float2(__double2float_rn(ud - (double)q.u), __double2float_rn(vd - (double)q.v));
+        const float *Ph = sp + v * 12, *Pl = spl + v * 12;
+        float xh, xl, yh, yl, zh, zl;
+        df_row(Ph, Pl, Ph[3], Pl[3], g0.x, g0.y, g0.z, xh, xl);
+        df_row(Ph + 4, Pl + 4, Ph[7], Pl[7], g0.x, g0.y, g0.z, yh, yl);
+        df_row(Ph + 8, Pl + 8, Ph[11], Pl[11], g0.x, g0.y, g0.z, zh, zl);
+        df_project(xh, xl, zh, zl, r.fx, r.cx, q.u, ulo.x);
+        df_project(yh, yl, zh, zl, r.fy, r.cy, q.v, ulo.y);
       }
       const float lo = log2f(q.o);
       const float thr = lo - r.log2_alpha_min;             // ellipse: Q(d) <= thr
