@@ -183,6 +183,21 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
                    const int32_t *last, uint32_t grad_flags, float *grad_gauss,
                    double *grad_pose, void *stream);
 
+/* Backward of a caller's own function F of the rendered channels through
+ * the preceding splat_forward on this ctx (same gauss, n, cam, poses,
+ * n_views, raster config, image and last; DAGS_E_ORDER otherwise): the
+ * adjoint of the compositing of Eq. (20) and of the projection, with the
+ * upstream gradients given per pixel instead of formed from the loss of
+ * Eqs. (21), (22). Lets a caller put its own loss on C, D, O and R_MP.
+ * grad_image   device, n_views x 6 x H*W floats: dF/dC_r, dF/dC_g, dF/dC_b,
+ *              dF/dD, dF/dO, dF/dR_MP planes (image planes 0-5).
+ * grad_flags, grad_gauss, grad_pose   as for splat_backward (overwritten).
+ * The forward's targets and loss are not used. */
+int splat_backward_upstream(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam,
+                            const double *poses, int32_t n_views, const dags_raster_cfg *rcfg,
+                            const float *image, const int32_t *last, const float *grad_image,
+                            uint32_t grad_flags, float *grad_gauss, double *grad_pose, void *stream);
+
 /* FP64 pose step for n_views poses: Adam on the twist (state per view: 13
  * doubles m[6], v[6], step, device, in/out), then pose <- exp(xi^) pose.
  * poses device in/out n_views x 12; grad device n_views x 6; cfg host.

@@ -1,7 +1,8 @@
-"""torch.autograd wrapper of the splatting path: the forward kernels render and
-reduce the MP-weighted loss of Eqs. (20)-(22); the hand-written adjoint
-kernels give its gradient with respect to the Gaussian records and to the
-camera poses. No arithmetic of the path runs here: both directions call the
+"""torch.autograd wrappers of the splatting path: SplatLoss, whose forward
+kernels render and reduce the MP-weighted loss of Eqs. (20)-(22), and
+SplatRender, which returns the rendered channels for a caller's own loss; the
+hand-written adjoint kernels give the gradients with respect to the Gaussian
+records and to the camera poses. No arithmetic of the path runs here: both directions call the
 library through the C ABI.
 
 Pose gradient convention: the poses are world-to-camera T_CW (V x 12
@@ -51,6 +52,52 @@ class SplatLoss(torch.autograd.Function):
         if gp is not None:
             gp = gp * s
         return gg, gp, None, None, None, None, None, None
+
+
+class SplatRender(torch.autograd.Function):
+    """C, D, O, R_MP = SplatRender.apply(gauss, xi, ctx, cam, poses, rcfg)
+
+    The rendered channels themselves, for a caller's own loss: C [V, 3, H, W],
+    D, O and R_MP [V, H, W] float32. Their gradients go back through the
+    library's adjoint (splat_backward_upstream) to the records and the pose
+    twist xi ([V, 6] float64, all zero)."""
+
+    @staticmethod
+    def forward(fctx, gauss, xi, ctx, cam, poses, rcfg=None):
+        image, last, _ = ctx.forward(gauss, cam, poses, None, rcfg=rcfg)
+        fctx.save_for_backward(gauss, poses, image, last)
+        fctx.dags_ctx, fctx.cam, fctx.rcfg = ctx, cam, rcfg
+        fctx.mark_non_differentiable(last)
+        return image[:, 0:3], image[:, 3], image[:, 4], image[:, 5]
+
+    @staticmethod
+    def backward(fctx, gC, gD, gO, gR):
+        gauss, poses, image, last = fctx.saved_tensors
+        V, _, H, W = image.shape
+        up = torch.zeros((V, 6, H, W), dtype=torch.float32, device=image.device)
+        if gC is not None:
+            up[:, 0:3] = gC
+        for k, g in ((3, gD), (4, gO), (5, gR)):
+            if g is not None:
+                up[:, k] = g
+        flags = 0
+        if fctx.needs_input_grad[0]:
+            flags |= dags.GRAD_GAUSS
+        if fctx.needs_input_grad[1]:
+            flags |= dags.GRAD_POSE
+        gg = gp = None
+        if flags:
+            gg, gp = fctx.dags_ctx.backward_upstream(gauss, fctx.cam, poses, image, last, up, flags=flags,
+                                                     rcfg=fctx.rcfg)
+        return gg, gp, None, None, None, None
+
+
+def splat_render(ctx, cam, gauss, poses, xi=None, rcfg=None):
+    """Differentiable rendering: returns (C, D, O, R_MP); pass xi (zeros,
+    requires_grad) to get the pose-twist gradient of a loss on them."""
+    if xi is None:
+        xi = torch.zeros((poses.shape[0], 6), dtype=torch.float64, device=poses.device)
+    return SplatRender.apply(gauss, xi, ctx, cam, poses, rcfg)
 
 
 def splat_loss(ctx, cam, gauss, poses, targets, xi=None, rcfg=None, lcfg=None):

@@ -89,7 +89,8 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
            "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
            "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp",
-           "epipolar_verify", "dags_eval_counting", "dags_eval_read", "dags_measure_alu"]
+           "epipolar_verify", "dags_eval_counting", "dags_eval_read", "dags_measure_alu",
+           "splat_backward_upstream"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
@@ -136,6 +137,9 @@ def load(path: str = LIB_PATH):
     lib.splat_backward.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, I32, P, ctypes.POINTER(CRasterCfg),
                                    ctypes.POINTER(CLossCfg), P, P, U32, P, P, P]
     lib.splat_backward.restype = ctypes.c_int
+    lib.splat_backward_upstream.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, I32,
+                                            ctypes.POINTER(CRasterCfg), P, P, P, U32, P, P, P]
+    lib.splat_backward_upstream.restype = ctypes.c_int
     lib.pose_step.argtypes = [P, P, P, P, I32, ctypes.POINTER(CPoseCfg), P]
     lib.pose_step.restype = ctypes.c_int
     lib.dags_copy_bins.argtypes = [P, P, I64, P, I64, ctypes.POINTER(I64)]
@@ -403,6 +407,30 @@ class Context:
                                        ctypes.byref(rc), ctypes.byref(lc), _ptr(image), _ptr(last), int(flags),
                                        _ptr(grad_gauss if flags & GRAD_GAUSS else None),
                                        _ptr(grad_pose if flags & GRAD_POSE else None), _stream()), "splat_backward")
+        return (grad_gauss if flags & GRAD_GAUSS else None), (grad_pose if flags & GRAD_POSE else None)
+
+    def backward_upstream(self, gauss, cam: Camera, poses, image, last, grad_image, flags=GRAD_POSE, rcfg=None,
+                          grad_gauss=None, grad_pose=None):
+        """Backward of a caller's function of the rendered channels: grad_image
+        [V, 6, H, W] f32 holds its gradients with respect to image planes 0-5
+        (C_r, C_g, C_b, D, O, R_MP). Returns (grad_gauss, grad_pose) as backward."""
+        _need(grad_image, torch.float32, "grad_image")
+        n = gauss.shape[0]
+        V = poses.shape[0]
+        if tuple(grad_image.shape) != (V, 6, cam.height, cam.width):
+            raise ValueError(f"grad_image must be [{V}, 6, {cam.height}, {cam.width}]")
+        dev = gauss.device
+        if flags & GRAD_GAUSS and grad_gauss is None:
+            grad_gauss = torch.empty((n, GRAD_WORDS), dtype=torch.float32, device=dev)
+        if flags & GRAD_POSE and grad_pose is None:
+            grad_pose = torch.empty((V, 6), dtype=torch.float64, device=dev)
+        c = cam.c()
+        rc = rcfg if rcfg is not None else default_raster_cfg()
+        _check(self.lib.splat_backward_upstream(self.h, _ptr(gauss), n, ctypes.byref(c), _ptr(poses), V,
+                                                ctypes.byref(rc), _ptr(image), _ptr(last), _ptr(grad_image),
+                                                int(flags), _ptr(grad_gauss if flags & GRAD_GAUSS else None),
+                                                _ptr(grad_pose if flags & GRAD_POSE else None), _stream()),
+               "splat_backward_upstream")
         return (grad_gauss if flags & GRAD_GAUSS else None), (grad_pose if flags & GRAD_POSE else None)
 
     def track(self, gauss, cam: Camera, pose, targets, iters, adam_state, image, last, loss, grad_pose,
