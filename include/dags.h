@@ -584,6 +584,7 @@ enum {
   DAGS_K_LM_STEP,          /* LM: FP64 decision, solve and pose step       */
   DAGS_K_REGULARISER,      /* L_MP and L_edge regularisers                 */
   DAGS_K_EPIPOLAR,         /* epipolar verification and static recovery    */
+  DAGS_K_RENDER_TRACK,     /* tracking: fused compositing + pose adjoint   */
   DAGS_KERNEL_COUNT
 };
 int dags_timing_enable(dags_ctx *ctx, int enable);

@@ -92,7 +92,6 @@ struct dags_ctx {
   EpiBuffers epi;                 // epipolar verification, grown on demand
   MpBuffers mp;
   MpnetScratch net;
-  PoseStep fused_step;            // set only inside the tracking loop
   cudaStream_t last_stream = nullptr;
   // the buffers of the latest forward (backward must follow its forward)
   const void *fwd_image = nullptr;
@@ -493,7 +492,7 @@ int splat_backward(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
     ev = tm.begin(DAGS_K_PREPROCESS_BWD, s);
     e = launch_preprocess_bwd(ctx->ws, reinterpret_cast<const float4 *>(gauss), n, n_views, r,
                               full ? grad_gauss : nullptr, (grad_flags & DAGS_GRAD_POSE) ? grad_pose : nullptr,
-                              ctx->fused_step, s);
+                              PoseStep(), s);
     tm.end(ev, s);
   }
   return cuda_status(e);
@@ -556,21 +555,55 @@ int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_sta
 
 namespace {
 
-// Enqueues one tracking iteration: forward with loss, pose-only backward, pose step.
+// Enqueues one tracking iteration: projection and binning, the fused
+// forward + pose-only adjoint, and the chain to the pose twist with the pose
+// step in its last CTA (arguments checked by the caller).
 int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                     const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                     const dags_pose_cfg *pcfg, double *adam_state, float *image, int32_t *last, double *loss,
                     double *grad_pose, cudaStream_t s) {
-  int rc = splat_forward(ctx, gauss, n, cam, pose, 1, targets, rcfg, lcfg, image, last, loss, s);
-  if (rc) return rc;
-  // the pose step runs in the last CTA of the preprocess backward
-  ctx->fused_step.poses = pose;
-  ctx->fused_step.state = adam_state;
-  ctx->fused_step.cfg = *pcfg;
-  rc = splat_backward(ctx, gauss, n, cam, pose, 1, targets, rcfg, lcfg, image, last, DAGS_GRAD_POSE, nullptr,
-                      grad_pose, s);
-  ctx->fused_step = PoseStep();
-  return rc;
+  Raster r;
+  Loss l;
+  int rc;
+  if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
+  ctx->last_stream = s;
+  const Workspace &w = ctx->ws;
+  const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
+  KernelTimer &tm = ctx->timer;
+  // the pose path accumulates 2D-gradient words G2_U .. G2_Z: two float4
+  int ev = tm.begin(DAGS_K_PREPROCESS, s);
+  cudaError_t e = launch_preprocess(w, g4, n, pose, 1, r, 8, s);
+  tm.end(ev, s);
+  if (e == cudaSuccess && n > 0) {
+    ev = tm.begin(DAGS_K_EMIT, s);
+    e = launch_emit(w, n, 1, r, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_RENDER_TRACK, s);
+    e = launch_render_track(w, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    // the pose step runs in the last CTA of the preprocess backward
+    PoseStep ps;
+    ps.poses = pose;
+    ps.state = adam_state;
+    ps.cfg = *pcfg;
+    ev = tm.begin(DAGS_K_PREPROCESS_BWD, s);
+    e = launch_preprocess_bwd(w, g4, n, 1, r, nullptr, grad_pose, ps, s);
+    tm.end(ev, s);
+  }
+  if (e != cudaSuccess) return DAGS_E_CUDA;
+  ctx->fwd_image = image;
+  ctx->fwd_last = last;
+  ctx->fwd_gauss = gauss;
+  ctx->fwd_n = n;
+  ctx->fwd_views = 1;
+  ctx->fwd_w = cam->width;
+  ctx->fwd_h = cam->height;
+  ctx->fwd_tiles = r.T;
+  return DAGS_OK;
 }
 
 template <class T>

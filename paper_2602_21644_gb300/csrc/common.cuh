@@ -151,6 +151,11 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
                                   cudaStream_t s);
 cudaError_t launch_pose_step(double *poses, const double *grad, double *state, int views,
                              const dags_pose_cfg &cfg, cudaStream_t s);
+// Fused forward + pose-only adjoint of one view (splat_track.cu): image,
+// last and the loss as launch_render_fwd writes them, and the 2D gradients of
+// the pose path (words G2_U .. G2_Z) added into ws.grad2d.
+cudaError_t launch_render_track(const Workspace &ws, const Raster &r, const Loss &l, const float4 *targets,
+                                float *image, int32_t *last, double *loss, cudaStream_t s);
 
 // Levenberg-Marquardt pose refinement (lm.cu).
 struct LmBuffers {

@@ -95,3 +95,34 @@ def test_tracking_converges_to_the_pose_that_rendered_the_target(dags):
 
     e0, e1 = err(start), err(t["pose"].cpu().numpy()[0])
     assert e1 < 0.25 * e0, (e0, e1)
+
+
+@pytest.mark.parametrize("size", ["tiny", "full"])
+def test_fused_iteration_equals_separate_forward_and_backward(dags, size):
+    # One tracking iteration with a zero learning rate (the pose stays put)
+    # runs the fused forward + pose adjoint; splat_forward + splat_backward run
+    # the same arithmetic in two kernels. Image and last are bit-identical,
+    # the loss too (the same FP64 tile sums in the same order); the pose
+    # gradient differs by the order of the FP32 atomics only.
+    if size == "tiny":
+        sc = synth.tiny_scene(2)
+    else:
+        sc = synth.tracking_scene(300_000, frame=10, width=640, height=480)
+    cam, t = setup(dags, sc)
+    ctx = dags.Context(sc.records.shape[0], cam.width, cam.height, 1)
+    pcfg = dags.default_pose_cfg(lr=[0.0] * 6)
+    ctx.track(t["gauss"], cam, t["pose"], t["targets"], 1, t["state"], t["image"], t["last"], t["loss"], t["gp"],
+              pcfg=pcfg, use_graph=False)
+    torch.cuda.synchronize()
+    ctx.check()
+    np.testing.assert_array_equal(t["pose"].cpu().numpy(), sc.poses)
+    image, last, loss = ctx.forward(t["gauss"], cam, t["pose"], t["targets"])
+    _, gp = ctx.backward(t["gauss"], cam, t["pose"], t["targets"], image, last, dags.GRAD_POSE)
+    torch.cuda.synchronize()
+    ctx.check()
+    assert torch.equal(image, t["image"])
+    assert torch.equal(last, t["last"])
+    assert loss.item() == t["loss"].item()
+    a, b = t["gp"].cpu().numpy(), gp.cpu().numpy()
+    assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), (a, b)
+    ctx.close()
