@@ -215,15 +215,21 @@ int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_sta
  * exits. Limits: n <= 16384 Gaussians, width and height <= 256, at most
  * 131072 (tile, Gaussian) pairs; larger n, width or height return
  * DAGS_E_INVAL before any launch. The first call on a device resolves the
- * array's device address (cudaGetSymbolAddress) for that device; make that
- * first call before any stream capture. Each call clears the array's
- * counters and leaves its other contents in place; calls whose work
- * overlaps on the GPU (different streams, or devices sharing nothing but
- * this process) race on the shared array and must be ordered by the caller.
+ * array's device address (cudaGetSymbolAddress) for that device, and so does
+ * the first call after the device's primary context was reset and created
+ * again (the address is cached with the context it belongs to); make those
+ * calls before any stream capture. Each device that loads the library has
+ * its own copy of the array. Each call clears the array's counters and
+ * leaves its other contents in place; two calls on the same device whose
+ * work overlaps on the GPU (different streams, or the same stream with no
+ * ordering between them) race on that device's copy and must be ordered by
+ * the caller; calls on different devices do not share it.
  * Arguments are those of splat_forward with n_views = 1 (pose: device, 12
- * doubles); status: device, 2 int64 or NULL, receives DAGS_OK or
- * DAGS_E_CAPACITY (pairs beyond the limit: image, last and loss are then
- * undefined) and the number of pairs the call needed. */
+ * doubles); status: device, 2 int64 or NULL. status[0] receives DAGS_OK,
+ * DAGS_E_CAPACITY (more pairs than the limit; image, last and loss are then
+ * undefined) or, from a DAGS_CHECK build, DAGS_E_BOUNDS (an index check
+ * failed and the access was skipped); status[1] the number of pairs the call
+ * needed. */
 int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
                          const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                          float *image, int32_t *last, double *loss, int64_t *status, void *stream);

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 #include <nvtx3/nvToolsExt.h>
@@ -1228,29 +1230,64 @@ constexpr size_t kStaticBytes = kOffSorted + al256(kStaticMaxPairs * 4);
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
 // Per-device device address of g_static_scratch (host code cannot use the
-// symbol itself: on the host it names a stand-in, not device memory).
+// symbol itself: on the host it names a stand-in, not device memory), with
+// the context it was resolved in: a device reset or a new primary context
+// loads the module again, and the address is then resolved again.
 std::mutex g_static_mu;
 unsigned char *g_static_addr[256] = {};
+CUcontext g_static_ctx[256] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
 
 int static_scratch(unsigned char **out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return DAGS_E_CUDA;
+  // the runtime makes the device's primary context current; its handle
+  // comes from the driver entry point (no link against the driver library)
+  static CtxGetCurrentFn get_current = nullptr;
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  if (!get_current) {
+    cudaDriverEntryPointQueryResult q;
+    void *fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return DAGS_E_CUDA;
+    }
+    get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+  }
+  CUcontext cur = nullptr;
+  if (get_current(&cur) != CUDA_SUCCESS) return DAGS_E_CUDA;
+  if (!cur) {
+    // no context current yet: cudaSetDevice initialises the primary context
+    if (cudaSetDevice(dev) != cudaSuccess || get_current(&cur) != CUDA_SUCCESS || !cur) {
+      cudaGetLastError();
+      return DAGS_E_CUDA;
+    }
+  }
+  if (!g_static_addr[dev] || g_static_ctx[dev] != cur) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return DAGS_E_CUDA;
     }
     g_static_addr[dev] = static_cast<unsigned char *>(p);
+    g_static_ctx[dev] = cur;
   }
   *out = g_static_addr[dev];
   return DAGS_OK;
 }
 
+// status[0]: the call's outcome from the array's status word and pair count
+// (capacity first, then a failed index check of a DAGS_CHECK build);
+// status[1]: the pairs the call needed.
 __global__ void static_status_kernel(const uint32_t *counters, int64_t *status, int64_t max_pairs) {
   const uint64_t req = (uint64_t)counters[CNT_REQ_LO] | ((uint64_t)counters[CNT_REQ_HI] << 32);
-  status[0] = req > (uint64_t)max_pairs ? DAGS_E_CAPACITY : DAGS_OK;
+  const uint32_t st = counters[CNT_STATUS];
+  int64_t code = DAGS_OK;
+  if ((st & kStatusCapacity) || req > (uint64_t)max_pairs) code = DAGS_E_CAPACITY;
+  else if (st & kStatusBounds) code = DAGS_E_BOUNDS;
+  status[0] = code;
   status[1] = (int64_t)req;
 }
 

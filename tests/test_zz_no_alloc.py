@@ -88,3 +88,35 @@ def test_sizes_beyond_the_limit_are_refused(dags):
     assert static_forward(dags, big)[0] == -1
     wide = synth.tiny_scene(0, n=100, width=320, height=120)
     assert static_forward(dags, wide)[0] == -1
+
+
+def test_pairs_beyond_the_limit_report_capacity_then_the_next_call_is_whole(dags):
+    # 1,200 large, nearly opaque Gaussians in front of a 256 x 256 camera each
+    # reach most of its 256 tiles: far more than the array's 131,072 (tile,
+    # Gaussian) pairs, while n, width and height stay within the limits. The
+    # status reports DAGS_E_CAPACITY and the pair count splat_forward needs;
+    # a normal call afterwards still matches splat_forward.
+    sc = synth.tiny_scene(6, n=1200, width=256, height=256, f=200.0)
+    rec = sc.records.copy()
+    rec[:, 8:11] = np.log(0.6)        # log-scales: 0.6 m at 1-4 m
+    rec[:, 3] = 3.0                   # opacity logit
+    big = synth.Scene(rec, sc.camera, sc.poses, sc.targets)
+    code, image, last, loss, st = static_forward(dags, big)
+    assert code == 0
+    cam = dags.Camera(*big.camera.as_tuple())
+    g = torch.from_numpy(np.ascontiguousarray(big.records)).cuda()
+    ctx = dags.Context(g.shape[0], cam.width, cam.height, 1, max_pairs=4_000_000)
+    ctx.forward(g, cam, torch.from_numpy(np.ascontiguousarray(big.poses)).cuda(),
+                torch.from_numpy(np.ascontiguousarray(big.targets)).cuda())
+    rc, req = ctx.sync_status()
+    assert rc == 0 and req > 131_072
+    assert st.cpu().tolist() == [-3, req]          # DAGS_E_CAPACITY
+    ctx.close()
+    sc = synth.tiny_scene(0)
+    code, image, last, loss, st = static_forward(dags, sc)
+    assert code == 0
+    ref_image, ref_last, ref_loss, req = ctx_forward(dags, sc)
+    np.testing.assert_allclose(image.double().cpu().numpy(), ref_image.double().cpu().numpy(), rtol=IMG_RTOL,
+                               atol=IMG_ATOL)
+    np.testing.assert_array_equal(last.cpu().numpy(), ref_last.cpu().numpy())
+    assert st.cpu().tolist() == [0, req]
