@@ -234,17 +234,25 @@ int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, 
                          const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                          float *image, int32_t *last, double *loss, int64_t *status, void *stream);
 
-/* Tracking loop: iters x { splat_forward with loss, splat_backward
- * (DAGS_GRAD_POSE), pose_step } on one view, enqueued by the library -- the
- * pose refinement of the tracking thread (Sec. III) with the pose part of
- * Eq. (27). pose (device, 12 doubles) and adam_state (device, 13 doubles)
- * are updated in place; image, last, loss and grad_pose hold the last
- * iteration's values. With use_graph != 0 (and timing off) one iteration
- * and a chunk of ten are captured once into CUDA graphs on a private stream,
- * cached in the ctx for exactly these arguments (pointers, sizes, camera,
- * configs), and replayed on `stream` (chunks, then single iterations);
- * (re)capturing synchronises `stream` first. Capacity overflow is reported by dags_sync_status as for
- * splat_forward. */
+/* Tracking loop: iters x { the forward with loss of splat_forward, the
+ * pose-only backward of splat_backward (DAGS_GRAD_POSE), pose_step } on one
+ * view, enqueued by the library -- the pose refinement of the tracking thread
+ * (Sec. III) with the pose part of Eq. (27). Each iteration is three kernels:
+ * projection and binning straight into per-tile buckets of max_pairs /
+ * tiles slots each, one fused kernel that composites, forms the loss and
+ * runs the pose adjoint per tile, and the chain to the pose twist with the
+ * FP64 pose step. pose (device, 12 doubles) and adam_state (device, 13
+ * doubles) are updated in place; image, last, loss and grad_pose hold the
+ * last iteration's values. With use_graph != 0 (and timing off) one
+ * iteration and a chunk of ten are captured once into CUDA graphs on a
+ * private stream, cached in the ctx for exactly these arguments (pointers,
+ * sizes, camera, configs), and replayed on `stream` (chunks, then single
+ * iterations); (re)capturing synchronises `stream` first. A tile whose list
+ * exceeds its bucket is reported by dags_sync_status as DAGS_E_CAPACITY with
+ * the max_pairs that would hold every bucket (the longest list times the
+ * tiles); the iteration's outputs are then undefined. A splat_backward or
+ * dags_copy_bins after splat_track returns DAGS_E_ORDER (no forward of its
+ * own precedes it). */
 int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                 const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                 const dags_pose_cfg *pcfg, int32_t iters, double *adam_state, float *image, int32_t *last,

@@ -569,18 +569,18 @@ int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_cam
   int rc;
   if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
   ctx->last_stream = s;
-  const Workspace &w = ctx->ws;
+  // the tile buckets take the fixed-capacity layout: max_pairs / tiles slots
+  // per tile, filled by the preprocess directly (no scan or emit launch)
+  Workspace w = ctx->ws;
+  const int64_t cap = w.max_pairs / r.T;
+  w.bucket_cap = (uint32_t)(cap < 0xFFFFFFFFll ? cap : 0xFFFFFFFFll);
+  if (w.bucket_cap == 0) return DAGS_E_INVAL;
   const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
   KernelTimer &tm = ctx->timer;
   // the pose path accumulates 2D-gradient words G2_U .. G2_Z: two float4
   int ev = tm.begin(DAGS_K_PREPROCESS, s);
-  cudaError_t e = launch_preprocess(w, g4, n, pose, 1, r, 8, s);
+  cudaError_t e = launch_preprocess_direct(w, g4, n, pose, r, 8, s);
   tm.end(ev, s);
-  if (e == cudaSuccess && n > 0) {
-    ev = tm.begin(DAGS_K_EMIT, s);
-    e = launch_emit(w, n, 1, r, s);
-    tm.end(ev, s);
-  }
   if (e == cudaSuccess) {
     ev = tm.begin(DAGS_K_RENDER_TRACK, s);
     e = launch_render_track(w, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
@@ -596,15 +596,10 @@ int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_cam
     e = launch_preprocess_bwd(w, g4, n, 1, r, nullptr, grad_pose, ps, s);
     tm.end(ev, s);
   }
+  // the workspace's lists are in the fixed-bucket layout: no splat_backward
+  // or dags_copy_bins may follow
+  ctx->fwd_image = nullptr;
   if (e != cudaSuccess) return DAGS_E_CUDA;
-  ctx->fwd_image = image;
-  ctx->fwd_last = last;
-  ctx->fwd_gauss = gauss;
-  ctx->fwd_n = n;
-  ctx->fwd_views = 1;
-  ctx->fwd_w = cam->width;
-  ctx->fwd_h = cam->height;
-  ctx->fwd_tiles = r.T;
   return DAGS_OK;
 }
 

@@ -97,7 +97,23 @@ struct Workspace {
   // backward compositing, [fwd eval, fwd contrib, bwd eval, bwd contrib].
   unsigned long long *evals = nullptr;
   int count_evals = 0;
+  // Fixed-capacity layout of the tile buckets (the tracking loop, one view):
+  // when non-zero, tile t's keys and sorted ids occupy [t cap, t cap +
+  // min(count_t, cap)) and tile_count holds the counts; otherwise the
+  // buckets are packed at tile_start offsets.
+  uint32_t bucket_cap = 0;
 };
+
+// The list range [s, e) of tile t in the workspace's bucket layout.
+__device__ __forceinline__ void tile_range(const Workspace &ws, int t, uint32_t &s, uint32_t &e) {
+  if (ws.bucket_cap) {
+    s = (uint32_t)t * ws.bucket_cap;
+    e = s + min(ws.tile_count[t], ws.bucket_cap);
+  } else {
+    s = ws.tile_start[t];
+    e = ws.tile_start[t + 1];
+  }
+}
 
 // Adds a lane's evaluation counts to the workspace totals (one atomic per
 // warp and counter); called by whole warps.
@@ -138,6 +154,11 @@ struct PoseStep {
 cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t n, const double *poses,
                               int views, const Raster &r, int zero_grad_words, cudaStream_t s);
 cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s);
+// Projection and binning of one view into fixed-capacity tile buckets
+// (ws.bucket_cap > 0): keys written directly, the render order and the pair
+// requirement by the last CTA (no scan or emit launch).
+cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
+                                     const Raster &r, int zero_grad_words, cudaStream_t s);
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s);

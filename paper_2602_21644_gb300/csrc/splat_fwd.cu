@@ -173,10 +173,14 @@ __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t 
 // together: lane l takes candidate c = base + l of the warp's concatenated
 // candidate lists, finds its owner by binary search over the warp's
 // inclusive prefix of candidate counts, and tests whether the owner's
-// ellipse reaches that tile. EMIT = false: the kept pairs are counted per
-// tile (one atomic per distinct tile per warp); EMIT = true: each kept pair
-// gets a slot in its tile's bucket the same way and its key is written.
-template <bool EMIT>
+// ellipse reaches that tile. MODE kWalkCount: the kept pairs are counted per
+// tile (one atomic per distinct tile per warp); kWalkEmit: each kept pair
+// gets a slot in its tile's bucket (after the offsets scan) the same way and
+// its key is written; kWalkDirect: each kept pair's slot comes from the
+// tile's count itself and its key goes to the tile's fixed-capacity bucket
+// (slots beyond the capacity are counted, not written).
+enum { kWalkCount = 0, kWalkEmit = 1, kWalkDirect = 2 };
+template <int MODE>
 __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r, int v, uint32_t id, uint2 rect,
                                            float4 r0, float4 r1, float zkey) {
   const unsigned FULL = 0xffffffffu;
@@ -224,8 +228,17 @@ __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r,
     }
     const unsigned grp = __match_any_sync(FULL, key);
     const int leader = __ffs(grp) - 1;
-    if (!EMIT) {
+    if (MODE == kWalkCount) {
       if (keep && lane == leader) atomicAdd(ws.tile_count + key, (uint32_t)__popc(grp));
+    } else if (MODE == kWalkDirect) {
+      uint32_t basepos = 0;
+      if (keep && lane == leader) basepos = atomicAdd(ws.tile_count + key, (uint32_t)__popc(grp));
+      basepos = __shfl_sync(FULL, basepos, leader);
+      if (keep) {
+        const uint32_t slot = basepos + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+        if (slot < ws.bucket_cap)
+          ws.keys[(size_t)key * ws.bucket_cap + slot] = ((uint64_t)__float_as_uint(o_z) << 32) | (uint64_t)o_id;
+      }
     } else {
       // the bucket bounds are loaded before the cursor atomic so that the
       // two round trips overlap
@@ -242,6 +255,81 @@ __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r,
   }
 }
 
+// The last CTA of the preprocess in the fixed-bucket layout (one view): the
+// render launch order (tiles ranked by descending count in bins of 8,
+// band-reversed as block_scan_tiles orders them), the required pairs (the
+// largest count times the tiles: what max_pairs must be for every bucket to
+// hold its list) and the capacity flag, and the visible count. The counts
+// stay for the render, which clears its tile's.
+__device__ void order_direct_buckets(const Workspace &ws, int total) {
+  __shared__ uint32_t s_bin[kLenBins];
+  __shared__ uint32_t s_maxc;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < kLenBins; k += blockDim.x) s_bin[k] = 0u;
+  if (tid == 0) s_maxc = 0u;
+  __syncthreads();
+  uint32_t mx = 0;
+  for (int k0 = 0; k0 < total; k0 += blockDim.x) {
+    const int k = k0 + tid;
+    int bin = 1024 + lane;   // no element: a key of its own
+    if (k < total) {
+      const uint32_t c = __ldcg(ws.tile_count + k);
+      mx = max(mx, c);
+      bin = length_bin(c);
+    }
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    if (bin < kLenBins && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+  }
+  mx = __reduce_max_sync(0xffffffffu, mx);
+  if (lane == 0) atomicMax(&s_maxc, mx);
+  __syncthreads();
+  if (tid < 32) {
+    uint32_t loc[9], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int bb = 9 * lane + j;
+      loc[j] = bb < kLenBins ? s_bin[bb] : 0u;
+      sum += loc[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int bb = 9 * lane + j;
+      if (bb < kLenBins) s_bin[bb] = run;
+      run += loc[j];
+    }
+  }
+  __syncthreads();
+  const uint32_t band = ws.band > 0 ? (uint32_t)ws.band : 1u;
+  for (int k0 = 0; k0 < total; k0 += blockDim.x) {
+    const int k = k0 + tid;
+    int bin = 1024 + lane;
+    if (k < total) bin = length_bin(__ldcg(ws.tile_count + k));
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    const int leader = __ffs(grp) - 1;
+    uint32_t pos = 0;
+    if (bin < kLenBins && lane == leader) pos = atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+    if (k < total) ws.tile_order[snake_slot(pos, (uint32_t)total, band)] = (uint32_t)k;
+  }
+  if (tid == 0) {
+    const uint64_t req = (uint64_t)s_maxc * (uint64_t)total;
+    ws.counters[CNT_REQ_LO] = (uint32_t)req;
+    ws.counters[CNT_REQ_HI] = (uint32_t)(req >> 32);
+    if (s_maxc > ws.bucket_cap) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
+    ws.vis_n[0] = ws.vis_append[0];
+    ws.vis_append[0] = 0u;
+    ws.counters[CNT_DONE_PREP] = 0u;
+  }
+}
+
+template <bool DIRECT>
 __global__ void __launch_bounds__(kPrepBlock)
 preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
@@ -271,6 +359,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
 
   uint2 my_rect = make_uint2(0u, 0u);
   float4 my_r0 = make_float4(0.f, 0.f, 0.f, 0.f), my_r1 = my_r0;
+  float my_z = 0.f;
   if (i < n) {
     const float *P = sp + v * 12;
     const size_t slot = (size_t)v * ws.max_n + i;
@@ -321,6 +410,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     my_rect = rect;
     my_r0 = o0;
     my_r1 = o1;
+    my_z = o2.x;
   }
   // Visible Gaussians (non-empty candidate range) are appended to the view's
   // list, one atomic per warp.
@@ -335,8 +425,22 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       ws.vis_ids[(size_t)v * ws.max_n + basev + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
   }
   // Warp-cooperative walk over the candidate tiles of the warp's Gaussians.
-  walk_tiles<false>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, 0.f);
-
+  if (!DIRECT) {
+    walk_tiles<kWalkCount>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, 0.f);
+    return;
+  }
+  walk_tiles<kWalkDirect>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, my_z);
+  // the last CTA orders the renders
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
+    s_last = (t == gridDim.x * gridDim.y - 1);
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (s_last) order_direct_buckets(ws, r.T);
 }
 
 // One CTA turns the per-tile counts into offsets and the launch order, and
@@ -391,7 +495,7 @@ emit_kernel(Workspace ws, int64_t n, Raster r) {
   } else {
     id = 0;
   }
-  walk_tiles<true>(ws, r, v, id, rect, r0, r1, z);
+  walk_tiles<kWalkEmit>(ws, r, v, id, rect, r0, r1, z);
 }
 
 __global__ void __launch_bounds__(kTilePix, 6)
@@ -541,10 +645,19 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
   if (views > kMaxViewsSmem) return cudaErrorInvalidValue;
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
   dim3 grid(gx > 0 ? gx : 1u, (unsigned)views);
-  cudaError_t e = launch_pdl(preprocess_kernel, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, poses, views, r,
+  cudaError_t e = launch_pdl(preprocess_kernel<false>, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, poses, views, r,
                              zero_grad_words);
   if (e == cudaSuccess) e = launch_pdl(tile_scan_kernel, dim3(1), dim3(kScanThreads), 0, s, ws, views, r);
   return e;
+}
+
+cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
+                                     const Raster &r, int zero_grad_words, cudaStream_t s) {
+  if (ws.bucket_cap == 0) return cudaErrorInvalidValue;
+  const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
+  dim3 grid(gx > 0 ? gx : 1u, 1u);
+  return launch_pdl(preprocess_kernel<true>, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, pose, 1, r,
+                    zero_grad_words);
 }
 
 cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s) {

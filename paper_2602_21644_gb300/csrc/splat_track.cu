@@ -46,8 +46,8 @@ render_track_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ t
   const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
-  const uint32_t s = ovf ? 0u : ws.tile_start[tile];
-  const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
+  uint32_t s = 0u, e = 0u;
+  if (!ovf) tile_range(ws, tile, s, e);
   const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
   const float fpx = (float)px, fpy = (float)py;
   // the pose-only adjoint's reduce-scatter leaves word `comp` of the six
@@ -265,6 +265,8 @@ render_track_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ t
   }
   add_eval_counts(ws, 0, n_eval, n_contrib);
   add_eval_counts(ws, 1, b_eval, b_contrib);
+  // the fixed-bucket layout's counts start at zero for the next preprocess
+  if (ws.bucket_cap && tid == 0) ws.tile_count[tile] = 0u;
 
   if (!loss) return;
   __syncthreads();
