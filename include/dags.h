@@ -234,6 +234,37 @@ int splat_forward_static(const float *gauss, int64_t n, const dags_camera *cam, 
                          const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                          float *image, int32_t *last, double *loss, int64_t *status, void *stream);
 
+/* Mapping optimiser on the Gaussian parameters (the map side of the joint
+ * optimisation of Eq. (27); the paper names no optimiser): Adam (Kingma and
+ * Ba) per parameter with one learning rate per group. Defaults from
+ * dags_default_gauss_adam_cfg: the published 3D Gaussian splatting rates
+ * (opacity 0.05, quaternion 1e-3, log-scale 5e-3, colour 2.5e-3) and 1e-3 m
+ * for the means; beta 0.9 / 0.999, eps 1e-8. */
+typedef struct {
+  float lr_mean, lr_opacity, lr_quat, lr_scale, lr_colour;
+  float beta1, beta2, eps;
+} dags_gauss_adam_cfg;
+
+void dags_default_gauss_adam_cfg(dags_gauss_adam_cfg *cfg);
+
+/* Optimiser state of n Gaussians: colour (device, n x 4 floats) receives the
+ * FP32 master colour decoded from the records' BF16 colours, and adam_m,
+ * adam_v (device, n x 16 floats each, in the gradient's slot order) are
+ * zeroed. Call once before the first gauss_adam_step. */
+int gauss_adam_init(dags_ctx *ctx, const float *gauss, int64_t n, float *colour, float *adam_m, float *adam_v,
+                    void *stream);
+
+/* One Adam step, step number `step` >= 1 (bias corrections 1 - beta^step),
+ * on the records' mean (words 0-2), opacity logit (3), quaternion (4-7) and
+ * log-scale (8-10), in place in FP32, and on the FP32 master colour, which
+ * is then written into the record's BF16 colour words (round to nearest,
+ * ties to even). The MP word (11) is left to mp_update. grad: device, n x 16
+ * floats as splat_backward writes them (colour in slots 12-14); the moments
+ * are updated in place. All buffers 16-byte aligned; DAGS_E_INVAL on a
+ * bad argument, a non-finite rate or beta outside [0, 1). */
+int gauss_adam_step(dags_ctx *ctx, float *gauss, int64_t n, float *colour, float *adam_m, float *adam_v,
+                    const float *grad, int64_t step, const dags_gauss_adam_cfg *cfg, void *stream);
+
 /* Tracking loop: iters x { the forward with loss of splat_forward, the
  * pose-only backward of splat_backward (DAGS_GRAD_POSE), pose_step } on one
  * view, enqueued by the library -- the pose refinement of the tracking thread
@@ -599,6 +630,7 @@ enum {
   DAGS_K_REGULARISER,      /* L_MP and L_edge regularisers                 */
   DAGS_K_EPIPOLAR,         /* epipolar verification and static recovery    */
   DAGS_K_RENDER_TRACK,     /* tracking: fused compositing + pose adjoint   */
+  DAGS_K_GAUSS_ADAM,       /* mapping: Adam step on the Gaussians          */
   DAGS_KERNEL_COUNT
 };
 int dags_timing_enable(dags_ctx *ctx, int enable);

@@ -535,6 +535,51 @@ int splat_backward_upstream(dags_ctx *ctx, const float *gauss, int64_t n, const 
   return cuda_status(e);
 }
 
+void dags_default_gauss_adam_cfg(dags_gauss_adam_cfg *c) {
+  if (!c) return;
+  c->lr_mean = 1e-3f;
+  c->lr_opacity = 0.05f;
+  c->lr_quat = 1e-3f;
+  c->lr_scale = 5e-3f;
+  c->lr_colour = 2.5e-3f;
+  c->beta1 = 0.9f;
+  c->beta2 = 0.999f;
+  c->eps = 1e-8f;
+}
+
+int gauss_adam_init(dags_ctx *ctx, const float *gauss, int64_t n, float *colour, float *adam_m, float *adam_v,
+                    void *stream) {
+  NvtxRange nv("gauss_adam_init");
+  if (!ctx || n < 0 || (n > 0 && (!gauss || !colour || !adam_m || !adam_v))) return DAGS_E_INVAL;
+  if ((((uintptr_t)gauss | (uintptr_t)colour | (uintptr_t)adam_m | (uintptr_t)adam_v) & 15u) != 0)
+    return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  return cuda_status(launch_gauss_adam_init(gauss, colour, adam_m, adam_v, n, s));
+}
+
+int gauss_adam_step(dags_ctx *ctx, float *gauss, int64_t n, float *colour, float *adam_m, float *adam_v,
+                    const float *grad, int64_t step, const dags_gauss_adam_cfg *cfg, void *stream) {
+  NvtxRange nv("gauss_adam_step");
+  if (!ctx || n < 0 || step < 1 || (n > 0 && (!gauss || !colour || !adam_m || !adam_v || !grad)))
+    return DAGS_E_INVAL;
+  if ((((uintptr_t)gauss | (uintptr_t)colour | (uintptr_t)adam_m | (uintptr_t)adam_v | (uintptr_t)grad) & 15u) != 0)
+    return DAGS_E_INVAL;
+  dags_gauss_adam_cfg c;
+  if (cfg) c = *cfg;
+  else dags_default_gauss_adam_cfg(&c);
+  const float rates[5] = {c.lr_mean, c.lr_opacity, c.lr_quat, c.lr_scale, c.lr_colour};
+  for (float x : rates)
+    if (!isfinite(x) || x < 0.f) return DAGS_E_INVAL;
+  if (!(c.beta1 >= 0.f && c.beta1 < 1.f) || !(c.beta2 >= 0.f && c.beta2 < 1.f) || !(c.eps > 0.f)) return DAGS_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->last_stream = s;
+  const int ev = ctx->timer.begin(DAGS_K_GAUSS_ADAM, s);
+  const cudaError_t e = launch_gauss_adam(gauss, colour, adam_m, adam_v, grad, n, step, c, s);
+  ctx->timer.end(ev, s);
+  return cuda_status(e);
+}
+
 int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_state, int32_t n_views,
               const dags_pose_cfg *cfg, void *stream) {
   NvtxRange nv("pose_step");

@@ -178,6 +178,11 @@ cudaError_t launch_pose_step(double *poses, const double *grad, double *state, i
 cudaError_t launch_render_track(const Workspace &ws, const Raster &r, const Loss &l, const float4 *targets,
                                 float *image, int32_t *last, double *loss, cudaStream_t s);
 
+// Mapping optimiser (gauss_adam.cu).
+cudaError_t launch_gauss_adam_init(const float *gauss, float *colour, float *m, float *v, int64_t n, cudaStream_t s);
+cudaError_t launch_gauss_adam(float *gauss, float *colour, float *m, float *v, const float *grad, int64_t n,
+                              int64_t step, const dags_gauss_adam_cfg &c, cudaStream_t s);
+
 // Levenberg-Marquardt pose refinement (lm.cu).
 struct LmBuffers {
   float4 *tan = nullptr;      // [max_n][9] twist tangents of the projected records (view 0)

@@ -77,6 +77,11 @@ MPNET_ACT_WORDS = 96
 MPNET_PARAMS = 10881
 
 
+class CGaussAdamCfg(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("lr_mean", "lr_opacity", "lr_quat", "lr_scale", "lr_colour", "beta1",
+                                              "beta2", "eps")]
+
+
 class CPoseCfg(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_double * 6), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("eps", ctypes.c_double)]
@@ -90,11 +95,11 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
            "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp",
            "epipolar_verify", "dags_eval_counting", "dags_eval_read", "dags_measure_alu",
-           "splat_backward_upstream"]
+           "splat_backward_upstream", "dags_default_gauss_adam_cfg", "gauss_adam_init", "gauss_adam_step"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
-           "regulariser", "epipolar", "render_track"]
+           "regulariser", "epipolar", "render_track", "gauss_adam"]
 
 _lib = None
 
@@ -140,6 +145,12 @@ def load(path: str = LIB_PATH):
     lib.splat_backward_upstream.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, I32,
                                             ctypes.POINTER(CRasterCfg), P, P, P, U32, P, P, P]
     lib.splat_backward_upstream.restype = ctypes.c_int
+    lib.dags_default_gauss_adam_cfg.argtypes = [ctypes.POINTER(CGaussAdamCfg)]
+    lib.dags_default_gauss_adam_cfg.restype = None
+    lib.gauss_adam_init.argtypes = [P, P, I64, P, P, P, P]
+    lib.gauss_adam_init.restype = ctypes.c_int
+    lib.gauss_adam_step.argtypes = [P, P, I64, P, P, P, P, I64, ctypes.POINTER(CGaussAdamCfg), P]
+    lib.gauss_adam_step.restype = ctypes.c_int
     lib.pose_step.argtypes = [P, P, P, P, I32, ctypes.POINTER(CPoseCfg), P]
     lib.pose_step.restype = ctypes.c_int
     lib.dags_copy_bins.argtypes = [P, P, I64, P, I64, ctypes.POINTER(I64)]
@@ -248,6 +259,14 @@ def default_pose_cfg(lr=None, **kw) -> CPoseCfg:
     if lr is not None:
         for k in range(6):
             c.lr[k] = float(lr[k] if hasattr(lr, "__len__") else lr)
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def default_gauss_adam_cfg(**kw) -> CGaussAdamCfg:
+    c = CGaussAdamCfg()
+    load().dags_default_gauss_adam_cfg(ctypes.byref(c))
     for k, v in kw.items():
         setattr(c, k, v)
     return c
@@ -408,6 +427,24 @@ class Context:
                                        _ptr(grad_gauss if flags & GRAD_GAUSS else None),
                                        _ptr(grad_pose if flags & GRAD_POSE else None), _stream()), "splat_backward")
         return (grad_gauss if flags & GRAD_GAUSS else None), (grad_pose if flags & GRAD_POSE else None)
+
+    def gauss_adam_state(self, gauss):
+        """(colour master [n,4] f32, m [n,16], v [n,16]) initialised for gauss_adam_step."""
+        n = gauss.shape[0]
+        dev = gauss.device
+        colour = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        m = torch.empty((n, GRAD_WORDS), dtype=torch.float32, device=dev)
+        v = torch.empty((n, GRAD_WORDS), dtype=torch.float32, device=dev)
+        _check(self.lib.gauss_adam_init(self.h, _ptr(gauss), n, _ptr(colour), _ptr(m), _ptr(v), _stream()),
+               "gauss_adam_init")
+        return colour, m, v
+
+    def gauss_adam_step(self, gauss, state, grad, step, cfg=None):
+        """One Adam step (step >= 1) of the Gaussian parameters in place."""
+        colour, m, v = state
+        c = cfg if cfg is not None else default_gauss_adam_cfg()
+        _check(self.lib.gauss_adam_step(self.h, _ptr(gauss), gauss.shape[0], _ptr(colour), _ptr(m), _ptr(v),
+                                        _ptr(grad), int(step), ctypes.byref(c), _stream()), "gauss_adam_step")
 
     def backward_upstream(self, gauss, cam: Camera, poses, image, last, grad_image, flags=GRAD_POSE, rcfg=None,
                           grad_gauss=None, grad_pose=None):
