@@ -75,7 +75,7 @@ def _load():
         lib.oracle_project.restype = None
         lib.oracle_binning.argtypes = [I64, P, P, P, P, I64, P, P, P]
         lib.oracle_binning.restype = I64
-        lib.oracle_render.argtypes = [I64, P, P, P, P, P, P, P, P, ctypes.c_int, P, P, P, P, P]
+        lib.oracle_render.argtypes = [I64, P, P, P, P, P, P, P, P, ctypes.c_int, P, P, P, P, P, P]
         lib.oracle_render.restype = ctypes.c_int
         lib.oracle_render_pixel.argtypes = [I64, P, P, P, P, ctypes.c_int, ctypes.c_int, P]
         lib.oracle_render_pixel.restype = ctypes.c_int
@@ -168,15 +168,20 @@ def binning(G, cam, pose, rc=None):
     return tiles[:total], ids[:total], ties[:total]
 
 
-def render(G, cam, pose, rc=None, lc=None, targets=None, grads=False, accel=True, wfix=None, upstream=None):
+def render(G, cam, pose, rc=None, lc=None, targets=None, grads=False, accel=True, wfix=None, upstream=None,
+           grad_mag=False):
     """Render one view and, with targets (H*W x 4: r, g, b, depth), the loss
     and, with grads=True, its adjoint. wfix (H*W) freezes the static weight.
     upstream (H*W x 6: dF/d(C_r, C_g, C_b, D, O, R_MP) of a caller's function
     F of the rendered channels) replaces the loss: with grads=True the
     adjoint is that of F, and targets are not used.
 
+    grad_mag=True (with grads) also returns grad_mag (n x 15): per parameter,
+    the sum over pixels and 2D words of |term| |d parameter / d word|, the
+    magnitude of what the gradient sums (its rounding bound scales with it).
+
     Returns dict(pix=(H*W x 10), flags=(H*W,), loss=float|None,
-    grad=(n x 15)|None, pose_grad=(6,)|None).
+    grad=(n x 15)|None, pose_grad=(6,)|None, grad_mag=(n x 15)|None).
     """
     lib = _load()
     G = _f64(G, (-1, G_STRIDE))
@@ -191,14 +196,15 @@ def render(G, cam, pose, rc=None, lc=None, targets=None, grads=False, accel=True
     tg = None if (targets is None or up is not None) else _f64(targets, (W * H, 4))
     gr = np.zeros((G.shape[0], G_STRIDE)) if (grads and (tg is not None or up is not None)) else None
     pg = np.zeros(6) if gr is not None else None
+    gm = np.zeros((G.shape[0], G_STRIDE)) if (gr is not None and grad_mag) else None
     rcode = lib.oracle_render(G.shape[0], _ptr(G), _ptr(cam), _ptr(_f64(pose, (12,))), _ptr(rc), _ptr(lc),
                               _ptr(tg), _ptr(None if wfix is None else _f64(wfix, (W * H,))), _ptr(up),
                               int(bool(accel)), _ptr(pix), _ptr(flags),
-                              _ptr(loss) if tg is not None else None, _ptr(gr), _ptr(pg))
+                              _ptr(loss) if tg is not None else None, _ptr(gr), _ptr(pg), _ptr(gm))
     if rcode != 0:
         raise MemoryError("oracle_render failed")
     return dict(pix=pix, flags=flags, loss=float(loss[0]) if tg is not None else None, grad=gr,
-                pose_grad=pg)
+                pose_grad=pg, grad_mag=gm)
 
 
 def render_pixel(G, cam, pose, i, j, rc=None):

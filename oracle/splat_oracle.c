@@ -462,7 +462,7 @@ static void build_cells(int64_t n, const proj_t *P, const int64_t *order, int W,
  * contributors behind k, d/d alpha_k = sum_ch gF_ch (f_ch T_k - S_ch /
  * (1 - alpha_k)); a clamped alpha passes nothing to its exponent. */
 static void adjoint_pixel(const contrib_t *list, int64_t nl, const proj_t *P, const double *G,
-                          const double *gF, double *g2) {
+                          const double *gF, double *g2, double *g2abs) {
   double S[6] = {0, 0, 0, 0, 0, 0}; /* sum over later contributors */
   for (int64_t k = nl - 1; k >= 0; k--) {
     const contrib_t *e = &list[k];
@@ -474,21 +474,140 @@ static void adjoint_pixel(const contrib_t *list, int64_t nl, const proj_t *P, co
     for (int ch = 0; ch < 6; ch++)
       dal += gF[ch] * (f[ch] * e->T - S[ch] / (1.0 - e->alpha));
     double *gg = g2 + e->id * 10;
-    gg[7] += gF[0] * wk;
-    gg[8] += gF[1] * wk;
-    gg[9] += gF[2] * wk;
-    gg[6] += gF[3] * wk;
+    double t[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    t[7] = gF[0] * wk;
+    t[8] = gF[1] * wk;
+    t[9] = gF[2] * wk;
+    t[6] = gF[3] * wk;
     if (!e->clamped) {
-      gg[5] += dal * e->G;
+      t[5] = dal * e->G;
       double dpw = dal * e->alpha;
-      gg[0] += dpw * (-(p->a * e->dx + p->b * e->dy));
-      gg[1] += dpw * (-(p->b * e->dx + p->c * e->dy));
-      gg[2] += dpw * (-0.5 * e->dx * e->dx);
-      gg[3] += dpw * (-e->dx * e->dy);
-      gg[4] += dpw * (-0.5 * e->dy * e->dy);
+      t[0] = dpw * (-(p->a * e->dx + p->b * e->dy));
+      t[1] = dpw * (-(p->b * e->dx + p->c * e->dy));
+      t[2] = dpw * (-0.5 * e->dx * e->dx);
+      t[3] = dpw * (-e->dx * e->dy);
+      t[4] = dpw * (-0.5 * e->dy * e->dy);
     }
+    for (int k = 0; k < 10; k++) gg[k] += t[k];
+    if (g2abs)
+      for (int k = 0; k < 10; k++) g2abs[e->id * 10 + k] += fabs(t[k]);
     for (int ch = 0; ch < 6; ch++) S[ch] += f[ch] * wk;
   }
+}
+
+/* The chain of one Gaussian's 2D gradients gg[10] (u, v, a, b, c, o, z,
+ * colour) to its parameters (ADDED to out[G_STRIDE], if non-NULL) and to the
+ * pose twist (ADDED to pg[6]): conic to 2D covariance, EWA covariance and
+ * Jacobian to the camera-space mean and covariance, camera transform, scale
+ * and rotation (through the quaternion's normalisation). Linear in gg. */
+static void chain_gauss(const proj_t *p, const double *R, double fx, double fy, const double *gg, double *out,
+                        double *pg) {
+  double x = p->p[0], y = p->p[1], z = p->p[2];
+  /* conic -> 2D covariance: dL/dSigma' = -Q Gq Q (symmetric matrix form) */
+  double Q[4] = {p->a, p->b, p->b, p->c};
+  double Gq[4] = {gg[2], 0.5 * gg[3], 0.5 * gg[3], gg[4]};
+  double QG[4], dS2[4];
+  for (int r = 0; r < 2; r++)
+    for (int s = 0; s < 2; s++)
+      QG[2 * r + s] = Q[2 * r] * Gq[s] + Q[2 * r + 1] * Gq[2 + s];
+  for (int r = 0; r < 2; r++)
+    for (int s = 0; s < 2; s++)
+      dS2[2 * r + s] = -(QG[2 * r] * Q[s] + QG[2 * r + 1] * Q[2 + s]);
+  const double *J = p->J;
+  /* dL/dSc = J^T dS2 J */
+  double dSc[9];
+  for (int r = 0; r < 3; r++)
+    for (int s = 0; s < 3; s++) {
+      double acc2 = 0;
+      for (int k = 0; k < 2; k++)
+        for (int l = 0; l < 2; l++) acc2 += J[3 * k + r] * dS2[2 * k + l] * J[3 * l + s];
+      dSc[3 * r + s] = acc2;
+    }
+  /* dL/dJ = 2 dS2 J Sc */
+  double JSc[6], dJ[6];
+  for (int r = 0; r < 2; r++)
+    for (int s = 0; s < 3; s++) {
+      double acc2 = 0;
+      for (int k = 0; k < 3; k++) acc2 += J[3 * r + k] * p->Sc[3 * k + s];
+      JSc[3 * r + s] = acc2;
+    }
+  for (int r = 0; r < 2; r++)
+    for (int s = 0; s < 3; s++) dJ[3 * r + s] = 2.0 * (dS2[2 * r] * JSc[s] + dS2[2 * r + 1] * JSc[3 + s]);
+  /* dL/dp (camera-space mean) */
+  double dp[3] = {0, 0, 0};
+  dp[0] += gg[0] * fx / z;
+  dp[2] += gg[0] * (-fx * x / (z * z));
+  dp[1] += gg[1] * fy / z;
+  dp[2] += gg[1] * (-fy * y / (z * z));
+  dp[2] += gg[6];
+  dp[2] += dJ[0] * (-fx / (z * z));
+  dp[2] += dJ[4] * (-fy / (z * z));
+  if (!p->clx) {
+    dp[0] += dJ[2] * (-fx / (z * z));
+    dp[2] += dJ[2] * (2.0 * fx * x / (z * z * z));
+  } else {
+    dp[2] += dJ[2] * (fx * p->tx / (z * z));
+  }
+  if (!p->cly) {
+    dp[1] += dJ[5] * (-fy / (z * z));
+    dp[2] += dJ[5] * (2.0 * fy * y / (z * z * z));
+  } else {
+    dp[2] += dJ[5] * (fy * p->ty / (z * z));
+  }
+  /* pose: rho += dp; phi += p x dp + covariance term */
+  pg[0] += dp[0]; pg[1] += dp[1]; pg[2] += dp[2];
+  pg[3] += y * dp[2] - z * dp[1];
+  pg[4] += z * dp[0] - x * dp[2];
+  pg[5] += x * dp[1] - y * dp[0];
+  double Am[9];
+  mm3(p->Sc, dSc, Am);
+  pg[3] += 2.0 * (Am[5] - Am[7]);
+  pg[4] += 2.0 * (Am[6] - Am[2]);
+  pg[5] += 2.0 * (Am[1] - Am[3]);
+
+  if (!out) return;
+  /* mean: p = R mu + t */
+  for (int k = 0; k < 3; k++)
+    out[G_MX + k] += R[k] * dp[0] + R[3 + k] * dp[1] + R[6 + k] * dp[2];
+  /* world covariance: dSig = R^T dSc R */
+  double Rt[9], tmp[9], dSig[9];
+  tr3(R, Rt);
+  mm3(Rt, dSc, tmp);
+  mm3(tmp, R, dSig);
+  /* Sig = M M^T, M = Rq diag(S): dM = 2 dSig M */
+  double M[9], dM[9];
+  for (int r = 0; r < 3; r++)
+    for (int s = 0; s < 3; s++) M[3 * r + s] = p->Rq[3 * r + s] * p->S[s];
+  mm3(dSig, M, dM);
+  for (int k = 0; k < 9; k++) dM[k] *= 2.0;
+  double dRq[9];
+  for (int s = 0; s < 3; s++) {
+    double dSs = 0;
+    for (int r = 0; r < 3; r++) {
+      dSs += p->Rq[3 * r + s] * dM[3 * r + s];
+      dRq[3 * r + s] = dM[3 * r + s] * p->S[s];
+    }
+    out[G_S0 + s] += dSs * p->S[s];
+  }
+  double w = p->nq[0], qx = p->nq[1], qy = p->nq[2], qz = p->nq[3];
+  double dn[4];
+  dn[0] = dRq[1] * (-2 * qz) + dRq[2] * (2 * qy) + dRq[3] * (2 * qz) + dRq[5] * (-2 * qx) +
+          dRq[6] * (-2 * qy) + dRq[7] * (2 * qx);
+  dn[1] = dRq[1] * (2 * qy) + dRq[2] * (2 * qz) + dRq[3] * (2 * qy) + dRq[4] * (-4 * qx) +
+          dRq[5] * (-2 * w) + dRq[6] * (2 * qz) + dRq[7] * (2 * w) + dRq[8] * (-4 * qx);
+  dn[2] = dRq[0] * (-4 * qy) + dRq[1] * (2 * qx) + dRq[2] * (2 * w) + dRq[3] * (2 * qx) +
+          dRq[5] * (2 * qz) + dRq[6] * (-2 * w) + dRq[7] * (2 * qz) + dRq[8] * (-4 * qy);
+  dn[3] = dRq[0] * (-4 * qz) + dRq[1] * (-2 * w) + dRq[2] * (2 * qx) + dRq[3] * (2 * w) +
+          dRq[4] * (-4 * qz) + dRq[5] * (2 * qy) + dRq[6] * (2 * qx) + dRq[7] * (2 * qy);
+  double ndn = w * dn[0] + qx * dn[1] + qy * dn[2] + qz * dn[3];
+  out[G_QW] += (dn[0] - w * ndn) / p->qlen;
+  out[G_QX] += (dn[1] - qx * ndn) / p->qlen;
+  out[G_QY] += (dn[2] - qy * ndn) / p->qlen;
+  out[G_QZ] += (dn[3] - qz * ndn) / p->qlen;
+  out[G_LOGIT] += gg[5] * p->o * (1.0 - p->o);
+  out[G_CR] += gg[7];
+  out[G_CG] += gg[8];
+  out[G_CB] += gg[9];
 }
 
 /* Render one view: out_px[P * PX_STRIDE], out_flags[P]; if targets
@@ -497,6 +616,10 @@ static void adjoint_pixel(const contrib_t *list, int64_t nl, const proj_t *P, co
  * written to pose_grad[6] = (rho, phi) of the left-perturbation twist.
  * wfix (P, or NULL) replaces the static weight w(u) by given constants, so
  * that finite differences can check the stop-gradient adjoint.
+ * grad_mag (n * G_STRIDE, or NULL; with grads) receives, per parameter, the
+ * sum over pixels and 2D words of |term| |d parameter / d word|: the size of
+ * the terms the gradient sums, which bounds its rounding error in any
+ * arithmetic that rounds each term relatively (added, like grads).
  * upstream (P x 6, or NULL) replaces the loss: the adjoint is that of
  * sum_u upstream[u] . (C_r, C_g, C_b, D, O, R_MP)(u), a caller's gradient of
  * its own function of the composited channels (targets are then unused).
@@ -504,7 +627,7 @@ static void adjoint_pixel(const contrib_t *list, int64_t nl, const proj_t *P, co
 int oracle_render(int64_t n, const double *G, const double *cam, const double *pose,
                   const double *rc, const double *lc, const double *targets, const double *wfix,
                   const double *upstream, int accel, double *out_px, int32_t *out_flags, double *loss,
-                  double *grads, double *pose_grad) {
+                  double *grads, double *pose_grad, double *grad_mag) {
   int W = (int)cam[CAM_W], H = (int)cam[CAM_H];
   proj_t *P = (proj_t *)malloc(sizeof(proj_t) * (size_t)(n > 0 ? n : 1));
   zkey_t *zk = (zkey_t *)malloc(sizeof(zkey_t) * (size_t)(n > 0 ? n : 1));
@@ -524,6 +647,9 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
   const int want_grad = (targets != NULL || upstream != NULL) && (grads != NULL || pose_grad != NULL);
   /* per-Gaussian accumulated 2D gradients: u, v, a, b, c, o, z, cr, cg, cb */
   double *g2 = want_grad ? (double *)calloc((size_t)(n > 0 ? n : 1) * 10, sizeof(double)) : NULL;
+  /* with grad_mag: the per-Gaussian sums of the 2D terms' magnitudes */
+  if (!want_grad) grad_mag = NULL;
+  double *g2abs = grad_mag ? (double *)calloc((size_t)(n > 0 ? n : 1) * 10, sizeof(double)) : NULL;
   int64_t cap = 256;
   contrib_t *list = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)cap);
   double L = 0.0;
@@ -582,7 +708,7 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
         /* the caller's upstream gradients of the six composited channels */
         double gF[6];
         for (int k = 0; k < 6; k++) gF[k] = upstream[pix * 6 + k];
-        adjoint_pixel(list, nl, P, G, gF, g2);
+        adjoint_pixel(list, nl, P, G, gF, g2, g2abs);
       }
       if (targets) {
         const double *tg = targets + pix * 4;
@@ -629,7 +755,7 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
               gF[4] += lw; gF[5] += -lw;
             }
           }
-          adjoint_pixel(list, nl, P, G, gF, g2);
+          adjoint_pixel(list, nl, P, G, gF, g2, g2abs);
         }
       }
       out_flags[pix] = flags;
@@ -643,114 +769,20 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
     for (int64_t id = 0; id < n; id++) {
       const proj_t *p = &P[id];
       if (!p->vis) continue;
-      const double *gg = g2 + id * 10;
-      double x = p->p[0], y = p->p[1], z = p->p[2];
-      /* conic -> 2D covariance: dL/dSigma' = -Q Gq Q (symmetric matrix form) */
-      double Q[4] = {p->a, p->b, p->b, p->c};
-      double Gq[4] = {gg[2], 0.5 * gg[3], 0.5 * gg[3], gg[4]};
-      double QG[4], dS2[4];
-      for (int r = 0; r < 2; r++)
-        for (int s = 0; s < 2; s++)
-          QG[2 * r + s] = Q[2 * r] * Gq[s] + Q[2 * r + 1] * Gq[2 + s];
-      for (int r = 0; r < 2; r++)
-        for (int s = 0; s < 2; s++)
-          dS2[2 * r + s] = -(QG[2 * r] * Q[s] + QG[2 * r + 1] * Q[2 + s]);
-      const double *J = p->J;
-      /* dL/dSc = J^T dS2 J */
-      double dSc[9];
-      for (int r = 0; r < 3; r++)
-        for (int s = 0; s < 3; s++) {
-          double acc2 = 0;
-          for (int k = 0; k < 2; k++)
-            for (int l = 0; l < 2; l++) acc2 += J[3 * k + r] * dS2[2 * k + l] * J[3 * l + s];
-          dSc[3 * r + s] = acc2;
+      chain_gauss(p, R, fx, fy, g2 + id * 10, grads ? grads + id * G_STRIDE : NULL, pg);
+      if (grad_mag) {
+        /* |J| times the sum of the pixel terms' magnitudes: the chain of
+         * each unit 2D word, taken in absolute value */
+        double *mag = grad_mag + id * G_STRIDE;
+        for (int k = 0; k < 10; k++) {
+          const double a = g2abs[id * 10 + k];
+          if (a == 0.0) continue;
+          double e[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, col[G_STRIDE], pcol[6] = {0, 0, 0, 0, 0, 0};
+          for (int c = 0; c < G_STRIDE; c++) col[c] = 0.0;
+          e[k] = 1.0;
+          chain_gauss(p, R, fx, fy, e, col, pcol);
+          for (int c = 0; c < G_STRIDE; c++) mag[c] += fabs(col[c]) * a;
         }
-      /* dL/dJ = 2 dS2 J Sc */
-      double JSc[6], dJ[6];
-      for (int r = 0; r < 2; r++)
-        for (int s = 0; s < 3; s++) {
-          double acc2 = 0;
-          for (int k = 0; k < 3; k++) acc2 += J[3 * r + k] * p->Sc[3 * k + s];
-          JSc[3 * r + s] = acc2;
-        }
-      for (int r = 0; r < 2; r++)
-        for (int s = 0; s < 3; s++) dJ[3 * r + s] = 2.0 * (dS2[2 * r] * JSc[s] + dS2[2 * r + 1] * JSc[3 + s]);
-      /* dL/dp (camera-space mean) */
-      double dp[3] = {0, 0, 0};
-      dp[0] += gg[0] * fx / z;
-      dp[2] += gg[0] * (-fx * x / (z * z));
-      dp[1] += gg[1] * fy / z;
-      dp[2] += gg[1] * (-fy * y / (z * z));
-      dp[2] += gg[6];
-      dp[2] += dJ[0] * (-fx / (z * z));
-      dp[2] += dJ[4] * (-fy / (z * z));
-      if (!p->clx) {
-        dp[0] += dJ[2] * (-fx / (z * z));
-        dp[2] += dJ[2] * (2.0 * fx * x / (z * z * z));
-      } else {
-        dp[2] += dJ[2] * (fx * p->tx / (z * z));
-      }
-      if (!p->cly) {
-        dp[1] += dJ[5] * (-fy / (z * z));
-        dp[2] += dJ[5] * (2.0 * fy * y / (z * z * z));
-      } else {
-        dp[2] += dJ[5] * (fy * p->ty / (z * z));
-      }
-      /* pose: rho += dp; phi += p x dp + covariance term */
-      pg[0] += dp[0]; pg[1] += dp[1]; pg[2] += dp[2];
-      pg[3] += y * dp[2] - z * dp[1];
-      pg[4] += z * dp[0] - x * dp[2];
-      pg[5] += x * dp[1] - y * dp[0];
-      double Am[9];
-      mm3(p->Sc, dSc, Am);
-      pg[3] += 2.0 * (Am[5] - Am[7]);
-      pg[4] += 2.0 * (Am[6] - Am[2]);
-      pg[5] += 2.0 * (Am[1] - Am[3]);
-
-      if (grads) {
-        double *out = grads + id * G_STRIDE;
-        /* mean: p = R mu + t */
-        for (int k = 0; k < 3; k++)
-          out[G_MX + k] += R[k] * dp[0] + R[3 + k] * dp[1] + R[6 + k] * dp[2];
-        /* world covariance: dSig = R^T dSc R */
-        double Rt[9], tmp[9], dSig[9];
-        tr3(R, Rt);
-        mm3(Rt, dSc, tmp);
-        mm3(tmp, R, dSig);
-        /* Sig = M M^T, M = Rq diag(S): dM = 2 dSig M */
-        double M[9], dM[9];
-        for (int r = 0; r < 3; r++)
-          for (int s = 0; s < 3; s++) M[3 * r + s] = p->Rq[3 * r + s] * p->S[s];
-        mm3(dSig, M, dM);
-        for (int k = 0; k < 9; k++) dM[k] *= 2.0;
-        double dRq[9];
-        for (int s = 0; s < 3; s++) {
-          double dSs = 0;
-          for (int r = 0; r < 3; r++) {
-            dSs += p->Rq[3 * r + s] * dM[3 * r + s];
-            dRq[3 * r + s] = dM[3 * r + s] * p->S[s];
-          }
-          out[G_S0 + s] += dSs * p->S[s];
-        }
-        double w = p->nq[0], qx = p->nq[1], qy = p->nq[2], qz = p->nq[3];
-        double dn[4];
-        dn[0] = dRq[1] * (-2 * qz) + dRq[2] * (2 * qy) + dRq[3] * (2 * qz) + dRq[5] * (-2 * qx) +
-                dRq[6] * (-2 * qy) + dRq[7] * (2 * qx);
-        dn[1] = dRq[1] * (2 * qy) + dRq[2] * (2 * qz) + dRq[3] * (2 * qy) + dRq[4] * (-4 * qx) +
-                dRq[5] * (-2 * w) + dRq[6] * (2 * qz) + dRq[7] * (2 * w) + dRq[8] * (-4 * qx);
-        dn[2] = dRq[0] * (-4 * qy) + dRq[1] * (2 * qx) + dRq[2] * (2 * w) + dRq[3] * (2 * qx) +
-                dRq[5] * (2 * qz) + dRq[6] * (-2 * w) + dRq[7] * (2 * qz) + dRq[8] * (-4 * qy);
-        dn[3] = dRq[0] * (-4 * qz) + dRq[1] * (-2 * w) + dRq[2] * (2 * qx) + dRq[3] * (2 * w) +
-                dRq[4] * (-4 * qz) + dRq[5] * (2 * qy) + dRq[6] * (2 * qx) + dRq[7] * (2 * qy);
-        double ndn = w * dn[0] + qx * dn[1] + qy * dn[2] + qz * dn[3];
-        out[G_QW] += (dn[0] - w * ndn) / p->qlen;
-        out[G_QX] += (dn[1] - qx * ndn) / p->qlen;
-        out[G_QY] += (dn[2] - qy * ndn) / p->qlen;
-        out[G_QZ] += (dn[3] - qz * ndn) / p->qlen;
-        out[G_LOGIT] += gg[5] * p->o * (1.0 - p->o);
-        out[G_CR] += gg[7];
-        out[G_CG] += gg[8];
-        out[G_CB] += gg[9];
       }
     }
     if (pose_grad)
@@ -758,6 +790,7 @@ int oracle_render(int64_t n, const double *G, const double *cam, const double *p
   }
   free(list);
   free(g2);
+  free(g2abs);
   free(cs.start);
   free(cs.ids);
   free(order);

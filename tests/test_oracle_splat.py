@@ -473,3 +473,24 @@ def test_upstream_of_the_l1_loss_reproduces_the_loss_adjoint():
     r2 = oracle.render(G, cam, pose, upstream=up, grads=True)
     np.testing.assert_allclose(r2["grad"], r["grad"], rtol=1e-12, atol=1e-14 * np.abs(r["grad"]).max())
     np.testing.assert_allclose(r2["pose_grad"], r["pose_grad"], rtol=1e-12, atol=1e-14)
+
+
+def test_gradient_magnitude_bounds_the_gradient_and_is_exact_for_one_signed_sum():
+    # grad_mag = sum over pixels and 2D words of |term| |d param / d word|:
+    # (1) it bounds |grad| (triangle inequality); (2) for the colour, whose
+    # chain is the identity, an all-positive upstream on the colour channels
+    # makes every term positive, so grad_mag equals grad exactly; (3) it
+    # scales with |upstream|.
+    G, cam, pose, _ = fd_scene(15)
+    W, H = int(cam[4]), int(cam[5])
+    up = np.random.default_rng(7).normal(size=(W * H, 6))
+    r = oracle.render(G, cam, pose, upstream=up, grads=True, grad_mag=True)
+    assert np.all(r["grad_mag"] >= np.abs(r["grad"]) * (1 - 1e-12))
+    r3 = oracle.render(G, cam, pose, upstream=-3.0 * up, grads=True, grad_mag=True)
+    np.testing.assert_allclose(r3["grad_mag"], 3.0 * r["grad_mag"], rtol=1e-12, atol=0)
+    pos = np.zeros((W * H, 6))
+    pos[:, 0:3] = np.abs(up[:, 0:3]) + 0.1
+    rp = oracle.render(G, cam, pose, upstream=pos, grads=True, grad_mag=True)
+    cols = [12, 13, 14]                      # colour slots
+    np.testing.assert_allclose(rp["grad_mag"][:, cols], rp["grad"][:, cols], rtol=1e-12, atol=0)
+    assert np.all(rp["grad"][:, cols] >= 0)
