@@ -21,7 +21,18 @@ IMG_RTOL, IMG_ATOL, IMG_NORM = 1e-5, 1e-7, 1e-5
 T_RTOL, T_NORM = 1e-4, 1e-5
 W_ATOL = 1e-5
 GRAD_NORM = 1e-4          # per parameter group, L2, relative
-GRAD_ELEM = 1e-4          # elementwise relative where |g| > GRAD_FLOOR * max |g| of the group
+# Elementwise, on every entry above GRAD_FLOOR of its group's largest
+# magnitude: |g_gpu - g| <= GRAD_ELEM |g| + GRAD_KAPPA M, with M the oracle's
+# magnitude of the terms the entry sums (grad_mag: sum over pixels and 2D
+# words of |term| |d param / d word|). The FP32 path rounds each pixel term
+# (about 15 operations), each 2D-gradient sum (the warp's shuffle tree and
+# the atomics across warps and tiles) and the chain to the parameter (about
+# 30 operations) relatively, so its error is a few tens of 2^-24 times M,
+# whatever the cancellation: where the terms do not cancel (M ~ |g|) the
+# bound is the stated 1e-4 relative; where they cancel a hundredfold it
+# grows with M, as any FP32 evaluation of the sum must.
+GRAD_ELEM = 1e-4
+GRAD_KAPPA = 2e-6
 GRAD_FLOOR = 1e-3
 POSE_REL = 1e-4           # pose twist gradient, L2, relative
 LOSS_REL = 1e-5
@@ -62,7 +73,7 @@ def mask_flagged_targets(sc, lc=None):
 def oracle_views(sc, grads=True, lc=None):
     G = oracle.params_from_records(sc.records)
     cam = oracle.camera_vec(*sc.camera.as_tuple())
-    outs = [oracle.render(G, cam, sc.poses[v], lc=lc, targets=sc.targets[v], grads=grads)
+    outs = [oracle.render(G, cam, sc.poses[v], lc=lc, targets=sc.targets[v], grads=grads, grad_mag=grads)
             for v in range(sc.poses.shape[0])]
     return G, cam, outs
 
@@ -111,24 +122,32 @@ def compare_image(img, ref_pix, flags, report=None, label=""):
 GROUPS = {"mean": [0, 1, 2], "logit": [3], "quat": [4, 5, 6, 7], "logscale": [8, 9, 10], "colour": [12, 13, 14]}
 
 
-def compare_grads(gg, ref_grad, report=None, elementwise=True):
-    """gg: (n, 16) GPU; ref_grad: (n, 15) oracle. Returns the per-group
-    relative L2 errors; with elementwise, also asserts the elementwise
-    relative error <= GRAD_ELEM on every entry above GRAD_FLOOR of its group's
-    largest magnitude."""
+def compare_grads(gg, ref_grad, report=None, mag=None, elementwise=True):
+    """gg: (n, 16) GPU; ref_grad: (n, 15) oracle; mag: (n, 15) the oracle's
+    grad_mag (for a sum over views, the sum of the views'). Returns the
+    per-group relative L2 errors; with elementwise, also asserts on every
+    entry above GRAD_FLOOR of its group's largest magnitude |d| <= GRAD_ELEM
+    |g| + GRAD_KAPPA M (M = 0 without mag: the plain relative bound)."""
     out = {}
+    fails = []
     for name, cols in GROUPS.items():
         a = gg[:, cols]
         b = ref_grad[:, cols]
+        m = mag[:, cols] if mag is not None else np.zeros_like(b)
         nrm = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
         out[name] = float(nrm)
         big = np.abs(b) > GRAD_FLOOR * np.abs(b).max() if b.size else np.zeros(b.shape, bool)
-        rel = np.abs(a - b)[big] / np.abs(b)[big] if big.any() else np.zeros(0)
+        d = np.abs(a - b)[big]
+        rel = d / np.abs(b)[big] if big.any() else np.zeros(0)
+        ratio = d / (GRAD_ELEM * np.abs(b)[big] + GRAD_KAPPA * m[big]) if big.any() else np.zeros(0)
         el = float(rel.max()) if rel.size else 0.0
+        worst = float(ratio.max()) if ratio.size else 0.0
         if report is not None:
             report.append(f"grad {name}: norm rel={nrm:.3e} elem rel (|g|>{GRAD_FLOOR:g}max)={el:.3e} "
-                          f"over {int(big.sum())} entries")
-        if elementwise:
-            assert el <= GRAD_ELEM, (f"gradient group {name}: elementwise relative error {el:.3e} "
-                                     f"({int((rel > GRAD_ELEM).sum())} of {int(big.sum())} entries above {GRAD_ELEM:g})")
+                          f"(>{GRAD_ELEM:g}: {int((rel > GRAD_ELEM).sum())} of {int(big.sum())}), "
+                          f"worst error / bound {worst:.3f}")
+        if elementwise and worst > 1.0:
+            fails.append(f"{name}: {int((ratio > 1).sum())} of {int(big.sum())} entries beyond "
+                         f"{GRAD_ELEM:g}|g| + {GRAD_KAPPA:g}M (worst {worst:.2f}x, max rel {el:.3e})")
+    assert not fails, "gradient elementwise: " + "; ".join(fails)
     return out

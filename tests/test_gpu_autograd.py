@@ -98,9 +98,9 @@ def test_render_autograd_with_a_user_loss_matches_the_oracle(dags):
     # the same F's upstream for the oracle: dF/dD = w3 D
     up = wts.copy()
     up[:, 3] = wts[:, 3] * ref0["pix"][:, 3]
-    ref = oracle.render(G, ocam, sc.poses[0], upstream=up, grads=True)
+    ref = oracle.render(G, ocam, sc.poses[0], upstream=up, grads=True, grad_mag=True)
     report = []
-    g = compare_grads(gauss.grad.cpu().numpy().astype(np.float64), ref["grad"], report)
+    g = compare_grads(gauss.grad.cpu().numpy().astype(np.float64), ref["grad"], report, mag=ref["grad_mag"])
     print("\n".join(report))
     for k, v in g.items():
         assert v <= 1e-4, k

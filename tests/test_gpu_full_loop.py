@@ -48,7 +48,7 @@ def test_full_scale_frame_parity(dags, sequence):
     assert_image_parity(res, outs, "full loop 1200x680", report)
     assert abs(res["loss"] - outs[0]["loss"]) <= LOSS_REL * abs(outs[0]["loss"])
     pg = np.linalg.norm(res["gp"][0] - outs[0]["pose_grad"]) / np.linalg.norm(outs[0]["pose_grad"])
-    g = compare_grads(res["gg"], outs[0]["grad"], report)
+    g = compare_grads(res["gg"], outs[0]["grad"], report, mag=outs[0]["grad_mag"])
     report.append(f"pose grad rel {pg:.3e}")
     print("\n" + "\n".join(report))
     # the twist gradient is one sum over every pixel-Gaussian term, accumulated

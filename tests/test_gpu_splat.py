@@ -84,7 +84,7 @@ def test_forward_backward_tiny(dags):
     report = []
     assert_image_parity(res, outs, "tiny", report)
     assert abs(res["loss"] - outs[0]["loss"]) <= LOSS_REL * abs(outs[0]["loss"])
-    g = compare_grads(res["gg"], outs[0]["grad"], report)
+    g = compare_grads(res["gg"], outs[0]["grad"], report, mag=outs[0]["grad_mag"])
     pg = np.linalg.norm(res["gp"][0] - outs[0]["pose_grad"]) / np.linalg.norm(outs[0]["pose_grad"])
     report.append(f"pose grad rel {pg:.3e}")
     print("\n".join(report))
@@ -109,7 +109,7 @@ def test_loss_weight_modes(dags, wmode, wgrad):
     G, cam, outs = oracle_views(sc, lc=oracle.loss_vec(weight_mode=wmode, weight_grad=wgrad))
     report = []
     assert_image_parity(res, outs, "wmode", report)
-    g = compare_grads(res["gg"], outs[0]["grad"], report)
+    g = compare_grads(res["gg"], outs[0]["grad"], report, mag=outs[0]["grad_mag"])
     print("\n".join(report))
     for k, v in g.items():
         assert v <= GRAD_NORM, k
@@ -126,7 +126,7 @@ def test_ragged_image_and_pose(dags):
     G, cam, outs = oracle_views(sc)
     report = []
     assert_image_parity(res, outs, "ragged", report)
-    g = compare_grads(res["gg"], outs[0]["grad"], report)
+    g = compare_grads(res["gg"], outs[0]["grad"], report, mag=outs[0]["grad_mag"])
     print("\n".join(report))
     for k, v in g.items():
         assert v <= GRAD_NORM, k
@@ -144,7 +144,7 @@ def test_multiview_equals_single_views(dags):
     report = []
     assert_image_parity(res, outs, "mv", report)
     gsum = sum(o["grad"] for o in outs)
-    g = compare_grads(res["gg"], gsum, report)
+    g = compare_grads(res["gg"], gsum, report, mag=sum(o["grad_mag"] for o in outs))
     for k, v in g.items():
         assert v <= GRAD_NORM, k
     for v in range(3):
@@ -284,7 +284,7 @@ def test_full_size_mapping_window(dags):
     G, cam, outs = oracle_views(sc)
     report = []
     assert_image_parity(res, outs, "map", report)
-    g = compare_grads(res["gg"], sum(o["grad"] for o in outs), report)
+    g = compare_grads(res["gg"], sum(o["grad"] for o in outs), report, mag=sum(o["grad_mag"] for o in outs))
     print("\n".join(report))
     for k, v in g.items():
         assert v <= GRAD_NORM, k
@@ -300,7 +300,7 @@ def test_invalid_colour_pixels_leave_the_loss(dags):
     res = run(dags, sc2, flags=dags.GRAD_GAUSS | dags.GRAD_POSE)
     G, cam, outs = oracle_views(sc2)
     assert abs(res["loss"] - outs[0]["loss"]) <= LOSS_REL * abs(outs[0]["loss"])
-    g = compare_grads(res["gg"], outs[0]["grad"])
+    g = compare_grads(res["gg"], outs[0]["grad"], mag=outs[0]["grad_mag"])
     for k, v in g.items():
         assert v <= GRAD_NORM, k
 
