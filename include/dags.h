@@ -114,8 +114,11 @@ void dags_default_pose_cfg(dags_pose_cfg *cfg);
 
 /* Create a context on the current CUDA device with workspace for up to
  * max_gaussians Gaussians, images up to max_width x max_height, max_views
- * views per call and max_pairs (tile, Gaussian) pairs per call (0 picks
- * 16 * max_gaussians * max_views). Allocates device memory (cudaMalloc).
+ * views per call and max_pairs (tile, Gaussian) pairs per call (0 picks the
+ * larger of 16 * max_gaussians * max_views and min(max_gaussians, 4096) *
+ * tiles * max_views, so that splat_track's fixed-capacity tile buckets hold
+ * at least min(max_gaussians, 4096) entries each). Allocates device memory
+ * (cudaMalloc).
  * Returns DAGS_E_INVAL / DAGS_E_NOMEM / DAGS_E_CUDA on failure (*out = NULL). */
 int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_t max_height,
                 int32_t max_views, int64_t max_pairs);

@@ -266,7 +266,14 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   if (max_gaussians < 0 || max_gaussians > (int64_t)0x7FFFFFFF || max_width <= 0 || max_height <= 0 ||
       max_width > 32768 || max_height > 32768 || max_views < 1 || max_views > 64 || max_pairs < 0)
     return DAGS_E_INVAL;
-  if (max_pairs == 0) max_pairs = 16 * max_gaussians * (int64_t)max_views;
+  if (max_pairs == 0) {
+    // 16 pairs per Gaussian and view, and at least min(N, 4096) slots per
+    // tile for the fixed-capacity buckets of the tracking loop
+    const int64_t tiles = (int64_t)((max_width + kTile - 1) / kTile) * ((max_height + kTile - 1) / kTile);
+    const int64_t per_tile = max_gaussians < 4096 ? max_gaussians : 4096;
+    max_pairs = 16 * max_gaussians * (int64_t)max_views;
+    if (per_tile * tiles * max_views > max_pairs) max_pairs = per_tile * tiles * max_views;
+  }
   if (max_pairs < 1024) max_pairs = 1024;
   if (max_pairs > (int64_t)0xFFFFFFFE) return DAGS_E_INVAL;
   dags_ctx *c = new (std::nothrow) dags_ctx();

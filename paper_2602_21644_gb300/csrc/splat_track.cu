@@ -55,7 +55,9 @@ render_track_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ t
   const int comp = rs_component<6>(lane);
   const bool writer = __ffs(__match_any_sync(FULL, (unsigned)comp)) - 1 == lane;
 
-  const bool own_sort = sort_tile_bucket(ws, s, (int)(e - s), s_key);
+  // the order stays in shared memory for lists that fit (both passes read it
+  // there); longer lists are merged through sorted_ids
+  const bool own_sort = sort_tile_bucket(ws, s, (int)(e - s), s_key, false);
   for (int k = tid; k < (kTilePix / 32) * kMaskGroups; k += kTilePix) (&s_cm[0][0])[k] = 0u;
 
   // stages list entries [base, base + cnt) of the tile (called by the CTA)

@@ -62,9 +62,12 @@ __device__ __forceinline__ bool pairs_overflow_ws(const Workspace &ws) {
 // in sorted_ids[s, s + len): in shared memory (s_key, kSortSmallCap keys) when
 // the bucket fits, then the sorted keys stay in s_key and the function
 // returns true; otherwise out of core (chunks sorted in shared memory, then
-// merged pairwise through global memory) and it returns false. Called by all
-// threads of the CTA.
-__device__ __forceinline__ bool sort_tile_bucket(const Workspace &ws, uint32_t s, int len, uint64_t *s_key) {
+// merged pairwise through global memory) and it returns false. With
+// publish_small = false a bucket sorted in shared memory is not copied to
+// sorted_ids (for a caller that reads its order from s_key only). Called by
+// all threads of the CTA.
+__device__ __forceinline__ bool sort_tile_bucket(const Workspace &ws, uint32_t s, int len, uint64_t *s_key,
+                                                 bool publish_small = true) {
   const int tid = threadIdx.x;
   const bool own_sort = len <= kSortSmallCap;
   if (own_sort && len > 0) {
@@ -72,7 +75,8 @@ __device__ __forceinline__ bool sort_tile_bucket(const Workspace &ws, uint32_t s
     for (int k = tid; k < len2; k += kTilePix) s_key[k] = k < len ? ws.keys[s + k] : ~0ull;
     __syncthreads();
     bitonic_smem(s_key, len2);
-    for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)s_key[k];
+    if (publish_small)
+      for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)s_key[k];
   } else if (len > 0) {
     uint64_t *src = ws.keys + s, *dst = ws.keys_tmp + s;
     for (int c0 = 0; c0 < len; c0 += kSortSmallCap) {

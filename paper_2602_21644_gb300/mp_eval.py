@@ -49,6 +49,9 @@ class Sequence:
         self.rec[:, 11] = 0.2                      # uninformed initial MP
         moving = [k for k, ob in enumerate(self.objs) if np.any(ob.velocity != 0)]
         self.dynamic = np.isin(self.oid, moving)
+        self.velocity = np.zeros((n_gauss, 3), np.float32)
+        for k, ob in enumerate(self.objs):
+            self.velocity[self.oid == k] = ob.velocity
         f = 525.0 * width / 640.0                  # the 640x480 rig's field of view
         self.cam = synth.Camera(f, f, width / 2.0, height / 2.0, width, height)
         self.poses = synth.camera_path(n_frames)
@@ -97,12 +100,17 @@ class Runner:
         self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out)
         return out
 
-    def run(self, mode, net=None, collect=False, schedule=None):
+    def run(self, mode, net=None, collect=False, schedule=None, follow=False):
         """mode: 'fresh' (fresh prior every frame), 'stale' (the method without
         the network), 'learned' (network proposal between refreshes).
         Refreshes come every REFRESH frames, or from the semantic-on-demand
-        trigger (Eqs. (13)-(16)) when schedule (a dags_sched_cfg) is given."""
+        trigger (Eqs. (13)-(16)) when schedule (a dags_sched_cfg) is given.
+        follow: the map's moving-object Gaussians are placed at their frame's
+        positions before each frame (a map that mapping keeps up to date), so
+        that the frame's residuals come from the observation noise only."""
         gauss = torch.from_numpy(self.seq.rec.copy()).cuda()
+        base = gauss[:, 0:3].clone()
+        vel = torch.from_numpy(self.seq.velocity).cuda()
         labels = torch.zeros(self.seq.n, dtype=torch.uint8, device="cuda")
         state = torch.zeros(2, dtype=torch.int32, device="cuda")
         score = torch.zeros(3, dtype=torch.float64, device="cuda")
@@ -110,6 +118,8 @@ class Runner:
         nxt, last_ref = True, 0
         for f in range(len(self.seq.poses)):
             pose, tg = self.frame_inputs(f)
+            if follow:
+                gauss[:, 0:3] = base + vel * (f / 30.0)
             image = self.render(gauss, pose)
             if mode == "fresh":
                 refreshed = True
@@ -145,10 +155,10 @@ class Runner:
         return hist
 
 
-def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0):
+def train_net(dags, runner, steps=1000, lr=2e-3, batch=16, seed=0, follow=False):
     """Adam training on the fresh-prior maps of the runner's sequence; returns
     (weight blob, per-step losses)."""
-    hist = runner.run("stale", collect=True)
+    hist = runner.run("stale", collect=True, follow=follow)
     feats = torch.stack([h["feats"] for h in hist])                    # [T, H, W, 8]
     target = torch.stack([h["target"].reshape(runner.seq.height, runner.seq.width) for h in hist])
     return train_on(runner.ctx, feats, target, steps, lr, batch, seed)
@@ -180,17 +190,21 @@ def iou(a, b):
     return np.logical_and(a, b).sum() / u if u else 1.0
 
 
-def experiment(dags, steps=1000):
-    """Train on one sequence, run fresh / stale / learned on the held-out one."""
+def experiment(dags, steps=1000, follow=False):
+    """Train on one sequence, run fresh / stale / learned on the held-out one.
+    follow: the map keeps its moving objects at their current positions (see
+    Runner.run), in training and evaluation."""
     train_seq = Sequence(seed=11, velocities=[(0.0, 0.0, 0.3), (-0.3, 0.0, 0.0)], n_frames=60)
     tr = Runner(dags, train_seq)
-    net, losses = train_net(dags, tr, steps=steps)
+    net, losses = train_net(dags, tr, steps=steps, follow=follow)
     tr.ctx.close()
     eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=40)
     ev = Runner(dags, eval_seq)
-    out = dict(losses=losses, fresh=ev.run("fresh"), stale=ev.run("stale"), learned=ev.run("learned", net=net),
-               scheduled=ev.run("stale", schedule=dags.default_sched_cfg()),
-               scheduled_learned=ev.run("learned", net=net, schedule=dags.default_sched_cfg()), seq=eval_seq)
+    sc = dags.default_sched_cfg()
+    out = dict(losses=losses, fresh=ev.run("fresh", follow=follow), stale=ev.run("stale", follow=follow),
+               learned=ev.run("learned", net=net, follow=follow),
+               scheduled=ev.run("stale", schedule=sc, follow=follow),
+               scheduled_learned=ev.run("learned", net=net, schedule=sc, follow=follow), seq=eval_seq)
     ev.ctx.close()
     return out
 
