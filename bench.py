@@ -227,8 +227,9 @@ def replica_throughput(iters_per_step: int, steps: int, world: int, t_ms_max: fl
 # ------------------------------------------------------------------ our arm
 
 def algorithmic_bytes(n, nv, K, P):
-    """Compulsory bytes per kernel launch (pose-only mode): each stage reads
-    its inputs and writes its outputs once."""
+    """Compulsory bytes per stage of one pose-only iteration: each stage
+    reads its inputs and writes its outputs once (the method's stages,
+    whatever kernels run them)."""
     return {"preprocess": 64 * n + 48 * nv,
             "emit": 12 * K,
             "tile_sort": 24 * K,
@@ -236,6 +237,21 @@ def algorithmic_bytes(n, nv, K, P):
             "render_bwd": 52 * K + 48 * P + 24 * nv,
             "preprocess_bwd": 64 * nv + 24 * nv,
             "pose_step": 6 * 8 + 13 * 8 * 2 + 12 * 8 * 2}
+
+
+def kernel_bytes(n, nv, K, P):
+    """Compulsory bytes per launch of the tracking loop's kernels: the
+    preprocess reads every record and writes the projected records and the
+    keys into the tile buckets; the forward sorts its keys (read 8, write 4
+    bytes per pair), reads each pair's projected record and the targets, and
+    writes the image (8 planes) and last; the adjoint reads each pair's id
+    and record, the targets, the image and last, and adds the 2D gradients
+    (6 words per visible Gaussian); the pose chain reads the records and 2D
+    gradients of the visible Gaussians."""
+    return {"preprocess": 64 * n + 48 * nv + 8 * K,
+            "render_fwd": 12 * K + 52 * K + 16 * P + 36 * P,
+            "render_bwd": 52 * K + 16 * P + 36 * P + 24 * nv,
+            "preprocess_bwd": 64 * nv + 24 * nv}
 
 
 # FP32 lane operations of the compositing loops (the method's arithmetic; an
@@ -630,13 +646,18 @@ def splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, f
     mctx = dags.Context(mg.shape[0], mcam.width, mcam.height, ms.poses.shape[0])
 
     mprev = mg.clone()          # the records after the previous mapping update (Eq. (23))
+    mstate = mctx.gauss_adam_state(mg)
+    mstep = [0]
 
     def map_iter():
-        # Eq. (27) without the edge term: MP-weighted L1 of every view, then
-        # lambda_3 L_MP added into the Gaussian gradient
+        # Eq. (27) without the edge term: MP-weighted L1 of every view,
+        # lambda_3 L_MP added into the Gaussian gradient, then the Adam step
+        # on the Gaussian parameters
         image, last, _ = mctx.forward(mg, mcam, mp, mt)
         gg, _ = mctx.backward(mg, mcam, mp, mt, image, last, flags)
         mctx.mp_consistency(mg, mprev, 500.0, grad=gg, want_loss=False)
+        mstep[0] += 1
+        mctx.gauss_adam_step(mg, mstate, gg, mstep[0])
 
     t_map = time_it(map_iter)
     # the regulariser alone at the tracking map's size: HBM-bound, 80 bytes
@@ -651,13 +672,47 @@ def splat_variants_section(args, ctx, dags, synth, gauss, cam, targets, poses, f
     ctx.check()
     mctx.check()
     mctx.close()
-    return {"full_param_fwd_bwd": {"workload": f"{gauss.shape[0]} Gaussians, {cam.width}x{cam.height}, one view, "
+    # the tiny scene (2,000 Gaussians, 160x120): fwd+bwd of all parameters
+    # and the pose on the GPU, and 100 iterations of the FP64 oracle on one
+    # host core, as the same units
+    ts = synth.tiny_scene(0)
+    tcam = dags.Camera(*ts.camera.as_tuple())
+    tgx = torch.from_numpy(ts.records).cuda()
+    tpx = torch.from_numpy(np.ascontiguousarray(ts.poses)).cuda()
+    ttx = torch.from_numpy(np.ascontiguousarray(ts.targets)).cuda()
+    tctx = dags.Context(tgx.shape[0], tcam.width, tcam.height, 1)
+
+    def tiny_iter():
+        image, last, _ = tctx.forward(tgx, tcam, tpx, ttx)
+        tctx.backward(tgx, tcam, tpx, ttx, image, last, flags)
+
+    t_tiny = time_it(tiny_iter, reps=20)
+    torch.cuda.synchronize()
+    tctx.check()
+    tctx.close()
+    tiny = {"workload": "2000 Gaussians, 160x120, one view, gradients of all Gaussian parameters and the pose",
+            "ms_per_iter": round(t_tiny, 4), "iters_per_s": round(1e3 / t_tiny, 2)}
+    if not args.no_cpu_baseline:
+        import oracle
+        G = oracle.params_from_records(ts.records)
+        ocam = oracle.camera_vec(*ts.camera.as_tuple())
+        oracle.render(G, ocam, ts.poses[0], targets=ts.targets[0], grads=True)
+        t0 = time.perf_counter()
+        for _ in range(100):
+            oracle.render(G, ocam, ts.poses[0], targets=ts.targets[0], grads=True)
+        dt = time.perf_counter() - t0
+        tiny["cpu_baseline"] = {"value": round(100 / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"100 fwd+bwd iterations (all gradients) of the tiny scene, FP64 C, "
+                                          f"{dt:.2f} s"}
+    return {"tiny": tiny,
+            "full_param_fwd_bwd": {"workload": f"{gauss.shape[0]} Gaussians, {cam.width}x{cam.height}, one view, "
                                                "gradients of all Gaussian parameters and the pose",
                                    "ms_per_iter": round(t_full, 4), "iters_per_s": round(1e3 / t_full, 2)},
             "mapping": {"workload": f"200000 Gaussians, 8 keyframes of {mcam.width}x{mcam.height}, render + "
                                     "backward of all views w.r.t. all parameters",
                         "ms_per_iter": round(t_map, 4), "iters_per_s": round(1e3 / t_map, 2),
-                        "includes": "lambda_3 L_MP gradient (Eqs. (23), (24))"},
+                        "includes": "lambda_3 L_MP gradient (Eqs. (23), (24)) and the Adam step on the "
+                                    "Gaussian parameters"},
             "mp_consistency": {"workload": f"lambda_3 L_MP and its gradient over {gauss.shape[0]} Gaussians",
                                "us": round(1e3 * t_reg, 3), "alg_bytes": reg_bytes,
                                "hbm_frac": round(reg_bytes / (t_reg * 1e-3) / 1e9 / hbm, 4)}}
@@ -724,6 +779,10 @@ def run_ours(args):
     frame(use_graph=False)
     torch.cuda.synchronize()
     ctx.check()
+    # the pairs K and visible Gaussians N_v at the frame's final pose (a
+    # plain forward: the tracking loop keeps its lists in the fixed-bucket
+    # layout)
+    ctx.forward(gauss, cam, poses, targets, image=image, last=last, loss=loss)
     start_bins, ids = ctx.copy_bins(1, cam)
     K = int(len(ids))
     nv = int(len(np.unique(ids)))
@@ -766,12 +825,18 @@ def run_ours(args):
     # compositing kernels also count the exponents they evaluate and the
     # contributions among them (one atomic per warp and counter)
     ctx.timing_read()
+    t_direct = timed(args.steps, lambda: frame(use_graph=False), timing=True)
+    kt = ctx.timing_read()
+    # the compositing kernels' evaluation counts, in a pass of their own (the
+    # counting variants of the kernels are not the timed ones)
     ctx.eval_read()
     ctx.eval_counting(True)
-    t_direct = timed(args.steps, lambda: frame(use_graph=False), timing=True)
+    n_count = min(args.steps, 5)
+    for _ in range(n_count):
+        frame(use_graph=False)
     ctx.eval_counting(False)
-    kt = ctx.timing_read()
     evals = ctx.eval_read()
+    count_launches = n_count * args.iters
 
     # e2e: public API with host buffers; every step copies the frame (RGB-D
     # target) and the starting pose from pinned host memory and reads back the
@@ -809,7 +874,7 @@ def run_ours(args):
 
     peaks, src = load_peaks()
     hbm = float(peaks["hbm_gbs"])
-    ab = algorithmic_bytes(n, nv, K, P)
+    ab = kernel_bytes(n, nv, K, P)
     kernels = {}
     kt_total = sum(ms for ms, _ in kt.values())
     for name, (ms, cnt) in kt.items():
@@ -825,10 +890,12 @@ def run_ours(args):
     # E_listed (every list entry up to each pixel's last contributor) is
     # reported beside them
     E_listed = int(last.to(torch.int64).sum().item())
-    n_fwd = max(1, kt.get("render_fwd", (0, 0))[1])
-    n_bwd = max(1, kt.get("render_bwd", (0, 0))[1])
-    per = {"render_fwd": (evals["fwd_eval"] / n_fwd, evals["fwd_contrib"] / n_fwd, OPS_FWD_CONTRIB, SFU_FWD_CONTRIB),
-           "render_bwd": (evals["bwd_eval"] / n_bwd, evals["bwd_contrib"] / n_bwd, OPS_BWD_CONTRIB, SFU_BWD_CONTRIB)}
+    # the forward's units are its evaluations and contributions, the
+    # adjoint's its own (the kernels count them)
+    fe, fc = evals["fwd_eval"] / count_launches, evals["fwd_contrib"] / count_launches
+    be, bc = evals["bwd_eval"] / count_launches, evals["bwd_contrib"] / count_launches
+    per = {"render_fwd": (fe, fc, OPS_FWD_CONTRIB, SFU_FWD_CONTRIB),
+           "render_bwd": (be, bc, OPS_BWD_CONTRIB, SFU_BWD_CONTRIB)}
     for name, (ee, ec, oc, sc) in per.items():
         if name in kernels:
             t_s = kernels[name]["avg_us"] * 1e-6
@@ -862,13 +929,13 @@ def run_ours(args):
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 2), "peak": hbm, "unit": "GB/s",
                 "frac": round(ach / hbm, 4), "traffic": None, "peak_source": f"{src} hbm_gbs (copy)",
                 "alg_bytes_per_launch": ab[dom]}
-    iter_bytes = sum(ab.values())
+    iter_bytes = sum(algorithmic_bytes(n, nv, K, P).values())
     iter_us = 1e3 * t_ms / (args.iters * args.steps)
-    # kernels per step: per iteration preprocess, tile scan, emit, render_fwd,
-    # render_bwd, preprocess_bwd (pose step fused); per frame the MP update's 8
-    # kernels (pixel sum, pixel var, gauss, apply, 2 select levels, labels,
-    # region stats)
-    gpu_launches = args.steps * (args.iters * 6 + 8)
+    # kernels per step: per iteration the preprocess (with direct binning),
+    # the forward, the adjoint and the pose chain (pose step fused); per frame
+    # the MP update's 9 kernels (pixel sum, pixel var, pixel map, gauss,
+    # apply, 2 select levels, labels, region stats)
+    gpu_launches = args.steps * (args.iters * 4 + 9)
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

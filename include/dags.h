@@ -271,11 +271,12 @@ int gauss_adam_step(dags_ctx *ctx, float *gauss, int64_t n, float *colour, float
 /* Tracking loop: iters x { the forward with loss of splat_forward, the
  * pose-only backward of splat_backward (DAGS_GRAD_POSE), pose_step } on one
  * view, enqueued by the library -- the pose refinement of the tracking thread
- * (Sec. III) with the pose part of Eq. (27). Each iteration is three kernels:
+ * (Sec. III) with the pose part of Eq. (27). Each iteration is four kernels:
  * projection and binning straight into per-tile buckets of max_pairs /
- * tiles slots each, one fused kernel that composites, forms the loss and
- * runs the pose adjoint per tile, and the chain to the pose twist with the
- * FP64 pose step. pose (device, 12 doubles) and adam_state (device, 13
+ * tiles slots each (no scan or emit pass), the forward with loss, which also
+ * records per warp the list entries its pixels took, the pose adjoint, which
+ * visits only those, and the chain to the pose twist with the FP64 pose
+ * step. pose (device, 12 doubles) and adam_state (device, 13
  * doubles) are updated in place; image, last, loss and grad_pose hold the
  * last iteration's values. With use_graph != 0 (and timing off) one
  * iteration and a chunk of ten are captured once into CUDA graphs on a
@@ -632,7 +633,6 @@ enum {
   DAGS_K_LM_STEP,          /* LM: FP64 decision, solve and pose step       */
   DAGS_K_REGULARISER,      /* L_MP and L_edge regularisers                 */
   DAGS_K_EPIPOLAR,         /* epipolar verification and static recovery    */
-  DAGS_K_RENDER_TRACK,     /* tracking: fused compositing + pose adjoint   */
   DAGS_K_GAUSS_ADAM,       /* mapping: Adam step on the Gaussians          */
   DAGS_KERNEL_COUNT
 };

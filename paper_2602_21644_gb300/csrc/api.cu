@@ -88,6 +88,7 @@ struct dags_ctx {
   TrackGraph graph;
   TrackGraph graph_lm;            // captured LM iteration
   LmBuffers lm;                   // allocated by the first LM call
+  uint32_t *warp_masks = nullptr; // [max_tiles][kMaskGroups][8] forward masks of the tracking loop
   double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
   double *edge_partial = nullptr; // per-CTA sums of the edge-warp term (first call)
   float *rel32 = nullptr;         // [12] FP32 relative pose of the regularisers (first call)
@@ -315,6 +316,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&w.vis_n, (size_t)w.max_v));
   A(alloc(&w.counters, (size_t)CNT_N));
   A(alloc(&w.evals, (size_t)4));
+  A(alloc(&c->warp_masks, (size_t)w.max_tiles * kMaskGroups * 8));
   if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
   MpBuffers &mb = c->mp;
@@ -339,6 +341,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
     cudaGetLastError();
     free_mp(c->mp);
     free_ws(w);
+    if (c->warp_masks) cudaFree(c->warp_masks);
     delete c;
     return code;
   }
@@ -361,6 +364,7 @@ void dags_destroy(dags_ctx *ctx) {
   if (ctx->graph_lm.exec_chunk) cudaGraphExecDestroy(ctx->graph_lm.exec_chunk);
   if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
   free_lm(ctx->lm);
+  if (ctx->warp_masks) cudaFree(ctx->warp_masks);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
   if (ctx->edge_partial) cudaFree(ctx->edge_partial);
   if (ctx->rel32) cudaFree(ctx->rel32);
@@ -609,9 +613,10 @@ int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_sta
 
 namespace {
 
-// Enqueues one tracking iteration: projection and binning, the fused
-// forward + pose-only adjoint, and the chain to the pose twist with the pose
-// step in its last CTA (arguments checked by the caller).
+// Enqueues one tracking iteration: projection and binning into the
+// fixed-capacity buckets, the forward with loss, the pose-only adjoint, and
+// the chain to the pose twist with the pose step in its last CTA (arguments
+// checked by the caller).
 int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                     const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                     const dags_pose_cfg *pcfg, double *adam_state, float *image, int32_t *last, double *loss,
@@ -633,9 +638,17 @@ int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_cam
   int ev = tm.begin(DAGS_K_PREPROCESS, s);
   cudaError_t e = launch_preprocess_direct(w, g4, n, pose, r, 8, s);
   tm.end(ev, s);
+  // the forward records, per warp, which list entries its pixels took; the
+  // adjoint visits only those
+  w.warp_masks = ctx->warp_masks;
   if (e == cudaSuccess) {
-    ev = tm.begin(DAGS_K_RENDER_TRACK, s);
-    e = launch_render_track(w, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
+    ev = tm.begin(DAGS_K_RENDER_FWD, s);
+    e = launch_render_fwd(w, 1, n, r, l, reinterpret_cast<const float4 *>(targets), image, last, loss, s);
+    tm.end(ev, s);
+  }
+  if (e == cudaSuccess) {
+    ev = tm.begin(DAGS_K_RENDER_BWD, s);
+    e = launch_render_bwd(w, 1, n, r, l, reinterpret_cast<const float4 *>(targets), image, last, false, s);
     tm.end(ev, s);
   }
   if (e == cudaSuccess) {

@@ -16,6 +16,7 @@ constexpr int kSortSmallCap = 1024;     // tile lists up to this length are sort
 constexpr int kPrepBlock = 128;         // threads per preprocess / emit CTA
 constexpr int kBwdPrepBlock = 128;      // threads per preprocess-backward CTA
 constexpr int kBwdPoseBlocks = 304;     // CTAs of the pose-only preprocess backward (2 per SM)
+constexpr int kMaskGroups = 32;         // list groups of 32 entries with a recorded forward mask (1024 entries)
 
 // Status word bits (device).
 constexpr uint32_t kStatusCapacity = 1u;
@@ -102,6 +103,10 @@ struct Workspace {
   // min(count_t, cap)) and tile_count holds the counts; otherwise the
   // buckets are packed at tile_start offsets.
   uint32_t bucket_cap = 0;
+  // Per tile, warp and 32-entry group of the first kMaskGroups groups: the
+  // entries at least one pixel of the warp took in the forward (one bit
+  // each), for the adjoint of the same iteration; null: not recorded.
+  uint32_t *warp_masks = nullptr;   // [max_tiles][kMaskGroups][8]
 };
 
 // The list range [s, e) of tile t in the workspace's bucket layout.
@@ -172,11 +177,7 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
                                   cudaStream_t s);
 cudaError_t launch_pose_step(double *poses, const double *grad, double *state, int views,
                              const dags_pose_cfg &cfg, cudaStream_t s);
-// Fused forward + pose-only adjoint of one view (splat_track.cu): image,
-// last and the loss as launch_render_fwd writes them, and the 2D gradients of
-// the pose path (words G2_U .. G2_Z) added into ws.grad2d.
-cudaError_t launch_render_track(const Workspace &ws, const Raster &r, const Loss &l, const float4 *targets,
-                                float *image, int32_t *last, double *loss, cudaStream_t s);
+
 
 // Mapping optimiser (gauss_adam.cu).
 cudaError_t launch_gauss_adam_init(const float *gauss, float *colour, float *m, float *v, int64_t n, cudaStream_t s);

@@ -26,8 +26,11 @@ constexpr int kMaxViewsSmem = 64;
 // the reduce-scatter's component k is 2D-gradient word k
 static_assert(G2_U == 0 && G2_Z == 5 && G2_BL == 9 && kGradWords >= 10, "2D-gradient word order");
 
-template <bool FULL>
-__global__ void __launch_bounds__(kTilePix)
+// FULL: every parameter's 2D gradients (else the pose path's six words);
+// MASKS: visit only the entries the forward recorded as taken by the warp
+// (ws.warp_masks); COUNT: count evaluations and contributions (ws.evals).
+template <bool FULL, bool MASKS, bool COUNT>
+__global__ void __launch_bounds__(kTilePix, 5)
 render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ targets,
                   const float *__restrict__ image, const int32_t *__restrict__ last,
                   const float *__restrict__ upstream) {
@@ -51,7 +54,11 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
-  const uint32_t s = ws.tile_start[tile];
+  uint32_t s, e_unused;
+  tile_range(ws, tile, s, e_unused);
+  // the forward's record of the entries this warp's pixels took (groups of
+  // 32 entries; later groups fall back to the box test)
+  const uint32_t *const wmask = MASKS ? ws.warp_masks + (size_t)tile * kMaskGroups * 8 + warp : nullptr;
   const size_t vbase = (size_t)v * ws.max_n;
   const size_t P = (size_t)r.W * r.H;
   const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
@@ -125,15 +132,24 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
     __syncthreads();
     const int cnt = end - beg;
     if (wmax <= beg) continue;               // no pixel of this warp reaches this batch
-    for (int g = (cnt - 1) >> 5; g >= 0; --g) {
-      const int jj = g * 32 + lane;
-      bool hit = false;
-      if (jj < cnt) {
-        const float4 a = s_a[jj];
-        const float2 ex = s_e[jj];
-        hit = fabsf(a.x - bcx) <= ex.x + 3.5f && fabsf(a.y - bcy) <= ex.y + 1.5f;
+    const int top = min(cnt, wmax - beg);    // entries [beg, beg + top) may matter to this warp
+    for (int g = (top - 1) >> 5; g >= 0; --g) {
+      const int gk = (beg >> 5) + g;
+      unsigned mask;
+      if (MASKS && gk < kMaskGroups) {
+        mask = __ldg(wmask + gk * 8);
+      } else {
+        const int jj = g * 32 + lane;
+        bool hit = false;
+        if (jj < cnt) {
+          const float4 a = s_a[jj];
+          const float2 ex = s_e[jj];
+          hit = fabsf(a.x - bcx) <= ex.x + 3.5f && fabsf(a.y - bcy) <= ex.y + 1.5f;
+        }
+        mask = __ballot_sync(FULLM, hit);
       }
-      unsigned mask = __ballot_sync(FULLM, hit);
+      const int lim = top - g * 32;
+      if (lim < 32) mask &= (1u << lim) - 1u;
       while (mask) {
         const int bit = 31 - __clz(mask);
         mask &= ~(1u << bit);
@@ -146,10 +162,10 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
           const float4 a = s_a[j], b = s_b[j];
           const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
           const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
-          ++n_eval;
+          if (COUNT) ++n_eval;
           if (p >= r.log2_alpha_min) {
             contrib = true;
-            ++n_contrib;
+            if (COUNT) ++n_contrib;
             const float ag = hw_exp2(p);
             const float alpha = fminf(r.alpha_max, ag);
             const float inv = hw_rcp(1.f - alpha);
@@ -195,7 +211,10 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
       }
     }
   }
-  add_eval_counts(ws, 1, n_eval, n_contrib);
+  if (COUNT) add_eval_counts(ws, 1, n_eval, n_contrib);
+  // the fixed-bucket layout's counts start at zero for the next preprocess
+  // (the adjoint is the last reader of the tile's range)
+  if (ws.bucket_cap && tid == 0) ws.tile_count[tile] = 0u;
 }
 
 // Chains the 2D gradients of Gaussian i in view v (pose Pm) to the pose
@@ -424,12 +443,14 @@ cudaError_t launch_render_bwd(const Workspace &ws, int views, int64_t n, const R
                               const float4 *targets, const float *image, const int32_t *last, bool full,
                               cudaStream_t s, const float *upstream) {
   (void)n;
-  const unsigned grid = (unsigned)(views * r.T);
-  if (full)
-    return launch_pdl(render_bwd_kernel<true>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last,
-                      upstream);
-  return launch_pdl(render_bwd_kernel<false>, dim3(grid), dim3(kTilePix), 0, s, ws, r, l, targets, image, last,
-                    upstream);
+  const dim3 grid((unsigned)(views * r.T));
+  const bool masks = ws.warp_masks != nullptr, count = ws.count_evals != 0;
+#define DAGS_BWD(F, M, C) \
+  launch_pdl(render_bwd_kernel<F, M, C>, grid, dim3(kTilePix), 0, s, ws, r, l, targets, image, last, upstream)
+  if (full) return count ? DAGS_BWD(true, false, true) : DAGS_BWD(true, false, false);
+  if (masks) return count ? DAGS_BWD(false, true, true) : DAGS_BWD(false, true, false);
+  return count ? DAGS_BWD(false, false, true) : DAGS_BWD(false, false, false);
+#undef DAGS_BWD
 }
 
 cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int64_t n, int views,

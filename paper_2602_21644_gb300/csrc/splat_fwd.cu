@@ -498,7 +498,10 @@ emit_kernel(Workspace ws, int64_t n, Raster r) {
   walk_tiles<kWalkEmit>(ws, r, v, id, rect, r0, r1, z);
 }
 
-__global__ void __launch_bounds__(kTilePix, 6)
+// MASKS: record per warp the list entries its pixels took (ws.warp_masks,
+// the tracking loop); COUNT: count evaluations and contributions (ws.evals).
+template <bool MASKS, bool COUNT>
+__global__ void __launch_bounds__(kTilePix, MASKS ? 5 : 6)
 render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
                   float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
   pdl_wait();
@@ -518,8 +521,9 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
-  const uint32_t s = ovf ? 0u : ws.tile_start[tile];
-  const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
+  uint32_t s = 0u, e = 0u;
+  if (!ovf) tile_range(ws, tile, s, e);
+  uint32_t *const wmask = MASKS ? ws.warp_masks + (size_t)tile * kMaskGroups * 8 + warp : nullptr;
   const size_t vbase = (size_t)v * ws.max_n;
   const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
 
@@ -559,32 +563,46 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
         hit = fabsf(a.x - bcx) <= ex.x + 3.5f && fabsf(a.y - bcy) <= ex.y + 1.5f;
       }
       unsigned mask = __ballot_sync(FULL, hit);
+      unsigned took = 0u;   // entries at least one pixel of the warp took
       while (mask) {
-        const int j = g * 32 + __ffs(mask) - 1;
+        const int bit = __ffs(mask) - 1;
+        const int j = g * 32 + bit;
         mask &= mask - 1;
-        if (done) continue;
-        const float4 a = s_a[j], b = s_b[j];
-        const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
-        const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
-        ++n_eval;
-        if (p < r.log2_alpha_min) continue;               // alpha < alpha_min
-        ++n_contrib;
-        const float alpha = fminf(r.alpha_max, hw_exp2(p));
-        const float tt = T * (1.f - alpha);
-        if (tt < r.t_min) { done = true; continue; }
-        const float w = alpha * T;
-        const float4 c = s_c[j];
-        const uint32_t rg = __float_as_uint(c.z), bl = __float_as_uint(c.w);
-        cr += bf16_lo(rg) * w; cg += bf16_hi(rg) * w; cb += bf16_lo(bl) * w;
-        dd += c.x * w; oo += w; rm += c.y * w;
-        T = tt;
-        lastk = (int)(base - s) + j + 1;
+        bool contrib = false;
+        if (!done) {
+          const float4 a = s_a[j], b = s_b[j];
+          const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
+          const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+          if (COUNT) ++n_eval;
+          if (p >= r.log2_alpha_min) {                    // else alpha < alpha_min
+            const float alpha = fminf(r.alpha_max, hw_exp2(p));
+            const float tt = T * (1.f - alpha);
+            if (tt < r.t_min) {
+              done = true;
+            } else {
+              contrib = true;
+              if (COUNT) ++n_contrib;
+              const float w = alpha * T;
+              const float4 c = s_c[j];
+              const uint32_t rg = __float_as_uint(c.z), bl = __float_as_uint(c.w);
+              cr += bf16_lo(rg) * w; cg += bf16_hi(rg) * w; cb += bf16_lo(bl) * w;
+              dd += c.x * w; oo += w; rm += c.y * w;
+              T = tt;
+              lastk = (int)(base - s) + j + 1;
+            }
+          }
+        }
+        if (MASKS && __any_sync(FULL, contrib)) took |= 1u << bit;
+      }
+      if (MASKS) {
+        const int gk = (int)((base - s) >> 5) + g;
+        if (lane == 0 && gk < kMaskGroups) wmask[gk * 8] = took;
       }
       if (__all_sync(FULL, done)) break;
     }
   }
 
-  add_eval_counts(ws, 0, n_eval, n_contrib);
+  if (COUNT) add_eval_counts(ws, 0, n_eval, n_contrib);
   float lpx = 0.f;
   if (inside) {
     const size_t P = (size_t)r.W * r.H;
@@ -670,8 +688,18 @@ cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const R
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s) {
   (void)n;
-  return launch_pdl(render_fwd_kernel, dim3((unsigned)(views * r.T)), dim3(kTilePix), 0, s, ws, views, r, l, targets,
-                    image, last, loss);
+  const dim3 grid((unsigned)(views * r.T));
+  const bool masks = ws.warp_masks != nullptr;
+  if (ws.count_evals) {
+    if (masks) return launch_pdl(render_fwd_kernel<true, true>, grid, dim3(kTilePix), 0, s, ws, views, r, l, targets,
+                                 image, last, loss);
+    return launch_pdl(render_fwd_kernel<false, true>, grid, dim3(kTilePix), 0, s, ws, views, r, l, targets, image,
+                      last, loss);
+  }
+  if (masks) return launch_pdl(render_fwd_kernel<true, false>, grid, dim3(kTilePix), 0, s, ws, views, r, l, targets,
+                               image, last, loss);
+  return launch_pdl(render_fwd_kernel<false, false>, grid, dim3(kTilePix), 0, s, ws, views, r, l, targets, image,
+                    last, loss);
 }
 
 }  // namespace dags

@@ -99,7 +99,7 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
            "mp_pixel", "mp_gauss", "mpnet", "mpnet_train", "pose_tangent", "render_jac", "lm_step",
-           "regulariser", "epipolar", "render_track", "gauss_adam"]
+           "regulariser", "epipolar", "gauss_adam"]
 
 _lib = None
 

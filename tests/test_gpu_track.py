@@ -98,12 +98,14 @@ def test_tracking_converges_to_the_pose_that_rendered_the_target(dags):
 
 
 @pytest.mark.parametrize("size", ["tiny", "full"])
-def test_fused_iteration_equals_separate_forward_and_backward(dags, size):
+def test_tracking_iteration_equals_forward_and_backward(dags, size):
     # One tracking iteration with a zero learning rate (the pose stays put)
-    # runs the fused forward + pose adjoint; splat_forward + splat_backward run
-    # the same arithmetic in two kernels. Image and last are bit-identical,
-    # the loss too (the same FP64 tile sums in the same order); the pose
-    # gradient differs by the order of the FP32 atomics only.
+    # bins into the fixed-capacity buckets and runs the adjoint over the
+    # entries the forward recorded per warp; splat_forward + splat_backward
+    # bin into packed buckets and run the adjoint over the box-tested entries.
+    # Image and last are bit-identical, the loss too (the same FP64 tile sums
+    # in the same order); the pose gradient differs by the order of the FP32
+    # atomics only.
     if size == "tiny":
         sc = synth.tiny_scene(2)
     else:
