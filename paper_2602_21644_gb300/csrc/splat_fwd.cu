@@ -508,7 +508,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   __shared__ uint64_t s_key[kSortSmallCap];
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
   __shared__ float2 s_e[kTilePix];                                  // box half extents
-  __shared__ double s_red[kTilePix / 32];
+  __shared__ float2 s_red[kTilePix / 32];
   __shared__ int s_last;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -622,15 +622,30 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
     last[(size_t)v * P + pix] = lastk;
   }
   if (!loss) return;
-  // the tile's 256 pixel losses are summed in FP64 (fixed shuffle tree, then
-  // the 8 warps in order)
-  const double lsum = warp_sum_d((double)lpx);
-  if ((tid & 31) == 0) s_red[tid >> 5] = lsum;
+  // the tile's 256 pixel losses are summed exactly enough for FP64 without
+  // the FP64 pipe: compensated FP32 (two-sum, a high and a low word) over a
+  // fixed shuffle tree, then over the 8 warps in order; the tile's partial is
+  // the FP64 sum of the two words
+  float lh = lpx, ll = 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, lh, o), ol = __shfl_xor_sync(0xffffffffu, ll, o);
+    float sh, se;
+    two_sum(lh, oh, sh, se);
+    lh = sh;
+    ll = __fadd_rn(__fadd_rn(ll, ol), se);
+  }
+  if ((tid & 31) == 0) s_red[tid >> 5] = make_float2(lh, ll);
   __syncthreads();
   if (tid == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kTilePix / 32; ++w) t += s_red[w];
-    ws.loss_partial[tile] = t;
+    float th = 0.f, tl = 0.f;
+    for (int w = 0; w < kTilePix / 32; ++w) {
+      float sh, se;
+      two_sum(th, s_red[w].x, sh, se);
+      th = sh;
+      tl = __fadd_rn(__fadd_rn(tl, s_red[w].y), se);
+    }
+    ws.loss_partial[tile] = (double)th + (double)tl;
     __threadfence();
     unsigned int done_ctas = atomicAdd(ws.counters + CNT_DONE_RENDER, 1u);
     s_last = (done_ctas == gridDim.x - 1);
