@@ -933,9 +933,9 @@ def run_ours(args):
     iter_us = 1e3 * t_ms / (args.iters * args.steps)
     # kernels per step: per iteration the preprocess (with direct binning),
     # the forward, the adjoint and the pose chain (pose step fused); per frame
-    # the MP update's 9 kernels (pixel sum, pixel var, pixel map, gauss,
+    # the culling and the MP update's 9 kernels (pixel sum, pixel var, pixel map, gauss,
     # apply, 2 select levels, labels, region stats)
-    gpu_launches = args.steps * (args.iters * 4 + 9)
+    gpu_launches = args.steps * (args.iters * 4 + 9 + 1)   # + the frame's culling
     line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -89,6 +89,9 @@ struct dags_ctx {
   TrackGraph graph_lm;            // captured LM iteration
   LmBuffers lm;                   // allocated by the first LM call
   uint32_t *warp_masks = nullptr; // [max_tiles][kMaskGroups][8] forward masks of the tracking loop
+  uint32_t *cand_ids = nullptr;   // [max_n] the tracking frame's culled candidates
+  uint32_t *cand_n = nullptr;     // [1]
+  float *cull_pose = nullptr;     // [12]
   double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
   double *edge_partial = nullptr; // per-CTA sums of the edge-warp term (first call)
   float *rel32 = nullptr;         // [12] FP32 relative pose of the regularisers (first call)
@@ -317,6 +320,9 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&w.counters, (size_t)CNT_N));
   A(alloc(&w.evals, (size_t)4));
   A(alloc(&c->warp_masks, (size_t)w.max_tiles * kMaskGroups * 8));
+  A(alloc(&c->cand_ids, (size_t)w.max_n));
+  A(alloc(&c->cand_n, (size_t)1));
+  A(alloc(&c->cull_pose, (size_t)12));
   if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
   MpBuffers &mb = c->mp;
@@ -341,7 +347,8 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
     cudaGetLastError();
     free_mp(c->mp);
     free_ws(w);
-    if (c->warp_masks) cudaFree(c->warp_masks);
+    for (void *p : {(void *)c->warp_masks, (void *)c->cand_ids, (void *)c->cand_n, (void *)c->cull_pose})
+      if (p) cudaFree(p);
     delete c;
     return code;
   }
@@ -364,7 +371,8 @@ void dags_destroy(dags_ctx *ctx) {
   if (ctx->graph_lm.exec_chunk) cudaGraphExecDestroy(ctx->graph_lm.exec_chunk);
   if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
   free_lm(ctx->lm);
-  if (ctx->warp_masks) cudaFree(ctx->warp_masks);
+  for (void *p : {(void *)ctx->warp_masks, (void *)ctx->cand_ids, (void *)ctx->cand_n, (void *)ctx->cull_pose})
+    if (p) cudaFree(p);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
   if (ctx->edge_partial) cudaFree(ctx->edge_partial);
   if (ctx->rel32) cudaFree(ctx->rel32);
@@ -613,6 +621,19 @@ int pose_step(dags_ctx *ctx, double *poses, const double *grad, double *adam_sta
 
 namespace {
 
+// The tracking loop's view of the workspace: the fixed-capacity bucket
+// layout (max_pairs / tiles slots per tile) and the frame's culled
+// candidates.
+Workspace track_workspace(const dags_ctx *ctx, const Raster &r) {
+  Workspace w = ctx->ws;
+  const int64_t cap = w.max_pairs / r.T;
+  w.bucket_cap = (uint32_t)(cap < 0xFFFFFFFFll ? cap : 0xFFFFFFFFll);
+  w.cand_ids = ctx->cand_ids;
+  w.cand_n = ctx->cand_n;
+  w.cull_pose = ctx->cull_pose;
+  return w;
+}
+
 // Enqueues one tracking iteration: projection and binning into the
 // fixed-capacity buckets, the forward with loss, the pose-only adjoint, and
 // the chain to the pose twist with the pose step in its last CTA (arguments
@@ -628,9 +649,7 @@ int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_cam
   ctx->last_stream = s;
   // the tile buckets take the fixed-capacity layout: max_pairs / tiles slots
   // per tile, filled by the preprocess directly (no scan or emit launch)
-  Workspace w = ctx->ws;
-  const int64_t cap = w.max_pairs / r.T;
-  w.bucket_cap = (uint32_t)(cap < 0xFFFFFFFFll ? cap : 0xFFFFFFFFll);
+  Workspace w = track_workspace(ctx, r);
   if (w.bucket_cap == 0) return DAGS_E_INVAL;
   const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
   KernelTimer &tm = ctx->timer;
@@ -698,6 +717,16 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   if (!(pc_v.beta1 >= 0 && pc_v.beta1 < 1) || !(pc_v.beta2 >= 0 && pc_v.beta2 < 1) || !(pc_v.eps > 0))
     return DAGS_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  // the frame's culling at its starting pose (the iterations fall back to
+  // every Gaussian if their pose leaves the culling bounds)
+  {
+    Raster r;
+    if ((rc = make_raster(cam, &rc_v, &r))) return rc;
+    const int ev = ctx->timer.begin(DAGS_K_PREPROCESS, s);
+    const cudaError_t e = launch_cull(track_workspace(ctx, r), reinterpret_cast<const float4 *>(gauss), n, pose, r, s);
+    ctx->timer.end(ev, s);
+    if (e != cudaSuccess) return DAGS_E_CUDA;
+  }
   if (!use_graph || ctx->timer.on) {
     for (int k = 0; k < iters; ++k) {
       rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,

@@ -107,6 +107,11 @@ struct Workspace {
   // entries at least one pixel of the warp took in the forward (one bit
   // each), for the adjoint of the same iteration; null: not recorded.
   uint32_t *warp_masks = nullptr;   // [max_tiles][kMaskGroups][8]
+  // Per-frame culling of the tracking loop: the candidates of the frame's
+  // starting pose (cull_pose, FP32 3x4) and their count; null: no culling.
+  uint32_t *cand_ids = nullptr;     // [max_n]
+  uint32_t *cand_n = nullptr;       // [1]
+  float *cull_pose = nullptr;       // [12]
 };
 
 // The list range [s, e) of tile t in the workspace's bucket layout.
@@ -164,6 +169,11 @@ cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster 
 // requirement by the last CTA (no scan or emit launch).
 cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
                                      const Raster &r, int zero_grad_words, cudaStream_t s);
+// The frame's culling: candidates of `pose` into ws.cand_ids / cand_n and
+// the pose into ws.cull_pose (the tracking loop's preprocess uses them while
+// its pose stays within the culling bounds).
+cudaError_t launch_cull(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose, const Raster &r,
+                        cudaStream_t s);
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s);

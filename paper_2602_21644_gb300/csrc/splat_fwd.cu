@@ -329,38 +329,26 @@ __device__ void order_direct_buckets(const Workspace &ws, int total) {
   }
 }
 
+// Projection of Gaussian i (valid: i < n, else an empty lane) into view v:
+// the projected record, its FP32 remainders, the candidate tiles and the
+// zeroed 2D gradient of a visible Gaussian, its visible-list entry and the
+// warp-cooperative walk over its tiles (counting, or emitting into the
+// fixed-capacity buckets). Called by whole warps (ballot, walk).
 template <bool DIRECT>
-__global__ void __launch_bounds__(kPrepBlock)
-preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
-                  const double *__restrict__ poses, int views, Raster r, int zero_words) {
-  pdl_wait();
-  __shared__ float sp[kMaxViewsSmem * 12];
-  __shared__ float spl[kMaxViewsSmem * 12];   // FP32 remainders of the FP64 poses
-  const int v = blockIdx.y;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // the record loads are issued before the pose barrier, so that the two
-  // memory round trips overlap
+__device__ __forceinline__ void preprocess_one(const Workspace &ws, const float4 *__restrict__ gauss, int64_t i,
+                                               bool valid, int v, const float *sp, const float *spl, const Raster &r,
+                                               int zero_words) {
   float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
-  if (i < n) {
+  if (valid) {
     g0 = __ldg(gauss + 4 * i + 0);
     g1 = __ldg(gauss + 4 * i + 1);
     g2 = __ldg(gauss + 4 * i + 2);
     g3 = __ldg(gauss + 4 * i + 3);
   }
-  for (int k = threadIdx.x; k < views * 12; k += blockDim.x) {
-    const double pk = poses[k];
-    const float hi = __double2float_rn(pk);
-    sp[k] = hi;
-    spl[k] = __double2float_rn(pk - (double)hi);
-  }
-  __syncthreads();
-  if (blockIdx.x == 0 && blockIdx.y == 0)
-    for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
-
   uint2 my_rect = make_uint2(0u, 0u);
   float4 my_r0 = make_float4(0.f, 0.f, 0.f, 0.f), my_r1 = my_r0;
   float my_z = 0.f;
-  if (i < n) {
+  if (valid) {
     const float *P = sp + v * 12;
     const size_t slot = (size_t)v * ws.max_n + i;
 
@@ -425,11 +413,36 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       ws.vis_ids[(size_t)v * ws.max_n + basev + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
   }
   // Warp-cooperative walk over the candidate tiles of the warp's Gaussians.
-  if (!DIRECT) {
-    walk_tiles<kWalkCount>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, 0.f);
-    return;
+  const uint32_t id = (uint32_t)(valid ? i : 0);
+  if (DIRECT) walk_tiles<kWalkDirect>(ws, r, v, id, my_rect, my_r0, my_r1, my_z);
+  else walk_tiles<kWalkCount>(ws, r, v, id, my_rect, my_r0, my_r1, 0.f);
+}
+
+// FP32 copies (high words and remainders) of the FP64 poses in shared memory.
+__device__ __forceinline__ void stage_poses(const double *__restrict__ poses, int views, float *sp, float *spl) {
+  for (int k = threadIdx.x; k < views * 12; k += blockDim.x) {
+    const double pk = poses[k];
+    const float hi = __double2float_rn(pk);
+    sp[k] = hi;
+    spl[k] = __double2float_rn(pk - (double)hi);
   }
-  walk_tiles<kWalkDirect>(ws, r, v, (uint32_t)(i < n ? i : 0), my_rect, my_r0, my_r1, my_z);
+}
+
+template <bool DIRECT>
+__global__ void __launch_bounds__(kPrepBlock)
+preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
+                  const double *__restrict__ poses, int views, Raster r, int zero_words) {
+  pdl_wait();
+  __shared__ float sp[kMaxViewsSmem * 12];
+  __shared__ float spl[kMaxViewsSmem * 12];   // FP32 remainders of the FP64 poses
+  const int v = blockIdx.y;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  stage_poses(poses, views, sp, spl);
+  __syncthreads();
+  if (blockIdx.x == 0 && blockIdx.y == 0)
+    for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
+  preprocess_one<DIRECT>(ws, gauss, i, i < n, v, sp, spl, r, zero_words);
+  if (!DIRECT) return;
   // the last CTA orders the renders
   __shared__ int s_last;
   __syncthreads();
@@ -437,6 +450,115 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     __threadfence();
     const unsigned t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
     s_last = (t == gridDim.x * gridDim.y - 1);
+    if (s_last) __threadfence();
+  }
+  __syncthreads();
+  if (s_last) order_direct_buckets(ws, r.T);
+}
+
+// Per-frame culling of the tracking loop: the Gaussians that can be visible
+// under any pose whose rotation differs from the frame's starting pose by at
+// most kCullRot rad and whose camera-space translation differs by at most
+// kCullTrans m. Every camera-space point then moves by at most kCullRot |p|
+// + kCullTrans; a Gaussian at least kCullNear in front of the camera moves on
+// the image by less than `margin` px (set by the host from the focal length
+// and the guard-clamped field of view, with a factor 2 to spare) and its
+// alpha-ellipse box grows by less than 4%, so a candidate is one whose box,
+// widened by 25% plus the margin, reaches the tile grid. Every Gaussian
+// nearer than kCullNear that can come in front of the near plane is a
+// candidate. A Gaussian below alpha_min opacity is never visible.
+constexpr float kCullRot = 0.01f, kCullTrans = 0.01f, kCullNear = 0.5f, kCullGrow = 1.25f;
+
+__global__ void __launch_bounds__(kPrepBlock)
+cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose, Raster r,
+            float margin) {
+  pdl_wait();
+  __shared__ float sp[12];
+  if (threadIdx.x < 12) sp[threadIdx.x] = (float)pose[threadIdx.x];
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < 12) ws.cull_pose[threadIdx.x] = sp[threadIdx.x];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool cand = false;
+  if (i < n) {
+    const float4 g0 = __ldg(gauss + 4 * i), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
+    const float x = sp[0] * g0.x + sp[1] * g0.y + sp[2] * g0.z + sp[3];
+    const float y = sp[4] * g0.x + sp[5] * g0.y + sp[6] * g0.z + sp[7];
+    const float z = sp[8] * g0.x + sp[9] * g0.y + sp[10] * g0.z + sp[11];
+    const float m = kCullRot * sqrtf(x * x + y * y + z * z) + kCullTrans;
+    const float o = 1.f / (1.f + expf(-g0.w));
+    if (o > r.alpha_min) {
+      Proj q;
+      if (z < kCullNear) {
+        cand = z > r.z_near - m;
+      } else if (project_gaussian(g0, g1, g2, sp, r, q)) {
+        const float cnat = 2.f * (logf(q.o) - logf(r.alpha_min));
+        const float ex = kCullGrow * sqrtf(fmaxf(cnat, 0.f) * q.A) + margin;
+        const float ey = kCullGrow * sqrtf(fmaxf(cnat, 0.f) * q.C) + margin;
+        const float X1 = (float)(r.tiles_x * kTile), Y1 = (float)(r.tiles_y * kTile);
+        cand = q.u + ex >= 0.f && q.u - ex <= X1 && q.v + ey >= 0.f && q.v - ey <= Y1;
+      }
+    }
+  }
+  const unsigned ball = __ballot_sync(0xffffffffu, cand);
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (ball && lane == __ffs(ball) - 1) base = atomicAdd(ws.cand_n, (uint32_t)__popc(ball));
+  base = __shfl_sync(0xffffffffu, base, ball ? __ffs(ball) - 1 : 0);
+  if (cand) ws.cand_ids[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+// Whether pose P (FP32, 3x4) lies within the culling bounds of pose C:
+// the relative motion p -> R_d p + t_d, R_d = R_P R_C^T, t_d = t_P - R_d t_C,
+// with ||R_d - I||_F / (2 sqrt 2) = sin(theta / 2) <= sin(kCullRot / 2) and
+// |t_d| <= kCullTrans (both with a rounding allowance).
+__device__ __forceinline__ bool within_cull_bounds(const float *P, const float *C) {
+  float Rd[9], fro = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Rd[3 * a + b] = P[4 * a] * C[4 * b] + P[4 * a + 1] * C[4 * b + 1] + P[4 * a + 2] * C[4 * b + 2];
+      const float d = Rd[3 * a + b] - (a == b ? 1.f : 0.f);
+      fro += d * d;
+    }
+  float t2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float td = P[4 * a + 3] - (Rd[3 * a] * C[3] + Rd[3 * a + 1] * C[7] + Rd[3 * a + 2] * C[11]);
+    t2 += td * td;
+  }
+  const float s_max = 0.999f * sinf(0.5f * kCullRot);
+  return sqrtf(fro) <= 2.f * 1.41421356f * s_max && sqrtf(t2) <= 0.999f * kCullTrans;
+}
+
+// The tracking loop's preprocess (one view, fixed-capacity buckets) over
+// the frame's candidates, or over all Gaussians when the pose has left the
+// culling bounds; a fixed grid strides over the list.
+__global__ void __launch_bounds__(kPrepBlock)
+preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
+                       Raster r, int zero_words) {
+  pdl_wait();
+  __shared__ float sp[12], spl[12];
+  __shared__ int s_valid, s_last;
+  stage_poses(pose, 1, sp, spl);
+  __syncthreads();
+  if (threadIdx.x == 0) s_valid = within_cull_bounds(sp, ws.cull_pose) ? 1 : 0;
+  if (blockIdx.x == 0 && threadIdx.x < 12) ws.pose32[threadIdx.x] = sp[threadIdx.x];
+  __syncthreads();
+  const bool use_cand = s_valid != 0;
+  const int64_t count = use_cand ? (int64_t)*ws.cand_n : n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
+    const int64_t k = base + threadIdx.x;
+    const bool valid = k < count;
+    const int64_t i = !valid ? 0 : (use_cand ? (int64_t)ws.cand_ids[k] : k);
+    preprocess_one<true>(ws, gauss, i, valid && i < n, 0, sp, spl, r, zero_words);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
+    s_last = (t == gridDim.x - 1);
     if (s_last) __threadfence();
   }
   __syncthreads();
@@ -688,9 +810,27 @@ cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, i
                                      const Raster &r, int zero_grad_words, cudaStream_t s) {
   if (ws.bucket_cap == 0) return cudaErrorInvalidValue;
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
+  if (ws.cand_ids) {
+    // the culled list of the frame: a fixed grid strides over it
+    const unsigned g = gx < (unsigned)(8 * ws.band) ? (gx > 0 ? gx : 1u) : (unsigned)(8 * ws.band);
+    return launch_pdl(preprocess_cull_kernel, dim3(g), dim3(kPrepBlock), 0, s, ws, gauss, n, pose, r,
+                      zero_grad_words);
+  }
   dim3 grid(gx > 0 ? gx : 1u, 1u);
   return launch_pdl(preprocess_kernel<true>, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, pose, 1, r,
                     zero_grad_words);
+}
+
+cudaError_t launch_cull(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose, const Raster &r,
+                        cudaStream_t s) {
+  // the candidates' image motion bound: (rot (1 + L)^2 + trans / near) f, L
+  // the guard-clamped half field of view, times 2
+  const float L = fmaxf(r.limx, r.limy), f = fmaxf(r.fx, r.fy);
+  const float margin = 2.f * f * (kCullRot * (1.f + L) * (1.f + L) + kCullTrans / kCullNear);
+  cudaError_t e = cudaMemsetAsync(ws.cand_n, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess || n == 0) return e;
+  return launch_pdl(cull_kernel, dim3((unsigned)((n + kPrepBlock - 1) / kPrepBlock)), dim3(kPrepBlock), 0, s, ws,
+                    gauss, n, pose, r, margin);
 }
 
 cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s) {

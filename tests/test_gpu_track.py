@@ -128,3 +128,41 @@ def test_tracking_iteration_equals_forward_and_backward(dags, size):
     a, b = t["gp"].cpu().numpy(), gp.cpu().numpy()
     assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b), (a, b)
     ctx.close()
+
+
+@pytest.mark.parametrize("lr", [4e-3, 5e-2])
+def test_culled_iterations_render_what_an_unculled_forward_renders(dags, lr):
+    # splat_track culls the map once at the frame's starting pose for every
+    # pose within 0.01 rad and 0.01 m of it, and falls back to every Gaussian
+    # beyond. Adam's first step moves each twist component by lr: 4e-3 keeps
+    # the second iteration's pose inside the bounds (|rho|, |phi| ~ 7e-3),
+    # 5e-2 takes it outside. Either way the second iteration's forward must
+    # render what splat_forward (no culling) renders at that pose; a
+    # Gaussian the culling missed would change whole pixels.
+    sc = synth.tracking_scene(60_000, frame=12, width=320, height=240)
+    cam, t = setup(dags, sc)
+    ctx = dags.Context(sc.records.shape[0], cam.width, cam.height, 1)
+    pcfg = dags.default_pose_cfg(lr=[lr] * 6)
+    start = t["pose"].clone()
+    ctx.track(t["gauss"], cam, t["pose"], t["targets"], 1, t["state"], t["image"], t["last"], t["loss"], t["gp"],
+              pcfg=pcfg, use_graph=False)
+    torch.cuda.synchronize()
+    ctx.check()
+    pose1 = t["pose"].clone()
+    rel = pose1.cpu().numpy()[0][:, :3] @ start.cpu().numpy()[0][:, :3].T
+    angle = np.arccos(np.clip((np.trace(rel) - 1) / 2, -1, 1))
+    assert (angle < 0.01) == (lr < 0.01), angle
+    image_ref, last_ref, loss_ref = ctx.forward(t["gauss"], cam, pose1, t["targets"])
+    torch.cuda.synchronize()
+    t["pose"].copy_(start)
+    t["state"].zero_()
+    ctx.track(t["gauss"], cam, t["pose"], t["targets"], 2, t["state"], t["image"], t["last"], t["loss"], t["gp"],
+              pcfg=pcfg, use_graph=False)
+    torch.cuda.synchronize()
+    ctx.check()
+    # the two runs' first steps agree to the rounding of the FP32 atomics in
+    # the pose gradient (Adam's first step is lr g / (|g| + eps)), far below
+    # a pixel's worth of motion
+    np.testing.assert_allclose(t["image"].cpu().numpy(), image_ref.cpu().numpy(), rtol=1e-5, atol=1e-6)
+    assert (t["last"] != last_ref).float().mean().item() < 1e-4
+    ctx.close()
