@@ -114,8 +114,11 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   float Sg = 0.f;
   unsigned n_eval = 0, n_contrib = 0;
   const float fpx = (float)px, fpy = (float)py;
-  for (int end = kmax; end > 0; end -= kTilePix) {
-    const int beg = max(0, end - kTilePix);
+  // batches of kTilePix entries aligned as the forward's (the recorded
+  // masks address entries by their 32-entry group in the tile's list); the
+  // first batch walked is the one holding the last contributor
+  for (int end = kmax, beg; end > 0; end = beg) {
+    beg = ((end - 1) / kTilePix) * kTilePix;
     __syncthreads();
     if (beg + tid < end && DAGS_IN_BOUNDS((uint64_t)s + beg + tid < (uint64_t)ws.max_pairs, ws.counters + CNT_STATUS)) {
       uint32_t id = ws.sorted_ids[s + beg + tid];

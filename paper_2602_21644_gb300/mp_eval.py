@@ -75,8 +75,9 @@ class Runner:
     """One sequence through the library: render, MP update (fresh, stale or
     learned), network features and inference."""
 
-    def __init__(self, dags, seq):
+    def __init__(self, dags, seq, mp_cfg=None):
         self.d, self.seq = dags, seq
+        self.mp_cfg = mp_cfg
         self.cam = dags.Camera(*seq.cam.as_tuple())
         self.ctx = dags.Context(seq.n, seq.width, seq.height, 1)
         self.table = torch.from_numpy(TABLE).cuda()
@@ -97,7 +98,7 @@ class Runner:
         lab = torch.zeros(self.seq.n, dtype=torch.uint8, device="cuda")
         out = torch.empty(self.P, dtype=torch.float32, device="cuda")
         inst = torch.from_numpy(self.seq.inst[f]).cuda()
-        self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out)
+        self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out, cfg=self.mp_cfg)
         return out
 
     def run(self, mode, net=None, collect=False, schedule=None, follow=False):
@@ -142,7 +143,7 @@ class Runner:
                 rec["net"] = mp_map
             stale_px = torch.empty(self.P, dtype=torch.float32, device="cuda")
             stats = self.ctx.mp_update(gauss, self.cam, pose, tg, image, inst, self.table, labels,
-                                       seg_refreshed=refreshed, mp_map=mp_map, mp_pixel=stale_px)
+                                       seg_refreshed=refreshed, mp_map=mp_map, mp_pixel=stale_px, cfg=self.mp_cfg)
             if schedule is not None:
                 self.ctx.semantic_trigger(stats, state, refreshed, cfg=schedule, score=score)
                 nxt = bool(state[1].item())
@@ -190,16 +191,17 @@ def iou(a, b):
     return np.logical_and(a, b).sum() / u if u else 1.0
 
 
-def experiment(dags, steps=1000, follow=False):
+def experiment(dags, steps=1000, follow=False, mp_cfg=None):
     """Train on one sequence, run fresh / stale / learned on the held-out one.
     follow: the map keeps its moving objects at their current positions (see
-    Runner.run), in training and evaluation."""
+    Runner.run), in training and evaluation; mp_cfg: the MP update's
+    constants (default dags_default_mp_cfg)."""
     train_seq = Sequence(seed=11, velocities=[(0.0, 0.0, 0.3), (-0.3, 0.0, 0.0)], n_frames=60)
-    tr = Runner(dags, train_seq)
+    tr = Runner(dags, train_seq, mp_cfg)
     net, losses = train_net(dags, tr, steps=steps, follow=follow)
     tr.ctx.close()
     eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=40)
-    ev = Runner(dags, eval_seq)
+    ev = Runner(dags, eval_seq, mp_cfg)
     sc = dags.default_sched_cfg()
     out = dict(losses=losses, fresh=ev.run("fresh", follow=follow), stale=ev.run("stale", follow=follow),
                learned=ev.run("learned", net=net, follow=follow),

@@ -106,7 +106,18 @@ def test_render_autograd_with_a_user_loss_matches_the_oracle(dags):
         assert v <= 1e-4, k
     pg = np.linalg.norm(xi.grad[0].cpu().numpy() - ref["pose_grad"]) / np.linalg.norm(ref["pose_grad"])
     assert pg <= 1e-4, pg
-    # the rendered channels are the forward's
-    np.testing.assert_allclose(C[0].permute(1, 2, 0).reshape(P, 3).detach().cpu().numpy(), ref0["pix"][:, 0:3],
-                               rtol=1e-5, atol=1e-7)
+    # the rendered channels are the forward's (pixels whose decisions FP32
+    # may take otherwise are compared within their validity envelope)
+    from gpu_common import compare_image
+    img = np.zeros((P, 8))
+    img[:, 0:3] = C[0].permute(1, 2, 0).reshape(P, 3).detach().cpu().numpy()
+    img[:, 3] = D[0].reshape(P).detach().cpu().numpy()
+    img[:, 4] = O[0].reshape(P).detach().cpu().numpy()
+    img[:, 5] = R[0].reshape(P).detach().cpu().numpy()
+    ref_pix = ref0["pix"].copy()
+    img[:, 6] = ref_pix[:, 6]           # transmittance and weight: not outputs of SplatRender
+    img[:, 7] = ref_pix[:, 9]
+    worst, _ = compare_image(img, ref_pix, ref0["flags"])
+    for c in range(6):
+        assert worst[c][2] == 0, (c, worst[c])
     ctx.close()
