@@ -15,7 +15,6 @@ constexpr int kGradWords = 12;          // per (view, Gaussian) 2D gradient slot
 constexpr int kSortSmallCap = 1024;     // tile lists up to this length are sorted by the render CTA
 constexpr int kPrepBlock = 128;         // threads per preprocess / emit CTA
 constexpr int kBwdPrepBlock = 128;      // threads per preprocess-backward CTA
-constexpr int kBwdPoseBlocks = 304;     // CTAs of the pose-only preprocess backward (2 per SM)
 constexpr int kMaskGroups = 32;         // list groups of 32 entries with a recorded forward mask (1024 entries)
 
 // Status word bits (device).
@@ -87,7 +86,7 @@ struct Workspace {
   uint32_t *sorted_ids = nullptr; // [max_pairs]
   uint32_t *tile_order = nullptr; // [V * T] launch order of the renders (length-ranked, band-reversed)
   double *loss_partial = nullptr; // [V * T] per-tile loss sums (FP64)
-  double *pose_partial = nullptr; // [bwd_prep_blocks][V][6]
+  float2 *pose_partial = nullptr; // [bwd_prep_blocks][V][6] compensated (high, low) CTA sums
   float *pose32 = nullptr;        // [V][12] FP32 copy of the poses of the last forward
   uint32_t *vis_ids = nullptr;    // [V][N] ids of the Gaussians with a non-empty candidate range
   uint32_t *vis_append = nullptr; // [V] append cursors (zero between calls)
@@ -644,15 +643,23 @@ __device__ inline void pose_adam_exp_cta(double *T, const double *grad, double *
                                          double *xi_s, double *sc_s) {
   const int t = threadIdx.x;
   const double k = st[12] + 1.0;
+  // threads 6 and 7 form 1 / (1 - beta1^k) and 1 / sqrt(1 - beta2^k) while
+  // threads 0-5 update the moments: the step is then
+  // -lr (m / bc1) / (sqrt(s2) / sqrt(bc2) + eps), one division deep
+  double m = 0.0, s2 = 0.0;
   if (t < 6) {
-    const double bc1 = 1.0 - pow_int(cfg.beta1, k), bc2 = 1.0 - pow_int(cfg.beta2, k);
     const double g = grad[t];
-    const double m = cfg.beta1 * st[t] + (1.0 - cfg.beta1) * g;
-    const double s2 = cfg.beta2 * st[6 + t] + (1.0 - cfg.beta2) * g * g;
+    m = cfg.beta1 * st[t] + (1.0 - cfg.beta1) * g;
+    s2 = cfg.beta2 * st[6 + t] + (1.0 - cfg.beta2) * g * g;
     st[t] = m;
     st[6 + t] = s2;
-    xi_s[t] = -cfg.lr[t] * (m / bc1) / (sqrt(s2 / bc2) + cfg.eps);
+  } else if (t == 6) {
+    sc_s[0] = 1.0 / (1.0 - pow_int(cfg.beta1, k));
+  } else if (t == 7) {
+    sc_s[1] = 1.0 / sqrt(1.0 - pow_int(cfg.beta2, k));
   }
+  __syncthreads();
+  if (t < 6) xi_s[t] = -cfg.lr[t] * (m * sc_s[0]) / (sqrt(s2) * sc_s[1] + cfg.eps);
   __syncthreads();
   if (t == 0) {
     st[12] = k;

@@ -327,20 +327,33 @@ __device__ __forceinline__ void chain_one(const Workspace &ws, const Raster &r, 
   }
 }
 
-// Sums pg[6] over the CTA and stores the FP64 partial of (view v, CTA b).
+// Compensated (double-FP32) addition: (h, l) += (bh, bl) through two-sum,
+// the high words' rounding error carried into the low word.
+__device__ __forceinline__ void cadd(float &h, float &l, float bh, float bl) {
+  float sh, se;
+  two_sum(h, bh, sh, se);
+  h = sh;
+  l = __fadd_rn(__fadd_rn(l, bl), se);
+}
+
+// Sums pg[6] over the CTA in compensated FP32 (a fixed shuffle tree, then
+// the warps in order) and stores the (high, low) partial of (view v, CTA b).
 __device__ __forceinline__ void store_pose_partial(const Workspace &ws, float *pg, int v, int b, int nb,
-                                                   float (*s_red)[6]) {
+                                                   float2 (*s_red)[6]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < 6; ++c) {
-    const float t = warp_sum(pg[c]);
-    if (lane == 0) s_red[wid][c] = t;
+    float h = pg[c], l = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      cadd(h, l, __shfl_xor_sync(0xffffffffu, h, o), __shfl_xor_sync(0xffffffffu, l, o));
+    if (lane == 0) s_red[wid][c] = make_float2(h, l);
   }
   __syncthreads();
   if (threadIdx.x < 6) {
-    float t = 0.f;
-    for (int w = 0; w < kBwdPrepBlock / 32; ++w) t += s_red[w][threadIdx.x];
-    ws.pose_partial[((size_t)v * nb + b) * 6 + threadIdx.x] = (double)t;
+    float h = 0.f, l = 0.f;
+    for (int w = 0; w < kBwdPrepBlock / 32; ++w) cadd(h, l, s_red[w][threadIdx.x].x, s_red[w][threadIdx.x].y);
+    ws.pose_partial[((size_t)v * nb + b) * 6 + threadIdx.x] = make_float2(h, l);
   }
   __syncthreads();
 }
@@ -355,7 +368,7 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                       float *__restrict__ grad_gauss, double *__restrict__ grad_pose, PoseStep ps) {
   pdl_wait();
   __shared__ float sp[kMaxViewsSmem * 12];
-  __shared__ float s_red[kBwdPrepBlock / 32][6];
+  __shared__ float2 s_red[kBwdPrepBlock / 32][6];
   __shared__ int s_last;
   for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = ws.pose32[k];
   __syncthreads();
@@ -411,25 +424,31 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   }
   __syncthreads();
   if (!s_last) return;
-  // one warp per (view, component): lane-strided partial sums in a fixed
-  // order, then a fixed shuffle tree
+  // one warp per (view, component): lane-strided compensated sums of the
+  // CTA partials (four independent accumulators, in a fixed order), then a
+  // fixed shuffle tree; the result is the FP64 sum of the high and low words
   for (int vc = wid; vc < views * 6; vc += kBwdPrepBlock / 32) {
     const int v = vc / 6, c = vc % 6;
-    const double *src = ws.pose_partial + (size_t)v * nb * 6 + c;
-    double a = 0.0;
-    // loads issued in groups of 8 before they are summed (fixed order)
+    const float2 *src = ws.pose_partial + (size_t)v * nb * 6 + c;
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
     for (int b0 = lane; b0 < nb; b0 += 32 * 8) {
-      double t[8];
+      float2 t[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int b = b0 + 32 * u;
-        t[u] = b < nb ? __ldcg(src + (size_t)b * 6) : 0.0;
+        t[u] = b < nb ? __ldcg(src + (size_t)b * 6) : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a += t[u];
+      for (int u = 0; u < 8; ++u) cadd(h[u & 3], l[u & 3], t[u].x, t[u].y);
     }
-    a = warp_sum_d(a);
-    if (lane == 0) grad_pose[v * 6 + c] = a;
+    cadd(h[0], l[0], h[1], l[1]);
+    cadd(h[2], l[2], h[3], l[3]);
+    cadd(h[0], l[0], h[2], l[2]);
+    float hh = h[0], ll = l[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      cadd(hh, ll, __shfl_xor_sync(0xffffffffu, hh, o), __shfl_xor_sync(0xffffffffu, ll, o));
+    if (lane == 0) grad_pose[v * 6 + c] = (double)hh + (double)ll;
   }
   __syncthreads();
   if (tid == 0) ws.counters[CNT_DONE_BWDPREP] = 0u;
@@ -466,8 +485,10 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
     return launch_pdl(preprocess_bwd_kernel<true>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,
                       grad_gauss, grad_pose, ps);
   } else {
-    // pose only: a fixed grid of kBwdPoseBlocks CTAs strides over the Gaussians
-    if (grid > (unsigned)kBwdPoseBlocks) grid = kBwdPoseBlocks;
+    // pose only: a fixed grid of 8 CTAs per SM strides over the visible
+    // Gaussians (about one each at the tracking size)
+    const unsigned cap = (unsigned)(8 * (ws.band > 0 ? ws.band : 1));
+    if (grid > cap) grid = cap;
     return launch_pdl(preprocess_bwd_kernel<false>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,
                       grad_gauss, grad_pose, ps);
   }
