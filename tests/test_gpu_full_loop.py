@@ -117,6 +117,7 @@ def test_full_loop_runs_at_scale(dags, sequence):
     image = torch.empty((1, dags.IMG_CHANNELS, H, W), dtype=torch.float32, device=dev)
     last = torch.empty((1, H, W), dtype=torch.int32, device=dev)
     pose = torch.from_numpy(seq[0]["gt_pose"].copy()).to(dev)
+    prev_pose = None
     adam = mctx.gauss_adam_state(gauss)
     # fine-tuning rates: the map starts at the ground truth the frames render
     acfg = dags.default_gauss_adam_cfg(lr_mean=1e-4, lr_opacity=5e-3, lr_quat=1e-4, lr_scale=5e-4, lr_colour=2.5e-4)
@@ -127,6 +128,13 @@ def test_full_loop_runs_at_scale(dags, sequence):
         t0 = time.perf_counter()
         tg = targets[k]
         if k > 0:
+            # constant-velocity start: the last frame's motion applied again
+            cur = pose.cpu().numpy()
+            if prev_pose is not None:
+                Rd = cur[:, :3] @ prev_pose[:, :3].T
+                init = np.hstack([Rd @ cur[:, :3], (Rd @ cur[:, 3] + cur[:, 3] - Rd @ prev_pose[:, 3])[:, None]])
+                pose.copy_(torch.from_numpy(init))
+            prev_pose = cur
             st = tctx.track_lm(gauss, cam, pose, tg, 15)
             accepted.append(int(st[41].item()))
         tctx.forward(gauss, cam, pose[None], tg[None], image=image, last=last)
