@@ -21,11 +21,16 @@
  *             poses, Eq. (27));
  *   binning   the (tile, Gaussian) pair list sorted by (tile, depth, id).
  *
- * The paper does not print the rasteriser's equations or constants; the
- * readings used here (alpha clamp 0.99, skip below 1/255, stop before
- * transmittance falls under 1e-4, 0.3 px^2 dilation, near plane 0.2 m,
- * 1.3x frustum guard on the Jacobian, opacity-aware bounding radius) are
- * stated in the design notes and mirrored in the C ABI's config struct.
+ * The paper does not print the rasteriser's equations or constants. The
+ * readings used here are those of the published 3D Gaussian splatting
+ * rasteriser, restated: alpha = min(0.99, o exp(-d^T Q d / 2)); a Gaussian
+ * with alpha below 1/255 is skipped; compositing stops before the
+ * contribution that would take the transmittance under 1e-4; 0.3 px^2 is
+ * added to the 2D covariance's diagonal; means with camera z <= 0.2 m are
+ * culled; the EWA Jacobian is evaluated with x/z and y/z clamped to 1.3
+ * times the half field of view; a Gaussian is binned to the tiles its
+ * alpha >= 1/255 ellipse reaches. The same constants are the defaults of the
+ * C ABI's raster config.
  *
  * The depth order is decided on an FP32 depth key that both this oracle and
  * the CUDA path evaluate bit-identically (see depth_key). Other decisions
