@@ -92,6 +92,9 @@ struct dags_ctx {
   uint32_t *cand_ids = nullptr;   // [max_n] the tracking frame's culled candidates
   uint32_t *cand_n = nullptr;     // [1]
   float *cull_pose = nullptr;     // [12]
+  uint32_t *track_order = nullptr;  // [max_tiles] the tracking loop's render order (ranked one iteration late)
+  uint32_t *prev_count = nullptr;   // [max_tiles] the counts it is ranked from
+  int track_order_tiles = 0;        // the tile count track_order is a permutation of (0: none yet)
   double *reg_partial = nullptr;  // per-CTA sums of the regulariser (first call)
   double *edge_partial = nullptr; // per-CTA sums of the edge-warp term (first call)
   float *rel32 = nullptr;         // [12] FP32 relative pose of the regularisers (first call)
@@ -323,6 +326,8 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   A(alloc(&c->cand_ids, (size_t)w.max_n));
   A(alloc(&c->cand_n, (size_t)1));
   A(alloc(&c->cull_pose, (size_t)12));
+  A(alloc(&c->track_order, (size_t)w.max_tiles));
+  A(alloc(&c->prev_count, (size_t)w.max_tiles));
   if (e == cudaSuccess) e = cudaMemset(w.tile_count, 0, vt * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(w.tile_cursor, 0, vt * sizeof(uint32_t));
   MpBuffers &mb = c->mp;
@@ -347,7 +352,8 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
     cudaGetLastError();
     free_mp(c->mp);
     free_ws(w);
-    for (void *p : {(void *)c->warp_masks, (void *)c->cand_ids, (void *)c->cand_n, (void *)c->cull_pose})
+    for (void *p : {(void *)c->warp_masks, (void *)c->cand_ids, (void *)c->cand_n, (void *)c->cull_pose,
+                    (void *)c->track_order, (void *)c->prev_count})
       if (p) cudaFree(p);
     delete c;
     return code;
@@ -371,7 +377,8 @@ void dags_destroy(dags_ctx *ctx) {
   if (ctx->graph_lm.exec_chunk) cudaGraphExecDestroy(ctx->graph_lm.exec_chunk);
   if (ctx->graph_lm.cap) cudaStreamDestroy(ctx->graph_lm.cap);
   free_lm(ctx->lm);
-  for (void *p : {(void *)ctx->warp_masks, (void *)ctx->cand_ids, (void *)ctx->cand_n, (void *)ctx->cull_pose})
+  for (void *p : {(void *)ctx->warp_masks, (void *)ctx->cand_ids, (void *)ctx->cand_n, (void *)ctx->cull_pose,
+                  (void *)ctx->track_order, (void *)ctx->prev_count})
     if (p) cudaFree(p);
   if (ctx->reg_partial) cudaFree(ctx->reg_partial);
   if (ctx->edge_partial) cudaFree(ctx->edge_partial);
@@ -631,6 +638,12 @@ Workspace track_workspace(const dags_ctx *ctx, const Raster &r) {
   w.cand_ids = ctx->cand_ids;
   w.cand_n = ctx->cand_n;
   w.cull_pose = ctx->cull_pose;
+  // the renders launch in an order ranked from the previous iteration's
+  // counts (a permutation of the tiles whatever the counts; ranking this
+  // iteration's would add a serial step before the forward)
+  w.tile_order = ctx->track_order;
+  w.order_next = ctx->track_order;
+  w.prev_count = ctx->prev_count;
   return w;
 }
 
@@ -722,6 +735,11 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   {
     Raster r;
     if ((rc = make_raster(cam, &rc_v, &r))) return rc;
+    if (ctx->track_order_tiles != r.T) {
+      // a new image size: the first iteration renders in tile order
+      if (launch_order_identity(ctx->track_order, r.T, s) != cudaSuccess) return DAGS_E_CUDA;
+      ctx->track_order_tiles = r.T;
+    }
     const int ev = ctx->timer.begin(DAGS_K_PREPROCESS, s);
     const cudaError_t e = launch_cull(track_workspace(ctx, r), reinterpret_cast<const float4 *>(gauss), n, pose, r, s);
     ctx->timer.end(ev, s);

@@ -46,6 +46,7 @@ enum {
   CNT_DONE_BWDPREP,    // CTAs of the preprocess backward that finished
   CNT_DONE_REG,        // CTAs of the regulariser that finished
   CNT_STATUS,          // status bits
+  CNT_PAD,             // (keeps the 64-bit requirement 8-byte aligned)
   CNT_REQ_LO,          // pairs required by the last forward (low / high word)
   CNT_REQ_HI,
   CNT_N
@@ -111,6 +112,11 @@ struct Workspace {
   uint32_t *cand_ids = nullptr;     // [max_n]
   uint32_t *cand_n = nullptr;       // [1]
   float *cull_pose = nullptr;       // [12]
+  // Render order of the tracking loop: tile_order is ranked from the
+  // previous iteration's counts (prev_count, written by the forward), by an
+  // extra CTA of the pose chain, into order_next for the next iteration.
+  uint32_t *prev_count = nullptr;   // [max_tiles]
+  uint32_t *order_next = nullptr;   // [max_tiles]
 };
 
 // The list range [s, e) of tile t in the workspace's bucket layout.
@@ -173,6 +179,9 @@ cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, i
 // its pose stays within the culling bounds).
 cudaError_t launch_cull(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose, const Raster &r,
                         cudaStream_t s);
+// The identity render order of `tiles` tiles (the tracking loop's first
+// iteration at a new image size).
+cudaError_t launch_order_identity(uint32_t *order, int tiles, cudaStream_t s);
 cudaError_t launch_render_fwd(const Workspace &ws, int views, int64_t n, const Raster &r, const Loss &l,
                               const float4 *targets, float *image, int32_t *last, double *loss,
                               cudaStream_t s);

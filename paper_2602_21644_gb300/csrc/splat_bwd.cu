@@ -17,6 +17,7 @@
 //                          per CTA and then, by the last CTA, in a fixed order
 //                          in FP64.
 #include "common.cuh"
+#include "tile_sort.cuh"
 
 namespace dags {
 
@@ -40,9 +41,20 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   __shared__ uint32_t s_id[kTilePix];
   __shared__ int s_max;
   const unsigned FULLM = 0xffffffffu;
-  const uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
-  if (tot > (uint64_t)ws.max_pairs) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (ws.bucket_cap) {
+    // fixed-bucket layout: an overflowed tile is skipped (its count is
+    // cleared for the next preprocess all the same)
+    const int t = (int)ws.tile_order[blockIdx.x];
+    if (ws.tile_count[t] > ws.bucket_cap) {
+      __syncthreads();
+      if (tid == 0) ws.tile_count[t] = 0u;
+      return;
+    }
+  } else {
+    const uint64_t tot = (uint64_t)ws.counters[CNT_REQ_LO] | ((uint64_t)ws.counters[CNT_REQ_HI] << 32);
+    if (tot > (uint64_t)ws.max_pairs) return;
+  }
   // the 2D-gradient word whose warp sum this lane receives from the
   // reduce-scatter below (words G2_U .. G2_Z, and with FULL up to G2_BL), and
   // whether it is the lowest lane holding that word (the one that adds it)
@@ -367,13 +379,21 @@ __global__ void __launch_bounds__(kBwdPrepBlock)
 preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, int views, Raster r,
                       float *__restrict__ grad_gauss, double *__restrict__ grad_pose, PoseStep ps) {
   pdl_wait();
+  // pose only, tracking loop: the grid's last CTA ranks the tiles by this
+  // iteration's counts for the next iteration's render order, beside the
+  // chain CTAs and outside their count
+  const bool ordering = !FULL && ws.order_next != nullptr;
+  if (ordering && blockIdx.x == gridDim.x - 1) {
+    rank_tiles(ws.prev_count, r.T, ws.order_next, ws.band);
+    return;
+  }
   __shared__ float sp[kMaxViewsSmem * 12];
   __shared__ float2 s_red[kBwdPrepBlock / 32][6];
   __shared__ int s_last;
   for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = ws.pose32[k];
   __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nb = gridDim.x;
+  const int nb = gridDim.x - (ordering ? 1 : 0);
   if (FULL) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
@@ -419,38 +439,47 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   if (tid == 0) {
     __threadfence();
     const unsigned t = atomicAdd(ws.counters + CNT_DONE_BWDPREP, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nb - 1u);
     if (s_last) __threadfence();
   }
   __syncthreads();
   if (!s_last) return;
-  // one warp per (view, component): lane-strided compensated sums of the
-  // CTA partials (four independent accumulators, in a fixed order), then a
-  // fixed shuffle tree; the result is the FP64 sum of the high and low words
-  for (int vc = wid; vc < views * 6; vc += kBwdPrepBlock / 32) {
-    const int v = vc / 6, c = vc % 6;
-    const float2 *src = ws.pose_partial + (size_t)v * nb * 6 + c;
-    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int b0 = lane; b0 < nb; b0 += 32 * 8) {
-      float2 t[8];
+  // the CTA partials of each view, summed by every thread of the last CTA:
+  // thread t takes CTAs t, t + 128, ... (all loads of a round issued before
+  // they are added), each component in compensated FP32 in a fixed order,
+  // then a fixed shuffle tree and the warps in order; the result is the
+  // FP64 sum of the high and low words
+  for (int v = 0; v < views; ++v) {
+    const float2 *src = ws.pose_partial + (size_t)v * nb * 6;
+    float h[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, l[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int b0 = tid; b0 < nb; b0 += kBwdPrepBlock * 4) {
+      float2 t[4][6];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int b = b0 + 32 * u;
-        t[u] = b < nb ? __ldcg(src + (size_t)b * 6) : make_float2(0.f, 0.f);
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + kBwdPrepBlock * u;
+#pragma unroll
+        for (int c = 0; c < 6; ++c) t[u][c] = b < nb ? __ldcg(src + (size_t)b * 6 + c) : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) cadd(h[u & 3], l[u & 3], t[u].x, t[u].y);
-    }
-    cadd(h[0], l[0], h[1], l[1]);
-    cadd(h[2], l[2], h[3], l[3]);
-    cadd(h[0], l[0], h[2], l[2]);
-    float hh = h[0], ll = l[0];
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      cadd(hh, ll, __shfl_xor_sync(0xffffffffu, hh, o), __shfl_xor_sync(0xffffffffu, ll, o));
-    if (lane == 0) grad_pose[v * 6 + c] = (double)hh + (double)ll;
+        for (int c = 0; c < 6; ++c) cadd(h[c], l[c], t[u][c].x, t[u][c].y);
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        cadd(h[c], l[c], __shfl_xor_sync(0xffffffffu, h[c], o), __shfl_xor_sync(0xffffffffu, l[c], o));
+      if (lane == 0) s_red[wid][c] = make_float2(h[c], l[c]);
+    }
+    __syncthreads();
+    if (tid < 6) {
+      float hh = 0.f, ll = 0.f;
+      for (int w = 0; w < kBwdPrepBlock / 32; ++w) cadd(hh, ll, s_red[w][tid].x, s_red[w][tid].y);
+      grad_pose[v * 6 + tid] = (double)hh + (double)ll;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid == 0) ws.counters[CNT_DONE_BWDPREP] = 0u;
   if (ps.poses) {
     __shared__ double s_xi[6], s_sc[3];
@@ -486,9 +515,11 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
                       grad_gauss, grad_pose, ps);
   } else {
     // pose only: a fixed grid of 8 CTAs per SM strides over the visible
-    // Gaussians (about one each at the tracking size)
+    // Gaussians (about one each at the tracking size); the tracking loop adds
+    // one CTA that ranks the tiles for the next iteration's render order
     const unsigned cap = (unsigned)(8 * (ws.band > 0 ? ws.band : 1));
     if (grid > cap) grid = cap;
+    if (ws.order_next) grid += 1;
     return launch_pdl(preprocess_bwd_kernel<false>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,
                       grad_gauss, grad_pose, ps);
   }

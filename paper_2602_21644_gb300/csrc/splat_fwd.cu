@@ -49,16 +49,6 @@ __device__ __forceinline__ int clampi(float x, int lo, int hi) {
 // other band, so that the SM that receives a band's longest tile receives the
 // next band's shortest one. Returns the sum.
 constexpr int kScanChunk = 4096;
-constexpr int kLenBins = 257;   // 256 length bins (descending) + empty tiles
-
-__device__ __forceinline__ int length_bin(uint32_t c) { return c ? 255 - (int)min(c >> 3, 255u) : 256; }
-
-// Slot of rank `pos` in the band-reversed ("snake") order of `total` ranks.
-__device__ __forceinline__ uint32_t snake_slot(uint32_t pos, uint32_t total, uint32_t band) {
-  const uint32_t b = pos / band, q = pos - b * band, base = b * band;
-  const uint32_t width = min(band, total - base);
-  return base + ((b & 1u) ? width - 1u - q : q);
-}
 
 __device__ uint64_t block_scan_tiles(uint32_t *count, uint32_t *start, uint32_t *cursor, int total,
                                      uint32_t *order, int band) {
@@ -255,80 +245,6 @@ __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r,
   }
 }
 
-// The last CTA of the preprocess in the fixed-bucket layout (one view): the
-// render launch order (tiles ranked by descending count in bins of 8,
-// band-reversed as block_scan_tiles orders them), the required pairs (the
-// largest count times the tiles: what max_pairs must be for every bucket to
-// hold its list) and the capacity flag, and the visible count. The counts
-// stay for the render, which clears its tile's.
-__device__ void order_direct_buckets(const Workspace &ws, int total) {
-  __shared__ uint32_t s_bin[kLenBins];
-  __shared__ uint32_t s_maxc;
-  const int tid = threadIdx.x, lane = tid & 31;
-  for (int k = tid; k < kLenBins; k += blockDim.x) s_bin[k] = 0u;
-  if (tid == 0) s_maxc = 0u;
-  __syncthreads();
-  uint32_t mx = 0;
-  for (int k0 = 0; k0 < total; k0 += blockDim.x) {
-    const int k = k0 + tid;
-    int bin = 1024 + lane;   // no element: a key of its own
-    if (k < total) {
-      const uint32_t c = __ldcg(ws.tile_count + k);
-      mx = max(mx, c);
-      bin = length_bin(c);
-    }
-    const unsigned grp = __match_any_sync(0xffffffffu, bin);
-    if (bin < kLenBins && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
-  }
-  mx = __reduce_max_sync(0xffffffffu, mx);
-  if (lane == 0) atomicMax(&s_maxc, mx);
-  __syncthreads();
-  if (tid < 32) {
-    uint32_t loc[9], sum = 0;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const int bb = 9 * lane + j;
-      loc[j] = bb < kLenBins ? s_bin[bb] : 0u;
-      sum += loc[j];
-    }
-    uint32_t inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += y;
-    }
-    uint32_t run = inc - sum;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-      const int bb = 9 * lane + j;
-      if (bb < kLenBins) s_bin[bb] = run;
-      run += loc[j];
-    }
-  }
-  __syncthreads();
-  const uint32_t band = ws.band > 0 ? (uint32_t)ws.band : 1u;
-  for (int k0 = 0; k0 < total; k0 += blockDim.x) {
-    const int k = k0 + tid;
-    int bin = 1024 + lane;
-    if (k < total) bin = length_bin(__ldcg(ws.tile_count + k));
-    const unsigned grp = __match_any_sync(0xffffffffu, bin);
-    const int leader = __ffs(grp) - 1;
-    uint32_t pos = 0;
-    if (bin < kLenBins && lane == leader) pos = atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
-    pos = __shfl_sync(0xffffffffu, pos, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
-    if (k < total) ws.tile_order[snake_slot(pos, (uint32_t)total, band)] = (uint32_t)k;
-  }
-  if (tid == 0) {
-    const uint64_t req = (uint64_t)s_maxc * (uint64_t)total;
-    ws.counters[CNT_REQ_LO] = (uint32_t)req;
-    ws.counters[CNT_REQ_HI] = (uint32_t)(req >> 32);
-    if (s_maxc > ws.bucket_cap) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
-    ws.vis_n[0] = ws.vis_append[0];
-    ws.vis_append[0] = 0u;
-    ws.counters[CNT_DONE_PREP] = 0u;
-  }
-}
-
 // Projection of Gaussian i (valid: i < n, else an empty lane) into view v:
 // the projected record, its FP32 remainders, the candidate tiles and the
 // zeroed 2D gradient of a visible Gaussian, its visible-list entry and the
@@ -428,7 +344,6 @@ __device__ __forceinline__ void stage_poses(const double *__restrict__ poses, in
   }
 }
 
-template <bool DIRECT>
 __global__ void __launch_bounds__(kPrepBlock)
 preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
                   const double *__restrict__ poses, int views, Raster r, int zero_words) {
@@ -441,19 +356,7 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   __syncthreads();
   if (blockIdx.x == 0 && blockIdx.y == 0)
     for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
-  preprocess_one<DIRECT>(ws, gauss, i, i < n, v, sp, spl, r, zero_words);
-  if (!DIRECT) return;
-  // the last CTA orders the renders
-  __shared__ int s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
-    s_last = (t == gridDim.x * gridDim.y - 1);
-    if (s_last) __threadfence();
-  }
-  __syncthreads();
-  if (s_last) order_direct_buckets(ws, r.T);
+  preprocess_one<false>(ws, gauss, i, i < n, v, sp, spl, r, zero_words);
 }
 
 // Per-frame culling of the tracking loop: the Gaussians that can be visible
@@ -539,11 +442,14 @@ preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n
                        Raster r, int zero_words) {
   pdl_wait();
   __shared__ float sp[12], spl[12];
-  __shared__ int s_valid, s_last;
+  __shared__ int s_valid;
   stage_poses(pose, 1, sp, spl);
   __syncthreads();
   if (threadIdx.x == 0) s_valid = within_cull_bounds(sp, ws.cull_pose) ? 1 : 0;
   if (blockIdx.x == 0 && threadIdx.x < 12) ws.pose32[threadIdx.x] = sp[threadIdx.x];
+  // the forward takes the largest bucket's requirement with atomicMax
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    *reinterpret_cast<unsigned long long *>(ws.counters + CNT_REQ_LO) = 0ull;
   __syncthreads();
   const bool use_cand = s_valid != 0;
   const int64_t count = use_cand ? (int64_t)*ws.cand_n : n;
@@ -554,15 +460,10 @@ preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n
     const int64_t i = !valid ? 0 : (use_cand ? (int64_t)ws.cand_ids[k] : k);
     preprocess_one<true>(ws, gauss, i, valid && i < n, 0, sp, spl, r, zero_words);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(ws.counters + CNT_DONE_PREP, 1u);
-    s_last = (t == gridDim.x - 1);
-    if (s_last) __threadfence();
-  }
-  __syncthreads();
-  if (s_last) order_direct_buckets(ws, r.T);
+}
+
+__global__ void order_identity_kernel(uint32_t *order, int tiles) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < tiles; k += gridDim.x * blockDim.x) order[k] = (uint32_t)k;
 }
 
 // One CTA turns the per-tile counts into offsets and the launch order, and
@@ -634,9 +535,30 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   __shared__ int s_last;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool ovf = pairs_overflow(ws, views * r.T);
-  // blocks are launched in order of descending list length
-  const int tile = ovf ? (int)blockIdx.x : (int)ws.tile_order[blockIdx.x];
+  // blocks are launched in order of descending list length. In the
+  // fixed-bucket layout a tile whose list overflowed its bucket is skipped
+  // (and reported); the forward publishes the visible count, the largest
+  // bucket's requirement and the counts the next iteration's order is
+  // ranked from. Otherwise an overflow anywhere skips every tile.
+  bool ovf;
+  int tile;
+  if (ws.bucket_cap) {
+    tile = (int)ws.tile_order[blockIdx.x];
+    const uint32_t c = ws.tile_count[tile];
+    ovf = c > ws.bucket_cap;
+    if (tid == 0) {
+      ws.prev_count[tile] = c;
+      atomicMax(reinterpret_cast<unsigned long long *>(ws.counters + CNT_REQ_LO), (unsigned long long)c * r.T);
+      if (ovf) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
+      if (blockIdx.x == 0) {
+        ws.vis_n[0] = ws.vis_append[0];
+        ws.vis_append[0] = 0u;
+      }
+    }
+  } else {
+    ovf = pairs_overflow(ws, views * r.T);
+    tile = ovf ? (int)blockIdx.x : (int)ws.tile_order[blockIdx.x];
+  }
   const int v = tile / r.T, tv = tile - v * r.T;
   const int tx = tv % r.tiles_x, ty = tv / r.tiles_x;
   // warp w covers the 8x4 pixel block (w % 2, w / 2) of the tile
@@ -800,7 +722,7 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
   if (views > kMaxViewsSmem) return cudaErrorInvalidValue;
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
   dim3 grid(gx > 0 ? gx : 1u, (unsigned)views);
-  cudaError_t e = launch_pdl(preprocess_kernel<false>, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, poses, views, r,
+  cudaError_t e = launch_pdl(preprocess_kernel, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, poses, views, r,
                              zero_grad_words);
   if (e == cudaSuccess) e = launch_pdl(tile_scan_kernel, dim3(1), dim3(kScanThreads), 0, s, ws, views, r);
   return e;
@@ -808,17 +730,18 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
 
 cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
                                      const Raster &r, int zero_grad_words, cudaStream_t s) {
-  if (ws.bucket_cap == 0) return cudaErrorInvalidValue;
+  if (ws.bucket_cap == 0 || !ws.cand_ids) return cudaErrorInvalidValue;
+  // the frame's culled list: a fixed grid strides over it
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
-  if (ws.cand_ids) {
-    // the culled list of the frame: a fixed grid strides over it
-    const unsigned g = gx < (unsigned)(8 * ws.band) ? (gx > 0 ? gx : 1u) : (unsigned)(8 * ws.band);
-    return launch_pdl(preprocess_cull_kernel, dim3(g), dim3(kPrepBlock), 0, s, ws, gauss, n, pose, r,
-                      zero_grad_words);
-  }
-  dim3 grid(gx > 0 ? gx : 1u, 1u);
-  return launch_pdl(preprocess_kernel<true>, grid, dim3(kPrepBlock), 0, s, ws, gauss, n, pose, 1, r,
+  const unsigned g = gx < (unsigned)(8 * ws.band) ? (gx > 0 ? gx : 1u) : (unsigned)(8 * ws.band);
+  return launch_pdl(preprocess_cull_kernel, dim3(g), dim3(kPrepBlock), 0, s, ws, gauss, n, pose, r,
                     zero_grad_words);
+}
+
+cudaError_t launch_order_identity(uint32_t *order, int tiles, cudaStream_t s) {
+  if (tiles <= 0) return cudaSuccess;
+  order_identity_kernel<<<(tiles + 255) / 256, 256, 0, s>>>(order, tiles);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_cull(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose, const Raster &r,

@@ -6,6 +6,74 @@
 
 namespace dags {
 
+// Render launch order: tiles ranked by descending list length in bins of 8
+// entries (empty tiles last), each band of `band` consecutive ranks (one CTA
+// per SM in a dispatch round) reversed every other band, so that the SM that
+// receives a band's longest tile receives the next band's shortest one.
+constexpr int kLenBins = 257;   // 256 length bins (descending) + empty tiles
+
+__device__ __forceinline__ int length_bin(uint32_t c) { return c ? 255 - (int)min(c >> 3, 255u) : 256; }
+
+// Slot of rank `pos` in the band-reversed ("snake") order of `total` ranks.
+__device__ __forceinline__ uint32_t snake_slot(uint32_t pos, uint32_t total, uint32_t band) {
+  const uint32_t b = pos / band, q = pos - b * band, base = b * band;
+  const uint32_t width = min(band, total - base);
+  return base + ((b & 1u) ? width - 1u - q : q);
+}
+
+// Ranks tiles by descending count (bins of 8 entries, empty tiles last),
+// band-reversed as block_scan_tiles orders them; one whole CTA.
+__device__ inline void rank_tiles(const uint32_t *count, int total, uint32_t *order, int band) {
+  __shared__ uint32_t s_bin[kLenBins];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < kLenBins; k += blockDim.x) s_bin[k] = 0u;
+  __syncthreads();
+  for (int k0 = 0; k0 < total; k0 += blockDim.x) {
+    const int k = k0 + tid;
+    int bin = 1024 + lane;   // no element: a key of its own
+    if (k < total) bin = length_bin(__ldcg(count + k));
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    if (bin < kLenBins && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+  }
+  __syncthreads();
+  if (tid < 32) {
+    uint32_t loc[9], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int bb = 9 * lane + j;
+      loc[j] = bb < kLenBins ? s_bin[bb] : 0u;
+      sum += loc[j];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    uint32_t run = inc - sum;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      const int bb = 9 * lane + j;
+      if (bb < kLenBins) s_bin[bb] = run;
+      run += loc[j];
+    }
+  }
+  __syncthreads();
+  const uint32_t bnd = band > 0 ? (uint32_t)band : 1u;
+  for (int k0 = 0; k0 < total; k0 += blockDim.x) {
+    const int k = k0 + tid;
+    int bin = 1024 + lane;
+    if (k < total) bin = length_bin(__ldcg(count + k));
+    const unsigned grp = __match_any_sync(0xffffffffu, bin);
+    const int leader = __ffs(grp) - 1;
+    uint32_t pos = 0;
+    if (bin < kLenBins && lane == leader) pos = atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+    if (k < total) order[snake_slot(pos, (uint32_t)total, bnd)] = (uint32_t)k;
+  }
+}
+
+
 // Ascending bitonic sort of s[0, len2) (len2 a power of two) by the CTA.
 __device__ __forceinline__ void bitonic_smem(uint64_t *s, int len2) {
   for (int k = 2; k <= len2; k <<= 1) {
