@@ -151,7 +151,8 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
     for (int g = (top - 1) >> 5; g >= 0; --g) {
       const int gk = (beg >> 5) + g;
       unsigned mask;
-      if (MASKS && gk < kMaskGroups) {
+      const bool recorded = MASKS && gk < kMaskGroups;
+      if (recorded) {
         mask = __ldg(wmask + gk * 8);
       } else {
         const int jj = g * 32 + lane;
@@ -170,46 +171,49 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
         mask &= ~(1u << bit);
         const int j = g * 32 + bit;
         const int k = beg + j;
-        bool contrib = false;
-        float gu = 0.f, gv = 0.f, ga = 0.f, gb = 0.f, gc = 0.f, gz = 0.f;
-        float go = 0.f, gr = 0.f, gg = 0.f, gbl = 0.f;
-        if (k < lastp) {
-          const float4 a = s_a[j], b = s_b[j];
-          const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
-          const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
-          if (COUNT) ++n_eval;
-          if (p >= r.log2_alpha_min) {
-            contrib = true;
-            if (COUNT) ++n_contrib;
-            const float ag = hw_exp2(p);
-            const float alpha = fminf(r.alpha_max, ag);
-            const float inv = hw_rcp(1.f - alpha);
-            T *= inv;                       // transmittance in front of this Gaussian
-            const float wk = alpha * T;
-            const float4 c = s_c[j];
-            const uint32_t rgb = __float_as_uint(c.z), blb = __float_as_uint(c.w);
-            const float fr = bf16_lo(rgb), fg = bf16_hi(rgb), fb = bf16_lo(blb);
-            // dL/dalpha = sum_ch g_ch (c_ch T - S_ch / (1 - alpha))
-            const float gcv = fmaf(g0, fr, fmaf(g1, fg, fmaf(g2, fb, fmaf(g3, c.x, fmaf(g5, c.y, g4)))));
-            const float dal = fmaf(gcv, T, -Sg * inv);
-            gz = g3 * wk;
-            if (FULL) { gr = g0 * wk; gg = g1 * wk; gbl = g2 * wk; }
-            if (ag <= r.alpha_max) {
-              // d alpha / d(natural exponent) = alpha; the exponent in log2
-              // units is p, so d/dx of the natural exponent is ln2 * dp/dx
-              const float dpw = dal * alpha;
-              const float hl = dpw * kLn2;
-              gu = hl * (2.f * b.x * dx + b.y * dy);
-              gv = hl * (b.y * dx + 2.f * b.z * dy);
-              ga = -0.5f * dpw * dx * dx;
-              gb = -dpw * dx * dy;
-              gc = -0.5f * dpw * dy * dy;
-              if (FULL) go = dal * hw_exp2(p - b.w);
-            }
-            Sg = fmaf(gcv, wk, Sg);
-          }
+        // evaluated by every lane, without branches: a lane past its last
+        // contributor or below alpha_min keeps T and Sg and carries zero
+        // gradients, so each contributing lane's values are those of the
+        // branching form, operation for operation
+        const float4 a = s_a[j], b = s_b[j];
+        const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
+        const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+        const bool contrib = k < lastp && p >= r.log2_alpha_min;
+        if (COUNT) { n_eval += k < lastp ? 1u : 0u; n_contrib += contrib ? 1u : 0u; }
+        const float ag = hw_exp2(p);
+        const float alpha = fminf(r.alpha_max, ag);
+        const float inv = hw_rcp(1.f - alpha);
+        T = contrib ? T * inv : T;           // transmittance in front of this Gaussian
+        const float wk = alpha * T;
+        const float4 c = s_c[j];
+        const uint32_t rgb = __float_as_uint(c.z), blb = __float_as_uint(c.w);
+        const float fr = bf16_lo(rgb), fg = bf16_hi(rgb), fb = bf16_lo(blb);
+        // dL/dalpha = sum_ch g_ch (c_ch T - S_ch / (1 - alpha))
+        const float gcv = fmaf(g0, fr, fmaf(g1, fg, fmaf(g2, fb, fmaf(g3, c.x, fmaf(g5, c.y, g4)))));
+        const float dal = fmaf(gcv, T, -Sg * inv);
+        const float gz = contrib ? g3 * wk : 0.f;
+        float gr = 0.f, gg = 0.f, gbl = 0.f, go = 0.f;
+        if (FULL) {
+          gr = contrib ? g0 * wk : 0.f;
+          gg = contrib ? g1 * wk : 0.f;
+          gbl = contrib ? g2 * wk : 0.f;
         }
-        if (__any_sync(FULLM, contrib)) {
+        // below the clamp, d alpha / d(natural exponent) = alpha; the
+        // exponent in log2 units is p, so d/dx of the natural exponent is
+        // ln2 * dp/dx (at the clamp alpha does not move with the exponent)
+        const bool slope = contrib && ag <= r.alpha_max;
+        const float dpw = slope ? dal * alpha : 0.f;
+        const float hl = dpw * kLn2;
+        const float gu = hl * (2.f * b.x * dx + b.y * dy);
+        const float gv = hl * (b.y * dx + 2.f * b.z * dy);
+        const float ga = -0.5f * dpw * dx * dx;
+        const float gb = -dpw * dx * dy;
+        const float gc = -0.5f * dpw * dy * dy;
+        if (FULL) go = slope ? dal * hw_exp2(p - b.w) : 0.f;
+        Sg = contrib ? fmaf(gcv, wk, Sg) : Sg;
+        // a recorded entry has a contributing lane: the forward took it for
+        // the same pixels by the same arithmetic
+        if (recorded || __any_sync(FULLM, contrib)) {
           // reduce-scatter over the warp: every lane then holds the warp sum
           // of word `comp`, and one lane per word adds it with one atomic
           float *dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
@@ -379,11 +383,12 @@ __global__ void __launch_bounds__(kBwdPrepBlock)
 preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, int views, Raster r,
                       float *__restrict__ grad_gauss, double *__restrict__ grad_pose, PoseStep ps) {
   pdl_wait();
-  // pose only, tracking loop: the grid's last CTA ranks the tiles by this
-  // iteration's counts for the next iteration's render order, beside the
-  // chain CTAs and outside their count
+  // pose only, tracking loop: the grid's first CTA (dispatched first, so
+  // that it runs beside the chain CTAs from the start) ranks the tiles by
+  // this iteration's counts for the next iteration's render order; the
+  // chain CTAs are numbered from the second
   const bool ordering = !FULL && ws.order_next != nullptr;
-  if (ordering && blockIdx.x == gridDim.x - 1) {
+  if (ordering && blockIdx.x == 0) {
     rank_tiles(ws.prev_count, r.T, ws.order_next, ws.band);
     return;
   }
@@ -394,6 +399,7 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = gridDim.x - (ordering ? 1 : 0);
+  const int bid = blockIdx.x - (ordering ? 1 : 0);
   if (FULL) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
@@ -424,13 +430,13 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       float pg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int64_t nv = ws.vis_n[v];
       const uint32_t *vis = ws.vis_ids + (size_t)v * ws.max_n;
-      for (int64_t k = (int64_t)blockIdx.x * blockDim.x + tid; k < nv; k += (int64_t)nb * blockDim.x) {
+      for (int64_t k = (int64_t)bid * blockDim.x + tid; k < nv; k += (int64_t)nb * blockDim.x) {
         int64_t i = vis[k];
         if (!DAGS_IN_BOUNDS(i >= 0 && i < n, ws.counters + CNT_STATUS)) continue;
         const float4 g0 = __ldg(gauss + 4 * i + 0), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
         chain_one<false>(ws, r, g0, g1, g2, sp + v * 12, (size_t)v * ws.max_n + i, pg, nullptr);
       }
-      store_pose_partial(ws, pg, v, blockIdx.x, nb, s_red);
+      store_pose_partial(ws, pg, v, bid, nb, s_red);
     }
   }
   if (!grad_pose) return;
@@ -514,10 +520,11 @@ cudaError_t launch_preprocess_bwd(const Workspace &ws, const float4 *gauss, int6
     return launch_pdl(preprocess_bwd_kernel<true>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,
                       grad_gauss, grad_pose, ps);
   } else {
-    // pose only: a fixed grid of 8 CTAs per SM strides over the visible
-    // Gaussians (about one each at the tracking size); the tracking loop adds
-    // one CTA that ranks the tiles for the next iteration's render order
-    const unsigned cap = (unsigned)(8 * (ws.band > 0 ? ws.band : 1));
+    // pose only: a fixed grid of 4 CTAs per SM (one wave) strides over the
+    // visible Gaussians (at most one per thread at the tracking size); the
+    // tracking loop adds one CTA that ranks the tiles for the next
+    // iteration's render order
+    const unsigned cap = (unsigned)(4 * (ws.band > 0 ? ws.band : 1));
     if (grid > cap) grid = cap;
     if (ws.order_next) grid += 1;
     return launch_pdl(preprocess_bwd_kernel<false>, dim3(grid), dim3(kBwdPrepBlock), 0, s, ws, gauss, n, views, r,

@@ -612,30 +612,27 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
         const int bit = __ffs(mask) - 1;
         const int j = g * 32 + bit;
         mask &= mask - 1;
-        bool contrib = false;
-        if (!done) {
-          const float4 a = s_a[j], b = s_b[j];
-          const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
-          const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
-          if (COUNT) ++n_eval;
-          if (p >= r.log2_alpha_min) {                    // else alpha < alpha_min
-            const float alpha = fminf(r.alpha_max, hw_exp2(p));
-            const float tt = T * (1.f - alpha);
-            if (tt < r.t_min) {
-              done = true;
-            } else {
-              contrib = true;
-              if (COUNT) ++n_contrib;
-              const float w = alpha * T;
-              const float4 c = s_c[j];
-              const uint32_t rg = __float_as_uint(c.z), bl = __float_as_uint(c.w);
-              cr += bf16_lo(rg) * w; cg += bf16_hi(rg) * w; cb += bf16_lo(bl) * w;
-              dd += c.x * w; oo += w; rm += c.y * w;
-              T = tt;
-              lastk = (int)(base - s) + j + 1;
-            }
-          }
-        }
+        // evaluated by every lane, without branches: a lane that is done,
+        // or whose alpha is below alpha_min, or that would stop here adds
+        // a zero weight and keeps T (x + 0 * c == x), so each pixel's sums
+        // are those of the branching form, operation for operation
+        const float4 a = s_a[j], b = s_b[j];
+        const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
+        const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+        const bool live = !done && p >= r.log2_alpha_min;   // else alpha < alpha_min
+        const float alpha = fminf(r.alpha_max, hw_exp2(p));
+        const float tt = T * (1.f - alpha);
+        const bool stop = live && tt < r.t_min;
+        const bool contrib = live && !stop;
+        if (COUNT) { n_eval += done ? 0u : 1u; n_contrib += contrib ? 1u : 0u; }
+        done = done || stop;
+        const float w = contrib ? alpha * T : 0.f;
+        const float4 c = s_c[j];
+        const uint32_t rg = __float_as_uint(c.z), bl = __float_as_uint(c.w);
+        cr += bf16_lo(rg) * w; cg += bf16_hi(rg) * w; cb += bf16_lo(bl) * w;
+        dd += c.x * w; oo += w; rm += c.y * w;
+        T = contrib ? tt : T;
+        lastk = contrib ? (int)(base - s) + j + 1 : lastk;
         if (MASKS && __any_sync(FULL, contrib)) took |= 1u << bit;
       }
       if (MASKS) {

@@ -22,16 +22,28 @@ __device__ __forceinline__ uint32_t snake_slot(uint32_t pos, uint32_t total, uin
 }
 
 // Ranks tiles by descending count (bins of 8 entries, empty tiles last),
-// band-reversed as block_scan_tiles orders them; one whole CTA.
+// band-reversed as block_scan_tiles orders them; one whole CTA. Up to
+// kRankStage tiles, the bins are formed once into shared memory by loads
+// issued four at a time, so that the two passes wait on L2 once rather
+// than once per round.
+constexpr int kRankStage = 4096;
+
 __device__ inline void rank_tiles(const uint32_t *count, int total, uint32_t *order, int band) {
   __shared__ uint32_t s_bin[kLenBins];
+  __shared__ uint16_t s_tb[kRankStage];
   const int tid = threadIdx.x, lane = tid & 31;
+  const bool staged = total <= kRankStage;
   for (int k = tid; k < kLenBins; k += blockDim.x) s_bin[k] = 0u;
+  if (staged) {
+#pragma unroll 4
+    for (int k = tid; k < total; k += blockDim.x) s_tb[k] = (uint16_t)length_bin(__ldcg(count + k));
+  }
   __syncthreads();
+  auto bin_of = [&](int k) { return staged ? (int)s_tb[k] : length_bin(__ldcg(count + k)); };
   for (int k0 = 0; k0 < total; k0 += blockDim.x) {
     const int k = k0 + tid;
     int bin = 1024 + lane;   // no element: a key of its own
-    if (k < total) bin = length_bin(__ldcg(count + k));
+    if (k < total) bin = bin_of(k);
     const unsigned grp = __match_any_sync(0xffffffffu, bin);
     if (bin < kLenBins && lane == __ffs(grp) - 1) atomicAdd(&s_bin[bin], (uint32_t)__popc(grp));
   }
@@ -63,7 +75,7 @@ __device__ inline void rank_tiles(const uint32_t *count, int total, uint32_t *or
   for (int k0 = 0; k0 < total; k0 += blockDim.x) {
     const int k = k0 + tid;
     int bin = 1024 + lane;
-    if (k < total) bin = length_bin(__ldcg(count + k));
+    if (k < total) bin = bin_of(k);
     const unsigned grp = __match_any_sync(0xffffffffu, bin);
     const int leader = __ffs(grp) - 1;
     uint32_t pos = 0;

@@ -101,14 +101,16 @@ class Runner:
         self.ctx.mp_update(g, self.cam, pose, tg, image, inst, self.table, lab, mp_pixel=out, cfg=self.mp_cfg)
         return out
 
-    def run(self, mode, net=None, collect=False, schedule=None, follow=False):
+    def run(self, mode, net=None, collect=False, schedule=None, follow=False, score_only=False):
         """mode: 'fresh' (fresh prior every frame), 'stale' (the method without
         the network), 'learned' (network proposal between refreshes).
         Refreshes come every REFRESH frames, or from the semantic-on-demand
         trigger (Eqs. (13)-(16)) when schedule (a dags_sched_cfg) is given.
         follow: the map's moving-object Gaussians are placed at their frame's
         positions before each frame (a map that mapping keeps up to date), so
-        that the frame's residuals come from the observation noise only."""
+        that the frame's residuals come from the observation noise only.
+        score_only (with schedule): the trigger scores every frame but the
+        refreshes keep the fixed cadence."""
         gauss = torch.from_numpy(self.seq.rec.copy()).cuda()
         base = gauss[:, 0:3].clone()
         vel = torch.from_numpy(self.seq.velocity).cuda()
@@ -124,7 +126,7 @@ class Runner:
             image = self.render(gauss, pose)
             if mode == "fresh":
                 refreshed = True
-            elif schedule is not None:
+            elif schedule is not None and not score_only:
                 refreshed = nxt
             else:
                 refreshed = f % REFRESH == 0
@@ -191,6 +193,28 @@ def iou(a, b):
     return np.logical_and(a, b).sum() / u if u else 1.0
 
 
+def calibrate_schedule(dags, runner, follow=False):
+    """The trigger's constants (Eqs. (14)-(16)) fitted to a training sequence
+    run with the fixed cadence: e_ref is twice the largest mean background
+    residual at any prior age, so that R = e_bar / e_ref stays below 1/2
+    and follows the residual instead of saturating; theta lies halfway
+    between the mean score S of the frames with a fresh prior and of those
+    REFRESH - 1 frames after a refresh, so that the trigger fires once the
+    stale prior has cost half of what a full interval costs. Returns
+    (dags_sched_cfg, dict of the fitted statistics)."""
+    base = dags.default_sched_cfg()
+    hist = runner.run("stale", schedule=base, score_only=True, follow=follow)
+    age = np.array([f % REFRESH for f in range(len(hist))])
+    e_bar = np.array([h["score"][0].item() for h in hist])
+    e_ref = 2.0 * max(e_bar[age == a].mean() for a in range(REFRESH))
+    cfg = dags.default_sched_cfg(e_ref=float(e_ref))
+    hist = runner.run("stale", schedule=cfg, score_only=True, follow=follow)
+    S = np.array([h["score"][2].item() for h in hist])
+    s0, s9 = S[age == 0].mean(), S[age == REFRESH - 1].mean()
+    cfg.theta = float(s0 + 0.5 * (s9 - s0))
+    return cfg, {"e_ref": float(e_ref), "theta": cfg.theta, "S_fresh": float(s0), "S_stale": float(s9)}
+
+
 def experiment(dags, steps=1000, follow=False, mp_cfg=None):
     """Train on one sequence, run fresh / stale / learned on the held-out one.
     follow: the map keeps its moving objects at their current positions (see
@@ -199,6 +223,7 @@ def experiment(dags, steps=1000, follow=False, mp_cfg=None):
     train_seq = Sequence(seed=11, velocities=[(0.0, 0.0, 0.3), (-0.3, 0.0, 0.0)], n_frames=60)
     tr = Runner(dags, train_seq, mp_cfg)
     net, losses = train_net(dags, tr, steps=steps, follow=follow)
+    cal, cal_stats = calibrate_schedule(dags, tr, follow=follow)
     tr.ctx.close()
     eval_seq = Sequence(seed=12, velocities=[(0.3, 0.0, 0.0), (0.0, 0.0, 0.3)], n_frames=40)
     ev = Runner(dags, eval_seq, mp_cfg)
@@ -206,7 +231,10 @@ def experiment(dags, steps=1000, follow=False, mp_cfg=None):
     out = dict(losses=losses, fresh=ev.run("fresh", follow=follow), stale=ev.run("stale", follow=follow),
                learned=ev.run("learned", net=net, follow=follow),
                scheduled=ev.run("stale", schedule=sc, follow=follow),
-               scheduled_learned=ev.run("learned", net=net, schedule=sc, follow=follow), seq=eval_seq)
+               scheduled_learned=ev.run("learned", net=net, schedule=sc, follow=follow),
+               calibrated=ev.run("stale", schedule=cal, follow=follow),
+               calibrated_learned=ev.run("learned", net=net, schedule=cal, follow=follow),
+               calibration=cal_stats, seq=eval_seq)
     ev.ctx.close()
     return out
 
@@ -250,7 +278,9 @@ def schedule_metrics(ex):
     learned proposal's map where it stands in for M_p)."""
     j = ex["fresh"]
     out = {}
-    for name in ("stale", "scheduled", "learned", "scheduled_learned"):
+    for name in ("stale", "scheduled", "learned", "scheduled_learned", "calibrated", "calibrated_learned"):
+        if name not in ex:
+            continue
         h = ex[name]
         mae, agree = [], []
         for f in range(1, len(j)):

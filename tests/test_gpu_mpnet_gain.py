@@ -39,12 +39,31 @@ def test_scheduled_refreshes(experiment):
     sm = mp_eval.schedule_metrics(experiment)
     print("\n" + repr(sm))
     T = len(experiment["fresh"])
-    for name in ("scheduled", "scheduled_learned"):
+    for name in ("scheduled", "scheduled_learned", "calibrated", "calibrated_learned"):
         h = experiment[name]
         ref = [f for f, r in enumerate(h) if r["refreshed"]]
         assert ref[0] == 0 and all(b - a <= 10 for a, b in zip(ref, ref[1:] + [T]))
         assert sm[name]["calls"] == len(ref) <= T
     assert sm["stale"]["calls"] == (T + 9) // 10
+
+
+def test_calibrated_trigger(experiment):
+    # The default e_ref (5 cm) lies below the background residual of these
+    # sequences, so R = 1 every frame and the trigger fires on every frame.
+    # Fitted on the training sequence (e_ref = twice the largest mean
+    # background residual at any prior age, theta halfway between the scores
+    # of fresh and nine-frame-old priors), R stays below 1/2 and the trigger
+    # skips frames on the held-out sequence
+    from paper_2602_21644_gb300 import mp_eval
+    cal = experiment["calibration"]
+    sm = mp_eval.schedule_metrics(experiment)
+    print("\n" + repr(cal) + "\n" + repr({k: sm[k] for k in ("calibrated", "calibrated_learned")}))
+    T = len(experiment["fresh"])
+    assert cal["e_ref"] > 0 and np.isfinite(cal["theta"])
+    assert min(cal["S_fresh"], cal["S_stale"]) <= cal["theta"] <= max(cal["S_fresh"], cal["S_stale"])
+    R = [r["score"][1].item() for r in experiment["calibrated"]]
+    assert np.mean(np.array(R) < 1.0) > 0.9, R
+    assert sm["calibrated"]["calls"] < T, sm
 
 
 def test_training_converges(result):
