@@ -650,11 +650,12 @@ Workspace track_workspace(const dags_ctx *ctx, const Raster &r) {
 // Enqueues one tracking iteration: projection and binning into the
 // fixed-capacity buckets, the forward with loss, the pose-only adjoint, and
 // the chain to the pose twist with the pose step in its last CTA (arguments
-// checked by the caller).
+// checked by the caller). follows_iteration: the launch just before is the
+// previous iteration's last kernel, in the same stream or captured graph.
 int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                     const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                     const dags_pose_cfg *pcfg, double *adam_state, float *image, int32_t *last, double *loss,
-                    double *grad_pose, cudaStream_t s) {
+                    double *grad_pose, bool follows_iteration, cudaStream_t s) {
   Raster r;
   Loss l;
   int rc;
@@ -668,7 +669,10 @@ int track_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_cam
   KernelTimer &tm = ctx->timer;
   // the pose path accumulates 2D-gradient words G2_U .. G2_Z: two float4
   int ev = tm.begin(DAGS_K_PREPROCESS, s);
-  cudaError_t e = launch_preprocess_direct(w, g4, n, pose, r, 8, s);
+  // after an iteration, the candidate list is three launches old and the
+  // preprocess may load it before waiting for the pose step; after the
+  // culling launch it may not
+  cudaError_t e = launch_preprocess_direct(w, g4, n, pose, r, 8, follows_iteration, s);
   tm.end(ev, s);
   // the forward records, per warp, which list entries its pixels took; the
   // adjoint visits only those
@@ -748,7 +752,7 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
   if (!use_graph || ctx->timer.on) {
     for (int k = 0; k < iters; ++k) {
       rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
-                           grad_pose, s);
+                           grad_pose, k > 0, s);
       if (rc) return rc;
     }
     return DAGS_OK;
@@ -777,7 +781,7 @@ int splat_track(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
       if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
       for (int k = 0; k < reps && rc == DAGS_OK; ++k)
         rc = track_iteration(ctx, gauss, n, cam, pose, targets, &rc_v, &lc_v, &pc_v, adam_state, image, last, loss,
-                             grad_pose, g.cap);
+                             grad_pose, k > 0, g.cap);
       cudaGraph_t graph = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
       if (rc != DAGS_OK || ce != cudaSuccess) {

@@ -170,10 +170,12 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
                               int views, const Raster &r, int zero_grad_words, cudaStream_t s);
 cudaError_t launch_emit(const Workspace &ws, int64_t n, int views, const Raster &r, cudaStream_t s);
 // Projection and binning of one view into fixed-capacity tile buckets
-// (ws.bucket_cap > 0): keys written directly, the render order and the pair
-// requirement by the last CTA (no scan or emit launch).
+// (ws.bucket_cap > 0) over the frame's culled candidates: keys written
+// directly (no scan or emit launch). prefetch: the candidate list was
+// written two or more launches before this one (not by the launch just
+// before it), so the kernel may read it before its pdl_wait.
 cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
-                                     const Raster &r, int zero_grad_words, cudaStream_t s);
+                                     const Raster &r, int zero_grad_words, bool prefetch, cudaStream_t s);
 // The frame's culling: candidates of `pose` into ws.cand_ids / cand_n and
 // the pose into ws.cull_pose (the tracking loop's preprocess uses them while
 // its pose stays within the culling bounds).
@@ -299,6 +301,13 @@ cudaError_t launch_mpnet_features(const float *image, const float4 *targets, con
 // wait returns at once.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Lets the next kernel's CTAs be scheduled before this one completes. Every
+// kernel calls it only after its own pdl_wait, so when a successor starts,
+// the launch before this one has completed: a successor may therefore read,
+// before its own pdl_wait, data written two or more launches earlier (and
+// nothing this kernel writes). Harmless without the launch attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               Args... args) {
@@ -347,12 +356,18 @@ __device__ __forceinline__ double warp_sum_d(double x) {
 // Rotation matrix (row-major) of q / |q|, Hamilton convention, scalar first.
 __device__ __forceinline__ void quat_to_rot(float qw, float qx, float qy, float qz, float *R,
                                             float *n, float *qlen) {
-  float len = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-  float inv = 1.0f / len;
-  float w = qw * inv, x = qx * inv, y = qy * inv, z = qz * inv;
-  R[0] = 1.f - 2.f * (y * y + z * z); R[1] = 2.f * (x * y - w * z);       R[2] = 2.f * (x * z + w * y);
-  R[3] = 2.f * (x * y + w * z);       R[4] = 1.f - 2.f * (x * x + z * z); R[5] = 2.f * (y * z - w * x);
-  R[6] = 2.f * (x * z - w * y);       R[7] = 2.f * (y * z + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+  // every operation explicitly rounded (no contraction left to the
+  // compiler), so that each kernel that inlines this computes the same bits
+  const float len = __fsqrt_rn(__fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmaf_rn(qx, qx, __fmul_rn(qw, qw)))));
+  const float inv = __fdiv_rn(1.0f, len);
+  const float w = __fmul_rn(qw, inv), x = __fmul_rn(qx, inv), y = __fmul_rn(qy, inv), z = __fmul_rn(qz, inv);
+  auto diag = [](float a, float b) { return __fmaf_rn(-2.f, __fmaf_rn(a, a, __fmul_rn(b, b)), 1.f); };
+  auto offd = [](float a, float b, float c, float d, float sg) {
+    return __fmul_rn(2.f, __fmaf_rn(a, b, __fmul_rn(sg * c, d)));
+  };
+  R[0] = diag(y, z);               R[1] = offd(x, y, w, z, -1.f); R[2] = offd(x, z, w, y, 1.f);
+  R[3] = offd(x, y, w, z, 1.f);    R[4] = diag(x, z);             R[5] = offd(y, z, w, x, -1.f);
+  R[6] = offd(x, z, w, y, -1.f);   R[7] = offd(y, z, w, x, 1.f);  R[8] = diag(x, y);
   if (n) { n[0] = w; n[1] = x; n[2] = y; n[3] = z; }
   if (qlen) *qlen = len;
 }
@@ -387,18 +402,20 @@ struct Proj {
 // computed separately.
 __device__ __forceinline__ bool project_gaussian(const float4 &g0, const float4 &g1, const float4 &g2,
                                                  const float *P, const Raster &r, Proj &q) {
-  q.x = P[0] * g0.x + P[1] * g0.y + P[2] * g0.z + P[3];
-  q.y = P[4] * g0.x + P[5] * g0.y + P[6] * g0.z + P[7];
+  // every operation explicitly rounded (no contraction left to the
+  // compiler), so that each kernel that inlines this computes the same bits
+  q.x = __fadd_rn(__fmaf_rn(P[2], g0.z, __fmaf_rn(P[1], g0.y, __fmul_rn(P[0], g0.x))), P[3]);
+  q.y = __fadd_rn(__fmaf_rn(P[6], g0.z, __fmaf_rn(P[5], g0.y, __fmul_rn(P[4], g0.x))), P[7]);
   q.z = depth_key(g0, P);
   if (!(q.z > r.z_near)) return false;
-  q.txz = q.x / q.z;
-  q.tyz = q.y / q.z;
+  q.txz = __fdiv_rn(q.x, q.z);
+  q.tyz = __fdiv_rn(q.y, q.z);
   q.tx = q.txz > r.limx ? r.limx : (q.txz < -r.limx ? -r.limx : q.txz);
   q.ty = q.tyz > r.limy ? r.limy : (q.tyz < -r.limy ? -r.limy : q.tyz);
-  q.j00 = r.fx / q.z;
-  q.j02 = -r.fx * q.tx / q.z;
-  q.j11 = r.fy / q.z;
-  q.j12 = -r.fy * q.ty / q.z;
+  q.j00 = __fdiv_rn(r.fx, q.z);
+  q.j02 = __fdiv_rn(__fmul_rn(-r.fx, q.tx), q.z);
+  q.j11 = __fdiv_rn(r.fy, q.z);
+  q.j12 = __fdiv_rn(__fmul_rn(-r.fy, q.ty), q.z);
   quat_to_rot(g1.x, g1.y, g1.z, g1.w, q.Rq, q.nq, &q.qlen);
   q.S[0] = expf(g2.x);
   q.S[1] = expf(g2.y);
@@ -410,30 +427,35 @@ __device__ __forceinline__ bool project_gaussian(const float4 &g0, const float4 
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int s = 0; s < 3; ++s)
-      q.K[3 * a + s] = (P[4 * a] * q.Rq[s] + P[4 * a + 1] * q.Rq[3 + s] + P[4 * a + 2] * q.Rq[6 + s]) * q.S[s];
+      q.K[3 * a + s] = __fmul_rn(__fmaf_rn(P[4 * a + 2], q.Rq[6 + s],
+                                           __fmaf_rn(P[4 * a + 1], q.Rq[3 + s], __fmul_rn(P[4 * a], q.Rq[s]))),
+                                 q.S[s]);
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    q.m0[s] = q.j00 * q.K[s] + q.j02 * q.K[6 + s];
-    q.m1[s] = q.j11 * q.K[3 + s] + q.j12 * q.K[6 + s];
+    q.m0[s] = __fmaf_rn(q.j02, q.K[6 + s], __fmul_rn(q.j00, q.K[s]));
+    q.m1[s] = __fmaf_rn(q.j12, q.K[6 + s], __fmul_rn(q.j11, q.K[3 + s]));
   }
-  const float A0 = q.m0[0] * q.m0[0] + q.m0[1] * q.m0[1] + q.m0[2] * q.m0[2];
-  const float C0 = q.m1[0] * q.m1[0] + q.m1[1] * q.m1[1] + q.m1[2] * q.m1[2];
-  q.B = q.m0[0] * q.m1[0] + q.m0[1] * q.m1[1] + q.m0[2] * q.m1[2];
-  const float cx0 = q.m0[1] * q.m1[2] - q.m0[2] * q.m1[1];
-  const float cx1 = q.m0[2] * q.m1[0] - q.m0[0] * q.m1[2];
-  const float cx2 = q.m0[0] * q.m1[1] - q.m0[1] * q.m1[0];
+  auto dot3 = [](const float *a, const float *b) {
+    return __fmaf_rn(a[2], b[2], __fmaf_rn(a[1], b[1], __fmul_rn(a[0], b[0])));
+  };
+  const float A0 = dot3(q.m0, q.m0), C0 = dot3(q.m1, q.m1);
+  q.B = dot3(q.m0, q.m1);
+  const float cx0 = __fmaf_rn(q.m0[1], q.m1[2], -__fmul_rn(q.m0[2], q.m1[1]));
+  const float cx1 = __fmaf_rn(q.m0[2], q.m1[0], -__fmul_rn(q.m0[0], q.m1[2]));
+  const float cx2 = __fmaf_rn(q.m0[0], q.m1[1], -__fmul_rn(q.m0[1], q.m1[0]));
   const float d = r.dilation;
-  q.A = A0 + d;
-  q.C = C0 + d;
-  q.det = (cx0 * cx0 + cx1 * cx1 + cx2 * cx2) + d * (A0 + C0) + d * d;
-  q.o = 1.f / (1.f + expf(-g0.w));
+  q.A = __fadd_rn(A0, d);
+  q.C = __fadd_rn(C0, d);
+  const float cc = __fmaf_rn(cx2, cx2, __fmaf_rn(cx1, cx1, __fmul_rn(cx0, cx0)));
+  q.det = __fadd_rn(__fmaf_rn(d, __fadd_rn(A0, C0), cc), __fmul_rn(d, d));
+  q.o = __fdiv_rn(1.f, __fadd_rn(1.f, expf(-g0.w)));
   if (!(q.det > 0.f) || !(q.o > r.alpha_min)) return false;
-  const float idet = 1.f / q.det;
-  q.ca = q.C * idet;
-  q.cb = -q.B * idet;
-  q.cc = q.A * idet;
-  q.u = r.fx * q.x / q.z + r.cx;
-  q.v = r.fy * q.y / q.z + r.cy;
+  const float idet = __fdiv_rn(1.f, q.det);
+  q.ca = __fmul_rn(q.C, idet);
+  q.cb = __fmul_rn(-q.B, idet);
+  q.cc = __fmul_rn(q.A, idet);
+  q.u = __fadd_rn(__fdiv_rn(__fmul_rn(r.fx, q.x), q.z), r.cx);
+  q.v = __fadd_rn(__fdiv_rn(__fmul_rn(r.fy, q.y), q.z), r.cy);
   return true;
 }
 

@@ -36,6 +36,7 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
                   const float *__restrict__ image, const int32_t *__restrict__ last,
                   const float *__restrict__ upstream) {
   pdl_wait();
+  pdl_trigger();
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
   __shared__ float2 s_e[kTilePix];                                  // box half extents
   __shared__ uint32_t s_id[kTilePix];
@@ -236,14 +237,12 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   if (ws.bucket_cap && tid == 0) ws.tile_count[tile] = 0u;
 }
 
-// Chains the 2D gradients of Gaussian i in view v (pose Pm) to the pose
-// twist (pg, added) and, FULL, to the record's parameters (acc, added).
+// Chains the 2D gradients of the Gaussian projected as q in view slot `slot`
+// (pose Pm) to the pose twist (pg, added) and, FULL, to the record's
+// parameters (acc, added).
 template <bool FULL>
-__device__ __forceinline__ void chain_one(const Workspace &ws, const Raster &r, const float4 &g0, const float4 &g1,
-                                          const float4 &g2, const float *Pm, size_t slot, float *pg, float *acc) {
-  const uint2 rc = ws.rect[slot];
-  Proj q;
-  if (!((rc.x >> 16) > (rc.x & 0xFFFF)) || !project_gaussian(g0, g1, g2, Pm, r, q)) return;
+__device__ __forceinline__ void chain_proj(const Workspace &ws, const Raster &r, const Proj &q, const float *Pm,
+                                           size_t slot, float *pg, float *acc) {
   const float *gd = ws.grad2d + slot * kGradWords;
   const float4 ga4 = *reinterpret_cast<const float4 *>(gd);
   const float4 gb4 = *reinterpret_cast<const float4 *>(gd + 4);
@@ -343,6 +342,23 @@ __device__ __forceinline__ void chain_one(const Workspace &ws, const Raster &r, 
   }
 }
 
+// Whether the Gaussian of view slot `slot` has a non-empty tile range, and if
+// so its projection.
+__device__ __forceinline__ bool visible_proj(const Workspace &ws, const Raster &r, const float4 &g0,
+                                             const float4 &g1, const float4 &g2, const float *Pm, size_t slot,
+                                             Proj &q) {
+  const uint2 rc = ws.rect[slot];
+  return (rc.x >> 16) > (rc.x & 0xFFFF) && project_gaussian(g0, g1, g2, Pm, r, q);
+}
+
+// chain_proj of Gaussian (g0, g1, g2) when it is visible.
+template <bool FULL>
+__device__ __forceinline__ void chain_one(const Workspace &ws, const Raster &r, const float4 &g0, const float4 &g1,
+                                          const float4 &g2, const float *Pm, size_t slot, float *pg, float *acc) {
+  Proj q;
+  if (visible_proj(ws, r, g0, g1, g2, Pm, slot, q)) chain_proj<FULL>(ws, r, q, Pm, slot, pg, acc);
+}
+
 // Compensated (double-FP32) addition: (h, l) += (bh, bl) through two-sum,
 // the high words' rounding error carried into the low word.
 __device__ __forceinline__ void cadd(float &h, float &l, float bh, float bl) {
@@ -382,24 +398,51 @@ template <bool FULL>
 __global__ void __launch_bounds__(kBwdPrepBlock)
 preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, int views, Raster r,
                       float *__restrict__ grad_gauss, double *__restrict__ grad_pose, PoseStep ps) {
-  pdl_wait();
   // pose only, tracking loop: the grid's first CTA (dispatched first, so
   // that it runs beside the chain CTAs from the start) ranks the tiles by
   // this iteration's counts for the next iteration's render order; the
   // chain CTAs are numbered from the second
   const bool ordering = !FULL && ws.order_next != nullptr;
   if (ordering && blockIdx.x == 0) {
+    pdl_wait();
+    pdl_trigger();
     rank_tiles(ws.prev_count, r.T, ws.order_next, ws.band);
     return;
   }
   __shared__ float sp[kMaxViewsSmem * 12];
   __shared__ float2 s_red[kBwdPrepBlock / 32][6];
   __shared__ int s_last;
-  for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = ws.pose32[k];
-  __syncthreads();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nb = gridDim.x - (ordering ? 1 : 0);
   const int bid = blockIdx.x - (ordering ? 1 : 0);
+  // pose only, one view: the visible list, the records, their tile ranges
+  // and the FP32 pose were written two or more launches before this one, so
+  // each thread projects its first visible Gaussian before waiting for the
+  // adjoint, whose 2D gradients it reads after the wait
+  Proj q0;
+  bool pre = false, pre_vis = false;
+  int64_t pre_k = 0;
+  size_t pre_slot = 0;
+  if (!FULL && views == 1) {
+    for (int k = tid; k < 12; k += blockDim.x) sp[k] = __ldcg(ws.pose32 + k);
+    __syncthreads();
+    pre = true;
+    pre_k = (int64_t)bid * blockDim.x + tid;
+    if (pre_k < (int64_t)__ldcg(ws.vis_n)) {
+      const int64_t i = __ldcg(ws.vis_ids + pre_k);
+      if (DAGS_IN_BOUNDS(i >= 0 && i < n, ws.counters + CNT_STATUS)) {
+        pre_slot = (size_t)i;
+        const float4 g0 = __ldg(gauss + 4 * i + 0), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
+        pre_vis = visible_proj(ws, r, g0, g1, g2, sp, pre_slot, q0);
+      }
+    }
+  }
+  pdl_wait();
+  pdl_trigger();
+  if (!pre) {
+    for (int k = threadIdx.x; k < views * 12; k += blockDim.x) sp[k] = ws.pose32[k];
+    __syncthreads();
+  }
   if (FULL) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0;
@@ -431,6 +474,10 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
       const int64_t nv = ws.vis_n[v];
       const uint32_t *vis = ws.vis_ids + (size_t)v * ws.max_n;
       for (int64_t k = (int64_t)bid * blockDim.x + tid; k < nv; k += (int64_t)nb * blockDim.x) {
+        if (pre && k == pre_k) {
+          if (pre_vis) chain_proj<false>(ws, r, q0, sp, pre_slot, pg, nullptr);
+          continue;
+        }
         int64_t i = vis[k];
         if (!DAGS_IN_BOUNDS(i >= 0 && i < n, ws.counters + CNT_STATUS)) continue;
         const float4 g0 = __ldg(gauss + 4 * i + 0), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);

@@ -250,17 +250,26 @@ __device__ __forceinline__ void walk_tiles(const Workspace &ws, const Raster &r,
 // zeroed 2D gradient of a visible Gaussian, its visible-list entry and the
 // warp-cooperative walk over its tiles (counting, or emitting into the
 // fixed-capacity buckets). Called by whole warps (ballot, walk).
-template <bool DIRECT>
-__device__ __forceinline__ void preprocess_one(const Workspace &ws, const float4 *__restrict__ gauss, int64_t i,
-                                               bool valid, int v, const float *sp, const float *spl, const Raster &r,
-                                               int zero_words) {
-  float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0, g2 = g0, g3 = g0;
+struct Rec {
+  float4 g0, g1, g2, g3;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4 *__restrict__ gauss, int64_t i, bool valid) {
+  Rec a;
+  a.g0 = a.g1 = a.g2 = a.g3 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (valid) {
-    g0 = __ldg(gauss + 4 * i + 0);
-    g1 = __ldg(gauss + 4 * i + 1);
-    g2 = __ldg(gauss + 4 * i + 2);
-    g3 = __ldg(gauss + 4 * i + 3);
+    a.g0 = __ldg(gauss + 4 * i + 0);
+    a.g1 = __ldg(gauss + 4 * i + 1);
+    a.g2 = __ldg(gauss + 4 * i + 2);
+    a.g3 = __ldg(gauss + 4 * i + 3);
   }
+  return a;
+}
+
+template <bool DIRECT>
+__device__ __forceinline__ void preprocess_one(const Workspace &ws, const Rec &rec, int64_t i, bool valid, int v,
+                                               const float *sp, const float *spl, const Raster &r, int zero_words) {
+  const float4 &g0 = rec.g0, &g1 = rec.g1, &g2 = rec.g2, &g3 = rec.g3;
   uint2 my_rect = make_uint2(0u, 0u);
   float4 my_r0 = make_float4(0.f, 0.f, 0.f, 0.f), my_r1 = my_r0;
   float my_z = 0.f;
@@ -356,7 +365,8 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   __syncthreads();
   if (blockIdx.x == 0 && blockIdx.y == 0)
     for (int k = threadIdx.x; k < views * 12; k += blockDim.x) ws.pose32[k] = sp[k];
-  preprocess_one<false>(ws, gauss, i, i < n, v, sp, spl, r, zero_words);
+  pdl_trigger();
+  preprocess_one<false>(ws, load_rec(gauss, i, i < n), i, i < n, v, sp, spl, r, zero_words);
 }
 
 // Per-frame culling of the tracking loop: the Gaussians that can be visible
@@ -436,13 +446,27 @@ __device__ __forceinline__ bool within_cull_bounds(const float *P, const float *
 
 // The tracking loop's preprocess (one view, fixed-capacity buckets) over
 // the frame's candidates, or over all Gaussians when the pose has left the
-// culling bounds; a fixed grid strides over the list.
-__global__ void __launch_bounds__(kPrepBlock)
+// culling bounds; a fixed grid strides over the list. With prefetch (the
+// candidate list was written two or more launches earlier), each thread
+// loads its first candidate's id and record before waiting for the
+// predecessor (which writes the pose), so that those round trips overlap the
+// predecessor's tail.
+__global__ void __launch_bounds__(kPrepBlock, 6)
 preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
-                       Raster r, int zero_words) {
-  pdl_wait();
+                       Raster r, int zero_words, int prefetch) {
   __shared__ float sp[12], spl[12];
   __shared__ int s_valid;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t pre_count = 0, pre_i = 0;
+  Rec pre;
+  if (prefetch) {
+    pre_count = (int64_t)__ldcg(ws.cand_n);
+    if (first < pre_count) pre_i = (int64_t)__ldcg(ws.cand_ids + first);
+    pre = load_rec(gauss, pre_i, first < pre_count && pre_i < n);
+  }
+  // (no early trigger: the forward's longest-first CTAs are placed once
+  // this grid has left the SMs)
+  pdl_wait();
   stage_poses(pose, 1, sp, spl);
   __syncthreads();
   if (threadIdx.x == 0) s_valid = within_cull_bounds(sp, ws.cull_pose) ? 1 : 0;
@@ -457,8 +481,12 @@ preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
     const int64_t k = base + threadIdx.x;
     const bool valid = k < count;
+    if (prefetch && use_cand && k == first) {
+      preprocess_one<true>(ws, pre, pre_i, valid && pre_i < n, 0, sp, spl, r, zero_words);
+      continue;
+    }
     const int64_t i = !valid ? 0 : (use_cand ? (int64_t)ws.cand_ids[k] : k);
-    preprocess_one<true>(ws, gauss, i, valid && i < n, 0, sp, spl, r, zero_words);
+    preprocess_one<true>(ws, load_rec(gauss, i, valid && i < n), i, valid && i < n, 0, sp, spl, r, zero_words);
   }
 }
 
@@ -524,9 +552,11 @@ emit_kernel(Workspace ws, int64_t n, Raster r) {
 // MASKS: record per warp the list entries its pixels took (ws.warp_masks,
 // the tracking loop); COUNT: count evaluations and contributions (ws.evals).
 template <bool MASKS, bool COUNT>
-__global__ void __launch_bounds__(kTilePix, MASKS ? 5 : 6)
+__global__ void __launch_bounds__(kTilePix, 5)
 render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__restrict__ targets,
                   float *__restrict__ image, int32_t *__restrict__ last, double *__restrict__ loss) {
+  // (no early trigger: the adjoint's CTAs are placed on the SMs as they
+  // empty, which keeps its longest-first launch order spread over the SMs)
   pdl_wait();
   __shared__ uint64_t s_key[kSortSmallCap];
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
@@ -616,21 +646,24 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
         // or whose alpha is below alpha_min, or that would stop here adds
         // a zero weight and keeps T (x + 0 * c == x), so each pixel's sums
         // are those of the branching form, operation for operation
+        // (explicitly rounded operations: every kernel variant computes the
+        // same bits)
         const float4 a = s_a[j], b = s_b[j];
-        const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
-        const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+        const float dx = __fadd_rn(__fsub_rn(a.x, fpx), a.z), dy = __fadd_rn(__fsub_rn(a.y, fpy), a.w);
+        const float p = __fmaf_rn(__fmul_rn(b.x, dx), dx,
+                                  __fmaf_rn(__fmul_rn(b.y, dx), dy, __fmaf_rn(__fmul_rn(b.z, dy), dy, b.w)));
         const bool live = !done && p >= r.log2_alpha_min;   // else alpha < alpha_min
         const float alpha = fminf(r.alpha_max, hw_exp2(p));
-        const float tt = T * (1.f - alpha);
+        const float tt = __fmul_rn(T, __fsub_rn(1.f, alpha));
         const bool stop = live && tt < r.t_min;
         const bool contrib = live && !stop;
         if (COUNT) { n_eval += done ? 0u : 1u; n_contrib += contrib ? 1u : 0u; }
         done = done || stop;
-        const float w = contrib ? alpha * T : 0.f;
+        const float w = contrib ? __fmul_rn(alpha, T) : 0.f;
         const float4 c = s_c[j];
         const uint32_t rg = __float_as_uint(c.z), bl = __float_as_uint(c.w);
-        cr += bf16_lo(rg) * w; cg += bf16_hi(rg) * w; cb += bf16_lo(bl) * w;
-        dd += c.x * w; oo += w; rm += c.y * w;
+        cr = __fmaf_rn(bf16_lo(rg), w, cr); cg = __fmaf_rn(bf16_hi(rg), w, cg); cb = __fmaf_rn(bf16_lo(bl), w, cb);
+        dd = __fmaf_rn(c.x, w, dd); oo = __fadd_rn(oo, w); rm = __fmaf_rn(c.y, w, rm);
         T = contrib ? tt : T;
         lastk = contrib ? (int)(base - s) + j + 1 : lastk;
         if (MASKS && __any_sync(FULL, contrib)) took |= 1u << bit;
@@ -655,7 +688,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
       const float4 tg = targets[(size_t)v * P + pix];
       const float l1 = fabsf(cr - tg.x) + fabsf(cg - tg.y) + fabsf(cb - tg.z);
       const float ld = tg.w > 0.f ? fabsf(dd - tg.w) : 0.f;
-      lpx = tg.x >= 0.f ? wgt * (l.lambda_pho * l1 + l.lambda_depth * ld) : 0.f;
+      lpx = tg.x >= 0.f ? __fmul_rn(wgt, __fmaf_rn(l.lambda_pho, l1, __fmul_rn(l.lambda_depth, ld))) : 0.f;
     }
     float *img = image + (size_t)v * DAGS_IMG_CHANNELS * P + pix;
     img[0 * P] = cr; img[1 * P] = cg; img[2 * P] = cb; img[3 * P] = dd;
@@ -726,13 +759,14 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
 }
 
 cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
-                                     const Raster &r, int zero_grad_words, cudaStream_t s) {
+                                     const Raster &r, int zero_grad_words, bool prefetch, cudaStream_t s) {
   if (ws.bucket_cap == 0 || !ws.cand_ids) return cudaErrorInvalidValue;
-  // the frame's culled list: a fixed grid strides over it
+  // the frame's culled list: a fixed grid of one wave (6 CTAs per SM, the
+  // register budget with the prefetched record) strides over it
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
-  const unsigned g = gx < (unsigned)(8 * ws.band) ? (gx > 0 ? gx : 1u) : (unsigned)(8 * ws.band);
+  const unsigned g = gx < (unsigned)(6 * ws.band) ? (gx > 0 ? gx : 1u) : (unsigned)(6 * ws.band);
   return launch_pdl(preprocess_cull_kernel, dim3(g), dim3(kPrepBlock), 0, s, ws, gauss, n, pose, r,
-                    zero_grad_words);
+                    zero_grad_words, prefetch ? 1 : 0);
 }
 
 cudaError_t launch_order_identity(uint32_t *order, int tiles, cudaStream_t s) {
