@@ -273,14 +273,27 @@ SFU_FWD_CONTRIB, SFU_BWD_CONTRIB = 1, 2
 # tangent 2, four channel accumulations 5, T' 1) over six directions
 OPS_JAC = 16 + 10 + 6 * 14
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+# the tracking iteration's kernels as the traffic file names them
+TRAFFIC_NAMES = {"preprocess": "preprocess_cull_kernel", "render_fwd": "render_fwd_kernel",
+                 "render_bwd": "render_bwd_kernel<pose-only>", "preprocess_bwd": "preprocess_bwd_kernel<pose-only>"}
+
+
+def source_digest(paths: str) -> str:
+    """SHA-256 (first 16 hex digits) of the concatenated bytes of the
+    '+'-separated source files (paths relative to the repository root)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths.split("+"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def committed_traffic(kernel: str, workload: str):
     """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
-    committed ncu summary, or (None, why) when there is no capture or the
-    kernel's source file has changed since it was taken (the file records the
-    source's SHA-256)."""
-    import hashlib
+    committed ncu summary, or (None, why) when there is no capture or one of
+    the kernel's source files has changed since it was taken (the file
+    records the SHA-256 of the sources the kernel compiles from)."""
     if not os.path.exists(TRAFFIC_FILE):
         return None, "no committed capture"
     for line in open(TRAFFIC_FILE):
@@ -289,13 +302,13 @@ def committed_traffic(kernel: str, workload: str):
         f = [x.strip() for x in line.split("|")]
         if len(f) < 5 or f[0] != kernel or f[1] != workload:
             continue
-        src = os.path.join(ROOT, f[3])
-        if not os.path.exists(src):
-            return None, f"source {f[3]} missing"
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        missing = [rel for rel in f[3].split("+") if not os.path.exists(os.path.join(ROOT, rel))]
+        if missing:
+            return None, f"source {missing[0]} missing"
+        sha = source_digest(f[3])
         if sha != f[4]:
             return None, f"{f[3]} changed since the capture"
-        return int(f[2]), f"ncu capture of this source ({f[3]} sha256 {sha})"
+        return int(f[2]), f"ncu capture of this source ({f[3]} sha256 {sha}; cold caches)"
     return None, "no committed capture of this kernel and workload"
 
 
@@ -884,6 +897,9 @@ def run_ours(args):
             if name in ab:
                 kernels[name]["alg_bytes"] = ab[name]
                 kernels[name]["hbm_frac"] = round(ab[name] / (avg_us * 1e-6) / 1e9 / hbm, 4)
+                tr, _ = committed_traffic(TRAFFIC_NAMES.get(name, name), f"tracking {args.gaussians // 1000}k "
+                                                                        f"{args.width}x{args.height}")
+                kernels[name]["dram_bytes"] = tr
     # the compositing kernels are ALU-bound: per launch, E_eval evaluated
     # exponents and E_contrib contributions (counted by the kernels), OPS_*
     # FP32 lane operations per unit, against the measured FMA lane rate;
@@ -911,8 +927,7 @@ def run_ours(args):
     workload = f"tracking {args.gaussians // 1000}k {args.width}x{args.height}"
     if dom in ("render_fwd", "render_bwd"):
         ach = kernels[dom]["alu_tops"]
-        traffic, tnote = committed_traffic({"render_fwd": "render_fwd_kernel",
-                                            "render_bwd": "render_bwd_kernel<pose-only>"}[dom], workload)
+        traffic, tnote = committed_traffic(TRAFFIC_NAMES[dom], workload)
         ee, ec, oc, _ = per[dom]
         roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                 "frac": round(ach / alu_peak, 4), "traffic": traffic, "traffic_source": tnote,

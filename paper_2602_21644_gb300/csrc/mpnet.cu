@@ -213,7 +213,12 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
                  uint32_t *__restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3, *sB2 = smem + kFB2, *sB3 = smem + kFB3;
+  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3;
+  // FP32 copies: b2, b3 (added in the epilogues), b1 as its BF16 (hi, lo)
+  // pair and W1, for the two halo pixels computed on the CUDA cores
+  float *sb2f = reinterpret_cast<float *>(smem + kFB2), *sb3f = sb2f + kCh, *sb1h = sb2f + 2 * kCh,
+        *sb1l = sb2f + 3 * kCh;
+  float *sw1f = reinterpret_cast<float *>(smem + kFB3);   // [32][8]
   float *sw4 = reinterpret_cast<float *>(smem + kFPar), *sb4 = sw4 + kCh;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);   // [g]: in0, in1, mma
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 128);
@@ -240,12 +245,15 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     *reinterpret_cast<uint16_t *>(sW2 + core_off(e / kK2, e % kK2, kK2)) = gw2[e];
   for (int e = tid; e < 32 * 32; e += kFwdThreads)
     *reinterpret_cast<uint16_t *>(sW3 + core_off(e / 32, e % 32, 32)) = gw3[e];
-  for (int e = tid; e < 2 * 32 * 16; e += kFwdThreads) {
-    const int which = e / 512, o = (e / 16) % 32, k = e % 16;
-    const float bias = which ? gb3[o] : gb2[o], hi = __bfloat162float(__float2bfloat16_rn(bias));
-    const uint16_t v = k == 0 ? bf16_bits(bias) : k == 1 ? bf16_bits(bias - hi) : (uint16_t)0;
-    *reinterpret_cast<uint16_t *>((which ? sB3 : sB2) + core_off(o, k, 16)) = v;
+  for (int e = tid; e < kCh; e += kFwdThreads) {
+    sb2f[e] = gb2[e];
+    sb3f[e] = gb3[e];
+    const float hi = __bfloat162float(__float2bfloat16_rn(gb1[e]));
+    sb1h[e] = hi;
+    sb1l[e] = __bfloat162float(__float2bfloat16_rn(gb1[e] - hi));
   }
+  for (int e = tid; e < kCh * 8; e += kFwdThreads)
+    sw1f[e] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(gw1)[(e / 8) * 16 + e % 8]);
   if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
   // the whole warpgroup area starts at zero (don't-care rows stay finite);
   // then the bias constants (1, 1, 0, ..., 0) of every row
@@ -321,9 +329,10 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         if (ok) {
           tc_after_sync();
           if (d1) {
+            // halo pixels 0..127 of the row (the last two are computed on the
+            // CUDA cores in the epilogue)
             const uint32_t in = wg_u32 + (q & 1u) * kInBuf, lbo = ones - in;
             mma_bf16(tmem + 0, sdesc(in, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
-            mma_bf16(tmem + 32, sdesc(in + 2048, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
           }
           if (d2) {
             const int j = k - 3;   // output row y0 + j from a1 rows j .. j + 2 of this unit
@@ -337,7 +346,6 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
                          sdesc(smem_u32(sW2) + (2 * tap + h) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
                          (tap | h) ? 1u : 0u);
             }
-            mma_bf16(tmem + 64, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256), idesc_bf16(128, 32), 1u);
           }
           if (d3) {
             const uint32_t a2 = smem_u32(sA2);
@@ -345,7 +353,6 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
             for (int h = 0; h < 2; ++h)
               mma_bf16(tmem + 96, sdesc(a2 + 2 * h * (kTileW * 16), kTileW * 16, 128),
                        sdesc(smem_u32(sW3) + h * 256, 128, 512), idesc_bf16(128, 32), h ? 1u : 0u);
-            mma_bf16(tmem + 96, sdesc(ones, 2048, 128), sdesc(smem_u32(sB3), 128, 256), idesc_bf16(128, 32), 1u);
           }
           mma_commit(bar_mma);
           in_flight |= 4u;
@@ -358,40 +365,49 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
       }
       ph_mma ^= 1u;
       tc_after_sync();
-      // the input buffer of a1 row k is free: fetch a1 row k + 2 (of this
-      // unit, else of the next)
-      if (t == 0 && ok && d1) {
-        if (k + 2 < nA) fetch(q + 2, x0, y0 + k + 1, b);
-        else if (has_next) fetch(q + 2, nx0, ny0 - 1 + (k + 2 - nA), nb);
-      }
       const int p = 32 * warp + lane;
-      // epilogue 1: a1 row r = y0 - 1 + k (zero outside the image) -> slot
+      // epilogue 1: a1 row r = y0 - 1 + k (zero outside the image) -> slot;
+      // slot pixel i <-> x = x0 - 1 + i
       if (d1) {
         const int r = y0 - 1 + k;
         const bool row_in = r >= 0 && r < H, own_row = r >= y0 && r < y1;
         uint8_t *slot = sRing + (k % kSlots) * kSlotBytes;
-#pragma unroll 1
-        for (int mb = 0; mb < 2; ++mb) {
-          if (mb == 1 && warp != 0) break;
+        {
           float z[32];
-          tmem_ld32(tmem + lane_base + mb * 32, z);
-          const int i = mb * 128 + p;   // slot pixel i <-> x = x0 - 1 + i
-          if (i < kHaloW) {
-            const int xx = x0 - 1 + i;
-            const bool in = row_in && xx >= 0 && xx < W;
-            uint32_t w[16];
+          tmem_ld32(tmem + lane_base, z);
+          const int i = p, xx = x0 - 1 + i;
+          const bool in = row_in && xx >= 0 && xx < W;
+          uint32_t w[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) w[e] = in ? relu_bf16x2(z[2 * e], z[2 * e + 1]) : 0u;
+          for (int e = 0; e < 16; ++e) w[e] = in ? relu_bf16x2(z[2 * e], z[2 * e + 1]) : 0u;
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-              *reinterpret_cast<uint4 *>(slot + c * kSlotChunk + i * 16) =
-                  make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-            if (acts && own_row && i >= 1 && i <= kTileW && xx < W) {
-              uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(slot + c * kSlotChunk + i * 16) =
+                make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+          if (acts && own_row && i >= 1 && xx < W) {
+            uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
 #pragma unroll
-              for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-            }
+            for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
           }
+        }
+        // halo pixels i = 128 (warp 1) and 129 (warp 2): lane = output
+        // channel, z1 = W1 x + hi + lo in FP32 from the row's input buffer
+        // (the next fetch into it is issued after this step's barrier)
+        if (warp == 1 || warp == 2) {
+          const int i = kTileW - 1 + warp, xx = x0 - 1 + i, c = lane;
+          const bool in = row_in && xx >= 0 && xx < W;
+          const uint4 xv = *reinterpret_cast<const uint4 *>(wg + (q & 1u) * kInBuf + i * 16);
+          const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+          float zc = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            const uint32_t bits = (kk & 1) ? (xw[kk >> 1] & 0xFFFF0000u) : (xw[kk >> 1] << 16);
+            zc = fmaf(__uint_as_float(bits), sw1f[c * 8 + kk], zc);
+          }
+          zc = (zc + sb1h[c]) + sb1l[c];
+          const uint16_t a = in ? bf16_bits(fmaxf(zc, 0.f)) : (uint16_t)0;
+          *reinterpret_cast<uint16_t *>(slot + (c >> 3) * kSlotChunk + i * 16 + (c & 7) * 2) = a;
+          if (acts && own_row && i <= kTileW && xx < W) acts[(((size_t)b * H + r) * W + xx) * 96 + c] = a;
         }
       }
       // epilogue 2: a2 of output row y0 + k - 3 -> a2 buffer
@@ -401,7 +417,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         tmem_ld32(tmem + lane_base + 64, z);
         uint32_t w[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e], z[2 * e + 1]);
+        for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e] + sb2f[2 * e], z[2 * e + 1] + sb2f[2 * e + 1]);
         uint8_t *a2 = sA2;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -423,7 +439,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         uint32_t w[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          w[e] = relu_bf16x2(z[2 * e], z[2 * e + 1]);
+          w[e] = relu_bf16x2(z[2 * e] + sb3f[2 * e], z[2 * e + 1] + sb3f[2 * e + 1]);
           acc += __uint_as_float(w[e] << 16) * sw4[2 * e] + __uint_as_float(w[e] & 0xFFFF0000u) * sw4[2 * e + 1];
         }
         if (x0 + p < W) {
@@ -439,6 +455,12 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
       fence_async_smem();
       tc_before_sync();
       wg_sync(g);   // slots, a2 and all D columns consumed before the next step's MMAs
+      // the input buffer of a1 row k is free: fetch a1 row k + 2 (of this
+      // unit, else of the next)
+      if (t == 0 && ok && d1) {
+        if (k + 2 < nA) fetch(q + 2, x0, y0 + k + 1, b);
+        else if (has_next) fetch(q + 2, nx0, ny0 - 1 + (k + 2 - nA), nb);
+      }
     }
     qbase += (uint32_t)nA;
     if (!ok) s_fail[g] = 1u;
