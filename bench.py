@@ -972,6 +972,18 @@ def run_ours(args):
     learned["roofline"] = {"bound": "tensor", "achieved": learned["infer_tflops"], "peak": bf16, "unit": "TFLOP/s",
                            "frac": round(learned["infer_tflops"] / bf16, 4),
                            "peak_source": f"{src} bf16_tflops (burst: the launch is timed alone)"}
+    # the tensor core's rate by MMA width (the network's layers are 32
+    # channels wide: its MMAs are M = 128 pixels x N = 32 x K = 16), measured
+    # on this device by the library's probe
+    rates = {}
+    for n_cols, groups in ((32, 4), (64, 4), (128, 4), (256, 2)):
+        rates[n_cols] = max(dags.measure_mma(n_cols, groups, 512)[0] for _ in range(2))
+    top = max(rates.values())
+    learned["roofline"]["mma_rate_by_n"] = {
+        "mac_per_sm_cycle": {str(k): round(v, 1) for k, v in rates.items()},
+        "n32_frac_of_best": round(rates[32] / top, 4),
+        "frac_of_n32_ceiling": round(learned["roofline"]["frac"] / (rates[32] / top), 4),
+        "how": "dags_measure_mma: one CTA, back-to-back BF16 MMAs (M 128, K 16) from 4 warpgroups (2 at N 256)"}
     line["learned_mp"] = learned
     line["splat_variants"] = variants
     line["lm_tracking"] = lm

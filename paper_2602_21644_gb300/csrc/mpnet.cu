@@ -9,8 +9,9 @@
 // b3, a3 = bf16(relu); y = sigmoid(w4 . a3 + b4).
 //
 // mpnet_fwd_kernel   inference (and the training forward): four warpgroups
-//                    per CTA walk 128-pixel column strips row by row in a
-//                    three-stage software pipeline (see its comment).
+//                    per CTA (four epilogue warps and one MMA-issuing
+//                    control warp each) walk 128-pixel column strips row by
+//                    row in a software pipeline (see its comment).
 // mpnet_bwd1_kernel  training: BCE gradient, dz3, da2 = dz3 W3 and dz2; the
 //                    weight gradients dW3, dw4 accumulated in TMEM.
 // mpnet_bwd2_kernel  training: da1 by the transposed 3x3 convolution, dz1;
@@ -131,8 +132,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 
 
 // Forward kernel: kGroups warpgroups per CTA, each running its own stream
-// of work units with its own operands, TMEM columns and mbarriers, so that
-// one warpgroup's epilogues overlap the others' MMAs.
+// of work units with its own operands, TMEM columns and mbarriers. A
+// warpgroup is four epilogue warps (TMEM lane quadrants 0..3: 128 pixels)
+// and one control warp whose lane 0 issues the MMAs and the TMA fetches, so
+// that the tensor core runs one step's MMAs while the epilogue warps convert
+// the previous results.
 //
 // Work unit: a 128-pixel-wide column strip of one image over a segment of
 // output rows [y0, y1). The warpgroup walks down the strip computing a1 for
@@ -140,14 +144,21 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // into a ring of row slots; every a1 row is computed once per unit (plus two
 // boundary rows), not three times as with independent row tiles.
 //
-// Software pipeline: step k issues, under one commit, z1 of a1 row k, z2 of
-// output row k - 3 (its a1 rows k - 3 .. k - 1 were written by earlier
-// steps) and z3 of output row k - 4 (its a2 by the previous step), then runs
-// the three epilogues. One MMA round trip per output row. The epilogues run
-// after the step's wait, when every MMA that read their target buffers has
-// completed, so three ring slots and one a2 buffer suffice; the input of a1
-// row k + 2 is fetched by TMA (two input buffers) while step k + 1 runs, and
-// out-of-image rows and columns read as zero.
+// Pipeline, step k (the control warp / the epilogue warps):
+//   control: wait for the previous step's epilogues (D1 and D3 read, a2
+//     written); batch 1 = z1 of a1 row k (halo pixels 0..127) and z3 of
+//     output row k - 4, one commit (which also covers the previous step's
+//     z2); wait for epilogue 1; fetch the input of a1 row k + 2 by TMA into
+//     the buffer row k used; batch 2 = z2 of output row k - 2 (a1 rows
+//     k - 2 .. k) into the D2 buffer of this step's parity.
+//   epilogues: wait for the commit; epilogue 1 (a1 row k into its slot; the
+//     halo pixels 128 and 129 on the CUDA cores); epilogue 2 (a2 of output
+//     row k - 3 from the other D2 buffer); epilogue 3 (a3, the dot product
+//     with w4 and the sigmoid of output row k - 4).
+// Batch 2 runs on the tensor core while the epilogue warps run epilogues 2
+// and 3. Three ring slots, one a2 buffer and two D2 buffers suffice: every
+// buffer is rewritten only after the barrier that follows its last reader.
+// Out-of-image rows and columns read as zero.
 //
 // Operand layouts (no swizzle): "row-contiguous chunks" - chunk c holds
 // channels 8c..8c+7 of every row as one 16-byte line, rows consecutive (SBO =
@@ -155,13 +166,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // at any row, which makes the 3 x 3 convolution an implicit GEMM: tap (ky, kx)
 // reads the slot of a1 row y - 1 + ky at rows kx + p directly, no im2col.
 //
-// Biases ride in the MMAs: a K-chunk of per-row constants (1, 1, 0, ..., 0)
-// meets a B column pair (hi, lo) with hi = bf16(b), lo = bf16(b - hi), so
-// that z = W a + hi + lo accumulates in FP32 in the tensor core (|hi + lo -
-// b| <= 2^-17 |b|); the epilogues are then ReLU + BF16 rounding in one
-// conversion per pair.
+// The first layer's bias rides in its MMA: a K-chunk of per-row constants
+// (1, 1, 0, ..., 0) meets a B column pair (hi, lo) with hi = bf16(b1), lo =
+// bf16(b1 - hi) (|hi + lo - b1| <= 2^-17 |b1|). The second and third layers'
+// biases are added in FP32 in the epilogues, before the ReLU + BF16 rounding
+// (one conversion per pair).
 constexpr int kGroups = 4;
-constexpr int kFwdThreads = 128 * kGroups;
+constexpr int kFwdThreads = 160 * kGroups;              // 4 epilogue warps + 1 control warp per warpgroup
+constexpr int kBars = 6;                                // mbarriers per warpgroup
 constexpr int kRowBytes = kHaloW * 16;                  // 2080 = the TMA box (8 x 130 x 1 x 1 bf16)
 constexpr int kInBuf = 2176;                            // one input row (+ pad)
 constexpr int kSlotRows = 136;
@@ -169,10 +181,10 @@ constexpr int kSlotChunk = kSlotRows * 16;              // 2176
 constexpr int kSlotBytes = 4 * kSlotChunk;              // 8704
 constexpr int kSlots = 3;
 constexpr int kA2Bytes = 4 * kTileW * 16;               // 8192
-// per warpgroup: in0, in1, ones (256 rows of (1, 1, 0, ...)), ring, a2 x 2.
-// An L1 MMA reads 256 rows from an input buffer; rows past 129 are
-// don't-care rows (they land in D rows that are never read).
-constexpr int kWgIn0 = 0, kWgIn1 = kInBuf, kWgOnes = 2 * kInBuf, kWgRing = kWgOnes + 4096;
+// per warpgroup: in0, in1 (one input row each, at 0 and kInBuf), ones (the
+// first layer's bias chunk: 256 rows of (1, 1, 0, ...), of which an L1 MMA
+// reads 128), ring, a2.
+constexpr int kWgOnes = 2 * kInBuf, kWgRing = kWgOnes + 4096;
 constexpr int kWgA2 = kWgRing + kSlots * kSlotBytes;
 constexpr int kWgBytes = kWgA2 + kA2Bytes;              // 42752
 constexpr int kFW1 = kGroups * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFB2 = kFW3 + 2048,
@@ -181,7 +193,9 @@ constexpr int kFBar = kFPar + 256;
 constexpr int kFwdSmem = kFBar + 256 + 1024;            // + alignment slack
 constexpr uint32_t kWgCols = 128;                       // D1 +0..63, D2 +64..95, D3 +96..127
 
-__device__ __forceinline__ void wg_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 
 // BF16 pair (lo, hi) of relu(lo), relu(hi), round to nearest even.
 __device__ __forceinline__ uint32_t relu_bf16x2(float lo, float hi) {
@@ -220,13 +234,20 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         *sb1l = sb2f + 3 * kCh;
   float *sw1f = reinterpret_cast<float *>(smem + kFB3);   // [32][8]
   float *sw4 = reinterpret_cast<float *>(smem + kFPar), *sb4 = sw4 + kCh;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);   // [g]: in0, in1, mma
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 128);
-  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 136);
-  const int tid = threadIdx.x, g = tid >> 7, t = tid & 127, warp = t >> 5, lane = tid & 31;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 8 * kBars * kGroups);
+  volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 8 * kBars * kGroups + 8);
+  // threads 0..511: four warpgroups of epilogue warps (warp w reads TMEM
+  // lane quadrant w % 4); threads 512..639: one control warp per warpgroup
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool ctl = tid >= 4 * kGroups * 32;
+  const int g = ctl ? (tid - 4 * kGroups * 32) >> 5 : tid >> 7, t = tid & 127, warp = t >> 5;
   uint8_t *wg = smem + g * kWgBytes;
   uint8_t *sRing = wg + kWgRing, *sA2 = wg + kWgA2;
-  uint64_t *bar_in = bars + 3 * g, *bar_mma = bars + 3 * g + 2;
+  // per warpgroup: in0, in1 (TMA), mma (commits), e1 (epilogue 1 done),
+  // ep (all epilogues done), mma2 (the final drain)
+  uint64_t *bar_in = bars + kBars * g, *bar_mma = bar_in + 2, *bar_e1 = bar_in + 3, *bar_ep = bar_in + 4,
+           *bar_mma2 = bar_in + 5;
 
   // weights into the K-major core-matrix layouts; bias columns (hi, lo)
   const uint16_t *gw1 = reinterpret_cast<const uint16_t *>(weights + kOffW1);
@@ -257,14 +278,18 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   if (tid < kCh) sw4[tid] = __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(weights + kOffW4)[tid]);
   // the whole warpgroup area starts at zero (don't-care rows stay finite);
   // then the bias constants (1, 1, 0, ..., 0) of every row
-  for (int e = t; e < kWgBytes / 16; e += 128) {
-    const bool one = e >= kWgOnes / 16 && e < kWgOnes / 16 + 256;   // one writer per line
-    *reinterpret_cast<uint4 *>(wg + 16 * e) = make_uint4(one ? 0x3F803F80u : 0u, 0u, 0u, 0u);
-  }
+  if (!ctl)
+    for (int e = t; e < kWgBytes / 16; e += 128) {
+      const bool one = e >= kWgOnes / 16 && e < kWgOnes / 16 + 256;   // one writer per line
+      *reinterpret_cast<uint4 *>(wg + 16 * e) = make_uint4(one ? 0x3F803F80u : 0u, 0u, 0u, 0u);
+    }
   if (tid == 0) {
     sb4[0] = reinterpret_cast<const float *>(weights + kOffB4)[0];
-    for (int k = 0; k < 3 * kGroups; ++k)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bars + k)));
+    for (int k = 0; k < kBars * kGroups; ++k) {
+      const int kind = k % kBars;   // e1 and ep: one arrival per epilogue warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + k)),
+                   "r"(kind == 3 || kind == 4 ? 4 : 1));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int k = 0; k < kGroups; ++k) s_fail[k] = 0u;
   }
@@ -278,16 +303,8 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   __syncthreads();
   tc_after_sync();
   const uint32_t tmem = *s_tmem + kWgCols * (uint32_t)g;
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
   const uint32_t wg_u32 = smem_u32(wg);
   const uint32_t ones = wg_u32 + kWgOnes;
-  uint32_t ph_mma = 0;
-  uint32_t qbase = 0;          // a1 rows of the earlier units (input buffer parity)
-  bool ok = true;
-  // thread 0: bit 0/1 = TMA into in0/in1 pending (bit 8/9 = the parity of
-  // that fetch's phase), bit 2 = MMA pending
-  uint32_t in_flight = 0;
-
   const long long stride = (long long)kGroups * gridDim.x;
   // unit u -> image b, strip x0, rows [y0, y1)
   auto unit = [&](long long u, int *b, int *x0, int *y0, int *y1) {
@@ -298,54 +315,51 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     *y0 = seg * units.seg_rows;
     *y1 = min(*y0 + units.seg_rows, H);
   };
-  auto fetch = [&](uint32_t q, int x0, int r, int b) {   // input of the q-th a1 row of this warpgroup
-    const uint32_t buf = q & 1u;
-    tma_row(&in_map, wg_u32 + buf * kInBuf, bar_in + buf, x0 - 1, r, b);
-    in_flight = (in_flight & ~(0x101u << buf)) | (1u << buf) | (((q >> 1) & 1u) << (8 + buf));
-  };
-  long long u = (long long)kGroups * blockIdx.x + g;
-  if (u < units.count && t == 0) {
-    int b, x0, y0, y1;
-    unit(u, &b, &x0, &y0, &y1);
-    fetch(0, x0, y0 - 1, b);
-    fetch(1, x0, y0, b);
-  }
-  for (; u < units.count; u += stride) {
-    int b, x0, y0, y1;
-    unit(u, &b, &x0, &y0, &y1);
-    const int nO = y1 - y0, nA = nO + 2;   // output rows; a1 rows y0 - 1 .. y1
-    int nb = 0, nx0 = 0, ny0 = 0, ny1 = 0;
-    const bool has_next = u + stride < units.count;
-    if (has_next) unit(u + stride, &nb, &nx0, &ny0, &ny1);
-    for (int k = 0; k < nA + 2; ++k) {
-      const bool d1 = k < nA, d2 = k >= 3 && k < nO + 3, d3 = k >= 4;
-      const uint32_t q = qbase + (uint32_t)k;
-      // MMAs of this step under one commit
-      if (t == 0) {
-        if (d1 && ok) {
-          ok = bar_wait(bar_in + (q & 1u), (q >> 1) & 1u);
-          if (ok) in_flight &= ~(1u << (q & 1u));
-        }
-        if (ok) {
+  uint32_t qbase = 0;          // a1 rows of the earlier units (input buffer parity)
+  uint32_t sc = 0;             // steps of the earlier units (barrier phases)
+  if (ctl) {
+    // ------------------------------------------------------------ control
+    if (lane == 0) {
+      // bit 0/1 = TMA into in0/in1 pending (bit 8/9 = the parity of that
+      // fetch's phase), bit 2 = MMAs issued since the last waited commit
+      uint32_t in_flight = 0;
+      bool ok = true;
+      auto fetch = [&](uint32_t q, int x0, int r, int b) {   // input of the q-th a1 row of this warpgroup
+        const uint32_t buf = q & 1u;
+        tma_row(&in_map, wg_u32 + buf * kInBuf, bar_in + buf, x0 - 1, r, b);
+        in_flight = (in_flight & ~(0x101u << buf)) | (1u << buf) | (((q >> 1) & 1u) << (8 + buf));
+      };
+      long long u = (long long)kGroups * blockIdx.x + g;
+      if (u < units.count) {
+        int b, x0, y0, y1;
+        unit(u, &b, &x0, &y0, &y1);
+        fetch(0, x0, y0 - 1, b);
+        fetch(1, x0, y0, b);
+      }
+      for (; u < units.count && ok; u += stride) {
+        int b, x0, y0, y1;
+        unit(u, &b, &x0, &y0, &y1);
+        const int nO = y1 - y0, nA = nO + 2;
+        int nb = 0, nx0 = 0, ny0 = 0, ny1 = 0;
+        const bool has_next = u + stride < units.count;
+        if (has_next) unit(u + stride, &nb, &nx0, &ny0, &ny1);
+        for (int k = 0; k < nA + 2; ++k, ++sc) {
+          const bool d1 = k < nA, d2i = k >= 2 && k < nO + 2, d3 = k >= 4;
+          const uint32_t q = qbase + (uint32_t)k;
+          if (s_fail[g]) { ok = false; break; }
+          // the previous step's epilogues have read D1 and D3 and written a2
+          if (sc > 0) ok = bar_wait(bar_ep, (sc - 1) & 1u);
+          if (ok && d1) {
+            ok = bar_wait(bar_in + (q & 1u), (q >> 1) & 1u);
+            if (ok) in_flight &= ~(1u << (q & 1u));
+          }
+          if (!ok) break;
           tc_after_sync();
+          // batch 1: z1 of a1 row k (halo pixels 0..127; the last two on the
+          // CUDA cores), z3 of output row k - 4
           if (d1) {
-            // halo pixels 0..127 of the row (the last two are computed on the
-            // CUDA cores in the epilogue)
             const uint32_t in = wg_u32 + (q & 1u) * kInBuf, lbo = ones - in;
             mma_bf16(tmem + 0, sdesc(in, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
-          }
-          if (d2) {
-            const int j = k - 3;   // output row y0 + j from a1 rows j .. j + 2 of this unit
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-              const int ky = tap / 3, kx = tap % 3;
-              const uint32_t sl = smem_u32(sRing) + ((j + ky) % kSlots) * kSlotBytes;
-#pragma unroll
-              for (int h = 0; h < 2; ++h)
-                mma_bf16(tmem + 64, sdesc(sl + 2 * h * kSlotChunk + kx * 16, kSlotChunk, 128),
-                         sdesc(smem_u32(sW2) + (2 * tap + h) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
-                         (tap | h) ? 1u : 0u);
-            }
           }
           if (d3) {
             const uint32_t a2 = smem_u32(sA2);
@@ -354,130 +368,171 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
               mma_bf16(tmem + 96, sdesc(a2 + 2 * h * (kTileW * 16), kTileW * 16, 128),
                        sdesc(smem_u32(sW3) + h * 256, 128, 512), idesc_bf16(128, 32), h ? 1u : 0u);
           }
+          // the commit also covers the previous step's z2 MMAs
           mma_commit(bar_mma);
           in_flight |= 4u;
+          // a1 row k is in its ring slot and the halo pixels have read the input buffer
+          ok = bar_wait(bar_e1, sc & 1u);
+          if (!ok) break;
+          tc_after_sync();
+          if (d1) {
+            if (k + 2 < nA) fetch(q + 2, x0, y0 + k + 1, b);
+            else if (has_next) fetch(q + 2, nx0, ny0 - 1 + (k + 2 - nA), nb);
+          }
+          // batch 2: z2 of output row k - 2 from a1 rows k - 2 .. k, into the
+          // D2 buffer of this step's parity; the next step's commit covers it
+          if (d2i) {
+            const int j = k - 2;
+            const uint32_t d2 = tmem + 32 + 32 * (uint32_t)(k & 1);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+              const int ky = tap / 3, kx = tap % 3;
+              const uint32_t sl = smem_u32(sRing) + ((j + ky) % kSlots) * kSlotBytes;
+#pragma unroll
+              for (int hh = 0; hh < 2; ++hh)
+                mma_bf16(d2, sdesc(sl + 2 * hh * kSlotChunk + kx * 16, kSlotChunk, 128),
+                         sdesc(smem_u32(sW2) + (2 * tap + hh) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
+                         (tap | hh) ? 1u : 0u);
+            }
+          }
         }
+        qbase += (uint32_t)nA;
       }
-      {
-        const bool done = ok && bar_wait(bar_mma, ph_mma);
-        if (done && t == 0) in_flight &= ~4u;
-        ok = done && ok;
+      if (!ok) {
+        // a wait gave up: record it, stop the epilogue warps, and give what
+        // may still be in flight one more bounded wait before the tensor
+        // memory is released
+        s_fail[g] = 1u;
+        atomicOr(status, kStatusTimeout);
+        for (uint32_t buf = 0; buf < 2; ++buf)
+          if (in_flight & (1u << buf)) bar_wait(bar_in + buf, (in_flight >> (8 + buf)) & 1u);
       }
-      ph_mma ^= 1u;
-      tc_after_sync();
-      const int p = 32 * warp + lane;
-      // epilogue 1: a1 row r = y0 - 1 + k (zero outside the image) -> slot;
-      // slot pixel i <-> x = x0 - 1 + i
-      if (d1) {
-        const int r = y0 - 1 + k;
-        const bool row_in = r >= 0 && r < H, own_row = r >= y0 && r < y1;
-        uint8_t *slot = sRing + (k % kSlots) * kSlotBytes;
-        {
+      // the last commit (and everything before it) completes
+      if (in_flight & 4u) {
+        mma_commit(bar_mma2);
+        bar_wait(bar_mma2, 0u);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------- epilogues
+    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int p = 32 * warp + lane;
+    bool ok = true;
+    for (long long u = (long long)kGroups * blockIdx.x + g; u < units.count && ok; u += stride) {
+      int b, x0, y0, y1;
+      unit(u, &b, &x0, &y0, &y1);
+      const int nO = y1 - y0, nA = nO + 2;
+      for (int k = 0; k < nA + 2; ++k, ++sc) {
+        const bool d1 = k < nA, d2 = k >= 3 && k < nO + 3, d3 = k >= 4;
+        const uint32_t q = qbase + (uint32_t)k;
+        if (s_fail[g]) { ok = false; break; }
+        // batch 1 of this step and the previous step's z2 have completed
+        ok = bar_wait(bar_mma, sc & 1u);
+        if (!ok) break;
+        tc_after_sync();
+        // epilogue 1: a1 row r = y0 - 1 + k (zero outside the image) -> slot;
+        // slot pixel i <-> x = x0 - 1 + i
+        if (d1) {
+          const int r = y0 - 1 + k;
+          const bool row_in = r >= 0 && r < H, own_row = r >= y0 && r < y1;
+          uint8_t *slot = sRing + (k % kSlots) * kSlotBytes;
+          {
+            float z[32];
+            tmem_ld32(tmem + lane_base, z);
+            const int i = p, xx = x0 - 1 + i;
+            const bool in = row_in && xx >= 0 && xx < W;
+            uint32_t w[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) w[e] = in ? relu_bf16x2(z[2 * e], z[2 * e + 1]) : 0u;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              *reinterpret_cast<uint4 *>(slot + c * kSlotChunk + i * 16) =
+                  make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+            if (acts && own_row && i >= 1 && xx < W) {
+              uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
+#pragma unroll
+              for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+            }
+          }
+          // halo pixels i = 128 (warp 1) and 129 (warp 2): lane = output
+          // channel, z1 = W1 x + hi + lo in FP32 from the row's input buffer
+          // (refilled only after this step's epilogue 1)
+          if (warp == 1 || warp == 2) {
+            ok = bar_wait(bar_in + (q & 1u), (q >> 1) & 1u);
+            const int i = kTileW - 1 + warp, xx = x0 - 1 + i, c = lane;
+            const bool in = row_in && xx >= 0 && xx < W;
+            const uint4 xv = *reinterpret_cast<const uint4 *>(wg + (q & 1u) * kInBuf + i * 16);
+            const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+            float zc = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint32_t bits = (kk & 1) ? (xw[kk >> 1] & 0xFFFF0000u) : (xw[kk >> 1] << 16);
+              zc = fmaf(__uint_as_float(bits), sw1f[c * 8 + kk], zc);
+            }
+            zc = (zc + sb1h[c]) + sb1l[c];
+            const uint16_t a = in ? bf16_bits(fmaxf(zc, 0.f)) : (uint16_t)0;
+            *reinterpret_cast<uint16_t *>(slot + (c >> 3) * kSlotChunk + i * 16 + (c & 7) * 2) = a;
+            if (acts && own_row && i <= kTileW && xx < W) acts[(((size_t)b * H + r) * W + xx) * 96 + c] = a;
+          }
+          fence_async_smem();
+        }
+        tc_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_e1);
+        // epilogue 2: a2 of output row y0 + k - 3 (z2 of the previous step's
+        // D2 buffer) -> a2 buffer
+        if (d2) {
+          const int y = y0 + k - 3;
           float z[32];
-          tmem_ld32(tmem + lane_base, z);
-          const int i = p, xx = x0 - 1 + i;
-          const bool in = row_in && xx >= 0 && xx < W;
+          tmem_ld32(tmem + lane_base + 32 + 32 * (uint32_t)((k - 1) & 1), z);
           uint32_t w[16];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) w[e] = in ? relu_bf16x2(z[2 * e], z[2 * e + 1]) : 0u;
+          for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e] + sb2f[2 * e], z[2 * e + 1] + sb2f[2 * e + 1]);
+          uint8_t *a2 = sA2;
 #pragma unroll
           for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4 *>(slot + c * kSlotChunk + i * 16) =
+            *reinterpret_cast<uint4 *>(a2 + c * (kTileW * 16) + p * 16) =
                 make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-          if (acts && own_row && i >= 1 && xx < W) {
-            uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
+          if (acts && x0 + p < W) {
+            uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
 #pragma unroll
             for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
           }
+          fence_async_smem();
         }
-        // halo pixels i = 128 (warp 1) and 129 (warp 2): lane = output
-        // channel, z1 = W1 x + hi + lo in FP32 from the row's input buffer
-        // (the next fetch into it is issued after this step's barrier)
-        if (warp == 1 || warp == 2) {
-          const int i = kTileW - 1 + warp, xx = x0 - 1 + i, c = lane;
-          const bool in = row_in && xx >= 0 && xx < W;
-          const uint4 xv = *reinterpret_cast<const uint4 *>(wg + (q & 1u) * kInBuf + i * 16);
-          const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
-          float zc = 0.f;
+        // epilogue 3: a3, the dot product with w4 and the sigmoid of output
+        // row y0 + k - 4
+        if (d3) {
+          const int y = y0 + k - 4;
+          float z[32];
+          tmem_ld32(tmem + lane_base + 96, z);
+          float acc = sb4[0];
+          uint32_t w[16];
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {
-            const uint32_t bits = (kk & 1) ? (xw[kk >> 1] & 0xFFFF0000u) : (xw[kk >> 1] << 16);
-            zc = fmaf(__uint_as_float(bits), sw1f[c * 8 + kk], zc);
+          for (int e = 0; e < 16; ++e) {
+            w[e] = relu_bf16x2(z[2 * e] + sb3f[2 * e], z[2 * e + 1] + sb3f[2 * e + 1]);
+            acc += __uint_as_float(w[e] << 16) * sw4[2 * e] + __uint_as_float(w[e] & 0xFFFF0000u) * sw4[2 * e + 1];
           }
-          zc = (zc + sb1h[c]) + sb1l[c];
-          const uint16_t a = in ? bf16_bits(fmaxf(zc, 0.f)) : (uint16_t)0;
-          *reinterpret_cast<uint16_t *>(slot + (c >> 3) * kSlotChunk + i * 16 + (c & 7) * 2) = a;
-          if (acts && own_row && i <= kTileW && xx < W) acts[(((size_t)b * H + r) * W + xx) * 96 + c] = a;
-        }
-      }
-      // epilogue 2: a2 of output row y0 + k - 3 -> a2 buffer
-      if (d2) {
-        const int y = y0 + k - 3;
-        float z[32];
-        tmem_ld32(tmem + lane_base + 64, z);
-        uint32_t w[16];
+          if (x0 + p < W) {
+            const size_t pix = ((size_t)b * H + y) * W + x0 + p;
+            out[pix] = 1.f / (1.f + expf(-acc));
+            if (acts) {
+              uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
 #pragma unroll
-        for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e] + sb2f[2 * e], z[2 * e + 1] + sb2f[2 * e + 1]);
-        uint8_t *a2 = sA2;
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-          *reinterpret_cast<uint4 *>(a2 + c * (kTileW * 16) + p * 16) =
-              make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-        if (acts && x0 + p < W) {
-          uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-        }
-      }
-      // epilogue 3: a3, the dot product with w4 and the sigmoid of output
-      // row y0 + k - 4
-      if (d3) {
-        const int y = y0 + k - 4;
-        float z[32];
-        tmem_ld32(tmem + lane_base + 96, z);
-        float acc = sb4[0];
-        uint32_t w[16];
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          w[e] = relu_bf16x2(z[2 * e] + sb3f[2 * e], z[2 * e + 1] + sb3f[2 * e + 1]);
-          acc += __uint_as_float(w[e] << 16) * sw4[2 * e] + __uint_as_float(w[e] & 0xFFFF0000u) * sw4[2 * e + 1];
-        }
-        if (x0 + p < W) {
-          const size_t pix = ((size_t)b * H + y) * W + x0 + p;
-          out[pix] = 1.f / (1.f + expf(-acc));
-          if (acts) {
-            uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+              for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+            }
           }
         }
+        tc_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_ep);
+        if (!ok) break;
       }
-      fence_async_smem();
-      tc_before_sync();
-      wg_sync(g);   // slots, a2 and all D columns consumed before the next step's MMAs
-      // the input buffer of a1 row k is free: fetch a1 row k + 2 (of this
-      // unit, else of the next)
-      if (t == 0 && ok && d1) {
-        if (k + 2 < nA) fetch(q + 2, x0, y0 + k + 1, b);
-        else if (has_next) fetch(q + 2, nx0, ny0 - 1 + (k + 2 - nA), nb);
-      }
+      qbase += (uint32_t)nA;
     }
-    qbase += (uint32_t)nA;
     if (!ok) s_fail[g] = 1u;
-    wg_sync(g);
-    if (s_fail[g]) break;
   }
-  if (s_fail[g]) {
-    // a wait gave up: record it; give what may still be in flight one more
-    // bounded wait before the tensor memory is released (the in-flight
-    // phase of each barrier is the one after its last completed phase)
-    if (t == 0) {
-      atomicOr(status, kStatusTimeout);
-      for (uint32_t buf = 0; buf < 2; ++buf)
-        if (in_flight & (1u << buf)) bar_wait(bar_in + buf, (in_flight >> (8 + buf)) & 1u);
-      if (in_flight & 4u) bar_wait(bar_mma, ph_mma ^ 1u);
-    }
-  }
+  if (!ctl && s_fail[g] && t == 0) atomicOr(status, kStatusTimeout);
   tc_before_sync();
   __syncthreads();
   if (tid < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*s_tmem), "r"(512));

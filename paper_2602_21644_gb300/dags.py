@@ -94,7 +94,7 @@ EXPORTS = ["dags_create", "dags_destroy", "dags_status_string", "dags_abi_versio
            "mpnet_train_step", "dags_selftest_timeout", "dags_default_sched_cfg", "semantic_trigger",
            "dags_default_lm_cfg", "splat_normal_equations", "lm_init", "lm_pose_step", "splat_track_lm",
            "splat_mp_consistency", "dags_default_edge_cfg", "splat_edge_warp",
-           "epipolar_verify", "dags_eval_counting", "dags_eval_read", "dags_measure_alu",
+           "epipolar_verify", "dags_eval_counting", "dags_eval_read", "dags_measure_alu", "dags_measure_mma",
            "splat_backward_upstream", "dags_default_gauss_adam_cfg", "gauss_adam_init", "gauss_adam_step"]
 
 KERNELS = ["preprocess", "emit", "tile_sort", "render_fwd", "render_bwd", "preprocess_bwd", "pose_step",
@@ -111,6 +111,17 @@ def measure_alu(kind: int, iters: int = 1 << 14):
     ops, ms = ctypes.c_double(), ctypes.c_double()
     _check(lib.dags_measure_alu(int(kind), int(iters), ctypes.byref(ops), ctypes.byref(ms)), "dags_measure_alu")
     return ops.value, ms.value
+
+
+def measure_mma(n_cols: int, groups: int, reps: int = 256):
+    """Measured tensor-core rate (multiply-adds per SM cycle) of back-to-back
+    M = 128, N = n_cols, K = 16 BF16 MMAs issued by `groups` warpgroups of one
+    CTA, and the issue cycles per MMA of one issuing thread."""
+    lib = load()
+    mac, cyc = ctypes.c_double(), ctypes.c_double()
+    _check(lib.dags_measure_mma(int(n_cols), int(groups), int(reps), ctypes.byref(mac), ctypes.byref(cyc)),
+           "dags_measure_mma")
+    return mac.value, cyc.value
 
 
 def load(path: str = LIB_PATH):
@@ -165,6 +176,8 @@ def load(path: str = LIB_PATH):
     lib.dags_eval_read.restype = ctypes.c_int
     lib.dags_measure_alu.argtypes = [I32, I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.dags_measure_alu.restype = ctypes.c_int
+    lib.dags_measure_mma.argtypes = [I32, I32, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.dags_measure_mma.restype = ctypes.c_int
     lib.splat_track.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
                                 ctypes.POINTER(CLossCfg), ctypes.POINTER(CPoseCfg), I32, P, P, P, P, P, I32, P]
     lib.splat_track.restype = ctypes.c_int

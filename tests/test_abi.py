@@ -86,7 +86,7 @@ def test_entry_points_reject_a_null_context():
     from paper_2602_21644_gb300 import dags
     lib = dags.load()
     host_only = {"dags_create", "dags_destroy", "dags_status_string", "dags_abi_version", "splat_forward_static",
-                 "dags_measure_alu"}
+                 "dags_measure_alu", "dags_measure_mma"}
     checked = []
     for name in dags.EXPORTS:
         if name in host_only or name.startswith("dags_default_"):
@@ -103,6 +103,11 @@ def test_entry_points_reject_a_null_context():
     assert lib.dags_measure_alu(0, 0, ctypes.byref(ops), None) == -1
     assert lib.dags_measure_alu(1, 1 << 25, ctypes.byref(ops), None) == -1
     assert lib.dags_measure_alu(0, 1024, None, None) == -1
+    # so does the tensor-core probe's (N, warpgroups, repetitions)
+    mac = ctypes.c_double()
+    for n, g, r in [(24, 1, 64), (0, 1, 64), (272, 1, 64), (256, 4, 64), (32, 3, 64), (32, 1, 0), (32, 1, 5000)]:
+        assert lib.dags_measure_mma(n, g, r, ctypes.byref(mac), None) == -1, (n, g, r)
+    assert lib.dags_measure_mma(32, 1, 64, None, None) == -1
 
 
 def test_static_forward_limits_are_checked_on_the_host():
