@@ -979,11 +979,18 @@ def run_ours(args):
     for n_cols, groups in ((32, 4), (64, 4), (128, 4), (256, 2)):
         rates[n_cols] = max(dags.measure_mma(n_cols, groups, 512)[0] for _ in range(2))
     top = max(rates.values())
+    # the probe's rates as TFLOP/s of the whole device at the maximum SM clock
+    sms = int(torch.cuda.get_device_properties(0).multi_processor_count)
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n32_tflops = rates[32] * 2 * sms * mhz * 1e6 / 1e12
     learned["roofline"]["mma_rate_by_n"] = {
         "mac_per_sm_cycle": {str(k): round(v, 1) for k, v in rates.items()},
         "n32_frac_of_best": round(rates[32] / top, 4),
-        "frac_of_n32_ceiling": round(learned["roofline"]["frac"] / (rates[32] / top), 4),
-        "how": "dags_measure_mma: one CTA, back-to-back BF16 MMAs (M 128, K 16) from 4 warpgroups (2 at N 256)"}
+        "n32_ceiling_tflops": round(n32_tflops, 1),
+        "best_tflops": round(top * 2 * sms * mhz * 1e6 / 1e12, 1),
+        "frac_of_n32_ceiling": round(learned["infer_tflops"] / n32_tflops, 4),
+        "how": "dags_measure_mma: one CTA, back-to-back BF16 MMAs (M 128, K 16) from 4 warpgroups (2 at N 256); "
+               "TFLOP/s = MAC/cycle x 2 x SMs x the maximum SM clock"}
     line["learned_mp"] = learned
     line["splat_variants"] = variants
     line["lm_tracking"] = lm
