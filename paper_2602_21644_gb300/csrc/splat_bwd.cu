@@ -39,7 +39,7 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
   pdl_trigger();
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
   __shared__ float2 s_e[kTilePix];                                  // box half extents
-  __shared__ uint32_t s_id[kTilePix];
+  __shared__ float *s_dst[kTilePix];                                // the entry's 2D-gradient words
   __shared__ int s_max;
   const unsigned FULLM = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -137,7 +137,7 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
       uint32_t id = ws.sorted_ids[s + beg + tid];
       if (!DAGS_IN_BOUNDS(id < (uint32_t)ws.max_n, ws.counters + CNT_STATUS)) id = 0;
       const size_t slot = vbase + id;
-      s_id[tid] = id;
+      s_dst[tid] = ws.grad2d + slot * kGradWords;
       const float4 r0 = ws.rec2d[slot * 3 + 0];
       const float2 lo = ws.rec_lo[slot];
       s_a[tid] = make_float4(r0.x, r0.y, lo.x, lo.y);
@@ -178,26 +178,29 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
         // branching form, operation for operation
         const float4 a = s_a[j], b = s_b[j];
         const float dx = (a.x - fpx) + a.z, dy = (a.y - fpy) + a.w;
-        const float p = fmaf(b.x * dx, dx, fmaf(b.y * dx, dy, fmaf(b.z * dy, dy, b.w)));
+        const float bxdx = b.x * dx, bydx = b.y * dx, bzdy = b.z * dy;
+        const float p = fmaf(bxdx, dx, fmaf(bydx, dy, fmaf(bzdy, dy, b.w)));
         const bool contrib = k < lastp && p >= r.log2_alpha_min;
         if (COUNT) { n_eval += k < lastp ? 1u : 0u; n_contrib += contrib ? 1u : 0u; }
         const float ag = hw_exp2(p);
         const float alpha = fminf(r.alpha_max, ag);
         const float inv = hw_rcp(1.f - alpha);
         T = contrib ? T * inv : T;           // transmittance in front of this Gaussian
-        const float wk = alpha * T;
+        // the weight, zero for a lane that does not take the entry (its
+        // depth gradient and suffix update then vanish without a select)
+        const float wk = contrib ? alpha * T : 0.f;
         const float4 c = s_c[j];
         const uint32_t rgb = __float_as_uint(c.z), blb = __float_as_uint(c.w);
         const float fr = bf16_lo(rgb), fg = bf16_hi(rgb), fb = bf16_lo(blb);
         // dL/dalpha = sum_ch g_ch (c_ch T - S_ch / (1 - alpha))
         const float gcv = fmaf(g0, fr, fmaf(g1, fg, fmaf(g2, fb, fmaf(g3, c.x, fmaf(g5, c.y, g4)))));
         const float dal = fmaf(gcv, T, -Sg * inv);
-        const float gz = contrib ? g3 * wk : 0.f;
+        const float gz = g3 * wk;
         float gr = 0.f, gg = 0.f, gbl = 0.f, go = 0.f;
         if (FULL) {
-          gr = contrib ? g0 * wk : 0.f;
-          gg = contrib ? g1 * wk : 0.f;
-          gbl = contrib ? g2 * wk : 0.f;
+          gr = g0 * wk;
+          gg = g1 * wk;
+          gbl = g2 * wk;
         }
         // below the clamp, d alpha / d(natural exponent) = alpha; the
         // exponent in log2 units is p, so d/dx of the natural exponent is
@@ -205,19 +208,23 @@ render_bwd_kernel(Workspace ws, Raster r, Loss l, const float4 *__restrict__ tar
         const bool slope = contrib && ag <= r.alpha_max;
         const float dpw = slope ? dal * alpha : 0.f;
         const float hl = dpw * kLn2;
-        const float gu = hl * (2.f * b.x * dx + b.y * dy);
-        const float gv = hl * (b.y * dx + 2.f * b.z * dy);
-        const float ga = -0.5f * dpw * dx * dx;
-        const float gb = -dpw * dx * dy;
-        const float gc = -0.5f * dpw * dy * dy;
+        // d p / d(u, v) = (2 a' dx + b' dy, b' dx + 2 c' dy) from the
+        // exponent's products; d(natural exponent) / d(conic) = -(dx^2 / 2,
+        // dx dy, dy^2 / 2)
+        const float gu = hl * fmaf(2.f, bxdx, b.y * dy);
+        const float gv = hl * fmaf(2.f, bzdy, bydx);
+        const float tx = dpw * dx, ty = dpw * dy;
+        const float ga = -0.5f * (tx * dx);
+        const float gb = -(tx * dy);
+        const float gc = -0.5f * (ty * dy);
         if (FULL) go = slope ? dal * hw_exp2(p - b.w) : 0.f;
-        Sg = contrib ? fmaf(gcv, wk, Sg) : Sg;
+        Sg = fmaf(gcv, wk, Sg);
         // a recorded entry has a contributing lane: the forward took it for
         // the same pixels by the same arithmetic
         if (recorded || __any_sync(FULLM, contrib)) {
           // reduce-scatter over the warp: every lane then holds the warp sum
           // of word `comp`, and one lane per word adds it with one atomic
-          float *dst = ws.grad2d + (vbase + s_id[j]) * kGradWords;
+          float *dst = s_dst[j];
           float sum;
           if constexpr (FULL) {
             const float v10[10] = {gu, gv, ga, gb, gc, gz, go, gr, gg, gbl};
