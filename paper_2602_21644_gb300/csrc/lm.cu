@@ -220,7 +220,7 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
                   const float4 *__restrict__ tan, float *__restrict__ partial, double *__restrict__ normal,
                   float *__restrict__ jac, float *__restrict__ image, int32_t *__restrict__ last, LmFuse fuse) {
   pdl_wait();
-  __shared__ uint64_t s_key[kSortSmallCap];
+  __shared__ __align__(16) uint64_t s_key[kSortSmallCap];
   __shared__ float4 s_a[kJacBatch], s_b[kJacBatch], s_c[kJacBatch];   // s_a: {u hi, v hi, u lo, v lo}
   __shared__ float2 s_e[kJacBatch];                                   // box half extents
   extern __shared__ float4 s_t[];   // kJacBatch * kTan4

@@ -558,7 +558,7 @@ render_fwd_kernel(Workspace ws, int views, Raster r, Loss l, const float4 *__res
   // (no early trigger: the adjoint's CTAs are placed on the SMs as they
   // empty, which keeps its longest-first launch order spread over the SMs)
   pdl_wait();
-  __shared__ uint64_t s_key[kSortSmallCap];
+  __shared__ __align__(16) uint64_t s_key[kSortSmallCap];
   __shared__ float4 s_a[kTilePix], s_b[kTilePix], s_c[kTilePix];   // s_a: {u hi, v hi, u lo, v lo}
   __shared__ float2 s_e[kTilePix];                                  // box half extents
   __shared__ float2 s_red[kTilePix / 32];

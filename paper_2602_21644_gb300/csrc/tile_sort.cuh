@@ -102,6 +102,29 @@ __device__ __forceinline__ void bitonic_smem(uint64_t *s, int len2) {
   }
 }
 
+// Ascending sort of s[0, n) (s 16-byte aligned, n <= kTilePix, unique keys)
+// by rank: thread i counts the keys below key i with broadcast reads of the
+// whole list, then every key is stored at its rank. The same order as the
+// bitonic network; n steps of one thread instead of log2(n)^2 / 2 barrier
+// stages of the CTA, which pays for lists of up to one key per thread.
+__device__ __forceinline__ void rank_sort_smem(uint64_t *s, int n) {
+  const int tid = threadIdx.x;
+  const bool has = tid < n;
+  const uint64_t key = has ? s[tid] : 0ull;
+  int rank = 0;
+  if (has) {
+    int j = 0;
+    for (; j + 1 < n; j += 2) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(s + j);
+      rank += (v.x < key) + (v.y < key);
+    }
+    if (j < n) rank += s[j] < key;
+  }
+  __syncthreads();
+  if (has) s[rank] = key;
+  __syncthreads();
+}
+
 __device__ __forceinline__ int next_pow2(int x) {
   int p = 1;
   while (p < x) p <<= 1;
@@ -150,7 +173,14 @@ __device__ __forceinline__ bool sort_tile_bucket(const Workspace &ws, uint32_t s
                                                  bool publish_small = true) {
   const int tid = threadIdx.x;
   const bool own_sort = len <= kSortSmallCap;
-  if (own_sort && len > 0) {
+  if (own_sort && len > 0 && len <= kTilePix) {
+    // (s_key is 16-byte aligned: the rank count reads two keys at a time)
+    for (int k = tid; k < len; k += kTilePix) s_key[k] = ws.keys[s + k];
+    __syncthreads();
+    rank_sort_smem(s_key, len);
+    if (publish_small)
+      for (int k = tid; k < len; k += kTilePix) ws.sorted_ids[s + k] = (uint32_t)s_key[k];
+  } else if (own_sort && len > 0) {
     const int len2 = next_pow2(len);
     for (int k = tid; k < len2; k += kTilePix) s_key[k] = k < len ? ws.keys[s + k] : ~0ull;
     __syncthreads();
