@@ -546,9 +546,9 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
 // the K dimension (A = activations channel-major, B = upstream gradients
 // channel-major), accumulated in TMEM across all tiles of a persistent CTA
 // and added to the global FP32 gradient once per CTA. A row of ones appended
-// to A gives the bias gradients from the same MMAs. Only M = 128 MMAs are
-// used; A rows past the real ones are don't-care rows whose D rows are
-// ignored.
+// to A gives the bias gradients from the same MMAs. The weight-gradient MMAs
+// are M = 64, the data MMAs M = 128; A rows past the real ones are
+// don't-care rows whose D rows are ignored.
 
 constexpr int kGW1 = 0, kGW2 = 512, kGW3 = 512 + 9216, kGw4 = 512 + 9216 + 1024, kGb1 = kGw4 + 32,
               kGb2 = kGb1 + 32, kGb3 = kGb2 + 32, kGb4 = kGb3 + 32, kGTotal = kGb4 + 1;   // 10881 floats
@@ -584,10 +584,17 @@ __global__ void mpnet_count_finish_kernel(float *inv_n) {
 //   MN-major, MN = channels, K = pixels (instruction-descriptor bits 15/16):
 //     SBO = chunk stride (the next 8 channels), LBO = 128 B (the next 8
 //     pixels) - the weight-gradient GEMMs, which reduce over pixels.
-// Weight-gradient MMAs are M = 128 over 32 (+1) real channel rows: the rows
-// past them read whatever follows in shared memory (in bounds), and their D
-// rows are never read. A chunk of (1, 0, ..., 0) after the real channels
-// gives the bias gradient in D row 32.
+// Weight-gradient MMAs are M = 64 over 32 (+1) real channel rows (M = 64
+// reads half the A operand of M = 128, and at N = 32 the MMA rate is bound
+// by the operands' shared-memory reads): the rows past them read whatever
+// follows in shared memory (in bounds), and their D rows are never read. A
+// chunk of (1, 0, ..., 0) after the real channels gives the bias gradient in
+// D row 32.
+
+// The D row an M = 64 accumulator keeps in TMEM lane `lane`: rows 16q ..
+// 16q + 15 sit in lanes 32q .. 32q + 15 of lane quadrant q (measured on the
+// device; lanes 16..31 of each quadrant hold none: -1).
+__device__ __forceinline__ int m64_row(int lane) { return (lane & 31) < 16 ? 16 * (lane >> 5) + (lane & 31) : -1; }
 
 __host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
   return idesc_bf16(M, N) | (1u << 15) | (1u << 16);   // A and B MN-major
@@ -703,9 +710,9 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
       for (int s = 0; s < kTileW / 16; ++s) {
         const uint32_t acc = (!first || s > 0) ? 1u : 0u;
         mma_bf16(tmem + 32, sdesc(smem_u32(sA2) + s * 256, 128, kChunkPx),
-                 sdesc(smem_u32(sDz3) + s * 256, 128, kChunkPx), idesc_bf16_mn(128, 32), acc);
+                 sdesc(smem_u32(sDz3) + s * 256, 128, kChunkPx), idesc_bf16_mn(64, 32), acc);
         mma_bf16(tmem + 64, sdesc(smem_u32(sA3) + s * 256, 128, kChunkPx),
-                 sdesc(smem_u32(sDz4) + s * 256, 128, kChunkPx), idesc_bf16_mn(128, 16), acc);
+                 sdesc(smem_u32(sDz4) + s * 256, 128, kChunkPx), idesc_bf16_mn(64, 16), acc);
       }
       mma_commit(bar);
     }
@@ -737,19 +744,20 @@ mpnet_bwd1_kernel(const uint8_t *__restrict__ weights, const float *__restrict__
     bar_wait(bar, phase ^ 1u);
   }
   // the CTA's accumulated weight gradients: row r of D = input channel (or the
-  // ones row), column = output channel
+  // ones row), column = output channel; an M = 64 accumulator's row r is in
+  // TMEM lane 32 (r / 16) + r % 16
   if (!first) {
     tc_after_sync();
     float d[32];
     tmem_ld32(tmem + lane_base + 32, d);
-    const int r = tid;
-    if (r < 32) {
+    const int r = m64_row(tid);
+    if (r >= 0 && r < 32) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW3 + o * 32 + r, d[o]);
     } else if (r == 32) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb3 + o, d[o]);
     }
     tmem_ld32(tmem + lane_base + 64, d);
-    if (r < 32) atomicAdd(grad + kGw4 + r, d[0]);
+    if (r >= 0 && r < 32) atomicAdd(grad + kGw4 + r, d[0]);
     else if (r == 32) atomicAdd(grad + kGb4, d[0]);
   }
   lsum = warp_sum(lsum);
@@ -875,7 +883,7 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
         for (int tap = 0; tap < 9; ++tap) {
           const int ky = tap / 3, kx = tap % 3;
           mma_bf16(tmem + 32 + 32 * tap, sdesc(smem_u32(sA1) + (ky * kHaloW + kx) * 16 + s2 * 256, 128, kHaloChunk),
-                   sdesc(bdz2, 128, kHaloChunk), idesc_bf16_mn(128, 32), acc);
+                   sdesc(bdz2, 128, kHaloChunk), idesc_bf16_mn(64, 32), acc);
         }
       }
     }
@@ -910,7 +918,7 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
     if (tid == 0) {
       for (int s2 = 0; s2 < kTileW / 16; ++s2)
         mma_bf16(tmem + 320, sdesc(smem_u32(sX) + s2 * 256, 128, kChunkPx),
-                 sdesc(smem_u32(sDz1) + s2 * 256, 128, kChunkPx), idesc_bf16_mn(128, 32),
+                 sdesc(smem_u32(sDz1) + s2 * 256, 128, kChunkPx), idesc_bf16_mn(64, 32),
                  (!first || s2 > 0) ? 1u : 0u);
     }
     first = false;
@@ -930,17 +938,17 @@ mpnet_bwd2_kernel(const uint8_t *__restrict__ weights, const uint4 *__restrict__
   if (!first) {
     tc_after_sync();
     float d[32];
-    const int r = tid;
+    const int r = m64_row(tid);
     for (int tap = 0; tap < 9; ++tap) {
       tmem_ld32(tmem + lane_base + 32 + 32 * tap, d);
-      if (r < 32) {
+      if (r >= 0 && r < 32) {
         for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW2 + o * 288 + tap * 32 + r, d[o]);
       } else if (r == 32 && tap == 0) {
         for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb2 + o, d[o]);
       }
     }
     tmem_ld32(tmem + lane_base + 320, d);
-    if (r < 8) {
+    if (r >= 0 && r < 8) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGW1 + o * 16 + r, d[o]);
     } else if (r == 8) {
       for (int o = 0; o < 32; ++o) atomicAdd(grad + kGb1 + o, d[o]);
