@@ -978,6 +978,8 @@ def run_ours(args):
     rates = {}
     for n_cols, groups in ((32, 4), (64, 4), (128, 4), (256, 2)):
         rates[n_cols] = max(dags.measure_mma(n_cols, groups, 512)[0] for _ in range(2))
+    # M = 64, the training step's weight-gradient MMAs (33 real rows)
+    m64 = {n_cols: max(dags.measure_mma(n_cols, 4, 512, m_rows=64)[0] for _ in range(2)) for n_cols in (32, 64)}
     top = max(rates.values())
     # the probe's rates as TFLOP/s of the whole device at the maximum SM clock
     sms = int(torch.cuda.get_device_properties(0).multi_processor_count)
@@ -985,6 +987,7 @@ def run_ours(args):
     n32_tflops = rates[32] * 2 * sms * mhz * 1e6 / 1e12
     learned["roofline"]["mma_rate_by_n"] = {
         "mac_per_sm_cycle": {str(k): round(v, 1) for k, v in rates.items()},
+        "mac_per_sm_cycle_m64": {str(k): round(v, 1) for k, v in m64.items()},
         "n32_frac_of_best": round(rates[32] / top, 4),
         "n32_ceiling_tflops": round(n32_tflops, 1),
         "best_tflops": round(top * 2 * sms * mhz * 1e6 / 1e12, 1),

@@ -665,15 +665,16 @@ int dags_measure_alu(int32_t kind, int64_t iters, double *ops_per_s, double *ms)
 /* Rate probe of the current device's tensor core (measurement; no paper
  * counterpart): one CTA of `groups` warpgroups (1, 2 or 4), thread 0 of each
  * issuing `reps` back-to-back accumulating tcgen05.mma kind::f16 with M =
- * 128, N = n_cols, K = 16, BF16 operands in shared memory and FP32
+ * m_rows (64 or 128), N = n_cols, K = 16, BF16 operands in shared memory and FP32
  * accumulators in tensor memory, then a commit and a bounded wait; on a
  * private launch, synchronised. mac_per_cycle (host out): multiply-adds per
  * SM cycle of the slowest-to-complete average warpgroup; cycles_per_mma
  * (host out, or NULL): the mean issue cycles per MMA of one issuing thread.
- * n_cols a multiple of 16 in [16, 256] with n_cols <= 512 / groups and
- * n_cols <= 128 for 4 groups, 1 <= reps <= 4096, else DAGS_E_INVAL;
+ * m_rows 64 or 128, n_cols a multiple of 16 in [16, 256] with n_cols <= 512 /
+ * groups and n_cols <= 128 for 4 groups, 1 <= reps <= 4096, else DAGS_E_INVAL;
  * DAGS_E_TIMEOUT if a wait ran out. */
-int dags_measure_mma(int32_t n_cols, int32_t groups, int32_t reps, double *mac_per_cycle, double *cycles_per_mma);
+int dags_measure_mma(int32_t m_rows, int32_t n_cols, int32_t groups, int32_t reps, double *mac_per_cycle,
+                     double *cycles_per_mma);
 
 #ifdef __cplusplus
 }

@@ -7,8 +7,8 @@
 //                         per thread (one lane operation per FMA)
 //   alu_probe_kernel<1>   eight independent ex2.approx.ftz chains per thread
 //                         (x <- 2^-x keeps every value in [0.5, 1])
-//   mma_probe_kernel      back-to-back tcgen05.mma kind::f16 (M = 128, N =
-//                         n_cols, K = 16, BF16 operands in shared memory,
+//   mma_probe_kernel      back-to-back tcgen05.mma kind::f16 (M = 64 or 128,
+//                         N = n_cols, K = 16, BF16 operands in shared memory,
 //                         FP32 accumulators in tensor memory), issued by one
 //                         thread of each of 1..4 warpgroups of one CTA: the
 //                         tensor core's rate as a function of N
@@ -53,7 +53,8 @@ constexpr int kProbeSmem = 40960;
 // accumulating MMAs into its own TMEM columns, commits them to its mbarrier
 // and waits (bounded); cycles[2g] = the issue loop's SM cycles, cycles[2g +
 // 1] = issue to completion. The operands are zeros.
-__global__ void mma_probe_kernel(int groups, int n_cols, int reps, unsigned long long *cycles, uint32_t *status) {
+__global__ void mma_probe_kernel(int groups, int m_rows, int n_cols, int reps, unsigned long long *cycles,
+                                 uint32_t *status) {
   __shared__ __align__(1024) uint8_t sm[kProbeSmem];
   __shared__ uint64_t bars[4];
   __shared__ uint32_t s_tmem;
@@ -77,7 +78,8 @@ __global__ void mma_probe_kernel(int groups, int n_cols, int reps, unsigned long
     const uint32_t a = probe_smem_u32(sm + g * (kProbeSmem / groups)), b = a + 4096;
     const uint64_t ad = probe_sdesc(a, 128, 256), bd = probe_sdesc(b, 128, 256);
     // kind::f16: D FP32, A and B BF16, both K-major; N >> 3 at bit 17, M >> 4 at bit 24
-    const uint32_t id = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t id = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n_cols >> 3) << 17) |
+                        ((uint32_t)(m_rows >> 4) << 24);
     const uint32_t mb = probe_smem_u32(bars + g);
     for (int pass = 0; pass < 2; ++pass) {
       const unsigned long long c0 = clock64();
@@ -114,9 +116,9 @@ __global__ void mma_probe_kernel(int groups, int n_cols, int reps, unsigned long
 
 using namespace dags;
 
-extern "C" int dags_measure_mma(int32_t n_cols, int32_t groups, int32_t reps, double *mac_per_cycle,
+extern "C" int dags_measure_mma(int32_t m_rows, int32_t n_cols, int32_t groups, int32_t reps, double *mac_per_cycle,
                                 double *cycles_per_mma) {
-  if (!(groups == 1 || groups == 2 || groups == 4) || n_cols < 16 || n_cols > 256 || n_cols % 16 ||
+  if (!(m_rows == 64 || m_rows == 128) || !(groups == 1 || groups == 2 || groups == 4) || n_cols < 16 || n_cols > 256 || n_cols % 16 ||
       n_cols > 512 / groups || 4096 + n_cols * 32 > kProbeSmem / groups || reps < 1 || reps > 4096 ||
       !mac_per_cycle)
     return DAGS_E_INVAL;
@@ -127,7 +129,7 @@ extern "C" int dags_measure_mma(int32_t n_cols, int32_t groups, int32_t reps, do
   if (e == cudaSuccess) e = cudaMemset(d_cyc, 0, 8 * sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(uint32_t));
   if (e == cudaSuccess) {
-    mma_probe_kernel<<<1, 128 * groups>>>(groups, n_cols, reps, d_cyc, d_status);
+    mma_probe_kernel<<<1, 128 * groups>>>(groups, m_rows, n_cols, reps, d_cyc, d_status);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -144,7 +146,7 @@ extern "C" int dags_measure_mma(int32_t n_cols, int32_t groups, int32_t reps, do
   tot /= groups;
   iss /= groups;
   if (!(tot > 0.0)) return DAGS_E_CUDA;
-  *mac_per_cycle = 128.0 * n_cols * 16.0 * reps * groups / tot;
+  *mac_per_cycle = (double)m_rows * n_cols * 16.0 * reps * groups / tot;
   if (cycles_per_mma) *cycles_per_mma = iss / reps;
   return DAGS_OK;
 }

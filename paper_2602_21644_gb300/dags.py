@@ -113,14 +113,14 @@ def measure_alu(kind: int, iters: int = 1 << 14):
     return ops.value, ms.value
 
 
-def measure_mma(n_cols: int, groups: int, reps: int = 256):
+def measure_mma(n_cols: int, groups: int, reps: int = 256, m_rows: int = 128):
     """Measured tensor-core rate (multiply-adds per SM cycle) of back-to-back
-    M = 128, N = n_cols, K = 16 BF16 MMAs issued by `groups` warpgroups of one
-    CTA, and the issue cycles per MMA of one issuing thread."""
+    M = m_rows, N = n_cols, K = 16 BF16 MMAs issued by `groups` warpgroups of
+    one CTA, and the issue cycles per MMA of one issuing thread."""
     lib = load()
     mac, cyc = ctypes.c_double(), ctypes.c_double()
-    _check(lib.dags_measure_mma(int(n_cols), int(groups), int(reps), ctypes.byref(mac), ctypes.byref(cyc)),
-           "dags_measure_mma")
+    _check(lib.dags_measure_mma(int(m_rows), int(n_cols), int(groups), int(reps), ctypes.byref(mac),
+                                ctypes.byref(cyc)), "dags_measure_mma")
     return mac.value, cyc.value
 
 
@@ -176,7 +176,8 @@ def load(path: str = LIB_PATH):
     lib.dags_eval_read.restype = ctypes.c_int
     lib.dags_measure_alu.argtypes = [I32, I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     lib.dags_measure_alu.restype = ctypes.c_int
-    lib.dags_measure_mma.argtypes = [I32, I32, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.dags_measure_mma.argtypes = [I32, I32, I32, I32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]
     lib.dags_measure_mma.restype = ctypes.c_int
     lib.splat_track.argtypes = [P, P, I64, ctypes.POINTER(CCamera), P, P, ctypes.POINTER(CRasterCfg),
                                 ctypes.POINTER(CLossCfg), ctypes.POINTER(CPoseCfg), I32, P, P, P, P, P, I32, P]

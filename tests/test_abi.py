@@ -105,9 +105,10 @@ def test_entry_points_reject_a_null_context():
     assert lib.dags_measure_alu(0, 1024, None, None) == -1
     # so does the tensor-core probe's (N, warpgroups, repetitions)
     mac = ctypes.c_double()
-    for n, g, r in [(24, 1, 64), (0, 1, 64), (272, 1, 64), (256, 4, 64), (32, 3, 64), (32, 1, 0), (32, 1, 5000)]:
-        assert lib.dags_measure_mma(n, g, r, ctypes.byref(mac), None) == -1, (n, g, r)
-    assert lib.dags_measure_mma(32, 1, 64, None, None) == -1
+    for m, n, g, r in [(128, 24, 1, 64), (128, 0, 1, 64), (128, 272, 1, 64), (128, 256, 4, 64), (128, 32, 3, 64),
+                       (128, 32, 1, 0), (128, 32, 1, 5000), (96, 32, 1, 64), (256, 32, 1, 64)]:
+        assert lib.dags_measure_mma(m, n, g, r, ctypes.byref(mac), None) == -1, (m, n, g, r)
+    assert lib.dags_measure_mma(128, 32, 1, 64, None, None) == -1
 
 
 def test_static_forward_limits_are_checked_on_the_host():
