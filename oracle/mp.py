@@ -27,8 +27,12 @@ Follows Sec. IV-A and Eq. (17) step by step, one view:
                 of the image with di^2 + dj^2 <= r_s^2, whatever their label
     K_p, M_p    Eqs. (6), (7)  (fusion_mode 1 forces K = 0, 2 forces K = 1)
   per Gaussian G
-    N(G)        pixels within r_s of the projected mean, Eq. (1), one scale;
-                w(p, G) = exp(-|p - pi(G)|^2 / (2 sigma_w^2))
+    N(G)        Eq. (1): the union over pyramid levels s = 0 .. S-1 of the
+                level-s pixels within r_s of pi(G) / 2^s (S = cfg.scales;
+                level s + 1 is the 2x2 box mean of level s for M_p and e and
+                the 2x2 max for D_rend, odd last rows/columns dropped);
+                w(p, G) = 2^-s exp(-|p - pi(G) / 2^s|^2 / (2 sigma_w^2))
+                for a member of level s (S = 1: the single-scale disk)
     observed    z > z_near, N(G) non-empty, and not behind the rendered
                 surface: z <= max_{N(G)} D_rend + vis_tol
     M_hat       Eq. (8)
@@ -78,6 +82,7 @@ class MPConfig:
     z_near: float = 0.2
     tau_floor: float = 0.5     # Eq. (12)
     fusion_mode: int = 0       # 0 fused, 1 K = 0 (MP_ins only), 2 K = 1 (MP_geo only)
+    scales: int = 1            # pyramid levels S of the association, Eq. (1)
 
     def as_dict(self):
         return asdict(self)
@@ -87,6 +92,21 @@ def lower_median(x: np.ndarray) -> float:
     """Element at index floor((n-1)/2) of the ascending sort."""
     s = np.sort(np.asarray(x, dtype=np.float64))
     return float(s[(len(s) - 1) // 2])
+
+
+def pyramid(x, W, H, S, pool):
+    """Levels 0 .. S-1 of a per-pixel map: level 0 is x (H x W); level s + 1
+    has floor(W_s / 2) x floor(H_s / 2) pixels, each the mean (pool = "mean")
+    or the maximum (pool = "max") of the 2 x 2 level-s pixels it covers.
+    Returns [(flat values, W_s, H_s)]."""
+    a = np.asarray(x, np.float64).reshape(H, W)
+    out = [(a.ravel(), W, H)]
+    for _ in range(1, S):
+        h, w = a.shape[0] // 2, a.shape[1] // 2
+        q = a[:2 * h, :2 * w].reshape(h, 2, w, 2)
+        a = q.mean(axis=(1, 3)) if pool == "mean" else q.max(axis=(1, 3))
+        out.append((a.ravel(), w, h))
+    return out
 
 
 def neighbourhood_std(e, W, H, r_s):
@@ -202,9 +222,13 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
     sig_e = np.zeros(n)
     disk_flag = np.zeros(n, bool)
     vis_flag = np.zeros(n, bool)
-    # Eq. (1) for all Gaussians at once: the candidate pixels are a square of
-    # integer offsets around the projected mean; N(G) keeps those inside the
-    # image within r_s.
+    # Eq. (1) for all Gaussians at once: at each pyramid level the candidate
+    # pixels are a square of integer offsets around the scaled projected mean;
+    # N(G) keeps those inside the level within r_s, over all levels.
+    S = int(cfg.scales)
+    lv_m = pyramid(M_p, W, H, S, "mean")
+    lv_e = pyramid(e, W, H, S, "mean")
+    lv_d = pyramid(d_rend, W, H, S, "max")
     R = int(np.ceil(cfg.r_s)) + 1
     off = np.arange(-R, R + 2)
     oi, oj = np.meshgrid(off, off, indexing="xy")
@@ -219,26 +243,38 @@ def mp_update(means, mp_prev, labels_prev, cam, pose, inst, d_obs, c_obs, d_rend
         ok_uv = front & np.isfinite(u) & np.isfinite(v) & (np.abs(u) < 1e7) & (np.abs(v) < 1e7)
         u = np.where(ok_uv, u, -1e6)
         v = np.where(ok_uv, v, -1e6)
-        ii = np.floor(u).astype(np.int64)[:, None] + oi[None, :]
-        jj = np.floor(v).astype(np.int64)[:, None] + oj[None, :]
-        inside = (ii >= 0) & (ii < W) & (jj >= 0) & (jj < H) & ok_uv[:, None]
-        d2 = (ii - u[:, None]) ** 2 + (jj - v[:, None]) ** 2
         # a pixel whose distance lies within the FP32 rounding of the projected
-        # centre (a few ulps of |u|, |v|) of the radius is an undecided member
-        ecoord = 2.0 ** -22 * np.maximum(np.maximum(np.abs(u), np.abs(v)), 1.0)[:, None]
-        dmarg = 4.0 * cfg.r_s * ecoord + 1e-5 * cfg.r_s ** 2
-        disk_flag[c0:c1] = np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= dmarg), axis=1)
-        sel = inside & (d2 <= cfg.r_s ** 2)
+        # centre (a few ulps of |u|, |v|, scaled with the level) of the radius
+        # is an undecided member
+        ecoord0 = 2.0 ** -22 * np.maximum(np.maximum(np.abs(u), np.abs(v)), 1.0)[:, None]
+        sel_l, w_l, m_l, e_l, d_l = [], [], [], [], []
+        dflag = np.zeros(c1 - c0, bool)
+        for s, ((Mv, Ws, Hs), (Ev, _, _), (Dv, _, _)) in enumerate(zip(lv_m, lv_e, lv_d)):
+            us, vs = u / 2.0 ** s, v / 2.0 ** s
+            ii = np.floor(us).astype(np.int64)[:, None] + oi[None, :]
+            jj = np.floor(vs).astype(np.int64)[:, None] + oj[None, :]
+            inside = (ii >= 0) & (ii < Ws) & (jj >= 0) & (jj < Hs) & ok_uv[:, None]
+            d2 = (ii - us[:, None]) ** 2 + (jj - vs[:, None]) ** 2
+            dmarg = 4.0 * cfg.r_s * ecoord0 / 2.0 ** s + 1e-5 * cfg.r_s ** 2
+            dflag |= np.any(inside & (np.abs(d2 - cfg.r_s ** 2) <= dmarg), axis=1)
+            sel = inside & (d2 <= cfg.r_s ** 2)
+            pidx = np.where(sel, jj * Ws + ii, 0)
+            sel_l.append(sel)
+            w_l.append(np.where(sel, 2.0 ** -s * np.exp(-d2 / (2.0 * cfg.sigma_w ** 2)), 0.0))
+            m_l.append(np.where(sel, Mv[pidx] if Mv.size else 0.0, 0.0))
+            e_l.append(np.where(sel, Ev[pidx] if Ev.size else 0.0, 0.0))
+            d_l.append(np.where(sel, Dv[pidx] if Dv.size else 0.0, -np.inf))
+        disk_flag[c0:c1] = dflag
+        sel = np.concatenate(sel_l, axis=1)
+        w = np.concatenate(w_l, axis=1)
+        mps = np.concatenate(m_l, axis=1)
+        es = np.concatenate(e_l, axis=1)
         cnt = sel.sum(1)
-        pidx = np.where(sel, jj * W + ii, 0)
-        dmax = np.where(sel, d_rend[pidx], -np.inf).max(1)
+        dmax = np.concatenate(d_l, axis=1).max(1)
         lim = dmax + cfg.vis_tol
         occl = (cfg.vis_tol > 0) & (dmax > 0) & (z > lim)
         vis_flag[c0:c1] = (cfg.vis_tol > 0) & (dmax > 0) & (np.abs(z - lim) <= 1e-5 * np.abs(lim))
         obs = (cnt > 0) & ~occl
-        w = np.where(sel, np.exp(-d2 / (2.0 * cfg.sigma_w ** 2)), 0.0)
-        mps = np.where(sel, M_p[pidx], 0.0)
-        es = np.where(sel, e[pidx], 0.0)
         cntf = np.maximum(cnt, 1)
         with np.errstate(invalid="ignore", divide="ignore"):
             mh = (w * mps).sum(1) / w.sum(1)                      # Eq. (8)

@@ -274,3 +274,132 @@ def test_external_map_closed_forms():
     r = M.mp_update(*args, mp_map=one)
     d2 = np.array([0, 1, 1, 1, 1, 2, 2, 2, 2, 4, 4, 4, 4], float)
     np.testing.assert_allclose(r["m_hat"], 1.0 / np.exp(-d2 / 2).sum(), rtol=1e-12)
+
+
+def test_pyramid_levels_closed_form():
+    # the 2x2 box mean of a linear ramp is the ramp at the block centre, the
+    # 2x2 max its value at the block's far corner; odd sizes drop the last
+    # row and column
+    w, h = 7, 5
+    jj, ii = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    ramp = 0.3 * ii + 0.05 * jj + 1.0
+    lv = M.pyramid(ramp.ravel(), w, h, 3, "mean")
+    assert [(a.size, ws, hs) for a, ws, hs in lv] == [(35, 7, 5), (6, 3, 2), (1, 1, 1)]
+    J, I = np.meshgrid(np.arange(2), np.arange(3), indexing="ij")
+    np.testing.assert_allclose(lv[1][0], (0.3 * (2 * I + 0.5) + 0.05 * (2 * J + 0.5) + 1.0).ravel(), rtol=1e-14)
+    np.testing.assert_allclose(lv[2][0], [0.3 * 1.5 + 0.05 * 1.5 + 1.0], rtol=1e-14)
+    mx = M.pyramid(ramp.ravel(), w, h, 2, "max")
+    np.testing.assert_allclose(mx[1][0], (0.3 * (2 * I + 1) + 0.05 * (2 * J + 1) + 1.0).ravel(), rtol=1e-14)
+
+
+def _at_pixel(i, j, z):
+    return np.array([[(i - 12.0) * z / 30.0, (j - 10.0) * z / 30.0, z]])
+
+
+def test_multiscale_association_closed_form():
+    # r_s = 0.5 keeps one pixel per level: (8, 8) at level 0, (4, 4) at
+    # level 1, (2, 2) at level 2, each at distance 0; on the map
+    # M(i, j) = i / 100 + j / 1000 they hold 0.088, the mean over i, j in
+    # {8, 9} (0.0935) and over i, j in 8..11 (0.1045), weighted 1, 1/2, 1/4
+    jj, ii = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    mp_map = (ii / 100.0 + jj / 1000.0).ravel()
+    inst, d_obs, c, d_rend, c2 = flat_obs()
+    vals = np.array([0.088, 0.0935, 0.1045])
+    wts = np.array([1.0, 0.5, 0.25])
+    for S in (1, 2, 3):
+        cfg = M.MPConfig(r_s=0.5, scales=S, alpha_min=1.0, alpha_max=1.0)
+        r = M.mp_update(_at_pixel(8, 8, 2.0), np.array([0.5]), np.zeros(1, np.uint8), CAM, synth.identity_pose(),
+                        inst, d_obs, c, d_rend, c2, TABLE, cfg, mp_map=mp_map)
+        v, wt = vals[:S], wts[:S]
+        assert r["observed"][0]
+        np.testing.assert_allclose(r["m_hat"], (wt * v).sum() / wt.sum(), rtol=1e-13)
+        np.testing.assert_allclose(r["var"], ((v - v.mean()) ** 2).mean(), rtol=1e-12, atol=1e-18)
+        np.testing.assert_allclose(r["mp"], (wt * v).sum() / wt.sum(), rtol=1e-13)
+
+
+def test_multiscale_reaches_past_the_image_edge():
+    # projected at u = -3: the level-0 disk of radius 2 is empty; at level 1
+    # (u = -1.5, v = 5) column 0 holds rows 4, 5, 6
+    inst, d_obs, c, d_rend, c2 = flat_obs()
+    means = _at_pixel(-3, 10, 2.0)
+    for S, seen in ((1, False), (2, True), (3, True)):
+        r = M.mp_update(means, np.array([0.5]), np.zeros(1, np.uint8), CAM, synth.identity_pose(), inst, d_obs, c,
+                        d_rend, c2, TABLE, M.MPConfig(scales=S, alpha_min=1.0, alpha_max=1.0),
+                        mp_map=np.full(W * H, 0.7))
+        assert r["observed"][0] == seen
+        if seen:
+            np.testing.assert_allclose(r["mp"], 0.7, rtol=1e-14)
+        else:
+            assert r["mp"][0] == 0.5
+
+
+def test_multiscale_occlusion_uses_the_max_pooled_depth():
+    # rendered depth 1 except 3 at pixel (9, 9); a Gaussian at depth 2.5 on
+    # pixel (8, 8), r_s = 0.5: alone, level 0 puts it behind the surface
+    # (2.5 > 1 + 0.1); level 1's pixel (4, 4) covers (9, 9) and its max-pooled
+    # depth 3 makes it visible (a box mean, 1.5, would not)
+    inst, d_obs, c, d_rend, c2 = flat_obs(d_rend=1.0)
+    d_rend = d_rend.copy()
+    d_rend[9 * W + 9] = 3.0
+    for S, seen in ((1, False), (2, True)):
+        r = M.mp_update(_at_pixel(8, 8, 2.5), np.array([0.5]), np.zeros(1, np.uint8), CAM, synth.identity_pose(),
+                        inst, d_obs, c, d_rend, c2, TABLE, M.MPConfig(r_s=0.5, scales=S))
+        assert r["observed"][0] == seen
+
+
+def test_multiscale_against_brute_force():
+    # every pixel of every level visited one by one, the pyramid built by
+    # explicit loops, odd image sizes
+    w, h = 13, 11
+    cam = (14.0, 14.0, 6.3, 5.1, w, h)
+    rng = np.random.default_rng(21)
+    n = 40
+    z = rng.uniform(1.0, 3.0, n)
+    u = rng.uniform(-4.0, w + 3.0, n)
+    v = rng.uniform(-4.0, h + 3.0, n)
+    means = np.stack([(u - 6.3) * z / 14.0, (v - 5.1) * z / 14.0, z], 1)
+    inst = (rng.random(w * h) < 0.3).astype(np.uint8)
+    d_rend = rng.uniform(1.0, 3.5, w * h)
+    d_obs = d_rend + rng.normal(0, 0.1, w * h)
+    c_obs, c_rend = rng.uniform(0, 1, (w * h, 3)), rng.uniform(0, 1, (w * h, 3))
+    cfg = M.MPConfig(r_s=1.7, sigma_w=1.3, scales=3, vis_tol=0.3)
+    r = M.mp_update(means, rng.uniform(0.05, 0.95, n), np.zeros(n, np.uint8), cam, synth.identity_pose(), inst,
+                    d_obs, c_obs, d_rend, c_rend, TABLE, cfg)
+    px = M.pixel_mp(inst, d_obs, c_obs, d_rend, c_rend, TABLE, cfg, (w, h))
+
+    def down(grid, pool):
+        hh, ww = len(grid) // 2, len(grid[0]) // 2
+        out = [[0.0] * ww for _ in range(hh)]
+        for J in range(hh):
+            for I in range(ww):
+                q = [grid[2 * J + a][2 * I + b] for a in (0, 1) for b in (0, 1)]
+                out[J][I] = sum(q) / 4.0 if pool == "mean" else max(q)
+        return out
+
+    levels = []
+    g = [[(px["M_p"][j * w + i], px["e"][j * w + i], d_rend[j * w + i]) for i in range(w)] for j in range(h)]
+    gm, ge, gd = ([[t[k] for t in row] for row in g] for k in range(3))
+    for s in range(3):
+        levels.append((gm, ge, gd))
+        gm, ge, gd = down(gm, "mean"), down(ge, "mean"), down(gd, "max")
+    for k in range(n):
+        mem = []
+        for s, (lm, le, ld) in enumerate(levels):
+            for j in range(len(lm)):
+                for i in range(len(lm[0]) if lm else 0):
+                    d2 = (i - u[k] / 2 ** s) ** 2 + (j - v[k] / 2 ** s) ** 2
+                    if d2 <= cfg.r_s ** 2:
+                        mem.append((2.0 ** -s * np.exp(-d2 / (2 * cfg.sigma_w ** 2)), lm[j][i], le[j][i], ld[j][i]))
+        if r["disk_flag"][k] or r["vis_flag"][k]:
+            continue
+        seen = bool(mem) and not (max(t[3] for t in mem) > 0 and z[k] > max(t[3] for t in mem) + cfg.vis_tol)
+        assert r["observed"][k] == seen
+        if not seen:
+            continue
+        wt = np.array([t[0] for t in mem])
+        mv = np.array([t[1] for t in mem])
+        ev = np.array([t[2] for t in mem])
+        np.testing.assert_allclose(r["m_hat"][k], (wt * mv).sum() / wt.sum(), rtol=1e-12)
+        np.testing.assert_allclose(r["var"][k], mv.var(), rtol=1e-10, atol=1e-15)
+        np.testing.assert_allclose(r["sigma_e"][k], ev.std(), rtol=1e-10, atol=1e-15)
+    assert r["observed"].sum() > 15
