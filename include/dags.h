@@ -313,11 +313,13 @@ typedef struct {
   float z_near;      /* m (0.2)                                                            */
   float tau_floor;   /* Eq. (12) (0.5)                                                     */
   int32_t fusion_mode;  /* 0 fused, 1 K = 0 (MP_ins only), 2 K = 1 (MP_geo only)           */
+  int32_t scales;       /* pyramid levels S of the association, Eq. (1), 1..DAGS_MP_MAX_SCALES (1) */
 } dags_mp_cfg;
 
 void dags_default_mp_cfg(dags_mp_cfg *cfg);
 
 #define DAGS_MP_MAX_REGIONS 256
+#define DAGS_MP_MAX_SCALES 3
 #define DAGS_MP_STATS_HEAD 6
 
 /* Spatiotemporal MP update of one view (Sec. IV-A, Eqs. (1)-(12); Eq. (17)).
@@ -331,10 +333,13 @@ void dags_default_mp_cfg(dags_mp_cfg *cfg);
  * instance and, for a background pixel, the population std of e over the
  * pixel's own disk {di^2 + dj^2 <= r_s^2} clipped to the image (its
  * associated neighbourhood, the sentence after Eq. (7)); fusion, Eqs. (6),(7),
- * stored per pixel in the ctx. Per Gaussian (in FP32): the pixels within r_s of its
- * projected mean, Eq. (1), weighted exp(-d^2 / (2 sigma_w^2)); observed iff
- * z > z_near, the disk is non-empty and z <= max rendered depth over the disk
- * + vis_tol; M_hat, Eq. (8); U, Eq. (10), min-max normalised over the
+ * stored per pixel in the ctx. Per Gaussian (in FP32): N(G), Eq. (1), the
+ * union over pyramid levels s = 0 .. scales-1 of the level-s pixels within
+ * r_s of its projected mean / 2^s, weighted 2^-s exp(-d^2 / (2 sigma_w^2))
+ * (level s + 1: 2x2 box means of level s for M_p and e, 2x2 maxima for the
+ * rendered depth, an odd last row or column dropped; scales = 1 is the
+ * single-scale disk); observed iff z > z_near, N(G) is non-empty and
+ * z <= max rendered depth over N(G) + vis_tol; M_hat, Eq. (8); U, Eq. (10), min-max normalised over the
  * observed Gaussians; alpha, Eq. (11), times rho unless seg_refreshed,
  * Eq. (17); M^t, Eq. (9), written into word 11 of each observed record.
  * Per frame: tau = max(lower median of M^t over observed, tau_floor), Eq. (12);

@@ -333,6 +333,7 @@ int dags_create(dags_ctx **out, int64_t max_gaussians, int32_t max_width, int32_
   MpBuffers &mb = c->mp;
   A(alloc(&mb.e, (size_t)max_width * max_height));
   A(alloc(&mb.mpf, (size_t)max_width * max_height));
+  A(alloc(&mb.pyr, mp_pyramid_floats(max_width, max_height)));
   A(alloc(&mb.acc, (size_t)DAGS_MP_MAX_REGIONS * 4));
   A(alloc(&mb.mhat, (size_t)w.max_n));
   A(alloc(&mb.sige, (size_t)w.max_n));
@@ -1143,6 +1144,7 @@ void dags_default_mp_cfg(dags_mp_cfg *c) {
   c->z_near = 0.2f;
   c->tau_floor = 0.5f;
   c->fusion_mode = 0;
+  c->scales = 1;
 }
 
 int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, const double *pose,
@@ -1160,7 +1162,7 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
   else dags_default_mp_cfg(&c);
   if (!(c.r_s > 0.f) || !(c.sigma_w > 0.f) || !(c.sigma_g > 0.f) || !(c.sigma_c > 0.f) || !(c.e_floor > 0.f) ||
       !(c.alpha_min >= 0.f && c.alpha_min <= c.alpha_max && c.alpha_max <= 1.f) || !(c.rho >= 0.f && c.rho <= 1.f) ||
-      c.fusion_mode < 0 || c.fusion_mode > 2 || c.r_s > 64.f)
+      c.fusion_mode < 0 || c.fusion_mode > 2 || c.r_s > 64.f || c.scales < 1 || c.scales > DAGS_MP_MAX_SCALES)
     return DAGS_E_INVAL;
   Raster r;
   if ((rc = make_raster(cam, nullptr, &r))) return rc;

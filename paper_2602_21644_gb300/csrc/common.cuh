@@ -272,9 +272,19 @@ cudaError_t launch_mpnet_train(void *weights, float *master, float *adam_m, floa
                                double *loss, const MpnetScratch &sc, uint32_t *status, int num_sms, cudaStream_t s);
 
 // Buffers of the MP update (owned by the ctx).
+// Floats of the association pyramid's levels 1 .. DAGS_MP_MAX_SCALES-1 for
+// a W x H frame: three maps (M_p, e, rendered depth) per level, level s of
+// (W >> s) x (H >> s) pixels.
+inline size_t mp_pyramid_floats(int W, int H) {
+  size_t t = 0;
+  for (int s = 1; s < DAGS_MP_MAX_SCALES; ++s) t += 3 * (size_t)(W >> s) * (size_t)(H >> s);
+  return t > 0 ? t : 1;
+}
+
 struct MpBuffers {
   float *e = nullptr;                 // [max_w * max_h]
   float *mpf = nullptr;               // [max_w * max_h] fused per-pixel M_p
+  float *pyr = nullptr;               // [mp_pyramid_floats] levels 1.. of the association pyramid
   double *acc = nullptr;              // [DAGS_MP_MAX_REGIONS * 4]
   float *mhat = nullptr, *sige = nullptr, *U = nullptr, *Mt = nullptr, *Ut = nullptr;  // [max_n]
   uint8_t *obs = nullptr;             // [max_n]

@@ -11,10 +11,16 @@
 //                         instance claims uses the dispersion of e over the
 //                         pixel's own disk of radius r_s (its associated
 //                         neighbourhood); stored for the gather
-//   mp_gauss_kernel       per Gaussian: projection, the association disk
-//                         N(G), Eq. (1), over the stored M_p (or the caller's
-//                         map); M_hat, Eq. (8); Var{M_p}; sigma_e,G; U,
-//                         Eq. (10); CTA min/max of U -> global
+//   mp_pyramid_kernel     per pixel of pyramid level s >= 1 (only when the
+//                         association uses S > 1 levels): the 2x2 box mean
+//                         of level s - 1 for M_p and e, the 2x2 max for the
+//                         rendered depth
+//   mp_gauss_kernel       per Gaussian: projection, the association N(G),
+//                         Eq. (1), the union over the levels of the disks of
+//                         radius r_s around pi(G) / 2^s, over the stored M_p
+//                         (or the caller's map); M_hat, Eq. (8), with weights
+//                         2^-s exp(-d^2 / (2 sigma_w^2)); Var{M_p}; sigma_e,G;
+//                         U, Eq. (10); CTA min/max of U -> global
 //   mp_apply_kernel       per observed Gaussian: normalised U, C, alpha,
 //                         Eqs. (11), (17); M^t, Eq. (9), written into the
 //                         record; first radix-select level of the two medians
@@ -40,8 +46,10 @@ constexpr int kSelBins = 2048;
 struct MpCfg {
   float kappa_c, lam, sigma_min, e_floor, sigma_g, sigma_c, lam_u, eps, alpha_min, alpha_max, rho, r_s, sigma_w,
       vis_tol, z_near, tau_floor;
-  int fusion_mode, seg_refreshed, n_regions;
+  int fusion_mode, seg_refreshed, n_regions, scales;
 };
+
+constexpr int kMaxScales = DAGS_MP_MAX_SCALES;
 
 // Workspace of the update (carved from the ctx's MP buffers).
 struct MpWs {
@@ -57,6 +65,10 @@ struct MpWs {
   float *mp_pixel;       // [P] out: the fused M_p, or null
   float *mpf;            // [P] the fused M_p (workspace)
   uint32_t *status;      // the ctx's status word (index checks of a DAGS_CHECK build)
+  // association pyramid, level s: M_p (or the external map), e and the
+  // rendered depth as row-major Ws x Hs maps (level 0: the frame's own)
+  const float *lm[kMaxScales], *le[kMaxScales], *ld[kMaxScales];
+  int lw[kMaxScales], lh[kMaxScales];
 };
 
 // The region of pixel p (its instance label; checked against the table size
@@ -237,6 +249,35 @@ mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__re
   }
 }
 
+// Level s of the association pyramid from level s - 1: each pixel covers a
+// 2x2 block; M_p and e take the block's mean, the rendered depth its maximum
+// (the occlusion test's maximum over a level-s pixel is then the maximum over
+// the full-resolution pixels it covers).
+__global__ void __launch_bounds__(kMpBlock)
+mp_pyramid_kernel(MpWs m, int s, float *__restrict__ om, float *__restrict__ oe, float *__restrict__ od) {
+  const int W = m.lw[s], H = m.lh[s], Wp = m.lw[s - 1];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= W * H) return;
+  const int x = q % W, y = q / W;
+  const size_t a = (size_t)(2 * y) * Wp + 2 * x, b = a + Wp;
+  const float *__restrict__ im = m.lm[s - 1], *__restrict__ ie = m.le[s - 1], *__restrict__ id = m.ld[s - 1];
+  om[q] = ((im[a] + im[a + 1]) + (im[b] + im[b + 1])) * 0.25f;
+  oe[q] = ((ie[a] + ie[a + 1]) + (ie[b] + ie[b + 1])) * 0.25f;
+  od[q] = fmaxf(fmaxf(id[a], id[a + 1]), fmaxf(id[b], id[b + 1]));
+}
+
+// The pixel rectangle of the disk of radius r_s around (us, vs) clipped to a
+// Ws x Hs level; false when it is empty (or the centre is not finite).
+__device__ __forceinline__ bool disk_rect(float us, float vs, int Ws, int Hs, float r_s, int *i0, int *i1, int *j0,
+                                          int *j1) {
+  if (!(us > -r_s - 1.f && us < (float)Ws + r_s && vs > -r_s - 1.f && vs < (float)Hs + r_s)) return false;
+  *i0 = (int)fmaxf(ceilf(us - r_s), 0.f);
+  *i1 = (int)fminf(floorf(us + r_s), (float)(Ws - 1));
+  *j0 = (int)fmaxf(ceilf(vs - r_s), 0.f);
+  *j1 = (int)fminf(floorf(vs + r_s), (float)(Hs - 1));
+  return *i0 <= *i1 && *j0 <= *j1;
+}
+
 __global__ void __launch_bounds__(kMpBlock)
 mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
                 const float *__restrict__ image, Raster r, MpCfg c) {
@@ -255,25 +296,30 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
     bool observed = false;
     float mhat = 0.f, var = 0.f, sige = 0.f;
     const float u = r.fx * x / z + r.cx, v = r.fy * y / z + r.cy;
-    if (z > c.z_near && u > -c.r_s - 1.f && u < (float)r.W + c.r_s && v > -c.r_s - 1.f &&
-        v < (float)r.H + c.r_s) {
-      const size_t P = (size_t)r.W * r.H;
+    if (z > c.z_near) {
       const float rs2 = c.r_s * c.r_s, inv2s2 = 1.f / (2.f * c.sigma_w * c.sigma_w);
-      const int i0 = (int)fmaxf(ceilf(u - c.r_s), 0.f), i1 = (int)fminf(floorf(u + c.r_s), (float)(r.W - 1));
-      const int j0 = (int)fmaxf(ceilf(v - c.r_s), 0.f), j1 = (int)fminf(floorf(v + c.r_s), (float)(r.H - 1));
       float sw = 0.f, swm = 0.f, sm = 0.f, se = 0.f, dmax = -INFINITY;
       int cnt = 0;
-      if (i0 <= i1 && j0 <= j1) {
+#pragma unroll
+      for (int s = 0; s < kMaxScales; ++s) {
+        if (s >= c.scales) break;
+        const float sc = 1.f / (float)(1 << s);              // 2^-s: exact
+        const float us = u * sc, vs = v * sc;
+        const int Ws = m.lw[s];
+        int i0, i1, j0, j1;
+        if (!disk_rect(us, vs, Ws, m.lh[s], c.r_s, &i0, &i1, &j0, &j1)) continue;
+        const float *__restrict__ lm = s == 0 ? mpsrc : m.lm[s];
+        const float *__restrict__ le = m.le[s], *__restrict__ ld = m.ld[s];
         for (int jj = j0; jj <= j1; ++jj)
           for (int ii = i0; ii <= i1; ++ii) {
-            const float dx = (float)ii - u, dy = (float)jj - v, d2 = dx * dx + dy * dy;
+            const float dx = (float)ii - us, dy = (float)jj - vs, d2 = dx * dx + dy * dy;
             if (d2 > rs2) continue;
-            const size_t p = (size_t)jj * r.W + ii;
-            const float e = m.e[p];
-            const float mp = mpsrc[p];
-            const float w = expf(-d2 * inv2s2);
+            const size_t p = (size_t)jj * Ws + ii;
+            const float e = le[p];
+            const float mp = lm[p];
+            const float w = sc * expf(-d2 * inv2s2);
             sw += w; swm += w * mp; sm += mp; se += e; ++cnt;
-            dmax = fmaxf(dmax, image[3 * P + p]);
+            dmax = fmaxf(dmax, ld[p]);
           }
       }
       observed = cnt > 0 && !(c.vis_tol > 0.f && dmax > 0.f && z > dmax + c.vis_tol);
@@ -281,16 +327,27 @@ mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const doubl
         mhat = swm / sw;
         const float mm = sm / cnt, me = se / cnt;
         float vm = 0.f, ve = 0.f;
-        for (int jj = j0; jj <= j1; ++jj)
-          for (int ii = i0; ii <= i1; ++ii) {
-            const float dx = (float)ii - u, dy = (float)jj - v;
-            if (dx * dx + dy * dy > rs2) continue;
-            const size_t p = (size_t)jj * r.W + ii;
-            const float e = m.e[p];
-            const float mp = mpsrc[p];
-            vm += (mp - mm) * (mp - mm);
-            ve += (e - me) * (e - me);
-          }
+#pragma unroll
+        for (int s = 0; s < kMaxScales; ++s) {
+          if (s >= c.scales) break;
+          const float sc = 1.f / (float)(1 << s);
+          const float us = u * sc, vs = v * sc;
+          const int Ws = m.lw[s];
+          int i0, i1, j0, j1;
+          if (!disk_rect(us, vs, Ws, m.lh[s], c.r_s, &i0, &i1, &j0, &j1)) continue;
+          const float *__restrict__ lm = s == 0 ? mpsrc : m.lm[s];
+          const float *__restrict__ le = m.le[s];
+          for (int jj = j0; jj <= j1; ++jj)
+            for (int ii = i0; ii <= i1; ++ii) {
+              const float dx = (float)ii - us, dy = (float)jj - vs;
+              if (dx * dx + dy * dy > rs2) continue;
+              const size_t p = (size_t)jj * Ws + ii;
+              const float e = le[p];
+              const float mp = lm[p];
+              vm += (mp - mm) * (mp - mm);
+              ve += (e - me) * (e - me);
+            }
+        }
         var = vm / cnt;
         sige = sqrtf(ve / cnt);
       }
@@ -516,7 +573,30 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   c.alpha_min = cfg.alpha_min; c.alpha_max = cfg.alpha_max; c.rho = cfg.rho; c.r_s = cfg.r_s;
   c.sigma_w = cfg.sigma_w; c.vis_tol = cfg.vis_tol; c.z_near = cfg.z_near; c.tau_floor = cfg.tau_floor;
   c.fusion_mode = cfg.fusion_mode; c.seg_refreshed = seg_refreshed; c.n_regions = n_regions;
+  c.scales = cfg.scales < 1 ? 1 : (cfg.scales > kMaxScales ? kMaxScales : cfg.scales);
   const int P = r.W * r.H;
+  // the association pyramid: level 0 is the frame's own maps, levels 1.. are
+  // carved from b.pyr (M_p, e, depth per level)
+  float *pyr_out[kMaxScales][3] = {};
+  {
+    float *cur = b.pyr;
+    for (int s = 0; s < kMaxScales; ++s) {
+      m.lw[s] = r.W >> s;
+      m.lh[s] = r.H >> s;
+      if (s == 0) {
+        m.lm[0] = mp_map ? mp_map : b.mpf;
+        m.le[0] = b.e;
+        m.ld[0] = image + 3 * (size_t)P;
+        continue;
+      }
+      const size_t Ps = (size_t)m.lw[s] * m.lh[s];
+      for (int k = 0; k < 3; ++k) pyr_out[s][k] = cur + k * Ps;
+      cur += 3 * Ps;
+      m.lm[s] = pyr_out[s][0];
+      m.le[s] = pyr_out[s][1];
+      m.ld[s] = pyr_out[s][2];
+    }
+  }
   // the region accumulators start at zero (the select state is cleared by
   // the first kernel)
   cudaError_t e = cudaMemsetAsync(b.acc, 0, DAGS_MP_MAX_REGIONS * 4 * sizeof(double), s);
@@ -527,6 +607,12 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   mp_pixel_var_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, P, c);
   if (!mp_map || mp_pixel)
     mp_pixel_map_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, reinterpret_cast<const float2 *>(table), r.W, r.H, c);
+  for (int l = 1; l < c.scales; ++l) {
+    const int Pl = m.lw[l] * m.lh[l];
+    if (Pl > 0)
+      mp_pyramid_kernel<<<(unsigned)((Pl + kMpBlock - 1) / kMpBlock), kMpBlock, 0, s>>>(m, l, pyr_out[l][0],
+                                                                                        pyr_out[l][1], pyr_out[l][2]);
+  }
   mp_gauss_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<const float4 *>(gauss), n, pose, image, r, c);
   mp_apply_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<float4 *>(gauss), n, c);
   mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 1, c);

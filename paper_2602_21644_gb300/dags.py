@@ -52,7 +52,8 @@ class CLossCfg(ctypes.Structure):
 class CMpCfg(ctypes.Structure):
     _fields_ = [(k, ctypes.c_float) for k in ("kappa_c", "lam", "sigma_min", "e_floor", "sigma_g", "sigma_c",
                                               "lam_u", "eps", "alpha_min", "alpha_max", "rho", "r_s", "sigma_w",
-                                              "vis_tol", "z_near", "tau_floor")] + [("fusion_mode", ctypes.c_int32)]
+                                              "vis_tol", "z_near", "tau_floor")] + [("fusion_mode", ctypes.c_int32),
+                                                                                    ("scales", ctypes.c_int32)]
 
 
 class CSchedCfg(ctypes.Structure):

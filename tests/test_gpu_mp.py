@@ -168,3 +168,32 @@ def test_mpnet_features_match_oracle(dags):
     ctx.check()
     ref = N.features(image[5], image[0:3].T, image[3], image[4], tg[:, 0:3], tg[:, 3], inst, table)
     np.testing.assert_array_equal(f.float().cpu().numpy().reshape(P, 8), ref)
+
+
+@pytest.mark.parametrize("scales,size,frame", [(2, (320, 240), 40), (3, (320, 240), 40), (3, (251, 187), 25)])
+def test_mp_update_multiscale(dags, scales, size, frame):
+    # Eq. (1)'s union over pyramid levels: the pyramid is built from the
+    # frame's M_p, e and rendered depth on the device; odd sizes drop the last
+    # row and column of a level
+    d = mp_scene(60_000, frame, *size, seed=5)
+    gpu, ref = run_both(dags, d, {"scales": scales})
+    check(gpu, ref, d["table"].shape[0])
+    plain, _ = run_both(dags, d)
+    assert np.abs(gpu["mp"] - plain["mp"]).max() > 1e-3        # the coarser levels are used
+
+
+def test_mp_update_multiscale_external_map_full_size(dags):
+    d = mp_scene(300_000, 20, 640, 480, seed=6)
+    cam = d["cam"]
+    jj, ii = np.meshgrid(np.arange(cam.height), np.arange(cam.width), indexing="ij")
+    mp_map = (0.5 + 0.45 * np.sin(ii / 17.0) * np.cos(jj / 23.0)).astype(np.float32).ravel()
+    gpu, ref = run_both(dags, d, {"scales": 3}, mp_map=mp_map)
+    check(gpu, ref, d["table"].shape[0])
+
+
+@pytest.mark.parametrize("scales", [0, 4])
+def test_mp_update_rejects_bad_scales(dags, scales):
+    d = mp_scene(2_000, 5, 160, 120)
+    with pytest.raises(dags.DagsError) as e:
+        run_both(dags, d, {"scales": scales})
+    assert e.value.code == -1                                   # DAGS_E_INVAL
