@@ -134,64 +134,78 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // Forward kernel: kGroups warpgroups per CTA, each running its own stream
 // of work units with its own operands, TMEM columns and mbarriers. A
 // warpgroup is four epilogue warps (TMEM lane quadrants 0..3: 128 pixels)
-// and one control warp whose lane 0 issues the MMAs and the TMA fetches, so
-// that the tensor core runs one step's MMAs while the epilogue warps convert
-// the previous results.
+// and one control warp whose lane 0 issues the MMAs and the TMA fetches.
 //
 // Work unit: a 128-pixel-wide column strip of one image over a segment of
 // output rows [y0, y1). The warpgroup walks down the strip computing a1 for
-// one 130-pixel halo row at a time (rows y0 - 1 .. y1; x0 - 1 .. x0 + 128)
-// into a ring of row slots; every a1 row is computed once per unit (plus two
-// boundary rows), not three times as with independent row tiles.
+// one 130-pixel halo row at a time (rows y0 - 1 .. y1; x0 - 1 .. x0 + 128);
+// every a1 row is computed once per unit (plus two boundary rows).
 //
-// Pipeline, step k (the control warp / the epilogue warps):
-//   control: wait for the previous step's epilogues (D1 and D3 read, a2
-//     written); batch 1 = z1 of a1 row k (halo pixels 0..127) and z3 of
-//     output row k - 4, one commit (which also covers the previous step's
-//     z2); wait for epilogue 1; fetch the input of a1 row k + 2 by TMA into
-//     the buffer row k used; batch 2 = z2 of output row k - 2 (a1 rows
-//     k - 2 .. k) into the D2 buffer of this step's parity.
-//   epilogues: wait for the commit; epilogue 1 (a1 row k into its slot; the
-//     halo pixels 128 and 129 on the CUDA cores); epilogue 2 (a2 of output
-//     row k - 3 from the other D2 buffer); epilogue 3 (a3, the dot product
-//     with w4 and the sigmoid of output row k - 4).
-// Batch 2 runs on the tensor core while the epilogue warps run epilogues 2
-// and 3. Three ring slots, one a2 buffer and two D2 buffers suffice: every
-// buffer is rewritten only after the barrier that follows its last reader.
-// Out-of-image rows and columns read as zero.
+// The 3 x 3 convolution reads each a1 row once: a1 row k meets all three
+// kernel rows in one N = 96 product (K = the three column taps x 32
+// channels), whose 32-column thirds go to the outputs k, k - 1 and k - 2
+// (kernel rows 0, 1, 2). Output j accumulates in TMEM slot j mod 3 of a ring
+// of three; because the thirds of one MMA are contiguous columns, the kernel
+// rows are stacked in the order that puts each into the slot of its output
+// (one of three row permutations of the weights, chosen by k mod 3). A slot
+// starts as the layer-2 bias: a K = 16 MMA of per-row constants (1, 1, 0, ...)
+// with the bias as a BF16 column pair (hi, lo), before the first product
+// that reaches it. The A operand of an MMA is read from shared memory once
+// per instruction, so one N = 96 product per row costs about as much as
+// 1.4 products of N = 32 instead of three.
+//
+// Pipeline, step s of a unit with nO output rows (nA = nO + 2 a1 rows):
+//   control: wait for the previous step's epilogues; fetch the input of a1
+//     row s + 2; z1 of a1 row s (s < nA), commit; z3 of output row s - 4
+//     (4 <= s <= nA + 1), commit; the bias of slot (s - 1) mod 3 and the
+//     product of a1 row s - 1 (1 <= s <= nA), commit.
+//   epilogues: epilogue 1 once z1 is done (a1 row s into buffer s mod 2; the
+//     halo pixels 128 and 129 on the CUDA cores); epilogue 3 once z3 is done
+//     (a3, the dot product with w4 and the sigmoid of output row s - 4);
+//     epilogue 2 once the product is done (output row s - 3 complete in slot
+//     s mod 3: a2 into its buffer).
+// The product runs on the tensor core while epilogues 1 and 3 run. Every
+// buffer is rewritten only after the barrier that follows its last reader:
+// the a1 buffer s mod 2 was last read by the product of step s - 1, which
+// the commits of step s cover; the a2 buffer by the z3 of step s; a slot
+// is re-biased one step after epilogue 2 read it. Out-of-image rows and
+// columns read as zero.
 //
 // Operand layouts (no swizzle): "row-contiguous chunks" - chunk c holds
 // channels 8c..8c+7 of every row as one 16-byte line, rows consecutive (SBO =
 // 128 B between 8-row groups, LBO = the chunk stride). An MMA may then start
-// at any row, which makes the 3 x 3 convolution an implicit GEMM: tap (ky, kx)
-// reads the slot of a1 row y - 1 + ky at rows kx + p directly, no im2col.
+// at any row, which makes the 3 x 3 convolution an implicit GEMM: column tap
+// kx reads the a1 row at rows kx + p directly, no im2col.
 //
-// The first layer's bias rides in its MMA: a K-chunk of per-row constants
-// (1, 1, 0, ..., 0) meets a B column pair (hi, lo) with hi = bf16(b1), lo =
-// bf16(b1 - hi) (|hi + lo - b1| <= 2^-17 |b1|). The second and third layers'
-// biases are added in FP32 in the epilogues, before the ReLU + BF16 rounding
-// (one conversion per pair).
-constexpr int kGroups = 4;
+// The first layer's bias rides in its MMA the same way as the second's:
+// a K-chunk of per-row constants (1, 1, 0, ..., 0) meets a B column pair
+// (hi, lo) with hi = bf16(b), lo = bf16(b - hi) (|hi + lo - b| <= 2^-17 |b|).
+// The third layer's bias is added in FP32 in its epilogue.
+constexpr int kGroups = 3;
 constexpr int kFwdThreads = 160 * kGroups;              // 4 epilogue warps + 1 control warp per warpgroup
-constexpr int kBars = 6;                                // mbarriers per warpgroup
+constexpr int kBars = 8;                                // mbarriers per warpgroup
 constexpr int kRowBytes = kHaloW * 16;                  // 2080 = the TMA box (8 x 130 x 1 x 1 bf16)
 constexpr int kInBuf = 2176;                            // one input row (+ pad)
+constexpr int kInBufs = 3;
 constexpr int kSlotRows = 136;
 constexpr int kSlotChunk = kSlotRows * 16;              // 2176
-constexpr int kSlotBytes = 4 * kSlotChunk;              // 8704
-constexpr int kSlots = 3;
+constexpr int kSlotBytes = 4 * kSlotChunk;              // 8704: one a1 row, four chunks
+constexpr int kA1Bufs = 2;
 constexpr int kA2Bytes = 4 * kTileW * 16;               // 8192
-// per warpgroup: in0, in1 (one input row each, at 0 and kInBuf), ones (the
-// first layer's bias chunk: 256 rows of (1, 1, 0, ...), of which an L1 MMA
-// reads 128), ring, a2.
-constexpr int kWgOnes = 2 * kInBuf, kWgRing = kWgOnes + 4096;
-constexpr int kWgA2 = kWgRing + kSlots * kSlotBytes;
-constexpr int kWgBytes = kWgA2 + kA2Bytes;              // 42752
-constexpr int kFW1 = kGroups * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 32 * kK2 * 2, kFB2 = kFW3 + 2048,
-              kFB3 = kFB2 + 1024, kFPar = kFB3 + 1024;
+// per warpgroup: three input rows, ones (the bias chunks: 256 rows of
+// (1, 1, 0, ...), of which an MMA reads 128 per K-chunk), two a1 rows, a2.
+constexpr int kWgOnes = kInBufs * kInBuf, kWgA1 = kWgOnes + 4096;
+constexpr int kWgA2 = kWgA1 + kA1Bufs * kSlotBytes;
+constexpr int kWgBytes = kWgA2 + kA2Bytes;              // 36224
+constexpr int kW2Perm = 96 * 96 * 2;                    // 18432: one stacking of the three kernel rows
+constexpr int kFW1 = kGroups * kWgBytes, kFW2 = kFW1 + 1024, kFW3 = kFW2 + 3 * kW2Perm, kFB2 = kFW3 + 2048,
+              kFB3 = kFB2 + 1024, kFW1f = kFB3 + 512, kFPar = kFW1f + 1024;
 constexpr int kFBar = kFPar + 256;
 constexpr int kFwdSmem = kFBar + 256 + 1024;            // + alignment slack
-constexpr uint32_t kWgCols = 128;                       // D1 +0..63, D2 +64..95, D3 +96..127
+constexpr uint32_t kWgCols = 160;                       // D1 +0..31, D3 +32..63, ring +64..159
+constexpr uint32_t kColD1 = 0, kColD3 = 32, kColRing = 64;
+static_assert(kGroups * kWgCols <= 512, "TMEM columns");
+static_assert(kFwdSmem <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -227,27 +241,26 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
                  uint32_t *__restrict__ status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3;
-  // FP32 copies: b2, b3 (added in the epilogues), b1 as its BF16 (hi, lo)
-  // pair and W1, for the two halo pixels computed on the CUDA cores
-  float *sb2f = reinterpret_cast<float *>(smem + kFB2), *sb3f = sb2f + kCh, *sb1h = sb2f + 2 * kCh,
-        *sb1l = sb2f + 3 * kCh;
-  float *sw1f = reinterpret_cast<float *>(smem + kFB3);   // [32][8]
+  uint8_t *sW1 = smem + kFW1, *sW2 = smem + kFW2, *sW3 = smem + kFW3, *sB2 = smem + kFB2;
+  // FP32 copies: b3 (added in its epilogue), b1 as its BF16 (hi, lo) pair and
+  // W1, for the two halo pixels computed on the CUDA cores
+  float *sb3f = reinterpret_cast<float *>(smem + kFB3), *sb1h = sb3f + kCh, *sb1l = sb3f + 2 * kCh;
+  float *sw1f = reinterpret_cast<float *>(smem + kFW1f);  // [32][8]
   float *sw4 = reinterpret_cast<float *>(smem + kFPar), *sb4 = sw4 + kCh;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kFBar);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + kFBar + 8 * kBars * kGroups);
   volatile uint32_t *s_fail = reinterpret_cast<volatile uint32_t *>(smem + kFBar + 8 * kBars * kGroups + 8);
-  // threads 0..511: four warpgroups of epilogue warps (warp w reads TMEM
-  // lane quadrant w % 4); threads 512..639: one control warp per warpgroup
+  // threads 0..4*32*kGroups-1: the warpgroups' epilogue warps (warp w reads
+  // TMEM lane quadrant w % 4); then one control warp per warpgroup
   const int tid = threadIdx.x, lane = tid & 31;
   const bool ctl = tid >= 4 * kGroups * 32;
   const int g = ctl ? (tid - 4 * kGroups * 32) >> 5 : tid >> 7, t = tid & 127, warp = t >> 5;
   uint8_t *wg = smem + g * kWgBytes;
-  uint8_t *sRing = wg + kWgRing, *sA2 = wg + kWgA2;
-  // per warpgroup: in0, in1 (TMA), mma (commits), e1 (epilogue 1 done),
-  // ep (all epilogues done), mma2 (the final drain)
-  uint64_t *bar_in = bars + kBars * g, *bar_mma = bar_in + 2, *bar_e1 = bar_in + 3, *bar_ep = bar_in + 4,
-           *bar_mma2 = bar_in + 5;
+  uint8_t *sA1 = wg + kWgA1, *sA2 = wg + kWgA2;
+  // per warpgroup: in0..in2 (TMA), z1, z3, prod (MMA commits), ep (all
+  // epilogues done), drain (the final wait)
+  uint64_t *bar_in = bars + kBars * g, *bar_z1 = bar_in + 3, *bar_z3 = bar_in + 4, *bar_prod = bar_in + 5,
+           *bar_ep = bar_in + 6, *bar_drain = bar_in + 7;
 
   // weights into the K-major core-matrix layouts; bias columns (hi, lo)
   const uint16_t *gw1 = reinterpret_cast<const uint16_t *>(weights + kOffW1);
@@ -261,13 +274,20 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     const float bias = gb1[o], hi = __bfloat162float(__float2bfloat16_rn(bias));
     const uint16_t v = k < 8 ? gw1[e] : k == 8 ? bf16_bits(bias) : k == 9 ? bf16_bits(bias - hi) : (uint16_t)0;
     *reinterpret_cast<uint16_t *>(sW1 + core_off(o, k, 16)) = v;
+    const float b2 = gb2[o], h2 = __bfloat162float(__float2bfloat16_rn(b2));
+    const uint16_t v2 = k == 0 ? bf16_bits(b2) : k == 1 ? bf16_bits(b2 - h2) : (uint16_t)0;
+    *reinterpret_cast<uint16_t *>(sB2 + core_off(o, k, 16)) = v2;
   }
-  for (int e = tid; e < 32 * kK2; e += kFwdThreads)
-    *reinterpret_cast<uint16_t *>(sW2 + core_off(e / kK2, e % kK2, kK2)) = gw2[e];
+  // the three stackings of the kernel rows: in stacking p, rows 32c + o hold
+  // output channel o of kernel row ky = (p - c) mod 3; K = kx * 32 + channel
+  for (int e = tid; e < 3 * 96 * 96; e += kFwdThreads) {
+    const int p = e / (96 * 96), n = (e / 96) % 96, kk = e % 96;
+    const int c = n >> 5, o = n & 31, kx = kk >> 5, ci = kk & 31, ky = (p - c + 3) % 3;
+    *reinterpret_cast<uint16_t *>(sW2 + p * kW2Perm + core_off(n, kk, 96)) = gw2[o * kK2 + (ky * 3 + kx) * kCh + ci];
+  }
   for (int e = tid; e < 32 * 32; e += kFwdThreads)
     *reinterpret_cast<uint16_t *>(sW3 + core_off(e / 32, e % 32, 32)) = gw3[e];
   for (int e = tid; e < kCh; e += kFwdThreads) {
-    sb2f[e] = gb2[e];
     sb3f[e] = gb3[e];
     const float hi = __bfloat162float(__float2bfloat16_rn(gb1[e]));
     sb1h[e] = hi;
@@ -286,9 +306,8 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
   if (tid == 0) {
     sb4[0] = reinterpret_cast<const float *>(weights + kOffB4)[0];
     for (int k = 0; k < kBars * kGroups; ++k) {
-      const int kind = k % kBars;   // e1 and ep: one arrival per epilogue warp
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + k)),
-                   "r"(kind == 3 || kind == 4 ? 4 : 1));
+      const int kind = k % kBars;   // ep: one arrival per epilogue warp
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + k)), "r"(kind == 6 ? 4 : 1));
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (int k = 0; k < kGroups; ++k) s_fail[k] = 0u;
@@ -315,19 +334,20 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
     *y0 = seg * units.seg_rows;
     *y1 = min(*y0 + units.seg_rows, H);
   };
-  uint32_t qbase = 0;          // a1 rows of the earlier units (input buffer parity)
-  uint32_t sc = 0;             // steps of the earlier units (barrier phases)
+  uint32_t qbase = 0;          // a1 rows of the earlier units (input buffer and phase)
+  uint32_t sc = 0;             // steps of the earlier units (epilogue barrier phase)
+  uint32_t n_z1 = 0, n_z3 = 0, n_prod = 0;   // commits so far on each MMA barrier
   if (ctl) {
     // ------------------------------------------------------------ control
     if (lane == 0) {
-      // bit 0/1 = TMA into in0/in1 pending (bit 8/9 = the parity of that
-      // fetch's phase), bit 2 = MMAs issued since the last waited commit
+      // bits 0..2 = TMA into in0..in2 pending (bits 8..10 = the parity of
+      // that fetch's phase), bit 3 = MMAs issued since the last waited commit
       uint32_t in_flight = 0;
       bool ok = true;
       auto fetch = [&](uint32_t q, int x0, int r, int b) {   // input of the q-th a1 row of this warpgroup
-        const uint32_t buf = q & 1u;
+        const uint32_t buf = q % kInBufs;
         tma_row(&in_map, wg_u32 + buf * kInBuf, bar_in + buf, x0 - 1, r, b);
-        in_flight = (in_flight & ~(0x101u << buf)) | (1u << buf) | (((q >> 1) & 1u) << (8 + buf));
+        in_flight = (in_flight & ~(0x101u << buf)) | (1u << buf) | (((q / kInBufs) & 1u) << (8 + buf));
       };
       long long u = (long long)kGroups * blockIdx.x + g;
       if (u < units.count) {
@@ -343,57 +363,64 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         int nb = 0, nx0 = 0, ny0 = 0, ny1 = 0;
         const bool has_next = u + stride < units.count;
         if (has_next) unit(u + stride, &nb, &nx0, &ny0, &ny1);
-        for (int k = 0; k < nA + 2; ++k, ++sc) {
-          const bool d1 = k < nA, d2i = k >= 2 && k < nO + 2, d3 = k >= 4;
-          const uint32_t q = qbase + (uint32_t)k;
+        for (int s = 0; s < nA + 2; ++s, ++sc) {
+          const bool d1 = s < nA, dp = s >= 1 && s <= nA, d3 = s >= 4;
+          const uint32_t q = qbase + (uint32_t)s;
           if (s_fail[g]) { ok = false; break; }
-          // the previous step's epilogues have read D1 and D3 and written a2
+          // the previous step's epilogues have read D1, D3 and their slot and
+          // written a1 and a2; the input buffer of a1 row s - 1 is free
           if (sc > 0) ok = bar_wait(bar_ep, (sc - 1) & 1u);
-          if (ok && d1) {
-            ok = bar_wait(bar_in + (q & 1u), (q >> 1) & 1u);
-            if (ok) in_flight &= ~(1u << (q & 1u));
-          }
           if (!ok) break;
           tc_after_sync();
-          // batch 1: z1 of a1 row k (halo pixels 0..127; the last two on the
-          // CUDA cores), z3 of output row k - 4
-          if (d1) {
-            const uint32_t in = wg_u32 + (q & 1u) * kInBuf, lbo = ones - in;
-            mma_bf16(tmem + 0, sdesc(in, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
-          }
-          if (d3) {
+          if (s + 2 < nA) fetch(q + 2, x0, y0 + s + 1, b);
+          else if (has_next && s + 2 - nA < 2) fetch(q + 2, nx0, ny0 - 1 + (s + 2 - nA), nb);
+          // The MMAs of one accumulator run one after another (about 68
+          // cycles apart); the three independent groups are interleaved so
+          // that the tensor core overlaps them: the bias of slot (s - 1) mod 3
+          // and the product of a1 row s - 1 (1 <= s <= nA), with z1 of a1 row
+          // s (s < nA; halo pixels 0..127, the last two on the CUDA cores)
+          // and z3 of output row s - 4 (4 <= s <= nA + 1) between its steps.
+          // A commit covers everything issued before it.
+          const int k = s - 1, pk = (k + 3) % 3;
+          const uint32_t a1 = smem_u32(sA1) + (uint32_t)(k & 1) * kSlotBytes;
+          auto prod = [&](int j) {   // j = 2 * kx + hh
+            const int kx = j >> 1, hh = j & 1;
+            mma_bf16(tmem + kColRing, sdesc(a1 + 2 * hh * kSlotChunk + kx * 16, kSlotChunk, 128),
+                     sdesc(smem_u32(sW2) + pk * kW2Perm + j * 256, 128, 1536), idesc_bf16(128, 96), 1u);
+          };
+          auto z3 = [&](int h) {
             const uint32_t a2 = smem_u32(sA2);
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-              mma_bf16(tmem + 96, sdesc(a2 + 2 * h * (kTileW * 16), kTileW * 16, 128),
-                       sdesc(smem_u32(sW3) + h * 256, 128, 512), idesc_bf16(128, 32), h ? 1u : 0u);
-          }
-          // the commit also covers the previous step's z2 MMAs
-          mma_commit(bar_mma);
-          in_flight |= 4u;
-          // a1 row k is in its ring slot and the halo pixels have read the input buffer
-          ok = bar_wait(bar_e1, sc & 1u);
-          if (!ok) break;
-          tc_after_sync();
+            mma_bf16(tmem + kColD3, sdesc(a2 + 2 * h * (kTileW * 16), kTileW * 16, 128),
+                     sdesc(smem_u32(sW3) + h * 256, 128, 512), idesc_bf16(128, 32), h ? 1u : 0u);
+          };
           if (d1) {
-            if (k + 2 < nA) fetch(q + 2, x0, y0 + k + 1, b);
-            else if (has_next) fetch(q + 2, nx0, ny0 - 1 + (k + 2 - nA), nb);
+            const uint32_t buf = q % kInBufs;
+            ok = bar_wait(bar_in + buf, (q / kInBufs) & 1u);
+            if (!ok) break;
+            in_flight = (in_flight & ~(1u << buf)) | 8u;
+            const uint32_t in = wg_u32 + buf * kInBuf, lbo = ones - in;
+            mma_bf16(tmem + kColD1, sdesc(in, lbo, 128), sdesc(smem_u32(sW1), 128, 256), idesc_bf16(128, 32), 0u);
+            mma_commit(bar_z1);
+            ++n_z1;
           }
-          // batch 2: z2 of output row k - 2 from a1 rows k - 2 .. k, into the
-          // D2 buffer of this step's parity; the next step's commit covers it
-          if (d2i) {
-            const int j = k - 2;
-            const uint32_t d2 = tmem + 32 + 32 * (uint32_t)(k & 1);
+          in_flight |= 8u;
+          if (dp) {
+            mma_bf16(tmem + kColRing + 32 * (uint32_t)pk, sdesc(ones, 2048, 128), sdesc(smem_u32(sB2), 128, 256),
+                     idesc_bf16(128, 32), 0u);
+            prod(0);
+          }
+          if (d3) z3(0);
+          if (dp) prod(1);
+          if (d3) {
+            z3(1);
+            mma_commit(bar_z3);
+            ++n_z3;
+          }
+          if (dp) {
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-              const int ky = tap / 3, kx = tap % 3;
-              const uint32_t sl = smem_u32(sRing) + ((j + ky) % kSlots) * kSlotBytes;
-#pragma unroll
-              for (int hh = 0; hh < 2; ++hh)
-                mma_bf16(d2, sdesc(sl + 2 * hh * kSlotChunk + kx * 16, kSlotChunk, 128),
-                         sdesc(smem_u32(sW2) + (2 * tap + hh) * 256, 128, (kK2 / 8) * 128), idesc_bf16(128, 32),
-                         (tap | hh) ? 1u : 0u);
-            }
+            for (int j = 2; j < 6; ++j) prod(j);
+            mma_commit(bar_prod);
+            ++n_prod;
           }
         }
         qbase += (uint32_t)nA;
@@ -404,13 +431,13 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
         // memory is released
         s_fail[g] = 1u;
         atomicOr(status, kStatusTimeout);
-        for (uint32_t buf = 0; buf < 2; ++buf)
+        for (uint32_t buf = 0; buf < kInBufs; ++buf)
           if (in_flight & (1u << buf)) bar_wait(bar_in + buf, (in_flight >> (8 + buf)) & 1u);
       }
       // the last commit (and everything before it) completes
-      if (in_flight & 4u) {
-        mma_commit(bar_mma2);
-        bar_wait(bar_mma2, 0u);
+      if (in_flight & 8u) {
+        mma_commit(bar_drain);
+        bar_wait(bar_drain, 0u);
       }
     }
   } else {
@@ -422,23 +449,23 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
       int b, x0, y0, y1;
       unit(u, &b, &x0, &y0, &y1);
       const int nO = y1 - y0, nA = nO + 2;
-      for (int k = 0; k < nA + 2; ++k, ++sc) {
-        const bool d1 = k < nA, d2 = k >= 3 && k < nO + 3, d3 = k >= 4;
-        const uint32_t q = qbase + (uint32_t)k;
+      for (int s = 0; s < nA + 2; ++s, ++sc) {
+        const bool d1 = s < nA, d2 = s >= 3 && s <= nA, d3 = s >= 4;
+        const uint32_t q = qbase + (uint32_t)s;
         if (s_fail[g]) { ok = false; break; }
-        // batch 1 of this step and the previous step's z2 have completed
-        ok = bar_wait(bar_mma, sc & 1u);
-        if (!ok) break;
-        tc_after_sync();
-        // epilogue 1: a1 row r = y0 - 1 + k (zero outside the image) -> slot;
-        // slot pixel i <-> x = x0 - 1 + i
+        // epilogue 1: a1 row r = y0 - 1 + s (zero outside the image) -> a1
+        // buffer s mod 2; buffer pixel i <-> x = x0 - 1 + i
         if (d1) {
-          const int r = y0 - 1 + k;
+          ok = bar_wait(bar_z1, n_z1 & 1u);
+          ++n_z1;
+          if (!ok) break;
+          tc_after_sync();
+          const int r = y0 - 1 + s;
           const bool row_in = r >= 0 && r < H, own_row = r >= y0 && r < y1;
-          uint8_t *slot = sRing + (k % kSlots) * kSlotBytes;
+          uint8_t *a1 = sA1 + (s & 1) * kSlotBytes;
           {
             float z[32];
-            tmem_ld32(tmem + lane_base, z);
+            tmem_ld32(tmem + lane_base + kColD1, z);
             const int i = p, xx = x0 - 1 + i;
             const bool in = row_in && xx >= 0 && xx < W;
             uint32_t w[16];
@@ -446,7 +473,7 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
             for (int e = 0; e < 16; ++e) w[e] = in ? relu_bf16x2(z[2 * e], z[2 * e + 1]) : 0u;
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-              *reinterpret_cast<uint4 *>(slot + c * kSlotChunk + i * 16) =
+              *reinterpret_cast<uint4 *>(a1 + c * kSlotChunk + i * 16) =
                   make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
             if (acts && own_row && i >= 1 && xx < W) {
               uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + r) * W + xx) * 96);
@@ -456,12 +483,12 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
           }
           // halo pixels i = 128 (warp 1) and 129 (warp 2): lane = output
           // channel, z1 = W1 x + hi + lo in FP32 from the row's input buffer
-          // (refilled only after this step's epilogue 1)
+          // (refilled only after this step's epilogues)
           if (warp == 1 || warp == 2) {
-            ok = bar_wait(bar_in + (q & 1u), (q >> 1) & 1u);
+            ok = bar_wait(bar_in + q % kInBufs, (q / kInBufs) & 1u);
             const int i = kTileW - 1 + warp, xx = x0 - 1 + i, c = lane;
             const bool in = row_in && xx >= 0 && xx < W;
-            const uint4 xv = *reinterpret_cast<const uint4 *>(wg + (q & 1u) * kInBuf + i * 16);
+            const uint4 xv = *reinterpret_cast<const uint4 *>(wg + (q % kInBufs) * kInBuf + i * 16);
             const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
             float zc = 0.f;
 #pragma unroll
@@ -471,41 +498,21 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
             }
             zc = (zc + sb1h[c]) + sb1l[c];
             const uint16_t a = in ? bf16_bits(fmaxf(zc, 0.f)) : (uint16_t)0;
-            *reinterpret_cast<uint16_t *>(slot + (c >> 3) * kSlotChunk + i * 16 + (c & 7) * 2) = a;
+            *reinterpret_cast<uint16_t *>(a1 + (c >> 3) * kSlotChunk + i * 16 + (c & 7) * 2) = a;
             if (acts && own_row && i <= kTileW && xx < W) acts[(((size_t)b * H + r) * W + xx) * 96 + c] = a;
           }
           fence_async_smem();
         }
-        tc_before_sync();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar_e1);
-        // epilogue 2: a2 of output row y0 + k - 3 (z2 of the previous step's
-        // D2 buffer) -> a2 buffer
-        if (d2) {
-          const int y = y0 + k - 3;
-          float z[32];
-          tmem_ld32(tmem + lane_base + 32 + 32 * (uint32_t)((k - 1) & 1), z);
-          uint32_t w[16];
-#pragma unroll
-          for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e] + sb2f[2 * e], z[2 * e + 1] + sb2f[2 * e + 1]);
-          uint8_t *a2 = sA2;
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-            *reinterpret_cast<uint4 *>(a2 + c * (kTileW * 16) + p * 16) =
-                make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-          if (acts && x0 + p < W) {
-            uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
-          }
-          fence_async_smem();
-        }
         // epilogue 3: a3, the dot product with w4 and the sigmoid of output
-        // row y0 + k - 4
-        if (d3) {
-          const int y = y0 + k - 4;
+        // row y0 + s - 4
+        if (ok && d3) {
+          ok = bar_wait(bar_z3, n_z3 & 1u);
+          ++n_z3;
+          if (!ok) break;
+          tc_after_sync();
+          const int y = y0 + s - 4;
           float z[32];
-          tmem_ld32(tmem + lane_base + 96, z);
+          tmem_ld32(tmem + lane_base + kColD3, z);
           float acc = sb4[0];
           uint32_t w[16];
 #pragma unroll
@@ -515,13 +522,43 @@ mpnet_fwd_kernel(const __grid_constant__ CUtensorMap in_map, const uint8_t *__re
           }
           if (x0 + p < W) {
             const size_t pix = ((size_t)b * H + y) * W + x0 + p;
-            out[pix] = 1.f / (1.f + expf(-acc));
+            out[pix] = __fdividef(1.f, 1.f + __expf(-acc));
             if (acts) {
               uint4 *ga = reinterpret_cast<uint4 *>(acts + pix * 96 + 64);
 #pragma unroll
               for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
             }
           }
+        }
+        // epilogue 2: output row y0 + s - 3 is complete in slot s mod 3 (its
+        // bias included) -> a2 buffer
+        if (ok && d2) {
+          ok = bar_wait(bar_prod, n_prod & 1u);
+          ++n_prod;
+          if (!ok) break;
+          tc_after_sync();
+          const int y = y0 + s - 3;
+          float z[32];
+          tmem_ld32(tmem + lane_base + kColRing + 32 * (uint32_t)(s % 3), z);
+          uint32_t w[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) w[e] = relu_bf16x2(z[2 * e], z[2 * e + 1]);
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+            *reinterpret_cast<uint4 *>(sA2 + c * (kTileW * 16) + p * 16) =
+                make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+          if (acts && x0 + p < W) {
+            uint4 *ga = reinterpret_cast<uint4 *>(acts + (((size_t)b * H + y) * W + x0 + p) * 96 + 32);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) ga[c] = make_uint4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
+          }
+          fence_async_smem();
+        } else if (ok && s >= 1 && s <= nA) {
+          // a product without a complete output row: its commit still has a
+          // phase to pass
+          ok = bar_wait(bar_prod, n_prod & 1u);
+          ++n_prod;
+          if (!ok) break;
         }
         tc_before_sync();
         __syncwarp();
