@@ -156,9 +156,10 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 //
 // Pipeline, step s of a unit with nO output rows (nA = nO + 2 a1 rows):
 //   control: wait for the previous step's epilogues; fetch the input of a1
-//     row s + 2; z1 of a1 row s (s < nA), commit; z3 of output row s - 4
-//     (4 <= s <= nA + 1), commit; the bias of slot (s - 1) mod 3 and the
-//     product of a1 row s - 1 (1 <= s <= nA), commit.
+//     row s + 2; z1 of a1 row s (s < nA), commit; the bias of slot
+//     (s - 1) mod 3 and the product of a1 row s - 1 (1 <= s <= nA) with
+//     z3 of output row s - 4 (4 <= s <= nA + 1) issued between its first
+//     MMAs, commit after z3, commit after the product.
 //   epilogues: epilogue 1 once z1 is done (a1 row s into buffer s mod 2; the
 //     halo pixels 128 and 129 on the CUDA cores); epilogue 3 once z3 is done
 //     (a3, the dot product with w4 and the sigmoid of output row s - 4);
