@@ -197,3 +197,31 @@ def test_mp_update_rejects_bad_scales(dags, scales):
     with pytest.raises(dags.DagsError) as e:
         run_both(dags, d, {"scales": scales})
     assert e.value.code == -1                                   # DAGS_E_INVAL
+
+
+@pytest.mark.parametrize("w,h", [(7, 5), (5, 3), (3, 2)])
+def test_mp_update_multiscale_tiny_images(dags, w, h):
+    # images whose coarser levels have one pixel or none (5 x 3 -> 2 x 1 ->
+    # 1 x 0; 3 x 2 -> 1 x 1 -> 0 x 0): Gaussians projected in and around them
+    rng = np.random.default_rng(w * 10 + h)
+    n = 400
+    cam = synth.Camera(4.0, 4.0, w / 2.0, h / 2.0, w, h)
+    z = rng.uniform(1.0, 3.0, n)
+    u = rng.uniform(-4.0, w + 3.0, n)
+    v = rng.uniform(-4.0, h + 3.0, n)
+    rec = np.zeros((n, 16), np.float32)
+    rec[:, 0] = (u - cam.cx) * z / cam.fx
+    rec[:, 1] = (v - cam.cy) * z / cam.fy
+    rec[:, 2] = z
+    rec[:, 11] = rng.uniform(0.05, 0.95, n)
+    P = w * h
+    rend = np.concatenate([rng.uniform(0, 1, (P, 3)), rng.uniform(1.0, 3.5, (P, 1))], 1).astype(np.float32)
+    obs = rend.copy()
+    obs[:, 3] += rng.normal(0, 0.2, P).astype(np.float32)
+    obs[:, 0:3] = rng.uniform(0, 1, (P, 3))
+    d = dict(rec=rec, cam=cam, pose=synth.identity_pose(), obs=obs, rend=rend,
+             inst=(rng.random(P) < 0.3).astype(np.uint8), table=np.array([[0.1, 0.05], [0.9, 0.8]], np.float32),
+             labels0=(rng.random(n) < 0.3).astype(np.uint8))
+    gpu, ref = run_both(dags, d, {"scales": 3, "vis_tol": 0.3})
+    assert ref["observed"].sum() > 20
+    check(gpu, ref, 2)
