@@ -215,7 +215,12 @@ __device__ void lm_step_cta(const double *nrm, double *state, double *pose_try, 
   }
 }
 
-__global__ void __launch_bounds__(kTilePix, 2)
+// Three CTAs per SM (a budget of 80 registers, 30 tangent accumulators per
+// pixel, some of them spilled to L1): the kernel is bound by instruction
+// issue, and six warps per scheduler hide more latency than the four that
+// the unspilled 118 registers allowed (146 against 160 us per launch at the
+// tracking size; four CTAs per SM spill more and take 154).
+__global__ void __launch_bounds__(kTilePix, 3)
 render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__restrict__ targets,
                   const float4 *__restrict__ tan, float *__restrict__ partial, double *__restrict__ normal,
                   float *__restrict__ jac, float *__restrict__ image, int32_t *__restrict__ last, LmFuse fuse) {
