@@ -1171,7 +1171,7 @@ int mp_update(dags_ctx *ctx, float *gauss, int64_t n, const dags_camera *cam, co
   const int ev = ctx->timer.begin(DAGS_K_MP_GAUSS, s);
   const cudaError_t e = launch_mp_update(ctx->mp, gauss, n, pose, r, reinterpret_cast<const float4 *>(targets),
                                          image, inst, table, n_regions, c, seg_refreshed ? 1 : 0, labels, stats,
-                                         mp_map, mp_pixel, ctx->ws.counters + CNT_STATUS, s);
+                                         mp_map, mp_pixel, ctx->ws.counters + CNT_STATUS, ctx->num_sms, s);
   ctx->timer.end(ev, s);
   return cuda_status(e);
 }

@@ -297,7 +297,7 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
                              double *stats, const float *mp_map, float *mp_pixel, uint32_t *status,
-                             cudaStream_t s);
+                             int num_sms, cudaStream_t s);
 cudaError_t launch_mpnet_features(const float *image, const float4 *targets, const uint8_t *inst, const float *table,
                                   int n_regions, int P, uint16_t *feats, uint32_t *status, cudaStream_t s);
 

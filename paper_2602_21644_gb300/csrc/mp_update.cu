@@ -100,6 +100,7 @@ __device__ __forceinline__ float residual(const float4 tg, const float *img, siz
 __global__ void __launch_bounds__(kMpBlock)
 mp_pixel_sum_kernel(MpWs m, const float4 *__restrict__ targets, const float *__restrict__ image,
                     const uint8_t *__restrict__ inst, int P, MpCfg c) {
+  pdl_wait();
   __shared__ float s_cnt[DAGS_MP_MAX_REGIONS], s_sum[DAGS_MP_MAX_REGIONS];
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) { s_cnt[k] = 0.f; s_sum[k] = 0.f; }
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,6 +145,7 @@ mp_pixel_sum_kernel(MpWs m, const float4 *__restrict__ targets, const float *__r
 
 __global__ void __launch_bounds__(kMpBlock)
 mp_pixel_var_kernel(MpWs m, const uint8_t *__restrict__ inst, int P, MpCfg c) {
+  pdl_wait();
   __shared__ float s_mean[DAGS_MP_MAX_REGIONS], s_sq[DAGS_MP_MAX_REGIONS];
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
     const double cnt = m.acc[4 * k + 0];
@@ -231,6 +233,7 @@ __device__ __forceinline__ float disk_std(const float *__restrict__ e, int x, in
 __global__ void __launch_bounds__(kMpBlock)
 mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__restrict__ table, int W, int H,
                     MpCfg c) {
+  pdl_wait();
   __shared__ float4 s_reg[DAGS_MP_MAX_REGIONS];
   __shared__ float2 s_tab[DAGS_MP_MAX_REGIONS];
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
@@ -255,6 +258,7 @@ mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__re
 // the full-resolution pixels it covers).
 __global__ void __launch_bounds__(kMpBlock)
 mp_pyramid_kernel(MpWs m, int s, float *__restrict__ om, float *__restrict__ oe, float *__restrict__ od) {
+  pdl_wait();
   const int W = m.lw[s], H = m.lh[s], Wp = m.lw[s - 1];
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= W * H) return;
@@ -281,6 +285,7 @@ __device__ __forceinline__ bool disk_rect(float us, float vs, int Ws, int Hs, fl
 __global__ void __launch_bounds__(kMpBlock)
 mp_gauss_kernel(MpWs m, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
                 const float *__restrict__ image, Raster r, MpCfg c) {
+  pdl_wait();
   __shared__ float sp[12];
   __shared__ uint32_t s_min, s_max, s_cnt;
   const float *__restrict__ mpsrc = m.mp_map ? m.mp_map : m.mpf;
@@ -464,12 +469,13 @@ __device__ void select_finish(const MpWs &m, int level, const MpCfg &c) {
 
 __global__ void __launch_bounds__(kMpBlock)
 mp_apply_kernel(MpWs m, float4 *__restrict__ gauss, int64_t n, MpCfg c) {
+  pdl_wait();
   __shared__ uint32_t s_h[2 * kSelBins];
   for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x) s_h[k] = 0u;
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && m.obs[i]) {
-    const float umin = o2f(m.sel[1]), umax = o2f(m.sel[2]);
+  const float umin = o2f(m.sel[1]), umax = o2f(m.sel[2]);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!m.obs[i]) continue;
     const float ut = umax > umin ? (m.U[i] - umin) / (umax - umin) : 0.f;
     const float C = expf(-m.sige[i] / c.sigma_c);
     float a = c.alpha_min + (c.alpha_max - c.alpha_min) * (1.f - ut) * C;
@@ -492,6 +498,7 @@ mp_apply_kernel(MpWs m, float4 *__restrict__ gauss, int64_t n, MpCfg c) {
 
 __global__ void __launch_bounds__(kMpBlock)
 mp_select_kernel(MpWs m, int64_t n, int level, MpCfg c) {
+  pdl_wait();
   __shared__ uint32_t s_h[2 * kSelBins];
   for (int k = threadIdx.x; k < 2 * kSelBins; k += blockDim.x) s_h[k] = 0u;
   __syncthreads();
@@ -499,9 +506,9 @@ mp_select_kernel(MpWs m, int64_t n, int level, MpCfg c) {
   uint32_t mask;
   select_shift(level, &shift, &mask);
   const int top = shift + (level == 2 ? 10 : 11);   // bits above this level are the prefix
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n && m.obs[i]) {
-    const uint32_t pm = m.sel[4], pu = m.sel[5];
+  const uint32_t pm = m.sel[4], pu = m.sel[5];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!m.obs[i]) continue;
     const uint32_t bm = __float_as_uint(m.Mt[i]), bu = __float_as_uint(m.Ut[i]);
     if ((bm >> top) == (pm >> top)) atomicAdd(&s_h[(bm >> shift) & mask], 1u);
     if ((bu >> top) == (pu >> top)) atomicAdd(&s_h[kSelBins + ((bu >> shift) & mask)], 1u);
@@ -514,12 +521,14 @@ mp_select_kernel(MpWs m, int64_t n, int level, MpCfg c) {
 
 __global__ void __launch_bounds__(kMpBlock)
 mp_labels_kernel(MpWs m, int64_t n, uint8_t *__restrict__ labels) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || !m.obs[i]) return;
-  labels[i] = (double)m.Mt[i] > m.stats[0] ? 1 : 0;
+  pdl_wait();
+  const double tau = m.stats[0];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (m.obs[i]) labels[i] = (double)m.Mt[i] > tau ? 1 : 0;
 }
 
 __global__ void mp_region_stats_kernel(MpWs m, MpCfg c) {
+  pdl_wait();
   for (int k = threadIdx.x; k < c.n_regions; k += blockDim.x) {
     float4 reg;
     region_params(m, c, k, &reg);
@@ -559,7 +568,7 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
                              const float4 *targets, const float *image, const uint8_t *inst, const float *table,
                              int n_regions, const dags_mp_cfg &cfg, int seg_refreshed, uint8_t *labels,
                              double *stats, const float *mp_map, float *mp_pixel, uint32_t *status,
-                             cudaStream_t s) {
+                             int num_sms, cudaStream_t s) {
   MpWs m;
   m.status = status;
   m.mp_map = mp_map;
@@ -603,22 +612,32 @@ cudaError_t launch_mp_update(const MpBuffers &b, float *gauss, int64_t n, const 
   if (e != cudaSuccess) return e;
   const unsigned gp = (unsigned)((P + kMpBlock - 1) / kMpBlock);
   const unsigned gg = (unsigned)((n + kMpBlock - 1) / kMpBlock > 0 ? (n + kMpBlock - 1) / kMpBlock : 1);
+  // the histogram passes (median selection) and the labels: two CTAs per SM
+  // striding over the Gaussians, so that each CTA's clearing and flushing of
+  // its 2 x 2048 shared bins is spread over several Gaussians per thread
+  const unsigned gs = gg < 2u * (unsigned)num_sms ? gg : 2u * (unsigned)num_sms;
   mp_pixel_sum_kernel<<<gp, kMpBlock, 0, s>>>(m, targets, image, inst, P, c);
-  mp_pixel_var_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, P, c);
+  if (e == cudaSuccess) e = launch_pdl(mp_pixel_var_kernel, dim3(gp), dim3(kMpBlock), 0, s, m, inst, P, c);
   if (!mp_map || mp_pixel)
-    mp_pixel_map_kernel<<<gp, kMpBlock, 0, s>>>(m, inst, reinterpret_cast<const float2 *>(table), r.W, r.H, c);
+    if (e == cudaSuccess)
+      e = launch_pdl(mp_pixel_map_kernel, dim3(gp), dim3(kMpBlock), 0, s, m, inst,
+                     reinterpret_cast<const float2 *>(table), r.W, r.H, c);
   for (int l = 1; l < c.scales; ++l) {
     const int Pl = m.lw[l] * m.lh[l];
-    if (Pl > 0)
-      mp_pyramid_kernel<<<(unsigned)((Pl + kMpBlock - 1) / kMpBlock), kMpBlock, 0, s>>>(m, l, pyr_out[l][0],
-                                                                                        pyr_out[l][1], pyr_out[l][2]);
+    if (Pl > 0 && e == cudaSuccess)
+      e = launch_pdl(mp_pyramid_kernel, dim3((unsigned)((Pl + kMpBlock - 1) / kMpBlock)), dim3(kMpBlock), 0, s, m, l,
+                     pyr_out[l][0], pyr_out[l][1], pyr_out[l][2]);
   }
-  mp_gauss_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<const float4 *>(gauss), n, pose, image, r, c);
-  mp_apply_kernel<<<gg, kMpBlock, 0, s>>>(m, reinterpret_cast<float4 *>(gauss), n, c);
-  mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 1, c);
-  mp_select_kernel<<<gg, kMpBlock, 0, s>>>(m, n, 2, c);
-  mp_labels_kernel<<<gg, kMpBlock, 0, s>>>(m, n, labels);
-  mp_region_stats_kernel<<<1, 256, 0, s>>>(m, c);
+  if (e == cudaSuccess)
+    e = launch_pdl(mp_gauss_kernel, dim3(gg), dim3(kMpBlock), 0, s, m, reinterpret_cast<const float4 *>(gauss), n,
+                   pose, image, r, c);
+  if (e == cudaSuccess)
+    e = launch_pdl(mp_apply_kernel, dim3(gs), dim3(kMpBlock), 0, s, m, reinterpret_cast<float4 *>(gauss), n, c);
+  if (e == cudaSuccess) e = launch_pdl(mp_select_kernel, dim3(gs), dim3(kMpBlock), 0, s, m, n, 1, c);
+  if (e == cudaSuccess) e = launch_pdl(mp_select_kernel, dim3(gs), dim3(kMpBlock), 0, s, m, n, 2, c);
+  if (e == cudaSuccess) e = launch_pdl(mp_labels_kernel, dim3(gs), dim3(kMpBlock), 0, s, m, n, labels);
+  if (e == cudaSuccess) e = launch_pdl(mp_region_stats_kernel, dim3(1), dim3(256), 0, s, m, c);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
