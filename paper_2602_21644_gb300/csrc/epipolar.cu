@@ -35,6 +35,7 @@ constexpr int kScanTile = kEpiBlock * kScanItems;
 // only reads it).
 __global__ void epi_F_kernel(Raster r, const double *__restrict__ pose_1, const double *__restrict__ pose_2,
                              double *__restrict__ F) {
+  pdl_wait();
   if (threadIdx.x != 0) return;
   {
     // R = R2 R1^T, t = t2 - R t1, E = [t]x R, F = K^-T E K^-1
@@ -70,6 +71,7 @@ __global__ void __launch_bounds__(kEpiBlock)
 epi_dist_kernel(const double *__restrict__ F, const float2 *__restrict__ p1, const float2 *__restrict__ p2,
                 const int32_t *__restrict__ gid, int64_t m, int64_t n, float *__restrict__ dist,
                 uint32_t *__restrict__ count, uint32_t *__restrict__ rank, uint32_t *status) {
+  pdl_wait();
   __shared__ double s_F[9];
   if (threadIdx.x < 9) s_F[threadIdx.x] = F[threadIdx.x];
   __syncthreads();
@@ -97,6 +99,7 @@ epi_dist_kernel(const double *__restrict__ F, const float2 *__restrict__ p1, con
 __global__ void __launch_bounds__(kEpiBlock)
 scan_tiles_kernel(const uint32_t *__restrict__ count, int64_t n, uint32_t *__restrict__ off,
                   uint32_t *__restrict__ block_sum) {
+  pdl_wait();
   __shared__ uint32_t s[kEpiBlock];
   const int tid = threadIdx.x;
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)tid * kScanItems;
@@ -126,6 +129,7 @@ scan_tiles_kernel(const uint32_t *__restrict__ count, int64_t n, uint32_t *__res
 // One CTA: exclusive scan of the block sums in place, sequential chunks.
 __global__ void __launch_bounds__(kEpiBlock)
 scan_sums_kernel(uint32_t *__restrict__ block_sum, int nb) {
+  pdl_wait();
   __shared__ uint32_t s[kEpiBlock];
   __shared__ uint32_t carry;
   const int tid = threadIdx.x;
@@ -150,6 +154,7 @@ scan_sums_kernel(uint32_t *__restrict__ block_sum, int nb) {
 
 __global__ void __launch_bounds__(kEpiBlock)
 scan_add_kernel(uint32_t *__restrict__ off, int64_t n, const uint32_t *__restrict__ block_sum) {
+  pdl_wait();
   const int64_t i = (int64_t)blockIdx.x * kEpiBlock + threadIdx.x;
   if (i < n) off[i] += block_sum[i / kScanTile];
 }
@@ -157,6 +162,7 @@ scan_add_kernel(uint32_t *__restrict__ off, int64_t n, const uint32_t *__restric
 __global__ void __launch_bounds__(kEpiBlock)
 epi_scatter_kernel(const int32_t *__restrict__ gid, const uint32_t *__restrict__ rank, const float *__restrict__ dist,
                    int64_t m, const uint32_t *__restrict__ off, float *__restrict__ vals) {
+  pdl_wait();
   const int64_t k = (int64_t)blockIdx.x * kEpiBlock + threadIdx.x;
   if (k >= m) return;
   const uint32_t rk = rank[k];
@@ -168,6 +174,7 @@ __global__ void __launch_bounds__(kEpiBlock)
 epi_median_kernel(const uint32_t *__restrict__ count, const uint32_t *__restrict__ off,
                   const float *__restrict__ vals, int64_t n, float eps, float m_static, float4 *__restrict__ gauss,
                   uint8_t *__restrict__ labels, float *__restrict__ dbar) {
+  pdl_wait();
   const int64_t g = (int64_t)blockIdx.x * kEpiBlock + threadIdx.x;
   if (g >= n) return;
   const uint32_t c = count[g];
@@ -210,17 +217,28 @@ cudaError_t launch_epipolar(const Raster &r, const double *pose_1, const double 
   const unsigned gm = (unsigned)((m + kEpiBlock - 1) / kEpiBlock);
   const unsigned gn = (unsigned)((n + kEpiBlock - 1) / kEpiBlock);
   const int nb = (int)epi_scan_blocks(n);
+  // programmatic launches after the first: each kernel waits for its
+  // predecessor's memory before its first access, and its launch overlaps
+  // the predecessor's last wave
   if (m > 0) {
     epi_F_kernel<<<1, 32, 0, s>>>(r, pose_1, pose_2, b.F);
-    epi_dist_kernel<<<gm, kEpiBlock, 0, s>>>(b.F, p1, p2, gid, m, n, dist, b.count, b.rank, status);
+    e = launch_pdl(epi_dist_kernel, dim3(gm), dim3(kEpiBlock), 0, s, (const double *)b.F, p1, p2, gid, m, n, dist,
+                   b.count, b.rank, status);
   }
-  if (n > 0) {
-    scan_tiles_kernel<<<(unsigned)nb, kEpiBlock, 0, s>>>(b.count, n, b.off, b.block_sum);
-    scan_sums_kernel<<<1, kEpiBlock, 0, s>>>(b.block_sum, nb);
-    scan_add_kernel<<<gn, kEpiBlock, 0, s>>>(b.off, n, b.block_sum);
+  if (n > 0 && e == cudaSuccess) {
+    e = launch_pdl(scan_tiles_kernel, dim3((unsigned)nb), dim3(kEpiBlock), 0, s, (const uint32_t *)b.count, n, b.off,
+                   b.block_sum);
+    if (e == cudaSuccess) e = launch_pdl(scan_sums_kernel, dim3(1), dim3(kEpiBlock), 0, s, b.block_sum, nb);
+    if (e == cudaSuccess)
+      e = launch_pdl(scan_add_kernel, dim3(gn), dim3(kEpiBlock), 0, s, b.off, n, (const uint32_t *)b.block_sum);
   }
-  if (m > 0) epi_scatter_kernel<<<gm, kEpiBlock, 0, s>>>(gid, b.rank, dist, m, b.off, b.vals);
-  if (n > 0) epi_median_kernel<<<gn, kEpiBlock, 0, s>>>(b.count, b.off, b.vals, n, eps, m_static, gauss, labels, dbar);
+  if (m > 0 && e == cudaSuccess)
+    e = launch_pdl(epi_scatter_kernel, dim3(gm), dim3(kEpiBlock), 0, s, gid, (const uint32_t *)b.rank,
+                   (const float *)dist, m, (const uint32_t *)b.off, b.vals);
+  if (n > 0 && e == cudaSuccess)
+    e = launch_pdl(epi_median_kernel, dim3(gn), dim3(kEpiBlock), 0, s, (const uint32_t *)b.count,
+                   (const uint32_t *)b.off, (const float *)b.vals, n, eps, m_static, gauss, labels, dbar);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

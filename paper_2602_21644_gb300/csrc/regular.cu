@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kRegBlock)
 mp_consistency_kernel(const float4 *__restrict__ gauss, const float4 *__restrict__ prev, int64_t n,
                       const float *__restrict__ rel, float lam, float *__restrict__ grad,
                       double *__restrict__ partial, uint32_t *__restrict__ done, double *__restrict__ loss) {
+  pdl_wait();
   __shared__ double s_sum[kRegBlock];
   __shared__ float s_warp[kRegBlock / 32];
   __shared__ int s_last;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kEdgeBlock)
 edge_warp_kernel(Raster r, const float *__restrict__ Di, const float *__restrict__ Dj,
                  const float *__restrict__ wj, const float *__restrict__ Tji, dags_edge_cfg c, float lam,
                  double *__restrict__ partial, uint32_t *__restrict__ done, double *__restrict__ out) {
+  pdl_wait();
   __shared__ float s_T[12];
   __shared__ float s_red[kEdgeBlock / 32][kEdgeOut];
   __shared__ int s_last;
@@ -249,8 +251,11 @@ cudaError_t launch_edge_warp(const Raster &r, const float *Di, const float *Dj, 
                              const double *pose_j, const dags_edge_cfg &c, float lam, double *partial, uint32_t *done,
                              double *out, float *tji, cudaStream_t s) {
   rel_pose_kernel<<<1, 32, 0, s>>>(pose_i, pose_j, tji);
-  edge_warp_kernel<<<(unsigned)edge_warp_blocks((int64_t)r.W * r.H), kEdgeBlock, 0, s>>>(r, Di, Dj, wj, tji, c, lam,
-                                                                                          partial, done, out);
+  // a programmatic launch: the warp's launch overlaps the one-thread kernel
+  const cudaError_t e = launch_pdl(edge_warp_kernel, dim3((unsigned)edge_warp_blocks((int64_t)r.W * r.H)),
+                                   dim3(kEdgeBlock), 0, s, r, Di, Dj, wj, (const float *)tji, c, lam, partial, done,
+                                   out);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -264,8 +269,9 @@ cudaError_t launch_mp_consistency(const float4 *gauss, const float4 *prev, int64
     return cudaSuccess;
   }
   if (rel) rel_pose_kernel<<<1, 32, 0, s>>>(nullptr, rel, rel32);
-  mp_consistency_kernel<<<(unsigned)mp_consistency_blocks(n), kRegBlock, 0, s>>>(gauss, prev, n, rel ? rel32 : nullptr,
-                                                                                 lam, grad, partial, done, loss);
+  const cudaError_t e = launch_pdl(mp_consistency_kernel, dim3((unsigned)mp_consistency_blocks(n)), dim3(kRegBlock), 0, s,
+                                   gauss, prev, n, (const float *)(rel ? rel32 : nullptr), lam, grad, partial, done, loss);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
