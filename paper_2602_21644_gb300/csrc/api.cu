@@ -841,18 +841,25 @@ int make_lm_cfg(const dags_lm_cfg *in, dags_lm_cfg *c) {
 }
 
 // Enqueues the normal equations of one view at `pose` (arguments checked).
+// track: the LM loop's iteration, on the frame's culled candidates and the
+// fixed-capacity tile buckets of the first-order loop (a cull must precede
+// the first such iteration of a frame); follows_iteration: the launch just
+// before is the previous iteration's last kernel.
 int normal_core(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, const double *pose,
                 const float *targets, const Raster &r, const Loss &l, float delta, double *normal, float *jac,
-                float *image, int32_t *last, const LmFuse &fuse, cudaStream_t s) {
+                float *image, int32_t *last, const LmFuse &fuse, bool track, bool follows_iteration,
+                cudaStream_t s) {
   ctx->last_stream = s;
   ctx->fwd_image = nullptr;     // the workspace no longer holds a forward for splat_backward
-  const Workspace &w = ctx->ws;
+  const Workspace w = track ? track_workspace(ctx, r) : ctx->ws;
+  if (track && w.bucket_cap == 0) return DAGS_E_INVAL;
   const float4 *g4 = reinterpret_cast<const float4 *>(gauss);
   KernelTimer &tm = ctx->timer;
   int ev = tm.begin(DAGS_K_PREPROCESS, s);
-  cudaError_t e = launch_preprocess(w, g4, n, pose, 1, r, 0, s);
+  cudaError_t e = track ? launch_preprocess_direct(w, g4, n, pose, r, 0, follows_iteration, s)
+                        : launch_preprocess(w, g4, n, pose, 1, r, 0, s);
   tm.end(ev, s);
-  if (e == cudaSuccess && n > 0) {
+  if (e == cudaSuccess && n > 0 && !track) {
     ev = tm.begin(DAGS_K_EMIT, s);
     e = launch_emit(w, n, 1, r, s);
     tm.end(ev, s);
@@ -874,7 +881,7 @@ int normal_core(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera 
 
 int lm_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                  const float *targets, const Raster &r, const Loss &l, const dags_lm_cfg &c, double *state,
-                 cudaStream_t s) {
+                 bool follows_iteration, cudaStream_t s) {
   // the LM step runs in the last CTA of the Jacobian render
   LmFuse fuse;
   fuse.state = state;
@@ -882,7 +889,7 @@ int lm_iteration(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera
   fuse.pose_best = pose;
   fuse.cfg = c;
   return normal_core(ctx, gauss, n, cam, ctx->lm.pose_try, targets, r, l, (float)c.delta, ctx->lm.normal, nullptr,
-                     nullptr, nullptr, fuse, s);
+                     nullptr, nullptr, fuse, true, follows_iteration, s);
 }
 
 }  // namespace
@@ -914,7 +921,7 @@ int splat_normal_equations(dags_ctx *ctx, const float *gauss, int64_t n, const d
   if ((rc = make_raster(cam, rcfg, &r)) || (rc = make_loss(lcfg, &l))) return rc;
   if ((rc = ensure_lm(ctx))) return rc;
   return normal_core(ctx, gauss, n, cam, pose, targets, r, l, (float)delta, normal, jac, image, last, LmFuse(),
-                     (cudaStream_t)stream);
+                     false, false, (cudaStream_t)stream);
 }
 
 int lm_init(dags_ctx *ctx, const double *pose, const dags_lm_cfg *cfg, double *state, double *pose_try,
@@ -960,9 +967,21 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
   cudaStream_t s = (cudaStream_t)stream;
   ctx->last_stream = s;
   if (launch_lm_init(pose, state, ctx->lm.pose_try, c.mu0, s) != cudaSuccess) return DAGS_E_CUDA;
+  // the frame's culling at its starting pose, as in the first-order loop
+  // (an iteration whose pose leaves the culling bounds takes every Gaussian)
+  if (ctx->track_order_tiles != r.T) {
+    if (launch_order_identity(ctx->track_order, r.T, s) != cudaSuccess) return DAGS_E_CUDA;
+    ctx->track_order_tiles = r.T;
+  }
+  {
+    const int ev = ctx->timer.begin(DAGS_K_PREPROCESS, s);
+    const cudaError_t e = launch_cull(track_workspace(ctx, r), reinterpret_cast<const float4 *>(gauss), n, pose, r, s);
+    ctx->timer.end(ev, s);
+    if (e != cudaSuccess) return DAGS_E_CUDA;
+  }
   if (!use_graph || ctx->timer.on) {
     for (int k = 0; k < iters; ++k)
-      if ((rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, s))) return rc;
+      if ((rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, k > 0, s))) return rc;
     return DAGS_OK;
   }
   dags_raster_cfg rc_v;
@@ -985,7 +1004,7 @@ int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_came
       const int reps = pass == 0 ? 1 : kTrackUnroll;
       if (cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return DAGS_E_CUDA;
       for (int k = 0; k < reps && rc == DAGS_OK; ++k)
-        rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, g.cap);
+        rc = lm_iteration(ctx, gauss, n, cam, pose, targets, r, l, c, state, k > 0, g.cap);
       cudaGraph_t graph = nullptr;
       const cudaError_t ce = cudaStreamEndCapture(g.cap, &graph);
       if (rc != DAGS_OK || ce != cudaSuccess) {

@@ -43,16 +43,26 @@ constexpr int kNormal = 28;      // L, the upper triangle of H (21), g (6)
 // Tangent record of a visible Gaussian: for twist direction k = 0..5 the six
 // floats (du, dv, da', db', dc', dz) at offset 6k, where (a', b', c') are the
 // exponent coefficients of the projected record (log2 units).
-__global__ void __launch_bounds__(kPrepBlock)
+__global__ void __launch_bounds__(kPrepBlock, 6)
 pose_tangent_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, Raster r,
                     float4 *__restrict__ tan) {
   pdl_wait();
-  const uint32_t nv = ws.vis_n[0];
+  // the tracking loop's bucket layout: the grid's first CTA (dispatched
+  // first, so that it runs beside the first wave) ranks the tiles by the
+  // previous Jacobian render's counts into this iteration's render order,
+  // and the visible list is still the preprocess's append cursor
+  const bool ordering = ws.order_next != nullptr;
+  if (ordering && blockIdx.x == 0) {
+    rank_tiles(ws.prev_count, r.T, ws.order_next, ws.band);
+    return;
+  }
+  const int64_t nb = (int64_t)gridDim.x - (ordering ? 1 : 0);
+  const int64_t bid = (int64_t)blockIdx.x - (ordering ? 1 : 0);
+  const uint32_t nv = ws.bucket_cap ? ws.vis_append[0] : ws.vis_n[0];
   float P[12];
 #pragma unroll
   for (int k = 0; k < 12; ++k) P[k] = ws.pose32[k];
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)nv;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = bid * blockDim.x + threadIdx.x; t < (int64_t)nv; t += nb * blockDim.x) {
     const uint32_t id = ws.vis_ids[t];
     if (!DAGS_IN_BOUNDS(id < (uint64_t)n, ws.counters + CNT_STATUS)) continue;
     const float4 g0 = __ldg(gauss + 4 * id), g1 = __ldg(gauss + 4 * id + 1), g2 = __ldg(gauss + 4 * id + 2);
@@ -233,14 +243,35 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   __shared__ int s_last;
   const unsigned FULL = 0xffffffffu;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool ovf = pairs_overflow_ws(ws);
-  const int tile = ovf ? (int)blockIdx.x : (int)ws.tile_order[blockIdx.x];
+  // the tracking loop's fixed-capacity buckets: a tile whose list overflowed
+  // its bucket is skipped and reported, and the render publishes the counts
+  // and the visible count as the forward of the first-order loop does;
+  // otherwise an overflow anywhere skips every tile
+  bool ovf;
+  int tile;
+  if (ws.bucket_cap) {
+    tile = (int)ws.tile_order[blockIdx.x];
+    const uint32_t c = ws.tile_count[tile];
+    ovf = c > ws.bucket_cap;
+    if (tid == 0) {
+      ws.prev_count[tile] = c;
+      atomicMax(reinterpret_cast<unsigned long long *>(ws.counters + CNT_REQ_LO), (unsigned long long)c * r.T);
+      if (ovf) atomicOr(ws.counters + CNT_STATUS, kStatusCapacity);
+      if (blockIdx.x == 0) {
+        ws.vis_n[0] = ws.vis_append[0];
+        ws.vis_append[0] = 0u;
+      }
+    }
+  } else {
+    ovf = pairs_overflow_ws(ws);
+    tile = ovf ? (int)blockIdx.x : (int)ws.tile_order[blockIdx.x];
+  }
   const int tx = tile % r.tiles_x, ty = tile / r.tiles_x;
   const int bx0 = tx * kTile + (warp & 1) * 8, by0 = ty * kTile + (warp >> 1) * 4;
   const int px = bx0 + (lane & 7), py = by0 + (lane >> 3);
   const bool inside = px < r.W && py < r.H;
-  const uint32_t s = ovf ? 0u : ws.tile_start[tile];
-  const uint32_t e = ovf ? 0u : ws.tile_start[tile + 1];
+  uint32_t s = 0u, e = 0u;
+  if (!ovf) tile_range(ws, tile, s, e);
   const float bcx = (float)bx0 + 3.5f, bcy = (float)by0 + 1.5f;
   const bool own_sort = sort_tile_bucket(ws, s, (int)(e - s), s_key);
 
@@ -390,10 +421,14 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
     float t = 0.f;
 #pragma unroll
     for (int w = 0; w < kTilePix / 32; ++w) t += s_red[w][tid];
-    partial[(size_t)blockIdx.x * kNormal + tid] = t;
+    // by tile, so that the final sum's order does not depend on the launch order
+    partial[(size_t)tile * kNormal + tid] = t;
   }
   __syncthreads();
   if (tid == 0) {
+    // the bucket is empty again for the next iteration's binning (its list
+    // was read before the compositing)
+    if (ws.bucket_cap) ws.tile_count[tile] = 0u;
     __threadfence();
     const unsigned int done_ctas = atomicAdd(ws.counters + CNT_DONE_RENDER, 1u);
     s_last = (done_ctas == gridDim.x - 1);
@@ -415,13 +450,19 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   }
   __syncthreads();
   __shared__ double s_nrm[kNormal];
+  // a pair-capacity overflow leaves tiles unrendered (all of them in the
+  // general layout; in the bucket layout those whose list exceeded its
+  // bucket, which the largest requirement of this iteration tells)
+  bool any_ovf = ovf;
+  if (ws.bucket_cap)
+    any_ovf = __ldcg(reinterpret_cast<const unsigned long long *>(ws.counters + CNT_REQ_LO)) >
+              (unsigned long long)ws.bucket_cap * (unsigned long long)r.T;
   if (tid < kNormal) {
     double t = 0.0;
 #pragma unroll
     for (int k = 0; k < 8; ++k) t += s_d[tid * 8 + k];
-    // a pair-capacity overflow leaves nothing rendered: the loss is NaN, so
-    // the LM step rejects this point
-    if (ovf && tid == 0) t = __longlong_as_double(0x7ff8000000000000ll);
+    // then the loss is NaN, so the LM step rejects this point
+    if (any_ovf && tid == 0) t = __longlong_as_double(0x7ff8000000000000ll);
     normal[tid] = t;
     s_nrm[tid] = t;
   }
@@ -460,7 +501,9 @@ cudaError_t launch_pose_tangents(const Workspace &ws, const float4 *gauss, int64
   if (n == 0) return cudaSuccess;
   const int64_t need = (n + kPrepBlock - 1) / kPrepBlock;
   const unsigned grid = (unsigned)(need < (int64_t)num_sms * 8 ? need : (int64_t)num_sms * 8);
-  return launch_pdl(pose_tangent_kernel, dim3(grid), dim3(kPrepBlock), 0, s, ws, gauss, n, r, tan);
+  // (plus the ranking CTA of the tracking loop)
+  return launch_pdl(pose_tangent_kernel, dim3(grid + (ws.order_next ? 1u : 0u)), dim3(kPrepBlock), 0, s, ws, gauss,
+                    n, r, tan);
 }
 
 // The Jacobian render's dynamic shared memory (the batch's tangent records)
