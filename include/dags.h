@@ -427,11 +427,18 @@ int lm_pose_step(dags_ctx *ctx, const double *normal, const dags_lm_cfg *cfg, do
                  double *pose_best, void *stream);
 
 /* iters LM iterations of one view starting from pose (device in/out, 12
- * doubles; out: T_best): lm_init, then per iteration splat_normal_equations
- * at the ctx's pose_try and lm_pose_step. state: device, DAGS_LM_STATE
- * doubles. With use_graph one iteration and a chunk of ten are captured once
- * per argument set into CUDA graphs and replayed (chunks, then single
- * iterations). */
+ * doubles; out: T_best): lm_init, then per iteration the normal equations
+ * at the ctx's pose_try (as splat_normal_equations computes them) and the
+ * step of lm_pose_step. state: device, DAGS_LM_STATE doubles. As in
+ * splat_track, the map is culled once at the starting pose and the
+ * iterations bin into fixed-capacity tile buckets (an iteration whose pose
+ * leaves the culling bounds takes every Gaussian); a tile whose list
+ * exceeds its bucket makes the iteration's loss NaN, so its point is
+ * rejected, and dags_sync_status reports DAGS_E_CAPACITY with the max_pairs
+ * that would hold every bucket. A splat_backward or dags_copy_bins after it
+ * returns DAGS_E_ORDER. With use_graph one iteration and a chunk of ten are
+ * captured once per argument set into CUDA graphs and replayed (chunks,
+ * then single iterations). */
 int splat_track_lm(dags_ctx *ctx, const float *gauss, int64_t n, const dags_camera *cam, double *pose,
                    const float *targets, const dags_raster_cfg *rcfg, const dags_loss_cfg *lcfg,
                    const dags_lm_cfg *lmcfg, int32_t iters, double *state, int32_t use_graph, void *stream);
