@@ -49,6 +49,7 @@ enum {
   CNT_PAD,             // (keeps the 64-bit requirement 8-byte aligned)
   CNT_REQ_LO,          // pairs required by the last forward (low / high word)
   CNT_REQ_HI,
+  CNT_RECULL,          // tracking loop: the next preprocess re-culls at its pose
   CNT_N
 };
 
@@ -317,6 +318,35 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // before its own pdl_wait, data written two or more launches earlier (and
 // nothing this kernel writes). Harmless without the launch attribute.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Culling bounds of the tracking loop (the per-frame cull in splat_fwd.cu):
+// poses within kCullRot rad and kCullTrans m of the pose the candidates were
+// culled at.
+constexpr float kCullRot = 0.01f, kCullTrans = 0.01f, kCullNear = 0.5f, kCullGrow = 1.25f;
+
+// Whether pose P (FP32, 3x4) lies within the culling bounds of pose C:
+// the relative motion p -> R_d p + t_d, R_d = R_P R_C^T, t_d = t_P - R_d t_C,
+// with ||R_d - I||_F / (2 sqrt 2) = sin(theta / 2) <= sin(kCullRot / 2) and
+// |t_d| <= kCullTrans (both with a rounding allowance).
+__device__ __forceinline__ bool within_cull_bounds(const float *P, const float *C) {
+  float Rd[9], fro = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      Rd[3 * a + b] = P[4 * a] * C[4 * b] + P[4 * a + 1] * C[4 * b + 1] + P[4 * a + 2] * C[4 * b + 2];
+      const float d = Rd[3 * a + b] - (a == b ? 1.f : 0.f);
+      fro += d * d;
+    }
+  float t2 = 0.f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float td = P[4 * a + 3] - (Rd[3 * a] * C[3] + Rd[3 * a + 1] * C[7] + Rd[3 * a + 2] * C[11]);
+    t2 += td * td;
+  }
+  const float s_max = 0.999f * sinf(0.5f * kCullRot);
+  return sqrtf(fro) <= 2.f * 1.41421356f * s_max && sqrtf(t2) <= 0.999f * kCullTrans;
+}
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

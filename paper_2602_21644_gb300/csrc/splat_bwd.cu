@@ -545,6 +545,24 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
     __shared__ double s_xi[6], s_sc[3];
     for (int v = 0; v < views; ++v)
       pose_adam_exp_cta(ps.poses + 12 * v, grad_pose + 6 * v, ps.state + 13 * v, ps.cfg, s_xi, s_sc);
+    // the tracking loop: if the new pose (as the preprocess stages it in
+    // FP32) has left the bounds the candidates were culled for, move the
+    // culling pose to it and empty the list; the next preprocess then takes
+    // every Gaussian once and re-culls
+    if (ordering && ws.cand_n && ws.cull_pose) {
+      __shared__ float s_np[12];
+      __shared__ int s_out;
+      __syncthreads();
+      if (tid < 12) s_np[tid] = __double2float_rn(ps.poses[tid]);
+      __syncthreads();
+      if (tid == 0) s_out = within_cull_bounds(s_np, ws.cull_pose) ? 0 : 1;
+      __syncthreads();
+      if (s_out && tid < 12) ws.cull_pose[tid] = s_np[tid];
+      if (tid == 0) {
+        if (s_out) *ws.cand_n = 0u;
+        ws.counters[CNT_RECULL] = s_out ? 1u : 0u;
+      }
+    }
   }
 }
 

@@ -380,7 +380,39 @@ preprocess_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
 // widened by 25% plus the margin, reaches the tile grid. Every Gaussian
 // nearer than kCullNear that can come in front of the near plane is a
 // candidate. A Gaussian below alpha_min opacity is never visible.
-constexpr float kCullRot = 0.01f, kCullTrans = 0.01f, kCullNear = 0.5f, kCullGrow = 1.25f;
+
+// Whether Gaussian (g0, g1, g2) is a candidate under the culling bounds of
+// pose sp (FP32 3x4): its alpha-ellipse box, widened by kCullGrow and the
+// image-motion margin, reaches the tile grid, or it is nearer than kCullNear
+// and can come in front of the near plane; never below alpha_min opacity.
+// (The tracking preprocess calls it only when it re-culls.)
+__device__ __forceinline__ bool cull_keep(const float4 g0, const float4 g1, const float4 g2, const float *sp,
+                                       const Raster &r, float margin) {
+  const float x = sp[0] * g0.x + sp[1] * g0.y + sp[2] * g0.z + sp[3];
+  const float y = sp[4] * g0.x + sp[5] * g0.y + sp[6] * g0.z + sp[7];
+  const float z = sp[8] * g0.x + sp[9] * g0.y + sp[10] * g0.z + sp[11];
+  const float m = kCullRot * sqrtf(x * x + y * y + z * z) + kCullTrans;
+  const float o = 1.f / (1.f + expf(-g0.w));
+  if (!(o > r.alpha_min)) return false;
+  if (z < kCullNear) return z > r.z_near - m;
+  Proj q;
+  if (!project_gaussian(g0, g1, g2, sp, r, q)) return false;
+  const float cnat = 2.f * (logf(q.o) - logf(r.alpha_min));
+  const float ex = kCullGrow * sqrtf(fmaxf(cnat, 0.f) * q.A) + margin;
+  const float ey = kCullGrow * sqrtf(fmaxf(cnat, 0.f) * q.C) + margin;
+  const float X1 = (float)(r.tiles_x * kTile), Y1 = (float)(r.tiles_y * kTile);
+  return q.u + ex >= 0.f && q.u - ex <= X1 && q.v + ey >= 0.f && q.v - ey <= Y1;
+}
+
+// Appends the warp's candidates to the list (every lane of the warp calls it).
+__device__ __forceinline__ void cull_append(const Workspace &ws, bool cand, uint32_t i) {
+  const unsigned ball = __ballot_sync(0xffffffffu, cand);
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (ball && lane == __ffs(ball) - 1) base = atomicAdd(ws.cand_n, (uint32_t)__popc(ball));
+  base = __shfl_sync(0xffffffffu, base, ball ? __ffs(ball) - 1 : 0);
+  if (cand) ws.cand_ids[base + __popc(ball & ((1u << lane) - 1u))] = i;
+}
 
 __global__ void __launch_bounds__(kPrepBlock)
 cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose, Raster r,
@@ -390,58 +422,15 @@ cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, const dou
   if (threadIdx.x < 12) sp[threadIdx.x] = (float)pose[threadIdx.x];
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x < 12) ws.cull_pose[threadIdx.x] = sp[threadIdx.x];
+  // the frame's own cull: no re-cull is pending
+  if (blockIdx.x == 0 && threadIdx.x == 0) ws.counters[CNT_RECULL] = 0u;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool cand = false;
   if (i < n) {
     const float4 g0 = __ldg(gauss + 4 * i), g1 = __ldg(gauss + 4 * i + 1), g2 = __ldg(gauss + 4 * i + 2);
-    const float x = sp[0] * g0.x + sp[1] * g0.y + sp[2] * g0.z + sp[3];
-    const float y = sp[4] * g0.x + sp[5] * g0.y + sp[6] * g0.z + sp[7];
-    const float z = sp[8] * g0.x + sp[9] * g0.y + sp[10] * g0.z + sp[11];
-    const float m = kCullRot * sqrtf(x * x + y * y + z * z) + kCullTrans;
-    const float o = 1.f / (1.f + expf(-g0.w));
-    if (o > r.alpha_min) {
-      Proj q;
-      if (z < kCullNear) {
-        cand = z > r.z_near - m;
-      } else if (project_gaussian(g0, g1, g2, sp, r, q)) {
-        const float cnat = 2.f * (logf(q.o) - logf(r.alpha_min));
-        const float ex = kCullGrow * sqrtf(fmaxf(cnat, 0.f) * q.A) + margin;
-        const float ey = kCullGrow * sqrtf(fmaxf(cnat, 0.f) * q.C) + margin;
-        const float X1 = (float)(r.tiles_x * kTile), Y1 = (float)(r.tiles_y * kTile);
-        cand = q.u + ex >= 0.f && q.u - ex <= X1 && q.v + ey >= 0.f && q.v - ey <= Y1;
-      }
-    }
+    cand = cull_keep(g0, g1, g2, sp, r, margin);
   }
-  const unsigned ball = __ballot_sync(0xffffffffu, cand);
-  const int lane = threadIdx.x & 31;
-  uint32_t base = 0;
-  if (ball && lane == __ffs(ball) - 1) base = atomicAdd(ws.cand_n, (uint32_t)__popc(ball));
-  base = __shfl_sync(0xffffffffu, base, ball ? __ffs(ball) - 1 : 0);
-  if (cand) ws.cand_ids[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
-}
-
-// Whether pose P (FP32, 3x4) lies within the culling bounds of pose C:
-// the relative motion p -> R_d p + t_d, R_d = R_P R_C^T, t_d = t_P - R_d t_C,
-// with ||R_d - I||_F / (2 sqrt 2) = sin(theta / 2) <= sin(kCullRot / 2) and
-// |t_d| <= kCullTrans (both with a rounding allowance).
-__device__ __forceinline__ bool within_cull_bounds(const float *P, const float *C) {
-  float Rd[9], fro = 0.f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      Rd[3 * a + b] = P[4 * a] * C[4 * b] + P[4 * a + 1] * C[4 * b + 1] + P[4 * a + 2] * C[4 * b + 2];
-      const float d = Rd[3 * a + b] - (a == b ? 1.f : 0.f);
-      fro += d * d;
-    }
-  float t2 = 0.f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float td = P[4 * a + 3] - (Rd[3 * a] * C[3] + Rd[3 * a + 1] * C[7] + Rd[3 * a + 2] * C[11]);
-    t2 += td * td;
-  }
-  const float s_max = 0.999f * sinf(0.5f * kCullRot);
-  return sqrtf(fro) <= 2.f * 1.41421356f * s_max && sqrtf(t2) <= 0.999f * kCullTrans;
+  cull_append(ws, cand, (uint32_t)i);
 }
 
 // The tracking loop's preprocess (one view, fixed-capacity buckets) over
@@ -453,9 +442,9 @@ __device__ __forceinline__ bool within_cull_bounds(const float *P, const float *
 // predecessor's tail.
 __global__ void __launch_bounds__(kPrepBlock, 6)
 preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n, const double *__restrict__ pose,
-                       Raster r, int zero_words, int prefetch) {
+                       Raster r, int zero_words, int prefetch, float margin) {
   __shared__ float sp[12], spl[12];
-  __shared__ int s_valid;
+  __shared__ int s_valid, s_recull;
   const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t pre_count = 0, pre_i = 0;
   Rec pre;
@@ -469,13 +458,20 @@ preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n
   pdl_wait();
   stage_poses(pose, 1, sp, spl);
   __syncthreads();
-  if (threadIdx.x == 0) s_valid = within_cull_bounds(sp, ws.cull_pose) ? 1 : 0;
+  if (threadIdx.x == 0) {
+    s_valid = within_cull_bounds(sp, ws.cull_pose) ? 1 : 0;
+    // the previous iteration's pose step left the bounds: it moved the
+    // culling pose to this pose and emptied the list, which this launch
+    // refills while it takes every Gaussian
+    s_recull = __ldcg(ws.counters + CNT_RECULL) != 0u ? 1 : 0;
+  }
   if (blockIdx.x == 0 && threadIdx.x < 12) ws.pose32[threadIdx.x] = sp[threadIdx.x];
   // the forward takes the largest bucket's requirement with atomicMax
   if (blockIdx.x == 0 && threadIdx.x == 0)
     *reinterpret_cast<unsigned long long *>(ws.counters + CNT_REQ_LO) = 0ull;
   __syncthreads();
-  const bool use_cand = s_valid != 0;
+  const bool recull = s_recull != 0;
+  const bool use_cand = s_valid != 0 && !recull;
   const int64_t count = use_cand ? (int64_t)*ws.cand_n : n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += stride) {
@@ -486,7 +482,9 @@ preprocess_cull_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n
       continue;
     }
     const int64_t i = !valid ? 0 : (use_cand ? (int64_t)ws.cand_ids[k] : k);
-    preprocess_one<true>(ws, load_rec(gauss, i, valid && i < n), i, valid && i < n, 0, sp, spl, r, zero_words);
+    const Rec rec = load_rec(gauss, i, valid && i < n);
+    if (recull) cull_append(ws, valid && i < n && cull_keep(rec.g0, rec.g1, rec.g2, sp, r, margin), (uint32_t)i);
+    preprocess_one<true>(ws, rec, i, valid && i < n, 0, sp, spl, r, zero_words);
   }
 }
 
@@ -758,6 +756,13 @@ cudaError_t launch_preprocess(const Workspace &ws, const float4 *gauss, int64_t 
   return e;
 }
 
+// The candidates' image motion bound: (rot (1 + L)^2 + trans / near) f, L
+// the guard-clamped half field of view, times 2.
+static float cull_margin(const Raster &r) {
+  const float L = fmaxf(r.limx, r.limy), f = fmaxf(r.fx, r.fy);
+  return 2.f * f * (kCullRot * (1.f + L) * (1.f + L) + kCullTrans / kCullNear);
+}
+
 cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose,
                                      const Raster &r, int zero_grad_words, bool prefetch, cudaStream_t s) {
   if (ws.bucket_cap == 0 || !ws.cand_ids) return cudaErrorInvalidValue;
@@ -766,7 +771,7 @@ cudaError_t launch_preprocess_direct(const Workspace &ws, const float4 *gauss, i
   const unsigned gx = (unsigned)((n + kPrepBlock - 1) / kPrepBlock);
   const unsigned g = gx < (unsigned)(6 * ws.band) ? (gx > 0 ? gx : 1u) : (unsigned)(6 * ws.band);
   return launch_pdl(preprocess_cull_kernel, dim3(g), dim3(kPrepBlock), 0, s, ws, gauss, n, pose, r,
-                    zero_grad_words, prefetch ? 1 : 0);
+                    zero_grad_words, prefetch ? 1 : 0, cull_margin(r));
 }
 
 cudaError_t launch_order_identity(uint32_t *order, int tiles, cudaStream_t s) {
@@ -777,10 +782,7 @@ cudaError_t launch_order_identity(uint32_t *order, int tiles, cudaStream_t s) {
 
 cudaError_t launch_cull(const Workspace &ws, const float4 *gauss, int64_t n, const double *pose, const Raster &r,
                         cudaStream_t s) {
-  // the candidates' image motion bound: (rot (1 + L)^2 + trans / near) f, L
-  // the guard-clamped half field of view, times 2
-  const float L = fmaxf(r.limx, r.limy), f = fmaxf(r.fx, r.fy);
-  const float margin = 2.f * f * (kCullRot * (1.f + L) * (1.f + L) + kCullTrans / kCullNear);
+  const float margin = cull_margin(r);
   cudaError_t e = cudaMemsetAsync(ws.cand_n, 0, sizeof(uint32_t), s);
   if (e != cudaSuccess || n == 0) return e;
   return launch_pdl(cull_kernel, dim3((unsigned)((n + kPrepBlock - 1) / kPrepBlock)), dim3(kPrepBlock), 0, s, ws,
