@@ -469,7 +469,27 @@ render_jac_kernel(Workspace ws, Raster r, Loss l, float delta, const float4 *__r
   if (tid == 0) ws.counters[CNT_DONE_RENDER] = 0u;
   __syncthreads();
   // inside the LM loop the step runs here, in the last CTA
-  if (fuse.state) lm_step_cta(s_nrm, fuse.state, fuse.pose_try, fuse.pose_best, fuse.cfg);
+  if (fuse.state) {
+    lm_step_cta(s_nrm, fuse.state, fuse.pose_try, fuse.pose_best, fuse.cfg);
+    // the bucket layout: if the next linearisation point (as the preprocess
+    // stages it in FP32) has left the bounds the candidates were culled for,
+    // move the culling pose to it and empty the list; the next preprocess
+    // then takes every Gaussian once and re-culls
+    if (ws.bucket_cap && ws.cand_n && ws.cull_pose) {
+      __shared__ float s_np[12];
+      __shared__ int s_out;
+      __syncthreads();
+      if (tid < 12) s_np[tid] = __double2float_rn(fuse.pose_try[tid]);
+      __syncthreads();
+      if (tid == 0) s_out = within_cull_bounds(s_np, ws.cull_pose) ? 0 : 1;
+      __syncthreads();
+      if (s_out && tid < 12) ws.cull_pose[tid] = s_np[tid];
+      if (tid == 0) {
+        if (s_out) *ws.cand_n = 0u;
+        ws.counters[CNT_RECULL] = s_out ? 1u : 0u;
+      }
+    }
+  }
 }
 
 __global__ void lm_init_kernel(const double *__restrict__ pose, double *__restrict__ state,
