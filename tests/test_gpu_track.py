@@ -166,3 +166,47 @@ def test_culled_iterations_render_what_an_unculled_forward_renders(dags, lr):
     np.testing.assert_allclose(t["image"].cpu().numpy(), image_ref.cpu().numpy(), rtol=1e-5, atol=1e-6)
     assert (t["last"] != last_ref).float().mean().item() < 1e-4
     ctx.close()
+
+
+def test_recull_iterations_render_what_an_unculled_forward_renders(dags):
+    # Adam's steps move each twist component by about lr = 5e-3: one step
+    # stays within the culling bounds (0.01 rad, 0.01 m), two leave them, so
+    # the third iteration re-culls at its pose and the fourth renders from
+    # the re-culled candidates. Its image must be what splat_forward (no
+    # culling) renders at that pose.
+    sc = synth.tracking_scene(60_000, frame=12, width=320, height=240)
+    cam, t = setup(dags, sc)
+    ctx = dags.Context(sc.records.shape[0], cam.width, cam.height, 1)
+    pcfg = dags.default_pose_cfg(lr=[5e-3] * 6)
+    start = t["pose"].clone()
+
+    def rel(a, b):
+        a, b = a.cpu().numpy()[0], b.cpu().numpy()[0]
+        R = a[:, :3] @ b[:, :3].T
+        return np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1)), np.linalg.norm(a[:, 3] - R @ b[:, 3])
+
+    poses = []
+    for iters in (1, 2, 3):
+        t["pose"].copy_(start)
+        t["state"].zero_()
+        ctx.track(t["gauss"], cam, t["pose"], t["targets"], iters, t["state"], t["image"], t["last"], t["loss"],
+                  t["gp"], pcfg=pcfg, use_graph=False)
+        torch.cuda.synchronize()
+        poses.append(t["pose"].clone())
+    a1, d1 = rel(poses[0], start)
+    a2, d2 = rel(poses[1], start)
+    assert a1 < 0.01 and d1 < 0.01, (a1, d1)          # the second iteration uses the frame's list
+    assert a2 > 0.01 or d2 > 0.01, (a2, d2)           # the third re-culls at its pose
+    a3, d3 = rel(poses[2], poses[1])
+    assert a3 < 0.01 and d3 < 0.01, (a3, d3)          # the fourth uses the re-culled list
+    image_ref, last_ref, _ = ctx.forward(t["gauss"], cam, poses[2], t["targets"])
+    torch.cuda.synchronize()
+    t["pose"].copy_(start)
+    t["state"].zero_()
+    ctx.track(t["gauss"], cam, t["pose"], t["targets"], 4, t["state"], t["image"], t["last"], t["loss"], t["gp"],
+              pcfg=pcfg, use_graph=False)
+    torch.cuda.synchronize()
+    ctx.check()
+    np.testing.assert_allclose(t["image"].cpu().numpy(), image_ref.cpu().numpy(), rtol=1e-5, atol=1e-6)
+    assert (t["last"] != last_ref).float().mean().item() < 1e-4
+    ctx.close()
