@@ -505,7 +505,7 @@ def lm_section(args, ctx, dags, gauss, cam, targets0, pose0, gt_pose, pcfg, flus
     return {"workload": "tracking frame 10: 300k Gaussians, 640x480, 15 LM iterations per frame",
             "us_per_iter": round(1e3 * t_frame / iters, 3), "iters_per_s": round(iters / (t_frame * 1e-3), 1),
             "kernels": kern, "roofline": roof,
-            "gpu_launches_per_iter": 4,
+            "gpu_launches_per_iter": 3,
             "convergence": {"target": "the map rendered at the ground-truth pose",
                             "start_error": {"mm": round(1e3 * e0[0], 4), "deg": round(float(np.degrees(e0[1])), 5)},
                             "lm_15_iters": {"mm": round(1e3 * e_lm[0], 4), "deg": round(float(np.degrees(e_lm[1])), 5),
