@@ -8,7 +8,7 @@
 // z2 = conv3x3(a1) + b2 (32 -> 32, zero pad), a2 = bf16(relu); z3 = W3 a2 +
 // b3, a3 = bf16(relu); y = sigmoid(w4 . a3 + b4).
 //
-// mpnet_fwd_kernel   inference (and the training forward): four warpgroups
+// mpnet_fwd_kernel   inference (and the training forward): three warpgroups
 //                    per CTA (four epilogue warps and one MMA-issuing
 //                    control warp each) walk 128-pixel column strips row by
 //                    row in a software pipeline (see its comment).
