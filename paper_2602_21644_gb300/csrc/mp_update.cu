@@ -224,6 +224,32 @@ __device__ __forceinline__ float disk_std(const float *__restrict__ e, int x, in
   return sqrtf(sq / (float)cnt);
 }
 
+// The same for a disk of at most 5 x 5 pixels (floor(r_s) = 2, the default
+// radius): the box unrolled, one pass over the values less the centre's
+// (sums of d and d^2, whose mean square less the squared mean is the
+// population variance; the shift keeps both sums small).
+__device__ __forceinline__ float disk_std_r2(const float *__restrict__ e, int x, int y, int W, int H, float rs2) {
+  const float c = __ldg(e + (size_t)y * W + x);
+  float s = 0.f, s2 = 0.f, cnt = 0.f;
+#pragma unroll
+  for (int dj = -2; dj <= 2; ++dj) {
+    const int yy = y + dj;
+    const bool row = yy >= 0 && yy < H;
+#pragma unroll
+    for (int di = -2; di <= 2; ++di) {
+      const int xx = x + di;
+      if (row && xx >= 0 && xx < W && (float)(di * di + dj * dj) <= rs2) {
+        const float d = __ldg(e + (size_t)yy * W + xx) - c;
+        s += d;
+        s2 = fmaf(d, d, s2);
+        cnt += 1.f;
+      }
+    }
+  }
+  const float m = s / cnt;
+  return sqrtf(fmaxf(s2 / cnt - m * m, 0.f));
+}
+
 // The fused per-pixel M_p map, Eqs. (2)-(7): read by the gather and, when
 // asked for, returned to the caller (who may train or evaluate a learned
 // proposal against the method). Gamma_geo = exp(-sigma / sigma_g) takes the
@@ -245,7 +271,11 @@ mp_pixel_map_kernel(MpWs m, const uint8_t *__restrict__ inst, const float2 *__re
   if (p < W * H) {
     const int k = region_of(inst, p, c.n_regions, m.status);
     float4 reg = s_reg[k];
-    if (k == 0) reg.z = expf(-disk_std(m.e, p % W, p / W, W, H, c.r_s) / c.sigma_g);
+    if (k == 0) {
+      const float sd = floorf(c.r_s) == 2.f ? disk_std_r2(m.e, p % W, p / W, W, H, c.r_s * c.r_s)
+                                            : disk_std(m.e, p % W, p / W, W, H, c.r_s);
+      reg.z = expf(-sd / c.sigma_g);
+    }
     const float mp = pixel_mp(m.e[p], reg, s_tab[k], c.fusion_mode);
     m.mpf[p] = mp;
     if (m.mp_pixel) m.mp_pixel[p] = mp;
