@@ -710,27 +710,37 @@ __device__ inline void pose_adam_exp(double *T, const double *grad, double *st, 
 // component's Adam moments each, thread 0 the scalar series, threads 0-11
 // one entry of the new 3x4 pose each. Must be called by all threads of the
 // CTA (it synchronises); xi_s, sc_s are shared scratch of 6 and 3 doubles.
+// The bias corrections 1 / (1 - beta1^k) and 1 / sqrt(1 - beta2^k) of the
+// step that follows state st (they depend on its step count only).
+__device__ inline double adam_bias1(const dags_pose_cfg &cfg, double k) { return 1.0 / (1.0 - pow_int(cfg.beta1, k)); }
+__device__ inline double adam_bias2(const dags_pose_cfg &cfg, double k) {
+  return 1.0 / sqrt(1.0 - pow_int(cfg.beta2, k));
+}
+
+// pre_sc: the two bias corrections when the caller formed them already
+// (from the same step count), or null.
 __device__ inline void pose_adam_exp_cta(double *T, const double *grad, double *st, const dags_pose_cfg &cfg,
-                                         double *xi_s, double *sc_s) {
+                                         double *xi_s, double *sc_s, const double *pre_sc = nullptr) {
   const int t = threadIdx.x;
   const double k = st[12] + 1.0;
-  // threads 6 and 7 form 1 / (1 - beta1^k) and 1 / sqrt(1 - beta2^k) while
-  // threads 0-5 update the moments: the step is then
+  // threads 6 and 7 form the bias corrections (unless given) while threads
+  // 0-5 update the moments and take sqrt(s2): the step is then
   // -lr (m / bc1) / (sqrt(s2) / sqrt(bc2) + eps), one division deep
-  double m = 0.0, s2 = 0.0;
+  double m = 0.0, rs = 0.0;
   if (t < 6) {
     const double g = grad[t];
     m = cfg.beta1 * st[t] + (1.0 - cfg.beta1) * g;
-    s2 = cfg.beta2 * st[6 + t] + (1.0 - cfg.beta2) * g * g;
+    const double s2 = cfg.beta2 * st[6 + t] + (1.0 - cfg.beta2) * g * g;
     st[t] = m;
     st[6 + t] = s2;
+    rs = sqrt(s2);
   } else if (t == 6) {
-    sc_s[0] = 1.0 / (1.0 - pow_int(cfg.beta1, k));
+    sc_s[0] = pre_sc ? pre_sc[0] : adam_bias1(cfg, k);
   } else if (t == 7) {
-    sc_s[1] = 1.0 / sqrt(1.0 - pow_int(cfg.beta2, k));
+    sc_s[1] = pre_sc ? pre_sc[1] : adam_bias2(cfg, k);
   }
   __syncthreads();
-  if (t < 6) xi_s[t] = -cfg.lr[t] * (m * sc_s[0]) / (sqrt(s2) * sc_s[1] + cfg.eps);
+  if (t < 6) xi_s[t] = -cfg.lr[t] * (m * sc_s[0]) / (rs * sc_s[1] + cfg.eps);
   __syncthreads();
   if (t == 0) {
     st[12] = k;

@@ -428,6 +428,15 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   // adjoint, whose 2D gradients it reads after the wait
   Proj q0;
   bool pre = false, pre_vis = false;
+  // the pose step's bias corrections depend only on the Adam step count,
+  // written by the previous iteration's step (three launches back): every
+  // CTA forms them before its wait, and the last one uses its own
+  __shared__ double s_presc[2];
+  const bool presc = !FULL && views == 1 && ps.poses != nullptr;
+  if (presc && (tid == 6 || tid == 7)) {
+    const double k = __ldcg(ps.state + 12) + 1.0;
+    s_presc[tid - 6] = tid == 6 ? adam_bias1(ps.cfg, k) : adam_bias2(ps.cfg, k);
+  }
   int64_t pre_k = 0;
   size_t pre_slot = 0;
   if (!FULL && views == 1) {
@@ -544,7 +553,8 @@ preprocess_bwd_kernel(Workspace ws, const float4 *__restrict__ gauss, int64_t n,
   if (ps.poses) {
     __shared__ double s_xi[6], s_sc[3];
     for (int v = 0; v < views; ++v)
-      pose_adam_exp_cta(ps.poses + 12 * v, grad_pose + 6 * v, ps.state + 13 * v, ps.cfg, s_xi, s_sc);
+      pose_adam_exp_cta(ps.poses + 12 * v, grad_pose + 6 * v, ps.state + 13 * v, ps.cfg, s_xi, s_sc,
+                        presc ? s_presc : nullptr);
     // the tracking loop: if the new pose (as the preprocess stages it in
     // FP32) has left the bounds the candidates were culled for, move the
     // culling pose to it and empty the list; the next preprocess then takes
