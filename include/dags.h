@@ -271,7 +271,11 @@ int gauss_adam_step(dags_ctx *ctx, float *gauss, int64_t n, float *colour, float
 /* Tracking loop: iters x { the forward with loss of splat_forward, the
  * pose-only backward of splat_backward (DAGS_GRAD_POSE), pose_step } on one
  * view, enqueued by the library -- the pose refinement of the tracking thread
- * (Sec. III) with the pose part of Eq. (27). Each iteration is four kernels:
+ * (Sec. III) with the pose part of Eq. (27). The map is culled once at the
+ * starting pose (the Gaussians that can be visible within 0.01 rad and
+ * 0.01 m of it); when a pose step leaves those bounds, the next iteration
+ * takes every Gaussian and culls again at its pose. Results do not depend
+ * on the culling. Each iteration is four kernels:
  * projection and binning straight into per-tile buckets of max_pairs /
  * tiles slots each (no scan or emit pass), the forward with loss, which also
  * records per warp the list entries its pixels took, the pose adjoint, which
